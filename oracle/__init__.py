@@ -1,0 +1,234 @@
+"""FP64 CPU oracle for GMLS stencil generation (arXiv 2104.14447, Sec. 2).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, the package smoke check and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA path.  The arithmetic lives in ``gmls_oracle.c`` (plain C, FP64,
+``-ffp-contract=off``, OpenMP over targets); this module builds it, wraps it
+with ctypes and adds the bookkeeping that is pure layout (CSR assembly, the
+per-component divergence layout).
+
+Pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` against
+textbook finite differences, a square (interpolatory) case solved by a library
+routine, exact polynomial reproduction, the least-squares projection property,
+an extended-precision normal-equation solve, an extended-precision KKT solve
+for the Neumann variant, the paper's 2D divergence-free example and the
+convergence rate m + 1 - |beta|.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from . import basis as _basis
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gmls_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libgmls_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+def _soa(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.ndim == 2, "coordinates are (dim, n) structure-of-arrays"
+    return x
+
+
+def set_threads(n: int) -> None:
+    """Limit OpenMP threads (used for the single-core baseline)."""
+    os.environ["OMP_NUM_THREADS"] = str(n)
+
+
+# ---------------------------------------------------------------- neighbours
+def knn(x, targets, k, eps_factor, halfspace=None, method="brute", cell_h=None, r0=None):
+    """k nearest neighbours of each target, sorted by (d^2, index).
+
+    Returns (idx int32 [n_tgt, k], eps float64 [n_tgt]) with
+    eps = eps_factor * sqrt(d^2 of the k-th neighbour)."""
+    x = _soa(x)
+    dim, n = x.shape
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    hs = None if halfspace is None else np.ascontiguousarray(halfspace, dtype=np.float64).reshape(len(tg), dim)
+    idx = np.empty((len(tg), k), dtype=np.int32)
+    eps = np.empty(len(tg), dtype=np.float64)
+    L = lib()
+    if method == "brute":
+        rc = L.orc_knn_brute(ctypes.c_int(dim), ctypes.c_int64(n), _p(x), ctypes.c_int64(len(tg)), _p(tg),
+                             ctypes.c_int(k), ctypes.c_double(eps_factor), _p(hs), _p(idx), _p(eps))
+    else:
+        span = float(np.max(np.ptp(x, axis=1))) if n > 1 else 1.0
+        h = cell_h if cell_h is not None else span / max(1.0, (n ** (1.0 / dim)))
+        rr = r0 if r0 is not None else h * (k ** (1.0 / dim))
+        rc = L.orc_knn_grid(ctypes.c_int(dim), ctypes.c_int64(n), _p(x), ctypes.c_int64(len(tg)), _p(tg),
+                            ctypes.c_int(k), ctypes.c_double(eps_factor), _p(hs), ctypes.c_double(h),
+                            ctypes.c_double(rr), _p(idx), _p(eps))
+    if rc != 0:
+        raise ValueError(f"oracle knn failed rc={rc} (too few neighbours?)")
+    return idx, eps
+
+
+def radius(x, targets, eps, cap, halfspace=None, method="brute", cell_h=None):
+    """All neighbours with d^2 < eps^2, sorted by (d^2, index), at most cap.
+
+    Returns (offsets int64 [n_tgt+1], idx int32 [nnz])."""
+    x = _soa(x)
+    dim, n = x.shape
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    ep = np.ascontiguousarray(eps, dtype=np.float64)
+    hs = None if halfspace is None else np.ascontiguousarray(halfspace, dtype=np.float64).reshape(len(tg), dim)
+    buf = np.empty((len(tg), cap), dtype=np.int32)
+    cnt = np.empty(len(tg), dtype=np.int32)
+    L = lib()
+    if method == "brute":
+        rc = L.orc_radius_brute(ctypes.c_int(dim), ctypes.c_int64(n), _p(x), ctypes.c_int64(len(tg)), _p(tg),
+                                _p(ep), ctypes.c_int(cap), _p(hs), _p(buf), _p(cnt))
+    else:
+        h = cell_h if cell_h is not None else float(np.max(ep))
+        rc = L.orc_radius_grid(ctypes.c_int(dim), ctypes.c_int64(n), _p(x), ctypes.c_int64(len(tg)), _p(tg),
+                               _p(ep), ctypes.c_int(cap), _p(hs), ctypes.c_double(h), _p(buf), _p(cnt))
+    if rc != 0:
+        raise ValueError(f"oracle radius failed rc={rc}")
+    off = np.zeros(len(tg) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(cnt)
+    idx = np.concatenate([buf[q, : cnt[q]] for q in range(len(tg))]) if len(tg) else np.zeros(0, np.int32)
+    return off, idx.astype(np.int32)
+
+
+# ------------------------------------------------------------------ stencils
+def make_basis(kind: str, dim: int, m: int):
+    if kind == "scalar":
+        return _basis.basis_table(_basis.taylor_basis(dim, m), 1)
+    if kind == "divfree":
+        return _basis.basis_table(_basis.divfree_basis(dim, m), dim)
+    raise ValueError(kind)
+
+
+def stencils(x, targets, nbr_off, nbr_idx, eps, kind, m, functional, wpow=4.0, bflag=None, normals=None,
+             basis_table=None):
+    """GMLS stencil weights for one functional on every target.
+
+    Returns (w, beta, diag):
+      w     list/array: target q -> array [rows, k_q, nc]  (stacked to
+            [n_tgt, rows, k, nc] when all k_q are equal)
+      beta  [n_tgt, rows]  Neumann coefficient of h (zero for interior targets)
+      diag  [n_tgt, 2]     max |r_ii|, min |r_ii| of the triangular factor
+    ``functional`` is a name of ``basis.functional_terms`` or a row list.
+    For kind == 'scalar' and functional == 'div' the divergence of a vector
+    field reconstructed component by component is returned (layout only:
+    component c uses the d/dx_c weights)."""
+    x = _soa(x)
+    dim, n = x.shape
+    if kind == "scalar" and functional == "div":
+        g, beta, diag = stencils(x, targets, nbr_off, nbr_idx, eps, kind, m, "grad", wpow, bflag, normals,
+                                 basis_table)
+        return _div_from_grad(g, dim), beta[:, :1] * 0.0, diag
+    nb, nc, b_off, b_coef, b_expo = basis_table if basis_table is not None else make_basis(kind, dim, m)
+    rows = _basis.functional_terms(functional, dim) if isinstance(functional, str) else functional
+    nrows, f_off, f_coef, f_comp, f_beta = _basis.functional_table(rows)
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    off = np.ascontiguousarray(nbr_off, dtype=np.int64)
+    idx = np.ascontiguousarray(nbr_idx, dtype=np.int32)
+    ep = np.ascontiguousarray(eps, dtype=np.float64)
+    nt = len(tg)
+    ks = np.diff(off)
+    w_off = np.zeros(nt + 1, dtype=np.int64)
+    w_off[1:] = np.cumsum(ks * nc * nrows)
+    out_w = np.zeros(int(w_off[-1]), dtype=np.float64)
+    out_beta = np.zeros((nt, nrows), dtype=np.float64)
+    out_diag = np.zeros((nt, 2), dtype=np.float64)
+    bf = None if bflag is None else np.ascontiguousarray(bflag, dtype=np.uint8)
+    nr = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64).reshape(nt, dim)
+    if bf is not None and kind != "scalar":
+        raise ValueError("the Neumann constraint applies to the scalar (pressure) basis")
+    rc = lib().orc_stencils(
+        ctypes.c_int(dim), ctypes.c_int64(n), _p(x), ctypes.c_int64(nt), _p(tg), _p(off), _p(idx), _p(ep),
+        ctypes.c_double(wpow), ctypes.c_int(nb), ctypes.c_int(nc), _p(b_off), _p(b_coef), _p(b_expo),
+        ctypes.c_int(nrows), _p(f_off), _p(f_coef), _p(f_comp), _p(f_beta), _p(bf), _p(nr), _p(w_off),
+        _p(out_w), _p(out_beta), _p(out_diag))
+    if rc != 0:
+        raise ValueError(f"oracle stencils failed rc={rc}")
+    ws = [out_w[w_off[q]:w_off[q + 1]].reshape(nrows, ks[q], nc) for q in range(nt)]
+    if nt and np.all(ks == ks[0]):
+        ws = np.stack(ws)
+    return ws, out_beta, out_diag
+
+
+def _div_from_grad(g, dim):
+    if isinstance(g, np.ndarray):
+        # g [T, dim, k, 1] -> [T, 1, k, dim]
+        return np.ascontiguousarray(np.transpose(g[..., 0], (0, 2, 1))[:, None, :, :])
+    return [np.ascontiguousarray(gq[..., 0].T[None, :, :]) for gq in g]
+
+
+# ----------------------------------------------------------------------- CSR
+def csr(nbr_off, nbr_idx, weights, n_cols_points):
+    """CSR of one operator (Sec. 3.2, local-to-global map J = LTG(I, j)).
+
+    weights: per target an array [rows, k, nc].  Operator row (q, r) is
+    q*rows + r; its entries are (idx_j * nc + c, w[r, j, c]) sorted by column.
+    Returns (row_ptr int64, col int32, val float64, n_cols)."""
+    off = np.asarray(nbr_off, dtype=np.int64)
+    idx = np.asarray(nbr_idx, dtype=np.int64)
+    nt = len(off) - 1
+    w0 = weights[0]
+    rows, _, nc = w0.shape
+    row_ptr = [0]
+    cols, vals = [], []
+    for q in range(nt):
+        nb = idx[off[q]:off[q + 1]]
+        wq = weights[q]
+        colq = (nb[:, None] * nc + np.arange(nc)[None, :]).reshape(-1)
+        order = np.argsort(colq, kind="stable")
+        for r in range(rows):
+            cols.append(colq[order])
+            vals.append(wq[r].reshape(-1)[order])
+            row_ptr.append(row_ptr[-1] + len(colq))
+    return (np.asarray(row_ptr, dtype=np.int64), np.concatenate(cols).astype(np.int32),
+            np.concatenate(vals).astype(np.float64), int(n_cols_points) * nc)
+
+
+def qr(A):
+    """The oracle's Householder QR (column-major in/out) -- exposed for tests."""
+    A = np.asfortranarray(np.array(A, dtype=np.float64))
+    M, n = A.shape
+    tau = np.zeros(n, dtype=np.float64)
+    lib().orc_qr(ctypes.c_int(M), ctypes.c_int(n), _p(A), _p(tau))
+    return A, tau
+
+
+def apply_q(A, tau, z):
+    A = np.asfortranarray(A)
+    z = np.array(z, dtype=np.float64)
+    M, n = A.shape
+    lib().orc_apply_q(ctypes.c_int(M), ctypes.c_int(n), _p(A), _p(tau), _p(z))
+    return z
