@@ -1,0 +1,227 @@
+/*
+ * gmls.h -- C ABI of the GB300 GMLS stencil library (libgmls.so).
+ *
+ * The library generates generalized-moving-least-squares (GMLS) stencils, the
+ * local hot path of the compatible meshless Stokes scheme of "Parallel
+ * implementation of a compatible high-order meshless method for the Stokes'
+ * equations" (arXiv 2104.14447):
+ *
+ *   gmls_neighbors     the particles within the support of each target
+ *                      (Sec. 2.1, the set N_T of Eq. optimization-discretized-4)
+ *   gmls_stencils      for each target: weighted, eps-scaled basis matrix
+ *                      (Eqs. matrix-P, matrix-W, basis-functions-3d; the
+ *                      divergence-free basis of Sec. 2.2), the weighted
+ *                      least-squares solve (Eqs. matrix-A, matrix-B, vector-c),
+ *                      optionally the Neumann constraint of Sec. 2.3, and the
+ *                      target functionals (Sec. 2.5, Eq.
+ *                      polynomial-approximation-derivative) giving the
+ *                      stencil weights alpha_Ij of Sec. 3.2
+ *   gmls_assemble_csr  scatter of one operator's weights into CSR through the
+ *                      local-to-global map J = LTG(I, j) of Sec. 3.2
+ *
+ * Conventions
+ *   - Every function returns a gmls_status; 0 is success, negative values are
+ *     errors.  Argument errors are detected on the host and returned before
+ *     any work is queued.  gmls_last_error() describes the last error.
+ *   - Work is queued asynchronously on the context's CUDA stream.  Device-side
+ *     per-target conditions are reported in the per-target status array
+ *     (GMLS_T_* bits), never by aborting.
+ *   - Device memory: the context sub-allocates everything it owns from one
+ *     caller-provided device buffer (the arena); the library itself never
+ *     calls cudaMalloc.  Outputs of gmls_assemble_csr and gmls_export go to
+ *     caller-owned buffers.
+ *   - Pointers documented as "host or device" may be either; the library asks
+ *     the CUDA driver which one it is.
+ *   - Coordinates are FP64 structure-of-arrays: x[c * n + i] is coordinate c
+ *     of particle i.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - There is no CPU fallback: without a CUDA device every call that needs
+ *     one fails with GMLS_ECUDA.
+ */
+#ifndef GMLS_H
+#define GMLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gmls_ctx gmls_ctx;
+typedef int32_t gmls_status;
+
+/* call status */
+#define GMLS_OK 0
+#define GMLS_EINVAL (-1)    /* bad argument or unsupported (d, m, basis)      */
+#define GMLS_ENOMEM (-2)    /* the arena cannot hold the request             */
+#define GMLS_ECUDA (-3)     /* a CUDA call failed (message in last_error)    */
+#define GMLS_ETIMEOUT (-4)  /* a bounded device wait gave up                 */
+#define GMLS_EBUSY (-5)     /* handle still in use                           */
+#define GMLS_ENOTFOUND (-6) /* unknown handle                                */
+
+/* per-target status bits (uint8 per target) */
+#define GMLS_T_OK 0
+#define GMLS_T_RANK_DEFICIENT 1      /* |r_ii| <= 64 n u max|r|: weights unreliable          */
+#define GMLS_T_ILL_CONDITIONED 2     /* max|r_ii| / min|r_ii| > 1e6                            */
+#define GMLS_T_REFINE_NOT_CONVERGED 4 /* FP32 refinement missed its tolerance: FP64 redone */
+#define GMLS_T_TOO_FEW_NEIGHBOURS 8  /* fewer candidates than requested (weights zero)       */
+#define GMLS_T_FP64_FALLBACK 16      /* result recomputed by the FP64 path                    */
+#define GMLS_T_OVERFLOW 32           /* candidate buffer exceeded (neighbour list truncated) */
+
+/* neighbour modes */
+#define GMLS_NBR_KNN 0    /* k nearest by (d^2, index); eps = eps_factor * d_k                */
+#define GMLS_NBR_RADIUS 1 /* all with d^2 < eps^2, eps = eps_factor * d_k, nearest cap kept    */
+
+/* bases */
+#define GMLS_BASIS_SCALAR 0  /* scaled Taylor monomials, Q = C(m+d, d)          (Sec. 2.1) */
+#define GMLS_BASIS_DIVFREE 1 /* divergence-free vector polynomials of degree m  (Sec. 2.2) */
+
+/* weights */
+#define GMLS_WEIGHT_POLY 0 /* W(r) = (1 - r/eps)_+^p  (Eq. kernel, p = weight_power) */
+
+/* functionals (rows per target) */
+#define GMLS_F_GRAD 0          /* scalar basis: d rows, d/dx_c                                 */
+#define GMLS_F_LAPLACIAN 1     /* scalar basis: 1 row                                          */
+#define GMLS_F_DIV 2           /* 1 row over (neighbour, component): scalar basis applies
+                                  d/dx_c to component c; divergence-free basis gives zeros     */
+#define GMLS_F_VEC_LAPLACIAN 3 /* divergence-free basis: d rows over (neighbour, component)   */
+#define GMLS_F_CURLCURL 4      /* divergence-free basis: d rows, curl curl = -Laplacian        */
+
+/* precision */
+#define GMLS_FP64 0        /* FP64 basis, QR and apply                                       */
+#define GMLS_FP32_REFINE 1 /* FP32 QR, FP64 residuals, FP32 corrections (FP64 fallback)      */
+
+/* export selectors */
+#define GMLS_X_NBR_OFFSETS 0 /* int64 [n_targets + 1]                          */
+#define GMLS_X_NBR_INDEX 1   /* int32 [nnz]                                    */
+#define GMLS_X_NBR_EPS 2     /* double [n_targets]                             */
+#define GMLS_X_NBR_STATUS 3  /* uint8 [n_targets]                              */
+#define GMLS_X_WEIGHTS 4     /* double, layout of gmls_stencil_info            */
+#define GMLS_X_BETA 5        /* double [n_targets][rows] Neumann coefficient   */
+#define GMLS_X_STATUS 6      /* uint8 [n_targets] stencil status               */
+#define GMLS_X_ITERS 7       /* uint8 [n_targets] refinement iterations used   */
+
+typedef struct {
+  int32_t mode;              /* GMLS_NBR_KNN or GMLS_NBR_RADIUS                              */
+  int32_t k;                 /* k (>= 1)                                                     */
+  double eps_factor;         /* eps = eps_factor * (distance of the k-th neighbour), > 0     */
+  int32_t cap;               /* radius mode: at most cap neighbours (nearest kept); >= k     */
+  int32_t reserved;          /* must be 0                                                    */
+  const int32_t* targets;    /* host or device int32 [n_targets] particle ids; NULL = all    */
+  int64_t n_targets;         /* ignored when targets is NULL                                 */
+  const double* halfspace;   /* NULL, or host or device [n_targets][dim]: keep only j with
+                                n . (x_j - x_T) <= 0; an all-zero row disables the filter    */
+} gmls_nbr_params;
+
+typedef struct {
+  int32_t basis;              /* GMLS_BASIS_*                                                */
+  int32_t degree;             /* m in 1..4 (used when degree_per_target is NULL)             */
+  int32_t weight;             /* GMLS_WEIGHT_POLY                                            */
+  int32_t weight_power;       /* p >= 1 (4 in the paper's configuration)                     */
+  int32_t precision;          /* GMLS_FP64 or GMLS_FP32_REFINE                               */
+  int32_t n_functionals;      /* 1..5                                                        */
+  int32_t functionals[5];     /* GMLS_F_*, no repeats                                        */
+  int32_t neumann;            /* 1: targets whose cloud boundary flag is set take the
+                                 Neumann constraint n . grad u = h (scalar basis only)       */
+  int32_t max_refine;         /* FP32_REFINE: iteration cap (0 = default 3)                  */
+  double refine_tol;          /* FP32_REFINE: stop when |ds|_inf <= tol |s|_inf (0 = 1e-12)  */
+  const int8_t* degree_per_target; /* NULL, or host or device int8 [n_targets], m in 1..4    */
+} gmls_stencil_params;
+
+/*
+ * Create a context on CUDA device `device`, queueing work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  `arena` is a device buffer
+ * of `arena_bytes` bytes owned by the caller, which must outlive the context;
+ * all the context's device memory is carved out of it.
+ * Errors: GMLS_EINVAL (NULL out/arena, arena_bytes < 1 MiB), GMLS_ECUDA.
+ */
+gmls_status gmls_create(gmls_ctx** out, int device, void* cuda_stream, void* arena, size_t arena_bytes);
+
+/* Wait for queued work, then free the context (not the arena). */
+gmls_status gmls_destroy(gmls_ctx* ctx);
+
+/* Switch the stream later calls queue on (previous work is not waited for). */
+gmls_status gmls_set_stream(gmls_ctx* ctx, void* cuda_stream);
+
+/*
+ * Register a point cloud (Sec. 2.1: particles x_i, i = 1..N).  dim is 2 or 3;
+ * xyz is host or device FP64 SoA [dim][n]; normals (SoA [dim][n], outward unit
+ * normals, used for Neumann targets) and bflags (uint8 [n], nonzero = on the
+ * boundary Gamma) may be NULL.  The context copies them into its arena and
+ * builds the cell list on the device.  Returns a handle in *cloud_id.
+ */
+gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, const double* normals,
+                       const uint8_t* bflags, int64_t* cloud_id);
+
+/*
+ * Neighbour lists for the targets of a cloud (Sec. 2.1, "the particles within
+ * a distance eps of x_T").  Distances are exact FP64 squared distances
+ * ((dx*dx + dy*dy) + dz*dz, dx = x_j - x_T, no fused multiply-add); lists are
+ * sorted by (d^2, particle id) and include the target itself.  The result
+ * handle owns CSR offsets (int64), indices (int32), eps (double) and a status
+ * byte per target (GMLS_T_TOO_FEW_NEIGHBOURS, GMLS_T_OVERFLOW).
+ */
+gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_params* params, int64_t* nbrs_id);
+
+/*
+ * Stencil weights for every target of a neighbour handle.  For functional f
+ * with R_f rows and c_in components (1 for the scalar basis, d for the
+ * divergence-free basis and for GMLS_F_DIV), the weights of target t occupy
+ * R_f * k_t * c_in doubles starting at element off[t] * R_f * c_in (off = the
+ * neighbour offsets), ordered [row][neighbour][component], neighbours in list
+ * order.  Weight w satisfies, for every polynomial field q of the basis span,
+ * sum w q(x_j) = (L q)(x_T) (plus beta * h for Neumann targets).
+ */
+gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_params* params, int64_t* stencil_id);
+
+/* Shape of one functional's weights: rows per target, components, total doubles. */
+gmls_status gmls_stencil_info(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t* n_targets,
+                              int32_t* rows, int32_t* ncomp, int64_t* n_values);
+
+/*
+ * CSR operator of one functional (Sec. 3.2).  Operator row t * R_f + r holds
+ * the weights of target t, row r, at columns (particle id * c_in + component),
+ * sorted ascending; explicit zeros are kept.  gmls_csr_size waits for the
+ * stream (it reads the nonzero count) and returns n_rows, n_cols, nnz; the
+ * caller then passes device buffers row_ptr (int64 [n_rows + 1]), col (int32
+ * [nnz]) and val (double [nnz]) to gmls_assemble_csr, which is asynchronous.
+ */
+gmls_status gmls_csr_size(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t* n_rows, int64_t* n_cols,
+                          int64_t* nnz);
+gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t* row_ptr, int32_t* col,
+                              double* val);
+
+/*
+ * Copy one array of a handle to dst (host or device), `bytes` = capacity of
+ * dst; GMLS_EINVAL if too small.  Host destinations are synchronous.
+ */
+gmls_status gmls_export(gmls_ctx* ctx, int64_t id, int32_t what, int32_t functional, void* dst, size_t bytes);
+
+/* Size in bytes of what gmls_export would copy (waits for the stream when the
+   size depends on device results). */
+gmls_status gmls_export_size(gmls_ctx* ctx, int64_t id, int32_t what, int32_t functional, size_t* bytes);
+
+/* Free a handle (cloud, neighbours or stencils) and its arena memory.  A cloud
+   with live neighbour handles, or neighbours with live stencils, is EBUSY. */
+gmls_status gmls_release(gmls_ctx* ctx, int64_t id);
+
+/* Wait for all queued work.  GMLS_ECUDA on an asynchronous CUDA error. */
+gmls_status gmls_sync(gmls_ctx* ctx);
+
+/* Arena use in bytes: in use now, high-water mark, capacity. */
+gmls_status gmls_arena_usage(gmls_ctx* ctx, size_t* used, size_t* peak, size_t* capacity);
+
+/* Number of kernels this context has launched since creation. */
+gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
+
+/* Message of the last error on this context (NULL ctx: last create error). */
+const char* gmls_last_error(gmls_ctx* ctx);
+
+/* Library version string. */
+const char* gmls_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMLS_H */

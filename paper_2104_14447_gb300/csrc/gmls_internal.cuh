@@ -1,0 +1,172 @@
+// gmls_internal.cuh -- shared declarations of the CUDA side of libgmls.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cfloat>
+#include <climits>
+
+#include "../../include/gmls.h"
+
+namespace gmls {
+
+constexpr int kMaxDim = 3;
+constexpr int kWarp = 32;
+constexpr int kMaxSolveRows = 4;   // distinct functional rows solved per target
+constexpr int kNbrCap = 1024;      // candidate buffer per warp in the neighbour query
+constexpr int kMaxK = 1024;        // largest neighbour count per target
+
+// ------------------------------------------------------------------ exact FP64
+// Squared distance ((dx*dx + dy*dy) + dz*dz), dx = x_j - x_T, every operation
+// rounded separately (no contraction into fused multiply-adds), so that the
+// value is reproducible bit for bit.
+__device__ __forceinline__ double exact_d2(int dim, const double* dx) {
+  double d2 = __dmul_rn(dx[0], dx[0]);
+  if (dim > 1) d2 = __dadd_rn(d2, __dmul_rn(dx[1], dx[1]));
+  if (dim > 2) d2 = __dadd_rn(d2, __dmul_rn(dx[2], dx[2]));
+  return d2;
+}
+
+// n . (x_j - x_T) with the same evaluation order.
+__device__ __forceinline__ double exact_dot(int dim, const double* nrm, const double* dx) {
+  double s = __dmul_rn(nrm[0], dx[0]);
+  if (dim > 1) s = __dadd_rn(s, __dmul_rn(nrm[1], dx[1]));
+  if (dim > 2) s = __dadd_rn(s, __dmul_rn(nrm[2], dx[2]));
+  return s;
+}
+
+// candidate order: by d2, then by particle id
+__device__ __forceinline__ bool cand_less(double da, int32_t ia, double db, int32_t ib) {
+  return (da < db) || (da == db && ia < ib);
+}
+
+// ----------------------------------------------------------------- grid state
+struct GridParams {
+  double lo[kMaxDim];
+  double inv_h[kMaxDim];
+  double h[kMaxDim];
+  int32_t nc[kMaxDim];
+  double volume;  // bounding-box volume (for the initial search radius)
+};
+
+struct CloudDev {
+  int dim;
+  int64_t n;
+  const double* x;         // SoA [dim][n]
+  const double* xs;        // SoA [dim][n], in cell order
+  const int32_t* sorted;   // cell order -> particle id
+  const int32_t* cell_start;  // [ncell + 1]
+  const GridParams* grid;
+  int64_t ncell;
+};
+
+// ------------------------------------------------------------ launch helpers
+struct Launch {
+  cudaStream_t stream;
+  int64_t* counter;  // kernels launched
+};
+
+cudaError_t launch_bbox_and_grid(const Launch& L, int dim, int64_t n, const double* x, const int32_t nc_axis[3],
+                                 GridParams* grid, double* scratch_partials, int n_partials);
+cudaError_t launch_cell_count(const Launch& L, int dim, int64_t n, const double* x, const GridParams* grid,
+                              int32_t* cell_of, int32_t* counts);
+cudaError_t launch_scan_i32(const Launch& L, const int32_t* in, int32_t* out_excl, int64_t n, int32_t* scratch,
+                            int64_t scratch_elems);
+cudaError_t launch_scan_i64_from_i32(const Launch& L, const int32_t* in, int64_t* out_excl, int64_t n,
+                                     int64_t* scratch, int64_t scratch_elems);
+int64_t scan_scratch_elems(int64_t n);
+cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const int32_t* cell_of,
+                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs);
+
+struct NbrQuery {
+  CloudDev cloud;
+  int64_t n_tgt;
+  const int32_t* tgt;        // [n_tgt] or NULL (= identity)
+  const double* halfspace;   // [n_tgt][dim] or NULL
+  int mode;                  // GMLS_NBR_*
+  int k;
+  int cap;                   // radius mode
+  double eps_factor;
+  // outputs
+  int32_t* out_idx;          // kNN: [n_tgt*k]; radius: padded [n_tgt*cap]
+  int32_t* out_cnt;          // radius: [n_tgt]
+  double* out_eps;           // [n_tgt]
+  uint8_t* out_status;       // [n_tgt]
+};
+cudaError_t launch_nbr_query(const Launch& L, const NbrQuery& q);
+cudaError_t launch_fill_offsets_fixed(const Launch& L, int64_t* off, int64_t n_tgt, int k);
+cudaError_t launch_compact_padded(const Launch& L, const int32_t* padded, int cap, const int32_t* cnt,
+                                  const int64_t* off, int32_t* out, int64_t n_tgt);
+cudaError_t launch_fill_identity(const Launch& L, int32_t* out, int64_t n);
+
+// ----------------------------------------------------------------- stencils
+struct StencilJob {
+  // cloud
+  int dim;
+  int64_t n;
+  const double* x;
+  const double* normals;   // SoA [dim][n] or NULL
+  const uint8_t* bflag;    // [n] or NULL
+  // neighbours
+  int64_t n_tgt;
+  const int32_t* tgt;      // [n_tgt]
+  const int64_t* off;      // [n_tgt+1]
+  const int32_t* idx;
+  const double* eps;
+  const uint8_t* nbr_status;
+  // work list: items[0..*n_items) are target ordinals; NULL items = all
+  const int32_t* items;
+  const int32_t* n_items;
+  // basis
+  int kind;                // GMLS_BASIS_*
+  int degree;
+  const int8_t* degree_pt; // [n_tgt] or NULL
+  int nc;                  // components per neighbour (1 or dim)
+  double wpow;
+  int neumann;
+  // solve rows: row r of the L solve rows is functional code lam_fn[r], sub-row lam_row[r]
+  int L;
+  int lam_fn[kMaxSolveRows];
+  int lam_row[kMaxSolveRows];
+  int lam_order[kMaxSolveRows];  // |beta| of the row (power of 1/eps)
+  // outputs per requested functional
+  int nout;
+  int out_fn[5];
+  int out_rows[5];
+  int out_ncomp[5];
+  int out_src[5];          // first solve row it reads (-1: zeros)
+  int out_sign[5];         // +1 or -1 (curl curl = -vector Laplacian)
+  double* out_w[5];
+  double* beta;            // [n_tgt][L] or NULL
+  uint8_t* status;         // [n_tgt]
+  uint8_t* iters;          // [n_tgt]
+  // precision
+  int max_refine;
+  double tol;
+  int32_t* fb_items;       // FP32 path: targets to redo in FP64
+  int32_t* fb_count;
+  int fallback_run;        // 1: this FP64 launch redoes targets of the FP32 path
+  // launch shape
+  int ld;                  // tile leading dimension (>= max rows)
+  int nmax;                // max basis size
+  int warps_per_target;    // 1, 2 or 4 (block = 128 threads)
+};
+
+size_t stencil_smem_bytes(const StencilJob& j, bool fp32_refine);
+cudaError_t launch_stencils(const Launch& L, const StencilJob& j, bool fp32_refine, int grid_blocks);
+
+// -------------------------------------------------------------------- CSR
+struct CsrJob {
+  int64_t n_tgt;
+  const int64_t* off;
+  const int32_t* idx;
+  const double* w;
+  int rows;
+  int nc;
+  int64_t* row_ptr;
+  int32_t* col;
+  double* val;
+};
+cudaError_t launch_csr(const Launch& L, const CsrJob& j);
+
+}  // namespace gmls

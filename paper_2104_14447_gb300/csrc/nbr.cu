@@ -1,0 +1,493 @@
+// nbr.cu -- cell-list build and exact neighbour queries on the device.
+//
+// The paper gathers, for each target x_T, the particles within the support
+// radius eps (Sec. 2.1, the set N_T under Eq. optimization-discretized-4) with
+// a kd-tree; here a uniform cell list on the GPU replaces the tree.  Queries
+// are exact: squared distances are FP64 with every operation rounded
+// separately, and lists are ordered by (d^2, particle id), so the result is
+// identical on every run and machine.
+#include <cuda_runtime.h>
+
+#include "gmls_internal.cuh"
+
+namespace gmls {
+
+static inline unsigned blocks_for(int64_t n, int per_block, unsigned cap = 152u * 32u) {
+  int64_t b = (n + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > (int64_t)cap) b = cap;
+  return (unsigned)b;
+}
+
+// ---------------------------------------------------------------- bounding box
+__global__ void bbox_partial_kernel(int dim, int64_t n, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double smin[3][8], smax[3][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = 0; c < dim; ++c) {
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      double v = x[c * n + i];
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      smin[c][warp] = lo;
+      smax[c][warp] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < dim) {
+    int c = threadIdx.x;
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      lo = fmin(lo, smin[c][w]);
+      hi = fmax(hi, smax[c][w]);
+    }
+    part[(blockIdx.x * 3 + c) * 2 + 0] = lo;
+    part[(blockIdx.x * 3 + c) * 2 + 1] = hi;
+  }
+}
+
+__global__ void grid_finalize_kernel(int dim, int nparts, const double* __restrict__ part, int nc0, int nc1, int nc2,
+                                     GridParams* __restrict__ g) {
+  if (threadIdx.x != 0) return;
+  int ncs[3] = {nc0, nc1, nc2};
+  double vol = 1.0;
+  for (int c = 0; c < kMaxDim; ++c) {
+    if (c >= dim) {
+      g->lo[c] = 0.0;
+      g->h[c] = 1.0;
+      g->inv_h[c] = 0.0;
+      g->nc[c] = 1;
+      continue;
+    }
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int p = 0; p < nparts; ++p) {
+      lo = fmin(lo, part[(p * 3 + c) * 2 + 0]);
+      hi = fmax(hi, part[(p * 3 + c) * 2 + 1]);
+    }
+    double ext = hi - lo;
+    int nc = ncs[c];
+    if (!(ext > 0.0)) {  // flat axis: one cell, every point maps to it
+      nc = 1;
+      g->lo[c] = lo;
+      g->h[c] = 1.0;
+      g->inv_h[c] = 0.0;
+      g->nc[c] = 1;
+      continue;
+    }
+    g->lo[c] = lo;
+    g->h[c] = ext / nc;
+    g->inv_h[c] = nc / ext;
+    g->nc[c] = nc;
+    vol *= ext;
+  }
+  g->volume = vol;
+}
+
+cudaError_t launch_bbox_and_grid(const Launch& L, int dim, int64_t n, const double* x, const int32_t nc_axis[3],
+                                 GridParams* grid, double* part, int n_partials) {
+  bbox_partial_kernel<<<n_partials, 256, 0, L.stream>>>(dim, n, x, part);
+  grid_finalize_kernel<<<1, 32, 0, L.stream>>>(dim, n_partials, part, nc_axis[0], nc_axis[1], nc_axis[2], grid);
+  *L.counter += 2;
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ int32_t cell_coord(const GridParams& g, int c, double v) {
+  double f = floor((v - g.lo[c]) * g.inv_h[c]);
+  int32_t q = (f < 0.0) ? 0 : (f >= (double)g.nc[c] ? g.nc[c] - 1 : (int32_t)f);
+  return q;
+}
+
+__global__ void cell_count_kernel(int dim, int64_t n, const double* __restrict__ x, const GridParams* __restrict__ gp,
+                                  int32_t* __restrict__ cell_of, int32_t* __restrict__ counts) {
+  const GridParams g = *gp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t cell = 0;
+    for (int c = dim - 1; c >= 0; --c) cell = cell * g.nc[c] + cell_coord(g, c, x[c * n + i]);
+    cell_of[i] = cell;
+    atomicAdd(&counts[cell], 1);
+  }
+}
+
+cudaError_t launch_cell_count(const Launch& L, int dim, int64_t n, const double* x, const GridParams* grid,
+                              int32_t* cell_of, int32_t* counts) {
+  cell_count_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(dim, n, x, grid, cell_of, counts);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+__global__ void cell_scatter_kernel(int dim, int64_t n, const double* __restrict__ x, const int32_t* __restrict__ cell_of,
+                                    const int32_t* __restrict__ cell_start, int32_t* __restrict__ fill,
+                                    int32_t* __restrict__ sorted, double* __restrict__ xs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t cell = cell_of[i];
+    int32_t pos = cell_start[cell] + atomicAdd(&fill[cell], 1);
+    sorted[pos] = (int32_t)i;
+    for (int c = 0; c < dim; ++c) xs[c * n + pos] = x[c * n + i];
+  }
+}
+
+cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const int32_t* cell_of,
+                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs) {
+  cell_scatter_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(dim, n, x, cell_of, cell_start, fill, sorted, xs);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------- scan
+// Exclusive scan in three passes: tile sums, a one-block scan of the tile
+// sums, then each tile rescanned with its offset.  out has n + 1 entries;
+// out[n] is the total.
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 8;
+constexpr int kScanTile = kScanThreads * kScanPerThread;
+
+int64_t scan_scratch_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+template <typename TO>
+__device__ __forceinline__ TO block_exclusive_scan(TO v, TO* warp_sums, TO* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TO incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    TO t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    TO s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : TO(0);
+    TO si = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      TO t = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += t;
+    }
+    if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = si - s;
+    if (lane == 31) *total = si;
+  }
+  __syncthreads();
+  TO r = warp_sums[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+template <typename TI, typename TO>
+__global__ void scan_tile_sums_kernel(const TI* __restrict__ in, int64_t n, TO* __restrict__ sums) {
+  __shared__ TO ws[32];
+  __shared__ TO tot;
+  int64_t base = blockIdx.x * (int64_t)kScanTile;
+  TO s = 0;
+  for (int i = 0; i < kScanPerThread; ++i) {
+    int64_t p = base + (int64_t)threadIdx.x * kScanPerThread + i;
+    if (p < n) s += (TO)in[p];
+  }
+  block_exclusive_scan<TO>(s, ws, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename TO>
+__global__ void scan_sums_kernel(TO* __restrict__ sums, int64_t nt) {
+  __shared__ TO ws[32];
+  __shared__ TO tot;
+  TO carry = 0;
+  for (int64_t base = 0; base < nt; base += blockDim.x) {
+    int64_t p = base + threadIdx.x;
+    TO v = (p < nt) ? sums[p] : TO(0);
+    TO ex = block_exclusive_scan<TO>(v, ws, &tot);
+    if (p < nt) sums[p] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nt] = carry;
+}
+
+template <typename TI, typename TO>
+__global__ void scan_apply_kernel(const TI* __restrict__ in, int64_t n, const TO* __restrict__ sums, TO* __restrict__ out,
+                                  int64_t nt) {
+  __shared__ TO ws[32];
+  __shared__ TO tot;
+  int64_t base = blockIdx.x * (int64_t)kScanTile;
+  TI v[kScanPerThread];
+  TO s = 0;
+  for (int i = 0; i < kScanPerThread; ++i) {
+    int64_t p = base + (int64_t)threadIdx.x * kScanPerThread + i;
+    v[i] = (p < n) ? in[p] : TI(0);
+    s += (TO)v[i];
+  }
+  TO ex = block_exclusive_scan<TO>(s, ws, &tot) + sums[blockIdx.x];
+  for (int i = 0; i < kScanPerThread; ++i) {
+    int64_t p = base + (int64_t)threadIdx.x * kScanPerThread + i;
+    if (p < n) out[p] = ex;
+    ex += (TO)v[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[nt];
+}
+
+template <typename TI, typename TO>
+static cudaError_t scan_impl(const Launch& L, const TI* in, TO* out, int64_t n, TO* scratch, int64_t scratch_elems) {
+  int64_t nt = (n + kScanTile - 1) / kScanTile;
+  if (nt + 1 > scratch_elems) return cudaErrorInvalidValue;
+  if (nt == 0) {
+    cudaMemsetAsync(out, 0, sizeof(TO), L.stream);
+    return cudaGetLastError();
+  }
+  scan_tile_sums_kernel<TI, TO><<<(unsigned)nt, kScanThreads, 0, L.stream>>>(in, n, scratch);
+  scan_sums_kernel<TO><<<1, 1024, 0, L.stream>>>(scratch, nt);
+  scan_apply_kernel<TI, TO><<<(unsigned)nt, kScanThreads, 0, L.stream>>>(in, n, scratch, out, nt);
+  *L.counter += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i32(const Launch& L, const int32_t* in, int32_t* out, int64_t n, int32_t* scratch,
+                            int64_t scratch_elems) {
+  return scan_impl<int32_t, int32_t>(L, in, out, n, scratch, scratch_elems);
+}
+cudaError_t launch_scan_i64_from_i32(const Launch& L, const int32_t* in, int64_t* out, int64_t n, int64_t* scratch,
+                                     int64_t scratch_elems) {
+  return scan_impl<int32_t, int64_t>(L, in, out, n, scratch, scratch_elems);
+}
+
+// ------------------------------------------------------------- neighbour query
+constexpr int kQueryWarps = 4;
+
+struct WarpBuf {
+  double d2[kNbrCap];
+  int32_t id[kNbrCap];
+  int32_t row_begin[32];
+  int32_t row_end[32];  // inclusive scan of row lengths
+};
+
+// Collect every particle with d2 < R2 (after the optional half-space filter)
+// from the cells overlapping [x_T - R, x_T + R] into the warp's buffer.
+// Returns the number that passed (may exceed kNbrCap: overflow).
+__device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const double* xT, double R, double R2,
+                                 bool use_hs, const double* nrm, WarpBuf& wb) {
+  const int lane = threadIdx.x & 31;
+  const int dim = cl.dim;
+  const double Rb = R * 1.000001;
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int c = 0; c < dim; ++c) {
+    lo[c] = cell_coord(g, c, xT[c] - Rb);
+    hi[c] = cell_coord(g, c, xT[c] + Rb);
+  }
+  const int ny = hi[1] - lo[1] + 1;
+  const int nrows = ny * (hi[2] - lo[2] + 1);
+  int count = 0;
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
+    const int r = r0 + lane;
+    int32_t b = 0, len = 0;
+    if (r < nrows) {
+      int cy = lo[1] + r % ny, cz = lo[2] + r / ny;
+      int32_t row_cell = (cz * g.nc[1] + cy) * g.nc[0];
+      b = cl.cell_start[row_cell + lo[0]];
+      len = cl.cell_start[row_cell + hi[0] + 1] - b;
+    }
+    int32_t incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    wb.row_begin[lane] = b;
+    wb.row_end[lane] = incl;
+    __syncwarp();
+    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int32_t p0 = 0; p0 < total; p0 += 32) {
+      const int32_t p = p0 + lane;
+      bool pass = false;
+      int32_t j = 0;
+      double d2 = 0.0;
+      if (p < total) {
+        // row containing p: first row whose inclusive end exceeds p
+        int lo_r = 0, hi_r = 31;
+        while (lo_r < hi_r) {
+          int mid = (lo_r + hi_r) >> 1;
+          if (wb.row_end[mid] > p) hi_r = mid; else lo_r = mid + 1;
+        }
+        int32_t start = lo_r ? wb.row_end[lo_r - 1] : 0;
+        int64_t pos = wb.row_begin[lo_r] + (p - start);
+        double dx[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < dim; ++c) dx[c] = __dsub_rn(cl.xs[c * cl.n + pos], xT[c]);
+        d2 = exact_d2(dim, dx);
+        pass = d2 < R2;
+        if (pass && use_hs) pass = exact_dot(dim, nrm, dx) <= 0.0;
+        j = cl.sorted[pos];
+      }
+      unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        int slot = count + __popc(m & ((1u << lane) - 1u));
+        if (slot < kNbrCap) {
+          wb.d2[slot] = d2;
+          wb.id[slot] = j;
+        }
+      }
+      count += __popc(m);
+    }
+    __syncwarp();
+  }
+  return count;
+}
+
+// Bitonic sort of the first `count` candidates by (d2, id) within one warp.
+__device__ void warp_sort_candidates(WarpBuf& wb, int count) {
+  const int lane = threadIdx.x & 31;
+  int n2 = 1;
+  while (n2 < count) n2 <<= 1;
+  for (int i = count + lane; i < n2; i += 32) {
+    wb.d2[i] = DBL_MAX;
+    wb.id[i] = INT_MAX;
+  }
+  __syncwarp();
+  for (int size = 2; size <= n2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = lane; i < (n2 >> 1); i += 32) {
+        int a = 2 * stride * (i / stride) + (i % stride);
+        int b = a + stride;
+        bool asc = (a & size) == 0;
+        double da = wb.d2[a], db = wb.d2[b];
+        int32_t ia = wb.id[a], ib = wb.id[b];
+        bool gt = cand_less(db, ib, da, ia);
+        if (gt == asc) {
+          wb.d2[a] = db;
+          wb.d2[b] = da;
+          wb.id[a] = ib;
+          wb.id[b] = ia;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpBuf& wb = reinterpret_cast<WarpBuf*>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const CloudDev& cl = q.cloud;
+  const GridParams g = *cl.grid;
+  const int dim = cl.dim;
+  // unit-ball volume and the initial radius: about 1.5 k particles expected
+  const double ball = (dim == 1) ? 2.0 : (dim == 2) ? 3.141592653589793 : 4.1887902047863905;
+  const double dens = (double)cl.n / (g.volume > 0.0 ? g.volume : 1.0);
+  double span = 0.0;
+  for (int c = 0; c < dim; ++c) span += g.h[c] * g.nc[c];
+  for (int64_t to = blockIdx.x * (int64_t)kQueryWarps + (threadIdx.x >> 5); to < q.n_tgt;
+       to += (int64_t)gridDim.x * kQueryWarps) {
+    const int64_t t = q.tgt ? q.tgt[to] : to;
+    double xT[3] = {0.0, 0.0, 0.0}, nrm[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < dim; ++c) xT[c] = cl.x[c * cl.n + t];
+    bool use_hs = false;
+    if (q.halfspace) {
+      for (int c = 0; c < dim; ++c) {
+        nrm[c] = q.halfspace[to * dim + c];
+        use_hs |= (nrm[c] != 0.0);
+      }
+    }
+    uint8_t st = GMLS_T_OK;
+    double R = pow(1.5 * q.k / (dens * ball), 1.0 / dim);
+    int count = 0;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      count = gather_candidates(cl, g, xT, R, __dmul_rn(R, R), use_hs, nrm, wb);
+      if (count > kNbrCap) {
+        R *= 0.75;
+        continue;
+      }
+      if (count >= q.k) break;
+      if (R > 2.0 * span + 1.0) break;  // whole cloud inside: too few exist
+      R *= 1.6;
+    }
+    if (count > kNbrCap) {  // could not bring the candidate set under the cap
+      st |= GMLS_T_OVERFLOW;
+      count = kNbrCap;
+    }
+    if (count < q.k) st |= GMLS_T_TOO_FEW_NEIGHBOURS;
+    warp_sort_candidates(wb, count);
+    const int kk = count < q.k ? count : q.k;
+    double eps = 0.0;
+    if (kk == q.k) eps = __dmul_rn(q.eps_factor, __dsqrt_rn(wb.d2[q.k - 1]));
+    if (q.mode == GMLS_NBR_KNN) {
+      for (int i = lane; i < q.k; i += 32) q.out_idx[to * q.k + i] = (i < kk) ? wb.id[i] : -1;
+    } else {
+      int keep = 0;
+      if (kk == q.k) {
+        __syncwarp();
+        count = gather_candidates(cl, g, xT, eps, __dmul_rn(eps, eps), use_hs, nrm, wb);
+        if (count > kNbrCap) {
+          st |= GMLS_T_OVERFLOW;
+          count = kNbrCap;
+        }
+        warp_sort_candidates(wb, count);
+        keep = count < q.cap ? count : q.cap;
+      }
+      for (int i = lane; i < keep; i += 32) q.out_idx[to * q.cap + i] = wb.id[i];
+      if (lane == 0) q.out_cnt[to] = keep;
+    }
+    if (lane == 0) {
+      q.out_eps[to] = eps;
+      q.out_status[to] = st;
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_nbr_query(const Launch& L, const NbrQuery& q) {
+  if (q.n_tgt == 0) return cudaSuccess;
+  const size_t smem = sizeof(WarpBuf) * kQueryWarps;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(nbr_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int64_t blocks = (q.n_tgt + kQueryWarps - 1) / kQueryWarps;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  nbr_query_kernel<<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+__global__ void fill_offsets_fixed_kernel(int64_t* off, int64_t n_tgt, int k) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n_tgt; i += (int64_t)gridDim.x * blockDim.x)
+    off[i] = i * (int64_t)k;
+}
+
+cudaError_t launch_fill_offsets_fixed(const Launch& L, int64_t* off, int64_t n_tgt, int k) {
+  fill_offsets_fixed_kernel<<<blocks_for(n_tgt + 1, 256), 256, 0, L.stream>>>(off, n_tgt, k);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+__global__ void fill_identity_kernel(int32_t* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)i;
+}
+
+cudaError_t launch_fill_identity(const Launch& L, int32_t* out, int64_t n) {
+  fill_identity_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(out, n);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+// warp per target: copy cnt[t] entries of the padded row into the CSR slot
+__global__ void compact_padded_kernel(const int32_t* __restrict__ padded, int cap, const int32_t* __restrict__ cnt,
+                                      const int64_t* __restrict__ off, int32_t* __restrict__ out, int64_t n_tgt) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n_tgt;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int c = cnt[t];
+    const int64_t o = off[t];
+    for (int i = lane; i < c; i += 32) out[o + i] = padded[t * cap + i];
+  }
+}
+
+cudaError_t launch_compact_padded(const Launch& L, const int32_t* padded, int cap, const int32_t* cnt,
+                                  const int64_t* off, int32_t* out, int64_t n_tgt) {
+  compact_padded_kernel<<<blocks_for(n_tgt * 32, 256), 256, 0, L.stream>>>(padded, cap, cnt, off, out, n_tgt);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace gmls

@@ -1,0 +1,246 @@
+"""GPU parity: libgmls (through its C ABI) against the FP64 CPU oracle.
+
+Neighbour lists and CSR structure must match bit for bit; stencil weights
+must satisfy, per (target, functional row),
+    |w_gpu - w_oracle|_inf <= tol * |w_oracle|_inf
+with tol = 1e-10 for the FP64 path and 1e-9 for the FP32 + refinement path.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_14447_gb300 import gmls, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2104_14447_gb300 import build
+
+    build.build()
+    c = gmls.Context(0, arena_bytes=16 << 30)
+    yield c
+    c.close()
+
+
+def _gpu_knn(ctx, x, k, f, targets=None, halfspace=None):
+    cid = ctx.cloud(x)
+    nid = ctx.neighbors(cid, k, f, targets=targets, halfspace=halfspace)
+    idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy()
+    eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
+    st = ctx.export(nid, gmls.X_NBR_STATUS, torch.uint8).cpu().numpy()
+    return cid, nid, idx, eps, st
+
+
+def _release(ctx, *ids):
+    for i in reversed(ids):
+        ctx.release(i)
+
+
+def _rel_err_rows(wg, wo):
+    """max over (target,row) of |wg - wo|_inf / |wo|_inf; arrays [T, R, k, C]."""
+    T, R = wo.shape[:2]
+    a = np.abs(wg - wo).reshape(T, R, -1).max(axis=2)
+    b = np.abs(wo).reshape(T, R, -1).max(axis=2)
+    return float(np.max(a / np.where(b > 0, b, 1.0)))
+
+
+# ------------------------------------------------------------------ neighbours
+@pytest.mark.parametrize("dim,n_axis,k,jitter", [(2, 32, 12, 0.25), (2, 40, 48, 0.25), (3, 12, 40, 0.25),
+                                                 (3, 10, 80, 0.25), (2, 16, 13, 0.0), (3, 8, 27, 0.0),
+                                                 (2, 5, 7, 0.25)])
+def test_knn_bit_exact(ctx, dim, n_axis, k, jitter):
+    x = inputs.jittered_grid(dim, n_axis, jitter=jitter, seed=1)
+    n = x.shape[1]
+    cid, nid, idx, eps, st = _gpu_knn(ctx, x, k, 1.5)
+    oi, oe = oracle.knn(x, np.arange(n, dtype=np.int32), k, 1.5, method="grid")
+    assert np.all(st == 0)
+    assert np.array_equal(idx.reshape(n, k), oi)
+    assert np.array_equal(eps, oe)  # bit for bit
+    _release(ctx, cid, nid)
+
+
+def test_knn_halfspace_and_subset_targets(ctx):
+    x = inputs.jittered_grid(2, 48, seed=4)
+    n = x.shape[1]
+    inner = np.flatnonzero((np.abs(x[0] - 0.5) < 0.35) & (np.abs(x[1] - 0.5) < 0.35)).astype(np.int32)
+    tg = inner[::3]
+    hs = inputs.unit_vectors(2, 7, len(tg), 2).T.copy()
+    hs[::4] = 0.0
+    cid, nid, idx, eps, st = _gpu_knn(ctx, x, 20, 1.8, targets=tg, halfspace=hs)
+    oi, oe = oracle.knn(x, tg, 20, 1.8, halfspace=hs, method="grid")
+    assert np.array_equal(idx.reshape(len(tg), 20), oi) and np.array_equal(eps, oe)
+    _release(ctx, cid, nid)
+
+
+def test_radius_bit_exact(ctx):
+    x = inputs.jittered_grid(3, 20, seed=2)
+    n = x.shape[1]
+    tg = np.arange(0, n, 5, dtype=np.int32)
+    cid = ctx.cloud(x)
+    nid = ctx.neighbors(cid, 20, 1.8, mode=gmls.RADIUS, cap=160, targets=tg)
+    off = ctx.export(nid, gmls.X_NBR_OFFSETS, torch.int64).cpu().numpy()
+    idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy()
+    eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
+    _, oe = oracle.knn(x, tg, 20, 1.8, method="grid")
+    assert np.array_equal(eps, oe)
+    ooff, oidx = oracle.radius(x, tg, oe, 160, method="grid")
+    assert np.array_equal(off, ooff) and np.array_equal(idx, oidx)
+    _release(ctx, cid, nid)
+
+
+def test_too_few_neighbours_is_flagged(ctx):
+    x = inputs.jittered_grid(2, 6, seed=1)  # 36 points
+    cid = ctx.cloud(x)
+    hs = np.zeros((36, 2))
+    hs[0] = [1.0, 1.0]  # corner target, half-plane pointing inwards: few points qualify
+    hs[0] /= np.sqrt(2.0)
+    nid = ctx.neighbors(cid, 12, 1.5, halfspace=hs)
+    st = ctx.export(nid, gmls.X_NBR_STATUS, torch.uint8).cpu().numpy()
+    assert st[0] & gmls.T_TOO_FEW_NEIGHBOURS
+    assert np.all(st[1:] == 0)
+    sid = ctx.stencils(nid, gmls.SCALAR, 2, [gmls.LAPLACIAN])
+    sst = ctx.export(sid, gmls.X_STATUS, torch.uint8).cpu().numpy()
+    w = ctx.weights(sid, gmls.LAPLACIAN).cpu().numpy().reshape(36, 12)
+    assert sst[0] & gmls.T_TOO_FEW_NEIGHBOURS and np.all(w[0] == 0.0)
+    _release(ctx, cid, nid, sid)
+
+
+# -------------------------------------------------------------------- stencils
+CASES = [
+    # dim, n_axis, basis, m, k, functionals
+    (2, 32, gmls.SCALAR, 2, 12, [gmls.LAPLACIAN, gmls.GRAD]),
+    (2, 40, gmls.SCALAR, 4, 36, [gmls.GRAD, gmls.DIV, gmls.LAPLACIAN]),
+    (2, 40, gmls.DIVFREE, 4, 48, [gmls.VEC_LAPLACIAN, gmls.CURLCURL, gmls.DIV]),
+    (2, 24, gmls.DIVFREE, 2, 22, [gmls.VEC_LAPLACIAN]),
+    (3, 12, gmls.SCALAR, 3, 40, [gmls.GRAD, gmls.LAPLACIAN]),
+    (3, 12, gmls.DIVFREE, 3, 80, [gmls.VEC_LAPLACIAN]),
+    (3, 9, gmls.SCALAR, 4, 84, [gmls.LAPLACIAN]),
+    (3, 9, gmls.DIVFREE, 2, 42, [gmls.CURLCURL]),
+]
+NAMES = {gmls.GRAD: "grad", gmls.LAPLACIAN: "laplacian", gmls.DIV: "div", gmls.VEC_LAPLACIAN: "vec_laplacian",
+         gmls.CURLCURL: "curlcurl"}
+
+
+@pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
+@pytest.mark.parametrize("dim,n_axis,basis,m,k,fns", CASES)
+def test_stencils_match_oracle(ctx, dim, n_axis, basis, m, k, fns, precision):
+    x = inputs.jittered_grid(dim, n_axis, seed=m)
+    n = x.shape[1]
+    cid, nid, idx, eps, st = _gpu_knn(ctx, x, k, 1.5)
+    sid = ctx.stencils(nid, basis, m, fns, precision=precision)
+    status = ctx.export(sid, gmls.X_STATUS, torch.uint8).cpu().numpy()
+    tg = np.arange(n, dtype=np.int32)
+    off = np.arange(0, n * k + 1, k)
+    kind = "scalar" if basis == gmls.SCALAR else "divfree"
+    tol = TOL64 if precision == gmls.FP64 else TOL32
+    for fn in fns:
+        wo, _, diag = oracle.stencils(x, tg, off, idx, eps, kind, m, NAMES[fn])
+        wg = ctx.weights(sid, fn).cpu().numpy().reshape(wo.shape)
+        if fn == gmls.DIV and basis == gmls.DIVFREE:
+            # divergence of a divergence-free reconstruction: exactly zero on
+            # the GPU, zero up to rounding in the oracle
+            assert np.all(wg == 0.0)
+            assert np.abs(wo).max() <= 1e-9 / eps.min()
+            continue
+        kappa = diag[:, 0] / diag[:, 1]
+        well = kappa <= 1e6
+        assert well.mean() > 0.99
+        err = _rel_err_rows(wg[well], wo[well])
+        assert err <= tol, (NAMES[fn], err)
+    assert np.all((status & (gmls.T_RANK_DEFICIENT | gmls.T_TOO_FEW_NEIGHBOURS)) == 0)
+    _release(ctx, cid, nid, sid)
+
+
+def test_refinement_iterations_and_fallback_flags(ctx):
+    x = inputs.jittered_grid(2, 40, seed=4)
+    cid, nid, idx, eps, st = _gpu_knn(ctx, x, 48, 1.5)
+    sid = ctx.stencils(nid, gmls.DIVFREE, 4, [gmls.VEC_LAPLACIAN], precision=gmls.FP32_REFINE)
+    it = ctx.export(sid, gmls.X_ITERS, torch.uint8).cpu().numpy()
+    status = ctx.export(sid, gmls.X_STATUS, torch.uint8).cpu().numpy()
+    redone = (status & gmls.T_FP64_FALLBACK) != 0
+    assert np.all(it[~redone] >= 1) and np.all(it <= 3)
+    _release(ctx, cid, nid, sid)
+
+
+# ------------------------------------------------------------------- Neumann
+@pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
+@pytest.mark.parametrize("dim,n_axis,m,k", [(2, 24, 2, 12), (2, 24, 4, 36), (3, 10, 3, 40)])
+def test_neumann_matches_oracle(ctx, dim, n_axis, m, k, precision):
+    x = inputs.jittered_grid(dim, n_axis, seed=3)
+    n = x.shape[1]
+    nrm = inputs.unit_vectors(5, 6, n, dim)
+    bflag = (inputs.uniform(5, 8, n) < 0.3).astype(np.uint8)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nid = ctx.neighbors(cid, k, 1.5)
+    idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy()
+    eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
+    sid = ctx.stencils(nid, gmls.SCALAR, m, [gmls.LAPLACIAN, gmls.GRAD], precision=precision, neumann=True)
+    beta = ctx.export(sid, gmls.X_BETA, torch.float64).cpu().numpy().reshape(n, -1)
+    tg = np.arange(n, dtype=np.int32)
+    off = np.arange(0, n * k + 1, k)
+    tol = TOL64 if precision == gmls.FP64 else TOL32
+    # solve rows are ordered grad (dim rows) then laplacian
+    for fn, rows in ((gmls.GRAD, slice(0, dim)), (gmls.LAPLACIAN, slice(dim, dim + 1))):
+        wo, bo, _ = oracle.stencils(x, tg, off, idx, eps, "scalar", m, NAMES[fn], bflag=bflag, normals=nrm.T)
+        wg = ctx.weights(sid, fn).cpu().numpy().reshape(wo.shape)
+        assert _rel_err_rows(wg, wo) <= tol
+        bg = beta[:, rows]
+        # beta multiplies h = n . grad u ~ u / eps, so it scales like |w| eps
+        scale = np.abs(bo) + np.abs(wo).reshape(n, wo.shape[1], -1).max(axis=2) * eps[:, None]
+        assert np.all(np.abs(bg - bo) <= tol * scale)
+        assert np.all(bg[bflag == 0] == 0.0)
+    _release(ctx, cid, nid, sid)
+
+
+# ------------------------------------------------------------------------ CSR
+@pytest.mark.parametrize("basis,m,k,fn", [(gmls.SCALAR, 4, 36, gmls.GRAD), (gmls.DIVFREE, 4, 48, gmls.VEC_LAPLACIAN),
+                                          (gmls.SCALAR, 4, 36, gmls.DIV)])
+def test_csr_structure_bit_exact(ctx, basis, m, k, fn):
+    x = inputs.jittered_grid(2, 30, seed=2)
+    n = x.shape[1]
+    cid, nid, idx, eps, st = _gpu_knn(ctx, x, k, 1.5)
+    sid = ctx.stencils(nid, basis, m, [fn])
+    rp, col, val = (t.cpu().numpy() for t in ctx.assemble_csr(sid, fn))
+    wg = ctx.weights(sid, fn).cpu().numpy()
+    nt, rows, nc, _ = ctx.stencil_info(sid, fn)
+    off = np.arange(0, n * k + 1, k)
+    wq = [wg[q * rows * k * nc:(q + 1) * rows * k * nc].reshape(rows, k, nc) for q in range(n)]
+    orp, ocol, oval, _ = oracle.csr(off, idx, wq, n)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    assert np.array_equal(val, oval)  # the same weights, permuted: bit for bit
+    _release(ctx, cid, nid, sid)
+
+
+# ----------------------------------------------------- full-size configuration
+def test_full_size_512x512_sampled(ctx):
+    """The benchmark's workload (262,144 targets on a 512 x 512 jittered grid,
+    scalar m=4 with 36 neighbours and divergence-free m=4 with 48), checked
+    on sampled targets that the oracle computes one by one."""
+    x = inputs.jittered_grid(2, 512, seed=0)
+    n = x.shape[1]
+    cid = ctx.cloud(x)
+    sample = np.unique((inputs.uniform(0, 99, 300) * n).astype(np.int32))
+    for basis, k, fn in ((gmls.SCALAR, 36, gmls.GRAD), (gmls.DIVFREE, 48, gmls.VEC_LAPLACIAN)):
+        nid = ctx.neighbors(cid, k, 1.5)
+        sid = ctx.stencils(nid, basis, 4, [fn], precision=gmls.FP32_REFINE)
+        idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy().reshape(n, k)
+        eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
+        oi, oe = oracle.knn(x, sample, k, 1.5, method="grid")
+        assert np.array_equal(idx[sample], oi) and np.array_equal(eps[sample], oe)
+        kind = "scalar" if basis == gmls.SCALAR else "divfree"
+        off = np.arange(0, len(sample) * k + 1, k)
+        wo, _, _ = oracle.stencils(x, sample, off, oi.reshape(-1), oe, kind, 4, NAMES[fn])
+        _, rows, nc, _ = ctx.stencil_info(sid, fn)
+        wg = ctx.weights(sid, fn).cpu().numpy().reshape(n, rows, k, nc)[sample]
+        assert _rel_err_rows(wg, wo) <= TOL32
+        ctx.release(sid)
+        ctx.release(nid)
+    ctx.release(cid)
