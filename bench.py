@@ -1,0 +1,408 @@
+"""GMLS stencil-generation benchmark (one JSON line on rank 0).
+
+Workload (the 2D Stokes operators of the compatible GMLS scheme, arXiv
+2104.14447 Sec. 3): 262,144 targets on a 512 x 512 jittered grid in the unit
+square (h = 1/512, jitter +-h/4, seed 0), sources = targets.  One step is the
+whole hot path:
+
+  cell-list build -> 36- and 48-nearest-neighbour lists (eps = 1.5 d_k) ->
+  scalar Taylor degree-4 stencils (15 terms; pressure gradient and the
+  component-wise divergence) -> divergence-free degree-4 stencils (20 terms,
+  96 x 20 systems; vector Laplacian) -> three CSR operators.
+
+value: targets/s of the whole job (every target gets all three operators).
+The default precision is FP32 Householder QR with FP64-residual refinement;
+``--precision fp64`` times the plain FP64 path.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 it runs under torch.distributed.run, one rank per GPU; every rank
+processes its own copy of the workload (independent problems: weak scaling,
+no data-path collective; only the timing is reduced).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_AXIS = 512
+K_SCALAR, K_DIVFREE, EPS_FACTOR, DEGREE = 36, 48, 1.5, 4
+METRIC = "GMLS targets/sec"
+WORKLOAD = "stokes2d-512x512: scalar m=4 (36 nbrs; grad, div) + div-free m=4 (48 nbrs; vector Laplacian) + CSR"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ALU peaks of one GB300 from unit counts and the maximum SM clock (2070 MHz):
+#   FP32: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s
+#   FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz     = 1.26 TFLOP/s
+P32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+P64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def flops_per_target(M, n, rows, iters):
+    """Algorithmic flops of one target ('roofline'):
+    FP32: QR 2Mn^2 - 2n^3/3, initial apply (n^2 + 4Mn) per row, and per
+    refinement iteration and row the correction solve (2n^2 + 8Mn);
+    FP64: per iteration and row the residuals f = By - s and g = l - B^T s (4Mn)."""
+    f32 = 2 * M * n * n - 2 * n ** 3 / 3 + rows * (n * n + 4 * M * n) + iters * rows * (2 * n * n + 8 * M * n)
+    f64 = iters * rows * 4 * M * n
+    return f32, f64
+
+
+def flops_per_target_fp64(M, n, rows):
+    return 2 * M * n * n - 2 * n ** 3 / 3 + rows * (n * n + 4 * M * n)
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        try:
+            rows = [r.split(", ") for r in open(self.path).read().strip().splitlines()]
+            os.unlink(self.path)
+        except OSError:
+            return None
+        rows = [r for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload_points():
+    from paper_2104_14447_gb300 import inputs
+
+    return inputs.jittered_grid(2, N_AXIS, seed=0)
+
+
+def set_n_axis(v):
+    """Grid size per axis (512 is the benchmark; smaller values only for profiling)."""
+    global N_AXIS
+    N_AXIS = int(v)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2104_14447_gb300 import build, gmls
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prec = gmls.FP64 if args.precision == "fp64" else gmls.FP32_REFINE
+    x_host = workload_points()
+    n = x_host.shape[1]
+    x_dev = torch.from_numpy(x_host).to(dev)
+    ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
+    stream = ctx.stream
+    # output buffers of the three operators (sizes are fixed by k)
+    nnz_grad, nnz_div, nnz_vl = n * K_SCALAR * 2, n * K_SCALAR * 2, n * K_DIVFREE * 2 * 2
+    bufs = {}
+    for name, rows, nnz in (("grad", 2 * n, nnz_grad), ("div", n, nnz_div), ("vl", 2 * n, nnz_vl)):
+        bufs[name] = (torch.empty(rows + 1, dtype=torch.int64, device=dev),
+                      torch.empty(nnz, dtype=torch.int32, device=dev),
+                      torch.empty(nnz, dtype=torch.float64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    ev_k = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def step(x_src, k_events=None):
+        cid = ctx.cloud(x_src)
+        n36 = ctx.neighbors(cid, K_SCALAR, EPS_FACTOR)
+        n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+        s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
+        if k_events:
+            k_events[0].record(stream)
+        s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
+        if k_events:
+            k_events[1].record(stream)
+        ctx.assemble_csr(s_sc, gmls.GRAD, out=bufs["grad"])
+        ctx.assemble_csr(s_sc, gmls.DIV, out=bufs["div"])
+        ctx.assemble_csr(s_df, gmls.VEC_LAPLACIAN, out=bufs["vl"])
+        return cid, n36, n48, s_sc, s_df
+
+    def release(ids):
+        for h in reversed(ids):
+            ctx.release(h)
+
+    for _ in range(args.warmup):
+        release(step(x_dev))
+    torch.cuda.synchronize()
+    # refinement statistics of this workload (one untimed step)
+    ids = step(x_dev)
+    it_sc = ctx.export(ids[3], gmls.X_ITERS, torch.uint8).float()
+    it_df = ctx.export(ids[4], gmls.X_ITERS, torch.uint8).float()
+    st_df = ctx.export(ids[4], gmls.X_STATUS, torch.uint8)
+    st_sc = ctx.export(ids[3], gmls.X_STATUS, torch.uint8)
+    fb = int(((st_df & gmls.T_FP64_FALLBACK) != 0).sum()) + int(((st_sc & gmls.T_FP64_FALLBACK) != 0).sum())
+    mean_it_sc, mean_it_df = float(it_sc.mean()), float(it_df.mean())
+    release(ids)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    launches0 = ctx.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local_rank) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)  # evict L2 between timed steps (outside the events)
+            ev[s][0].record(stream)
+            ids = step(x_dev, kev[s])
+            ev[s][1].record(stream)
+            release(ids)
+        torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # e2e: the same step through the C ABI from pinned host input to host operators
+    x_pin = torch.from_numpy(x_host).pin_memory()
+    host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
+    d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v)
+    h2d = x_pin.numel() * x_pin.element_size()
+    e2e_ms = []
+    for s in range(max(2, min(args.steps, 5)) + 1):
+        flush.fill_(s & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = step(x_pin)
+        for kname in bufs:
+            for dst, src in zip(host_out[kname], bufs[kname]):
+                dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        release(ids)
+    e2e_ms = e2e_ms[1:]
+
+    # roofline of the dominant kernel (the divergence-free stencil launch)
+    M_df, n_df, rows_df = K_DIVFREE * 2, 20, 2
+    if prec == gmls.FP32_REFINE:
+        f32, f64 = flops_per_target(M_df, n_df, rows_df, mean_it_df)
+        t_bound = n * (f32 / (P32_TFLOPS * 1e12) + f64 / (P64_TFLOPS * 1e12))
+    else:
+        f32, f64 = 0.0, flops_per_target_fp64(M_df, n_df, rows_df)
+        t_bound = n * f64 / (P64_TFLOPS * 1e12)
+    k_avg = float(np.mean(kern_ms)) * 1e-3
+    total_flops = n * (f32 + f64)
+    roofline = {"bound": "alu", "achieved": total_flops / k_avg / 1e12,
+                "peak": total_flops / t_bound / 1e12, "unit": "TFLOP/s", "frac": t_bound / k_avg,
+                "traffic": None, "kernel": "stencil_kernel (divergence-free m=4, 96x20)",
+                "fp32_flops_per_target": f32, "fp64_flops_per_target": f64,
+                "p32_tflops": P32_TFLOPS, "p64_tflops": P64_TFLOPS, "peak_source": "unit counts x 2070 MHz",
+                "kernel_ms": k_avg * 1e3}
+    targets = n * args.steps * world
+    value = targets / (total_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == gmls.FP32_REFINE else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "targets_per_gpu": n, "precision": args.precision,
+                   "degree": DEGREE, "neighbours": [K_SCALAR, K_DIVFREE], "eps_factor": EPS_FACTOR,
+                   "weight": "(1-r/eps)_+^4", "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"independent replicas x{world}" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "e2e": {"value": n * world / (float(np.mean(e2e_ms)) * 1e-3), "unit": "targets/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(np.mean(e2e_ms))},
+        "gpu_launches": int(launches),
+        "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
+    return out, ctx
+
+
+def oracle_pipeline(x, targets, threads=None):
+    """The oracle as it stands on the same workload (a sample of targets)."""
+    import oracle
+
+    n = x.shape[1]
+    i36, e36 = oracle.knn(x, targets, K_SCALAR, EPS_FACTOR, method="grid")
+    i48, e48 = oracle.knn(x, targets, K_DIVFREE, EPS_FACTOR, method="grid")
+    nt = len(targets)
+    off36 = np.arange(0, nt * K_SCALAR + 1, K_SCALAR)
+    off48 = np.arange(0, nt * K_DIVFREE + 1, K_DIVFREE)
+    wg, _, _ = oracle.stencils(x, targets, off36, i36.reshape(-1), e36, "scalar", DEGREE, "grad")
+    wd, _, _ = oracle.stencils(x, targets, off36, i36.reshape(-1), e36, "scalar", DEGREE, "div")
+    wv, _, _ = oracle.stencils(x, targets, off48, i48.reshape(-1), e48, "divfree", DEGREE, "vec_laplacian")
+    oracle.csr(off36, i36.reshape(-1), wg, n)
+    oracle.csr(off36, i36.reshape(-1), wd, n)
+    oracle.csr(off48, i48.reshape(-1), wv, n)
+    return {"grad": wg, "div": wd, "vl": wv, "idx36": i36, "idx48": i48}
+
+
+def cpu_baseline(ctx=None, sample_stride=1):
+    """Time the oracle on the host cores; with a GPU context also report the
+    GPU path's error against it on a sample of targets."""
+    import oracle
+
+    oracle.build()
+    x = workload_points()
+    n = x.shape[1]
+    targets = np.arange(0, n, sample_stride, dtype=np.int32)
+    t0 = time.perf_counter()
+    res = oracle_pipeline(x, targets)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"value": len(targets) / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(targets)} of {n} targets (every {sample_stride}th), full pipeline incl. kNN and CSR",
+           "seconds": dt}
+    if ctx is not None:
+        out["max_rel_err_vs_oracle"] = gpu_error(ctx, x, res, targets)
+    return out
+
+
+def gpu_error(ctx, x, res, targets):
+    """max over sampled (target, row) of |w_gpu - w_oracle|_inf / |w_oracle|_inf."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls
+
+    n = x.shape[1]
+    samp = np.arange(0, len(targets), max(1, len(targets) // 4096))
+    errs = {}
+    cid = ctx.cloud(torch.from_numpy(x).to(ctx.device))
+    for key, k, basis, fn in (("grad", K_SCALAR, gmls.SCALAR, gmls.GRAD), ("div", K_SCALAR, gmls.SCALAR, gmls.DIV),
+                              ("vl", K_DIVFREE, gmls.DIVFREE, gmls.VEC_LAPLACIAN)):
+        nid = ctx.neighbors(cid, k, EPS_FACTOR)
+        sid = ctx.stencils(nid, basis, DEGREE, [fn], precision=gmls.FP32_REFINE)
+        _, rows, nc, _ = ctx.stencil_info(sid, fn)
+        wg = ctx.weights(sid, fn).cpu().numpy().reshape(n, rows, k, nc)[targets[samp]]
+        wo = res[key][samp]
+        a = np.abs(wg - wo).reshape(len(samp), rows, -1).max(axis=2)
+        b = np.abs(wo).reshape(len(samp), rows, -1).max(axis=2)
+        errs[key] = float(np.max(a / np.where(b > 0, b, 1.0)))
+        ctx.release(sid)
+        ctx.release(nid)
+    ctx.release(cid)
+    return errs
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle, as it stands, on the host cores (this workload's CPU program)."""
+    import oracle
+
+    oracle.build()
+    x = workload_points()
+    n = x.shape[1]
+    stride = args.ref_stride
+    targets = np.arange(0, n, stride, dtype=np.int32)
+    for _ in range(args.warmup):
+        oracle_pipeline(x, targets)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_pipeline(x, targets)
+        times.append(time.perf_counter() - t0)
+    total = float(np.sum(times))
+    value = len(targets) * args.steps / total
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{len(targets)} of {n} targets per step (every {stride}th), full pipeline incl. kNN and CSR"
+    return {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "targets_per_gpu": n, "precision": "fp64 (oracle)",
+                       "degree": DEGREE, "neighbours": [K_SCALAR, K_DIVFREE], "eps_factor": EPS_FACTOR},
+            "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32_refine", "fp64"], default="fp32_refine")
+    ap.add_argument("--arena-gb", type=int, default=24)
+    ap.add_argument("--ref-stride", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-axis", type=int, default=512, help="profiling only; the benchmark is 512")
+    args = ap.parse_args()
+    set_n_axis(args.n_axis)
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out, ctx = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

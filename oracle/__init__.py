@@ -202,6 +202,16 @@ def csr(nbr_off, nbr_idx, weights, n_cols_points):
     nt = len(off) - 1
     w0 = weights[0]
     rows, _, nc = w0.shape
+    if isinstance(weights, np.ndarray) and nt:
+        # every target has the same k: the same steps, vectorised over targets
+        k = weights.shape[2]
+        colq = (idx.reshape(nt, k)[:, :, None] * nc + np.arange(nc)[None, None, :]).reshape(nt, k * nc)
+        order = np.argsort(colq, axis=1, kind="stable")
+        cols = np.take_along_axis(colq, order, axis=1)
+        vals = np.take_along_axis(weights.reshape(nt, rows, k * nc), order[:, None, :], axis=2)
+        row_ptr = np.arange(nt * rows + 1, dtype=np.int64) * (k * nc)
+        return (row_ptr, np.repeat(cols[:, None, :], rows, axis=1).reshape(-1).astype(np.int32),
+                vals.reshape(-1).astype(np.float64), int(n_cols_points) * nc)
     row_ptr = [0]
     cols, vals = [], []
     for q in range(nt):

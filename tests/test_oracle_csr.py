@@ -28,3 +28,16 @@ def test_csr_matches_scipy():
     assert np.array_equal(row_ptr, ref.indptr)
     assert np.array_equal(col, ref.indices)
     assert np.array_equal(val, ref.data)
+
+
+def test_csr_fixed_k_fast_path_equals_general_path():
+    x = inputs.jittered_grid(2, 10, seed=3)
+    n = x.shape[1]
+    tg = np.arange(n, dtype=np.int32)
+    idx, eps = oracle.knn(x, tg, 12, 1.5)
+    off = np.arange(0, n * 12 + 1, 12)
+    w, _, _ = oracle.stencils(x, tg, off, idx.reshape(-1), eps, "scalar", 2, "grad")
+    a = oracle.csr(off, idx.reshape(-1), w, n)
+    b = oracle.csr(off, idx.reshape(-1), list(w), n)
+    for u, v in zip(a[:3], b[:3]):
+        assert np.array_equal(u, v)
