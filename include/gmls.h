@@ -90,7 +90,7 @@ typedef int32_t gmls_status;
 
 /* precision */
 #define GMLS_FP64 0        /* FP64 basis, QR and apply                                       */
-#define GMLS_FP32_REFINE 1 /* FP32 QR, FP64 residuals, FP32 corrections (FP64 fallback)      */
+#define GMLS_FP32_REFINE 1 /* FP32 QR, FP64-class residuals, FP32 corrections (FP64 redo)     */
 
 /* export selectors */
 #define GMLS_X_NBR_OFFSETS 0 /* int64 [n_targets + 1]                          */
@@ -214,6 +214,13 @@ gmls_status gmls_arena_usage(gmls_ctx* ctx, size_t* used, size_t* peak, size_t* 
 
 /* Number of kernels this context has launched since creation. */
 gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
+
+/* options of gmls_set_option */
+#define GMLS_OPT_FORCE_GENERIC 0 /* 1: every shape uses the shared-memory tile kernel, not the
+                                    warp-per-target register kernel (testing and tuning)    */
+
+/* Set a context option (GMLS_OPT_*); applies to later calls. */
+gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
 
 /* Message of the last error on this context (NULL ctx: last create error). */
 const char* gmls_last_error(gmls_ctx* ctx);

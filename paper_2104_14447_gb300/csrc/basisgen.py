@@ -33,9 +33,9 @@ DEGREES = (1, 2, 3, 4)
 
 
 def monomials(d: int, m: int):
-    """Exponents with |g| <= m; degree ascending, within a degree the last
-    coordinate varies slowest (reverse of the oracle's order on purpose is not
-    required: any order gives the same stencils)."""
+    """Exponents with |g| <= m, degree ascending; within a degree g_x
+    descends.  The linear monomials are entries 1..d (used by the Neumann
+    elimination)."""
     out = []
     for s in range(m + 1):
         if d == 2:
@@ -123,15 +123,19 @@ def cnum(fr: Fraction) -> str:
 
 
 def emit_monomials(d, m, lines, ind):
-    """px[a] = xi_x^a / a! etc. and p[i] = product."""
+    """px{a} = xi_x^a / a! etc. (no factor for a = 0), products per monomial."""
     names = "xyz"
     for k in range(d):
-        lines.append(f"{ind}T p{names[k]}0 = T(1);")
         for a in range(1, m + 1):
-            lines.append(f"{ind}T p{names[k]}{a} = p{names[k]}{a - 1} * xi[{k}] * T({cnum(Fraction(1, a))});")
-    return [
-        "*".join(f"p{names[k]}{g[k]}" for k in range(d)) for g in monomials(d, m)
-    ]
+            if a == 1:
+                lines.append(f"{ind}const T p{names[k]}1 = xi[{k}];")
+            else:
+                lines.append(f"{ind}const T p{names[k]}{a} = (p{names[k]}{a - 1} * xi[{k}]) * T({cnum(Fraction(1, a))});")
+    prods = []
+    for g in monomials(d, m):
+        f = [f"p{names[k]}{g[k]}" for k in range(d) if g[k] > 0]
+        prods.append("*".join(f) if f else "T(1)")
+    return prods
 
 
 def gen():
@@ -156,13 +160,15 @@ def gen():
                 nterms = sum(len(f) for f in funcs)
                 summary.append((kind, d, m, nb, nc, nterms))
                 L.append(f"// {name}: {nb} functions, {nc} component(s), {nterms} terms")
+                L.append(f"// out[i * ld + c] = s * psi_i,c(xi)")
                 L.append("template <typename T>")
-                L.append(f"__device__ __forceinline__ void eval_{name}(const T* xi, T* out, int ld) {{")
+                L.append(f"__device__ __forceinline__ void eval_{name}(const T* xi, T* out, int ld, const T s) {{")
                 ind = "  "
                 prods = emit_monomials(d, m, L, ind)
+                used = {mi for f in funcs for (_, mi, _) in f}
                 for i, g in enumerate(mons):
-                    L.append(f"{ind}const T q{i} = {prods[i]};")
-                    L.append(f"{ind}(void)q{i};")
+                    if i in used:
+                        L.append(f"{ind}const T q{i} = {'s' if prods[i] == 'T(1)' else 's * (' + prods[i] + ')'};")
                 # out[i*ld + c] = sum terms
                 for i, f in enumerate(funcs):
                     for c in range(nc):
@@ -206,14 +212,23 @@ def gen():
     L.append("    0;")
     L.append("}")
     L.append("template <typename T>")
-    L.append("__device__ __forceinline__ void eval_basis(int kind, int d, int m, const T* xi, T* out, int ld) {")
+    L.append("__device__ __forceinline__ void eval_basis(int kind, int d, int m, const T* xi, T* out, int ld, const T s) {")
     L.append("  switch (kind * 100 + d * 10 + m) {")
     for kind, d, m, nb, nc, _ in summary:
         name = f"{kind}_{d}d_m{m}"
-        L.append(f"    case {(0 if kind == 'scalar' else 1) * 100 + d * 10 + m}: eval_{name}<T>(xi, out, ld); break;")
+        L.append(f"    case {(0 if kind == 'scalar' else 1) * 100 + d * 10 + m}: eval_{name}<T>(xi, out, ld, s); break;")
     L.append("    default: break;")
     L.append("  }")
     L.append("}")
+    L.append("// compile-time dispatch: BasisEval<kind, d, m>::run<T>(xi, out, ld)")
+    L.append("template <int KIND, int D, int M> struct BasisEval;")
+    for kind, d, m, nb, nc, _ in summary:
+        name = f"{kind}_{d}d_m{m}"
+        kid = 0 if kind == "scalar" else 1
+        L.append(f"template <> struct BasisEval<{kid}, {d}, {m}> {{")
+        L.append("  template <typename T>")
+        L.append(f"  __device__ __forceinline__ static void run(const T* xi, T* out, int ld, const T s) {{ eval_{name}<T>(xi, out, ld, s); }}")
+        L.append("};")
     L.append("// functional row coefficient (before the eps^{-|beta|} factor)")
     L.append("// fn: 0 grad (d rows), 1 laplacian (1 row), 2 vector Laplacian (d rows),")
     L.append("//     3 curl curl (d rows), 4 divergence of a div-free field (1 row, zero)")

@@ -88,6 +88,8 @@ struct CloudObj {
   int dim = 0;
   int64_t n = 0;
   double* x = nullptr;
+  float* xh = nullptr;  // float-float split of x
+  float* xl = nullptr;
   double* normals = nullptr;
   uint8_t* bflag = nullptr;
   double* xs = nullptr;
@@ -143,6 +145,7 @@ struct gmls_ctx {
   std::unordered_map<int64_t, Obj> objs;
   int64_t next_id = 1;
   int64_t launches = 0;
+  bool force_generic = false;  // testing: use the generic tile kernel for every shape
   std::string err;
   Launch launch() { return Launch{stream, &launches}; }
 };
@@ -246,6 +249,14 @@ gmls_status gmls_arena_usage(gmls_ctx* ctx, size_t* used, size_t* peak, size_t* 
   return GMLS_OK;
 }
 
+gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return GMLS_EINVAL;
+  switch (option) {
+    case GMLS_OPT_FORCE_GENERIC: ctx->force_generic = value != 0; return GMLS_OK;
+    default: return fail(ctx, GMLS_EINVAL, "gmls_set_option: unknown option");
+  }
+}
+
 gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches) {
   if (!ctx || !launches) return GMLS_EINVAL;
   *launches = ctx->launches;
@@ -273,6 +284,8 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   const int n_part = (int)std::min<int64_t>(256, (n + 255) / 256);
   const int64_t scan_elems = scan_scratch_elems(ncell);
   c.x = arena_alloc<double>(ctx, (size_t)dim * n);
+  c.xh = arena_alloc<float>(ctx, (size_t)dim * n);
+  c.xl = arena_alloc<float>(ctx, (size_t)dim * n);
   c.xs = arena_alloc<double>(ctx, (size_t)dim * n);
   c.sorted = arena_alloc<int32_t>(ctx, n);
   c.cell_start = arena_alloc<int32_t>(ctx, ncell + 1);
@@ -284,7 +297,7 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   int32_t* counts = arena_alloc<int32_t>(ctx, ncell);
   int32_t* fill = arena_alloc<int32_t>(ctx, ncell);
   int32_t* scan_tmp = arena_alloc<int32_t>(ctx, scan_elems);
-  void* all[] = {c.x, c.xs, c.sorted, c.cell_start, c.grid, part, cell_of, counts, fill, scan_tmp};
+  void* all[] = {c.x, c.xh, c.xl, c.xs, c.sorted, c.cell_start, c.grid, part, cell_of, counts, fill, scan_tmp};
   bool oom = false;
   for (void* p : all) oom |= (p == nullptr);
   oom |= (normals && !c.normals) || (bflags && !c.bflag);
@@ -300,6 +313,7 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   if (bflags) CK(copy_in(ctx, c.bflag, bflags, n), "gmls_cloud copy flags");
   CK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * ncell, ctx->stream), "gmls_cloud memset");
   CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncell, ctx->stream), "gmls_cloud memset");
+  CK(launch_split_ff(L, c.x, c.xh, c.xl, (int64_t)dim * n), "gmls_cloud split");
   CK(launch_bbox_and_grid(L, dim, n, c.x, nc_axis, c.grid, part, n_part), "gmls_cloud bbox");
   CK(launch_cell_count(L, dim, n, c.x, c.grid, cell_of, counts), "gmls_cloud count");
   CK(launch_scan_i32(L, counts, c.cell_start, ncell, scan_tmp, scan_elems), "gmls_cloud scan");
@@ -533,6 +547,8 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.dim = dim;
   j.n = c.n;
   j.x = c.x;
+  j.xh = c.xh;
+  j.xl = c.xl;
   j.normals = c.normals;
   j.bflag = c.bflag;
   j.n_tgt = nt;
@@ -548,6 +564,7 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.degree_pt = deg;
   j.nc = nc;
   j.wpow = (double)p->weight_power;
+  j.wpow_half = p->weight_power / 2;
   j.neumann = p->neumann;
   j.L = L;
   j.nout = s.nout;
@@ -602,8 +619,15 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
     return (int)std::max<int64_t>(1, std::min(want, cap));
   };
   if (refine) CK(cudaMemsetAsync(s.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  // the warp-per-target float-float kernel when this shape is instantiated
+  int mr = 0;
+  const bool fast = refine && !p->degree_per_target && (p->weight_power % 2 == 0) && !ctx->force_generic &&
+                    fast_path_available(p->basis, dim, p->degree, ld, &mr);
   if (nt > 0) {
-    CK(launch_stencils(Lc, j, refine, grid_for(refine, nt)), "gmls_stencils launch");
+    if (fast)
+      CK(launch_stencils_fast(Lc, j, mr, dev_sms), "gmls_stencils fast launch");
+    else
+      CK(launch_stencils(Lc, j, refine, grid_for(refine, nt)), "gmls_stencils launch");
     if (refine) {
       StencilJob jf = j;
       jf.items = s.fb_items;
@@ -780,8 +804,8 @@ gmls_status gmls_release(gmls_ctx* ctx, int64_t id) {
   Arena& a = ctx->arena;
   if (o.kind == K_CLOUD) {
     if (o.c.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: cloud has live neighbour handles");
-    for (void* p : {(void*)o.c.x, (void*)o.c.normals, (void*)o.c.bflag, (void*)o.c.xs, (void*)o.c.sorted,
-                    (void*)o.c.cell_start, (void*)o.c.grid})
+    for (void* p : {(void*)o.c.x, (void*)o.c.xh, (void*)o.c.xl, (void*)o.c.normals, (void*)o.c.bflag,
+                    (void*)o.c.xs, (void*)o.c.sorted, (void*)o.c.cell_start, (void*)o.c.grid})
       a.release(p);
   } else if (o.kind == K_NBRS) {
     if (o.nb.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: neighbours have live stencil handles");

@@ -105,6 +105,8 @@ struct StencilJob {
   int dim;
   int64_t n;
   const double* x;
+  const float* xh;         // float-float split of x (x = xh + xl), SoA
+  const float* xl;
   const double* normals;   // SoA [dim][n] or NULL
   const uint8_t* bflag;    // [n] or NULL
   // neighbours
@@ -123,6 +125,7 @@ struct StencilJob {
   const int8_t* degree_pt; // [n_tgt] or NULL
   int nc;                  // components per neighbour (1 or dim)
   double wpow;
+  int wpow_half;           // p / 2 for even p (float-float path)
   int neumann;
   // solve rows: row r of the L solve rows is functional code lam_fn[r], sub-row lam_row[r]
   int L;
@@ -153,6 +156,9 @@ struct StencilJob {
 };
 
 size_t stencil_smem_bytes(const StencilJob& j, bool fp32_refine);
+bool fast_path_available(int kind, int dim, int deg, int rows, int* mr_out);
+cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int sms);
+cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count);
 cudaError_t launch_stencils(const Launch& L, const StencilJob& j, bool fp32_refine, int grid_blocks);
 
 // -------------------------------------------------------------------- CSR

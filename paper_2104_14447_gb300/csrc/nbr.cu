@@ -139,6 +139,23 @@ cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const doubl
   return cudaGetLastError();
 }
 
+// x = xh + xl with xh = fl32(x): the float-float coordinates of the FP32 path
+__global__ void split_ff_kernel(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
+                                int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = __double2float_rn(v);
+    xh[i] = h;
+    xl[i] = __double2float_rn(v - (double)h);
+  }
+}
+
+cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count) {
+  split_ff_kernel<<<blocks_for(count, 256), 256, 0, L.stream>>>(x, xh, xl, count);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------- scan
 // Exclusive scan in three passes: tile sums, a one-block scan of the tile
 // sums, then each tile rescanned with its offset.  out has n + 1 entries;

@@ -276,11 +276,8 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(StencilJob j) {
         }
         const double u = 1.0 - sqrt(r2) * inv_eps;
         const double s = (u > 0.0) ? (j.wpow == 4.0 ? u * u : pow(u, 0.5 * j.wpow)) : 0.0;
-        gmls_gen::eval_basis<double>(j.kind, dim, m, xi, Bd + q * nc, ld);
-        for (int c = 0; c < nc; ++c) {
-          sw[q * nc + c] = s;
-          for (int i = 0; i < nb; ++i) Bd[(size_t)i * ld + q * nc + c] *= s;
-        }
+        gmls_gen::eval_basis<double>(j.kind, dim, m, xi, Bd + q * nc, ld, s);
+        for (int c = 0; c < nc; ++c) sw[q * nc + c] = s;
       }
       // ---- 3. functional rows lambda (before Neumann)
       for (int e = g.tid; e < L * nb; e += g.nthr) {

@@ -37,8 +37,9 @@ X_NBR_OFFSETS, X_NBR_INDEX, X_NBR_EPS, X_NBR_STATUS, X_WEIGHTS, X_BETA, X_STATUS
 EXPORTED = [
     "gmls_create", "gmls_destroy", "gmls_set_stream", "gmls_cloud", "gmls_neighbors", "gmls_stencils",
     "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_export", "gmls_export_size", "gmls_release",
-    "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_last_error", "gmls_version",
+    "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_last_error", "gmls_version",
 ]
+OPT_FORCE_GENERIC = 0
 
 
 class GmlsError(RuntimeError):
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
         "gmls_sync": [vp],
         "gmls_arena_usage": [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "gmls_launch_count": [vp, P64],
+        "gmls_set_option": [vp, i32, i64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -231,6 +233,9 @@ class Context:
         u, p, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
         self._check(self.lib.gmls_arena_usage(self.h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(c)))
         return u.value, p.value, c.value
+
+    def set_option(self, option: int, value: int):
+        self._check(self.lib.gmls_set_option(self.h, option, value))
 
     def launch_count(self) -> int:
         v = ctypes.c_int64()
