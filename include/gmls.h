@@ -222,7 +222,34 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
 /* Set a context option (GMLS_OPT_*); applies to later calls. */
 gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
 
-/* Message of the last error on this context (NULL ctx: last create error). */
+/*
+ * k-nearest-neighbour lists of every particle of a cloud without allocating
+ * device memory (the paper has no counterpart; this entry point is for
+ * callers that cannot allocate at the point of use -- e.g. a solver embedded
+ * in a larger simulation code that reserves all device memory at start-up
+ * and treats any later cudaMalloc as an error, since cudaMalloc synchronises
+ * the device and can fail in the middle of a time step).
+ *
+ * Same results as gmls_cloud + gmls_neighbors(GMLS_NBR_KNN, k, eps_factor)
+ * with every particle a target: out_idx [n][k] sorted by (d^2, id), out_eps
+ * [n], out_status [n] (GMLS_T_* bits).  xyz (FP64 SoA [dim][n]) and the
+ * outputs are caller-owned DEVICE buffers; work is queued on cuda_stream.
+ * No context is needed and nothing is allocated or freed: the cell-list
+ * scratch is one static device array of about 11 MB that every GPU loading
+ * the library holds until exit, sized for at most GMLS_NOALLOC_MAX_POINTS
+ * particles (GMLS_EINVAL beyond that, message in gmls_last_error(NULL)).
+ * All calls on a device share that array and it keeps the last call's
+ * contents (the counters that must start at zero are cleared at the start of
+ * each call): calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * address once for that device; make it before any stream capture.
+ */
+#define GMLS_NOALLOC_MAX_POINTS 262144
+gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, int32_t k, double eps_factor, int32_t* out_idx,
+                             double* out_eps, uint8_t* out_status, void* cuda_stream);
+
+/* Message of the last error on this context (NULL ctx: the last error of a
+   call without a context: gmls_create or gmls_knn_noalloc). */
 const char* gmls_last_error(gmls_ctx* ctx);
 
 /* Library version string. */

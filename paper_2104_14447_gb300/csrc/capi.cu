@@ -138,6 +138,11 @@ std::string g_create_error;
 
 }  // namespace
 
+namespace gmls {
+// last error of a call made without a context (see gmls_last_error(NULL))
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace gmls
+
 struct gmls_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

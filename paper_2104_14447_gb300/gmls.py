@@ -37,8 +37,10 @@ X_NBR_OFFSETS, X_NBR_INDEX, X_NBR_EPS, X_NBR_STATUS, X_WEIGHTS, X_BETA, X_STATUS
 EXPORTED = [
     "gmls_create", "gmls_destroy", "gmls_set_stream", "gmls_cloud", "gmls_neighbors", "gmls_stencils",
     "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_export", "gmls_export_size", "gmls_release",
-    "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_last_error", "gmls_version",
+    "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
+    "gmls_version",
 ]
+NOALLOC_MAX_POINTS = 262144
 OPT_FORCE_GENERIC = 0
 
 
@@ -91,6 +93,7 @@ def load(path: str = LIB_PATH):
         "gmls_arena_usage": [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz)],
         "gmls_launch_count": [vp, P64],
         "gmls_set_option": [vp, i32, i64],
+        "gmls_knn_noalloc": [ctypes.c_int, i64, vp, i32, ctypes.c_double, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
