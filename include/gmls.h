@@ -68,6 +68,7 @@ typedef int32_t gmls_status;
 #define GMLS_T_TOO_FEW_NEIGHBOURS 8  /* fewer candidates than requested (weights zero)       */
 #define GMLS_T_FP64_FALLBACK 16      /* result recomputed by the FP64 path                    */
 #define GMLS_T_OVERFLOW 32           /* candidate buffer exceeded (neighbour list truncated) */
+#define GMLS_T_UNSUPPORTED 64        /* rows x basis size exceed every tile of this build (weights zero) */
 
 /* neighbour modes */
 #define GMLS_NBR_KNN 0    /* k nearest by (d^2, index); eps = eps_factor * d_k                */
@@ -112,6 +113,9 @@ typedef struct {
   int64_t n_targets;         /* ignored when targets is NULL                                 */
   const double* halfspace;   /* NULL, or host or device [n_targets][dim]: keep only j with
                                 n . (x_j - x_T) <= 0; an all-zero row disables the filter    */
+  const int32_t* k_per_target; /* NULL, or host or device int32 [n_targets] (1..cap): k of each
+                                target (KNN: list length; RADIUS: the k whose distance sets
+                                eps); k above is then the largest value                      */
 } gmls_nbr_params;
 
 typedef struct {
@@ -218,6 +222,11 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
 /* options of gmls_set_option */
 #define GMLS_OPT_FORCE_GENERIC 0 /* 1: every shape uses the shared-memory tile kernel, not the
                                     warp-per-target register kernel (testing and tuning)    */
+#define GMLS_OPT_AUTOTUNE 1      /* 1 (default): the first gmls_stencils call for a shape times
+                                    the kernel variants (register kernel; 1, 2 or 4 warps per
+                                    target) on up to 8192 targets and caches the fastest; this
+                                    call waits for the stream.  0: heuristic choice          */
+#define GMLS_OPT_CLEAR_TUNING 2  /* any value: forget the cached choices and timings         */
 
 /* Set a context option (GMLS_OPT_*); applies to later calls. */
 gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
@@ -247,6 +256,29 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
 #define GMLS_NOALLOC_MAX_POINTS 262144
 gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, int32_t k, double eps_factor, int32_t* out_idx,
                              double* out_eps, uint8_t* out_status, void* cuda_stream);
+
+/*
+ * Autotuner record `index` (0-based, in the order taken): fields[9] =
+ * {basis, dim, degree, precision, tile rows, solve rows, neumann, bucketed,
+ * variant (-1 register kernel, else warps per target)}, *ms its time.
+ * GMLS_ENOTFOUND past the last record.
+ */
+gmls_status gmls_tune_info(gmls_ctx* ctx, int32_t index, int32_t* fields, float* ms);
+
+/*
+ * CUDA-graph capture of a pipeline on the context's stream (which must not
+ * be the legacy default stream).  Calls between gmls_capture_begin and
+ * gmls_capture_end are recorded, not run; the handles they return stay valid
+ * and every gmls_graph_launch rewrites their outputs.  Capture the pipeline
+ * after one uncaptured run of the same shapes, so that the autotuner does not
+ * need to time anything (it never runs while capturing; uncached shapes then
+ * use the heuristic choice).  Calls that must read device results on the host
+ * (gmls_csr_size of radius-mode lists, exports to host) return GMLS_EBUSY or
+ * fail during capture.  The graph handle is freed by gmls_release.
+ */
+gmls_status gmls_capture_begin(gmls_ctx* ctx);
+gmls_status gmls_capture_end(gmls_ctx* ctx, int64_t* graph_id);
+gmls_status gmls_graph_launch(gmls_ctx* ctx, int64_t graph_id);
 
 /* Message of the last error on this context (NULL ctx: the last error of a
    call without a context: gmls_create or gmls_knn_noalloc). */

@@ -82,7 +82,7 @@ class Arena {
   std::map<size_t, size_t> free_, live_;
 };
 
-enum Kind { K_CLOUD = 1, K_NBRS = 2, K_STENCIL = 3 };
+enum Kind { K_CLOUD = 1, K_NBRS = 2, K_STENCIL = 3, K_GRAPH = 4 };
 
 struct CloudObj {
   int dim = 0;
@@ -110,6 +110,7 @@ struct NbrObj {
   double* eps = nullptr;
   uint8_t* status = nullptr;
   int mode = 0, k = 0, cap = 0;
+  bool variable = false;  // per-target list lengths (offsets from a scan)
   int64_t idx_cap = 0;  // allocated index entries
   int refs = 0;
 };
@@ -132,6 +133,7 @@ struct Obj {
   CloudObj c;
   NbrObj nb;
   StencilObj s;
+  cudaGraphExec_t exec = nullptr;
 };
 
 std::string g_create_error;
@@ -143,6 +145,22 @@ namespace gmls {
 void set_global_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace gmls
 
+struct TuneKey {
+  int basis, dim, degree, precision, ld, L, neumann, bucketed;
+  bool operator<(const TuneKey& o) const {
+    const int a[8] = {basis, dim, degree, precision, ld, L, neumann, bucketed};
+    const int b[8] = {o.basis, o.dim, o.degree, o.precision, o.ld, o.L, o.neumann, o.bucketed};
+    for (int i = 0; i < 8; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+struct TuneRecord {
+  TuneKey key;
+  int variant;  // -1 register kernel, else warps per target
+  float ms;
+};
+
 struct gmls_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -151,6 +169,9 @@ struct gmls_ctx {
   int64_t next_id = 1;
   int64_t launches = 0;
   bool force_generic = false;  // testing: use the generic tile kernel for every shape
+  bool autotune = true;
+  std::map<TuneKey, int> tune;        // chosen variant per shape
+  std::vector<TuneRecord> tune_log;   // every timing the autotuner took
   std::string err;
   Launch launch() { return Launch{stream, &launches}; }
 };
@@ -188,6 +209,273 @@ static bool is_host_ptr(const void* p) {
     return true;
   }
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+
+// ------------------------------------------------------------- launch planning
+// heuristic warps per target for a tile of ld rows: a warp up to 64 rows, two
+// up to 192, four beyond; more when the tile would not fit.
+static int heuristic_g(int ld, int nmax, bool fp32) {
+  int g = ld <= 64 ? 1 : (ld <= 192 ? 2 : 4);
+  while (g < 4 && (size_t)(4 / g) * tile_bytes(ld, nmax, fp32) > 110 * 1024) g *= 2;
+  return ((size_t)(4 / g) * tile_bytes(ld, nmax, fp32) <= 227 * 1024) ? g : 0;
+}
+
+static size_t plan_smem(const BatchPlan& pl, bool fp32) {
+  size_t m = 0;
+  for (int b = 0; b < (pl.single ? 1 : pl.nb); ++b)
+    if (pl.G[b] > 0) m = std::max(m, (size_t)(4 / pl.G[b]) * tile_bytes(pl.ld[b], pl.nmax[b], fp32));
+  return m;
+}
+
+static bool capturing(gmls_ctx* ctx) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// time one launch on the context stream (ms), for the autotuner
+template <typename F>
+static float time_launch(gmls_ctx* ctx, F&& launch) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  launch();  // warm
+  cudaEventRecord(a, ctx->stream);
+  launch();
+  cudaEventRecord(b, ctx->stream);
+  cudaEventSynchronize(b);
+  float ms = 1e30f;
+  if (cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+
+static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int G, int ld, int nmax, bool fp32,
+                                 int32_t* counter, int sms) {
+  BatchPlan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  pl.single = 1;
+  pl.nb = 1;
+  pl.G[0] = G;
+  pl.ld[0] = ld;
+  pl.nmax[0] = nmax;
+  pl.task_counter = counter;
+  const size_t smem = plan_smem(pl, fp32);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
+  if (e != cudaSuccess) return e;
+  const int grid = sms * stencil_blocks_per_sm(fp32, smem);
+  Launch L = ctx->launch();
+  return launch_stencils(L, j, pl, fp32, smem, grid);
+}
+
+// Uniform neighbour counts and degree: one shape.  Candidates: the
+// warp-per-target register kernel (when this shape is instantiated) and the
+// shared-memory kernel with 1, 2 or 4 warps per target; the autotuner times
+// each once on up to 8192 targets and the choice is cached per shape.
+static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls_stencil_params* p, bool refine,
+                                  int ld, int nmax, int sms, int32_t* counter) {
+  const int dim = j.dim;
+  int mr = 0;
+  const bool fast_ok = refine && (p->weight_power % 2 == 0) && !ctx->force_generic &&
+                       fast_path_available(p->basis, dim, p->degree, ld, &mr);
+  const TuneKey key{p->basis, dim, p->degree, p->precision, ld, j.L, p->neumann, 0};
+  int choice = 0;  // -1 fast kernel, else G
+  auto it = ctx->tune.find(key);
+  if (ctx->force_generic) {
+    choice = heuristic_g(ld, nmax, refine);
+  } else if (it != ctx->tune.end()) {
+    choice = it->second;
+  } else if (ctx->autotune && !capturing(ctx)) {
+    StencilJob js = j;
+    js.n_tgt = std::min<int64_t>(j.n_tgt, 8192);
+    float best = 1e30f;
+    std::vector<int> cands;
+    if (fast_ok) cands.push_back(-1);
+    for (int G = 1; G <= 4; G *= 2)
+      if ((size_t)(4 / G) * tile_bytes(ld, nmax, refine) <= 227 * 1024) cands.push_back(G);
+    for (int c : cands) {
+      float ms = time_launch(ctx, [&]() {
+        if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
+        if (c < 0)
+          launch_stencils_fast(ctx->launch(), js, mr, sms);
+        else
+          launch_single(ctx, js, c, ld, nmax, refine, counter, sms);
+      });
+      ctx->tune_log.push_back({key, c, ms});
+      if (ms < best) {
+        best = ms;
+        choice = c;
+      }
+    }
+    if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: no kernel variant fits this shape");
+    ctx->tune[key] = choice;
+  } else {
+    choice = fast_ok ? -1 : heuristic_g(ld, nmax, refine);
+  }
+  if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this shape");
+  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  if (choice < 0)
+    CK(launch_stencils_fast(ctx->launch(), j, mr, sms), "gmls_stencils fast launch");
+  else
+    CK(launch_single(ctx, j, choice, ld, nmax, refine, counter, sms), "gmls_stencils launch");
+  return GMLS_OK;
+}
+
+// Uneven shapes (per-target degree or radius neighbour lists): bucket the
+// targets on the device by (degree, row class) and run ONE persistent launch
+// over all buckets; warps per target per bucket from the autotuner cache (or
+// timed now, which reads the bucket sizes back once), else the heuristic.
+static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gmls_stencil_params* p, bool refine,
+                                   int ld_max, int sms, int32_t* counter) {
+  static const int kClasses[] = {32, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024};
+  const int dim = j.dim;
+  BucketJob b;
+  std::memset(&b, 0, sizeof(b));
+  b.n_tgt = j.n_tgt;
+  b.off = j.off;
+  b.degree_pt = j.degree_pt;
+  b.degree = j.degree;
+  b.nc = j.nc;
+  for (int c : kClasses) {
+    b.class_rows[b.n_classes++] = c;
+    if (c >= ld_max) break;
+  }
+  b.nb = 4 * b.n_classes + 1;
+  BatchPlan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  pl.single = 0;
+  pl.nb = b.nb;
+  for (int m = 1; m <= 4; ++m)
+    for (int rc = 0; rc < b.n_classes; ++rc) {
+      const int bi = (m - 1) * b.n_classes + rc;
+      pl.ld[bi] = b.class_rows[rc];
+      pl.nmax[bi] = gmls_gen::basis_size(p->basis, dim, m);
+      const TuneKey key{p->basis, dim, m, p->precision, pl.ld[bi], j.L, p->neumann, 1};
+      auto it = ctx->tune.find(key);
+      pl.G[bi] = (it != ctx->tune.end()) ? it->second : heuristic_g(pl.ld[bi], pl.nmax[bi], refine);
+    }
+  pl.ld[b.nb - 1] = 32;  // targets larger than every class: reported as unsupported
+  pl.nmax[b.nb - 1] = 1;
+  pl.G[b.nb - 1] = 1;
+  for (int bi = 0; bi < b.nb; ++bi) {
+    if (pl.G[bi] == 0) {  // no variant fits: send these targets to the unsupported bucket
+      pl.G[bi] = 1;
+      pl.ld[bi] = 32;
+      pl.nmax[bi] = 1;
+    }
+    b.gpb[bi] = 4 / pl.G[bi];
+  }
+  b.counts = arena_alloc<int32_t>(ctx, b.nb);
+  b.fill = arena_alloc<int32_t>(ctx, b.nb);
+  b.bucket_of = arena_alloc<int32_t>(ctx, std::max<int64_t>(j.n_tgt, 1));
+  b.bucket_start = arena_alloc<int32_t>(ctx, b.nb + 1);
+  b.task_start = arena_alloc<int32_t>(ctx, b.nb + 1);
+  b.items = arena_alloc<int32_t>(ctx, std::max<int64_t>(j.n_tgt, 1));
+  int32_t* nsample = arena_alloc<int32_t>(ctx, 1);
+  auto release = [&]() {
+    for (void* q : {(void*)b.counts, (void*)b.fill, (void*)b.bucket_of, (void*)b.bucket_start, (void*)b.task_start,
+                    (void*)b.items, (void*)nsample})
+      ctx->arena.release(q);
+  };
+  if (!b.counts || !b.fill || !b.bucket_of || !b.bucket_start || !b.task_start || !b.items || !nsample) {
+    release();
+    return fail(ctx, GMLS_ENOMEM, "gmls_stencils: arena exhausted (bucketing)");
+  }
+  Launch L = ctx->launch();
+  cudaError_t e = launch_bucketing(L, b);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(ctx, e, "gmls_stencils bucketing");
+  }
+  // autotune buckets that have no cached choice (reads the bucket sizes once)
+  bool need = false;
+  for (int m = 1; m <= 4 && !need; ++m)
+    for (int rc = 0; rc < b.n_classes; ++rc) {
+      const TuneKey key{p->basis, dim, m, p->precision, b.class_rows[rc], j.L, p->neumann, 1};
+      if (!ctx->tune.count(key)) need = true;
+    }
+  if (need && ctx->autotune && !ctx->force_generic && !capturing(ctx)) {
+    std::vector<int32_t> cnt(b.nb), start(b.nb + 1);
+    cudaMemcpyAsync(cnt.data(), b.counts, sizeof(int32_t) * b.nb, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(start.data(), b.bucket_start, sizeof(int32_t) * (b.nb + 1), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    for (int m = 1; m <= 4; ++m)
+      for (int rc = 0; rc < b.n_classes; ++rc) {
+        const int bi = (m - 1) * b.n_classes + rc;
+        const TuneKey key{p->basis, dim, m, p->precision, b.class_rows[rc], j.L, p->neumann, 1};
+        if (ctx->tune.count(key) || cnt[bi] == 0) continue;
+        const int32_t ns = std::min<int32_t>(cnt[bi], 4096);
+        cudaMemcpyAsync(nsample, &ns, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+        StencilJob js = j;
+        js.items = b.items + start[bi];
+        js.n_items = nsample;
+        float best = 1e30f;
+        int choice = 0;
+        for (int G = 1; G <= 4; G *= 2) {
+          if ((size_t)(4 / G) * tile_bytes(pl.ld[bi], pl.nmax[bi], refine) > 227 * 1024) continue;
+          float ms = time_launch(ctx, [&]() {
+            if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
+            launch_single(ctx, js, G, pl.ld[bi], pl.nmax[bi], refine, counter, sms);
+          });
+          ctx->tune_log.push_back({key, G, ms});
+          if (ms < best) {
+            best = ms;
+            choice = G;
+          }
+        }
+        if (choice) {
+          ctx->tune[key] = choice;
+          pl.G[bi] = choice;
+          b.gpb[bi] = 4 / choice;
+        }
+      }
+    // block tasks depend on the chosen G: recompute the plan
+    e = launch_bucketing(L, b);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(ctx, e, "gmls_stencils bucketing");
+    }
+  }
+  pl.items = b.items;
+  pl.bucket_start = b.bucket_start;
+  pl.task_start = b.task_start;
+  pl.task_counter = counter;
+  const size_t smem = plan_smem(pl, refine);
+  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
+  if (e == cudaSuccess) e = launch_stencils(L, j, pl, refine, smem, sms * stencil_blocks_per_sm(refine, smem));
+  release();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_stencils bucketed launch");
+  return GMLS_OK;
+}
+
+static gmls_status plan_and_launch(gmls_ctx* ctx, const StencilJob& j0, const gmls_stencil_params* p, NbrObj& nb,
+                                   StencilObj& s, bool refine, int ld, int nmax, int sms) {
+  StencilJob j = j0;
+  int32_t* counter = arena_alloc<int32_t>(ctx, 2);
+  if (!counter) return fail(ctx, GMLS_ENOMEM, "gmls_stencils: arena exhausted");
+  const bool uniform = !p->degree_per_target && !nb.variable;
+  gmls_status rc = uniform ? launch_uniform(ctx, j, p, refine, ld, nmax, sms, counter)
+                           : launch_bucketed(ctx, j, p, refine, ld, sms, counter);
+  if (rc == GMLS_OK && refine) {
+    // FP64 redo of the targets the FP32 path handed back
+    StencilJob jf = j;
+    jf.items = s.fb_items;
+    jf.n_items = s.fb_count;
+    jf.fallback_run = 1;
+    const int gf = heuristic_g(ld, nmax, false);
+    if (gf) {
+      cudaError_t e = launch_single(ctx, jf, gf, ld, nmax, false, counter + 1, sms);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "gmls_stencils FP64 redo");
+    }
+  }
+  ctx->arena.release(counter);
+  return rc;
 }
 
 extern "C" {
@@ -258,8 +546,59 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
   if (!ctx) return GMLS_EINVAL;
   switch (option) {
     case GMLS_OPT_FORCE_GENERIC: ctx->force_generic = value != 0; return GMLS_OK;
+    case GMLS_OPT_AUTOTUNE: ctx->autotune = value != 0; return GMLS_OK;
+    case GMLS_OPT_CLEAR_TUNING:
+      ctx->tune.clear();
+      ctx->tune_log.clear();
+      return GMLS_OK;
     default: return fail(ctx, GMLS_EINVAL, "gmls_set_option: unknown option");
   }
+}
+
+gmls_status gmls_tune_info(gmls_ctx* ctx, int32_t index, int32_t* fields, float* ms) {
+  if (!ctx || !fields) return GMLS_EINVAL;
+  if (index < 0 || index >= (int32_t)ctx->tune_log.size()) return fail(ctx, GMLS_ENOTFOUND, "gmls_tune_info: no such record");
+  const TuneRecord& r = ctx->tune_log[index];
+  const int32_t v[9] = {r.key.basis, r.key.dim, r.key.degree, r.key.precision, r.key.ld, r.key.L, r.key.neumann,
+                        r.key.bucketed, r.variant};
+  for (int i = 0; i < 9; ++i) fields[i] = v[i];
+  if (ms) *ms = r.ms;
+  return GMLS_OK;
+}
+
+gmls_status gmls_capture_begin(gmls_ctx* ctx) {
+  if (!ctx) return GMLS_EINVAL;
+  CK(cudaSetDevice(ctx->device), "gmls_capture_begin");
+  if (!ctx->stream) return fail(ctx, GMLS_EINVAL, "gmls_capture_begin: the legacy default stream cannot be captured");
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed), "gmls_capture_begin");
+  return GMLS_OK;
+}
+
+gmls_status gmls_capture_end(gmls_ctx* ctx, int64_t* graph_id) {
+  if (!ctx || !graph_id) return GMLS_EINVAL;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamEndCapture(ctx->stream, &graph), "gmls_capture_end");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_capture_end instantiate");
+  Obj o;
+  o.kind = K_GRAPH;
+  o.exec = exec;
+  int64_t id = ctx->next_id++;
+  ctx->objs.emplace(id, std::move(o));
+  *graph_id = id;
+  return GMLS_OK;
+}
+
+gmls_status gmls_graph_launch(gmls_ctx* ctx, int64_t graph_id) {
+  if (!ctx) return GMLS_EINVAL;
+  auto it = ctx->objs.find(graph_id);
+  if (it == ctx->objs.end() || it->second.kind != K_GRAPH) return fail(ctx, GMLS_ENOTFOUND, "gmls_graph_launch: no such graph");
+  CK(cudaSetDevice(ctx->device), "gmls_graph_launch");
+  CK(cudaGraphLaunch(it->second.exec, ctx->stream), "gmls_graph_launch");
+  ctx->launches += 1;
+  return GMLS_OK;
 }
 
 gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches) {
@@ -345,6 +684,7 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
     return fail(ctx, GMLS_EINVAL, "gmls_neighbors: need mode KNN/RADIUS, 1 <= k <= 1024, eps_factor > 0");
   if (p->mode == GMLS_NBR_RADIUS && (p->cap < p->k || p->cap > kMaxK))
     return fail(ctx, GMLS_EINVAL, "gmls_neighbors: radius mode needs k <= cap <= 1024");
+  const bool variable = p->mode == GMLS_NBR_RADIUS || p->k_per_target;
   if (p->mode == GMLS_NBR_KNN && p->k > c.n)
     return fail(ctx, GMLS_EINVAL, "gmls_neighbors: k exceeds the number of particles");
   const int64_t nt = p->targets ? p->n_targets : c.n;
@@ -359,6 +699,7 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   nb.mode = p->mode;
   nb.k = p->k;
   nb.cap = p->mode == GMLS_NBR_RADIUS ? p->cap : p->k;
+  nb.variable = variable;
   nb.idx_cap = nt * (int64_t)nb.cap;
   nb.tgt = arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1));
   nb.off = arena_alloc<int64_t>(ctx, nt + 1);
@@ -366,21 +707,22 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   nb.eps = arena_alloc<double>(ctx, std::max<int64_t>(nt, 1));
   nb.status = arena_alloc<uint8_t>(ctx, std::max<int64_t>(nt, 1));
   double* hs = p->halfspace ? arena_alloc<double>(ctx, (size_t)nt * c.dim) : nullptr;
+  int32_t* kpt = p->k_per_target ? arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1)) : nullptr;
   int32_t* padded = nullptr;
   int32_t* cnt = nullptr;
   int64_t* scan_tmp = nullptr;
   int64_t scan_elems = 0;
-  if (p->mode == GMLS_NBR_RADIUS) {
+  if (variable) {
     padded = arena_alloc<int32_t>(ctx, std::max<int64_t>(nb.idx_cap, 1));
     cnt = arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1));
     scan_elems = scan_scratch_elems(nt);
     scan_tmp = arena_alloc<int64_t>(ctx, scan_elems);
   }
   bool oom = !nb.tgt || !nb.off || !nb.idx || !nb.eps || !nb.status || (p->halfspace && !hs) ||
-             (p->mode == GMLS_NBR_RADIUS && (!padded || !cnt || !scan_tmp));
+             (p->k_per_target && !kpt) || (variable && (!padded || !cnt || !scan_tmp));
   if (oom) {
     for (void* q : {(void*)nb.tgt, (void*)nb.off, (void*)nb.idx, (void*)nb.eps, (void*)nb.status, (void*)hs,
-                    (void*)padded, (void*)cnt, (void*)scan_tmp})
+                    (void*)kpt, (void*)padded, (void*)cnt, (void*)scan_tmp})
       ctx->arena.release(q);
     return fail(ctx, GMLS_ENOMEM, "gmls_neighbors: arena exhausted");
   }
@@ -390,6 +732,7 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   else
     CK(launch_fill_identity(L, nb.tgt, nt), "gmls_neighbors identity");
   if (hs) CK(copy_in(ctx, hs, p->halfspace, sizeof(double) * nt * c.dim), "gmls_neighbors copy halfspace");
+  if (kpt) CK(copy_in(ctx, kpt, p->k_per_target, sizeof(int32_t) * nt), "gmls_neighbors copy k");
   NbrQuery q;
   q.cloud = CloudDev{c.dim, c.n, c.x, c.xs, c.sorted, c.cell_start, c.grid, c.ncell};
   q.n_tgt = nt;
@@ -397,20 +740,22 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   q.halfspace = hs;
   q.mode = p->mode;
   q.k = p->k;
+  q.k_pt = kpt;
   q.cap = nb.cap;
   q.eps_factor = p->eps_factor;
-  q.out_idx = (p->mode == GMLS_NBR_RADIUS) ? padded : nb.idx;
+  q.out_idx = variable ? padded : nb.idx;
   q.out_cnt = cnt;
   q.out_eps = nb.eps;
   q.out_status = nb.status;
   CK(launch_nbr_query(L, q), "gmls_neighbors query");
-  if (p->mode == GMLS_NBR_KNN) {
+  if (!variable) {
     CK(launch_fill_offsets_fixed(L, nb.off, nt, p->k), "gmls_neighbors offsets");
   } else {
     CK(launch_scan_i64_from_i32(L, cnt, nb.off, nt, scan_tmp, scan_elems), "gmls_neighbors scan");
     CK(launch_compact_padded(L, padded, nb.cap, cnt, nb.off, nb.idx, nt), "gmls_neighbors compact");
   }
   ctx->arena.release(hs);
+  ctx->arena.release(kpt);
   ctx->arena.release(padded);
   ctx->arena.release(cnt);
   ctx->arena.release(scan_tmp);
@@ -597,59 +942,15 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.ld = ld;
   j.nmax = nmax;
 
-  // warps per target: the smallest of 1, 2, 4 that fits and keeps lanes busy
-  auto pick_g = [&](bool fp32) -> int {
-    int g0 = ld <= 64 ? 1 : (ld <= 192 ? 2 : 4);
-    for (int g = g0; g <= 4; g *= 2) {
-      j.warps_per_target = g;
-      if (stencil_smem_bytes(j, fp32) <= 227 * 1024) return g;
-    }
-    return 0;
-  };
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  Launch Lc = ctx->launch();
-  const int g_main = pick_g(refine);
-  if (!g_main) {
-    release_all();
-    return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this (k, basis, degree)");
-  }
-  j.warps_per_target = g_main;
-  auto grid_for = [&](bool fp32, int64_t items) -> int {
-    const size_t smem = stencil_smem_bytes(j, fp32);
-    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (228 * 1024) / (smem + 1024)));
-    int64_t groups = (int64_t)(128 / (32 * j.warps_per_target));
-    int64_t want = (items + groups - 1) / groups;
-    int64_t cap = (int64_t)dev_sms * per_sm;
-    return (int)std::max<int64_t>(1, std::min(want, cap));
-  };
-  if (refine) CK(cudaMemsetAsync(s.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
-  // the warp-per-target float-float kernel when this shape is instantiated
-  int mr = 0;
-  const bool fast = refine && !p->degree_per_target && (p->weight_power % 2 == 0) && !ctx->force_generic &&
-                    fast_path_available(p->basis, dim, p->degree, ld, &mr);
+  gmls_status rc = GMLS_OK;
   if (nt > 0) {
-    if (fast)
-      CK(launch_stencils_fast(Lc, j, mr, dev_sms), "gmls_stencils fast launch");
-    else
-      CK(launch_stencils(Lc, j, refine, grid_for(refine, nt)), "gmls_stencils launch");
-    if (refine) {
-      StencilJob jf = j;
-      jf.items = s.fb_items;
-      jf.n_items = s.fb_count;
-      jf.fallback_run = 1;
-      int gf = 0;
-      for (int g = (ld <= 64 ? 1 : (ld <= 192 ? 2 : 4)); g <= 4; g *= 2) {
-        jf.warps_per_target = g;
-        if (stencil_smem_bytes(jf, false) <= 227 * 1024) {
-          gf = g;
-          break;
-        }
-      }
-      if (gf) {
-        jf.warps_per_target = gf;
-        CK(launch_stencils(Lc, jf, false, dev_sms * 2), "gmls_stencils fallback launch");
-      }
+    rc = plan_and_launch(ctx, j, p, nb, s, refine, ld, nmax, dev_sms);
+    if (rc != GMLS_OK) {
+      ctx->arena.release(deg);
+      release_all();
+      return rc;
     }
   }
   ctx->arena.release(deg);
@@ -668,10 +969,12 @@ static int find_out(const StencilObj& s, int fn) {
 
 // total neighbour entries (reads the device offset when the lists are variable)
 static gmls_status nbr_total(gmls_ctx* ctx, const NbrObj& nb, int64_t* total) {
-  if (nb.mode == GMLS_NBR_KNN) {
+  if (!nb.variable) {
     *total = nb.n_tgt * (int64_t)nb.k;
     return GMLS_OK;
   }
+  if (capturing(ctx))
+    return fail(ctx, GMLS_EBUSY, "the nonzero count of radius-mode lists is not readable during stream capture");
   int64_t v = 0;
   CK(cudaMemcpyAsync(&v, nb.off + nb.n_tgt, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream), "offset read");
   CK(cudaStreamSynchronize(ctx->stream), "offset read");
@@ -807,7 +1110,9 @@ gmls_status gmls_release(gmls_ctx* ctx, int64_t id) {
   if (it == ctx->objs.end()) return fail(ctx, GMLS_ENOTFOUND, "gmls_release: no such handle");
   Obj& o = it->second;
   Arena& a = ctx->arena;
-  if (o.kind == K_CLOUD) {
+  if (o.kind == K_GRAPH) {
+    cudaGraphExecDestroy(o.exec);
+  } else if (o.kind == K_CLOUD) {
     if (o.c.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: cloud has live neighbour handles");
     for (void* p : {(void*)o.c.x, (void*)o.c.xh, (void*)o.c.xl, (void*)o.c.normals, (void*)o.c.bflag,
                     (void*)o.c.xs, (void*)o.c.sorted, (void*)o.c.cell_start, (void*)o.c.grid})

@@ -95,6 +95,13 @@ __device__ __forceinline__ ff sqrt_ff(ff a) {
 
 __device__ __forceinline__ double to_double(ff a) { return (double)a.h + (double)a.l; }
 
+// (a_h + a_l) - (b_h + b_l) for coordinates stored as float pairs
+__device__ __forceinline__ ff sub_pair(float ah, float al, float bh, float bl) {
+  ff s = two_sum(ah, -bh);
+  float e = __fadd_rn(s.l, __fsub_rn(al, bl));
+  return quick_two_sum(s.h, e);
+}
+
 // Compensated accumulation of products (Ogita-Rump-Oishi Dot2 with
 // float-float factors): acc_h + acc_l tracks sum(a_i * b_i) to about 2^-48.
 struct Dot2 {

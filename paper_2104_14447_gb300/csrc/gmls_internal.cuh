@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -85,6 +86,7 @@ struct NbrQuery {
   const double* halfspace;   // [n_tgt][dim] or NULL
   int mode;                  // GMLS_NBR_*
   int k;
+  const int32_t* k_pt;       // per-target k or NULL
   int cap;                   // radius mode
   double eps_factor;
   // outputs
@@ -155,11 +157,47 @@ struct StencilJob {
   int warps_per_target;    // 1, 2 or 4 (block = 128 threads)
 };
 
-size_t stencil_smem_bytes(const StencilJob& j, bool fp32_refine);
+constexpr int kMaxBuckets = 48;
+
+// How one launch of the shared-memory stencil kernel walks its targets.
+struct BatchPlan {
+  int single;                   // 1: one bucket over job.items (or all targets)
+  int nb;                       // buckets
+  const int32_t* items;         // bucket-sorted target ordinals (bucketed mode)
+  const int32_t* bucket_start;  // [nb + 1]
+  const int32_t* task_start;    // [nb + 1] block tasks
+  int32_t* task_counter;        // zeroed before the launch
+  int G[kMaxBuckets];           // warps per target
+  int ld[kMaxBuckets];          // tile rows
+  int nmax[kMaxBuckets];        // tile columns
+};
+
+struct BucketJob {
+  int64_t n_tgt;
+  const int64_t* off;
+  const int8_t* degree_pt;
+  int degree;
+  int nc;
+  int n_classes;
+  int class_rows[16];
+  int nb;                       // n_classes * 4 + 1 (the last: too large)
+  int gpb[kMaxBuckets];         // targets per block task
+  int32_t* counts;
+  int32_t* fill;
+  int32_t* bucket_of;
+  int32_t* bucket_start;
+  int32_t* task_start;
+  int32_t* items;
+};
+
+size_t tile_bytes(int ld, int nmax, bool fp32_refine);
+int stencil_blocks_per_sm(bool fp32_refine, size_t smem);
+cudaError_t launch_stencils(const Launch& L, const StencilJob& j, const BatchPlan& plan, bool fp32_refine,
+                            size_t smem, int grid_blocks);
+cudaError_t launch_bucketing(const Launch& L, const BucketJob& b);
 bool fast_path_available(int kind, int dim, int deg, int rows, int* mr_out);
 cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int sms);
 cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count);
-cudaError_t launch_stencils(const Launch& L, const StencilJob& j, bool fp32_refine, int grid_blocks);
 
 // -------------------------------------------------------------------- CSR
 struct CsrJob {

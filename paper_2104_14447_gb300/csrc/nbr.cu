@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
       }
     }
     uint8_t st = GMLS_T_OK;
-    double R = pow(1.5 * q.k / (dens * ball), 1.0 / dim);
+    int kq = q.k_pt ? q.k_pt[to] : q.k;  // per-target k is clamped to 1..cap
+    kq = kq < 1 ? 1 : (kq > q.cap ? q.cap : kq);
+    double R = pow(1.5 * kq / (dens * ball), 1.0 / dim);
     int count = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
       count = gather_candidates(cl, g, xT, R, __dmul_rn(R, R), use_hs, nrm, wb);
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
         R *= 0.75;
         continue;
       }
-      if (count >= q.k) break;
+      if (count >= kq) break;
       if (R > 2.0 * span + 1.0) break;  // whole cloud inside: too few exist
       R *= 1.6;
     }
@@ -420,16 +422,19 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
       st |= GMLS_T_OVERFLOW;
       count = kNbrCap;
     }
-    if (count < q.k) st |= GMLS_T_TOO_FEW_NEIGHBOURS;
+    if (count < kq) st |= GMLS_T_TOO_FEW_NEIGHBOURS;
     warp_sort_candidates(wb, count);
-    const int kk = count < q.k ? count : q.k;
+    const int kk = count < kq ? count : kq;
     double eps = 0.0;
-    if (kk == q.k) eps = __dmul_rn(q.eps_factor, __dsqrt_rn(wb.d2[q.k - 1]));
-    if (q.mode == GMLS_NBR_KNN) {
+    if (kk == kq) eps = __dmul_rn(q.eps_factor, __dsqrt_rn(wb.d2[kq - 1]));
+    if (q.mode == GMLS_NBR_KNN && !q.k_pt) {
       for (int i = lane; i < q.k; i += 32) q.out_idx[to * q.k + i] = (i < kk) ? wb.id[i] : -1;
+    } else if (q.mode == GMLS_NBR_KNN) {  // per-target k: padded rows, compacted later
+      for (int i = lane; i < kq; i += 32) q.out_idx[to * q.cap + i] = (i < kk) ? wb.id[i] : -1;
+      if (lane == 0) q.out_cnt[to] = kq;
     } else {
       int keep = 0;
-      if (kk == q.k) {
+      if (kk == kq) {
         __syncwarp();
         count = gather_candidates(cl, g, xT, eps, __dmul_rn(eps, eps), use_hs, nrm, wb);
         if (count > kNbrCap) {

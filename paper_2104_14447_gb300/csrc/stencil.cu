@@ -1,4 +1,4 @@
-// stencil.cu -- per-target GMLS stencils on the device.
+// stencil.cu -- per-target GMLS stencils, shared-memory tiles, any shape.
 //
 // For each target x_T with neighbours x_j (Sec. 2.1) and support eps:
 //   1. B = sqrt(W) P with P_{j,i} = p_i((x_j - x_T)/eps)  (Eqs. matrix-P,
@@ -9,21 +9,27 @@
 //   3. functional rows lambda_i = L(p_i)(x_T)  (Sec. 2.5);
 //   4. s = Q [R^{-T} lambda^T; 0], so that w = sqrt(W) s = W P (P^T W P)^{-1}
 //      lambda^T  (Eq. polynomial-approximation-derivative);
-//   5. optionally (FP32 path) iterative refinement of the augmented system
-//      [[I, B], [B^T, 0]] [s; -y] = [0; lambda^T] with FP64 residuals and FP32
-//      corrections (Bjorck's method); targets that do not converge are queued
-//      for the FP64 path;
+//   5. FP32 path: refinement of the augmented system [[I, B], [B^T, 0]]
+//      [s; -y] = [0; lambda^T] (Bjorck) with float-float residuals and FP32
+//      corrections; targets that miss the tolerance go to the FP64 redo list;
 //   6. Neumann targets (Sec. 2.3) first eliminate the constraint
 //      F^T c = h, F = grad p(x_T)^T n, with a reflector H_F: the least-squares
 //      problem runs on B H_F without the pivot column, and the coefficient of h
-//      is beta = (lambda~_piv - w^T p~_piv) / rho.
+//      is beta = (lambda~_piv - s^T p~_piv) / rho.
 //
-// One group of G warps (G = 1, 2 or 4; 128-thread blocks) owns one target at a
-// time; its tiles live in shared memory, column-major with leading dimension
-// ld.  The block loops over a work list (persistent).
+// Precision is a template pair (TQ, HP): (double, double) is the FP64 path;
+// (float, ff) factors in FP32 and keeps B, sqrt(W), lambda and the iterates
+// in float-float (ff.cuh) so that no FP64 instruction runs in the loop.
+//
+// The kernel is persistent and bucketed: the targets are grouped on the device
+// into buckets of equal (degree, row class); a block of 4 warps repeatedly
+// takes a "block task" (G warps per target, 4/G targets of one bucket) from a
+// global counter.  G and the tile shape (ld rows, nmax columns) are per bucket
+// (chosen by the host, or by the autotuner), so one launch covers every shape.
 #include <cuda_runtime.h>
 
 #include "basis_tables.cuh"
+#include "ff.cuh"
 #include "gmls_internal.cuh"
 
 namespace gmls {
@@ -32,47 +38,31 @@ constexpr int kBlock = 128;
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-struct Lay {
-  size_t A, B64, tau, dots, sw, lam, S, Y, Z, D, pt, misc, total;
-};
-
-__host__ __device__ inline Lay make_lay(int ld, int nmax, bool refine, int tqs) {
-  Lay l;
-  size_t o = 0;
-  l.A = o;
-  o += align16((size_t)nmax * ld * tqs);
-  l.B64 = o;
-  if (refine) o += align16((size_t)nmax * ld * 8);
-  l.tau = o;
-  o += align16((size_t)nmax * tqs);
-  l.dots = o;
-  o += align16((size_t)nmax * tqs);
-  l.sw = o;
-  o += align16((size_t)ld * 8);
-  l.lam = o;
-  o += align16((size_t)kMaxSolveRows * nmax * 8);
-  l.S = o;
-  o += align16((size_t)kMaxSolveRows * ld * 8);
-  l.Y = o;
-  o += align16((size_t)kMaxSolveRows * nmax * 8);
-  l.Z = o;
-  o += align16((size_t)kMaxSolveRows * ld * tqs);
-  l.D = o;
-  o += align16((size_t)kMaxSolveRows * nmax * tqs);
-  l.pt = o;
-  o += align16((size_t)ld * 8);
-  l.misc = o;
-  o += 256;
-  l.total = o;
-  return l;
-}
+// ------------------------------------------------------- precision helpers
+__device__ __forceinline__ double hp_from(double v, double) { return v; }
+__device__ __forceinline__ ff hp_from(double v, ff) { return ff(v); }
+__device__ __forceinline__ double hp_to_double(double v) { return v; }
+__device__ __forceinline__ double hp_to_double(ff v) { return to_double(v); }
+__device__ __forceinline__ double hp_hi_d(double v) { return v; }
+__device__ __forceinline__ float hp_hi_f(ff v) { return v.h; }
+__device__ __forceinline__ double hp_recip(double v) { return 1.0 / v; }
+__device__ __forceinline__ ff hp_recip(ff v) { return recip(v); }
+__device__ __forceinline__ double hp_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ ff hp_sqrt(ff v) { return sqrt_ff(v); }
+__device__ __forceinline__ double hp_add_f(double a, double b) { return a + b; }
+__device__ __forceinline__ ff hp_add_f(ff a, float b) { return add_f(a, b); }
+__device__ __forceinline__ bool hp_pos(double v) { return v > 0.0; }
+__device__ __forceinline__ bool hp_pos(ff v) { return v.h > 0.0f; }
+__device__ __forceinline__ double hp_zero(double) { return 0.0; }
+__device__ __forceinline__ ff hp_zero(ff) { return ff(0.0f, 0.0f); }
+__device__ __forceinline__ double hp_one(double) { return 1.0; }
+__device__ __forceinline__ ff hp_one(ff) { return ff(1.0f, 0.0f); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -80,6 +70,17 @@ __device__ __forceinline__ T warp_max(T v) {
     v = u > v ? u : v;
   }
   return v;
+}
+// float-float all-reduce across the warp
+__device__ __forceinline__ ff warp_sum_ff(float h, float l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    const ff s = two_sum(h, oh);
+    h = s.h;
+    l = __fadd_rn(l, __fadd_rn(ol, s.l));
+  }
+  return quick_two_sum(h, l);
 }
 
 __device__ __forceinline__ void group_sync(int gid, int nthr) {
@@ -89,39 +90,71 @@ __device__ __forceinline__ void group_sync(int gid, int nthr) {
     asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(nthr) : "memory");
 }
 
-template <typename T>
-struct Eps;
-template <>
-struct Eps<float> {
-  static constexpr double u = 5.9604644775390625e-08;
-};
-template <>
-struct Eps<double> {
-  static constexpr double u = 1.1102230246251565e-16;
-};
-
 struct Group {
   int gid, nthr, tid, wg, G, lane;
 };
 
+// ------------------------------------------------------------ tile layout
+struct Lay {
+  size_t A, HB, tau, dots, sw, lam, S, Y, Z, D, pt, misc, total;
+};
+
+// tqs: bytes of TQ; hps: bytes of HP; hb: separate high-precision tile (FP32 path)
+__host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool hb) {
+  Lay l;
+  size_t o = 0;
+  l.A = o;
+  o += align16((size_t)nmax * ld * tqs);
+  l.HB = o;
+  if (hb) o += align16((size_t)nmax * ld * hps);
+  l.tau = o;
+  o += align16((size_t)nmax * tqs);
+  l.dots = o;
+  o += align16((size_t)nmax * tqs);
+  l.sw = o;
+  o += align16((size_t)ld * hps);
+  l.lam = o;
+  o += align16((size_t)kMaxSolveRows * nmax * hps);
+  l.S = o;
+  o += align16((size_t)kMaxSolveRows * ld * hps);
+  l.Y = o;
+  o += align16((size_t)kMaxSolveRows * nmax * hps);
+  l.Z = o;
+  o += align16((size_t)kMaxSolveRows * ld * tqs);
+  l.D = o;
+  o += align16((size_t)kMaxSolveRows * nmax * tqs);
+  l.pt = o;
+  o += align16((size_t)ld * hps);
+  l.misc = o;
+  o += 256;
+  l.total = o;
+  return l;
+}
+
+size_t tile_bytes(int ld, int nmax, bool fp32_refine) {
+  return fp32_refine ? make_lay(ld, nmax, 4, 8, true).total : make_lay(ld, nmax, 8, 8, false).total;
+}
+
 // ---------------------------------------------------------------- QR (in TQ)
 // Householder QR of the M x n tile A (column-major, leading dimension ld).
 // Column k below the diagonal keeps v_k (v_k[k] = 1 implied), tau[k] its scale.
+// Per column: warp 0 forms the reflector; then each warp takes whole trailing
+// columns, computing the dot product and applying the update in one pass.
 template <typename TQ>
-__device__ void tile_qr(const Group& g, TQ* A, int ld, int M, int n, TQ* tau, TQ* dots) {
+__device__ void tile_qr(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
   for (int k = 0; k < n; ++k) {
     TQ* a = A + (size_t)k * ld;
     if (g.wg == 0) {
       TQ sig = 0;
       for (int r = k + 1 + g.lane; r < M; r += 32) sig += a[r] * a[r];
       sig = warp_sum(sig);
-      TQ alpha = a[k];
+      const TQ alpha = a[k];
       if (sig == TQ(0)) {
         if (g.lane == 0) tau[k] = 0;
       } else {
-        TQ nrm = sqrt(alpha * alpha + sig);
-        TQ beta = alpha >= TQ(0) ? -nrm : nrm;
-        TQ scale = TQ(1) / (alpha - beta);
+        const TQ nrm = sqrt(alpha * alpha + sig);
+        const TQ beta = alpha >= TQ(0) ? -nrm : nrm;
+        const TQ scale = TQ(1) / (alpha - beta);
         for (int r = k + 1 + g.lane; r < M; r += 32) a[r] *= scale;
         __syncwarp();
         if (g.lane == 0) {
@@ -134,20 +167,12 @@ __device__ void tile_qr(const Group& g, TQ* A, int ld, int M, int n, TQ* tau, TQ
     const TQ tk = tau[k];
     if (tk != TQ(0) && k + 1 < n) {
       for (int jc = k + 1 + g.wg; jc < n; jc += g.G) {
-        const TQ* aj = A + (size_t)jc * ld;
+        TQ* aj = A + (size_t)jc * ld;
         TQ s = (g.lane == 0) ? aj[k] : TQ(0);
         for (int r = k + 1 + g.lane; r < M; r += 32) s += a[r] * aj[r];
-        s = warp_sum(s);
-        if (g.lane == 0) dots[jc] = s * tk;
-      }
-      group_sync(g.gid, g.nthr);
-      const int rows = M - k;
-      const int total = (n - k - 1) * rows;
-      for (int e = g.tid; e < total; e += g.nthr) {
-        const int jc = k + 1 + e / rows;
-        const int r = k + e % rows;
-        const TQ v = (r == k) ? TQ(1) : a[r];
-        A[(size_t)jc * ld + r] -= dots[jc] * v;
+        s = warp_sum(s) * tk;
+        for (int r = k + 1 + g.lane; r < M; r += 32) aj[r] -= s * a[r];
+        if (g.lane == 0) aj[k] -= s;
       }
       group_sync(g.gid, g.nthr);
     }
@@ -207,333 +232,470 @@ __device__ void apply_q(const Group& g, const TQ* A, int ld, int M, int n, const
   }
 }
 
-template <typename TQ, bool REFINE>
-__global__ void __launch_bounds__(kBlock) stencil_kernel(StencilJob j) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Group g;
-  g.G = j.warps_per_target;
-  g.nthr = 32 * g.G;
-  g.gid = (threadIdx.x >> 5) / g.G;
-  g.wg = (threadIdx.x >> 5) % g.G;
-  g.tid = threadIdx.x % g.nthr;
-  g.lane = threadIdx.x & 31;
-  const int groups_per_block = kBlock / g.nthr;
-  const Lay lay = make_lay(j.ld, j.nmax, REFINE, (int)sizeof(TQ));
-  unsigned char* base = smem + (size_t)g.gid * lay.total;
+// per-row offset of neighbour q from the target, in HP, and |x_j - x_T|^2
+__device__ __forceinline__ void offsets(const StencilJob& j, int64_t t, int32_t jj, double* dx) {
+  for (int c = 0; c < j.dim; ++c) dx[c] = j.x[c * j.n + jj] - j.x[c * j.n + t];
+}
+__device__ __forceinline__ void offsets(const StencilJob& j, int64_t t, int32_t jj, ff* dx) {
+  for (int c = 0; c < j.dim; ++c)
+    dx[c] = sub_pair(j.xh[c * j.n + jj], j.xl[c * j.n + jj], j.xh[c * j.n + t], j.xl[c * j.n + t]);
+}
+
+// sqrt(W) = u^(p/2), u = 1 - r/eps > 0
+__device__ __forceinline__ double sqrt_weight(double u, const StencilJob& j) {
+  return j.wpow == 4.0 ? u * u : pow(u, 0.5 * j.wpow);
+}
+__device__ __forceinline__ ff sqrt_weight(ff u, const StencilJob& j) {
+  ff s = (j.wpow_half * 2 == (int)j.wpow) ? u : sqrt_ff(u);
+  const int reps = (j.wpow_half * 2 == (int)j.wpow) ? j.wpow_half - 1 : j.wpow_half;
+  const ff base = u;
+  for (int p = 0; p < reps; ++p) s = s * base;
+  return s;
+}
+
+// ------------------------------------------------------------ one target
+template <typename TQ, typename HP, bool REFINE>
+__device__ void process_target(const StencilJob& j, const Group& g, unsigned char* base, int ld, int nmax,
+                               int64_t to) {
+  const Lay lay = make_lay(ld, nmax, (int)sizeof(TQ), (int)sizeof(HP), REFINE);
   TQ* A = reinterpret_cast<TQ*>(base + lay.A);
-  double* B64 = REFINE ? reinterpret_cast<double*>(base + lay.B64) : nullptr;
+  HP* HB = REFINE ? reinterpret_cast<HP*>(base + lay.HB) : reinterpret_cast<HP*>(base + lay.A);
   TQ* tau = reinterpret_cast<TQ*>(base + lay.tau);
-  TQ* dots = reinterpret_cast<TQ*>(base + lay.dots);
-  double* sw = reinterpret_cast<double*>(base + lay.sw);
-  double* lam = reinterpret_cast<double*>(base + lay.lam);
-  double* S = reinterpret_cast<double*>(base + lay.S);
-  double* Y = reinterpret_cast<double*>(base + lay.Y);
+  HP* sw = reinterpret_cast<HP*>(base + lay.sw);
+  HP* lam = reinterpret_cast<HP*>(base + lay.lam);
+  HP* S = reinterpret_cast<HP*>(base + lay.S);
+  HP* Y = reinterpret_cast<HP*>(base + lay.Y);
   TQ* Z = reinterpret_cast<TQ*>(base + lay.Z);
   TQ* D = reinterpret_cast<TQ*>(base + lay.D);
-  double* pt = reinterpret_cast<double*>(base + lay.pt);
-  double* misc = reinterpret_cast<double*>(base + lay.misc);  // [0] rho, [1..L] lambda~_piv, [8] flags
-  int* imisc = reinterpret_cast<int*>(misc + 8);
+  HP* pt = reinterpret_cast<HP*>(base + lay.pt);
+  HP* hmisc = reinterpret_cast<HP*>(base + lay.misc);  // [0] rho, [1..L] lambda~_piv
+  double* dmisc = reinterpret_cast<double*>(base + lay.misc + 128);  // [0..7] reductions
+  int* imisc = reinterpret_cast<int*>(base + lay.misc + 192);
+  const HP hz = hp_zero(HP());
 
-  const int ld = j.ld, nmax = j.nmax, L = j.L, dim = j.dim, nc = j.nc;
-  const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
+  const int L = j.L, dim = j.dim, nc = j.nc;
+  const int64_t t = j.tgt[to];
+  const int64_t o0 = j.off[to];
+  const int k = (int)(j.off[to + 1] - o0);
+  const int32_t* nbr = j.idx + o0;
+  const double eps = j.eps[to];
+  const int m = j.degree_pt ? (int)j.degree_pt[to] : j.degree;
+  const int nb = gmls_gen::basis_size(j.kind, dim, m);
+  const int M = k * nc;
+  const bool neu = j.neumann && j.bflag && j.bflag[t] && j.normals && j.kind == GMLS_BASIS_SCALAR;
+  const int n = neu ? nb - 1 : nb;
+  uint8_t st = j.nbr_status ? j.nbr_status[to] : 0;
+  if (j.fallback_run)  // FP64 redo of an FP32 target: keep why it was redone
+    st |= GMLS_T_FP64_FALLBACK | (j.status[to] & (GMLS_T_ILL_CONDITIONED | GMLS_T_REFINE_NOT_CONVERGED));
+  bool skip = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || nb <= 0 || M > ld || nb > nmax || !(eps > 0.0);
+  if (!(st & GMLS_T_TOO_FEW_NEIGHBOURS) && k > 0 && (M > ld || nb > nmax)) st |= GMLS_T_UNSUPPORTED;
+  if (!skip && M < n) {
+    st |= GMLS_T_RANK_DEFICIENT;
+    skip = true;
+  }
+  bool redo = false;
+  int used_iters = 0;
 
-  for (int64_t it = (int64_t)blockIdx.x * groups_per_block + g.gid; it < n_items;
-       it += (int64_t)gridDim.x * groups_per_block) {
-    const int64_t to = j.items ? (int64_t)j.items[it] : it;
-    const int64_t t = j.tgt[to];
-    const int64_t o0 = j.off[to];
-    const int k = (int)(j.off[to + 1] - o0);
-    const int32_t* nbr = j.idx + o0;
-    const double eps = j.eps[to];
-    const int m = j.degree_pt ? (int)j.degree_pt[to] : j.degree;
-    const int nb = gmls_gen::basis_size(j.kind, dim, m);
-    const int M = k * nc;
-    const bool neu = j.neumann && j.bflag && j.bflag[t] && j.normals && j.kind == GMLS_BASIS_SCALAR;
-    const int n = neu ? nb - 1 : nb;
-    uint8_t st = j.nbr_status ? j.nbr_status[to] : 0;
-    if (j.fallback_run)  // FP64 redo of an FP32 target: keep why it was redone
-      st |= GMLS_T_FP64_FALLBACK | (j.status[to] & (GMLS_T_ILL_CONDITIONED | GMLS_T_REFINE_NOT_CONVERGED));
-    bool skip = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || nb <= 0 || M > ld || nb > nmax || !(eps > 0.0);
-    if (!skip && M < n) {
-      st |= GMLS_T_RANK_DEFICIENT;
-      skip = true;
+  if (!skip) {
+    const HP heps = hp_from(eps, HP());
+    const HP inv_eps = hp_recip(heps);
+    // ---- 1. sqrt(W) P in HP, rows (neighbour, component)
+    for (int q = g.tid; q < k; q += g.nthr) {
+      HP dx[3] = {hz, hz, hz}, xi[3] = {hz, hz, hz};
+      offsets(j, t, nbr[q], dx);
+      HP r2 = hz;
+      for (int c = 0; c < dim; ++c) {
+        xi[c] = dx[c] * inv_eps;
+        r2 = r2 + dx[c] * dx[c];
+      }
+      const HP u = hp_one(HP()) - hp_sqrt(r2) * inv_eps;
+      const HP s = hp_pos(u) ? sqrt_weight(u, j) : hz;
+      gmls_gen::eval_basis<HP>(j.kind, dim, m, xi, HB + q * nc, ld, s);
+      for (int c = 0; c < nc; ++c) sw[q * nc + c] = s;
     }
-    const double inv_eps = skip ? 0.0 : 1.0 / eps;
+    // ---- 3. functional rows lambda (before Neumann)
+    for (int e = g.tid; e < L * nb; e += g.nthr) {
+      const int l = e / nb, i = e % nb;
+      HP f = hp_from(gmls_gen::lam_coef(j.kind, dim, m, j.lam_fn[l], j.lam_row[l], i), HP());
+      for (int p = 0; p < j.lam_order[l]; ++p) f = f * inv_eps;
+      lam[l * nmax + i] = f;
+    }
+    group_sync(g.gid, g.nthr);
 
-    if (!skip) {
-      // ---- 1. sqrt(W) P, rows (neighbour, component)
-      double* Bd = REFINE ? B64 : reinterpret_cast<double*>(A);
-      double xT[3] = {0.0, 0.0, 0.0};
-      for (int c = 0; c < dim; ++c) xT[c] = j.x[c * j.n + t];
-      for (int q = g.tid; q < k; q += g.nthr) {
-        const int32_t jj = nbr[q];
-        double xi[3] = {0.0, 0.0, 0.0};
-        double r2 = 0.0;
-        for (int c = 0; c < dim; ++c) {
-          double dx = j.x[c * j.n + jj] - xT[c];
-          xi[c] = dx * inv_eps;
-          r2 += dx * dx;
-        }
-        const double u = 1.0 - sqrt(r2) * inv_eps;
-        const double s = (u > 0.0) ? (j.wpow == 4.0 ? u * u : pow(u, 0.5 * j.wpow)) : 0.0;
-        gmls_gen::eval_basis<double>(j.kind, dim, m, xi, Bd + q * nc, ld, s);
-        for (int c = 0; c < nc; ++c) sw[q * nc + c] = s;
+    // ---- 6. Neumann: reflect the linear columns (indices 1..dim), move the
+    //         pivot column to the end, and keep it aside as p~
+    if (neu) {
+      double nvd[3] = {0.0, 0.0, 0.0};
+      int piv = 0;
+      for (int c = 0; c < dim; ++c) {
+        nvd[c] = j.normals[c * j.n + t];
+        if (fabs(nvd[c]) > fabs(nvd[piv])) piv = c;
       }
-      // ---- 3. functional rows lambda (before Neumann)
-      for (int e = g.tid; e < L * nb; e += g.nthr) {
-        const int l = e / nb, i = e % nb;
-        double f = 1.0;
-        for (int p = 0; p < j.lam_order[l]; ++p) f *= inv_eps;
-        lam[l * nmax + i] = gmls_gen::lam_coef(j.kind, dim, m, j.lam_fn[l], j.lam_row[l], i) * f;
+      HP v[3] = {hz, hz, hz}, fn2 = hz;
+      for (int c = 0; c < dim; ++c) {
+        v[c] = hp_from(nvd[c], HP()) * inv_eps;  // F restricted to the linear monomials
+        fn2 = fn2 + v[c] * v[c];
       }
+      const HP fn = hp_sqrt(fn2);
+      const HP rho = nvd[piv] >= 0.0 ? hz - fn : fn;
+      v[piv] = v[piv] - rho;  // v = F - rho e_piv
+      HP vv = hz;
+      for (int c = 0; c < dim; ++c) vv = vv + v[c] * v[c];
+      const HP two_vv = hp_from(2.0, HP()) * hp_recip(vv);
+      for (int r = g.tid; r < M; r += g.nthr) {
+        HP d = hz;
+        for (int c = 0; c < dim; ++c) d = d + HB[(size_t)(1 + c) * ld + r] * v[c];
+        d = d * two_vv;
+        for (int c = 0; c < dim; ++c) HB[(size_t)(1 + c) * ld + r] = HB[(size_t)(1 + c) * ld + r] - d * v[c];
+        const HP pc = HB[(size_t)(1 + piv) * ld + r];
+        HB[(size_t)(1 + piv) * ld + r] = HB[(size_t)(nb - 1) * ld + r];
+        HB[(size_t)(nb - 1) * ld + r] = pc;
+        pt[r] = pc;
+      }
+      if (g.tid < L) {
+        const int l = g.tid;
+        HP* ll = lam + l * nmax;
+        HP d = hz;
+        for (int c = 0; c < dim; ++c) d = d + ll[1 + c] * v[c];
+        d = d * two_vv;
+        for (int c = 0; c < dim; ++c) ll[1 + c] = ll[1 + c] - d * v[c];
+        const HP lp = ll[1 + piv];
+        ll[1 + piv] = ll[nb - 1];
+        ll[nb - 1] = lp;
+        hmisc[1 + l] = lp;
+      }
+      if (g.tid == 0) hmisc[0] = rho;
       group_sync(g.gid, g.nthr);
+    }
 
-      // ---- 6. Neumann: reflect the linear columns (indices 1..dim), move the
-      //         pivot column to the end, and keep it aside as p~
-      if (neu) {
-        double nv[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0};
-        double fn = 0.0;
-        int piv = 0;
-        for (int c = 0; c < dim; ++c) {
-          nv[c] = j.normals[c * j.n + t];
-          fn += nv[c] * nv[c];
-          if (fabs(nv[c]) > fabs(nv[piv])) piv = c;
+    if (REFINE) {  // FP32 working copy of the tile
+      for (int i = 0; i < n; ++i)
+        for (int r = g.tid; r < M; r += g.nthr) A[(size_t)i * ld + r] = (TQ)hp_hi_f(reinterpret_cast<ff*>(HB)[(size_t)i * ld + r]);
+      group_sync(g.gid, g.nthr);
+    }
+
+    // ---- 2. QR
+    tile_qr<TQ>(g, A, ld, M, n, tau);
+    if (g.wg == 0) {
+      TQ rmax = 0, rmin = TQ(3.0e38);
+      for (int i = g.lane; i < n; i += 32) {
+        TQ r = fabs(A[(size_t)i * ld + i]);
+        rmax = r > rmax ? r : rmax;
+        rmin = r < rmin ? r : rmin;
+      }
+      rmax = warp_max(rmax);
+      rmin = -warp_max(-rmin);
+      if (g.lane == 0) {
+        int fl = 0;
+        // rank deficiency is judged against FP64 roundoff (a property of the
+        // problem); an FP32 factor with a large ratio is caught as ill-conditioned
+        if (!((double)rmin > 64.0 * n * 1.1102230246251565e-16 * (double)rmax)) fl |= GMLS_T_RANK_DEFICIENT;
+        if (!((double)rmin * 1e6 >= (double)rmax)) fl |= GMLS_T_ILL_CONDITIONED;
+        imisc[0] = fl;
+      }
+    }
+    group_sync(g.gid, g.nthr);
+    st |= (uint8_t)imisc[0];
+
+    // ---- 4. s = Q [R^{-T} lambda; 0]
+    for (int e = g.tid; e < L * n; e += g.nthr) D[(e / n) * nmax + e % n] = (TQ)hp_to_double(lam[(e / n) * nmax + e % n]);
+    group_sync(g.gid, g.nthr);
+    solve_rt<TQ, TQ>(g, A, ld, n, L, nmax, D, D);
+    group_sync(g.gid, g.nthr);
+    for (int e = g.tid; e < L * M; e += g.nthr) {
+      const int l = e / M, r = e % M;
+      Z[(size_t)l * ld + r] = (r < n) ? D[l * nmax + r] : TQ(0);
+    }
+    group_sync(g.gid, g.nthr);
+    apply_q<TQ, false>(g, A, ld, M, n, tau, L, Z);
+    group_sync(g.gid, g.nthr);
+    for (int e = g.tid; e < L * M; e += g.nthr) {
+      const int l = e / M, r = e % M;
+      S[(size_t)l * ld + r] = hp_from((double)Z[(size_t)l * ld + r], HP());
+    }
+    if (REFINE) {
+      ff* B = reinterpret_cast<ff*>(HB);
+      ff* Sf = reinterpret_cast<ff*>(S);
+      ff* Yf = reinterpret_cast<ff*>(Y);
+      ff* lamf = reinterpret_cast<ff*>(lam);
+      // y = R^{-1} R^{-T} lambda (the least-squares coefficients)
+      solve_r<TQ>(g, A, ld, n, L, nmax, D);
+      group_sync(g.gid, g.nthr);
+      for (int e = g.tid; e < L * n; e += g.nthr) Yf[(e / n) * nmax + e % n] = ff((float)D[(e / n) * nmax + e % n], 0.f);
+      group_sync(g.gid, g.nthr);
+      bool conv = false;
+      float prev = 0.0f;
+      const bool ill = (st & GMLS_T_ILL_CONDITIONED) != 0;  // ill-conditioned: straight to FP64
+      for (int iter = 0; iter < j.max_refine && !ill; ++iter) {
+        // f = B y - s (into Z), compensated float-float
+        for (int e = g.tid; e < L * M; e += g.nthr) {
+          const int l = e / M, r = e % M;
+          Dot2 acc;
+          acc.init(-Sf[(size_t)l * ld + r]);
+          const ff* yl = Yf + l * nmax;
+          for (int i = 0; i < n; ++i) acc.add_prod(B[(size_t)i * ld + r], yl[i]);
+          Z[(size_t)l * ld + r] = (TQ)__fadd_rn(acc.h, acc.l);
         }
-        fn = sqrt(fn) * inv_eps;
-        const double rho = nv[piv] >= 0.0 ? -fn : fn;
-        double vv = 0.0;
-        for (int c = 0; c < dim; ++c) {
-          v[c] = nv[c] * inv_eps - (c == piv ? rho : 0.0);
-          vv += v[c] * v[c];
+        // g = lambda - B^T s (into D), one warp per (l, i)
+        for (int p = g.wg; p < L * n; p += g.G) {
+          const int l = p / n, i = p % n;
+          const ff* bi = B + (size_t)i * ld;
+          const ff* sl = Sf + (size_t)l * ld;
+          Dot2 acc;
+          for (int r = g.lane; r < M; r += 32) acc.add_prod(-bi[r], sl[r]);
+          const ff tot = warp_sum_ff(acc.h, acc.l) + lamf[l * nmax + i];
+          if (g.lane == 0) D[l * nmax + i] = (TQ)__fadd_rn(tot.h, tot.l);
         }
-        const double two_vv = 2.0 / vv;
-        for (int r = g.tid; r < M; r += g.nthr) {
-          double d = 0.0;
-          for (int c = 0; c < dim; ++c) d += Bd[(size_t)(1 + c) * ld + r] * v[c];
-          d *= two_vv;
-          for (int c = 0; c < dim; ++c) Bd[(size_t)(1 + c) * ld + r] -= d * v[c];
-          // swap pivot column with the last column
-          const double pc = Bd[(size_t)(1 + piv) * ld + r];
-          Bd[(size_t)(1 + piv) * ld + r] = Bd[(size_t)(nb - 1) * ld + r];
-          Bd[(size_t)(nb - 1) * ld + r] = pc;
-          pt[r] = pc;
-        }
-        if (g.tid < L) {
-          const int l = g.tid;
-          double* ll = lam + l * nmax;
-          double d = 0.0;
-          for (int c = 0; c < dim; ++c) d += ll[1 + c] * v[c];
-          d *= two_vv;
-          for (int c = 0; c < dim; ++c) ll[1 + c] -= d * v[c];
-          const double lp = ll[1 + piv];
-          ll[1 + piv] = ll[nb - 1];
-          ll[nb - 1] = lp;
-          misc[1 + l] = lp;
-        }
-        if (g.tid == 0) misc[0] = rho;
         group_sync(g.gid, g.nthr);
-      }
-
-      if (REFINE) {
-        for (int e = g.tid; e < n * M; e += g.nthr) {
-          const int i = e / M, r = e % M;
-          A[(size_t)i * ld + r] = (TQ)B64[(size_t)i * ld + r];
+        // d = Q^T f; a = R^{-T} g; dy = R^{-1}(a - d_1); ds = Q [a; d_2]
+        apply_q<TQ, true>(g, A, ld, M, n, tau, L, Z);
+        group_sync(g.gid, g.nthr);
+        solve_rt<TQ, TQ>(g, A, ld, n, L, nmax, D, D);
+        group_sync(g.gid, g.nthr);
+        for (int e = g.tid; e < L * n; e += g.nthr) {
+          const int l = e / n, i = e % n;
+          const TQ a = D[l * nmax + i];
+          const TQ d1 = Z[(size_t)l * ld + i];
+          D[l * nmax + i] = a - d1;  // becomes dy after the back substitution
+          Z[(size_t)l * ld + i] = a;
         }
         group_sync(g.gid, g.nthr);
-      }
-
-      // ---- 2. QR
-      tile_qr<TQ>(g, A, ld, M, n, tau, dots);
-      if (g.wg == 0) {
-        TQ rmax = 0, rmin = TQ(3.0e38);
-        for (int i = g.lane; i < n; i += 32) {
-          TQ r = fabs(A[(size_t)i * ld + i]);
-          rmax = r > rmax ? r : rmax;
-          rmin = r < rmin ? r : rmin;
-        }
-        rmax = warp_max(rmax);
-        rmin = -warp_max(-rmin);
-        if (g.lane == 0) {
-          int fl = 0;
-          // rank deficiency is judged against FP64 roundoff (a property of the
-          // problem); an FP32 factor with a large ratio is caught as ill-conditioned
-          if (!((double)rmin > 64.0 * n * Eps<double>::u * (double)rmax)) fl |= GMLS_T_RANK_DEFICIENT;
-          if (!((double)rmin * 1e6 >= (double)rmax)) fl |= GMLS_T_ILL_CONDITIONED;
-          imisc[0] = fl;
-        }
-      }
-      group_sync(g.gid, g.nthr);
-      st |= (uint8_t)imisc[0];
-
-      // ---- 4. s = Q [R^{-T} lambda; 0]
-      solve_rt<TQ, double>(g, A, ld, n, L, nmax, lam, D);
-      group_sync(g.gid, g.nthr);
-      for (int e = g.tid; e < L * M; e += g.nthr) {
-        const int l = e / M, r = e % M;
-        Z[(size_t)l * ld + r] = (r < n) ? D[l * nmax + r] : TQ(0);
-      }
-      group_sync(g.gid, g.nthr);
-      apply_q<TQ, false>(g, A, ld, M, n, tau, L, Z);
-      group_sync(g.gid, g.nthr);
-      for (int e = g.tid; e < L * M; e += g.nthr) {
-        const int l = e / M, r = e % M;
-        S[(size_t)l * ld + r] = (double)Z[(size_t)l * ld + r];
-      }
-      int used_iters = 0;
-      if (REFINE) {
-        // y = R^{-1} R^{-T} lambda (the least-squares coefficients), FP64 copy
         solve_r<TQ>(g, A, ld, n, L, nmax, D);
+        apply_q<TQ, false>(g, A, ld, M, n, tau, L, Z);
         group_sync(g.gid, g.nthr);
-        for (int e = g.tid; e < L * n; e += g.nthr) Y[(e / n) * nmax + e % n] = (double)D[(e / n) * nmax + e % n];
-        group_sync(g.gid, g.nthr);
-        bool conv = (st & GMLS_T_ILL_CONDITIONED) != 0;  // ill-conditioned: straight to FP64
-        double prev = 0.0;
-        const int maxit = j.max_refine;
-        for (int iter = 0; iter < maxit && !conv; ++iter) {
-          // f = B y - s (into Z), FP64 residual rounded to TQ for the correction
-          for (int e = g.tid; e < L * M; e += g.nthr) {
-            const int l = e / M, r = e % M;
-            double acc = -S[(size_t)l * ld + r];
-            const double* yl = Y + l * nmax;
-            for (int i = 0; i < n; ++i) acc = fma(B64[(size_t)i * ld + r], yl[i], acc);
-            Z[(size_t)l * ld + r] = (TQ)acc;
-          }
-          // g = lambda - B^T s (into D), one warp per (l, i)
-          for (int p = g.wg; p < L * n; p += g.G) {
-            const int l = p / n, i = p % n;
-            const double* bi = B64 + (size_t)i * ld;
-            const double* sl = S + (size_t)l * ld;
-            double acc = 0.0;
-            for (int r = g.lane; r < M; r += 32) acc = fma(bi[r], sl[r], acc);
-            acc = warp_sum(acc);
-            if (g.lane == 0) D[l * nmax + i] = (TQ)(lam[l * nmax + i] - acc);
-          }
-          group_sync(g.gid, g.nthr);
-          // d = Q^T f; a = R^{-T} g; dy = R^{-1}(a - d_1); ds = Q [a; d_2]
-          apply_q<TQ, true>(g, A, ld, M, n, tau, L, Z);
-          group_sync(g.gid, g.nthr);
-          // a into D (in place forward substitution from g)
-          solve_rt<TQ, TQ>(g, A, ld, n, L, nmax, D, D);
-          group_sync(g.gid, g.nthr);
-          // dy = R^{-1}(a - d_1) into the first n entries of Z after saving a
-          for (int e = g.tid; e < L * n; e += g.nthr) {
-            const int l = e / n, i = e % n;
-            const TQ a = D[l * nmax + i];
-            const TQ d1 = Z[(size_t)l * ld + i];
-            D[l * nmax + i] = a - d1;  // becomes dy after the back substitution
-            Z[(size_t)l * ld + i] = a;
-          }
-          group_sync(g.gid, g.nthr);
-          solve_r<TQ>(g, A, ld, n, L, nmax, D);
-          apply_q<TQ, false>(g, A, ld, M, n, tau, L, Z);
-          group_sync(g.gid, g.nthr);
-          // s += ds, y += dy; norms
-          double dmax = 0.0, smax = 0.0;
-          for (int e = g.tid; e < L * M; e += g.nthr) {
-            const int l = e / M, r = e % M;
-            const double ds = (double)Z[(size_t)l * ld + r];
-            const double sv = S[(size_t)l * ld + r] + ds;
-            S[(size_t)l * ld + r] = sv;
-            dmax = fmax(dmax, fabs(ds));
-            smax = fmax(smax, fabs(sv));
-          }
-          for (int e = g.tid; e < L * n; e += g.nthr) Y[(e / n) * nmax + e % n] += (double)D[(e / n) * nmax + e % n];
-          dmax = warp_max(dmax);
-          smax = warp_max(smax);
-          if (g.G > 1) {
-            if (g.lane == 0) {
-              misc[16 + 2 * g.wg] = dmax;
-              misc[17 + 2 * g.wg] = smax;
-            }
-            group_sync(g.gid, g.nthr);
-            dmax = 0.0;
-            smax = 0.0;
-            for (int w = 0; w < g.G; ++w) {
-              dmax = fmax(dmax, misc[16 + 2 * w]);
-              smax = fmax(smax, misc[17 + 2 * w]);
-            }
-          }
-          used_iters = iter + 1;
-          // error after this correction ~ |ds| * (contraction |ds|/|ds_prev|)
-          const double est = (iter == 0) ? dmax : dmax * fmin(1.0, dmax / fmax(prev, 1e-300));
-          conv = est <= j.tol * smax;
-          prev = dmax;
-          group_sync(g.gid, g.nthr);
+        float dmax = 0.0f, smax = 0.0f;
+        for (int e = g.tid; e < L * M; e += g.nthr) {
+          const int l = e / M, r = e % M;
+          const float ds = (float)Z[(size_t)l * ld + r];
+          const ff sv = add_f(Sf[(size_t)l * ld + r], ds);
+          Sf[(size_t)l * ld + r] = sv;
+          dmax = fmaxf(dmax, fabsf(ds));
+          smax = fmaxf(smax, fabsf(sv.h));
         }
-        if (!conv || (st & GMLS_T_ILL_CONDITIONED)) {
-          st |= (st & GMLS_T_ILL_CONDITIONED) ? 0 : GMLS_T_REFINE_NOT_CONVERGED;
-          if (g.tid == 0) {
-            int slot = atomicAdd(j.fb_count, 1);
-            j.fb_items[slot] = (int32_t)to;
+        for (int e = g.tid; e < L * n; e += g.nthr)
+          Yf[(e / n) * nmax + e % n] = add_f(Yf[(e / n) * nmax + e % n], (float)D[(e / n) * nmax + e % n]);
+        dmax = warp_max(dmax);
+        smax = warp_max(smax);
+        if (g.G > 1) {
+          if (g.lane == 0) {
+            dmisc[2 * g.wg] = dmax;
+            dmisc[2 * g.wg + 1] = smax;
           }
+          group_sync(g.gid, g.nthr);
+          dmax = 0.0f;
+          smax = 0.0f;
+          for (int w = 0; w < g.G; ++w) {
+            dmax = fmaxf(dmax, (float)dmisc[2 * w]);
+            smax = fmaxf(smax, (float)dmisc[2 * w + 1]);
+          }
+        }
+        used_iters = iter + 1;
+        // error after this correction ~ |ds| times the contraction |ds|/|ds_prev|
+        const float est = (iter == 0) ? dmax : dmax * fminf(1.0f, dmax / fmaxf(prev, 1e-37f));
+        conv = (double)est <= j.tol * (double)smax;
+        prev = dmax;
+        group_sync(g.gid, g.nthr);
+        if (conv) break;
+      }
+      if (!conv) {
+        st |= ill ? 0 : GMLS_T_REFINE_NOT_CONVERGED;
+        redo = true;
+        if (g.tid == 0) {
+          const int slot = atomicAdd(j.fb_count, 1);
+          j.fb_items[slot] = (int32_t)to;
         }
       }
-
-      // ---- Neumann coefficient of h: beta = (lambda~_piv - s^T p~) / rho
-      if (neu && j.beta) {
-        for (int l = g.wg; l < L; l += g.G) {
-          double acc = 0.0;
-          for (int r = g.lane; r < M; r += 32) acc += S[(size_t)l * ld + r] * pt[r];
-          acc = warp_sum(acc);
-          if (g.lane == 0) j.beta[to * L + l] = (misc[1 + l] - acc) / misc[0];
-        }
-      } else if (j.beta) {
-        for (int l = g.tid; l < L; l += g.nthr) j.beta[to * L + l] = 0.0;
-      }
-      if (g.tid == 0 && j.iters) j.iters[to] = (uint8_t)used_iters;
-      group_sync(g.gid, g.nthr);
     }
 
-    // ---- store w = sqrt(W) s in [row][neighbour][component] per functional
-    for (int f = 0; f < j.nout; ++f) {
-      const int R = j.out_rows[f], C = j.out_ncomp[f], src = j.out_src[f];
-      const double sgn = (double)j.out_sign[f];
-      double* w = j.out_w[f] + o0 * (int64_t)R * C;
-      const int total = R * k * C;
-      for (int e = g.tid; e < total; e += g.nthr) {
-        double val = 0.0;
-        if (!skip && src >= 0) {
-          const int r = e / (k * C), rem = e % (k * C), q = rem / C, c = rem % C;
-          if (j.out_fn[f] == GMLS_F_DIV) {  // scalar basis: component c uses the d/dx_c row
-            val = S[(size_t)(src + c) * ld + q] * sw[q];
-          } else {
-            const int row = q * nc + c;
-            val = sgn * S[(size_t)(src + r) * ld + row] * sw[row];
-          }
+    // ---- Neumann coefficient of h: beta = (lambda~_piv - s^T p~) / rho
+    if (!redo && neu && j.beta) {
+      for (int l = g.wg; l < L; l += g.G) {
+        HP acc = hz;
+        for (int r = g.lane; r < M; r += 32) acc = acc + S[(size_t)l * ld + r] * pt[r];
+        double tot;
+        if (REFINE) {
+          const ff a = *reinterpret_cast<ff*>(&acc);
+          tot = 0.0;
+          const ff red = warp_sum_ff(a.h, a.l);
+          const ff b = (reinterpret_cast<ff*>(hmisc)[1 + l] - red) * recip(reinterpret_cast<ff*>(hmisc)[0]);
+          tot = to_double(b);
+        } else {
+          const double red = warp_sum(hp_to_double(acc));
+          tot = (hp_to_double(hmisc[1 + l]) - red) / hp_to_double(hmisc[0]);
         }
-        w[e] = val;
+        if (g.lane == 0) j.beta[to * L + l] = tot;
       }
-    }
-    if (g.tid == 0) {
-      j.status[to] = st;
-      if (skip && j.iters) j.iters[to] = 0;
-    }
-    if (skip && j.beta)
+    } else if (!redo && j.beta) {
       for (int l = g.tid; l < L; l += g.nthr) j.beta[to * L + l] = 0.0;
+    }
     group_sync(g.gid, g.nthr);
   }
+
+  if (redo) {  // the FP64 redo writes this target's outputs and status
+    if (g.tid == 0) j.status[to] = st;
+    group_sync(g.gid, g.nthr);
+    return;
+  }
+  // ---- store w = sqrt(W) s in [row][neighbour][component] per functional
+  for (int f = 0; f < j.nout; ++f) {
+    const int R = j.out_rows[f], C = j.out_ncomp[f], src = j.out_src[f];
+    const double sgn = (double)j.out_sign[f];
+    double* w = j.out_w[f] + o0 * (int64_t)R * C;
+    const int total = R * k * C;
+    for (int e = g.tid; e < total; e += g.nthr) {
+      double val = 0.0;
+      if (!skip && src >= 0) {
+        const int r = e / (k * C), rem = e % (k * C), q = rem / C, c = rem % C;
+        if (j.out_fn[f] == GMLS_F_DIV) {  // scalar basis: component c uses the d/dx_c row
+          val = hp_to_double(S[(size_t)(src + c) * ld + q] * sw[q]);
+        } else {
+          const int row = q * nc + c;
+          val = sgn * hp_to_double(S[(size_t)(src + r) * ld + row] * sw[row]);
+        }
+      }
+      w[e] = val;
+    }
+  }
+  if (g.tid == 0) {
+    j.status[to] = st;
+    if (j.iters) j.iters[to] = (uint8_t)used_iters;
+  }
+  if (skip && j.beta)
+    for (int l = g.tid; l < L; l += g.nthr) j.beta[to * L + l] = 0.0;
+  group_sync(g.gid, g.nthr);
 }
 
-size_t stencil_smem_bytes(const StencilJob& j, bool fp32_refine) {
-  const Lay l = make_lay(j.ld, j.nmax, fp32_refine, fp32_refine ? 4 : 8);
-  return l.total * (size_t)(kBlock / (32 * j.warps_per_target));
+// -------------------------------------------------------- persistent kernel
+template <typename TQ, typename HP, bool REFINE>
+__global__ void __launch_bounds__(kBlock) stencil_kernel(StencilJob j, BatchPlan plan) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_task, s_bucket;
+  const int warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int task = atomicAdd(plan.task_counter, 1);
+      int b = -1;
+      int total;
+      if (plan.single) {
+        const int64_t cnt = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
+        const int gpb = 4 / plan.G[0];
+        total = (int)((cnt + gpb - 1) / gpb);
+        if (task < total) b = 0;
+      } else {
+        total = plan.task_start[plan.nb];
+        if (task < total) {
+          b = 0;
+          while (b + 1 < plan.nb && plan.task_start[b + 1] <= task) ++b;
+        }
+      }
+      s_task = task;
+      s_bucket = b;
+    }
+    __syncthreads();
+    const int task = s_task, b = s_bucket;
+    __syncthreads();
+    if (b < 0) break;
+    Group g;
+    g.G = plan.G[b];
+    g.nthr = 32 * g.G;
+    g.gid = warp / g.G;
+    g.wg = warp % g.G;
+    g.tid = threadIdx.x % g.nthr;
+    g.lane = threadIdx.x & 31;
+    const int gpb = 4 / g.G;
+    int64_t item, end;
+    if (plan.single) {
+      item = (int64_t)task * gpb + g.gid;
+      end = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
+    } else {
+      item = (int64_t)plan.bucket_start[b] + (int64_t)(task - plan.task_start[b]) * gpb + g.gid;
+      end = plan.bucket_start[b + 1];
+    }
+    if (item < end) {
+      const int64_t to = plan.items ? (int64_t)plan.items[item] : (j.items ? (int64_t)j.items[item] : item);
+      const size_t slice = (REFINE ? make_lay(plan.ld[b], plan.nmax[b], 4, 8, true)
+                                   : make_lay(plan.ld[b], plan.nmax[b], 8, 8, false)).total;
+      process_target<TQ, HP, REFINE>(j, g, smem + (size_t)g.gid * slice, plan.ld[b], plan.nmax[b], to);
+    }
+  }
 }
 
-cudaError_t launch_stencils(const Launch& L, const StencilJob& j, bool fp32_refine, int grid_blocks) {
-  const size_t smem = stencil_smem_bytes(j, fp32_refine);
+cudaError_t launch_stencils(const Launch& L, const StencilJob& j, const BatchPlan& plan, bool fp32_refine,
+                            size_t smem, int grid_blocks) {
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
   if (fp32_refine) {
-    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    e = cudaFuncSetAttribute(stencil_kernel<float, ff, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    stencil_kernel<float, true><<<grid_blocks, kBlock, smem, L.stream>>>(j);
+    stencil_kernel<float, ff, true><<<grid_blocks, kBlock, smem, L.stream>>>(j, plan);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    e = cudaFuncSetAttribute(stencil_kernel<double, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    stencil_kernel<double, false><<<grid_blocks, kBlock, smem, L.stream>>>(j);
+    stencil_kernel<double, double, false><<<grid_blocks, kBlock, smem, L.stream>>>(j, plan);
   }
   *L.counter += 1;
+  return cudaGetLastError();
+}
+
+int stencil_blocks_per_sm(bool fp32_refine, size_t smem) {
+  int blocks = 0;
+  const void* fn = fp32_refine ? (const void*)stencil_kernel<float, ff, true> : (const void*)stencil_kernel<double, double, false>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kBlock, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return blocks > 0 ? blocks : 1;
+}
+
+// ------------------------------------------------------------- bucketing
+// bucket = (degree - 1) * n_classes + row class; row class = first class whose
+// bound is >= rows (k * components); targets too large for every class get
+// bucket -1 and are reported by the stencil kernel as unsupported.
+__global__ void bucket_count_kernel(BucketJob b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < b.n_tgt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int m = b.degree_pt ? (int)b.degree_pt[t] : b.degree;
+    const int rows = (int)(b.off[t + 1] - b.off[t]) * b.nc;
+    int rc = 0;
+    while (rc < b.n_classes && b.class_rows[rc] < rows) ++rc;
+    int bucket = (m >= 1 && m <= 4 && rc < b.n_classes) ? (m - 1) * b.n_classes + rc : b.nb - 1;
+    b.bucket_of[t] = bucket;
+    atomicAdd(&b.counts[bucket], 1);
+  }
+}
+
+__global__ void bucket_plan_kernel(BucketJob b) {
+  if (threadIdx.x != 0) return;
+  int start = 0, task = 0;
+  for (int i = 0; i < b.nb; ++i) {
+    b.bucket_start[i] = start;
+    b.task_start[i] = task;
+    b.fill[i] = 0;
+    const int c = b.counts[i];
+    start += c;
+    task += (c + b.gpb[i] - 1) / b.gpb[i];
+  }
+  b.bucket_start[b.nb] = start;
+  b.task_start[b.nb] = task;
+}
+
+__global__ void bucket_scatter_kernel(BucketJob b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < b.n_tgt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int bucket = b.bucket_of[t];
+    const int pos = b.bucket_start[bucket] + atomicAdd(&b.fill[bucket], 1);
+    b.items[pos] = (int32_t)t;
+  }
+}
+
+cudaError_t launch_bucketing(const Launch& L, const BucketJob& b) {
+  const unsigned blocks = (unsigned)std::min<int64_t>(152 * 8, (b.n_tgt + 255) / 256 + 1);
+  cudaError_t e = cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * b.nb, L.stream);
+  if (e != cudaSuccess) return e;
+  bucket_count_kernel<<<blocks, 256, 0, L.stream>>>(b);
+  bucket_plan_kernel<<<1, 32, 0, L.stream>>>(b);
+  bucket_scatter_kernel<<<blocks, 256, 0, L.stream>>>(b);
+  *L.counter += 3;
   return cudaGetLastError();
 }
 

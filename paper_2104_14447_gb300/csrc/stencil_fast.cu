@@ -58,13 +58,6 @@ __device__ __forceinline__ float wmax(float v) {
   return v;
 }
 
-// (a_h + a_l) - (b_h + b_l) for coordinates stored as float pairs
-__device__ __forceinline__ ff sub_pair(float ah, float al, float bh, float bl) {
-  ff s = two_sum(ah, -bh);
-  float e = __fadd_rn(s.l, __fsub_rn(al, bl));
-  return quick_two_sum(s.h, e);
-}
-
 // apply Q (REV: H_0 ... H_{N-1} z, i.e. reflectors in reverse order) or Q^T
 // to the row-distributed vectors z[l][i], l < L
 template <int MR, int N, bool REV>

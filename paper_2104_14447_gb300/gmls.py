@@ -38,10 +38,11 @@ EXPORTED = [
     "gmls_create", "gmls_destroy", "gmls_set_stream", "gmls_cloud", "gmls_neighbors", "gmls_stencils",
     "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_export", "gmls_export_size", "gmls_release",
     "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
-    "gmls_version",
+    "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
 ]
 NOALLOC_MAX_POINTS = 262144
-OPT_FORCE_GENERIC = 0
+OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING = 0, 1, 2
+T_UNSUPPORTED = 64
 
 
 class GmlsError(RuntimeError):
@@ -53,7 +54,7 @@ class GmlsError(RuntimeError):
 class NbrParams(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("eps_factor", ctypes.c_double),
                 ("cap", ctypes.c_int32), ("reserved", ctypes.c_int32), ("targets", ctypes.c_void_p),
-                ("n_targets", ctypes.c_int64), ("halfspace", ctypes.c_void_p)]
+                ("n_targets", ctypes.c_int64), ("halfspace", ctypes.c_void_p), ("k_per_target", ctypes.c_void_p)]
 
 
 class StencilParams(ctypes.Structure):
@@ -94,6 +95,10 @@ def load(path: str = LIB_PATH):
         "gmls_launch_count": [vp, P64],
         "gmls_set_option": [vp, i32, i64],
         "gmls_knn_noalloc": [ctypes.c_int, i64, vp, i32, ctypes.c_double, vp, vp, vp, vp],
+        "gmls_tune_info": [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
+        "gmls_capture_begin": [vp],
+        "gmls_capture_end": [vp, P64],
+        "gmls_graph_launch": [vp, i64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -165,14 +170,15 @@ class Context:
         return out.value
 
     def neighbors(self, cloud: int, k: int, eps_factor: float, mode: int = KNN, cap: int | None = None,
-                  targets=None, halfspace=None) -> int:
+                  targets=None, halfspace=None, k_per_target=None) -> int:
         tg = _contig(targets, torch.int32) if targets is not None else None
         hs = _contig(halfspace, torch.float64) if halfspace is not None else None
+        kp = _contig(k_per_target, torch.int32) if k_per_target is not None else None
         p = NbrParams(mode, k, eps_factor, cap if cap is not None else k, 0, _ptr(tg),
-                      0 if tg is None else tg.shape[0], _ptr(hs))
+                      0 if tg is None else tg.shape[0], _ptr(hs), _ptr(kp))
         out = ctypes.c_int64()
         self._check(self.lib.gmls_neighbors(self.h, cloud, ctypes.byref(p), ctypes.byref(out)))
-        self._keep[out.value] = (tg, hs)
+        self._keep[out.value] = (tg, hs, kp)
         return out.value
 
     def stencils(self, nbrs: int, basis: int, degree: int, functionals, precision: int = FP64,
@@ -239,6 +245,29 @@ class Context:
 
     def set_option(self, option: int, value: int):
         self._check(self.lib.gmls_set_option(self.h, option, value))
+
+    def tune_log(self):
+        """The autotuner's timings: list of dicts (shape, variant, ms)."""
+        out = []
+        f = (ctypes.c_int32 * 9)()
+        ms = ctypes.c_float()
+        i = 0
+        while self.lib.gmls_tune_info(self.h, i, f, ctypes.byref(ms)) == OK:
+            keys = ["basis", "dim", "degree", "precision", "rows", "solve_rows", "neumann", "bucketed", "variant"]
+            out.append(dict(zip(keys, list(f)), ms=ms.value))
+            i += 1
+        return out
+
+    def capture_begin(self):
+        self._check(self.lib.gmls_capture_begin(self.h))
+
+    def capture_end(self) -> int:
+        out = ctypes.c_int64()
+        self._check(self.lib.gmls_capture_end(self.h, ctypes.byref(out)))
+        return out.value
+
+    def graph_launch(self, graph: int):
+        self._check(self.lib.gmls_graph_launch(self.h, graph))
 
     def launch_count(self) -> int:
         v = ctypes.c_int64()

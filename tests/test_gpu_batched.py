@@ -1,0 +1,179 @@
+"""GPU parity of the bucketed persistent path (uneven shapes in one launch),
+the autotuner, CUDA-graph capture, and mixed-versus-alone reproducibility.
+
+Workload in miniature of the uneven batch: jittered 2D and 3D clouds, degree
+U{2,3,4} per target, radius lists at eps = 1.8 x the distance of the Q(d,m)-th
+neighbour (capped at 160), 20 % one-sided targets (half-space filter)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_14447_gb300 import gmls, inputs
+
+pytestmark = pytest.mark.gpu
+
+Q = {(2, 1): 3, (2, 2): 6, (2, 3): 10, (2, 4): 15, (3, 1): 4, (3, 2): 10, (3, 3): 20, (3, 4): 35}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2104_14447_gb300 import build
+
+    build.build()
+    c = gmls.Context(0, arena_bytes=8 << 30)
+    yield c
+    c.close()
+
+
+def _rel(wg, wo):
+    a = np.abs(wg - wo).reshape(wo.shape[0], -1).max(axis=1)
+    b = np.abs(wo).reshape(wo.shape[0], -1).max(axis=1)
+    return a / np.where(b > 0, b, 1.0)
+
+
+def _uneven_case(dim, n_axis, seed):
+    x = inputs.jittered_grid(dim, n_axis, seed=seed)
+    n = x.shape[1]
+    deg = (2 + np.floor(3 * inputs.uniform(seed, 3, n))).astype(np.int8)
+    inner = np.all(np.abs(x - 0.5) < 0.3, axis=0)
+    one_sided = (inputs.uniform(seed, 4, n) < 0.2) & inner
+    hs = inputs.unit_vectors(seed, 5, n, dim).T.copy()
+    hs[~one_sided] = 0.0
+    kpt = np.array([Q[(dim, int(m))] for m in deg], dtype=np.int32)
+    return x, deg, hs, kpt, one_sided
+
+
+@pytest.mark.parametrize("precision", [gmls.FP32_REFINE, gmls.FP64])
+@pytest.mark.parametrize("dim,n_axis", [(2, 48), (3, 14)])
+def test_uneven_radius_batch_matches_oracle(ctx, dim, n_axis, precision):
+    x, deg, hs, kpt, one_sided = _uneven_case(dim, n_axis, 5)
+    n = x.shape[1]
+    tg = np.arange(n, dtype=np.int32)
+    cid = ctx.cloud(x)
+    nid = ctx.neighbors(cid, int(kpt.max()), 1.8, mode=gmls.RADIUS, cap=160, halfspace=hs, k_per_target=kpt)
+    off = ctx.export(nid, gmls.X_NBR_OFFSETS, torch.int64).cpu().numpy()
+    idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy()
+    eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
+    nst = ctx.export(nid, gmls.X_NBR_STATUS, torch.uint8).cpu().numpy()
+    # neighbour lists against the oracle, bit for bit (per-target k via one call per k)
+    for kk in np.unique(kpt):
+        sel = np.flatnonzero(kpt == kk).astype(np.int32)
+        ok = sel[nst[sel] == 0]
+        oi, oe = oracle.knn(x, ok, int(kk), 1.8, halfspace=hs[ok], method="grid")
+        assert np.array_equal(eps[ok], oe)
+        ooff, oidx = oracle.radius(x, ok, oe, 160, halfspace=hs[ok], method="grid")
+        for q, t in enumerate(ok):
+            assert np.array_equal(idx[off[t]:off[t + 1]], oidx[ooff[q]:ooff[q + 1]])
+    sid = ctx.stencils(nid, gmls.SCALAR, 0, [gmls.GRAD, gmls.LAPLACIAN], precision=precision, degree_per_target=deg)
+    st = ctx.export(sid, gmls.X_STATUS, torch.uint8).cpu().numpy()
+    wgrad = ctx.weights(sid, gmls.GRAD).cpu().numpy()
+    tol = 1e-9 if precision == gmls.FP32_REFINE else 1e-10
+    checked = 0
+    for m in (2, 3, 4):
+        sel = np.flatnonzero((deg == m) & (nst == 0)).astype(np.int32)
+        soff = np.concatenate([[0], np.cumsum(off[sel + 1] - off[sel])])
+        sidx = np.concatenate([idx[off[t]:off[t + 1]] for t in sel])
+        wo, _, diag = oracle.stencils(x, sel, soff, sidx, eps[sel], "scalar", m, "grad")
+        kappa = diag[:, 0] / diag[:, 1]
+        for q, t in enumerate(sel):
+            if st[t] & (gmls.T_RANK_DEFICIENT | gmls.T_UNSUPPORTED):
+                continue
+            k = off[t + 1] - off[t]
+            wg = wgrad[off[t] * dim:off[t + 1] * dim].reshape(dim, k, 1)
+            err = float(np.max(np.abs(wg - wo[q])) / np.max(np.abs(wo[q])))
+            assert err <= tol * max(1.0, kappa[q] * 1e-6), (m, t, err, kappa[q], st[t])
+            checked += 1
+    assert checked > 0.9 * n
+    ctx.release(sid)
+    ctx.release(nid)
+    ctx.release(cid)
+
+
+def test_per_target_degree_knn_and_autotune_log(ctx):
+    ctx.set_option(gmls.OPT_CLEAR_TUNING, 1)
+    x, deg, _, _, _ = _uneven_case(2, 40, 9)
+    n = x.shape[1]
+    cid = ctx.cloud(x)
+    nid = ctx.neighbors(cid, 36, 1.5)
+    idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy().reshape(n, 36)
+    eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
+    sid = ctx.stencils(nid, gmls.SCALAR, 0, [gmls.LAPLACIAN], precision=gmls.FP32_REFINE, degree_per_target=deg)
+    w = ctx.weights(sid, gmls.LAPLACIAN).cpu().numpy().reshape(n, 1, 36, 1)
+    log = ctx.tune_log()
+    assert log and all(r["bucketed"] == 1 for r in log) and {r["degree"] for r in log} == {2, 3, 4}
+    for m in (2, 3, 4):
+        sel = np.flatnonzero(deg == m).astype(np.int32)
+        off = np.arange(0, len(sel) * 36 + 1, 36)
+        wo, _, _ = oracle.stencils(x, sel, off, idx[sel].reshape(-1), eps[sel], "scalar", m, "laplacian")
+        assert np.max(_rel(w[sel], wo)) <= 1e-9
+    ctx.release(sid)
+    ctx.release(nid)
+    ctx.release(cid)
+
+
+def test_mixed_batch_equals_alone_bitwise(ctx):
+    """Each target's weights do not depend on the other targets of the launch:
+    a subset run alone equals the same targets inside a larger mixed batch."""
+    x, deg, hs, kpt, _ = _uneven_case(2, 40, 11)
+    n = x.shape[1]
+    cid = ctx.cloud(x)
+    sub = np.arange(0, n, 3, dtype=np.int32)
+
+    def run(targets):
+        nid = ctx.neighbors(cid, int(kpt.max()), 1.8, mode=gmls.RADIUS, cap=160, targets=targets,
+                            halfspace=hs[targets], k_per_target=kpt[targets])
+        sid = ctx.stencils(nid, gmls.SCALAR, 0, [gmls.GRAD], precision=gmls.FP32_REFINE,
+                           degree_per_target=deg[targets])
+        off = ctx.export(nid, gmls.X_NBR_OFFSETS, torch.int64).cpu().numpy()
+        w = ctx.weights(sid, gmls.GRAD).cpu().numpy()
+        ctx.release(sid)
+        ctx.release(nid)
+        return off, w
+
+    off_all, w_all = run(np.arange(n, dtype=np.int32))
+    off_sub, w_sub = run(sub)
+    for q, t in enumerate(sub):
+        a = w_sub[off_sub[q] * 2:off_sub[q + 1] * 2]
+        b = w_all[off_all[t] * 2:off_all[t + 1] * 2]
+        assert np.array_equal(a, b)
+    ctx.release(cid)
+
+
+def test_graph_capture_replays_pipeline():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    stream = torch.cuda.Stream()
+    c = gmls.Context(0, arena_bytes=2 << 30, stream=stream)
+    x = torch.from_numpy(inputs.jittered_grid(2, 64, seed=2)).cuda()
+    n = x.shape[1]
+    with torch.cuda.stream(stream):
+        # eager run (also fills the autotuner cache for these shapes)
+        cid = c.cloud(x)
+        nid = c.neighbors(cid, 36, 1.5)
+        sid = c.stencils(nid, gmls.SCALAR, 4, [gmls.GRAD], precision=gmls.FP32_REFINE)
+        w_eager = c.weights(sid, gmls.GRAD).clone()
+        bufs = c.assemble_csr(sid, gmls.GRAD)
+        c.sync()
+        ref = [t.clone() for t in bufs]
+        for h in (sid, nid, cid):
+            c.release(h)
+        # captured pipeline, launched twice
+        c.capture_begin()
+        cid = c.cloud(x)
+        nid = c.neighbors(cid, 36, 1.5)
+        sid = c.stencils(nid, gmls.SCALAR, 4, [gmls.GRAD], precision=gmls.FP32_REFINE)
+        c.assemble_csr(sid, gmls.GRAD, out=bufs)
+        gid = c.capture_end()
+        for t in bufs:
+            t.zero_()
+        c.graph_launch(gid)
+        c.graph_launch(gid)
+        c.sync()
+        assert all(torch.equal(a, b) for a, b in zip(bufs, ref))
+        assert torch.equal(c.weights(sid, gmls.GRAD), w_eager)
+    for h in (gid, sid, nid, cid):
+        c.release(h)
+    c.close()
