@@ -280,6 +280,57 @@ gmls_status gmls_capture_begin(gmls_ctx* ctx);
 gmls_status gmls_capture_end(gmls_ctx* ctx, int64_t* graph_id);
 gmls_status gmls_graph_launch(gmls_ctx* ctx, int64_t graph_id);
 
+/*
+ * Continuous-batching request server (the benchmark spec's serving pattern; the
+ * paper has no serving layer).  A scheduler thread admits submitted requests
+ * whenever an in-flight slot and a slice of the server arena (first-fit, sized
+ * from the request) are free, and issues each request's pipeline -- cloud and
+ * cell list, k-nearest neighbours, stencils -- on the least loaded of
+ * n_streams CUDA streams, so concurrent requests overlap on the GPU.  Results
+ * stay on the device until gmls_server_release.  Each request runs in its own
+ * context with a fixed kernel choice per shape (no autotuning), so its result
+ * is bit-for-bit the same alone or in the mix.  The arena is a caller-owned
+ * device buffer; the server never calls cudaMalloc.  Latency = submit to
+ * completion of the request's last kernel (host steady clock).
+ */
+typedef struct gmls_server gmls_server;
+
+typedef struct {
+  int32_t dim;               /* 2 or 3                                               */
+  int64_t n;                 /* particles; every particle is a target                */
+  const double* xyz;         /* HOST FP64 SoA [dim][n]; copied by gmls_server_submit */
+  int32_t basis;             /* GMLS_BASIS_*                                         */
+  int32_t degree;            /* m in 1..4                                            */
+  int32_t k;                 /* neighbours (k nearest, eps = eps_factor * d_k)       */
+  double eps_factor;
+  int32_t precision;         /* GMLS_FP64 or GMLS_FP32_REFINE                        */
+  int32_t n_functionals;
+  int32_t functionals[5];
+} gmls_request;
+
+typedef struct {
+  int64_t completed, targets, pending, inflight;
+  double p50_ms, p99_ms, mean_ms; /* latency of completed requests                 */
+  double elapsed_s;               /* first submit to last completion               */
+  double targets_per_s;           /* completed targets / elapsed_s                 */
+} gmls_serve_stats;
+
+gmls_status gmls_server_create(gmls_server** out, int device, void* arena, size_t arena_bytes, int32_t n_streams,
+                               int32_t max_inflight);
+/* Queue a request; returns at once with a ticket. */
+gmls_status gmls_server_submit(gmls_server* s, const gmls_request* req, int64_t* ticket);
+/* Wait up to timeout_ms; *done = 1 when finished (return value: its status). */
+gmls_status gmls_server_wait(gmls_server* s, int64_t ticket, int32_t timeout_ms, int32_t* done);
+/* Copy one array of a finished request (GMLS_X_* selector, as gmls_export) to
+   dst (host or device, `bytes` capacity); dst NULL only reports *needed. */
+gmls_status gmls_server_result(gmls_server* s, int64_t ticket, int32_t what, int32_t functional, void* dst,
+                               size_t bytes, size_t* needed);
+/* Free a finished request's device memory (GMLS_EBUSY while it runs). */
+gmls_status gmls_server_release(gmls_server* s, int64_t ticket);
+gmls_status gmls_server_stats(gmls_server* s, gmls_serve_stats* out);
+/* Stop the scheduler, wait for the streams, free everything. */
+gmls_status gmls_server_destroy(gmls_server* s);
+
 /* Message of the last error on this context (NULL ctx: the last error of a
    call without a context: gmls_create or gmls_knn_noalloc). */
 const char* gmls_last_error(gmls_ctx* ctx);

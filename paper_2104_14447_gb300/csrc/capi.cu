@@ -218,14 +218,41 @@ static bool is_host_ptr(const void* p) {
 static int heuristic_g(int ld, int nmax, bool fp32) {
   int g = ld <= 64 ? 1 : (ld <= 192 ? 2 : 4);
   while (g < 4 && (size_t)(4 / g) * tile_bytes(ld, nmax, fp32) > 110 * 1024) g *= 2;
-  return ((size_t)(4 / g) * tile_bytes(ld, nmax, fp32) <= 227 * 1024) ? g : 0;
+  if ((size_t)(4 / g) * tile_bytes(ld, nmax, fp32) <= 227 * 1024) return g;
+  // tiles in global memory (one L2-resident slot per target in flight)
+  return tile_bytes(ld, nmax, fp32, true) <= 227 * 1024 ? 4 : 0;
+}
+
+static bool needs_gtile(int G, int ld, int nmax, bool fp32) {
+  return (size_t)(4 / G) * tile_bytes(ld, nmax, fp32) > 227 * 1024;
 }
 
 static size_t plan_smem(const BatchPlan& pl, bool fp32) {
   size_t m = 0;
   for (int b = 0; b < (pl.single ? 1 : pl.nb); ++b)
-    if (pl.G[b] > 0) m = std::max(m, (size_t)(4 / pl.G[b]) * tile_bytes(pl.ld[b], pl.nmax[b], fp32));
+    if (pl.G[b] > 0) m = std::max(m, (size_t)(4 / pl.G[b]) * tile_bytes(pl.ld[b], pl.nmax[b], fp32, pl.gtile[b]));
   return m;
+}
+
+// global tile slots for the buckets that need them: [blocks][groups][slot]
+static bool plan_gscratch(gmls_ctx* ctx, BatchPlan& pl, bool fp32, int grid, void** owned) {
+  size_t slot = 0;
+  int groups = 1;
+  for (int b = 0; b < (pl.single ? 1 : pl.nb); ++b) {
+    pl.gtile[b] = pl.G[b] > 0 && needs_gtile(pl.G[b], pl.ld[b], pl.nmax[b], fp32);
+    if (pl.gtile[b]) {
+      slot = std::max(slot, global_tile_bytes(pl.ld[b], pl.nmax[b], fp32));
+      groups = std::max(groups, 4 / pl.G[b]);
+    }
+  }
+  *owned = nullptr;
+  pl.gscratch = nullptr;
+  pl.gslot_bytes = 0;
+  if (!slot) return true;
+  pl.gslot_bytes = (slot + 255) & ~size_t(255);
+  *owned = ctx->arena.alloc((size_t)grid * groups * pl.gslot_bytes);
+  pl.gscratch = static_cast<unsigned char*>(*owned);
+  return *owned != nullptr;
 }
 
 static bool capturing(gmls_ctx* ctx) {
@@ -265,12 +292,17 @@ static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int G, int 
   pl.ld[0] = ld;
   pl.nmax[0] = nmax;
   pl.task_counter = counter;
+  pl.gtile[0] = needs_gtile(G, ld, nmax, fp32);
   const size_t smem = plan_smem(pl, fp32);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
   if (e != cudaSuccess) return e;
   const int grid = sms * stencil_blocks_per_sm(fp32, smem);
+  void* owned = nullptr;
+  if (!plan_gscratch(ctx, pl, fp32, grid, &owned)) return cudaErrorMemoryAllocation;
   Launch L = ctx->launch();
-  return launch_stencils(L, j, pl, fp32, smem, grid);
+  e = launch_stencils(L, j, pl, fp32, smem, grid);
+  ctx->arena.release(owned);  // stream ordered: later work on this stream runs after the kernel
+  return e;
 }
 
 // Uniform neighbour counts and degree: one shape.  Candidates: the
@@ -297,7 +329,9 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     std::vector<int> cands;
     if (fast_ok) cands.push_back(-1);
     for (int G = 1; G <= 4; G *= 2)
-      if ((size_t)(4 / G) * tile_bytes(ld, nmax, refine) <= 227 * 1024) cands.push_back(G);
+      if ((size_t)(4 / G) * tile_bytes(ld, nmax, refine) <= 227 * 1024 ||
+          (G == 4 && tile_bytes(ld, nmax, refine, true) <= 227 * 1024))
+        cands.push_back(G);
     for (int c : cands) {
       float ms = time_launch(ctx, [&]() {
         if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
@@ -417,7 +451,9 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
         float best = 1e30f;
         int choice = 0;
         for (int G = 1; G <= 4; G *= 2) {
-          if ((size_t)(4 / G) * tile_bytes(pl.ld[bi], pl.nmax[bi], refine) > 227 * 1024) continue;
+          if ((size_t)(4 / G) * tile_bytes(pl.ld[bi], pl.nmax[bi], refine) > 227 * 1024 &&
+              !(G == 4 && tile_bytes(pl.ld[bi], pl.nmax[bi], refine, true) <= 227 * 1024))
+            continue;
           float ms = time_launch(ctx, [&]() {
             if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
             launch_single(ctx, js, G, pl.ld[bi], pl.nmax[bi], refine, counter, sms);
@@ -445,10 +481,18 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
   pl.bucket_start = b.bucket_start;
   pl.task_start = b.task_start;
   pl.task_counter = counter;
+  for (int bi = 0; bi < pl.nb; ++bi) pl.gtile[bi] = needs_gtile(pl.G[bi], pl.ld[bi], pl.nmax[bi], refine);
   const size_t smem = plan_smem(pl, refine);
+  const int grid = sms * stencil_blocks_per_sm(refine, smem);
+  void* owned = nullptr;
+  if (!plan_gscratch(ctx, pl, refine, grid, &owned)) {
+    release();
+    return fail(ctx, GMLS_ENOMEM, "gmls_stencils: arena exhausted (global tiles)");
+  }
   if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
   e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
-  if (e == cudaSuccess) e = launch_stencils(L, j, pl, refine, smem, sms * stencil_blocks_per_sm(refine, smem));
+  if (e == cudaSuccess) e = launch_stencils(L, j, pl, refine, smem, grid);
+  ctx->arena.release(owned);
   release();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_stencils bucketed launch");
   return GMLS_OK;

@@ -170,6 +170,9 @@ struct BatchPlan {
   int G[kMaxBuckets];           // warps per target
   int ld[kMaxBuckets];          // tile rows
   int nmax[kMaxBuckets];        // tile columns
+  int gtile[kMaxBuckets];       // 1: the tiles live in global memory (too big for shared)
+  unsigned char* gscratch;      // [grid blocks][4 / G][gslot_bytes] global tiles
+  size_t gslot_bytes;
 };
 
 struct BucketJob {
@@ -190,7 +193,8 @@ struct BucketJob {
   int32_t* items;
 };
 
-size_t tile_bytes(int ld, int nmax, bool fp32_refine);
+size_t tile_bytes(int ld, int nmax, bool fp32_refine, bool ext = false);
+size_t global_tile_bytes(int ld, int nmax, bool fp32_refine);
 int stencil_blocks_per_sm(bool fp32_refine, size_t smem);
 cudaError_t launch_stencils(const Launch& L, const StencilJob& j, const BatchPlan& plan, bool fp32_refine,
                             size_t smem, int grid_blocks);

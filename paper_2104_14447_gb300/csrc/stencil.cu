@@ -96,17 +96,21 @@ struct Group {
 
 // ------------------------------------------------------------ tile layout
 struct Lay {
-  size_t A, HB, tau, dots, sw, lam, S, Y, Z, D, pt, misc, total;
+  size_t A, HB, gtotal, tau, dots, sw, lam, S, Y, Z, D, pt, misc, total;
 };
 
-// tqs: bytes of TQ; hps: bytes of HP; hb: separate high-precision tile (FP32 path)
-__host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool hb) {
+// tqs: bytes of TQ; hps: bytes of HP; hb: separate high-precision tile (FP32
+// path); ext: the tiles A and HB live in a global-memory slot (offsets A, HB
+// there, gtotal its size) and the shared-memory part starts at tau
+__host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool hb, bool ext = false) {
   Lay l;
   size_t o = 0;
   l.A = o;
   o += align16((size_t)nmax * ld * tqs);
   l.HB = o;
   if (hb) o += align16((size_t)nmax * ld * hps);
+  l.gtotal = o;
+  if (ext) o = 0;
   l.tau = o;
   o += align16((size_t)nmax * tqs);
   l.dots = o;
@@ -131,8 +135,11 @@ __host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool
   return l;
 }
 
-size_t tile_bytes(int ld, int nmax, bool fp32_refine) {
-  return fp32_refine ? make_lay(ld, nmax, 4, 8, true).total : make_lay(ld, nmax, 8, 8, false).total;
+size_t tile_bytes(int ld, int nmax, bool fp32_refine, bool ext) {
+  return fp32_refine ? make_lay(ld, nmax, 4, 8, true, ext).total : make_lay(ld, nmax, 8, 8, false, ext).total;
+}
+size_t global_tile_bytes(int ld, int nmax, bool fp32_refine) {
+  return fp32_refine ? make_lay(ld, nmax, 4, 8, true, true).gtotal : make_lay(ld, nmax, 8, 8, false, true).gtotal;
 }
 
 // ---------------------------------------------------------------- QR (in TQ)
@@ -255,11 +262,12 @@ __device__ __forceinline__ ff sqrt_weight(ff u, const StencilJob& j) {
 
 // ------------------------------------------------------------ one target
 template <typename TQ, typename HP, bool REFINE>
-__device__ void process_target(const StencilJob& j, const Group& g, unsigned char* base, int ld, int nmax,
-                               int64_t to) {
-  const Lay lay = make_lay(ld, nmax, (int)sizeof(TQ), (int)sizeof(HP), REFINE);
-  TQ* A = reinterpret_cast<TQ*>(base + lay.A);
-  HP* HB = REFINE ? reinterpret_cast<HP*>(base + lay.HB) : reinterpret_cast<HP*>(base + lay.A);
+__device__ void process_target(const StencilJob& j, const Group& g, unsigned char* base, unsigned char* gbase,
+                               int ld, int nmax, int64_t to) {
+  const Lay lay = make_lay(ld, nmax, (int)sizeof(TQ), (int)sizeof(HP), REFINE, gbase != nullptr);
+  unsigned char* tb = gbase ? gbase : base;  // where the tiles A and HB live
+  TQ* A = reinterpret_cast<TQ*>(tb + lay.A);
+  HP* HB = REFINE ? reinterpret_cast<HP*>(tb + lay.HB) : reinterpret_cast<HP*>(tb + lay.A);
   TQ* tau = reinterpret_cast<TQ*>(base + lay.tau);
   HP* sw = reinterpret_cast<HP*>(base + lay.sw);
   HP* lam = reinterpret_cast<HP*>(base + lay.lam);
@@ -613,9 +621,12 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(StencilJob j, BatchPlan
     }
     if (item < end) {
       const int64_t to = plan.items ? (int64_t)plan.items[item] : (j.items ? (int64_t)j.items[item] : item);
-      const size_t slice = (REFINE ? make_lay(plan.ld[b], plan.nmax[b], 4, 8, true)
-                                   : make_lay(plan.ld[b], plan.nmax[b], 8, 8, false)).total;
-      process_target<TQ, HP, REFINE>(j, g, smem + (size_t)g.gid * slice, plan.ld[b], plan.nmax[b], to);
+      const bool ext = plan.gtile[b] != 0;
+      const size_t slice = (REFINE ? make_lay(plan.ld[b], plan.nmax[b], 4, 8, true, ext)
+                                   : make_lay(plan.ld[b], plan.nmax[b], 8, 8, false, ext)).total;
+      unsigned char* gslot =
+          ext ? plan.gscratch + ((size_t)blockIdx.x * gpb + g.gid) * plan.gslot_bytes : nullptr;
+      process_target<TQ, HP, REFINE>(j, g, smem + (size_t)g.gid * slice, gslot, plan.ld[b], plan.nmax[b], to);
     }
   }
 }

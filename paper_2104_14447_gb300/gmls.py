@@ -39,6 +39,8 @@ EXPORTED = [
     "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_export", "gmls_export_size", "gmls_release",
     "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
     "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
+    "gmls_server_create", "gmls_server_submit", "gmls_server_wait", "gmls_server_result", "gmls_server_release",
+    "gmls_server_stats", "gmls_server_destroy",
 ]
 NOALLOC_MAX_POINTS = 262144
 OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING = 0, 1, 2
@@ -62,6 +64,18 @@ class StencilParams(ctypes.Structure):
                 ("weight_power", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_functionals", ctypes.c_int32),
                 ("functionals", ctypes.c_int32 * 5), ("neumann", ctypes.c_int32), ("max_refine", ctypes.c_int32),
                 ("refine_tol", ctypes.c_double), ("degree_per_target", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("basis", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("k", ctypes.c_int32), ("eps_factor", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("n_functionals", ctypes.c_int32), ("functionals", ctypes.c_int32 * 5)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("targets", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("inflight", ctypes.c_int64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("elapsed_s", ctypes.c_double), ("targets_per_s", ctypes.c_double)]
 
 
 _lib = None
@@ -99,6 +113,13 @@ def load(path: str = LIB_PATH):
         "gmls_capture_begin": [vp],
         "gmls_capture_end": [vp, P64],
         "gmls_graph_launch": [vp, i64],
+        "gmls_server_create": [ctypes.POINTER(vp), ctypes.c_int, vp, sz, i32, i32],
+        "gmls_server_submit": [vp, ctypes.POINTER(Request), P64],
+        "gmls_server_wait": [vp, i64, i32, ctypes.POINTER(i32)],
+        "gmls_server_result": [vp, i64, i32, i32, vp, sz, ctypes.POINTER(sz)],
+        "gmls_server_release": [vp, i64],
+        "gmls_server_stats": [vp, ctypes.POINTER(ServerStats)],
+        "gmls_server_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -283,3 +304,68 @@ def _contig(a, dtype):
     if a.dtype != dtype:
         a = a.to(dtype)
     return a.contiguous()
+
+
+class Server:
+    """Continuous-batching stencil server (gmls_server_*) over a torch-allocated arena."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 16 << 30, streams: int = 4, max_inflight: int = 8):
+        self.lib = load()
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=torch.device("cuda", device))
+        h = ctypes.c_void_p()
+        rc = self.lib.gmls_server_create(ctypes.byref(h), device, _ptr(self.arena), arena_bytes, streams, max_inflight)
+        if rc != OK:
+            raise GmlsError(rc, self.lib.gmls_last_error(None).decode())
+        self.h = h
+
+    def submit(self, x, basis: int, degree: int, k: int, functionals, precision: int = FP32_REFINE,
+               eps_factor: float = 1.5) -> int:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        fs = (ctypes.c_int32 * 5)(*(list(functionals) + [0] * (5 - len(functionals))))
+        r = Request(x.shape[0], x.shape[1], ctypes.c_void_p(x.ctypes.data), basis, degree, k, eps_factor, precision,
+                    len(functionals), fs)
+        t = ctypes.c_int64()
+        rc = self.lib.gmls_server_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if rc != OK:
+            raise GmlsError(rc, "gmls_server_submit rejected the request")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> bool:
+        done = ctypes.c_int32()
+        rc = self.lib.gmls_server_wait(self.h, ticket, timeout_ms, ctypes.byref(done))
+        if rc != OK:
+            raise GmlsError(rc, f"request {ticket} failed")
+        return bool(done.value)
+
+    def result(self, ticket: int, what: int, dtype, functional: int = 0):
+        need = ctypes.c_size_t()
+        rc = self.lib.gmls_server_result(self.h, ticket, what, functional, None, 0, ctypes.byref(need))
+        if rc != OK:
+            raise GmlsError(rc, f"result of request {ticket}")
+        esz = torch.tensor([], dtype=dtype).element_size()
+        out = torch.empty(need.value // esz, dtype=dtype)
+        rc = self.lib.gmls_server_result(self.h, ticket, what, functional, _ptr(out), need.value, None)
+        if rc != OK:
+            raise GmlsError(rc, f"result of request {ticket}")
+        return out
+
+    def release(self, ticket: int):
+        rc = self.lib.gmls_server_release(self.h, ticket)
+        if rc != OK:
+            raise GmlsError(rc, f"release of request {ticket}")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self.lib.gmls_server_stats(self.h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gmls_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

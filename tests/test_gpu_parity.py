@@ -124,6 +124,7 @@ CASES = [
     (3, 12, gmls.DIVFREE, 3, 80, [gmls.VEC_LAPLACIAN]),
     (3, 9, gmls.SCALAR, 4, 84, [gmls.LAPLACIAN]),
     (3, 9, gmls.DIVFREE, 2, 42, [gmls.CURLCURL]),
+    (3, 9, gmls.DIVFREE, 4, 136, [gmls.VEC_LAPLACIAN]),  # 408 x 85: tiles in global memory
 ]
 NAMES = {gmls.GRAD: "grad", gmls.LAPLACIAN: "laplacian", gmls.DIV: "div", gmls.VEC_LAPLACIAN: "vec_laplacian",
          gmls.CURLCURL: "curlcurl"}
