@@ -140,7 +140,7 @@ def set_n_axis(v):
 def run_ours(args, rank, world, local_rank):
     import torch
 
-    from paper_2104_14447_gb300 import build, gmls
+    from paper_2104_14447_gb300 import build, gmls, shard
 
     if rank == 0 or world == 1:
         build.build()
@@ -214,11 +214,7 @@ def run_ours(args, rank, world, local_rank):
     launches = ctx.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kern_ms = [a.elapsed_time(b) for a, b in kev]
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(float(np.sum(step_ms)), dev)
 
     # e2e: the same step through the C ABI from pinned host input to host operators
     x_pin = torch.from_numpy(x_host).pin_memory()
@@ -255,8 +251,58 @@ def run_ours(args, rank, world, local_rank):
                 "pipe": pipe, "flops_per_target": flops / n, "mean_refine_iters": mean_it_df,
                 "peak_source": "unit counts x 2070 MHz (152 SMs x 128 FP32 lanes; FP64 1/64 of that)",
                 "kernel_ms": k_avg * 1e3}
-    targets = n * args.steps * world
-    value = targets / (total_ms * 1e-3)
+    # the same step captured once as a CUDA graph and replayed
+    graph_ms = None
+    if args.graph:
+        gstream = torch.cuda.Stream(dev)
+        gctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30, stream=gstream)
+        with torch.cuda.stream(gstream):
+            ids_g = None
+            ctx_save = ctx
+            # one eager run on this context fills its autotuner cache, then capture
+            for capture in (False, True):
+                if capture:
+                    gctx.capture_begin()
+                cid = gctx.cloud(x_dev)
+                n36 = gctx.neighbors(cid, K_SCALAR, EPS_FACTOR)
+                n48 = gctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+                s_sc = gctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
+                s_df = gctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
+                gctx.assemble_csr(s_sc, gmls.GRAD, out=bufs["grad"])
+                gctx.assemble_csr(s_sc, gmls.DIV, out=bufs["div"])
+                gctx.assemble_csr(s_df, gmls.VEC_LAPLACIAN, out=bufs["vl"])
+                if capture:
+                    gid = gctx.capture_end()
+                    ids_g = (cid, n36, n48, s_sc, s_df)
+                else:
+                    gctx.sync()
+                    for h in (s_df, s_sc, n48, n36, cid):
+                        gctx.release(h)
+            for _ in range(3):
+                gctx.graph_launch(gid)
+            gstream.synchronize()
+            gms = []
+            for s_ in range(args.steps):
+                flush.fill_(s_ & 0xFF)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(gstream)
+                gctx.graph_launch(gid)
+                b.record(gstream)
+                gms.append((a, b))
+            gstream.synchronize()
+            graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gms]))
+            gctx.release(gid)
+            for h in reversed(ids_g):
+                gctx.release(h)
+        gctx.close()
+        del ctx_save
+
+    tune = {}
+    for r in ctx.tune_log():
+        key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m={r['degree']} rows<={r['rows']}"
+        tune.setdefault(key, {})["register" if r["variant"] < 0 else f"{r['variant']} warp(s)/target"] = round(r["ms"], 3)
+
+    value = shard.job_throughput(n, args.steps, world, total_ms)
     out = {
         "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -274,8 +320,98 @@ def run_ours(args, rank, world, local_rank):
         "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
         "roofline": roofline,
         "clocks": clk.summary(),
+        "autotune_ms": tune,
     }
+    if graph_ms is not None:
+        out["graph"] = {"ms_per_step": graph_ms, "targets_per_s": n * world / (graph_ms * 1e-3)}
     return out, ctx
+
+
+SERVE_K = {(2, 0, 2): 12, (2, 0, 3): 20, (2, 0, 4): 36, (2, 1, 2): 22, (2, 1, 3): 34, (2, 1, 4): 48,
+           (3, 0, 2): 20, (3, 0, 3): 40, (3, 0, 4): 84, (3, 1, 2): 42, (3, 1, 3): 80, (3, 1, 4): 136}
+
+
+def serving(n_requests, seed=0):
+    """Poisson arrivals (200 req/s) of stencil requests -- 2D/3D clouds of
+    log-uniform 1e3..5e5 points, degree 2..4, scalar (gradient + Laplacian) or
+    divergence-free (vector Laplacian) basis -- through the continuous-batching
+    server (FP32 + refinement), and the same stream through the plain
+    per-request FP64 path (one request at a time, in arrival order)."""
+    import threading
+
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    reqs = inputs.request_stream(n_requests, 200.0, seed)
+    clouds = []
+    for r in reqs:
+        n_axis = max(3, int(round(r["n"] ** (1.0 / r["dim"]))))
+        clouds.append(inputs.jittered_grid(r["dim"], n_axis, seed=r["seed"]))
+    spec = []
+    for r in reqs:
+        b = gmls.SCALAR if r["basis"] == "scalar" else gmls.DIVFREE
+        fns = [gmls.GRAD, gmls.LAPLACIAN] if b == gmls.SCALAR else [gmls.VEC_LAPLACIAN]
+        spec.append((b, r["degree"], SERVE_K[(r["dim"], b, r["degree"])], fns))
+    total_targets = sum(c.shape[1] for c in clouds)
+    offered = total_targets / max(reqs[-1]["t"], 1e-9)
+
+    def run_server():
+        srv = gmls.Server(torch.cuda.current_device(), arena_bytes=48 << 30, streams=4, max_inflight=8)
+        tickets = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def client():
+            for i, r in enumerate(reqs):
+                dt = r["t"] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                b, m, k, fns = spec[i]
+                tickets[i] = srv.submit(clouds[i], b, m, k, fns, precision=gmls.FP32_REFINE)
+
+        th = threading.Thread(target=client)
+        th.start()
+        pending = set(range(len(reqs)))
+        while pending:
+            for i in list(pending):
+                if tickets[i] is not None and srv.wait(tickets[i], 0):
+                    srv.release(tickets[i])
+                    pending.discard(i)
+            time.sleep(0.0005)
+        th.join()
+        st = srv.stats()
+        srv.close()
+        return st
+
+    def run_plain_fp64():
+        ctx = gmls.Context(torch.cuda.current_device(), arena_bytes=48 << 30)
+        ctx.set_option(gmls.OPT_AUTOTUNE, 0)
+        lat, t0 = [], time.perf_counter()
+        for i, r in enumerate(reqs):
+            dt = r["t"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            b, m, k, fns = spec[i]
+            cid = ctx.cloud(clouds[i])
+            nid = ctx.neighbors(cid, k, 1.5)
+            sid = ctx.stencils(nid, b, m, fns, precision=gmls.FP64)
+            ctx.sync()
+            lat.append((time.perf_counter() - t0 - r["t"]) * 1e3)
+            for h in (sid, nid, cid):
+                ctx.release(h)
+        el = time.perf_counter() - t0
+        ctx.close()
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "targets_per_s": total_targets / el, "elapsed_s": el}
+
+    srv = run_server()
+    plain = run_plain_fp64()
+    return {"requests": n_requests, "rate_per_s": 200.0, "targets": int(total_targets),
+            "offered_targets_per_s": offered,
+            "continuous_batching_fp32_refine": {"p50_ms": srv["p50_ms"], "p99_ms": srv["p99_ms"],
+                                                "targets_per_s": srv["targets_per_s"], "elapsed_s": srv["elapsed_s"]},
+            "plain_per_request_fp64": plain,
+            "note": "bounded sample of the serving stream (first requests of the seeded Poisson sequence)"}
 
 
 def oracle_pipeline(x, targets, threads=None):
@@ -385,6 +521,8 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-axis", type=int, default=512, help="profiling only; the benchmark is 512")
+    ap.add_argument("--serve-requests", type=int, default=60, help="serving sample size (0: skip)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
     args = ap.parse_args()
     set_n_axis(args.n_axis)
     args.warmup = max(args.warmup, 3)
@@ -403,6 +541,8 @@ def main():
     out, ctx = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(ctx)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        out["serving"] = serving(args.serve_requests)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
