@@ -166,8 +166,8 @@ def run_ours(args, rank, world, local_rank):
 
     def step(x_src, k_events=None):
         cid = ctx.cloud(x_src)
-        n36 = ctx.neighbors(cid, K_SCALAR, EPS_FACTOR)
         n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+        n36 = ctx.neighbors_prefix(n48, K_SCALAR, EPS_FACTOR)  # the 36 nearest = first 36 of the 48
         s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
         if k_events:
             k_events[0].record(stream)
@@ -177,7 +177,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.assemble_csr(s_sc, gmls.GRAD, out=bufs["grad"])
         ctx.assemble_csr(s_sc, gmls.DIV, out=bufs["div"])
         ctx.assemble_csr(s_df, gmls.VEC_LAPLACIAN, out=bufs["vl"])
-        return cid, n36, n48, s_sc, s_df
+        return cid, n48, n36, s_sc, s_df
 
     def release(ids):
         for h in reversed(ids):
@@ -264,8 +264,8 @@ def run_ours(args, rank, world, local_rank):
                 if capture:
                     gctx.capture_begin()
                 cid = gctx.cloud(x_dev)
-                n36 = gctx.neighbors(cid, K_SCALAR, EPS_FACTOR)
                 n48 = gctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+                n36 = gctx.neighbors_prefix(n48, K_SCALAR, EPS_FACTOR)
                 s_sc = gctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
                 s_df = gctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
                 gctx.assemble_csr(s_sc, gmls.GRAD, out=bufs["grad"])
@@ -273,10 +273,10 @@ def run_ours(args, rank, world, local_rank):
                 gctx.assemble_csr(s_df, gmls.VEC_LAPLACIAN, out=bufs["vl"])
                 if capture:
                     gid = gctx.capture_end()
-                    ids_g = (cid, n36, n48, s_sc, s_df)
+                    ids_g = (cid, n48, n36, s_sc, s_df)
                 else:
                     gctx.sync()
-                    for h in (s_df, s_sc, n48, n36, cid):
+                    for h in (s_df, s_sc, n36, n48, cid):
                         gctx.release(h)
             for _ in range(3):
                 gctx.graph_launch(gid)
@@ -461,7 +461,7 @@ def gpu_error(ctx, x, res, targets):
     from paper_2104_14447_gb300 import gmls
 
     n = x.shape[1]
-    samp = np.arange(0, len(targets), max(1, len(targets) // 4096))
+    samp = np.arange(len(targets))  # every target the oracle computed
     errs = {}
     cid = ctx.cloud(torch.from_numpy(x).to(ctx.device))
     for key, k, basis, fn in (("grad", K_SCALAR, gmls.SCALAR, gmls.GRAD), ("div", K_SCALAR, gmls.SCALAR, gmls.DIV),

@@ -129,7 +129,8 @@ typedef struct {
   int32_t neumann;            /* 1: targets whose cloud boundary flag is set take the
                                  Neumann constraint n . grad u = h (scalar basis only)       */
   int32_t max_refine;         /* FP32_REFINE: iteration cap (0 = default 3)                  */
-  double refine_tol;          /* FP32_REFINE: stop when |ds|_inf <= tol |s|_inf (0 = 1e-12)  */
+  double refine_tol;          /* FP32_REFINE: stop when the estimated error left, |ds|_inf x
+                                 (contraction estimate), is <= tol |s|_inf (0 = 1e-10)       */
   const int8_t* degree_per_target; /* NULL, or host or device int8 [n_targets], m in 1..4    */
 } gmls_stencil_params;
 
@@ -167,6 +168,15 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
  * byte per target (GMLS_T_TOO_FEW_NEIGHBOURS, GMLS_T_OVERFLOW).
  */
 gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_params* params, int64_t* nbrs_id);
+
+/*
+ * The k nearest neighbours of every target of a fixed-k nearest-neighbour
+ * handle with at least k neighbours, without a new search: under the order by
+ * (d^2, particle id) the k nearest are the first k entries of the longer list,
+ * and eps = eps_factor * (distance of entry k), recomputed with the same
+ * exact formula -- identical to gmls_neighbors(KNN, k, eps_factor).
+ */
+gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, double eps_factor, int64_t* nbrs_id_out);
 
 /*
  * Stencil weights for every target of a neighbour handle.  For functional f

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgmls.so")
-SOURCES = ["capi.cu", "nbr.cu", "stencil.cu", "stencil_fast.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["capi.cu", "nbr.cu", "stencil.cu", "stencil_fast.cu", "noalloc.cu", "serve.cu", "fast_s2a.cu", "fast_s2b.cu",
+           "fast_s2c.cu", "fast_s3a.cu", "fast_s3b.cu", "fast_d2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -60,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)

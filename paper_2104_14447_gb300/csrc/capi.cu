@@ -314,7 +314,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
   const int dim = j.dim;
   int mr = 0;
   const bool fast_ok = refine && (p->weight_power % 2 == 0) && !ctx->force_generic &&
-                       fast_path_available(p->basis, dim, p->degree, ld, &mr);
+                       fast_path_available(p->basis, dim, p->degree, ld, j.L, &mr);
   const TuneKey key{p->basis, dim, p->degree, p->precision, ld, j.L, p->neumann, 0};
   int choice = 0;  // -1 fast kernel, else G
   auto it = ctx->tune.find(key);
@@ -810,6 +810,50 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   return GMLS_OK;
 }
 
+gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, double eps_factor, int64_t* out_id) {
+  if (!ctx) return GMLS_EINVAL;
+  auto it = ctx->objs.find(nbrs_id);
+  if (it == ctx->objs.end() || it->second.kind != K_NBRS)
+    return fail(ctx, GMLS_ENOTFOUND, "gmls_neighbors_prefix: no such neighbour handle");
+  if (!out_id) return fail(ctx, GMLS_EINVAL, "gmls_neighbors_prefix: NULL output");
+  NbrObj& src = it->second.nb;
+  if (src.variable || src.mode != GMLS_NBR_KNN || k < 1 || k > src.k || !(eps_factor > 0.0))
+    return fail(ctx, GMLS_EINVAL, "gmls_neighbors_prefix: needs a fixed-k nearest-neighbour handle and 1 <= k <= its k");
+  CloudObj& c = ctx->objs.at(src.cloud).c;
+  CK(cudaSetDevice(ctx->device), "gmls_neighbors_prefix");
+  Obj o;
+  o.kind = K_NBRS;
+  NbrObj& nb = o.nb;
+  nb.cloud = src.cloud;
+  nb.dim = src.dim;
+  nb.n_tgt = src.n_tgt;
+  nb.mode = GMLS_NBR_KNN;
+  nb.k = k;
+  nb.cap = k;
+  nb.idx_cap = src.n_tgt * (int64_t)k;
+  const int64_t nt = src.n_tgt;
+  nb.tgt = arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1));
+  nb.off = arena_alloc<int64_t>(ctx, nt + 1);
+  nb.idx = arena_alloc<int32_t>(ctx, std::max<int64_t>(nb.idx_cap, 1));
+  nb.eps = arena_alloc<double>(ctx, std::max<int64_t>(nt, 1));
+  nb.status = arena_alloc<uint8_t>(ctx, std::max<int64_t>(nt, 1));
+  if (!nb.tgt || !nb.off || !nb.idx || !nb.eps || !nb.status) {
+    for (void* q : {(void*)nb.tgt, (void*)nb.off, (void*)nb.idx, (void*)nb.eps, (void*)nb.status}) ctx->arena.release(q);
+    return fail(ctx, GMLS_ENOMEM, "gmls_neighbors_prefix: arena exhausted");
+  }
+  Launch L = ctx->launch();
+  CK(cudaMemcpyAsync(nb.tgt, src.tgt, sizeof(int32_t) * nt, cudaMemcpyDeviceToDevice, ctx->stream),
+     "gmls_neighbors_prefix copy");
+  CK(launch_fill_offsets_fixed(L, nb.off, nt, k), "gmls_neighbors_prefix offsets");
+  CK(launch_nbr_prefix(L, c.dim, c.n, c.x, src.tgt, nt, src.idx, src.k, k, eps_factor, nb.idx, nb.eps, nb.status),
+     "gmls_neighbors_prefix");
+  c.refs++;
+  int64_t id = ctx->next_id++;
+  ctx->objs.emplace(id, std::move(o));
+  *out_id = id;
+  return GMLS_OK;
+}
+
 // rows / components of one functional's output
 static bool functional_shape(int basis, int dim, int fn, int* rows, int* ncomp) {
   switch (fn) {
@@ -980,7 +1024,7 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.status = s.status;
   j.iters = s.iters;
   j.max_refine = p->max_refine > 0 ? p->max_refine : 3;
-  j.tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-12;
+  j.tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-10;
   j.fb_items = s.fb_items;
   j.fb_count = s.fb_count;
   j.ld = ld;

@@ -100,6 +100,9 @@ cudaError_t launch_fill_offsets_fixed(const Launch& L, int64_t* off, int64_t n_t
 cudaError_t launch_compact_padded(const Launch& L, const int32_t* padded, int cap, const int32_t* cnt,
                                   const int64_t* off, int32_t* out, int64_t n_tgt);
 cudaError_t launch_fill_identity(const Launch& L, int32_t* out, int64_t n);
+cudaError_t launch_nbr_prefix(const Launch& L, int dim, int64_t n, const double* x, const int32_t* tgt, int64_t n_tgt,
+                              const int32_t* idx, int k, int kp, double eps_factor, int32_t* out_idx, double* out_eps,
+                              uint8_t* out_status);
 
 // ----------------------------------------------------------------- stencils
 struct StencilJob {
@@ -199,7 +202,7 @@ int stencil_blocks_per_sm(bool fp32_refine, size_t smem);
 cudaError_t launch_stencils(const Launch& L, const StencilJob& j, const BatchPlan& plan, bool fp32_refine,
                             size_t smem, int grid_blocks);
 cudaError_t launch_bucketing(const Launch& L, const BucketJob& b);
-bool fast_path_available(int kind, int dim, int deg, int rows, int* mr_out);
+bool fast_path_available(int kind, int dim, int deg, int rows, int L, int* mr_out);
 cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int sms);
 cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count);
 

@@ -271,12 +271,28 @@ cudaError_t launch_scan_i64_from_i32(const Launch& L, const int32_t* in, int64_t
 // ------------------------------------------------------------- neighbour query
 constexpr int kQueryWarps = 4;
 
+// Per-warp candidate buffer in shared memory: cap entries of (d2, id) plus the
+// row table of the current cell rows.  cap is a power of two chosen per launch
+// (about twice k for k-nearest queries), so small k keeps many warps resident.
 struct WarpBuf {
-  double d2[kNbrCap];
-  int32_t id[kNbrCap];
-  int32_t row_begin[32];
-  int32_t row_end[32];  // inclusive scan of row lengths
+  double* d2;
+  int32_t* id;
+  int32_t* row_begin;
+  int32_t* row_end;  // inclusive scan of row lengths
+  int cap;
 };
+
+__host__ __device__ inline size_t warpbuf_bytes(int cap) { return (size_t)cap * 12 + 256; }
+
+__device__ inline WarpBuf warpbuf_at(unsigned char* base, int cap) {
+  WarpBuf w;
+  w.d2 = reinterpret_cast<double*>(base);
+  w.id = reinterpret_cast<int32_t*>(base + (size_t)cap * 8);
+  w.row_begin = reinterpret_cast<int32_t*>(base + (size_t)cap * 12);
+  w.row_end = w.row_begin + 32;
+  w.cap = cap;
+  return w;
+}
 
 // Collect every particle with d2 < R2 (after the optional half-space filter)
 // from the cells overlapping [x_T - R, x_T + R] into the warp's buffer.
@@ -336,7 +352,7 @@ __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const 
       unsigned m = __ballot_sync(0xffffffffu, pass);
       if (pass) {
         int slot = count + __popc(m & ((1u << lane) - 1u));
-        if (slot < kNbrCap) {
+        if (slot < wb.cap) {
           wb.d2[slot] = d2;
           wb.id[slot] = j;
         }
@@ -379,9 +395,9 @@ __device__ void warp_sort_candidates(WarpBuf& wb, int count) {
   }
 }
 
-__global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q) {
+__global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q, int buf_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpBuf& wb = reinterpret_cast<WarpBuf*>(smem_raw)[threadIdx.x >> 5];
+  WarpBuf wb = warpbuf_at(smem_raw + (size_t)(threadIdx.x >> 5) * warpbuf_bytes(buf_cap), buf_cap);
   const int lane = threadIdx.x & 31;
   const CloudDev& cl = q.cloud;
   const GridParams g = *cl.grid;
@@ -410,7 +426,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
     int count = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
       count = gather_candidates(cl, g, xT, R, __dmul_rn(R, R), use_hs, nrm, wb);
-      if (count > kNbrCap) {
+      if (count > wb.cap) {
         R *= 0.75;
         continue;
       }
@@ -418,9 +434,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
       if (R > 2.0 * span + 1.0) break;  // whole cloud inside: too few exist
       R *= 1.6;
     }
-    if (count > kNbrCap) {  // could not bring the candidate set under the cap
+    if (count > wb.cap) {  // could not bring the candidate set under the buffer size
       st |= GMLS_T_OVERFLOW;
-      count = kNbrCap;
+      count = wb.cap;
     }
     if (count < kq) st |= GMLS_T_TOO_FEW_NEIGHBOURS;
     warp_sort_candidates(wb, count);
@@ -437,9 +453,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
       if (kk == kq) {
         __syncwarp();
         count = gather_candidates(cl, g, xT, eps, __dmul_rn(eps, eps), use_hs, nrm, wb);
-        if (count > kNbrCap) {
+        if (count > wb.cap) {
           st |= GMLS_T_OVERFLOW;
-          count = kNbrCap;
+          count = wb.cap;
         }
         warp_sort_candidates(wb, count);
         keep = count < q.cap ? count : q.cap;
@@ -457,16 +473,18 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q)
 
 cudaError_t launch_nbr_query(const Launch& L, const NbrQuery& q) {
   if (q.n_tgt == 0) return cudaSuccess;
-  const size_t smem = sizeof(WarpBuf) * kQueryWarps;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(nbr_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // candidate buffer: about twice k for k-nearest lists (a fuller buffer only
+  // triggers a smaller search radius), the full 1024 for radius lists, which
+  // must hold every candidate inside eps
+  int cap = 64;
+  const int want = q.mode == GMLS_NBR_KNN ? 2 * q.k : kNbrCap;
+  while (cap < want && cap < kNbrCap) cap <<= 1;
+  const size_t smem = warpbuf_bytes(cap) * kQueryWarps;
+  cudaError_t e = cudaFuncSetAttribute(nbr_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int64_t blocks = (q.n_tgt + kQueryWarps - 1) / kQueryWarps;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  nbr_query_kernel<<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q);
+  nbr_query_kernel<<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q, cap);
   *L.counter += 1;
   return cudaGetLastError();
 }
@@ -489,6 +507,44 @@ __global__ void fill_identity_kernel(int32_t* out, int64_t n) {
 
 cudaError_t launch_fill_identity(const Launch& L, int32_t* out, int64_t n) {
   fill_identity_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(out, n);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+// The k' nearest of a target are the first k' entries of its k-nearest list
+// (both are prefixes of one total order by (d^2, id)); eps' = f * sqrt(d^2 of
+// entry k'-1), with d^2 recomputed by the search's exact formula.
+__global__ void nbr_prefix_kernel(int dim, int64_t n, const double* __restrict__ x, const int32_t* __restrict__ tgt,
+                                  int64_t n_tgt, const int32_t* __restrict__ idx, int k, int kp, double eps_factor,
+                                  int32_t* __restrict__ out_idx, double* __restrict__ out_eps,
+                                  uint8_t* __restrict__ out_status) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n_tgt;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t* src = idx + t * k;
+    for (int i = lane; i < kp; i += 32) out_idx[t * kp + i] = src[i];
+    if (lane == 0) {
+      const int32_t last = src[kp - 1];
+      if (last < 0) {
+        out_eps[t] = 0.0;
+        out_status[t] = GMLS_T_TOO_FEW_NEIGHBOURS;
+      } else {
+        const int64_t tt = tgt[t];
+        double dx[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < dim; ++c) dx[c] = __dsub_rn(x[c * n + last], x[c * n + tt]);
+        out_eps[t] = __dmul_rn(eps_factor, __dsqrt_rn(exact_d2(dim, dx)));
+        out_status[t] = 0;
+      }
+    }
+  }
+}
+
+cudaError_t launch_nbr_prefix(const Launch& L, int dim, int64_t n, const double* x, const int32_t* tgt, int64_t n_tgt,
+                              const int32_t* idx, int k, int kp, double eps_factor, int32_t* out_idx, double* out_eps,
+                              uint8_t* out_status) {
+  if (n_tgt == 0) return cudaSuccess;
+  nbr_prefix_kernel<<<blocks_for(n_tgt * 32, 256), 256, 0, L.stream>>>(dim, n, x, tgt, n_tgt, idx, k, kp, eps_factor,
+                                                                        out_idx, out_eps, out_status);
   *L.counter += 1;
   return cudaGetLastError();
 }

@@ -498,8 +498,11 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
           }
         }
         used_iters = iter + 1;
-        // error after this correction ~ |ds| times the contraction |ds|/|ds_prev|
-        const float est = (iter == 0) ? dmax : dmax * fminf(1.0f, dmax / fmaxf(prev, 1e-37f));
+        // error left after this correction ~ |ds| times the contraction factor,
+        // estimated by the relative size of the correction (first iteration)
+        // or by the ratio of successive corrections (later ones)
+        const float rho = (iter == 0) ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
+        const float est = dmax * fminf(1.0f, rho);
         conv = (double)est <= j.tol * (double)smax;
         prev = dmax;
         group_sync(g.gid, g.nthr);

@@ -35,7 +35,8 @@ FP64, FP32_REFINE = 0, 1
 X_NBR_OFFSETS, X_NBR_INDEX, X_NBR_EPS, X_NBR_STATUS, X_WEIGHTS, X_BETA, X_STATUS, X_ITERS = range(8)
 
 EXPORTED = [
-    "gmls_create", "gmls_destroy", "gmls_set_stream", "gmls_cloud", "gmls_neighbors", "gmls_stencils",
+    "gmls_create", "gmls_destroy", "gmls_set_stream", "gmls_cloud", "gmls_neighbors", "gmls_neighbors_prefix",
+    "gmls_stencils",
     "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_export", "gmls_export_size", "gmls_release",
     "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
     "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "gmls_set_stream": [vp, vp],
         "gmls_cloud": [vp, ctypes.c_int, i64, vp, vp, vp, P64],
         "gmls_neighbors": [vp, i64, ctypes.POINTER(NbrParams), P64],
+        "gmls_neighbors_prefix": [vp, i64, i32, ctypes.c_double, P64],
         "gmls_stencils": [vp, i64, ctypes.POINTER(StencilParams), P64],
         "gmls_stencil_info": [vp, i64, i32, P64, ctypes.POINTER(i32), ctypes.POINTER(i32), P64],
         "gmls_csr_size": [vp, i64, i32, P64, P64, P64],
@@ -200,6 +202,12 @@ class Context:
         out = ctypes.c_int64()
         self._check(self.lib.gmls_neighbors(self.h, cloud, ctypes.byref(p), ctypes.byref(out)))
         self._keep[out.value] = (tg, hs, kp)
+        return out.value
+
+    def neighbors_prefix(self, nbrs: int, k: int, eps_factor: float) -> int:
+        """k-nearest lists as prefixes of a longer k-nearest handle (gmls_neighbors_prefix)."""
+        out = ctypes.c_int64()
+        self._check(self.lib.gmls_neighbors_prefix(self.h, nbrs, k, eps_factor, ctypes.byref(out)))
         return out.value
 
     def stencils(self, nbrs: int, basis: int, degree: int, functionals, precision: int = FP64,

@@ -67,6 +67,18 @@ def test_knn_bit_exact(ctx, dim, n_axis, k, jitter):
     _release(ctx, cid, nid)
 
 
+def test_prefix_equals_direct_search(ctx):
+    x = inputs.jittered_grid(2, 64, seed=6)
+    cid = ctx.cloud(x)
+    n48 = ctx.neighbors(cid, 48, 1.5)
+    direct = ctx.neighbors(cid, 36, 1.5)
+    pref = ctx.neighbors_prefix(n48, 36, 1.5)
+    for what, dt in ((gmls.X_NBR_INDEX, torch.int32), (gmls.X_NBR_EPS, torch.float64),
+                     (gmls.X_NBR_STATUS, torch.uint8), (gmls.X_NBR_OFFSETS, torch.int64)):
+        assert torch.equal(ctx.export(pref, what, dt), ctx.export(direct, what, dt))
+    _release(ctx, cid, n48, direct, pref)
+
+
 def test_knn_halfspace_and_subset_targets(ctx):
     x = inputs.jittered_grid(2, 48, seed=4)
     n = x.shape[1]
