@@ -184,9 +184,9 @@ def gen():
                 if kind == "scalar":
                     grad = [[1 if g == tuple(int(j == k) for j in range(3)) else 0 for g in mons] for k in range(d)]
                     lap = [[1 if (sum(g) == 2 and max(g) == 2) else 0 for g in mons]]
-                    L.append(f"__device__ constexpr double lam_grad_{name}[{d}][{nb}] = {{" + ", ".join(
+                    L.append(f"__device__ constexpr float lam_grad_{name}[{d}][{nb}] = {{" + ", ".join(
                         "{" + ", ".join(f"{v}.0" for v in row) + "}" for row in grad) + "};")
-                    L.append(f"__device__ constexpr double lam_lap_{name}[1][{nb}] = {{" + ", ".join(
+                    L.append(f"__device__ constexpr float lam_lap_{name}[1][{nb}] = {{" + ", ".join(
                         "{" + ", ".join(f"{v}.0" for v in row) + "}" for row in lap) + "};")
                 else:
                     idx2 = [mons.index(e) for e in (tuple(2 * int(j == k) for j in range(3)) for k in range(d)) if e in mons]
@@ -197,7 +197,8 @@ def gen():
                             s = sum((a for (cc, mi, a) in f if cc == c and mi in idx2), Fraction(0))
                             row.append(s)
                         vlap.append(row)
-                    L.append(f"__device__ constexpr double lam_vlap_{name}[{d}][{nb}] = {{" + ", ".join(
+                    assert all(v.denominator == 1 and abs(v.numerator) < 2 ** 24 for row in vlap for v in row)
+                    L.append(f"__device__ constexpr float lam_vlap_{name}[{d}][{nb}] = {{" + ", ".join(
                         "{" + ", ".join(cnum(v) for v in row) + "}" for row in vlap) + "};")
                 L.append("")
     L.append("}  // namespace gmls_gen")
@@ -232,17 +233,24 @@ def gen():
     L.append("// functional row coefficient (before the eps^{-|beta|} factor)")
     L.append("// fn: 0 grad (d rows), 1 laplacian (1 row), 2 vector Laplacian (d rows),")
     L.append("//     3 curl curl (d rows), 4 divergence of a div-free field (1 row, zero)")
-    L.append("__device__ __forceinline__ double lam_coef(int kind, int d, int m, int fn, int row, int i) {")
+    L.append("__device__ __forceinline__ float lam_coef_raw(int kind, int d, int m, int fn, int row, int i) {")
     L.append("  switch (kind * 100 + d * 10 + m) {")
     for kind, d, m, nb, nc, _ in summary:
         name = f"{kind}_{d}d_m{m}"
         key = (0 if kind == "scalar" else 1) * 100 + d * 10 + m
         if kind == "scalar":
-            L.append(f"    case {key}: return fn == 0 ? lam_grad_{name}[row][i] : fn == 1 ? lam_lap_{name}[0][i] : 0.0;")
+            L.append(f"    case {key}: return fn == 0 ? lam_grad_{name}[row][i] : fn == 1 ? lam_lap_{name}[0][i] : 0.0f;")
         else:
-            L.append(f"    case {key}: return fn == 2 ? lam_vlap_{name}[row][i] : fn == 3 ? -lam_vlap_{name}[row][i] : 0.0;")
-    L.append("    default: return 0.0;")
+            L.append(f"    case {key}: return fn == 2 ? lam_vlap_{name}[row][i] : fn == 3 ? -lam_vlap_{name}[row][i] : 0.0f;")
+    L.append("    default: return 0.0f;")
     L.append("  }")
+    L.append("}")
+    L.append("// every coefficient is a small integer: exact in FP32 and in FP64")
+    L.append("__device__ __forceinline__ float lam_coef_f(int kind, int d, int m, int fn, int row, int i) {")
+    L.append("  return lam_coef_raw(kind, d, m, fn, row, i);")
+    L.append("}")
+    L.append("__device__ __forceinline__ double lam_coef(int kind, int d, int m, int fn, int row, int i) {")
+    L.append("  return (double)lam_coef_raw(kind, d, m, fn, row, i);")
     L.append("}")
     L.append("}  // namespace gmls_gen")
     return "\n".join(L) + "\n", summary

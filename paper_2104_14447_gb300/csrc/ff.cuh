@@ -93,7 +93,22 @@ __device__ __forceinline__ ff sqrt_ff(ff a) {
   return quick_two_sum(s, c);
 }
 
-__device__ __forceinline__ double to_double(ff a) { return (double)a.h + (double)a.l; }
+// float -> double by re-biasing the exponent field with integer ops (exact for
+// normal floats and zeros; denormals and inf/nan take the conversion
+// instruction), so that the float-float -> FP64 store costs one FP64 add
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
+    return (double)f;
+  }
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double to_double(ff a) { return f2d_exact(a.h) + f2d_exact(a.l); }
 
 // (a_h + a_l) - (b_h + b_l) for coordinates stored as float pairs
 __device__ __forceinline__ ff sub_pair(float ah, float al, float bh, float bl) {

@@ -36,10 +36,20 @@ __device__ __forceinline__ double exact_dot(int dim, const double* nrm, const do
   return s;
 }
 
-// candidate order: by d2, then by particle id
+// candidate order: by d2, then by particle id.  Squared distances are
+// non-negative (never -0), and for non-negative doubles the IEEE bit patterns
+// order exactly like the values, so the order is decided with 64-bit integer
+// compares on the ALU instead of FP64 compares on GB300's narrow FP64 pipe.
 __device__ __forceinline__ bool cand_less(double da, int32_t ia, double db, int32_t ib) {
-  return (da < db) || (da == db && ia < ib);
+  const long long ua = __double_as_longlong(da), ub = __double_as_longlong(db);
+  return (ua < ub) || (ua == ub && ia < ib);
 }
+// a < b for non-negative doubles, as an integer compare
+__device__ __forceinline__ bool nonneg_less(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+// s <= 0 (including -0) as a signed integer test of the bit pattern
+__device__ __forceinline__ bool nonpositive(double s) { return __double_as_longlong(s) <= 0; }
 
 // ----------------------------------------------------------------- grid state
 struct GridParams {

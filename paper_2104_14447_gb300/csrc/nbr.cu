@@ -345,8 +345,8 @@ __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const 
         double dx[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < dim; ++c) dx[c] = __dsub_rn(cl.xs[c * cl.n + pos], xT[c]);
         d2 = exact_d2(dim, dx);
-        pass = d2 < R2;
-        if (pass && use_hs) pass = exact_dot(dim, nrm, dx) <= 0.0;
+        pass = nonneg_less(d2, R2);
+        if (pass && use_hs) pass = nonpositive(exact_dot(dim, nrm, dx));
         j = cl.sorted[pos];
       }
       unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
   // unit-ball volume and the initial radius: about 1.5 k particles expected
   const double ball = (dim == 1) ? 2.0 : (dim == 2) ? 3.141592653589793 : 4.1887902047863905;
   const double dens = (double)cl.n / (g.volume > 0.0 ? g.volume : 1.0);
+  const float inv_dens_ball = (float)(1.0 / (dens * ball));
   double span = 0.0;
   for (int c = 0; c < dim; ++c) span += g.h[c] * g.nc[c];
   for (int64_t to = blockIdx.x * (int64_t)kQueryWarps + (threadIdx.x >> 5); to < q.n_tgt;
@@ -422,7 +423,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     uint8_t st = GMLS_T_OK;
     int kq = q.k_pt ? q.k_pt[to] : q.k;  // per-target k is clamped to 1..cap
     kq = kq < 1 ? 1 : (kq > q.cap ? q.cap : kq);
-    double R = pow(1.5 * kq / (dens * ball), 1.0 / dim);
+    // initial radius: any value is correct (the search widens or narrows it);
+    // computed in FP32 to keep the FP64 pipe for the exact distances
+    double R = (double)powf(1.5f * (float)kq * inv_dens_ball, 1.0f / (float)dim);
     int count = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
       count = gather_candidates(cl, g, xT, R, __dmul_rn(R, R), use_hs, nrm, wb);

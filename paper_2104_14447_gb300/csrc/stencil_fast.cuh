@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
   ff* PARTs = reinterpret_cast<ff*>(base + Lay::PART);
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
+  const float tolf = (float)j.tol;
 
   for (int64_t it = (int64_t)blockIdx.x * wpb + warp; it < n_items; it += (int64_t)gridDim.x * wpb) {
     const int64_t to = j.items ? (int64_t)j.items[it] : it;
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
     // functional rows (float-float), lanes over (row, column)
     for (int e = lane; e < L * N; e += 32) {
       const int l = e / N, i = e % N;
-      ff f = ff(gmls_gen::lam_coef(KIND, D, DEG, j.lam_fn[l], j.lam_row[l], i));
+      ff f(gmls_gen::lam_coef_f(KIND, D, DEG, j.lam_fn[l], j.lam_row[l], i), 0.0f);
       for (int p = 0; p < j.lam_order[l]; ++p) f = f * inv_eps;
       LAMs[l * N + i] = f;
     }
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
       // by the ratio of successive corrections (later ones)
       const float rho = (iter == 0) ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
       const float est = dmax * fminf(1.0f, rho);
-      conv = (double)est <= j.tol * (double)smax;
+      conv = est <= tolf * smax;
       prev = dmax;
       if (conv) break;
     }
