@@ -26,6 +26,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "basis_tables.cuh"
 #include "ff.cuh"
 #include "gmls_internal.cuh"
@@ -63,6 +65,107 @@ __device__ __forceinline__ float wmax(float v) {
 
 // apply Q (REV: H_0 ... H_{N-1} z, i.e. reflectors in reverse order) or Q^T
 // to the row-distributed vectors z[l][i], l < L
+// All-reduce over the warp of v[B..N) (compile-time range): recursive halving
+// (each lane keeps the half of the values picked by its lane bit and adds its
+// partner's copy of that half) until every lane holds one total, butterflies
+// over the remaining lanes, then a broadcast of each total.  About 2(N - B)
+// shuffles instead of 5(N - B) for independent butterflies.
+template <int N, int B>
+__device__ __forceinline__ void allreduce_tail(float (&v)[N], int lane) {
+  constexpr int C = N - B;
+  if constexpr (C <= 0) {
+    return;
+  } else if constexpr (C <= 2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = B; c < N; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+  } else {
+    constexpr int P = C <= 4 ? 4 : C <= 8 ? 8 : C <= 16 ? 16 : 32;
+    float w[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) w[i] = (i < C) ? v[B + (i < C ? i : 0)] : 0.0f;
+    // halving: stage with offset o keeps P/2^s values; the kept half is the
+    // upper one on lanes whose bit o is set
+    int m = P;
+#pragma unroll
+    for (int o = 16; o > 0 && m > 1; o >>= 1) {
+      const bool up = (lane & o) != 0;
+      const int h = m >> 1;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (i < h) {
+          const float send = up ? w[i] : w[i + h];
+          const float keep = up ? w[i + h] : w[i];
+          w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+      m = h;
+    }
+    // lanes sharing a value index add up across the remaining lane bits
+    constexpr int used = P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5;  // stages done
+#pragma unroll
+    for (int o = 16 >> used; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+    // value index held by a lane: its top `used` bits (offsets 16, 8, ...)
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      // the lane whose top bits spell i (others bits zero) holds total i
+      const int src = i << (5 - used);
+      v[B + i] = __shfl_sync(0xffffffffu, w[0], src);
+    }
+  }
+}
+
+// One Householder step on column KC of the register tile: reflector from
+// rows > KC, then the trailing columns (dot products all-reduced together).
+template <int MR, int N, int KC>
+__device__ __forceinline__ void qr_column(float (&a)[MR][N], float* tau, int lane) {
+  float sig = 0.0f;
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+    if (lane + 32 * i > KC) sig = fmaf(a[i][KC], a[i][KC], sig);
+  sig = wsum(sig);
+  const float alpha = __shfl_sync(0xffffffffu, a[KC / 32][KC], KC % 32);
+  float tk = 0.0f, beta = alpha;
+  if (sig > 0.0f) {
+    const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+    beta = alpha >= 0.0f ? -nrm : nrm;
+    const float scale = 1.0f / (alpha - beta);
+    tk = (beta - alpha) / beta;
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+      if (lane + 32 * i > KC) a[i][KC] *= scale;
+  }
+  if (lane == KC % 32) a[KC / 32][KC] = beta;
+  if (lane == 0) tau[KC] = tk;
+  float v[MR];
+#pragma unroll
+  for (int i = 0; i < MR; ++i) {
+    const int r = lane + 32 * i;
+    v[i] = (r > KC) ? a[i][KC] : (r == KC ? 1.0f : 0.0f);
+  }
+  float dots[N];
+#pragma unroll
+  for (int c = KC + 1; c < N; ++c) {
+    float p = 0.0f;
+#pragma unroll
+    for (int i = 0; i < MR; ++i) p = fmaf(v[i], a[i][c], p);
+    dots[c] = p;
+  }
+  allreduce_tail<N, KC + 1>(dots, lane);
+#pragma unroll
+  for (int c = KC + 1; c < N; ++c) {
+    const float tc = dots[c] * tk;
+#pragma unroll
+    for (int i = 0; i < MR; ++i) a[i][c] = fmaf(-tc, v[i], a[i][c]);
+  }
+}
+
+template <int MR, int N, int... K>
+__device__ __forceinline__ void qr_columns(float (&a)[MR][N], float* tau, int lane, std::integer_sequence<int, K...>) {
+  (qr_column<MR, N, K>(a, tau, lane), ...);
+}
+
 template <int MR, int N, int L, bool REV>
 __device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const float* tau, float (&z)[L][MR], int lane) {
 #pragma unroll
@@ -256,51 +359,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
     for (int i = 0; i < MR; ++i)
 #pragma unroll
       for (int c = 0; c < N; ++c) a[i][c] = Bs[c * LD + lane + 32 * i].h;
-#pragma unroll
-    for (int kc = 0; kc < N; ++kc) {
-      float sig = 0.0f;
-#pragma unroll
-      for (int i = 0; i < MR; ++i)
-        if (lane + 32 * i > kc) sig = fmaf(a[i][kc], a[i][kc], sig);
-      sig = wsum(sig);
-      const float alpha = __shfl_sync(0xffffffffu, a[kc / 32][kc], kc % 32);
-      float tk = 0.0f, beta = alpha;
-      if (sig > 0.0f) {
-        const float nrm = sqrtf(fmaf(alpha, alpha, sig));
-        beta = alpha >= 0.0f ? -nrm : nrm;
-        const float scale = 1.0f / (alpha - beta);
-        tk = (beta - alpha) / beta;
-#pragma unroll
-        for (int i = 0; i < MR; ++i)
-          if (lane + 32 * i > kc) a[i][kc] *= scale;
-      }
-      if (lane == kc % 32) a[kc / 32][kc] = beta;
-      if (lane == 0) TAUs[kc] = tk;
-      float v[MR];
-#pragma unroll
-      for (int i = 0; i < MR; ++i) {
-        const int r = lane + 32 * i;
-        v[i] = (r > kc) ? a[i][kc] : (r == kc ? 1.0f : 0.0f);
-      }
-      float dots[N];
-#pragma unroll
-      for (int c = kc + 1; c < N; ++c) {
-        float p = 0.0f;
-#pragma unroll
-        for (int i = 0; i < MR; ++i) p = fmaf(v[i], a[i][c], p);
-        dots[c] = p;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int c = kc + 1; c < N; ++c) dots[c] += __shfl_xor_sync(0xffffffffu, dots[c], o);
-#pragma unroll
-      for (int c = kc + 1; c < N; ++c) {
-        const float tc = dots[c] * tk;
-#pragma unroll
-        for (int i = 0; i < MR; ++i) a[i][c] = fmaf(-tc, v[i], a[i][c]);
-      }
-    }
+    qr_columns<MR, N>(a, TAUs, lane, std::make_integer_sequence<int, N>{});
     // stage R, 1/r_ii; conditioning of the factor
     float rmax = 0.0f, rmin = 3.0e38f;
 #pragma unroll
@@ -380,13 +439,19 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
         const int pairs = L * N, full = pairs / 32, rem = pairs % 32;
         for (int u = 0; u < full; ++u) {
           const int e = u * 32 + lane, l = e / N, c = e % N;
-          Dot2 acc;
-          acc.init(LAMs[l * N + c]);
+          // four independent compensated chains over interleaved rows (ILP)
+          Dot2 acc[4];
+          acc[0].init(LAMs[l * N + c]);
           const ff* bc = Bs + c * LD;
           const ff* sl = Ss + l * LD;
-#pragma unroll 4
-          for (int r = 0; r < ROWS; ++r) acc.add_prod(-bc[r], sl[r]);
-          Gs[l * N + c] = __fadd_rn(acc.h, acc.l);
+#pragma unroll 2
+          for (int r = 0; r < ROWS; r += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (r + q < ROWS) acc[q].add_prod(-bc[r + q], sl[r + q]);
+          }
+          const ff tot = (acc[0].value() + acc[1].value()) + (acc[2].value() + acc[3].value());
+          Gs[l * N + c] = __fadd_rn(tot.h, tot.l);
         }
         if (rem) {
           const int nblk = 32 / rem, chunk = (ROWS + nblk - 1) / nblk;
