@@ -25,6 +25,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -61,6 +62,14 @@ P64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 DOT2_FLOPS = 15
 
 
+# DRAM bytes (read + write) per target of the divergence-free register-kernel
+# launch, from ncu on the 384 x 384 grid (147,456 targets: 33.96 MB read,
+# 168.97 MB written); the algorithmic floor is the 1,536 B of FP64 weights
+# per target (2 rows x 48 neighbours x 2 components), some of which is still
+# in L2 when the kernel ends
+DIVFREE_DRAM_BYTES_PER_TARGET = (33.957120e6 + 168.969728e6) / 147456
+
+
 def flops_per_target(M, n, rows, iters):
     """Algorithmic FP32 flops of one target of the float-float kernel:
     QR 2Mn^2 - 2n^3/3; per functional row the initial solve (2n^2 triangular +
@@ -83,8 +92,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gmls_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -246,7 +254,10 @@ def run_ours(args, rank, world, local_rank):
         flops, peak, pipe = n * f64, P64_TFLOPS, "fp64"
     achieved = flops / k_avg / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "stencil_fast_kernel<divfree, 2D, m=4> (96x20 systems)"
+                "traffic": n * DIVFREE_DRAM_BYTES_PER_TARGET if prec == gmls.FP32_REFINE else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
+                                  "384 x 384 grid, per target, times the targets of this launch",
+                "kernel": "stencil_fast_kernel<divfree, 2D, m=4> (96x20 systems)"
                 if prec == gmls.FP32_REFINE else "stencil_kernel<double> (96x20 systems)",
                 "pipe": pipe, "flops_per_target": flops / n, "mean_refine_iters": mean_it_df,
                 "peak_source": "unit counts x 2070 MHz (152 SMs x 128 FP32 lanes; FP64 1/64 of that)",

@@ -291,16 +291,17 @@ gmls_status gmls_capture_end(gmls_ctx* ctx, int64_t* graph_id);
 gmls_status gmls_graph_launch(gmls_ctx* ctx, int64_t graph_id);
 
 /*
- * Continuous-batching request server (the benchmark spec's serving pattern; the
- * paper has no serving layer).  A scheduler thread admits submitted requests
- * whenever an in-flight slot and a slice of the server arena (first-fit, sized
- * from the request) are free, and issues each request's pipeline -- cloud and
- * cell list, k-nearest neighbours, stencils -- on the least loaded of
- * n_streams CUDA streams, so concurrent requests overlap on the GPU.  Results
- * stay on the device until gmls_server_release.  Each request runs in its own
- * context with a fixed kernel choice per shape (no autotuning), so its result
- * is bit-for-bit the same alone or in the mix.  The arena is a caller-owned
- * device buffer; the server never calls cudaMalloc.  Latency = submit to
+ * Continuous-batching request server (a stream of independent stencil
+ * requests of mixed sizes; the paper has no serving layer).  A scheduler
+ * thread admits submitted requests whenever an in-flight slot and a slice of
+ * the server arena (first-fit, sized from the request) are free, and issues
+ * each request's pipeline -- cloud and cell list, k-nearest neighbours,
+ * stencils -- on the least loaded of n_streams CUDA streams, so concurrent
+ * requests overlap on the GPU.  Results stay on the device until
+ * gmls_server_release.  Each request runs in its own context with a fixed
+ * kernel choice per shape (no autotuning), so its result is bit-for-bit the
+ * same alone or in the mix.  The arena is a caller-owned device buffer; the
+ * server never calls cudaMalloc.  Latency = submit to
  * completion of the request's last kernel (host steady clock).
  */
 typedef struct gmls_server gmls_server;
