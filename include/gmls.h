@@ -254,7 +254,7 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
  * [n], out_status [n] (GMLS_T_* bits).  xyz (FP64 SoA [dim][n]) and the
  * outputs are caller-owned DEVICE buffers; work is queued on cuda_stream.
  * No context is needed and nothing is allocated or freed: the cell-list
- * scratch is one static device array of about 11 MB that every GPU loading
+ * scratch is one static device array of about 14 MB that every GPU loading
  * the library holds until exit, sized for at most GMLS_NOALLOC_MAX_POINTS
  * particles (GMLS_EINVAL beyond that, message in gmls_last_error(NULL)).
  * All calls on a device share that array and it keeps the last call's

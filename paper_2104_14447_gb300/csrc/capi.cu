@@ -93,6 +93,7 @@ struct CloudObj {
   double* normals = nullptr;
   uint8_t* bflag = nullptr;
   double* xs = nullptr;
+  float* xsf = nullptr;  // fl32 of xs
   int32_t* sorted = nullptr;
   int32_t* cell_start = nullptr;
   GridParams* grid = nullptr;
@@ -675,6 +676,7 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   c.xh = arena_alloc<float>(ctx, (size_t)dim * n);
   c.xl = arena_alloc<float>(ctx, (size_t)dim * n);
   c.xs = arena_alloc<double>(ctx, (size_t)dim * n);
+  c.xsf = arena_alloc<float>(ctx, (size_t)dim * n);
   c.sorted = arena_alloc<int32_t>(ctx, n);
   c.cell_start = arena_alloc<int32_t>(ctx, ncell + 1);
   c.grid = arena_alloc<GridParams>(ctx, 1);
@@ -685,7 +687,7 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   int32_t* counts = arena_alloc<int32_t>(ctx, ncell);
   int32_t* fill = arena_alloc<int32_t>(ctx, ncell);
   int32_t* scan_tmp = arena_alloc<int32_t>(ctx, scan_elems);
-  void* all[] = {c.x, c.xh, c.xl, c.xs, c.sorted, c.cell_start, c.grid, part, cell_of, counts, fill, scan_tmp};
+  void* all[] = {c.x, c.xh, c.xl, c.xs, c.xsf, c.sorted, c.cell_start, c.grid, part, cell_of, counts, fill, scan_tmp};
   bool oom = false;
   for (void* p : all) oom |= (p == nullptr);
   oom |= (normals && !c.normals) || (bflags && !c.bflag);
@@ -705,7 +707,7 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   CK(launch_bbox_and_grid(L, dim, n, c.x, nc_axis, c.grid, part, n_part), "gmls_cloud bbox");
   CK(launch_cell_count(L, dim, n, c.x, c.grid, cell_of, counts), "gmls_cloud count");
   CK(launch_scan_i32(L, counts, c.cell_start, ncell, scan_tmp, scan_elems), "gmls_cloud scan");
-  CK(launch_cell_scatter(L, dim, n, c.x, cell_of, c.cell_start, fill, c.sorted, c.xs), "gmls_cloud scatter");
+  CK(launch_cell_scatter(L, dim, n, c.x, cell_of, c.cell_start, fill, c.sorted, c.xs, c.xsf), "gmls_cloud scatter");
   ctx->arena.release(part);
   ctx->arena.release(cell_of);
   ctx->arena.release(counts);
@@ -778,7 +780,7 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   if (hs) CK(copy_in(ctx, hs, p->halfspace, sizeof(double) * nt * c.dim), "gmls_neighbors copy halfspace");
   if (kpt) CK(copy_in(ctx, kpt, p->k_per_target, sizeof(int32_t) * nt), "gmls_neighbors copy k");
   NbrQuery q;
-  q.cloud = CloudDev{c.dim, c.n, c.x, c.xs, c.sorted, c.cell_start, c.grid, c.ncell};
+  q.cloud = CloudDev{c.dim, c.n, c.x, c.xs, c.sorted, c.cell_start, c.grid, c.ncell, c.xsf, c.xh};
   q.n_tgt = nt;
   q.tgt = nb.tgt;
   q.halfspace = hs;
@@ -1203,7 +1205,7 @@ gmls_status gmls_release(gmls_ctx* ctx, int64_t id) {
   } else if (o.kind == K_CLOUD) {
     if (o.c.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: cloud has live neighbour handles");
     for (void* p : {(void*)o.c.x, (void*)o.c.xh, (void*)o.c.xl, (void*)o.c.normals, (void*)o.c.bflag,
-                    (void*)o.c.xs, (void*)o.c.sorted, (void*)o.c.cell_start, (void*)o.c.grid})
+                    (void*)o.c.xs, (void*)o.c.xsf, (void*)o.c.sorted, (void*)o.c.cell_start, (void*)o.c.grid})
       a.release(p);
   } else if (o.kind == K_NBRS) {
     if (o.nb.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: neighbours have live stencil handles");

@@ -69,6 +69,8 @@ struct CloudDev {
   const int32_t* cell_start;  // [ncell + 1]
   const GridParams* grid;
   int64_t ncell;
+  const float* xsf;        // SoA [dim][n], fl32 of xs (the query's FP32 pre-filter)
+  const float* xh;         // SoA [dim][n], fl32 of x, or NULL
 };
 
 // ------------------------------------------------------------ launch helpers
@@ -87,7 +89,7 @@ cudaError_t launch_scan_i64_from_i32(const Launch& L, const int32_t* in, int64_t
                                      int64_t* scratch, int64_t scratch_elems);
 int64_t scan_scratch_elems(int64_t n);
 cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const int32_t* cell_of,
-                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs);
+                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs, float* xsf);
 
 struct NbrQuery {
   CloudDev cloud;

@@ -123,18 +123,24 @@ cudaError_t launch_cell_count(const Launch& L, int dim, int64_t n, const double*
 
 __global__ void cell_scatter_kernel(int dim, int64_t n, const double* __restrict__ x, const int32_t* __restrict__ cell_of,
                                     const int32_t* __restrict__ cell_start, int32_t* __restrict__ fill,
-                                    int32_t* __restrict__ sorted, double* __restrict__ xs) {
+                                    int32_t* __restrict__ sorted, double* __restrict__ xs,
+                                    float* __restrict__ xsf) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t cell = cell_of[i];
     int32_t pos = cell_start[cell] + atomicAdd(&fill[cell], 1);
     sorted[pos] = (int32_t)i;
-    for (int c = 0; c < dim; ++c) xs[c * n + pos] = x[c * n + i];
+    for (int c = 0; c < dim; ++c) {
+      const double v = x[c * n + i];
+      xs[c * n + pos] = v;
+      xsf[c * n + pos] = __double2float_rn(v);
+    }
   }
 }
 
 cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const int32_t* cell_of,
-                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs) {
-  cell_scatter_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(dim, n, x, cell_of, cell_start, fill, sorted, xs);
+                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs, float* xsf) {
+  cell_scatter_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(dim, n, x, cell_of, cell_start, fill, sorted, xs,
+                                                                xsf);
   *L.counter += 1;
   return cudaGetLastError();
 }
@@ -294,54 +300,101 @@ __device__ inline WarpBuf warpbuf_at(unsigned char* base, int cap) {
   return w;
 }
 
-// Collect every particle with d2 < R2 (after the optional half-space filter)
-// from the cells overlapping [x_T - R, x_T + R] into the warp's buffer.
-// Returns the number that passed (may exceed kNbrCap: overflow).
-__device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const double* xT, double R, double R2,
-                                 bool use_hs, const double* nrm, WarpBuf& wb) {
-  const int lane = threadIdx.x & 31;
-  const int dim = cl.dim;
-  const double Rb = R * 1.000001;
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  for (int c = 0; c < dim; ++c) {
-    lo[c] = cell_coord(g, c, xT[c] - Rb);
-    hi[c] = cell_coord(g, c, xT[c] + Rb);
+// Query-side grid constants in FP32, derived once per warp from the FP64 grid.
+struct QueryGeo {
+  float lo[3], inv_h[3];
+  int32_t nc[3];
+  float A;   // >= max |coordinate| of the cloud
+  float e2;  // 2 * 2^-23 * A: twice the bound on |fl32(x_j) - fl32(x_T) - (x_j - x_T)|
+};
+
+__device__ inline QueryGeo make_query_geo(const GridParams& g, int dim) {
+  QueryGeo q;
+  double a = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    q.lo[c] = 0.0f;
+    q.inv_h[c] = 0.0f;
+    q.nc[c] = 1;
   }
+  for (int c = 0; c < dim; ++c) {
+    q.lo[c] = __double2float_rn(g.lo[c]);
+    q.inv_h[c] = __double2float_rn(g.inv_h[c]);
+    q.nc[c] = g.nc[c];
+    a = fmax(a, fmax(fabs(g.lo[c]), fabs(g.lo[c] + g.h[c] * g.nc[c])));
+  }
+  q.A = __double2float_ru(a) * (1.0f + 0x1p-20f);
+  q.e2 = q.A * 0x1p-22f;
+  return q;
+}
+
+// Cells [lo, hi] on axis c that can hold a point with |x_c - x_T,c| <= Rbox.
+// The FP32 cell coordinates get a margin far above their rounding error (and
+// that of the FP64 cell assignment), so the box is never too small.
+__device__ __forceinline__ void cell_range(const QueryGeo& q, int c, float xt, float Rbox, int& lo, int& hi) {
+  const float m = fmaf((q.A + Rbox) * q.inv_h[c], 0x1p-19f, 0x1p-19f);
+  const float u = (xt - Rbox - q.lo[c]) * q.inv_h[c] - m;
+  const float v = (xt + Rbox - q.lo[c]) * q.inv_h[c] + m;
+  const float top = (float)(q.nc[c] - 1);
+  lo = (u > 0.0f) ? (u < top ? (int)floorf(u) : q.nc[c] - 1) : 0;
+  hi = (v < top) ? (v > 0.0f ? (int)floorf(v) : 0) : q.nc[c] - 1;
+}
+
+// Row table of the cell rows [r0, r0 + 32) of the box: per lane the first
+// cell-order position of its row and the inclusive scan of row lengths.
+// Returns the number of positions in these rows.
+__device__ __forceinline__ int32_t load_rows(const CloudDev& cl, const GridParams& g, const int* lo, const int* hi,
+                                             int ny, int nrows, int r0, WarpBuf& wb) {
+  const int lane = threadIdx.x & 31;
+  const int r = r0 + lane;
+  int32_t b = 0, len = 0;
+  if (r < nrows) {
+    int cy = lo[1] + r % ny, cz = lo[2] + r / ny;
+    int32_t row_cell = (cz * g.nc[1] + cy) * g.nc[0];
+    b = cl.cell_start[row_cell + lo[0]];
+    len = cl.cell_start[row_cell + hi[0] + 1] - b;
+  }
+  int32_t incl = len;
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  wb.row_begin[lane] = b;
+  wb.row_end[lane] = incl;
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// cell-order position of entry p of the loaded rows
+__device__ __forceinline__ int64_t row_position(const WarpBuf& wb, int32_t p) {
+  int lo_r = 0, hi_r = 31;
+  while (lo_r < hi_r) {
+    int mid = (lo_r + hi_r) >> 1;
+    if (wb.row_end[mid] > p) hi_r = mid; else lo_r = mid + 1;
+  }
+  const int32_t start = lo_r ? wb.row_end[lo_r - 1] : 0;
+  return wb.row_begin[lo_r] + (p - start);
+}
+
+// Every particle with exact FP64 d2 < R2 (and on the kept side of the
+// half-space) from the cells of the box, computing d2 for every particle in
+// the box.  Returns the number that passed (may exceed wb.cap: overflow).
+template <int D>
+__device__ int gather_exact(const CloudDev& cl, const GridParams& g, const int* lo, const int* hi, const double* xT,
+                            double R2, bool use_hs, const double* nrm, WarpBuf& wb) {
+  const int lane = threadIdx.x & 31;
+  constexpr int dim = D;
   const int ny = hi[1] - lo[1] + 1;
   const int nrows = ny * (hi[2] - lo[2] + 1);
   int count = 0;
   for (int r0 = 0; r0 < nrows; r0 += 32) {
-    const int r = r0 + lane;
-    int32_t b = 0, len = 0;
-    if (r < nrows) {
-      int cy = lo[1] + r % ny, cz = lo[2] + r / ny;
-      int32_t row_cell = (cz * g.nc[1] + cy) * g.nc[0];
-      b = cl.cell_start[row_cell + lo[0]];
-      len = cl.cell_start[row_cell + hi[0] + 1] - b;
-    }
-    int32_t incl = len;
-    for (int o = 1; o < 32; o <<= 1) {
-      int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    wb.row_begin[lane] = b;
-    wb.row_end[lane] = incl;
-    __syncwarp();
-    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const int32_t total = load_rows(cl, g, lo, hi, ny, nrows, r0, wb);
     for (int32_t p0 = 0; p0 < total; p0 += 32) {
       const int32_t p = p0 + lane;
       bool pass = false;
       int32_t j = 0;
       double d2 = 0.0;
       if (p < total) {
-        // row containing p: first row whose inclusive end exceeds p
-        int lo_r = 0, hi_r = 31;
-        while (lo_r < hi_r) {
-          int mid = (lo_r + hi_r) >> 1;
-          if (wb.row_end[mid] > p) hi_r = mid; else lo_r = mid + 1;
-        }
-        int32_t start = lo_r ? wb.row_end[lo_r - 1] : 0;
-        int64_t pos = wb.row_begin[lo_r] + (p - start);
+        const int64_t pos = row_position(wb, p);
         double dx[3] = {0.0, 0.0, 0.0};
         for (int c = 0; c < dim; ++c) dx[c] = __dsub_rn(cl.xs[c * cl.n + pos], xT[c]);
         d2 = exact_d2(dim, dx);
@@ -364,6 +417,83 @@ __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const 
   return count;
 }
 
+// Collect every particle with exact FP64 d2 < R2 (after the optional
+// half-space filter) into the warp's buffer.  The box of cells covers
+// |x_c - x_T,c| <= Rbox, Rbox >= sqrt(R2).  A first pass tests each
+// particle of the box in FP32 against a bound that no particle inside
+// sqrt(R2) can exceed (rounding of the float coordinates and of the FP32 sum
+// included) and compacts the survivors; only those get the exact FP64 d2, so
+// the FP64 pipe sees about the ball's share of the box.  If the survivors do
+// not fit the buffer the box is searched again with exact distances only.
+// Returns the number that passed (may exceed wb.cap: overflow).
+template <int D>
+__device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const QueryGeo& gq, const double* xT,
+                                 const float* xTf, float Rbox, double R2, bool use_hs, const double* nrm,
+                                 WarpBuf& wb) {
+  const int lane = threadIdx.x & 31;
+  constexpr int dim = D;
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int c = 0; c < dim; ++c) cell_range(gq, c, xTf[c], Rbox, lo[c], hi[c]);
+  const int ny = hi[1] - lo[1] + 1;
+  const int nrows = ny * (hi[2] - lo[2] + 1);
+  float bf = Rbox + gq.e2;
+  bf = bf * bf * (1.0f + 0x1p-19f);
+  // pass 1: FP32 pre-filter, positions of the survivors into wb.id
+  int staged = 0;
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
+    const int32_t total = load_rows(cl, g, lo, hi, ny, nrows, r0, wb);
+    for (int32_t p0 = 0; p0 < total; p0 += 32) {
+      const int32_t p = p0 + lane;
+      bool pass = false;
+      int32_t pos = 0;
+      if (p < total) {
+        pos = (int32_t)row_position(wb, p);
+        float d2f = 0.0f;
+        for (int c = 0; c < dim; ++c) {
+          const float dxf = cl.xsf[c * cl.n + pos] - xTf[c];
+          d2f = fmaf(dxf, dxf, d2f);
+        }
+        pass = d2f <= bf;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        int slot = staged + __popc(m & ((1u << lane) - 1u));
+        if (slot < wb.cap) wb.id[slot] = pos;
+      }
+      staged += __popc(m);
+    }
+    __syncwarp();
+  }
+  if (staged > wb.cap) return gather_exact<D>(cl, g, lo, hi, xT, R2, use_hs, nrm, wb);
+  // pass 2: exact FP64 distances of the survivors, compacted in place (an
+  // entry moves to a slot at or below its own, and each round's reads finish
+  // before its writes)
+  int count = 0;
+  for (int i0 = 0; i0 < staged; i0 += 32) {
+    const int i = i0 + lane;
+    const int32_t pos = (i < staged) ? wb.id[i] : 0;
+    __syncwarp();
+    bool pass = false;
+    double d2 = 0.0;
+    if (i < staged) {
+      double dx[3] = {0.0, 0.0, 0.0};
+      for (int c = 0; c < dim; ++c) dx[c] = __dsub_rn(cl.xs[c * cl.n + pos], xT[c]);
+      d2 = exact_d2(dim, dx);
+      pass = nonneg_less(d2, R2);
+      if (pass && use_hs) pass = nonpositive(exact_dot(dim, nrm, dx));
+    }
+    unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (pass) {
+      const int slot = count + __popc(m & ((1u << lane) - 1u));
+      wb.d2[slot] = d2;
+      wb.id[slot] = cl.sorted[pos];
+    }
+    count += __popc(m);
+    __syncwarp();
+  }
+  return count;
+}
+
 // Bitonic sort of the first `count` candidates by (d2, id) within one warp.
 __device__ void warp_sort_candidates(WarpBuf& wb, int count) {
   const int lane = threadIdx.x & 31;
@@ -377,8 +507,9 @@ __device__ void warp_sort_candidates(WarpBuf& wb, int count) {
   for (int size = 2; size <= n2; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int i = lane; i < (n2 >> 1); i += 32) {
-        int a = 2 * stride * (i / stride) + (i % stride);
-        int b = a + stride;
+        // stride is a power of two: a = 2 stride (i / stride) + i % stride
+        const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+        const int b = a + stride;
         bool asc = (a & size) == 0;
         double da = wb.d2[a], db = wb.d2[b];
         int32_t ia = wb.id[a], ib = wb.id[b];
@@ -395,24 +526,31 @@ __device__ void warp_sort_candidates(WarpBuf& wb, int count) {
   }
 }
 
+template <int D>
 __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q, int buf_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpBuf wb = warpbuf_at(smem_raw + (size_t)(threadIdx.x >> 5) * warpbuf_bytes(buf_cap), buf_cap);
   const int lane = threadIdx.x & 31;
   const CloudDev& cl = q.cloud;
   const GridParams g = *cl.grid;
-  const int dim = cl.dim;
+  constexpr int dim = D;
+  const QueryGeo gq = make_query_geo(g, dim);
   // unit-ball volume and the initial radius: about 1.5 k particles expected
   const double ball = (dim == 1) ? 2.0 : (dim == 2) ? 3.141592653589793 : 4.1887902047863905;
   const double dens = (double)cl.n / (g.volume > 0.0 ? g.volume : 1.0);
   const float inv_dens_ball = (float)(1.0 / (dens * ball));
   double span = 0.0;
   for (int c = 0; c < dim; ++c) span += g.h[c] * g.nc[c];
+  const float big = __double2float_ru(2.0 * span + 1.0);
   for (int64_t to = blockIdx.x * (int64_t)kQueryWarps + (threadIdx.x >> 5); to < q.n_tgt;
        to += (int64_t)gridDim.x * kQueryWarps) {
     const int64_t t = q.tgt ? q.tgt[to] : to;
     double xT[3] = {0.0, 0.0, 0.0}, nrm[3] = {0.0, 0.0, 0.0};
-    for (int c = 0; c < dim; ++c) xT[c] = cl.x[c * cl.n + t];
+    float xTf[3] = {0.0f, 0.0f, 0.0f};
+    for (int c = 0; c < dim; ++c) {
+      xT[c] = cl.x[c * cl.n + t];
+      xTf[c] = cl.xh ? cl.xh[c * cl.n + t] : __double2float_rn(xT[c]);
+    }
     bool use_hs = false;
     if (q.halfspace) {
       for (int c = 0; c < dim; ++c) {
@@ -423,19 +561,20 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     uint8_t st = GMLS_T_OK;
     int kq = q.k_pt ? q.k_pt[to] : q.k;  // per-target k is clamped to 1..cap
     kq = kq < 1 ? 1 : (kq > q.cap ? q.cap : kq);
-    // initial radius: any value is correct (the search widens or narrows it);
-    // computed in FP32 to keep the FP64 pipe for the exact distances
-    double R = (double)powf(1.5f * (float)kq * inv_dens_ball, 1.0f / (float)dim);
+    // search radius R in FP32 (any value is correct: the search widens or
+    // narrows it); the exact test is d2 < R2 = fl32(R * R) in FP64, and the
+    // box half-width R (1 + 2^-20) covers sqrt(R2)
+    float R = powf(1.5f * (float)kq * inv_dens_ball, 1.0f / (float)dim);
     int count = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
-      count = gather_candidates(cl, g, xT, R, __dmul_rn(R, R), use_hs, nrm, wb);
+      count = gather_candidates<D>(cl, g, gq, xT, xTf, R * (1.0f + 0x1p-20f), (double)(R * R), use_hs, nrm, wb);
       if (count > wb.cap) {
-        R *= 0.75;
+        R *= 0.75f;
         continue;
       }
       if (count >= kq) break;
-      if (R > 2.0 * span + 1.0) break;  // whole cloud inside: too few exist
-      R *= 1.6;
+      if (R > big) break;  // whole cloud inside: too few exist
+      R *= 1.6f;
     }
     if (count > wb.cap) {  // could not bring the candidate set under the buffer size
       st |= GMLS_T_OVERFLOW;
@@ -455,7 +594,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
       int keep = 0;
       if (kk == kq) {
         __syncwarp();
-        count = gather_candidates(cl, g, xT, eps, __dmul_rn(eps, eps), use_hs, nrm, wb);
+        count = gather_candidates<D>(cl, g, gq, xT, xTf, __double2float_ru(eps) * (1.0f + 0x1p-20f),
+                                  __dmul_rn(eps, eps), use_hs, nrm, wb);
         if (count > wb.cap) {
           st |= GMLS_T_OVERFLOW;
           count = wb.cap;
@@ -483,11 +623,15 @@ cudaError_t launch_nbr_query(const Launch& L, const NbrQuery& q) {
   const int want = q.mode == GMLS_NBR_KNN ? 2 * q.k : kNbrCap;
   while (cap < want && cap < kNbrCap) cap <<= 1;
   const size_t smem = warpbuf_bytes(cap) * kQueryWarps;
-  cudaError_t e = cudaFuncSetAttribute(nbr_query_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* fn = q.cloud.dim == 2 ? (const void*)nbr_query_kernel<2> : (const void*)nbr_query_kernel<3>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t blocks = (q.n_tgt + kQueryWarps - 1) / kQueryWarps;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  nbr_query_kernel<<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q, cap);
+  if (q.cloud.dim == 2)
+    nbr_query_kernel<2><<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q, cap);
+  else
+    nbr_query_kernel<3><<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q, cap);
   *L.counter += 1;
   return cudaGetLastError();
 }

@@ -55,7 +55,8 @@ constexpr size_t kOffStart = kOffFill + up256(sizeof(int32_t) * kMaxCells);
 constexpr size_t kOffScan = kOffStart + up256(sizeof(int32_t) * (kMaxCells + 1));
 constexpr size_t kOffSorted = kOffScan + up256(sizeof(int32_t) * (kMaxCells / 2048 + 4));
 constexpr size_t kOffXs = kOffSorted + up256(sizeof(int32_t) * kMaxPoints);
-constexpr size_t kScratchBytes = kOffXs + up256(sizeof(double) * 3 * kMaxPoints);  // about 10.6 MB
+constexpr size_t kOffXsf = kOffXs + up256(sizeof(double) * 3 * kMaxPoints);
+constexpr size_t kScratchBytes = kOffXsf + up256(sizeof(float) * 3 * kMaxPoints);  // about 13.7 MB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -124,6 +125,7 @@ extern "C" gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, i
   int32_t* scan_tmp = reinterpret_cast<int32_t*>(base + kOffScan);
   int32_t* sorted = reinterpret_cast<int32_t*>(base + kOffSorted);
   double* xs = reinterpret_cast<double*>(base + kOffXs);
+  float* xsf = reinterpret_cast<float*>(base + kOffXsf);
   const int64_t scan_elems = kMaxCells / 2048 + 4;
   const int n_part = (int)std::min<int64_t>(kMaxPartials, (n + 255) / 256);
 
@@ -136,11 +138,11 @@ extern "C" gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, i
       (e = launch_bbox_and_grid(L, dim, n, xyz, nc_axis, grid, part, n_part)) != cudaSuccess ||
       (e = launch_cell_count(L, dim, n, xyz, grid, cell_of, counts)) != cudaSuccess ||
       (e = launch_scan_i32(L, counts, cell_start, ncell, scan_tmp, scan_elems)) != cudaSuccess ||
-      (e = launch_cell_scatter(L, dim, n, xyz, cell_of, cell_start, fill, sorted, xs)) != cudaSuccess)
+      (e = launch_cell_scatter(L, dim, n, xyz, cell_of, cell_start, fill, sorted, xs, xsf)) != cudaSuccess)
     return err(GMLS_ECUDA, std::string("gmls_knn_noalloc: cell list: ") + cudaGetErrorString(e));
   NbrQuery q;
   std::memset(&q, 0, sizeof(q));
-  q.cloud = CloudDev{dim, n, xyz, xs, sorted, cell_start, grid, ncell};
+  q.cloud = CloudDev{dim, n, xyz, xs, sorted, cell_start, grid, ncell, xsf, nullptr};
   q.n_tgt = n;
   q.tgt = nullptr;
   q.halfspace = nullptr;

@@ -113,7 +113,7 @@ struct Request {
 size_t estimate_bytes(const gmls_request& r) {
   const int64_t n = r.n, k = r.k, d = r.dim;
   const int nc = r.basis == GMLS_BASIS_SCALAR ? 1 : (int)d;
-  size_t cloud = (size_t)n * (d * (8 + 4 + 4 + 8) + 4 + 4 + 2 * 4 * 3) + 64 * 1024;
+  size_t cloud = (size_t)n * (d * (8 + 4 + 4 + 8 + 4) + 4 + 4 + 2 * 4 * 3) + 64 * 1024;
   size_t nbrs = (size_t)n * (k * 4 * 2 + 8 + 8 + 4 + 1 + 16) + 64 * 1024;
   size_t weights = 0;
   for (int f = 0; f < r.n_functionals; ++f) {

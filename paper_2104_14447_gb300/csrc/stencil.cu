@@ -716,8 +716,11 @@ cudaError_t launch_bucketing(const Launch& L, const BucketJob& b) {
 // ------------------------------------------------------------------------ CSR
 // Warp per target: order the neighbours by particle id once (bitonic sort of
 // (id, position) pairs in shared memory) and write every row of the target.
+// C (components per neighbour) is a compile-time constant so that the
+// element -> (neighbour, component) split is a multiply-shift.
 constexpr int kCsrWarps = 4;
 
+template <int C>
 __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
   __shared__ int32_t sid[kCsrWarps][kMaxK];
   __shared__ int16_t spos[kCsrWarps][kMaxK];
@@ -737,7 +740,8 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
     for (int size = 2; size <= n2; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         for (int i = lane; i < (n2 >> 1); i += 32) {
-          int a = 2 * stride * (i / stride) + (i % stride), b = a + stride;
+          // stride is a power of two: a = 2 stride (i / stride) + i % stride
+          const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
           bool asc = (a & size) == 0;
           int32_t ia = ids[a], ib = ids[b];
           if ((ib < ia) == asc) {
@@ -751,7 +755,7 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
         __syncwarp();
       }
     }
-    const int C = j.nc, rowlen = k * C;
+    const int rowlen = k * C;
     const int64_t base = o * (int64_t)j.rows * C;
     for (int r = 0; r < j.rows; ++r) {
       const int64_t row = t * j.rows + r;
@@ -776,7 +780,14 @@ cudaError_t launch_csr(const Launch& L, const CsrJob& j) {
   }
   int64_t blocks = (j.n_tgt + kCsrWarps - 1) / kCsrWarps;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  csr_kernel<<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+  if (j.nc == 1)
+    csr_kernel<1><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+  else if (j.nc == 2)
+    csr_kernel<2><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+  else if (j.nc == 3)
+    csr_kernel<3><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+  else
+    return cudaErrorInvalidValue;
   *L.counter += 1;
   return cudaGetLastError();
 }
