@@ -311,7 +311,8 @@ def run_ours(args, rank, world, local_rank):
     tune = {}
     for r in ctx.tune_log():
         key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m={r['degree']} rows<={r['rows']}"
-        tune.setdefault(key, {})["register" if r["variant"] < 0 else f"{r['variant']} warp(s)/target"] = round(r["ms"], 3)
+        name = {-1: "register", -2: "register 16 lanes"}.get(r["variant"], f"{r['variant']} warp(s)/target")
+        tune.setdefault(key, {})[name] = round(r["ms"], 3)
 
     value = shard.job_throughput(n, args.steps, world, total_ms)
     out = {

@@ -122,20 +122,59 @@ def cnum(fr: Fraction) -> str:
     return f"({fr.numerator}.0/{fr.denominator}.0)"
 
 
+def f32_split(fr: Fraction):
+    """float-float split (h, l) of a rational: h = fl32(v), l = fl32(v - h)."""
+    import numpy as np
+    v = fr.numerator / fr.denominator
+    h = np.float32(v)
+    lo = np.float32(v - float(h))
+    return float(h), float(lo)
+
+
+def cconst(fr: Fraction) -> str:
+    """A constant of type T: exact value for double, float-float split for ff."""
+    h, lo = f32_split(fr)
+    return f"gmls_cst(T(), {cnum(fr)}, {h.hex()}f, {lo.hex()}f)"
+
+
 def emit_monomials(d, m, lines, ind):
-    """px{a} = xi_x^a / a! etc. (no factor for a = 0), products per monomial."""
+    """px{a} = xi_x^a / a! etc. (no factor for a = 0)."""
     names = "xyz"
     for k in range(d):
         for a in range(1, m + 1):
             if a == 1:
                 lines.append(f"{ind}const T p{names[k]}1 = xi[{k}];")
+            elif a & (a - 1) == 0:  # 1/a is a power of two: exact scaling
+                lines.append(f"{ind}const T p{names[k]}{a} = gmls_scale2(p{names[k]}{a - 1} * xi[{k}], {1.0 / a!r}f);")
             else:
-                lines.append(f"{ind}const T p{names[k]}{a} = (p{names[k]}{a - 1} * xi[{k}]) * T({cnum(Fraction(1, a))});")
-    prods = []
-    for g in monomials(d, m):
-        f = [f"p{names[k]}{g[k]}" for k in range(d) if g[k] > 0]
-        prods.append("*".join(f) if f else "T(1)")
-    return prods
+                lines.append(f"{ind}const T p{names[k]}{a} = (p{names[k]}{a - 1} * xi[{k}]) * {cconst(Fraction(1, a))};")
+
+
+def emit_scaled_products(d, mons, used, lines, ind):
+    """q{i} = s * prod_k p{k}{g_k} for the used monomials, built axis by axis
+    from memoised partial products s * px_a, s * px_a * py_b, ... so that every
+    monomial costs at most one product beyond its prefix."""
+    names = "xyz"
+    made = {}
+
+    def partial(g, k):  # name of s * prod_{j <= k} p{j}{g_j}
+        key = tuple(g[:k + 1])
+        if key in made:
+            return made[key]
+        if k < 0:
+            return "s"
+        prev = partial(g, k - 1) if k > 0 else "s"
+        if g[k] == 0:
+            made[key] = prev
+            return prev
+        nm = "t" + "_".join(str(e) for e in key)
+        lines.append(f"{ind}const T {nm} = {prev} * p{names[k]}{g[k]};")
+        made[key] = nm
+        return nm
+
+    for i, g in enumerate(mons):
+        if i in used:
+            lines.append(f"{ind}const T q{i} = {partial(g, d - 1)};")
 
 
 def gen():
@@ -144,6 +183,11 @@ def gen():
     L.append("// GPU (scaled Taylor monomials; divergence-free null-space basis).")
     L.append("#pragma once")
     L.append("namespace gmls_gen {")
+    L.append("")
+    L.append("// constants and exact power-of-two scalings for T = double; the float-float")
+    L.append("// type provides its own overloads (found by argument-dependent lookup)")
+    L.append("__device__ __forceinline__ double gmls_cst(double, double c, float, float) { return c; }")
+    L.append("__device__ __forceinline__ double gmls_scale2(double x, float p) { return x * (double)p; }")
     L.append("")
     summary = []
     for kind in ("scalar", "divfree"):
@@ -164,20 +208,18 @@ def gen():
                 L.append("template <typename T>")
                 L.append(f"__device__ __forceinline__ void eval_{name}(const T* xi, T* out, int ld, const T s) {{")
                 ind = "  "
-                prods = emit_monomials(d, m, L, ind)
+                emit_monomials(d, m, L, ind)
                 used = {mi for f in funcs for (_, mi, _) in f}
-                for i, g in enumerate(mons):
-                    if i in used:
-                        L.append(f"{ind}const T q{i} = {'s' if prods[i] == 'T(1)' else 's * (' + prods[i] + ')'};")
+                emit_scaled_products(d, mons, used, L, ind)
                 # out[i*ld + c] = sum terms
                 for i, f in enumerate(funcs):
                     for c in range(nc):
                         ts = [(mi, a) for (cc, mi, a) in f if cc == c]
                         if not ts:
-                            L.append(f"{ind}out[{i} * ld + {c}] = T(0);")
+                            L.append(f"{ind}out[{i} * ld + {c}] = gmls_cst(T(), 0.0, 0.0f, 0.0f);")
                             continue
                         expr = " + ".join(
-                            (f"q{mi}" if a == 1 else f"-q{mi}" if a == -1 else f"T({cnum(a)}) * q{mi}") for mi, a in ts)
+                            (f"q{mi}" if a == 1 else f"-q{mi}" if a == -1 else f"{cconst(a)} * q{mi}") for mi, a in ts)
                         L.append(f"{ind}out[{i} * ld + {c}] = {expr};")
                 L.append("}")
                 # functional rows (coefficients before the eps^{-|beta|} factor)

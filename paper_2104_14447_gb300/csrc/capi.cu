@@ -158,7 +158,7 @@ struct TuneKey {
 };
 struct TuneRecord {
   TuneKey key;
-  int variant;  // -1 register kernel, else warps per target
+  int variant;  // -1 / -2 register kernel (32 / 16 lanes per target), else warps per target
   float ms;
 };
 
@@ -170,6 +170,7 @@ struct gmls_ctx {
   int64_t next_id = 1;
   int64_t launches = 0;
   bool force_generic = false;  // testing: use the generic tile kernel for every shape
+  int force_variant = 0;       // testing: this kernel variant for uniform shapes (0: off)
   bool autotune = true;
   std::map<TuneKey, int> tune;        // chosen variant per shape
   std::vector<TuneRecord> tune_log;   // every timing the autotuner took
@@ -306,20 +307,36 @@ static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int G, int 
   return e;
 }
 
-// Uniform neighbour counts and degree: one shape.  Candidates: the
-// warp-per-target register kernel (when this shape is instantiated) and the
-// shared-memory kernel with 1, 2 or 4 warps per target; the autotuner times
-// each once on up to 8192 targets and the choice is cached per shape.
+// Uniform neighbour counts and degree: one shape.  Candidates: the register
+// kernel with a warp (variant -1) or a half warp (variant -2) per target, when
+// this shape is instantiated, and the shared-memory kernel with 1, 2 or 4
+// warps per target; the autotuner times each once on up to 8192 targets and
+// the choice is cached per shape.
 static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls_stencil_params* p, bool refine,
                                   int ld, int nmax, int sms, int32_t* counter) {
   const int dim = j.dim;
-  int mr = 0;
-  const bool fast_ok = refine && (p->weight_power % 2 == 0) && !ctx->force_generic &&
-                       fast_path_available(p->basis, dim, p->degree, ld, j.L, &mr);
+  int mr32 = 0, mr16 = 0, mr_pref = 0;
+  const bool fast_allowed = refine && (p->weight_power % 2 == 0) && !ctx->force_generic;
+  const bool ok32 = fast_allowed && fast_path_available(p->basis, dim, p->degree, ld, j.L, 32, &mr32);
+  const bool ok16 = fast_allowed && fast_path_available(p->basis, dim, p->degree, ld, j.L, 16, &mr16);
+  const int hw_pref = fast_allowed ? fast_path_preferred(p->basis, dim, p->degree, ld, j.L, &mr_pref) : 0;
+  auto launch_fast = [&](const StencilJob& jj, int variant) {
+    return variant == -2 ? launch_stencils_fast(ctx->launch(), jj, mr16, 16, sms)
+                         : launch_stencils_fast(ctx->launch(), jj, mr32, 32, sms);
+  };
   const TuneKey key{p->basis, dim, p->degree, p->precision, ld, j.L, p->neumann, 0};
-  int choice = 0;  // -1 fast kernel, else G
+  int choice = 0;  // -1 / -2 register kernel (32 / 16 lanes per target), else G
   auto it = ctx->tune.find(key);
-  if (ctx->force_generic) {
+  auto generic_fits = [&](int G) {
+    return (size_t)(4 / G) * tile_bytes(ld, nmax, refine) <= 227 * 1024 ||
+           (G == 4 && tile_bytes(ld, nmax, refine, true) <= 227 * 1024);
+  };
+  if (ctx->force_variant != 0) {
+    const int v = ctx->force_variant;
+    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || ((v == 1 || v == 2 || v == 4) && generic_fits(v));
+    if (!ok) return fail(ctx, GMLS_EINVAL, "gmls_stencils: the forced kernel variant is not available for this shape");
+    choice = v;
+  } else if (ctx->force_generic) {
     choice = heuristic_g(ld, nmax, refine);
   } else if (it != ctx->tune.end()) {
     choice = it->second;
@@ -328,16 +345,15 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     js.n_tgt = std::min<int64_t>(j.n_tgt, 8192);
     float best = 1e30f;
     std::vector<int> cands;
-    if (fast_ok) cands.push_back(-1);
+    if (ok32) cands.push_back(-1);
+    if (ok16) cands.push_back(-2);
     for (int G = 1; G <= 4; G *= 2)
-      if ((size_t)(4 / G) * tile_bytes(ld, nmax, refine) <= 227 * 1024 ||
-          (G == 4 && tile_bytes(ld, nmax, refine, true) <= 227 * 1024))
-        cands.push_back(G);
+      if (generic_fits(G)) cands.push_back(G);
     for (int c : cands) {
       float ms = time_launch(ctx, [&]() {
         if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
         if (c < 0)
-          launch_stencils_fast(ctx->launch(), js, mr, sms);
+          launch_fast(js, c);
         else
           launch_single(ctx, js, c, ld, nmax, refine, counter, sms);
       });
@@ -350,12 +366,12 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: no kernel variant fits this shape");
     ctx->tune[key] = choice;
   } else {
-    choice = fast_ok ? -1 : heuristic_g(ld, nmax, refine);
+    choice = hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_g(ld, nmax, refine);
   }
   if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this shape");
   if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
   if (choice < 0)
-    CK(launch_stencils_fast(ctx->launch(), j, mr, sms), "gmls_stencils fast launch");
+    CK(launch_fast(j, choice), "gmls_stencils fast launch");
   else
     CK(launch_single(ctx, j, choice, ld, nmax, refine, counter, sms), "gmls_stencils launch");
   return GMLS_OK;
@@ -592,6 +608,11 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
   switch (option) {
     case GMLS_OPT_FORCE_GENERIC: ctx->force_generic = value != 0; return GMLS_OK;
     case GMLS_OPT_AUTOTUNE: ctx->autotune = value != 0; return GMLS_OK;
+    case GMLS_OPT_FORCE_VARIANT:
+      if (value != 0 && value != -1 && value != -2 && value != 1 && value != 2 && value != 4)
+        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2, 1, 2 or 4");
+      ctx->force_variant = (int)value;
+      return GMLS_OK;
     case GMLS_OPT_CLEAR_TUNING:
       ctx->tune.clear();
       ctx->tune_log.clear();

@@ -3,6 +3,6 @@
 #include "stencil_fast.cuh"
 
 namespace gmls {
-extern const FastEntry kFastD2[] = {GMLS_FAST(1, 2, 2, 2, 2), GMLS_FAST(1, 2, 3, 3, 2), GMLS_FAST(1, 2, 4, 3, 2)};
+extern const FastEntry kFastD2[] = {GMLS_FAST(1, 2, 2, 2, 2, 32), GMLS_FAST(1, 2, 3, 3, 2, 32), GMLS_FAST(1, 2, 4, 3, 2, 32), GMLS_FAST(1, 2, 2, 3, 2, 16)};
 extern const int kFastD2Count = sizeof(kFastD2) / sizeof(kFastD2[0]);
 }  // namespace gmls

@@ -3,6 +3,6 @@
 #include "stencil_fast.cuh"
 
 namespace gmls {
-extern const FastEntry kFastS2c[] = {GMLS_FAST(0, 2, 4, 2, 2), GMLS_FAST(0, 2, 4, 2, 3), GMLS_FAST(0, 2, 4, 3, 2), GMLS_FAST(0, 2, 4, 3, 3)};
+extern const FastEntry kFastS2c[] = {GMLS_FAST(0, 2, 4, 2, 2, 32), GMLS_FAST(0, 2, 4, 2, 3, 32), GMLS_FAST(0, 2, 4, 3, 2, 32), GMLS_FAST(0, 2, 4, 3, 3, 32), GMLS_FAST(0, 2, 4, 3, 2, 16), GMLS_FAST(0, 2, 4, 3, 3, 16)};
 extern const int kFastS2cCount = sizeof(kFastS2c) / sizeof(kFastS2c[0]);
 }  // namespace gmls

@@ -3,6 +3,6 @@
 #include "stencil_fast.cuh"
 
 namespace gmls {
-extern const FastEntry kFastS3a[] = {GMLS_FAST(0, 3, 2, 1, 3), GMLS_FAST(0, 3, 2, 1, 4), GMLS_FAST(0, 3, 2, 2, 3), GMLS_FAST(0, 3, 2, 2, 4)};
+extern const FastEntry kFastS3a[] = {GMLS_FAST(0, 3, 2, 1, 3, 32), GMLS_FAST(0, 3, 2, 1, 4, 32), GMLS_FAST(0, 3, 2, 2, 3, 32), GMLS_FAST(0, 3, 2, 2, 4, 32), GMLS_FAST(0, 3, 2, 2, 3, 16), GMLS_FAST(0, 3, 2, 2, 4, 16)};
 extern const int kFastS3aCount = sizeof(kFastS3a) / sizeof(kFastS3a[0]);
 }  // namespace gmls

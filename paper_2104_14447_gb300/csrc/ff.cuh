@@ -83,13 +83,14 @@ __device__ __forceinline__ ff recip(ff a) {
   return quick_two_sum(q, c);
 }
 
-// sqrt(a), a >= 0: one Newton step on the float square root
+// sqrt(a), a >= 0: one Newton step on the float square root (the step's
+// quotient only needs float accuracy: it is about 2^-24 of the result)
 __device__ __forceinline__ ff sqrt_ff(ff a) {
   if (!(a.h > 0.0f)) return ff(0.0f, 0.0f);
   float s = sqrtf(a.h);
   ff ss = two_prod(s, s);
   float r = __fadd_rn(__fsub_rn(__fsub_rn(a.h, ss.h), ss.l), a.l);
-  float c = __fdiv_rn(r, __fmul_rn(2.0f, s));
+  float c = __fdividef(r, __fmul_rn(2.0f, s));
   return quick_two_sum(s, c);
 }
 
@@ -109,6 +110,11 @@ __device__ __forceinline__ double f2d_exact(float f) {
 }
 
 __device__ __forceinline__ double to_double(ff a) { return f2d_exact(a.h) + f2d_exact(a.l); }
+
+// constant with float-float split (h, l), and x * p for a power of two p
+// (exact: both parts scale); used by the generated basis evaluation
+__device__ __forceinline__ ff gmls_cst(ff, double, float h, float l) { return ff(h, l); }
+__device__ __forceinline__ ff gmls_scale2(ff x, float p) { return ff(x.h * p, x.l * p); }
 
 // (a_h + a_l) - (b_h + b_l) for coordinates stored as float pairs
 __device__ __forceinline__ ff sub_pair(float ah, float al, float bh, float bl) {

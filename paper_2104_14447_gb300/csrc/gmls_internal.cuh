@@ -214,8 +214,12 @@ int stencil_blocks_per_sm(bool fp32_refine, size_t smem);
 cudaError_t launch_stencils(const Launch& L, const StencilJob& j, const BatchPlan& plan, bool fp32_refine,
                             size_t smem, int grid_blocks);
 cudaError_t launch_bucketing(const Launch& L, const BucketJob& b);
-bool fast_path_available(int kind, int dim, int deg, int rows, int L, int* mr_out);
-cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int sms);
+// register kernel with groups of hw lanes (32 or 16) per target: is this
+// shape instantiated, and with how many rows per lane (smallest that fits)
+bool fast_path_available(int kind, int dim, int deg, int rows, int L, int hw, int* mr_out);
+// the preferred group width for a shape: fewest padded row slots, then 32
+int fast_path_preferred(int kind, int dim, int deg, int rows, int L, int* mr_out);
+cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms);
 cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count);
 
 // -------------------------------------------------------------------- CSR

@@ -31,43 +31,61 @@ static void for_each_entry(F&& f) {
     for (int i = 0; i < *t.n; ++i) f(t.e[i]);
 }
 
-bool fast_path_available(int kind, int dim, int deg, int rows, int L, int* mr_out) {
+bool fast_path_available(int kind, int dim, int deg, int rows, int L, int hw, int* mr_out) {
   int best = 0;
   for_each_entry([&](const FastEntry& e) {
-    if (e.kind == kind && e.dim == dim && e.deg == deg && e.L == L && 32 * e.mr >= rows && (best == 0 || e.mr < best))
+    if (e.kind == kind && e.dim == dim && e.deg == deg && e.L == L && e.hw == hw && e.hw * e.mr >= rows &&
+        (best == 0 || e.mr < best))
       best = e.mr;
   });
   if (mr_out) *mr_out = best;
   return best > 0;
 }
 
-cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int sms) {
+int fast_path_preferred(int kind, int dim, int deg, int rows, int L, int* mr_out) {
+  int mr32 = 0, mr16 = 0;
+  const bool a32 = fast_path_available(kind, dim, deg, rows, L, 32, &mr32);
+  const bool a16 = fast_path_available(kind, dim, deg, rows, L, 16, &mr16);
+  if (a16 && (!a32 || 16 * mr16 < 32 * mr32)) {
+    if (mr_out) *mr_out = mr16;
+    return 16;
+  }
+  if (a32) {
+    if (mr_out) *mr_out = mr32;
+    return 32;
+  }
+  return 0;
+}
+
+cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms) {
   const FastEntry* ent = nullptr;
   for_each_entry([&](const FastEntry& e) {
-    if (e.kind == j.kind && e.dim == j.dim && e.deg == j.degree && e.mr == mr && e.L == j.L) ent = &e;
+    if (e.kind == j.kind && e.dim == j.dim && e.deg == j.degree && e.mr == mr && e.L == j.L && e.hw == hw) ent = &e;
   });
   if (!ent) return cudaErrorInvalidValue;
-  // warps per block: the choice with the most resident warps per SM
-  const size_t per_warp = ent->bytes(j.L);
-  int best_w = 1, best_warps = 0, best_blocks = 1;
+  // warps per block: the choice with the most resident groups per SM
+  const int gpw = 32 / hw;  // groups (targets in flight) per warp
+  const size_t per_group = ent->bytes(j.L);
+  int best_w = 1, best_groups = 0, best_blocks = 1;
   for (int w = 1; w <= 4; ++w) {
-    const size_t smem = w * per_warp;
+    const size_t smem = (size_t)w * gpw * per_group;
     if (smem > 227 * 1024) break;
     cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ent->fn, 32 * w, smem);
     if (e != cudaSuccess) return e;
-    if (blocks * w >= best_warps) {
-      best_warps = blocks * w;
+    if (blocks * w >= best_groups) {
+      best_groups = blocks * w;
       best_w = w;
       best_blocks = blocks;
     }
   }
-  const size_t smem = best_w * per_warp;
+  const size_t smem = (size_t)best_w * gpw * per_group;
   cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t want = (j.n_tgt + best_w - 1) / best_w;
+  const int64_t per_block = (int64_t)best_w * gpw;
+  int64_t want = (j.n_tgt + per_block - 1) / per_block;
   int64_t cap = (int64_t)sms * (best_blocks > 0 ? best_blocks : 1);
   int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
   void* args[] = {(void*)&j};

@@ -7,10 +7,13 @@
 // Householder QR, functional rows lambda, weights w = sqrt(W) Q R^{-T}
 // lambda^T), laid out for GB300:
 //
-//  * one warp owns one target; lane l holds rows l, l+32, ... of the FP32
+//  * a group of HW lanes (a whole warp, HW = 32, or half of one, HW = 16)
+//    owns one target; lane l of the group holds rows l, l+HW, ... of the FP32
 //    QR tile in registers (compile-time basis size N and rows-per-lane MR, so
 //    the factorisation is fully unrolled); padded rows are zero and exactly
-//    neutral for Householder reflections;
+//    neutral for Householder reflections.  Half-warp groups suit systems of
+//    a few dozen rows (36 rows: 48 slots on 16 lanes instead of 64 on 32),
+//    and every cross-lane reduction then serves two targets at once;
 //  * the tile B is built directly in float-float (hi + lo, ~48 bits) from
 //    float-float coordinates, so no FP64 instruction runs in the hot loop;
 //  * refinement of the augmented system [[I, B], [B^T, 0]] [s; -y] =
@@ -34,17 +37,17 @@
 
 namespace gmls {
 
-template <int MR, int N>
+template <int HW, int MR, int N>
 struct FastLay {
-  static constexpr int LD = 32 * MR + 1;  // odd: column walks by different lanes avoid bank conflicts
+  static constexpr int LD = HW * MR + 1;  // odd: column walks by different lanes avoid bank conflicts
   static constexpr int RS = N | 1;        // odd row stride of the staged triangular factor
   static constexpr size_t B = 0;                                // ff [N][LD]
   static constexpr size_t SW = B + sizeof(ff) * N * LD;         // ff [LD]  sqrt(W) per row
   static constexpr size_t R = SW + sizeof(ff) * LD;             // float [N][RS] R (upper)
   static constexpr size_t ID = R + sizeof(float) * N * RS;      // float [N] 1 / r_ii
   static constexpr size_t TAU = ID + sizeof(float) * N;         // float [N]
-  static constexpr size_t PART = TAU + sizeof(float) * N;       // ff [32] partial sums
-  static constexpr size_t S = PART + sizeof(ff) * 32;           // ff [L][LD] s iterates
+  static constexpr size_t PART = TAU + sizeof(float) * N;       // ff [HW] partial sums
+  static constexpr size_t S = PART + sizeof(ff) * HW;           // ff [L][LD] s iterates
   // the rest depends on the number of solve rows L
   __host__ __device__ static size_t Y(int L) { return S + sizeof(ff) * L * LD; }      // ff [L][N]
   __host__ __device__ static size_t LAM(int L) { return Y(L) + sizeof(ff) * L * N; }  // ff [L][N]
@@ -52,96 +55,108 @@ struct FastLay {
   __host__ __device__ static size_t bytes(int L) { return (G(L) + sizeof(float) * L * N + 15) & ~size_t(15); }
 };
 
-__device__ __forceinline__ float wsum(float v) {
+// lanes of this thread's group of HW lanes
+template <int HW>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (HW == 32)
+    return 0xffffffffu;
+  else
+    return ((1u << HW) - 1u) << ((threadIdx.x & 31) & ~(HW - 1));
+}
+
+template <int HW>
+__device__ __forceinline__ float wsum(float v, unsigned mask) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = HW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, HW);
   return v;
 }
-__device__ __forceinline__ float wmax(float v) {
+template <int HW>
+__device__ __forceinline__ float wmax(float v, unsigned mask) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = HW / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, HW));
   return v;
 }
 
-// apply Q (REV: H_0 ... H_{N-1} z, i.e. reflectors in reverse order) or Q^T
-// to the row-distributed vectors z[l][i], l < L
-// All-reduce over the warp of v[B..N) (compile-time range): recursive halving
-// (each lane keeps the half of the values picked by its lane bit and adds its
-// partner's copy of that half) until every lane holds one total, butterflies
-// over the remaining lanes, then a broadcast of each total.  About 2(N - B)
-// shuffles instead of 5(N - B) for independent butterflies.
-template <int N, int B>
-__device__ __forceinline__ void allreduce_tail(float (&v)[N], int lane) {
+// All-reduce over the group of v[B..N) (compile-time range): recursive
+// halving (each lane keeps the half of the values picked by its lane bit and
+// adds its partner's copy of that half) for up to log2(HW) stages, butterflies
+// over the remaining lane bits, then a broadcast of each total.  About
+// 2(N - B) shuffles instead of log2(HW) (N - B) for independent butterflies.
+template <int HW, int N, int B>
+__device__ __forceinline__ void allreduce_tail(float (&v)[N], int lane, unsigned mask) {
   constexpr int C = N - B;
+  constexpr int LB = HW == 32 ? 5 : HW == 16 ? 4 : HW == 8 ? 3 : 2;
+  static_assert((1 << LB) == HW, "group width must be 4, 8, 16 or 32");
   if constexpr (C <= 0) {
     return;
   } else if constexpr (C <= 2) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = HW / 2; o > 0; o >>= 1)
 #pragma unroll
-      for (int c = B; c < N; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+      for (int c = B; c < N; ++c) v[c] += __shfl_xor_sync(mask, v[c], o, HW);
   } else {
-    constexpr int P = C <= 4 ? 4 : C <= 8 ? 8 : C <= 16 ? 16 : 32;
+    constexpr int P = C <= 4 ? 4 : C <= 8 ? 8 : C <= 16 ? 16 : C <= 32 ? 32 : 64;
+    constexpr int LP = P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : P == 32 ? 5 : 6;
+    constexpr int S = LP < LB ? LP : LB;  // halving stages
+    constexpr int M = P >> S;             // totals kept per lane afterwards
     float w[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) w[i] = (i < C) ? v[B + (i < C ? i : 0)] : 0.0f;
-    // halving: stage with offset o keeps P/2^s values; the kept half is the
-    // upper one on lanes whose bit o is set
-    int m = P;
+    // stage st (offset HW/2 >> st) keeps P >> (st+1) values: the upper half
+    // on lanes whose bit is set
 #pragma unroll
-    for (int o = 16; o > 0 && m > 1; o >>= 1) {
+    for (int st = 0; st < S; ++st) {
+      const int o = (HW / 2) >> st;
       const bool up = (lane & o) != 0;
-      const int h = m >> 1;
+      const int h = P >> (st + 1);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < P / 2; ++i) {
         if (i < h) {
           const float send = up ? w[i] : w[i + h];
           const float keep = up ? w[i + h] : w[i];
-          w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          w[i] = keep + __shfl_xor_sync(mask, send, o, HW);
         }
       }
-      m = h;
     }
-    // lanes sharing a value index add up across the remaining lane bits
-    constexpr int used = P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : 5;  // stages done
+    // lanes holding the same totals add up across the remaining lane bits
 #pragma unroll
-    for (int o = 16 >> used; o > 0; o >>= 1) w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
-    // value index held by a lane: its top `used` bits (offsets 16, 8, ...)
+    for (int o = (HW / 2) >> S; o > 0; o >>= 1)
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      // the lane whose top bits spell i (others bits zero) holds total i
-      const int src = i << (5 - used);
-      v[B + i] = __shfl_sync(0xffffffffu, w[0], src);
-    }
+      for (int i = 0; i < M; ++i) w[i] += __shfl_xor_sync(mask, w[i], o, HW);
+    // total c sits in w[c % M] of the lanes whose top S bits spell c / M
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[B + c] = __shfl_sync(mask, w[c % M], (c / M) << (LB - S), HW);
   }
 }
 
 // One Householder step on column KC of the register tile: reflector from
 // rows > KC, then the trailing columns (dot products all-reduced together).
-template <int MR, int N, int KC>
-__device__ __forceinline__ void qr_column(float (&a)[MR][N], float* tau, int lane) {
+template <int HW, int MR, int N, int KC>
+__device__ __forceinline__ void qr_column(float (&a)[MR][N], float* tau, int lane, unsigned mask) {
   float sig = 0.0f;
 #pragma unroll
   for (int i = 0; i < MR; ++i)
-    if (lane + 32 * i > KC) sig = fmaf(a[i][KC], a[i][KC], sig);
-  sig = wsum(sig);
-  const float alpha = __shfl_sync(0xffffffffu, a[KC / 32][KC], KC % 32);
+    if (lane + HW * i > KC) sig = fmaf(a[i][KC], a[i][KC], sig);
+  sig = wsum<HW>(sig, mask);
+  const float alpha = __shfl_sync(mask, a[KC / HW][KC], KC % HW, HW);
   float tk = 0.0f, beta = alpha;
   if (sig > 0.0f) {
     const float nrm = sqrtf(fmaf(alpha, alpha, sig));
     beta = alpha >= 0.0f ? -nrm : nrm;
-    const float scale = 1.0f / (alpha - beta);
-    tk = (beta - alpha) / beta;
+    // approximate quotients (a few ulp): the reflector's scaling and tau
+    // only need FP32 accuracy, the refinement absorbs the rest
+    const float scale = __fdividef(1.0f, alpha - beta);
+    tk = __fdividef(beta - alpha, beta);
 #pragma unroll
     for (int i = 0; i < MR; ++i)
-      if (lane + 32 * i > KC) a[i][KC] *= scale;
+      if (lane + HW * i > KC) a[i][KC] *= scale;
   }
-  if (lane == KC % 32) a[KC / 32][KC] = beta;
+  if (lane == KC % HW) a[KC / HW][KC] = beta;
   if (lane == 0) tau[KC] = tk;
   float v[MR];
 #pragma unroll
   for (int i = 0; i < MR; ++i) {
-    const int r = lane + 32 * i;
+    const int r = lane + HW * i;
     v[i] = (r > KC) ? a[i][KC] : (r == KC ? 1.0f : 0.0f);
   }
   float dots[N];
@@ -152,7 +167,7 @@ __device__ __forceinline__ void qr_column(float (&a)[MR][N], float* tau, int lan
     for (int i = 0; i < MR; ++i) p = fmaf(v[i], a[i][c], p);
     dots[c] = p;
   }
-  allreduce_tail<N, KC + 1>(dots, lane);
+  allreduce_tail<HW, N, KC + 1>(dots, lane, mask);
 #pragma unroll
   for (int c = KC + 1; c < N; ++c) {
     const float tc = dots[c] * tk;
@@ -161,13 +176,17 @@ __device__ __forceinline__ void qr_column(float (&a)[MR][N], float* tau, int lan
   }
 }
 
-template <int MR, int N, int... K>
-__device__ __forceinline__ void qr_columns(float (&a)[MR][N], float* tau, int lane, std::integer_sequence<int, K...>) {
-  (qr_column<MR, N, K>(a, tau, lane), ...);
+template <int HW, int MR, int N, int... K>
+__device__ __forceinline__ void qr_columns(float (&a)[MR][N], float* tau, int lane, unsigned mask,
+                                           std::integer_sequence<int, K...>) {
+  (qr_column<HW, MR, N, K>(a, tau, lane, mask), ...);
 }
 
-template <int MR, int N, int L, bool REV>
-__device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const float* tau, float (&z)[L][MR], int lane) {
+// apply Q (REV: H_0 ... H_{N-1} z, i.e. reflectors in reverse order) or Q^T
+// to the row-distributed vectors z[l][i], l < L
+template <int HW, int MR, int N, int L, bool REV>
+__device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const float* tau, float (&z)[L][MR], int lane,
+                                             unsigned mask) {
 #pragma unroll
   for (int s = 0; s < N; ++s) {
     const int k = REV ? N - 1 - s : s;
@@ -175,7 +194,7 @@ __device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const floa
     float v[MR];
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
-      const int r = lane + 32 * i;
+      const int r = lane + HW * i;
       v[i] = (r > k) ? a[i][k] : (r == k ? 1.0f : 0.0f);
     }
     float d[L];
@@ -186,9 +205,9 @@ __device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const floa
       for (int i = 0; i < MR; ++i) d[l] = fmaf(v[i], z[l][i], d[l]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o = HW / 2; o > 0; o >>= 1)
 #pragma unroll
-      for (int l = 0; l < L; ++l) d[l] += __shfl_xor_sync(0xffffffffu, d[l], o);
+      for (int l = 0; l < L; ++l) d[l] += __shfl_xor_sync(mask, d[l], o, HW);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       const float dl = d[l] * tk;
@@ -198,21 +217,21 @@ __device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const floa
   }
 }
 
-// w <- R^{-T} w (forward substitution), w[l][t] holds entry p = lane + 32 t
-template <int N, int L>
-__device__ __forceinline__ void solve_rt_lanes(const float* Rs, int RS, const float* idg, float (&w)[L][(N + 31) / 32],
-                                               int lane) {
-  constexpr int NT = (N + 31) / 32;
+// w <- R^{-T} w (forward substitution), w[l][t] holds entry p = lane + HW t
+template <int HW, int N, int L>
+__device__ __forceinline__ void solve_rt_lanes(const float* Rs, int RS, const float* idg,
+                                               float (&w)[L][(N + HW - 1) / HW], int lane, unsigned mask) {
+  constexpr int NT = (N + HW - 1) / HW;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const float inv = idg[i];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      const float yi = __shfl_sync(0xffffffffu, w[l][i / 32], i % 32) * inv;
-      if (lane == i % 32) w[l][i / 32] = yi;
+      const float yi = __shfl_sync(mask, w[l][i / HW], i % HW, HW) * inv;
+      if (lane == i % HW) w[l][i / HW] = yi;
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const int p = lane + 32 * t;
+        const int p = lane + HW * t;
         if (p > i && p < N) w[l][t] = fmaf(-Rs[i * RS + p], yi, w[l][t]);
       }
     }
@@ -220,38 +239,47 @@ __device__ __forceinline__ void solve_rt_lanes(const float* Rs, int RS, const fl
 }
 
 // w <- R^{-1} w (back substitution)
-template <int N, int L>
-__device__ __forceinline__ void solve_r_lanes(const float* Rs, int RS, const float* idg, float (&w)[L][(N + 31) / 32],
-                                              int lane) {
-  constexpr int NT = (N + 31) / 32;
+template <int HW, int N, int L>
+__device__ __forceinline__ void solve_r_lanes(const float* Rs, int RS, const float* idg,
+                                              float (&w)[L][(N + HW - 1) / HW], int lane, unsigned mask) {
+  constexpr int NT = (N + HW - 1) / HW;
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
     const float inv = idg[i];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      const float yi = __shfl_sync(0xffffffffu, w[l][i / 32], i % 32) * inv;
-      if (lane == i % 32) w[l][i / 32] = yi;
+      const float yi = __shfl_sync(mask, w[l][i / HW], i % HW, HW) * inv;
+      if (lane == i % HW) w[l][i / HW] = yi;
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
-        const int p = lane + 32 * t;
+        const int p = lane + HW * t;
         if (p < i) w[l][t] = fmaf(-Rs[p * RS + i], yi, w[l][t]);
       }
     }
   }
 }
 
-template <int KIND, int D, int DEG, int MR, int L>
-__global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
+// Small register tiles keep three 4-warp blocks resident (at most 168
+// registers per thread); larger ones are left to the register allocator.
+template <int HW, int MR, int N, int L>
+constexpr int fast_min_blocks() {
+  return MR * N * L <= 90 ? 3 : 1;
+}
+
+template <int KIND, int D, int DEG, int MR, int L, int HW>
+__global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()))
+    stencil_fast_kernel(StencilJob j) {
   constexpr int N = gmls_gen::basis_size(KIND, D, DEG);
   constexpr int NC = (KIND == GMLS_BASIS_SCALAR) ? 1 : D;
-  constexpr int ROWS = 32 * MR;
-  constexpr int NT = (N + 31) / 32;
-  using Lay = FastLay<MR, N>;
+  constexpr int ROWS = HW * MR;
+  constexpr int NT = (N + HW - 1) / HW;
+  using Lay = FastLay<HW, MR, N>;
   constexpr int LD = Lay::LD, RS = Lay::RS;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  unsigned char* base = smem + (size_t)warp * Lay::bytes(L);
+  const int grp = threadIdx.x / HW, lane = threadIdx.x & (HW - 1);
+  const int gpb = blockDim.x / HW;
+  const unsigned mask = group_mask<HW>();
+  unsigned char* base = smem + (size_t)grp * Lay::bytes(L);
   ff* Bs = reinterpret_cast<ff*>(base + Lay::B);
   ff* SWs = reinterpret_cast<ff*>(base + Lay::SW);
   ff* Ss = reinterpret_cast<ff*>(base + Lay::S);
@@ -266,7 +294,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
   const float tolf = (float)j.tol;
 
-  for (int64_t it = (int64_t)blockIdx.x * wpb + warp; it < n_items; it += (int64_t)gridDim.x * wpb) {
+  for (int64_t it = (int64_t)blockIdx.x * gpb + grp; it < n_items; it += (int64_t)gridDim.x * gpb) {
     const int64_t to = j.items ? (int64_t)j.items[it] : it;
     const int64_t t = j.tgt[to];
     const int64_t o0 = j.off[to];
@@ -288,10 +316,10 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
       for (int f = 0; f < j.nout; ++f) {
         const int64_t cnt = (int64_t)j.out_rows[f] * k * j.out_ncomp[f];
         double* w = j.out_w[f] + o0 * (int64_t)j.out_rows[f] * j.out_ncomp[f];
-        for (int64_t e = lane; e < cnt; e += 32) w[e] = 0.0;
+        for (int64_t e = lane; e < cnt; e += HW) w[e] = 0.0;
       }
       if (j.beta)
-        for (int l = lane; l < L; l += 32) j.beta[to * L + l] = 0.0;
+        for (int l = lane; l < L; l += HW) j.beta[to * L + l] = 0.0;
       if (lane == 0) {
         j.status[to] = st;
         if (j.iters) j.iters[to] = 0;
@@ -309,7 +337,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
       xtl[c] = j.xl[c * n + t];
     }
     const int half_p = j.wpow_half;
-    for (int q = lane; q < ROWS / NC; q += 32) {
+    for (int q = lane; q < ROWS / NC; q += HW) {
       if (q < k) {
         const int32_t jj = j.idx[o0 + q];
         ff dx[3], xi[3];
@@ -339,32 +367,32 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
       }
     }
     // rows past the last whole neighbour (ROWS not a multiple of NC)
-    for (int r = (ROWS / NC) * NC + lane; r < ROWS; r += 32) {
+    for (int r = (ROWS / NC) * NC + lane; r < ROWS; r += HW) {
       SWs[r] = ff(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < N; ++i) Bs[i * LD + r] = ff(0.f, 0.f);
     }
     // functional rows (float-float), lanes over (row, column)
-    for (int e = lane; e < L * N; e += 32) {
+    for (int e = lane; e < L * N; e += HW) {
       const int l = e / N, i = e % N;
       ff f(gmls_gen::lam_coef_f(KIND, D, DEG, j.lam_fn[l], j.lam_row[l], i), 0.0f);
       for (int p = 0; p < j.lam_order[l]; ++p) f = f * inv_eps;
       LAMs[l * N + i] = f;
     }
-    __syncwarp();
+    __syncwarp(mask);
 
     // ---- 2. FP32 Householder QR in registers
     float a[MR][N];
 #pragma unroll
     for (int i = 0; i < MR; ++i)
 #pragma unroll
-      for (int c = 0; c < N; ++c) a[i][c] = Bs[c * LD + lane + 32 * i].h;
-    qr_columns<MR, N>(a, TAUs, lane, std::make_integer_sequence<int, N>{});
+      for (int c = 0; c < N; ++c) a[i][c] = Bs[c * LD + lane + HW * i].h;
+    qr_columns<HW, MR, N>(a, TAUs, lane, mask, std::make_integer_sequence<int, N>{});
     // stage R, 1/r_ii; conditioning of the factor
     float rmax = 0.0f, rmin = 3.0e38f;
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
-      const int r = lane + 32 * i;
+      const int r = lane + HW * i;
       if (r < N) {
 #pragma unroll
         for (int c = 0; c < N; ++c) Rs[r * RS + c] = (c >= r) ? a[i][c] : 0.0f;
@@ -377,151 +405,138 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
         rmin = fminf(rmin, fabsf(d));
       }
     }
-    rmax = wmax(rmax);
-    rmin = -wmax(-rmin);
-    __syncwarp();
+    rmax = wmax<HW>(rmax, mask);
+    rmin = -wmax<HW>(-rmin, mask);
+    __syncwarp(mask);
     const bool ill = !(rmin * 1.0e6f >= rmax) || !(rmin > 0.0f);
 
-    // ---- 3. initial FP32 solve: y0 = R^{-T} lambda, s0 = Q [y0; 0], y = R^{-1} y0
+    // ---- 3./4. solve and refinement with float-float residuals.  Pass 0 is
+    // the plain FP32 solve, i.e. a refinement step from s = y = 0 (f = 0,
+    // g = lambda): a = R^{-T} lambda, s0 = Q [a; 0], y0 = R^{-1} a.  Passes
+    // it >= 1 correct with the residuals f = B y - s and g = lambda - B^T s:
+    // d = Q^T f, a = R^{-T} g, dy = R^{-1} (a - d_1), ds = Q [a; d_2].  One
+    // copy of the solve code serves all passes (the kernel is large enough
+    // for instruction fetch to matter).
     float w[L][NT];
     float z[L][MR];
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-      for (int tt = 0; tt < NT; ++tt) {
-        const int p = lane + 32 * tt;
-        w[l][tt] = (p < N) ? LAMs[l * N + p].h : 0.0f;
-      }
-    solve_rt_lanes<N, L>(Rs, RS, IDs, w, lane);
-#pragma unroll
-    for (int l = 0; l < L; ++l)
-#pragma unroll
-      for (int i = 0; i < MR; ++i) {
-        const int r = lane + 32 * i;
-        z[l][i] = (i < NT && r < N) ? w[l][i < NT ? i : 0] : 0.0f;
-      }
-    apply_q_regs<MR, N, L, true>(a, TAUs, z, lane);
-    solve_r_lanes<N, L>(Rs, RS, IDs, w, lane);
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-#pragma unroll
-      for (int i = 0; i < MR; ++i) Ss[l * LD + lane + 32 * i] = ff(z[l][i], 0.0f);
-#pragma unroll
-      for (int tt = 0; tt < NT; ++tt) {
-        const int p = lane + 32 * tt;
-        if (p < N) Ys[l * N + p] = ff(w[l][tt], 0.0f);
-      }
-    }
-    __syncwarp();
-
-    // ---- 4. refinement with float-float residuals
     bool conv = false;
     int used = 0;
     float prev = 0.0f;
-    for (int iter = 0; iter < j.max_refine && !ill; ++iter) {
-      // f = B y - s, lanes over rows
+#pragma unroll 1
+    for (int it = 0; it <= j.max_refine; ++it) {
+      if (it > 0) {
+        if (ill) break;
+        // f = B y - s, lanes over rows
 #pragma unroll
-      for (int l = 0; l < L; ++l) {
+        for (int l = 0; l < L; ++l) {
 #pragma unroll
-        for (int i = 0; i < MR; ++i) {
-          const int r = lane + 32 * i;
-          Dot2 acc;
-          acc.init(-Ss[l * LD + r]);
+          for (int i = 0; i < MR; ++i) {
+            const int r = lane + HW * i;
+            Dot2 acc;
+            acc.init(-Ss[l * LD + r]);
 #pragma unroll
-          for (int c = 0; c < N; ++c) acc.add_prod(Bs[c * LD + r], Ys[l * N + c]);
-          z[l][i] = __fadd_rn(acc.h, acc.l);
-        }
-      }
-      // g = lambda - B^T s over the L*N (l, c) pairs: whole pairs per lane in
-      // full rounds of 32, the remaining pairs split into row blocks so that
-      // every lane does about the same number of terms
-      {
-        const int pairs = L * N, full = pairs / 32, rem = pairs % 32;
-        for (int u = 0; u < full; ++u) {
-          const int e = u * 32 + lane, l = e / N, c = e % N;
-          // four independent compensated chains over interleaved rows (ILP)
-          Dot2 acc[4];
-          acc[0].init(LAMs[l * N + c]);
-          const ff* bc = Bs + c * LD;
-          const ff* sl = Ss + l * LD;
-#pragma unroll 2
-          for (int r = 0; r < ROWS; r += 4) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (r + q < ROWS) acc[q].add_prod(-bc[r + q], sl[r + q]);
+            for (int c = 0; c < N; ++c) acc.add_prod(Bs[c * LD + r], Ys[l * N + c]);
+            z[l][i] = __fadd_rn(acc.h, acc.l);
           }
-          const ff tot = (acc[0].value() + acc[1].value()) + (acc[2].value() + acc[3].value());
-          Gs[l * N + c] = __fadd_rn(tot.h, tot.l);
         }
-        if (rem) {
-          const int nblk = 32 / rem, chunk = (ROWS + nblk - 1) / nblk;
-          const int e = full * 32 + lane % rem, blk = lane / rem;
-          Dot2 acc;
-          if (blk < nblk) {
-            const int l = e / N, c = e % N;
+        // g = lambda - B^T s over the L*N (l, c) pairs: whole pairs per lane
+        // in full rounds of HW, the remaining pairs split into row blocks so
+        // that every lane does about the same number of terms
+        {
+          constexpr int pairs = L * N, full = pairs / HW, rem = pairs % HW;
+          for (int u = 0; u < full; ++u) {
+            const int e = u * HW + lane, l = e / N, c = e % N;
+            // four independent compensated chains over interleaved rows (ILP)
+            Dot2 acc[4];
+            acc[0].init(LAMs[l * N + c]);
             const ff* bc = Bs + c * LD;
             const ff* sl = Ss + l * LD;
-            const int r1 = min(ROWS, (blk + 1) * chunk);
-            for (int r = blk * chunk; r < r1; ++r) acc.add_prod(-bc[r], sl[r]);
-            PARTs[lane] = acc.value();
+#pragma unroll 2
+            for (int r = 0; r < ROWS; r += 4) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (r + q < ROWS) acc[q].add_prod(-bc[r + q], sl[r + q]);
+            }
+            const ff tot = (acc[0].value() + acc[1].value()) + (acc[2].value() + acc[3].value());
+            Gs[l * N + c] = __fadd_rn(tot.h, tot.l);
           }
-          __syncwarp();
-          if (lane < rem) {
-            const int l = e / N, c = e % N;
-            ff sum = LAMs[l * N + c];
-            for (int b = 0; b < nblk; ++b) sum = sum + PARTs[b * rem + lane];
-            Gs[l * N + c] = __fadd_rn(sum.h, sum.l);
+          if constexpr (rem > 0) {
+            constexpr int nblk = HW / rem, chunk = (ROWS + nblk - 1) / nblk;
+            const int e = full * HW + lane % rem, blk = lane / rem;
+            Dot2 acc;
+            if (blk < nblk) {
+              const int l = e / N, c = e % N;
+              const ff* bc = Bs + c * LD;
+              const ff* sl = Ss + l * LD;
+              const int r1 = min(ROWS, (blk + 1) * chunk);
+              for (int r = blk * chunk; r < r1; ++r) acc.add_prod(-bc[r], sl[r]);
+              PARTs[lane] = acc.value();
+            }
+            __syncwarp(mask);
+            if (lane < rem) {
+              const int l = e / N, c = e % N;
+              ff sum = LAMs[l * N + c];
+              for (int b = 0; b < nblk; ++b) sum = sum + PARTs[b * rem + lane];
+              Gs[l * N + c] = __fadd_rn(sum.h, sum.l);
+            }
           }
         }
+        __syncwarp(mask);
+        apply_q_regs<HW, MR, N, L, false>(a, TAUs, z, lane, mask);  // d = Q^T f
+      } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int i = 0; i < MR; ++i) z[l][i] = 0.0f;
       }
-      __syncwarp();
-      // d = Q^T f ; a = R^{-T} g ; dy = R^{-1} (a - d_1) ; ds = Q [a; d_2]
-      apply_q_regs<MR, N, L, false>(a, TAUs, z, lane);
 #pragma unroll
       for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int tt = 0; tt < NT; ++tt) {
-          const int p = lane + 32 * tt;
-          w[l][tt] = (p < N) ? Gs[l * N + p] : 0.0f;
+          const int p = lane + HW * tt;
+          w[l][tt] = (p < N) ? (it > 0 ? Gs[l * N + p] : LAMs[l * N + p].h) : 0.0f;
         }
-      solve_rt_lanes<N, L>(Rs, RS, IDs, w, lane);
+      solve_rt_lanes<HW, N, L>(Rs, RS, IDs, w, lane, mask);  // a = R^{-T} g
       float dyv[L][NT];
 #pragma unroll
       for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int tt = 0; tt < NT; ++tt) {
-          const int p = lane + 32 * tt;
+          const int p = lane + HW * tt;
           // rows r < N of z sit in the same lane/slot as entry p = r
           dyv[l][tt] = (p < N) ? w[l][tt] - z[l][tt < MR ? tt : 0] : 0.0f;
           if (p < N && tt < MR) z[l][tt < MR ? tt : 0] = w[l][tt];
         }
-      solve_r_lanes<N, L>(Rs, RS, IDs, dyv, lane);
-      apply_q_regs<MR, N, L, true>(a, TAUs, z, lane);
+      solve_r_lanes<HW, N, L>(Rs, RS, IDs, dyv, lane, mask);   // dy
+      apply_q_regs<HW, MR, N, L, true>(a, TAUs, z, lane, mask);  // ds = Q [a; d_2]
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
       for (int l = 0; l < L; ++l) {
 #pragma unroll
         for (int i = 0; i < MR; ++i) {
-          const int r = lane + 32 * i;
-          const ff s1 = add_f(Ss[l * LD + r], z[l][i]);
+          const int r = lane + HW * i;
+          const ff s1 = (it > 0) ? add_f(Ss[l * LD + r], z[l][i]) : ff(z[l][i], 0.0f);
           Ss[l * LD + r] = s1;
           dmax = fmaxf(dmax, fabsf(z[l][i]));
           smax = fmaxf(smax, fabsf(s1.h));
         }
 #pragma unroll
         for (int tt = 0; tt < NT; ++tt) {
-          const int p = lane + 32 * tt;
-          if (p < N) Ys[l * N + p] = add_f(Ys[l * N + p], dyv[l][tt]);
+          const int p = lane + HW * tt;
+          if (p < N) Ys[l * N + p] = (it > 0) ? add_f(Ys[l * N + p], dyv[l][tt]) : ff(dyv[l][tt], 0.0f);
         }
       }
-      dmax = wmax(dmax);
-      smax = wmax(smax);
-      __syncwarp();
-      used = iter + 1;
+      if (it > 0) {
+        dmax = wmax<HW>(dmax, mask);
+        smax = wmax<HW>(smax, mask);
+      }
+      __syncwarp(mask);
+      if (it == 0) continue;
+      used = it;
       // error left after this correction ~ |ds| times the contraction factor,
-      // estimated by the relative size of the correction (first iteration) or
-      // by the ratio of successive corrections (later ones)
-      const float rho = (iter == 0) ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
+      // estimated by the relative size of the correction (first refinement
+      // step) or by the ratio of successive corrections (later ones)
+      const float rho = (it == 1) ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
       const float est = dmax * fminf(1.0f, rho);
       conv = est <= tolf * smax;
       prev = dmax;
@@ -544,7 +559,7 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
       const bool div_scalar = (j.out_fn[f] == GMLS_F_DIV) && (KIND == GMLS_BASIS_SCALAR);
       const float sgn = (float)j.out_sign[f];
       for (int rr = 0; rr < R; ++rr) {
-        for (int e = lane; e < per_row; e += 32) {
+        for (int e = lane; e < per_row; e += HW) {
           double val = 0.0;
           if (src >= 0) {
             if (div_scalar) {
@@ -561,26 +576,26 @@ __global__ void __launch_bounds__(128) stencil_fast_kernel(StencilJob j) {
       }
     }
     if (j.beta)
-      for (int l = lane; l < L; l += 32) j.beta[to * L + l] = 0.0;
+      for (int l = lane; l < L; l += HW) j.beta[to * L + l] = 0.0;
     if (lane == 0) {
       j.status[to] = st;
       if (j.iters) j.iters[to] = (uint8_t)used;
     }
-    __syncwarp();
+    __syncwarp(mask);
   }
 }
 
 // ----------------------------------------------------------------- dispatch
 struct FastEntry {
-  int kind, dim, deg, mr, L;
+  int kind, dim, deg, mr, L, hw;
   const void* fn;
-  size_t (*bytes)(int L);
+  size_t (*bytes)(int L);  // shared memory per group (target)
 };
 
-#define GMLS_FAST(KIND, D, DEG, MR, L)                                                                                \
+#define GMLS_FAST(KIND, D, DEG, MR, L, HW)                                                                            \
   FastEntry {                                                                                                          \
-    KIND, D, DEG, MR, L, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L>,                                        \
-        &FastLay<MR, gmls_gen::basis_size(KIND, D, DEG)>::bytes                                                        \
+    KIND, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L, HW>,                                \
+        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG)>::bytes                                                    \
   }
 
 }  // namespace gmls

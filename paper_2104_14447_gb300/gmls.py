@@ -44,7 +44,7 @@ EXPORTED = [
     "gmls_server_stats", "gmls_server_destroy",
 ]
 NOALLOC_MAX_POINTS = 262144
-OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING = 0, 1, 2
+OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT = 0, 1, 2, 3
 T_UNSUPPORTED = 64
 
 
