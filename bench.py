@@ -11,8 +11,10 @@ whole hot path:
   96 x 20 systems; vector Laplacian) -> three CSR operators.
 
 value: targets/s of the whole job (every target gets all three operators).
-The default precision is FP32 Householder QR with FP64-residual refinement;
-``--precision fp64`` times the plain FP64 path.
+The default precision is FP32 Householder QR with refinement against
+float-float (FP64-class) residuals; ``--precision fp64`` times the plain FP64
+path.  The 36-nearest lists are the first 36 entries of the 48-nearest lists
+(one search; both are prefixes of the same (d^2, id) order).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 it runs under torch.distributed.run, one rank per GPU; every rank

@@ -535,7 +535,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
   const GridParams g = *cl.grid;
   constexpr int dim = D;
   const QueryGeo gq = make_query_geo(g, dim);
-  // unit-ball volume and the initial radius: about 1.5 k particles expected
+  // unit-ball volume and the initial radius: about 1.2 k particles expected
+  // (on quasi-uniform clouds the count then stays between k and the next
+  // power of two above k, which keeps the sort short)
   const double ball = (dim == 1) ? 2.0 : (dim == 2) ? 3.141592653589793 : 4.1887902047863905;
   const double dens = (double)cl.n / (g.volume > 0.0 ? g.volume : 1.0);
   const float inv_dens_ball = (float)(1.0 / (dens * ball));
@@ -564,17 +566,18 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     // search radius R in FP32 (any value is correct: the search widens or
     // narrows it); the exact test is d2 < R2 = fl32(R * R) in FP64, and the
     // box half-width R (1 + 2^-20) covers sqrt(R2)
-    float R = powf(1.5f * (float)kq * inv_dens_ball, 1.0f / (float)dim);
+    float R = powf(1.2f * (float)kq * inv_dens_ball, 1.0f / (float)dim);
     int count = 0;
     for (int attempt = 0; attempt < 64; ++attempt) {
       count = gather_candidates<D>(cl, g, gq, xT, xTf, R * (1.0f + 0x1p-20f), (double)(R * R), use_hs, nrm, wb);
+      // rescale R by the count it gave (ball volume ~ R^dim), within bounds
       if (count > wb.cap) {
-        R *= 0.75f;
+        R *= fmaxf(0.5f, fminf(0.9f, powf(0.8f * (float)wb.cap / (float)count, 1.0f / (float)dim)));
         continue;
       }
       if (count >= kq) break;
       if (R > big) break;  // whole cloud inside: too few exist
-      R *= 1.6f;
+      R *= (count > 0) ? fminf(2.0f, fmaxf(1.1f, powf(1.3f * (float)kq / (float)count, 1.0f / (float)dim))) : 2.0f;
     }
     if (count > wb.cap) {  // could not bring the candidate set under the buffer size
       st |= GMLS_T_OVERFLOW;
