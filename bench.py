@@ -65,11 +65,11 @@ DOT2_FLOPS = 15
 
 
 # DRAM bytes (read + write) per target of the divergence-free register-kernel
-# launch, from ncu on the 384 x 384 grid (147,456 targets: 33.96 MB read,
-# 168.97 MB written); the algorithmic floor is the 1,536 B of FP64 weights
+# launch, from ncu on the 384 x 384 grid (147,456 targets: 33.95 MB read,
+# 168.58 MB written); the algorithmic floor is the 1,536 B of FP64 weights
 # per target (2 rows x 48 neighbours x 2 components), some of which is still
 # in L2 when the kernel ends
-DIVFREE_DRAM_BYTES_PER_TARGET = (33.957120e6 + 168.969728e6) / 147456
+DIVFREE_DRAM_BYTES_PER_TARGET = (33.947648e6 + 168.576256e6) / 147456
 
 
 def flops_per_target(M, n, rows, iters):

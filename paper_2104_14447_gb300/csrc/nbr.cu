@@ -54,7 +54,25 @@ __global__ void bbox_partial_kernel(int dim, int64_t n, const double* __restrict
 
 __global__ void grid_finalize_kernel(int dim, int nparts, const double* __restrict__ part, int nc0, int nc1, int nc2,
                                      GridParams* __restrict__ g) {
-  if (threadIdx.x != 0) return;
+  // one warp: the lanes reduce the block partials (min / max are exact, so
+  // the order does not matter), lane 0 writes the grid
+  const int lane = threadIdx.x & 31;
+  double lo3[3], hi3[3];
+  for (int c = 0; c < kMaxDim; ++c) {
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    if (c < dim)
+      for (int p = lane; p < nparts; p += 32) {
+        lo = fmin(lo, part[(p * 3 + c) * 2 + 0]);
+        hi = fmax(hi, part[(p * 3 + c) * 2 + 1]);
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    lo3[c] = lo;
+    hi3[c] = hi;
+  }
+  if (lane != 0) return;
   int ncs[3] = {nc0, nc1, nc2};
   double vol = 1.0;
   for (int c = 0; c < kMaxDim; ++c) {
@@ -65,11 +83,7 @@ __global__ void grid_finalize_kernel(int dim, int nparts, const double* __restri
       g->nc[c] = 1;
       continue;
     }
-    double lo = DBL_MAX, hi = -DBL_MAX;
-    for (int p = 0; p < nparts; ++p) {
-      lo = fmin(lo, part[(p * 3 + c) * 2 + 0]);
-      hi = fmax(hi, part[(p * 3 + c) * 2 + 1]);
-    }
+    const double lo = lo3[c], hi = hi3[c];
     double ext = hi - lo;
     int nc = ncs[c];
     if (!(ext > 0.0)) {  // flat axis: one cell, every point maps to it
@@ -663,18 +677,22 @@ cudaError_t launch_fill_identity(const Launch& L, int32_t* out, int64_t n) {
 
 // The k' nearest of a target are the first k' entries of its k-nearest list
 // (both are prefixes of one total order by (d^2, id)); eps' = f * sqrt(d^2 of
-// entry k'-1), with d^2 recomputed by the search's exact formula.
+// entry k'-1), with d^2 recomputed by the search's exact formula.  A warp
+// takes 32 consecutive targets: lane l computes eps' of target l, then the
+// warp copies the 32 k'-prefixes as one contiguous, coalesced output range.
 __global__ void nbr_prefix_kernel(int dim, int64_t n, const double* __restrict__ x, const int32_t* __restrict__ tgt,
                                   int64_t n_tgt, const int32_t* __restrict__ idx, int k, int kp, double eps_factor,
                                   int32_t* __restrict__ out_idx, double* __restrict__ out_eps,
                                   uint8_t* __restrict__ out_status) {
   const int lane = threadIdx.x & 31;
-  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n_tgt;
-       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int32_t* src = idx + t * k;
-    for (int i = lane; i < kp; i += 32) out_idx[t * kp + i] = src[i];
-    if (lane == 0) {
-      const int32_t last = src[kp - 1];
+  const int64_t n_tiles = (n_tgt + 31) >> 5;
+  for (int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; tile < n_tiles;
+       tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t t0 = tile << 5;
+    const int nt = (int)((n_tgt - t0) < 32 ? (n_tgt - t0) : 32);
+    if (lane < nt) {
+      const int64_t t = t0 + lane;
+      const int32_t last = idx[t * k + kp - 1];
       if (last < 0) {
         out_eps[t] = 0.0;
         out_status[t] = GMLS_T_TOO_FEW_NEIGHBOURS;
@@ -686,6 +704,18 @@ __global__ void nbr_prefix_kernel(int dim, int64_t n, const double* __restrict__
         out_status[t] = 0;
       }
     }
+    // element e of the tile's output is entry (e % kp) of target e / kp;
+    // the quotient and remainder are carried along instead of divided
+    const int total = nt * kp;
+    int q = lane / kp, r = lane - (lane / kp) * kp;
+    for (int e = lane; e < total; e += 32) {
+      out_idx[t0 * kp + e] = idx[(t0 + q) * k + r];
+      r += 32;
+      while (r >= kp) {
+        r -= kp;
+        ++q;
+      }
+    }
   }
 }
 
@@ -693,8 +723,9 @@ cudaError_t launch_nbr_prefix(const Launch& L, int dim, int64_t n, const double*
                               const int32_t* idx, int k, int kp, double eps_factor, int32_t* out_idx, double* out_eps,
                               uint8_t* out_status) {
   if (n_tgt == 0) return cudaSuccess;
-  nbr_prefix_kernel<<<blocks_for(n_tgt * 32, 256), 256, 0, L.stream>>>(dim, n, x, tgt, n_tgt, idx, k, kp, eps_factor,
-                                                                        out_idx, out_eps, out_status);
+  nbr_prefix_kernel<<<blocks_for((n_tgt + 31) / 32 * 32, 256), 256, 0, L.stream>>>(dim, n, x, tgt, n_tgt, idx, k, kp,
+                                                                                     eps_factor, out_idx, out_eps,
+                                                                                     out_status);
   *L.counter += 1;
   return cudaGetLastError();
 }

@@ -37,23 +37,31 @@
 
 namespace gmls {
 
-template <int HW, int MR, int N>
+// Shared memory of one group (one target in flight), kept small so that
+// twelve warps fit on an SM for the 96 x 20 systems.
+template <int HW, int MR, int N, int NC>
 struct FastLay {
   static constexpr int LD = HW * MR + 1;  // odd: column walks by different lanes avoid bank conflicts
-  static constexpr int RS = N | 1;        // odd row stride of the staged triangular factor
+  static constexpr int NQ = (HW * MR + NC - 1) / NC;            // neighbour slots
+  static constexpr int NR = N * (N + 1) / 2;                    // packed upper triangle
   static constexpr size_t B = 0;                                // ff [N][LD]
-  static constexpr size_t SW = B + sizeof(ff) * N * LD;         // ff [LD]  sqrt(W) per row
-  static constexpr size_t R = SW + sizeof(ff) * LD;             // float [N][RS] R (upper)
-  static constexpr size_t ID = R + sizeof(float) * N * RS;      // float [N] 1 / r_ii
+  static constexpr size_t SW = B + sizeof(ff) * N * LD;         // ff [NQ]  sqrt(W) per neighbour
+  static constexpr size_t R = SW + sizeof(ff) * NQ;             // float [NR] R, rows packed
+  static constexpr size_t ID = R + sizeof(float) * NR;          // float [N] 1 / r_ii
   static constexpr size_t TAU = ID + sizeof(float) * N;         // float [N]
-  static constexpr size_t PART = TAU + sizeof(float) * N;       // ff [HW] partial sums
-  static constexpr size_t S = PART + sizeof(ff) * HW;           // ff [L][LD] s iterates
+  static constexpr size_t IEPS = (TAU + sizeof(float) * N + 7) & ~size_t(7);  // ff: 1 / eps
+  static constexpr size_t S = IEPS + sizeof(ff);                // ff [L][LD] s iterates
   // the rest depends on the number of solve rows L
   __host__ __device__ static size_t Y(int L) { return S + sizeof(ff) * L * LD; }      // ff [L][N]
-  __host__ __device__ static size_t LAM(int L) { return Y(L) + sizeof(ff) * L * N; }  // ff [L][N]
-  __host__ __device__ static size_t G(int L) { return LAM(L) + sizeof(ff) * L * N; }  // float [L][N]
+  __host__ __device__ static size_t G(int L) { return Y(L) + sizeof(ff) * L * N; }    // float [L][N]
   __host__ __device__ static size_t bytes(int L) { return (G(L) + sizeof(float) * L * N + 15) & ~size_t(15); }
 };
+
+// position of R(i, c), c >= i, in the packed rows of an N-column factor
+template <int N>
+__host__ __device__ __forceinline__ int rpk(int i, int c) {
+  return i * (2 * N - i - 1) / 2 + c;
+}
 
 // lanes of this thread's group of HW lanes
 template <int HW>
@@ -219,7 +227,7 @@ __device__ __forceinline__ void apply_q_regs(const float (&a)[MR][N], const floa
 
 // w <- R^{-T} w (forward substitution), w[l][t] holds entry p = lane + HW t
 template <int HW, int N, int L>
-__device__ __forceinline__ void solve_rt_lanes(const float* Rs, int RS, const float* idg,
+__device__ __forceinline__ void solve_rt_lanes(const float* Rs, const float* idg,
                                                float (&w)[L][(N + HW - 1) / HW], int lane, unsigned mask) {
   constexpr int NT = (N + HW - 1) / HW;
 #pragma unroll
@@ -232,7 +240,7 @@ __device__ __forceinline__ void solve_rt_lanes(const float* Rs, int RS, const fl
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const int p = lane + HW * t;
-        if (p > i && p < N) w[l][t] = fmaf(-Rs[i * RS + p], yi, w[l][t]);
+        if (p > i && p < N) w[l][t] = fmaf(-Rs[rpk<N>(i, p)], yi, w[l][t]);
       }
     }
   }
@@ -240,7 +248,7 @@ __device__ __forceinline__ void solve_rt_lanes(const float* Rs, int RS, const fl
 
 // w <- R^{-1} w (back substitution)
 template <int HW, int N, int L>
-__device__ __forceinline__ void solve_r_lanes(const float* Rs, int RS, const float* idg,
+__device__ __forceinline__ void solve_r_lanes(const float* Rs, const float* idg,
                                               float (&w)[L][(N + HW - 1) / HW], int lane, unsigned mask) {
   constexpr int NT = (N + HW - 1) / HW;
 #pragma unroll
@@ -253,7 +261,7 @@ __device__ __forceinline__ void solve_r_lanes(const float* Rs, int RS, const flo
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const int p = lane + HW * t;
-        if (p < i) w[l][t] = fmaf(-Rs[p * RS + i], yi, w[l][t]);
+        if (p < i) w[l][t] = fmaf(-Rs[rpk<N>(p, i)], yi, w[l][t]);
       }
     }
   }
@@ -273,8 +281,8 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
   constexpr int NC = (KIND == GMLS_BASIS_SCALAR) ? 1 : D;
   constexpr int ROWS = HW * MR;
   constexpr int NT = (N + HW - 1) / HW;
-  using Lay = FastLay<HW, MR, N>;
-  constexpr int LD = Lay::LD, RS = Lay::RS;
+  using Lay = FastLay<HW, MR, N, NC>;
+  constexpr int LD = Lay::LD;
   extern __shared__ __align__(16) unsigned char smem[];
   const int grp = threadIdx.x / HW, lane = threadIdx.x & (HW - 1);
   const int gpb = blockDim.x / HW;
@@ -284,12 +292,19 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
   ff* SWs = reinterpret_cast<ff*>(base + Lay::SW);
   ff* Ss = reinterpret_cast<ff*>(base + Lay::S);
   ff* Ys = reinterpret_cast<ff*>(base + Lay::Y(L));
-  ff* LAMs = reinterpret_cast<ff*>(base + Lay::LAM(L));
+  ff* IEPSs = reinterpret_cast<ff*>(base + Lay::IEPS);
   float* Rs = reinterpret_cast<float*>(base + Lay::R);
   float* IDs = reinterpret_cast<float*>(base + Lay::ID);
   float* TAUs = reinterpret_cast<float*>(base + Lay::TAU);
   float* Gs = reinterpret_cast<float*>(base + Lay::G(L));
-  ff* PARTs = reinterpret_cast<ff*>(base + Lay::PART);
+  // functional row l at basis column c (float-float): integer coefficient
+  // times eps^-order
+  auto lam = [&](int l, int c) {
+    ff f(gmls_gen::lam_coef_f(KIND, D, DEG, j.lam_fn[l], j.lam_row[l], c), 0.0f);
+    const ff ie = IEPSs[0];
+    for (int p = 0; p < j.lam_order[l]; ++p) f = f * ie;
+    return f;
+  };
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
   const float tolf = (float)j.tol;
@@ -355,12 +370,11 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
           for (int p = 1; p < half_p; ++p) sw = sw * u;
         }
         gmls_gen::BasisEval<KIND, D, DEG>::template run<ff>(xi, Bs + q * NC, LD, sw);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) SWs[q * NC + c] = sw;
+        SWs[q] = sw;
       } else {
+        SWs[q] = ff(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          SWs[q * NC + c] = ff(0.f, 0.f);
 #pragma unroll
           for (int i = 0; i < N; ++i) Bs[i * LD + q * NC + c] = ff(0.f, 0.f);
         }
@@ -368,17 +382,11 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
     }
     // rows past the last whole neighbour (ROWS not a multiple of NC)
     for (int r = (ROWS / NC) * NC + lane; r < ROWS; r += HW) {
-      SWs[r] = ff(0.f, 0.f);
+      if (r % NC == 0) SWs[r / NC] = ff(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < N; ++i) Bs[i * LD + r] = ff(0.f, 0.f);
     }
-    // functional rows (float-float), lanes over (row, column)
-    for (int e = lane; e < L * N; e += HW) {
-      const int l = e / N, i = e % N;
-      ff f(gmls_gen::lam_coef_f(KIND, D, DEG, j.lam_fn[l], j.lam_row[l], i), 0.0f);
-      for (int p = 0; p < j.lam_order[l]; ++p) f = f * inv_eps;
-      LAMs[l * N + i] = f;
-    }
+    if (lane == 0) IEPSs[0] = inv_eps;
     __syncwarp(mask);
 
     // ---- 2. FP32 Householder QR in registers
@@ -395,7 +403,8 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
       const int r = lane + HW * i;
       if (r < N) {
 #pragma unroll
-        for (int c = 0; c < N; ++c) Rs[r * RS + c] = (c >= r) ? a[i][c] : 0.0f;
+        for (int c = 0; c < N; ++c)
+          if (c >= r) Rs[rpk<N>(r, c)] = a[i][c];
         float d = 0.0f;
 #pragma unroll
         for (int c = 0; c < N; ++c)
@@ -448,7 +457,7 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
             const int e = u * HW + lane, l = e / N, c = e % N;
             // four independent compensated chains over interleaved rows (ILP)
             Dot2 acc[4];
-            acc[0].init(LAMs[l * N + c]);
+            acc[0].init(lam(l, c));
             const ff* bc = Bs + c * LD;
             const ff* sl = Ss + l * LD;
 #pragma unroll 2
@@ -461,24 +470,27 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
             Gs[l * N + c] = __fadd_rn(tot.h, tot.l);
           }
           if constexpr (rem > 0) {
+            // pair e is split over the lanes blk * rem + (e - full HW), blk <
+            // nblk; lane e - full HW gathers the partial sums by shuffles
             constexpr int nblk = HW / rem, chunk = (ROWS + nblk - 1) / nblk;
             const int e = full * HW + lane % rem, blk = lane / rem;
+            const int l = e / N, c = e % N;
             Dot2 acc;
             if (blk < nblk) {
-              const int l = e / N, c = e % N;
               const ff* bc = Bs + c * LD;
               const ff* sl = Ss + l * LD;
               const int r1 = min(ROWS, (blk + 1) * chunk);
               for (int r = blk * chunk; r < r1; ++r) acc.add_prod(-bc[r], sl[r]);
-              PARTs[lane] = acc.value();
             }
-            __syncwarp(mask);
-            if (lane < rem) {
-              const int l = e / N, c = e % N;
-              ff sum = LAMs[l * N + c];
-              for (int b = 0; b < nblk; ++b) sum = sum + PARTs[b * rem + lane];
-              Gs[l * N + c] = __fadd_rn(sum.h, sum.l);
+            const ff part = (blk < nblk) ? acc.value() : ff(0.f, 0.f);
+            ff sum = (lane < rem) ? lam(l, c) : ff(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < nblk; ++b) {
+              const int src = b * rem + lane % rem;
+              const ff v(__shfl_sync(mask, part.h, src, HW), __shfl_sync(mask, part.l, src, HW));
+              sum = sum + v;
             }
+            if (lane < rem) Gs[l * N + c] = __fadd_rn(sum.h, sum.l);
           }
         }
         __syncwarp(mask);
@@ -494,9 +506,9 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
 #pragma unroll
         for (int tt = 0; tt < NT; ++tt) {
           const int p = lane + HW * tt;
-          w[l][tt] = (p < N) ? (it > 0 ? Gs[l * N + p] : LAMs[l * N + p].h) : 0.0f;
+          w[l][tt] = (p < N) ? (it > 0 ? Gs[l * N + p] : lam(l, p).h) : 0.0f;
         }
-      solve_rt_lanes<HW, N, L>(Rs, RS, IDs, w, lane, mask);  // a = R^{-T} g
+      solve_rt_lanes<HW, N, L>(Rs, IDs, w, lane, mask);  // a = R^{-T} g
       float dyv[L][NT];
 #pragma unroll
       for (int l = 0; l < L; ++l)
@@ -507,7 +519,7 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
           dyv[l][tt] = (p < N) ? w[l][tt] - z[l][tt < MR ? tt : 0] : 0.0f;
           if (p < N && tt < MR) z[l][tt < MR ? tt : 0] = w[l][tt];
         }
-      solve_r_lanes<HW, N, L>(Rs, RS, IDs, dyv, lane, mask);   // dy
+      solve_r_lanes<HW, N, L>(Rs, IDs, dyv, lane, mask);   // dy
       apply_q_regs<HW, MR, N, L, true>(a, TAUs, z, lane, mask);  // ds = Q [a; d_2]
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
@@ -564,10 +576,10 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
           if (src >= 0) {
             if (div_scalar) {
               const int q = e / C, c = e % C;
-              const ff s = Ss[(src + c) * LD + q] * SWs[q];
+              const ff s = Ss[(src + c) * LD + q] * SWs[q];  // scalar basis: one row per neighbour
               val = to_double(s);
             } else {
-              const ff s = Ss[(src + rr) * LD + e] * SWs[e];
+              const ff s = Ss[(src + rr) * LD + e] * SWs[e / NC];
               val = to_double(ff(sgn * s.h, sgn * s.l));
             }
           }
@@ -595,7 +607,7 @@ struct FastEntry {
 #define GMLS_FAST(KIND, D, DEG, MR, L, HW)                                                                            \
   FastEntry {                                                                                                          \
     KIND, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L, HW>,                                \
-        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG)>::bytes                                                    \
+        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 0 ? 1 : D)>::bytes                               \
   }
 
 }  // namespace gmls
