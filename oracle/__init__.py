@@ -242,3 +242,92 @@ def apply_q(A, tau, z):
     M, n = A.shape
     lib().orc_apply_q(ctypes.c_int(M), ctypes.c_int(n), _p(A), _p(tau), _p(z))
     return z
+
+
+# ------------------------------------------------------------ Stokes system
+def stokes_system(dim, n, bflag, normals, vel, pres, nu):
+    """Collocation system of the Stokes problem (Sec. 3.2, Eq.
+    stokes-block-system), assembled from per-point stencils.
+
+    Unknowns: velocity v (point J, component c at J*dim + c), pressure phi
+    (n*dim + J) and the zero-mean multiplier lambda (n*dim + n).
+    Rows (Eqs. stokes-velocity-target .. stokes-pressure-neumann-target):
+      I interior, component c: nu * (curl curl stencil) v + (gradient stencil) phi
+      I boundary, component c: v_{I,c}                        (Dirichlet, delta rows)
+      I interior, pressure:    (Laplacian stencil) phi + lambda
+      I boundary, pressure:    -nu beta_I n_I . (curl curl stencil) v
+                               + (Neumann-constrained Laplacian stencil) phi + lambda
+      last row:                sum_J phi_J                    (zero mean)
+    The boundary pressure row follows from the Neumann condition
+    n . grad phi = n . f - nu n . curl curl v eliminated by the constrained
+    stencil (Laplacian ~ sum w_j phi_j + beta h): the velocity coefficient is
+    -nu beta n . (curl curl stencil); the right-hand side is
+    div f - beta n . f.  n . a is evaluated as ((n_0 a_0) + (n_1 a_1)) + (n_2 a_2)
+    and the coefficient as nu * (beta * (n . a)).
+
+    vel  = (off, idx, w_cc) with w_cc[I] of shape [dim, k_I, dim] (curl curl
+           rows, input components), targets = all points in order;
+    pres = (off, idx, w_grad, w_lap, beta_lap) with w_grad[I] [dim, k_I, 1],
+           w_lap[I] [1, k_I, 1] (constrained at boundary points) and
+           beta_lap[I] the Laplacian row's beta (zero at interior points).
+    Returns scipy.sparse.csr_matrix with ascending columns in every row."""
+    import scipy.sparse as sp
+
+    off_v, idx_v, w_cc = vel
+    off_p, idx_p, w_grad, w_lap, beta = pres
+    nd = n * dim
+    rows, cols, vals = [], [], []
+    for I in range(n):
+        jv = np.asarray(idx_v[off_v[I]:off_v[I + 1]], dtype=np.int64)
+        jp = np.asarray(idx_p[off_p[I]:off_p[I + 1]], dtype=np.int64)
+        a3 = np.asarray(w_cc[I])        # [dim, kv, dim]
+        a1 = np.asarray(w_grad[I])[..., 0]  # [dim, kp]
+        a2 = np.asarray(w_lap[I])[0, :, 0]  # [kp]
+        vcol = (jv[:, None] * dim + np.arange(dim)[None, :]).reshape(-1)
+        pcol = nd + jp
+        if bflag[I]:
+            for c in range(dim):
+                rows.append(np.array([I * dim + c]))
+                cols.append(np.array([I * dim + c]))
+                vals.append(np.array([1.0]))
+            nda = normals[0][I] * a3[0]
+            for c in range(1, dim):
+                nda = nda + normals[c][I] * a3[c]
+            vv = nu * (beta[I] * nda)
+            r = nd + I
+            rows.append(np.full(len(vcol) + len(pcol) + 1, r))
+            cols.append(np.concatenate([vcol, pcol, [nd + n]]))
+            vals.append(np.concatenate([-vv.reshape(-1), a2, [1.0]]))
+        else:
+            for c in range(dim):
+                r = I * dim + c
+                rows.append(np.full(len(vcol) + len(pcol), r))
+                cols.append(np.concatenate([vcol, pcol]))
+                vals.append(np.concatenate([nu * a3[c].reshape(-1), a1[c]]))
+            r = nd + I
+            rows.append(np.full(len(pcol) + 1, r))
+            cols.append(np.concatenate([pcol, [nd + n]]))
+            vals.append(np.concatenate([a2, [1.0]]))
+    rows.append(np.full(n, nd + n))
+    cols.append(nd + np.arange(n))
+    vals.append(np.ones(n))
+    N = nd + n + 1
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N)).tocsr()
+    A.sort_indices()
+    return A
+
+
+def stokes_rhs(dim, n, bflag, normals, f, w, div_f, beta_lap):
+    """Right-hand side of the system of ``stokes_system``: f (interior
+    momentum rows), w (Dirichlet rows), div f (interior pressure rows),
+    div f - beta n . f (boundary pressure rows), 0 (zero-mean row)."""
+    nd = n * dim
+    b = np.zeros(nd + n + 1)
+    bf = np.asarray(bflag).astype(bool)
+    for c in range(dim):
+        b[c:nd:dim] = np.where(bf, w[c], f[c])
+    nf = normals[0] * f[0]
+    for c in range(1, dim):
+        nf = nf + normals[c] * f[c]
+    b[nd:nd + n] = np.where(bf, div_f - beta_lap * nf, div_f)
+    return b

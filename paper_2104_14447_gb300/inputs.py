@@ -121,6 +121,35 @@ def porous_cube(n_axis: int = 128, n_spheres: int = 64, rmin: float = 0.05, rmax
             "spheres": spheres, "porosity": porosity, "lattice_points": n}
 
 
+def box_boundary(dim: int, n_axis: int):
+    """Boundary flags and outward unit normals of a jittered_grid cloud on the
+    unit box: the outermost lattice layer on each face (x fastest in the point
+    order); corner and edge points get the normalised sum of their faces'
+    normals.  Returns (bflag uint8 [N], normals [dim, N])."""
+    n = n_axis ** dim
+    idx = np.arange(n)
+    nrm = np.zeros((dim, n))
+    for c in range(dim):
+        ic = (idx // (n_axis ** c)) % n_axis
+        nrm[c, ic == 0] = -1.0
+        nrm[c, ic == n_axis - 1] = 1.0
+    length = np.sqrt(np.sum(nrm * nrm, axis=0))
+    bflag = (length > 0).astype(np.uint8)
+    nrm[:, length > 0] /= length[length > 0]
+    return bflag, np.ascontiguousarray(nrm)
+
+
+def stokes_manufactured_2d(x: np.ndarray, nu: float = 1.0):
+    """Data of the 2D Stokes problem (Sec. 3.1) whose solution is the
+    manufactured field u = (sin pi x cos pi y, -cos pi x sin pi y),
+    p = cos 2 pi x: f = nu curl curl u + grad p (curl curl u = 2 pi^2 u),
+    w = u on the boundary, div f = lap p."""
+    m = manufactured_2d(x)
+    curlcurl = -m["lap_u"]
+    f = nu * curlcurl + m["grad_p"]
+    return {"u": m["u"], "p": m["p"], "f": f, "w": m["u"], "div_f": m["lap_p"], "curlcurl_u": curlcurl}
+
+
 def unit_vectors(seed: int, stream: int, n: int, dim: int) -> np.ndarray:
     """n random unit vectors (dim, n) from normalised uniform cube samples."""
     out = np.zeros((dim, n), dtype=np.float64)

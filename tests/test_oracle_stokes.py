@@ -1,0 +1,133 @@
+"""Pins of the oracle's Stokes collocation system (Sec. 3.2, Eq.
+stokes-block-system) on the unit square with Dirichlet velocity and the
+Neumann pressure condition at the outermost lattice layer.
+
+* Polynomial exactness: for a divergence-free polynomial velocity of degree
+  <= m and a polynomial pressure of degree <= m, every stencil reproduces its
+  functional exactly, and the Neumann-constrained Laplacian reproduces the
+  Laplacian once beta times the exact normal derivative is added.  Hence
+  A x - b vanishes (up to rounding) on every row but the zero-mean row, for
+  any viscosity.  A sign slip in the coupling of the boundary pressure rows,
+  a missing nu or beta, or a mis-placed block fails this.
+* Consistency on the manufactured trigonometric field: the residual decays
+  like h^(m-1) on interior rows (second-derivative stencils) and h^(m-2) on
+  boundary pressure rows (beta ~ 1/eps multiplies an O(h^(m-1)) error).
+* Structure: Dirichlet rows are unit rows, every pressure row couples to the
+  multiplier, the last row sums the pressures, columns ascend.
+"""
+import numpy as np
+import pytest
+
+sympy = pytest.importorskip("sympy")
+
+import oracle
+from paper_2104_14447_gb300 import inputs
+
+M = 4
+KV, KP = 48, 36
+
+
+def _system(na, nu, seed=0):
+    x = inputs.jittered_grid(2, na, seed=seed)
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(2, na)
+    tg = np.arange(n, dtype=np.int32)
+    iv, ev = oracle.knn(x, tg, KV, 1.5, method="grid")
+    ip, ep = oracle.knn(x, tg, KP, 1.5, method="grid")
+    offv = np.arange(0, n * KV + 1, KV)
+    offp = np.arange(0, n * KP + 1, KP)
+    wcc, _, _ = oracle.stencils(x, tg, offv, iv.reshape(-1), ev, "divfree", M, "curlcurl")
+    wg, _, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "grad", bflag=bflag, normals=nrm.T)
+    wl, bl, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "laplacian", bflag=bflag,
+                                normals=nrm.T)
+    A = oracle.stokes_system(2, n, bflag, nrm, (offv, iv.reshape(-1), wcc),
+                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu)
+    return x, n, bflag, nrm, A, bl[:, 0]
+
+
+def _polynomial_fields(x, nu):
+    X, Y = sympy.symbols("x y")
+    psi = X ** 3 * Y ** 2 - 2 * X * Y ** 4 + X ** 2 * Y - 3 * X * Y ** 3 + Y ** 5 / 5  # degree 5: v of degree 4
+    v = [sympy.diff(psi, Y), -sympy.diff(psi, X)]
+    p = X ** 4 - 2 * X ** 2 * Y ** 2 + 3 * X * Y ** 3 - Y + 1
+    omega = sympy.diff(v[1], X) - sympy.diff(v[0], Y)
+    curlcurl = [sympy.diff(omega, Y), -sympy.diff(omega, X)]
+    f = [nu * curlcurl[c] + sympy.diff(p, (X, Y)[c]) for c in range(2)]
+    div_f = sympy.diff(f[0], X) + sympy.diff(f[1], Y)
+    ev = lambda e: np.asarray(sympy.lambdify((X, Y), e, "numpy")(x[0], x[1]), dtype=np.float64) * np.ones(x.shape[1])
+    assert sympy.simplify(sympy.diff(v[0], X) + sympy.diff(v[1], Y)) == 0
+    return (np.stack([ev(v[0]), ev(v[1])]), ev(p), np.stack([ev(f[0]), ev(f[1])]), ev(div_f))
+
+
+def _residual(A, n, bflag, nrm, beta, u, p, f, w, div_f):
+    xe = np.concatenate([u.T.reshape(-1), p, [0.0]])
+    b = oracle.stokes_rhs(2, n, bflag, nrm, f, w, div_f, beta)
+    return A @ xe - b, np.abs(A) @ np.abs(xe) + np.abs(b)
+
+
+@pytest.mark.parametrize("nu", [1.0, 0.37])
+def test_polynomial_fields_are_reproduced(nu):
+    x, n, bflag, nrm, A, beta = _system(18, nu)
+    u, p, f, div_f = _polynomial_fields(x, nu)
+    r, scale = _residual(A, n, bflag, nrm, beta, u, p, f, u, div_f)
+    rows = slice(0, 3 * n)  # all but the zero-mean row
+    assert np.max(np.abs(r[rows]) / scale[rows]) < 1e-10
+    assert np.any(bflag) and np.any(beta[bflag == 1] != 0.0)
+
+
+def test_planted_sign_slip_is_caught():
+    """The same check with the boundary pressure rows' velocity coupling
+    negated (the sign printed beside Eq. grad-pressure-stencil-1) fails."""
+    import scipy.sparse as sp
+
+    x, n, bflag, nrm, A, beta = _system(18, 1.0)
+    u, p, f, div_f = _polynomial_fields(x, 1.0)
+    C = A.tocoo()
+    flip = (C.row >= 2 * n) & (C.row < 3 * n) & (C.col < 2 * n)
+    data = C.data.copy()
+    data[flip] *= -1.0
+    Af = sp.csr_matrix((data, (C.row, C.col)), shape=A.shape)
+    r, scale = _residual(Af, n, bflag, nrm, beta, u, p, f, u, div_f)
+    assert np.max(np.abs(r[2 * n:3 * n]) / scale[2 * n:3 * n]) > 1e-3
+
+
+def test_manufactured_field_converges():
+    hs, res = [], {"mom": [], "p_int": [], "p_bdry": []}
+    for na in (20, 28, 40):
+        x, n, bflag, nrm, A, beta = _system(na, 1.0)
+        d = inputs.stokes_manufactured_2d(x, 1.0)
+        r, _ = _residual(A, n, bflag, nrm, beta, d["u"], d["p"], d["f"], d["w"], d["div_f"])
+        bf = bflag.astype(bool)
+        mom = np.abs(r[:2 * n]).reshape(n, 2)
+        assert np.all(mom[bf] == 0.0)  # Dirichlet rows: exact
+        pr = np.abs(r[2 * n:3 * n])
+        hs.append(1.0 / na)
+        res["mom"].append(mom[~bf].max())
+        res["p_int"].append(pr[~bf].max())
+        res["p_bdry"].append(pr[bf].max())
+    slope = {k: np.polyfit(np.log(hs), np.log(v), 1)[0] for k, v in res.items()}
+    assert slope["mom"] > M - 1 - 0.7, slope
+    assert slope["p_int"] > M - 1 - 0.7, slope
+    assert slope["p_bdry"] > M - 2 - 0.7, slope
+
+
+def test_structure():
+    x, n, bflag, nrm, A, beta = _system(12, 1.0)
+    nd = 2 * n
+    rp, col = A.indptr, A.indices
+    assert A.shape == (nd + n + 1, nd + n + 1)
+    for I in range(n):
+        for c in range(2):
+            r = 2 * I + c
+            cols = col[rp[r]:rp[r + 1]]
+            if bflag[I]:
+                assert list(cols) == [r] and A[r, r] == 1.0
+            else:
+                assert len(cols) == KV * 2 + KP and np.all(cols[KV * 2:] >= nd) and np.all(cols[:KV * 2] < nd)
+        r = nd + I
+        cols = col[rp[r]:rp[r + 1]]
+        assert cols[-1] == nd + n and A[r, nd + n] == 1.0
+        assert len(cols) == (KV * 2 + KP + 1 if bflag[I] else KP + 1)
+        assert np.all(np.diff(cols) > 0)
+    last = col[rp[nd + n]:rp[nd + n + 1]]
+    assert np.array_equal(last, nd + np.arange(n))
