@@ -345,6 +345,90 @@ SERVE_K = {(2, 0, 2): 12, (2, 0, 3): 20, (2, 0, 4): 36, (2, 1, 2): 22, (2, 1, 3)
            (3, 0, 2): 20, (3, 0, 3): 40, (3, 0, 4): 84, (3, 1, 2): 42, (3, 1, 3): 80, (3, 1, 4): 136}
 
 
+def stokes_system(ctx, steps=5):
+    """The Stokes collocation system (Sec. 3.2) on the benchmark grid with the
+    outermost lattice layer as the Dirichlet / Neumann boundary: stencils
+    (curl curl on the divergence-free basis; gradient and Neumann-constrained
+    Laplacian on the scalar basis), then per timed step assembly of the block
+    CSR, its right-hand side and one A x.  Reports times, bytes moved against
+    the measured HBM peak, and the manufactured-field residual."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    x = workload_points()
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(2, N_AXIS)
+    d = inputs.stokes_manufactured_2d(x, 1.0)
+    stream = ctx.stream
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+    npr = ctx.neighbors_prefix(nv, K_SCALAR, EPS_FACTOR)
+    sv = ctx.stencils(nv, gmls.DIVFREE, DEGREE, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+    sp = ctx.stencils(npr, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE,
+                      neumann=True)
+    n_rows, nnz = ctx.stokes_size(sv, sp, 1.0)
+    rp = torch.empty(n_rows + 1, dtype=torch.int64, device=ctx.device)
+    col = torch.empty(nnz, dtype=torch.int32, device=ctx.device)
+    val = torch.empty(nnz, dtype=torch.float64, device=ctx.device)
+    f, w, div_f = (torch.from_numpy(np.ascontiguousarray(a)).to(ctx.device) for a in (d["f"], d["w"], d["div_f"]))
+    xe = torch.from_numpy(np.concatenate([d["u"].T.reshape(-1), d["p"], [0.0]])).to(ctx.device)
+    b = torch.empty(n_rows, dtype=torch.float64, device=ctx.device)
+    y = torch.empty(n_rows, dtype=torch.float64, device=ctx.device)
+    P = gmls.StokesParams(sv, sp, 1.0)
+    lib, h = ctx.lib, ctx.h
+    import ctypes
+
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def assemble():
+        ctx._check(lib.gmls_stokes_assemble(h, ctypes.byref(P), ptr(rp), ptr(col), ptr(val)))
+        ctx._check(lib.gmls_stokes_rhs(h, ctypes.byref(P), ptr(f), ptr(w), ptr(div_f), ptr(b)))
+
+    def spmv():
+        ctx._check(lib.gmls_csr_spmv(h, n_rows, ptr(rp), ptr(col), ptr(val), ptr(xe), ptr(y)))
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=ctx.device)
+    for _ in range(2):
+        assemble()
+        spmv()
+    ta, tm = [], []
+    for s in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            assemble()
+            e[1].record(stream)
+            spmv()
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        ta.append(e[0].elapsed_time(e[1]))
+        tm.append(e[1].elapsed_time(e[2]))
+    r = (y - b).cpu().numpy()
+    bf = bflag.astype(bool)
+    mom = np.abs(r[:2 * n]).reshape(n, 2)
+    pr = np.abs(r[2 * n:3 * n])
+    nb = int(np.sum(bf))
+    # bytes: assembly reads the weights it scatters (nnz doubles, mostly) and
+    # both neighbour lists, writes col + val + row_ptr; A x reads val, col,
+    # row_ptr, writes y (x, 6.3 MB, stays in L2)
+    asm_bytes = nnz * (8 + 4 + 8) + (n_rows + 1) * 8 + n * (K_DIVFREE + K_SCALAR) * 4 + n_rows * 8
+    spmv_bytes = nnz * (8 + 4) + (n_rows + 1) * 8 + n_rows * 8 + n_rows * 8
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ta_m, tm_m = float(np.median(ta)), float(np.median(tm))
+    for hd in (sp, sv, npr, nv, cid):
+        ctx.release(hd)
+    return {"workload": f"stokes2d-{N_AXIS}x{N_AXIS} collocation system, {nb} boundary points, nu = 1",
+            "n_rows": n_rows, "nnz": nnz, "assemble_ms": ta_m, "spmv_ms": tm_m,
+            "assemble_gbs": asm_bytes / ta_m / 1e6, "spmv_gbs": spmv_bytes / tm_m / 1e6,
+            "spmv_frac_hbm": spmv_bytes / tm_m / 1e6 / hbm, "peak_source": src,
+            "residual_max": {"momentum_interior": float(mom[~bf].max()), "pressure_interior": float(pr[~bf].max()),
+                             "pressure_boundary": float(pr[bf].max()), "dirichlet": float(mom[bf].max())},
+            "l2": "flushed before each timed step (256 MB write)"}
+
+
 def serving(n_requests, seed=0):
     """Poisson arrivals (200 req/s) of stencil requests -- 2D/3D clouds of
     log-uniform 1e3..5e5 points, degree 2..4, scalar (gradient + Laplacian) or
@@ -534,6 +618,7 @@ def main():
     ap.add_argument("--arena-gb", type=int, default=24)
     ap.add_argument("--ref-stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stokes", action="store_true", help="skip the Stokes-system section")
     ap.add_argument("--n-axis", type=int, default=512, help="profiling only; the benchmark is 512")
     ap.add_argument("--serve-requests", type=int, default=60, help="serving sample size (0: skip)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
@@ -555,6 +640,8 @@ def main():
     out, ctx = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(ctx)
+    if rank == 0 and world == 1 and not args.no_stokes:
+        out["stokes_system"] = stokes_system(ctx)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving(args.serve_requests)
     if rank == 0:

@@ -18,6 +18,9 @@
  *                      stencil weights alpha_Ij of Sec. 3.2
  *   gmls_assemble_csr  scatter of one operator's weights into CSR through the
  *                      local-to-global map J = LTG(I, j) of Sec. 3.2
+ *   gmls_stokes_*      the block collocation system of Sec. 3.2 from velocity
+ *                      and pressure stencils, its right-hand side, and a CSR
+ *                      matrix-vector product to apply it
  *
  * Conventions
  *   - Every function returns a gmls_status; 0 is success, negative values are
@@ -205,6 +208,61 @@ gmls_status gmls_csr_size(gmls_ctx* ctx, int64_t stencil_id, int32_t functional,
                           int64_t* nnz);
 gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t* row_ptr, int32_t* col,
                               double* val);
+
+/*
+ * Stokes collocation system (Sec. 3.2, Eq. stokes-block-system) of the
+ * problem of Sec. 3.1 (nu curl curl v + grad phi = f in the interior,
+ * v = w on the boundary, Laplacian phi = div f with the Neumann condition
+ * n . grad phi = n . f - nu n . curl curl v on the boundary), assembled from
+ * two stencil handles over ONE cloud that carries boundary flags and outward
+ * normals, both computed for every point of the cloud in order (neighbour
+ * handles made without a target list):
+ *   velocity: divergence-free basis, functional GMLS_F_CURLCURL;
+ *   pressure: scalar basis, GMLS_F_GRAD and GMLS_F_LAPLACIAN, neumann = 1
+ *             (boundary points get the constrained Laplacian and its beta).
+ * Unknowns: velocity of point J, component c at column J d + c; pressure of
+ * J at n d + J; the zero-mean multiplier at n d + n (n = points, d = dim).
+ * Rows, in this order:
+ *   I d + c, interior I:  nu * curl curl weights (velocity columns), then the
+ *                         gradient row c (pressure columns)
+ *   I d + c, boundary I:  1 at column I d + c (Dirichlet)
+ *   n d + I, interior I:  Laplacian weights, then 1 at the multiplier
+ *   n d + I, boundary I:  -nu * beta_I * (n_I . curl curl weights) on the
+ *                         velocity columns (n . a evaluated
+ *                         ((n_0 a_0) + (n_1 a_1)) + (n_2 a_2), then
+ *                         nu * (beta * (n . a))), the constrained Laplacian
+ *                         weights, 1 at the multiplier
+ *   n d + n:              1 at every pressure column (zero mean)
+ * Columns ascend within each row; neighbour lists enter in particle-id order.
+ * The right-hand side (gmls_stokes_rhs) is f (interior momentum rows), w
+ * (Dirichlet rows), div f (interior pressure rows), div f - beta n . f
+ * (boundary pressure rows) and 0; f and w are SoA [d][n], div_f [n], b
+ * [n d + n + 1], all device buffers.
+ * gmls_stokes_size waits for the stream (it counts the nonzeros); the caller
+ * then passes device buffers row_ptr (int64 [n_rows + 1]), col (int32 [nnz])
+ * and val (double [nnz]) to gmls_stokes_assemble, which is asynchronous.
+ * GMLS_EINVAL for handles of the wrong kind, different clouds, target lists,
+ * a cloud without flags or normals, or more than 2^31 unknowns.
+ */
+typedef struct {
+  int64_t velocity; /* stencil handle (divergence-free basis, curl curl) */
+  int64_t pressure; /* stencil handle (scalar basis, gradient + Laplacian, neumann = 1) */
+  double nu;        /* kinematic viscosity, >= 0 */
+} gmls_stokes_params;
+
+gmls_status gmls_stokes_size(gmls_ctx* ctx, const gmls_stokes_params* params, int64_t* n_rows, int64_t* nnz);
+gmls_status gmls_stokes_assemble(gmls_ctx* ctx, const gmls_stokes_params* params, int64_t* row_ptr, int32_t* col,
+                                 double* val);
+gmls_status gmls_stokes_rhs(gmls_ctx* ctx, const gmls_stokes_params* params, const double* f, const double* w,
+                            const double* div_f, double* b);
+
+/*
+ * y = A x for a CSR matrix with n_rows rows (row_ptr int64 [n_rows + 1], col
+ * int32, val double; x and y double), FP64, all device buffers; asynchronous
+ * on the context stream.  The sum order within a row is not sequential.
+ */
+gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
+                          const double* val, const double* x, double* y);
 
 /*
  * Copy one array of a handle to dst (host or device), `bytes` = capacity of

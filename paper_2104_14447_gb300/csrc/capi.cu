@@ -112,6 +112,7 @@ struct NbrObj {
   uint8_t* status = nullptr;
   int mode = 0, k = 0, cap = 0;
   bool variable = false;  // per-target list lengths (offsets from a scan)
+  bool all_targets = false;  // targets are every point of the cloud, in order
   int64_t idx_cap = 0;  // allocated index entries
   int refs = 0;
 };
@@ -121,6 +122,8 @@ struct StencilObj {
   int basis = 0, dim = 0, L = 0;
   int nout = 0;
   int fn[5], rows[5], ncomp[5];
+  int src[5] = {0, 0, 0, 0, 0};  // first solve row of each functional (its beta column)
+  int neumann = 0;
   double* w[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double* beta = nullptr;
   uint8_t* status = nullptr;
@@ -767,6 +770,7 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   nb.k = p->k;
   nb.cap = p->mode == GMLS_NBR_RADIUS ? p->cap : p->k;
   nb.variable = variable;
+  nb.all_targets = p->targets == nullptr;
   nb.idx_cap = nt * (int64_t)nb.cap;
   nb.tgt = arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1));
   nb.off = arena_alloc<int64_t>(ctx, nt + 1);
@@ -850,6 +854,7 @@ gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, dou
   nb.cloud = src.cloud;
   nb.dim = src.dim;
   nb.n_tgt = src.n_tgt;
+  nb.all_targets = src.all_targets;
   nb.mode = GMLS_NBR_KNN;
   nb.k = k;
   nb.cap = k;
@@ -1043,6 +1048,8 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
       case GMLS_F_CURLCURL: j.out_src[f] = vlap0, j.out_sign[f] = -1; break;
     }
   }
+  for (int f = 0; f < s.nout; ++f) s.src[f] = j.out_src[f];
+  s.neumann = p->neumann;
   j.beta = s.beta;
   j.status = s.status;
   j.iters = s.iters;
@@ -1148,6 +1155,151 @@ gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functio
   CK(cudaSetDevice(ctx->device), "gmls_assemble_csr");
   CsrJob j{nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val};
   CK(launch_csr(ctx->launch(), j), "gmls_assemble_csr");
+  return GMLS_OK;
+}
+
+// ------------------------------------------------------------ Stokes system
+static int pow2_at_least(int v) {
+  int p = 32;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Validate the two stencil handles of a Stokes system and fill the job's
+// inputs; *n_rows = n d + n + 1.
+static gmls_status stokes_job(gmls_ctx* ctx, const gmls_stokes_params* p, StokesJob* j, int64_t* n_rows,
+                              const char* who) {
+  if (!ctx || !p) return GMLS_EINVAL;
+  auto iv = ctx->objs.find(p->velocity), ip = ctx->objs.find(p->pressure);
+  if (iv == ctx->objs.end() || iv->second.kind != K_STENCIL || ip == ctx->objs.end() ||
+      ip->second.kind != K_STENCIL)
+    return fail(ctx, GMLS_ENOTFOUND, std::string(who) + ": no such stencil handle");
+  const StencilObj& sv = iv->second.s;
+  const StencilObj& sp = ip->second.s;
+  const int fcc = find_out(sv, GMLS_F_CURLCURL), fg = find_out(sp, GMLS_F_GRAD), fl = find_out(sp, GMLS_F_LAPLACIAN);
+  if (sv.basis != GMLS_BASIS_DIVFREE || fcc < 0)
+    return fail(ctx, GMLS_EINVAL, std::string(who) + ": velocity handle needs the divergence-free basis with curl curl");
+  if (sp.basis != GMLS_BASIS_SCALAR || fg < 0 || fl < 0 || !sp.neumann)
+    return fail(ctx, GMLS_EINVAL,
+                std::string(who) + ": pressure handle needs the scalar basis with gradient and Laplacian, neumann = 1");
+  const NbrObj& nv = ctx->objs.at(sv.nbrs).nb;
+  const NbrObj& np = ctx->objs.at(sp.nbrs).nb;
+  if (nv.cloud != np.cloud || !nv.all_targets || !np.all_targets)
+    return fail(ctx, GMLS_EINVAL, std::string(who) + ": both stencils must cover every point of one cloud, in order");
+  const CloudObj& c = ctx->objs.at(nv.cloud).c;
+  if (!c.bflag || !c.normals)
+    return fail(ctx, GMLS_EINVAL, std::string(who) + ": the cloud needs boundary flags and normals");
+  if ((int64_t)c.n * (c.dim + 1) + 1 >= INT32_MAX)
+    return fail(ctx, GMLS_EINVAL, std::string(who) + ": too many unknowns for 32-bit column indices");
+  if (!(p->nu >= 0.0)) return fail(ctx, GMLS_EINVAL, std::string(who) + ": nu must be >= 0");
+  std::memset(j, 0, sizeof(*j));
+  j->dim = c.dim;
+  j->n = c.n;
+  j->nu = p->nu;
+  j->off_v = nv.off;
+  j->idx_v = nv.idx;
+  j->w_cc = sv.w[fcc];
+  j->off_p = np.off;
+  j->idx_p = np.idx;
+  j->w_grad = sp.w[fg];
+  j->w_lap = sp.w[fl];
+  j->beta = sp.beta;
+  j->beta_stride = std::max(sp.L, 1);
+  j->beta_col = sp.src[fl];
+  j->bflag = c.bflag;
+  j->normals = c.normals;
+  j->kcap_v = pow2_at_least(nv.cap);
+  j->kcap_p = pow2_at_least(np.cap);
+  *n_rows = c.n * c.dim + c.n + 1;
+  return GMLS_OK;
+}
+
+// row lengths and their exclusive scan into row_ptr (n_rows + 1 entries)
+static gmls_status stokes_rows(gmls_ctx* ctx, StokesJob& j, int64_t n_rows, int64_t* row_ptr, const char* who) {
+  j.row_len = arena_alloc<int32_t>(ctx, n_rows);
+  const int64_t se = scan_scratch_elems(n_rows);
+  int64_t* scratch = arena_alloc<int64_t>(ctx, se);
+  if (!j.row_len || !scratch) {
+    ctx->arena.release(j.row_len);
+    ctx->arena.release(scratch);
+    return fail(ctx, GMLS_ENOMEM, std::string(who) + ": arena exhausted");
+  }
+  j.row_ptr = row_ptr;
+  Launch L = ctx->launch();
+  cudaError_t e = launch_stokes_rowlen(L, j);
+  if (e == cudaSuccess) e = launch_scan_i64_from_i32(L, j.row_len, row_ptr, n_rows, scratch, se);
+  ctx->arena.release(j.row_len);  // stream ordered: later work on this stream runs after these kernels
+  ctx->arena.release(scratch);
+  j.row_len = nullptr;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, who);
+  return GMLS_OK;
+}
+
+gmls_status gmls_stokes_size(gmls_ctx* ctx, const gmls_stokes_params* p, int64_t* n_rows, int64_t* nnz) {
+  StokesJob j;
+  int64_t nr = 0;
+  gmls_status r = stokes_job(ctx, p, &j, &nr, "gmls_stokes_size");
+  if (r) return r;
+  if (!n_rows || !nnz) return fail(ctx, GMLS_EINVAL, "gmls_stokes_size: NULL output");
+  if (capturing(ctx)) return fail(ctx, GMLS_EBUSY, "gmls_stokes_size reads the device and cannot run during capture");
+  CK(cudaSetDevice(ctx->device), "gmls_stokes_size");
+  int64_t* rp = arena_alloc<int64_t>(ctx, nr + 1);
+  if (!rp) return fail(ctx, GMLS_ENOMEM, "gmls_stokes_size: arena exhausted");
+  r = stokes_rows(ctx, j, nr, rp, "gmls_stokes_size");
+  if (r) {
+    ctx->arena.release(rp);
+    return r;
+  }
+  int64_t total = 0;
+  cudaError_t e = cudaMemcpyAsync(&total, rp + nr, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  ctx->arena.release(rp);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_stokes_size");
+  *n_rows = nr;
+  *nnz = total;
+  return GMLS_OK;
+}
+
+gmls_status gmls_stokes_assemble(gmls_ctx* ctx, const gmls_stokes_params* p, int64_t* row_ptr, int32_t* col,
+                                 double* val) {
+  StokesJob j;
+  int64_t nr = 0;
+  gmls_status r = stokes_job(ctx, p, &j, &nr, "gmls_stokes_assemble");
+  if (r) return r;
+  if (!row_ptr || !col || !val) return fail(ctx, GMLS_EINVAL, "gmls_stokes_assemble: NULL output");
+  if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val))
+    return fail(ctx, GMLS_EINVAL, "gmls_stokes_assemble: outputs must be device buffers");
+  CK(cudaSetDevice(ctx->device), "gmls_stokes_assemble");
+  r = stokes_rows(ctx, j, nr, row_ptr, "gmls_stokes_assemble");
+  if (r) return r;
+  j.col = col;
+  j.val = val;
+  CK(launch_stokes_fill(ctx->launch(), j), "gmls_stokes_assemble fill");
+  return GMLS_OK;
+}
+
+gmls_status gmls_stokes_rhs(gmls_ctx* ctx, const gmls_stokes_params* p, const double* f, const double* w,
+                            const double* div_f, double* b) {
+  StokesJob j;
+  int64_t nr = 0;
+  gmls_status r = stokes_job(ctx, p, &j, &nr, "gmls_stokes_rhs");
+  if (r) return r;
+  if (!f || !w || !div_f || !b) return fail(ctx, GMLS_EINVAL, "gmls_stokes_rhs: NULL pointer");
+  if (is_host_ptr(f) || is_host_ptr(w) || is_host_ptr(div_f) || is_host_ptr(b))
+    return fail(ctx, GMLS_EINVAL, "gmls_stokes_rhs: arrays must be device buffers");
+  CK(cudaSetDevice(ctx->device), "gmls_stokes_rhs");
+  CK(launch_stokes_rhs(ctx->launch(), j, f, w, div_f, b), "gmls_stokes_rhs");
+  return GMLS_OK;
+}
+
+gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
+                          const double* val, const double* x, double* y) {
+  if (!ctx) return GMLS_EINVAL;
+  if (n_rows < 0 || !row_ptr || !col || !val || !x || !y) return fail(ctx, GMLS_EINVAL, "gmls_csr_spmv: bad argument");
+  if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val) || is_host_ptr(x) || is_host_ptr(y))
+    return fail(ctx, GMLS_EINVAL, "gmls_csr_spmv: arrays must be device buffers");
+  CK(cudaSetDevice(ctx->device), "gmls_csr_spmv");
+  CK(launch_csr_spmv(ctx->launch(), n_rows, row_ptr, col, val, x, y), "gmls_csr_spmv");
   return GMLS_OK;
 }
 

@@ -236,4 +236,36 @@ struct CsrJob {
 };
 cudaError_t launch_csr(const Launch& L, const CsrJob& j);
 
+// ------------------------------------------------------------ Stokes system
+// Collocation system of Sec. 3.2 from per-point stencils (targets = all
+// points in order).  Weight layouts as in the stencil handles: functional
+// rows R, components C, element offset off[t] R C.
+struct StokesJob {
+  int dim;
+  int64_t n;                 // points
+  double nu;                 // viscosity
+  const int64_t* off_v;      // velocity lists
+  const int32_t* idx_v;
+  const double* w_cc;        // curl curl: [off_v[I] d d + c (k d) + j d + c']
+  const int64_t* off_p;      // pressure lists
+  const int32_t* idx_p;
+  const double* w_grad;      // gradient: [off_p[I] d + c k + j]
+  const double* w_lap;       // Laplacian (Neumann-constrained at boundary points): [off_p[I] + j]
+  const double* beta;        // [I * beta_stride + beta_col]: beta of the Laplacian row
+  int beta_stride, beta_col;
+  const uint8_t* bflag;      // [n]
+  const double* normals;     // [c n + I]
+  int kcap_v, kcap_p;        // powers of two >= the longest list of each kind
+  int32_t* row_len;          // scratch [n d + n + 1]
+  int64_t* row_ptr;          // [n d + n + 2]
+  int32_t* col;
+  double* val;
+};
+cudaError_t launch_stokes_rowlen(const Launch& L, const StokesJob& j);
+cudaError_t launch_stokes_fill(const Launch& L, const StokesJob& j);
+cudaError_t launch_stokes_rhs(const Launch& L, const StokesJob& j, const double* f, const double* w,
+                              const double* div_f, double* b);
+cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
+                            const double* val, const double* x, double* y);
+
 }  // namespace gmls

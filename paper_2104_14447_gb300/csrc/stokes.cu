@@ -1,0 +1,242 @@
+// stokes.cu -- the Stokes collocation system of Sec. 3.2 (Eq.
+// stokes-block-system) assembled on the GPU from per-point stencils, its
+// right-hand side, and a CSR matrix-vector product.
+//
+// Unknowns: velocity (point J, component c at J d + c), pressure (n d + J),
+// the zero-mean multiplier (n d + n).  Rows (Eqs. stokes-velocity-target ..
+// stokes-pressure-neumann-target):
+//   interior point I, component c:  nu (curl curl stencil) v + (gradient stencil) phi
+//   boundary point I, component c:  v_{I,c}                            (delta rows)
+//   interior point I, pressure:     (Laplacian stencil) phi + lambda
+//   boundary point I, pressure:     -nu beta_I n_I . (curl curl stencil) v
+//                                   + (Neumann-constrained Laplacian stencil) phi + lambda
+//   last row:                       sum_J phi_J                        (zero mean)
+// The boundary pressure row eliminates the Neumann datum n . grad phi =
+// n . f - nu n . curl curl v (Eq. stokes-pressure-neumann) through the
+// constrained stencil (Laplacian ~ sum w_j phi_j + beta h, Sec. 2.3), which
+// puts -nu beta n . (curl curl stencil) on the velocity and div f - beta n . f
+// on the right.  Columns ascend within every row (velocity block first, then
+// pressure, then the multiplier), each neighbour list in particle-id order.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "gmls_internal.cuh"
+
+namespace gmls {
+
+namespace {
+
+constexpr int kStokesWarps = 4;
+
+inline unsigned grid_for(int64_t n, int per_block) {
+  int64_t b = (n + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)b;
+}
+
+__global__ void stokes_rowlen_kernel(StokesJob j) {
+  const int d = j.dim;
+  const int64_t nd = j.n * d;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < j.n; I += (int64_t)gridDim.x * blockDim.x) {
+    const int kv = (int)(j.off_v[I + 1] - j.off_v[I]);
+    const int kp = (int)(j.off_p[I + 1] - j.off_p[I]);
+    const bool bnd = j.bflag[I] != 0;
+    for (int c = 0; c < d; ++c) j.row_len[I * d + c] = bnd ? 1 : kv * d + kp;
+    j.row_len[nd + I] = bnd ? kv * d + kp + 1 : kp + 1;
+    if (I == 0) j.row_len[nd + j.n] = (int32_t)j.n;
+  }
+}
+
+// Sort the k ids of one list (padded to the power of two kc with INT_MAX)
+// together with their positions: bitonic network over shared memory, one warp.
+__device__ void warp_sort_ids(int32_t* ids, int16_t* pos, int k, int kc, int lane) {
+  for (int size = 2; size <= kc; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = lane; i < (kc >> 1); i += 32) {
+        // stride is a power of two: a = 2 stride (i / stride) + i % stride
+        const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
+        const bool asc = (a & size) == 0;
+        const int32_t ia = ids[a], ib = ids[b];
+        if ((ib < ia) == asc && ia != ib) {
+          ids[a] = ib;
+          ids[b] = ia;
+          const int16_t pa = pos[a];
+          pos[a] = pos[b];
+          pos[b] = pa;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  (void)k;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kStokesWarps * 32) stokes_fill_kernel(StokesJob j) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t per_warp = (size_t)(j.kcap_v + j.kcap_p) * (sizeof(int32_t) + sizeof(int16_t));
+  unsigned char* base = smem + warp * ((per_warp + 15) & ~size_t(15));
+  int32_t* idv = reinterpret_cast<int32_t*>(base);
+  int32_t* idp = idv + j.kcap_v;
+  int16_t* pv = reinterpret_cast<int16_t*>(idp + j.kcap_p);
+  int16_t* pp = pv + j.kcap_v;
+  const int64_t n = j.n, nd = n * D;
+  const double nu = j.nu;
+  for (int64_t I = blockIdx.x * (int64_t)kStokesWarps + warp; I < n; I += (int64_t)gridDim.x * kStokesWarps) {
+    const int64_t ov = j.off_v[I], op = j.off_p[I];
+    const int kv = (int)(j.off_v[I + 1] - ov), kp = (int)(j.off_p[I + 1] - op);
+    for (int i = lane; i < j.kcap_v; i += 32) {
+      idv[i] = (i < kv) ? j.idx_v[ov + i] : INT_MAX;
+      pv[i] = (int16_t)i;
+    }
+    for (int i = lane; i < j.kcap_p; i += 32) {
+      idp[i] = (i < kp) ? j.idx_p[op + i] : INT_MAX;
+      pp[i] = (int16_t)i;
+    }
+    __syncwarp();
+    warp_sort_ids(idv, pv, kv, j.kcap_v, lane);
+    warp_sort_ids(idp, pp, kp, j.kcap_p, lane);
+    const int kvd = kv * D;
+    const double* acc = j.w_cc + ov * D * D;  // this point's curl curl weights
+    if (!j.bflag[I]) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const int64_t r = I * D + c, s = j.row_ptr[r];
+        for (int e = lane; e < kvd; e += 32) {
+          const int q = e / D, cc = e - q * D;
+          j.col[s + e] = idv[q] * D + cc;
+          j.val[s + e] = __dmul_rn(nu, acc[(int64_t)c * kvd + pv[q] * D + cc]);
+        }
+        for (int e = lane; e < kp; e += 32) {
+          j.col[s + kvd + e] = (int32_t)(nd + idp[e]);
+          j.val[s + kvd + e] = j.w_grad[op * D + (int64_t)c * kp + pp[e]];
+        }
+      }
+      const int64_t s = j.row_ptr[nd + I];
+      for (int e = lane; e < kp; e += 32) {
+        j.col[s + e] = (int32_t)(nd + idp[e]);
+        j.val[s + e] = j.w_lap[op + pp[e]];
+      }
+      if (lane == 0) {
+        j.col[s + kp] = (int32_t)(nd + n);
+        j.val[s + kp] = 1.0;
+      }
+    } else {
+      if (lane < D) {
+        const int64_t r = I * D + lane, s = j.row_ptr[r];
+        j.col[s] = (int32_t)r;
+        j.val[s] = 1.0;
+      }
+      const double beta = j.beta[I * j.beta_stride + j.beta_col];
+      double nrm[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) nrm[c] = j.normals[c * n + I];
+      const int64_t s = j.row_ptr[nd + I];
+      for (int e = lane; e < kvd; e += 32) {
+        const int q = e / D, cc = e - q * D;
+        const int64_t w0 = (int64_t)pv[q] * D + cc;
+        // n . a, evaluated ((n_0 a_0) + (n_1 a_1)) + (n_2 a_2)
+        double nda = __dmul_rn(nrm[0], acc[w0]);
+#pragma unroll
+        for (int c = 1; c < D; ++c) nda = __dadd_rn(nda, __dmul_rn(nrm[c], acc[(int64_t)c * kvd + w0]));
+        j.col[s + e] = idv[q] * D + cc;
+        j.val[s + e] = -__dmul_rn(nu, __dmul_rn(beta, nda));
+      }
+      for (int e = lane; e < kp; e += 32) {
+        j.col[s + kvd + e] = (int32_t)(nd + idp[e]);
+        j.val[s + kvd + e] = j.w_lap[op + pp[e]];
+      }
+      if (lane == 0) {
+        j.col[s + kvd + kp] = (int32_t)(nd + n);
+        j.val[s + kvd + kp] = 1.0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void stokes_last_row_kernel(int64_t nd, int64_t n, const int64_t* __restrict__ row_ptr,
+                                       int32_t* __restrict__ col, double* __restrict__ val) {
+  const int64_t s = row_ptr[nd + n];
+  for (int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; J < n; J += (int64_t)gridDim.x * blockDim.x) {
+    col[s + J] = (int32_t)(nd + J);
+    val[s + J] = 1.0;
+  }
+}
+
+__global__ void stokes_rhs_kernel(StokesJob j, const double* __restrict__ f, const double* __restrict__ w,
+                                  const double* __restrict__ div_f, double* __restrict__ b) {
+  const int d = j.dim;
+  const int64_t n = j.n, nd = n * d;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n; I += (int64_t)gridDim.x * blockDim.x) {
+    const bool bnd = j.bflag[I] != 0;
+    for (int c = 0; c < d; ++c) b[I * d + c] = bnd ? w[c * n + I] : f[c * n + I];
+    if (bnd) {
+      double nf = __dmul_rn(j.normals[I], f[I]);
+      for (int c = 1; c < d; ++c) nf = __dadd_rn(nf, __dmul_rn(j.normals[c * n + I], f[c * n + I]));
+      b[nd + I] = __dsub_rn(div_f[I], __dmul_rn(j.beta[I * j.beta_stride + j.beta_col], nf));
+    } else {
+      b[nd + I] = div_f[I];
+    }
+    if (I == 0) b[nd + n] = 0.0;
+  }
+}
+
+// y = A x, FP64, one warp per row (lanes stride the row, then a butterfly)
+__global__ void csr_spmv_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n_rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t a = row_ptr[r], e = row_ptr[r + 1];
+    double s = 0.0;
+    for (int64_t p = a + lane; p < e; p += 32) s = fma(val[p], x[col[p]], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[r] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stokes_rowlen(const Launch& L, const StokesJob& j) {
+  stokes_rowlen_kernel<<<grid_for(j.n, 256), 256, 0, L.stream>>>(j);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stokes_fill(const Launch& L, const StokesJob& j) {
+  const size_t per_warp = ((size_t)(j.kcap_v + j.kcap_p) * (sizeof(int32_t) + sizeof(int16_t)) + 15) & ~size_t(15);
+  const size_t smem = per_warp * kStokesWarps;
+  const void* fn = j.dim == 2 ? (const void*)stokes_fill_kernel<2> : (const void*)stokes_fill_kernel<3>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (j.n + kStokesWarps - 1) / kStokesWarps;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (j.dim == 2)
+    stokes_fill_kernel<2><<<(unsigned)blocks, kStokesWarps * 32, smem, L.stream>>>(j);
+  else
+    stokes_fill_kernel<3><<<(unsigned)blocks, kStokesWarps * 32, smem, L.stream>>>(j);
+  stokes_last_row_kernel<<<grid_for(j.n, 256), 256, 0, L.stream>>>(j.n * j.dim, j.n, j.row_ptr, j.col, j.val);
+  *L.counter += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stokes_rhs(const Launch& L, const StokesJob& j, const double* f, const double* w,
+                              const double* div_f, double* b) {
+  stokes_rhs_kernel<<<grid_for(j.n, 256), 256, 0, L.stream>>>(j, f, w, div_f, b);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
+                            const double* val, const double* x, double* y) {
+  if (n_rows <= 0) return cudaSuccess;
+  csr_spmv_kernel<<<grid_for(n_rows * 32, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace gmls

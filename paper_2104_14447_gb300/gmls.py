@@ -41,7 +41,8 @@ EXPORTED = [
     "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
     "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
     "gmls_server_create", "gmls_server_submit", "gmls_server_wait", "gmls_server_result", "gmls_server_release",
-    "gmls_server_stats", "gmls_server_destroy",
+    "gmls_server_stats", "gmls_server_destroy", "gmls_stokes_size", "gmls_stokes_assemble", "gmls_stokes_rhs",
+    "gmls_csr_spmv",
 ]
 NOALLOC_MAX_POINTS = 262144
 OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT = 0, 1, 2, 3
@@ -71,6 +72,10 @@ class Request(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("basis", ctypes.c_int32),
                 ("degree", ctypes.c_int32), ("k", ctypes.c_int32), ("eps_factor", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("n_functionals", ctypes.c_int32), ("functionals", ctypes.c_int32 * 5)]
+
+
+class StokesParams(ctypes.Structure):
+    _fields_ = [("velocity", ctypes.c_int64), ("pressure", ctypes.c_int64), ("nu", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -122,6 +127,10 @@ def load(path: str = LIB_PATH):
         "gmls_server_release": [vp, i64],
         "gmls_server_stats": [vp, ctypes.POINTER(ServerStats)],
         "gmls_server_destroy": [vp],
+        "gmls_stokes_size": [vp, ctypes.POINTER(StokesParams), P64, P64],
+        "gmls_stokes_assemble": [vp, ctypes.POINTER(StokesParams), vp, vp, vp],
+        "gmls_stokes_rhs": [vp, ctypes.POINTER(StokesParams), vp, vp, vp, vp],
+        "gmls_csr_spmv": [vp, i64, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -259,6 +268,45 @@ class Context:
         rp, col, val = out
         self._check(self.lib.gmls_assemble_csr(self.h, sid, functional, _ptr(rp), _ptr(col), _ptr(val)))
         return out
+
+    # ------------------------------------------------------- Stokes system
+    def stokes_size(self, velocity: int, pressure: int, nu: float):
+        """(n_rows, nnz) of the collocation system (gmls_stokes_size)."""
+        p = StokesParams(velocity, pressure, nu)
+        r, z = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.gmls_stokes_size(self.h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(z)))
+        return r.value, z.value
+
+    def stokes_assemble(self, velocity: int, pressure: int, nu: float):
+        """The collocation system as device CSR tensors (row_ptr, col, val)."""
+        nr, nnz = self.stokes_size(velocity, pressure, nu)
+        rp = torch.empty(nr + 1, dtype=torch.int64, device=self.device)
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
+        val = torch.empty(max(nnz, 1), dtype=torch.float64, device=self.device)
+        p = StokesParams(velocity, pressure, nu)
+        self._check(self.lib.gmls_stokes_assemble(self.h, ctypes.byref(p), _ptr(rp), _ptr(col), _ptr(val)))
+        return rp, col, val
+
+    def stokes_rhs(self, velocity: int, pressure: int, nu: float, f, w, div_f):
+        """Right-hand side b (device) from f, w ([dim, n]) and div f ([n])."""
+        f, w, div_f = (_contig(a, torch.float64).to(self.device) for a in (f, w, div_f))
+        n = div_f.shape[0]
+        b = torch.empty(f.shape[0] * n + n + 1, dtype=torch.float64, device=self.device)
+        p = StokesParams(velocity, pressure, nu)
+        self._check(self.lib.gmls_stokes_rhs(self.h, ctypes.byref(p), _ptr(f), _ptr(w), _ptr(div_f), _ptr(b)))
+        for a in (f, w, div_f, b):
+            a.record_stream(self.stream)  # in use on the context stream until its kernels have run
+        return b
+
+    def spmv(self, row_ptr, col, val, x):
+        """y = A x (gmls_csr_spmv), device tensors."""
+        x = _contig(x, torch.float64).to(self.device)
+        n_rows = row_ptr.shape[0] - 1
+        y = torch.empty(n_rows, dtype=torch.float64, device=self.device)
+        self._check(self.lib.gmls_csr_spmv(self.h, n_rows, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y)))
+        for a in (row_ptr, col, val, x, y):
+            a.record_stream(self.stream)
+        return y
 
     def release(self, hid: int):
         self._check(self.lib.gmls_release(self.h, hid))

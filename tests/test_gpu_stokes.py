@@ -1,0 +1,143 @@
+"""GPU Stokes collocation system (Sec. 3.2, Eq. stokes-block-system) through
+the C ABI, against the oracle's system built from the oracle's own neighbour
+lists and stencils.
+
+* structure (row_ptr, col) bit for bit;
+* values per (row, block) within 1e-10 (FP64 stencils) / 1e-9 (FP32 +
+  refinement) of the block's largest entry;
+* the right-hand side and A x (gmls_csr_spmv) within the same tolerance of
+  the oracle's, relative to sum |a| |x| + |b|;
+* at GPU scale, the manufactured-field residual decays at the rates the
+  oracle pins (h^(m-1) interior, h^(m-2) boundary pressure rows) and the
+  Dirichlet rows are exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2104_14447_gb300 import gmls, inputs
+
+pytestmark = pytest.mark.gpu
+
+M, KV, KP = 4, 48, 36
+TOL = {gmls.FP64: 1e-10, gmls.FP32_REFINE: 1e-9}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2104_14447_gb300 import build
+
+    build.build()
+    c = gmls.Context(0, arena_bytes=16 << 30)
+    yield c
+    c.close()
+
+
+def _gpu(ctx, na, precision, nu):
+    x = inputs.jittered_grid(2, na, seed=0)
+    bflag, nrm = inputs.box_boundary(2, na)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, KV, 1.5)
+    npr = ctx.neighbors_prefix(nv, KP, 1.5)
+    sv = ctx.stencils(nv, gmls.DIVFREE, M, [gmls.CURLCURL], precision=precision)
+    sp = ctx.stencils(npr, gmls.SCALAR, M, [gmls.GRAD, gmls.LAPLACIAN], precision=precision, neumann=True)
+    rp, col, val = ctx.stokes_assemble(sv, sp, nu)
+    return x, bflag, nrm, (cid, nv, npr, sv, sp), (rp, col, val)
+
+
+def _release(ctx, ids):
+    for h in reversed(ids):
+        ctx.release(h)
+
+
+def _oracle(x, bflag, nrm, nu):
+    n = x.shape[1]
+    tg = np.arange(n, dtype=np.int32)
+    iv, ev = oracle.knn(x, tg, KV, 1.5, method="grid")
+    ip, ep = oracle.knn(x, tg, KP, 1.5, method="grid")
+    offv = np.arange(0, n * KV + 1, KV)
+    offp = np.arange(0, n * KP + 1, KP)
+    wcc, _, _ = oracle.stencils(x, tg, offv, iv.reshape(-1), ev, "divfree", M, "curlcurl")
+    wg, _, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "grad", bflag=bflag, normals=nrm.T)
+    wl, bl, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "laplacian", bflag=bflag,
+                                normals=nrm.T)
+    A = oracle.stokes_system(2, n, bflag, nrm, (offv, iv.reshape(-1), wcc),
+                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu)
+    return A, bl[:, 0]
+
+
+@pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
+def test_system_matches_oracle(ctx, precision):
+    nu = 0.7
+    x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, 30, precision, nu)
+    n = x.shape[1]
+    nd = 2 * n
+    A, beta = _oracle(x, bflag, nrm, nu)
+    rp, col, val = rp.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
+    assert np.array_equal(rp, A.indptr) and np.array_equal(col, A.indices)
+    tol = TOL[precision]
+    block = np.where(A.indices < nd, 0, np.where(A.indices < nd + n, 1, 2))
+    row = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    key = row * 3 + block
+    scale = np.zeros(A.shape[0] * 3)
+    np.maximum.at(scale, key, np.abs(A.data))
+    err = np.abs(val - A.data) / np.where(scale[key] > 0, scale[key], 1.0)
+    assert err.max() <= tol, err.max()
+    # right-hand side and A x
+    d = inputs.stokes_manufactured_2d(x, nu)
+    xe = np.concatenate([d["u"].T.reshape(-1), d["p"], [0.0]])
+    b_orc = oracle.stokes_rhs(2, n, bflag, nrm, d["f"], d["w"], d["div_f"], beta)
+    b_gpu = ctx.stokes_rhs(ids[3], ids[4], nu, d["f"], d["w"], d["div_f"]).cpu().numpy()
+    nf = np.abs(nrm[0] * d["f"][0] + nrm[1] * d["f"][1])
+    bscale = np.abs(b_orc)
+    bscale[nd:nd + n] += np.abs(beta) * nf
+    assert np.all(np.abs(b_gpu - b_orc) <= tol * np.maximum(bscale, 1e-300))
+    y_gpu = ctx.spmv(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), torch.from_numpy(val).cuda(),
+                     xe).cpu().numpy()
+    y_orc = A @ xe
+    yscale = np.abs(A) @ np.abs(xe)
+    assert np.all(np.abs(y_gpu - y_orc) <= tol * yscale + 1e-300)
+    _release(ctx, ids)
+
+
+def test_manufactured_residual_converges_at_scale(ctx):
+    """The GPU system alone at 64^2 .. 512^2 (the benchmark grid)."""
+    hs, res = [], {"mom": [], "p_int": [], "p_bdry": []}
+    for na in (64, 128, 256, 512):
+        x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, na, gmls.FP32_REFINE, 1.0)
+        n = x.shape[1]
+        d = inputs.stokes_manufactured_2d(x, 1.0)
+        xe = np.concatenate([d["u"].T.reshape(-1), d["p"], [0.0]])
+        b = ctx.stokes_rhs(ids[3], ids[4], 1.0, d["f"], d["w"], d["div_f"])
+        r = (ctx.spmv(rp, col, val, xe) - b).cpu().numpy()
+        bf = bflag.astype(bool)
+        mom = np.abs(r[:2 * n]).reshape(n, 2)
+        assert np.all(mom[bf] == 0.0)
+        pr = np.abs(r[2 * n:3 * n])
+        hs.append(1.0 / na)
+        res["mom"].append(mom[~bf].max())
+        res["p_int"].append(pr[~bf].max())
+        res["p_bdry"].append(pr[bf].max())
+        _release(ctx, ids)
+    slope = {k: np.polyfit(np.log(hs), np.log(v), 1)[0] for k, v in res.items()}
+    assert slope["mom"] > M - 1 - 0.7, (slope, res)
+    assert slope["p_int"] > M - 1 - 0.7, (slope, res)
+    assert slope["p_bdry"] > M - 2 - 0.7, (slope, res)
+
+
+def test_bad_handles_are_rejected(ctx):
+    x = inputs.jittered_grid(2, 12, seed=0)
+    bflag, nrm = inputs.box_boundary(2, 12)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, KV, 1.5)
+    sv = ctx.stencils(nv, gmls.DIVFREE, M, [gmls.CURLCURL])
+    sp_plain = ctx.stencils(nv, gmls.SCALAR, M, [gmls.GRAD, gmls.LAPLACIAN])  # no Neumann constraint
+    with pytest.raises(gmls.GmlsError) as e:
+        ctx.stokes_size(sv, sp_plain, 1.0)
+    assert e.value.code == gmls.EINVAL
+    with pytest.raises(gmls.GmlsError):
+        ctx.stokes_size(sp_plain, sv, 1.0)  # roles swapped
+    _release(ctx, [cid, nv, sv, sp_plain])
