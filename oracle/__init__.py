@@ -331,3 +331,99 @@ def stokes_rhs(dim, n, bflag, normals, f, w, div_f, beta_lap):
         nf = nf + normals[c] * f[c]
     b[nd:nd + n] = np.where(bf, div_f - beta_lap * nf, div_f)
     return b
+
+
+# ---------------------------------------------------- staggered GMLS (Sec. 2.4)
+def staggered_xi(dx, eps, dim, m, n_gauss=None):
+    """Line integrals xi_i(x_j) = int_{x_T}^{x_j} phi_i(x) . dx (Eq. vector-xi)
+    of the vector basis phi_(c, alpha) = e_c (x - x_T)^alpha / (alpha! eps^|alpha|),
+    |alpha| <= m (a basis of pi_m^v), along the straight segment from the
+    target, by Gauss-Legendre quadrature (exact for these polynomials).
+    dx: [k, dim] offsets x_j - x_T.  Returns Xi [k, dim * C(m+dim, dim)],
+    columns ordered (c, alpha) with c slowest."""
+    alphas = _basis.graded_exponents(dim, m)
+    ng = n_gauss or (m // 2 + 2)
+    t, wq = np.polynomial.legendre.leggauss(ng)
+    t, wq = 0.5 * (t + 1.0), 0.5 * wq  # on [0, 1]
+    dx = np.asarray(dx, dtype=np.float64).reshape(-1, dim)
+    cols = []
+    for c in range(dim):
+        for a in alphas:
+            fact = 1.0
+            for v in a[:dim]:
+                for q in range(2, v + 1):
+                    fact *= q
+            val = np.zeros(dx.shape[0])
+            for tq, wgt in zip(t, wq):
+                pt = tq * dx / eps  # scaled offset of the point on the segment
+                mono = np.ones(dx.shape[0])
+                for k in range(dim):
+                    mono = mono * pt[:, k] ** a[k]
+                val = val + wgt * (mono / fact) * dx[:, c]
+            cols.append(val)
+    return np.stack(cols, axis=1)
+
+
+def staggered_functional(dim, m, eps, name):
+    """Rows of the target functional on the vector basis: 'laplacian' =
+    div q_h(x_T) (Eq. staggered-laplacian-approximation): div phi_(c, alpha)(x_T)
+    = 1/eps for alpha = e_c, else 0; 'grad' = q_h(x_T): component c' of
+    phi_(c, alpha)(x_T) = 1 for c = c', alpha = 0."""
+    alphas = _basis.graded_exponents(dim, m)
+    nq = dim * len(alphas)
+    if name == "laplacian":
+        lam = np.zeros((1, nq))
+        for c in range(dim):
+            lam[0, c * len(alphas) + alphas.index(_e3(c))] = 1.0 / eps
+        return lam
+    if name == "grad":
+        lam = np.zeros((dim, nq))
+        for c in range(dim):
+            lam[c, c * len(alphas) + 0] = 1.0
+        return lam
+    raise ValueError(name)
+
+
+def _e3(k):
+    b = [0, 0, 0]
+    b[k] = 1
+    return tuple(b)
+
+
+def staggered_stencils(x, targets, nbr_off, nbr_idx, eps, m, functional, wpow=4.0):
+    """Staggered GMLS stencils (Sec. 2.4) on point values p.
+
+    Per target: rho_j = p_j - p(x_T) (Eq. vector-rho), the weighted least
+    squares of Eq. staggered-matrix-vector-multiplication over the line
+    integrals Xi, c = (Xi^T W Xi)^+ Xi^T W rho (Eq. staggered-vector-c; the
+    pseudo-inverse, because the line integrals of a basis of pi_m^v are
+    linearly dependent: e.g. e_x xi_y and e_y xi_x integrate to the same
+    xi_x xi_y / 2), and the functional row lambda gives weights on rho,
+    w_rho = W Xi (Xi^T W Xi)^+ lambda^T.  On p: w_j for every neighbour j but
+    the target itself, and -sum_j w_j for the target's own entry.
+    Returns [n_tgt, rows, k, 1] (all k equal) and the ranks of Xi."""
+    x = _soa(x)
+    dim, n = x.shape
+    off = np.asarray(nbr_off, dtype=np.int64)
+    idx = np.asarray(nbr_idx, dtype=np.int64)
+    out, ranks = [], []
+    for q, t in enumerate(np.asarray(targets, dtype=np.int64)):
+        nb = idx[off[q]:off[q + 1]]
+        dx = (x[:, nb] - x[:, t:t + 1]).T
+        r = np.sqrt(np.sum(dx * dx, axis=1))
+        e = float(eps[q])
+        W = np.where(r < e, (1.0 - r / e), 0.0) ** wpow
+        Xi = staggered_xi(dx, e, dim, m)
+        lam = staggered_functional(dim, m, e, functional)
+        B = np.sqrt(W)[:, None] * Xi
+        Bp = np.linalg.pinv(B, rcond=1e-11)
+        ranks.append(np.linalg.matrix_rank(B, tol=1e-11 * np.linalg.norm(B, 2)))
+        w_rho = (np.sqrt(W)[:, None] * (Bp.T @ lam.T)).T  # [rows, k]
+        self_pos = np.flatnonzero(nb == t)
+        if len(self_pos) != 1:
+            raise ValueError("the target must appear once in its own neighbour list")
+        w = w_rho.copy()
+        w[:, self_pos[0]] = 0.0
+        w[:, self_pos[0]] = -np.sum(w, axis=1)
+        out.append(w[:, :, None])
+    return np.stack(out), np.asarray(ranks)
