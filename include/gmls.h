@@ -80,6 +80,17 @@ typedef int32_t gmls_status;
 /* bases */
 #define GMLS_BASIS_SCALAR 0  /* scaled Taylor monomials, Q = C(m+d, d)          (Sec. 2.1) */
 #define GMLS_BASIS_DIVFREE 1 /* divergence-free vector polynomials of degree m  (Sec. 2.2) */
+#define GMLS_BASIS_STAGGERED 2 /* staggered GMLS (Sec. 2.4): the gradient is fitted by vector
+                                  polynomials of degree m through their line integrals
+                                  from x_T to each neighbour, against p_j - p(x_T); the
+                                  line integrals span the monomials of degree 1..m+1,
+                                  which form the basis used.  Functionals GMLS_F_GRAD
+                                  (q_h(x_T)) and GMLS_F_LAPLACIAN (div q_h(x_T)); the
+                                  weights act on point values: the target's own entry
+                                  carries minus the sum of the others.  The target must
+                                  be in its own neighbour list (k-nearest lists always
+                                  hold it); otherwise GMLS_T_UNSUPPORTED and zero
+                                  weights.  No Neumann constraint.                     */
 
 /* weights */
 #define GMLS_WEIGHT_POLY 0 /* W(r) = (1 - r/eps)_+^p  (Eq. kernel, p = weight_power) */

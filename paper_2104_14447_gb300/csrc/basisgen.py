@@ -7,6 +7,13 @@ Bases are written in the normalised scaled monomials of the paper's Taylor
 basis (Eq. basis-functions-3d), p_g(xi) = xi^g / g!, xi = (x - x_T)/eps:
 
 * scalar: p_g for all |g| <= m  (span pi_m(R^d), Sec. 2.1);
+* staggered (Sec. 2.4): p_g for 1 <= |g| <= m+1.  The line integrals
+  int_{x_T}^{x_j} phi . dx of the vector monomials phi = e_c p_a (|a| <= m,
+  the paper's basis of pi_m^v) are eps xi_c xi^a / (a! (|a| + 1)): monomials
+  of degree 1..m+1, so their span has this basis (the paper's d C(m+d, d)
+  columns are linearly dependent).  On it the staggered Laplacian
+  div q_h(x_T) is the Laplacian at 0 and q_h(x_T) the gradient at 0, and the
+  least squares fits the differences p_j - p(x_T);
 * divergence-free: a basis of pi^div_m(R^d) (Sec. 2.2) obtained as the
   reduced-row-echelon null space of the divergence map on (pi_m)^d.  With
   this normalisation d/dxi_k p_g = p_{g - e_k}, so the coefficient of p_q in
@@ -29,6 +36,7 @@ from math import comb
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "basis_tables.cuh")
 DIMS = (2, 3)
+KID = {"scalar": 0, "divfree": 1, "staggered": 2}  # basis codes of the C ABI
 DEGREES = (1, 2, 3, 4)
 
 
@@ -190,13 +198,17 @@ def gen():
     L.append("__device__ __forceinline__ double gmls_scale2(double x, float p) { return x * (double)p; }")
     L.append("")
     summary = []
-    for kind in ("scalar", "divfree"):
+    for kind in ("scalar", "divfree", "staggered"):
         for d in DIMS:
             for m in DEGREES:
                 if kind == "scalar":
                     mons = monomials(d, m)
                     nb, nc = len(mons), 1
                     funcs = [[(0, i, Fraction(1))] for i in range(nb)]
+                elif kind == "staggered":
+                    mons = monomials(d, m + 1)
+                    funcs = [[(0, i, Fraction(1))] for i in range(1, len(mons))]  # no constant
+                    nb, nc = len(funcs), 1
                 else:
                     mons, funcs = divfree(d, m)
                     nb, nc = len(funcs), d
@@ -208,7 +220,7 @@ def gen():
                 L.append("template <typename T>")
                 L.append(f"__device__ __forceinline__ void eval_{name}(const T* xi, T* out, int ld, const T s) {{")
                 ind = "  "
-                emit_monomials(d, m, L, ind)
+                emit_monomials(d, m + 1 if kind == "staggered" else m, L, ind)
                 used = {mi for f in funcs for (_, mi, _) in f}
                 emit_scaled_products(d, mons, used, L, ind)
                 # out[i*ld + c] = sum terms
@@ -223,9 +235,10 @@ def gen():
                         L.append(f"{ind}out[{i} * ld + {c}] = {expr};")
                 L.append("}")
                 # functional rows (coefficients before the eps^{-|beta|} factor)
-                if kind == "scalar":
-                    grad = [[1 if g == tuple(int(j == k) for j in range(3)) else 0 for g in mons] for k in range(d)]
-                    lap = [[1 if (sum(g) == 2 and max(g) == 2) else 0 for g in mons]]
+                if kind in ("scalar", "staggered"):
+                    bm = mons if kind == "scalar" else mons[1:]  # the basis' monomials, in column order
+                    grad = [[1 if g == tuple(int(j == k) for j in range(3)) else 0 for g in bm] for k in range(d)]
+                    lap = [[1 if (sum(g) == 2 and max(g) == 2) else 0 for g in bm]]
                     L.append(f"__device__ constexpr float lam_grad_{name}[{d}][{nb}] = {{" + ", ".join(
                         "{" + ", ".join(f"{v}.0" for v in row) + "}" for row in grad) + "};")
                     L.append(f"__device__ constexpr float lam_lap_{name}[1][{nb}] = {{" + ", ".join(
@@ -251,7 +264,7 @@ def gen():
     L.append("__host__ __device__ constexpr int basis_size(int kind, int d, int m) {")
     L.append("  return")
     for kind, d, m, nb, nc, _ in summary:
-        L.append(f"    (kind == {0 if kind == 'scalar' else 1} && d == {d} && m == {m}) ? {nb} :")
+        L.append(f"    (kind == {KID[kind]} && d == {d} && m == {m}) ? {nb} :")
     L.append("    0;")
     L.append("}")
     L.append("template <typename T>")
@@ -259,7 +272,7 @@ def gen():
     L.append("  switch (kind * 100 + d * 10 + m) {")
     for kind, d, m, nb, nc, _ in summary:
         name = f"{kind}_{d}d_m{m}"
-        L.append(f"    case {(0 if kind == 'scalar' else 1) * 100 + d * 10 + m}: eval_{name}<T>(xi, out, ld, s); break;")
+        L.append(f"    case {KID[kind] * 100 + d * 10 + m}: eval_{name}<T>(xi, out, ld, s); break;")
     L.append("    default: break;")
     L.append("  }")
     L.append("}")
@@ -267,7 +280,7 @@ def gen():
     L.append("template <int KIND, int D, int M> struct BasisEval;")
     for kind, d, m, nb, nc, _ in summary:
         name = f"{kind}_{d}d_m{m}"
-        kid = 0 if kind == "scalar" else 1
+        kid = KID[kind]
         L.append(f"template <> struct BasisEval<{kid}, {d}, {m}> {{")
         L.append("  template <typename T>")
         L.append(f"  __device__ __forceinline__ static void run(const T* xi, T* out, int ld, const T s) {{ eval_{name}<T>(xi, out, ld, s); }}")
@@ -279,8 +292,8 @@ def gen():
     L.append("  switch (kind * 100 + d * 10 + m) {")
     for kind, d, m, nb, nc, _ in summary:
         name = f"{kind}_{d}d_m{m}"
-        key = (0 if kind == "scalar" else 1) * 100 + d * 10 + m
-        if kind == "scalar":
+        key = KID[kind] * 100 + d * 10 + m
+        if kind in ("scalar", "staggered"):
             L.append(f"    case {key}: return fn == 0 ? lam_grad_{name}[row][i] : fn == 1 ? lam_lap_{name}[0][i] : 0.0f;")
         else:
             L.append(f"    case {key}: return fn == 2 ? lam_vlap_{name}[row][i] : fn == 3 ? -lam_vlap_{name}[row][i] : 0.0f;")

@@ -886,14 +886,15 @@ gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, dou
 static bool functional_shape(int basis, int dim, int fn, int* rows, int* ncomp) {
   switch (fn) {
     case GMLS_F_GRAD:
-      if (basis != GMLS_BASIS_SCALAR) return false;
+      if (basis != GMLS_BASIS_SCALAR && basis != GMLS_BASIS_STAGGERED) return false;
       *rows = dim, *ncomp = 1;
       return true;
     case GMLS_F_LAPLACIAN:
-      if (basis != GMLS_BASIS_SCALAR) return false;
+      if (basis != GMLS_BASIS_SCALAR && basis != GMLS_BASIS_STAGGERED) return false;
       *rows = 1, *ncomp = 1;
       return true;
     case GMLS_F_DIV:
+      if (basis == GMLS_BASIS_STAGGERED) return false;
       *rows = 1, *ncomp = dim;
       return true;
     case GMLS_F_VEC_LAPLACIAN:
@@ -914,7 +915,7 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   NbrObj& nb = it->second.nb;
   CloudObj& c = ctx->objs.at(nb.cloud).c;
   const int dim = nb.dim;
-  if (p->basis != GMLS_BASIS_SCALAR && p->basis != GMLS_BASIS_DIVFREE)
+  if (p->basis != GMLS_BASIS_SCALAR && p->basis != GMLS_BASIS_DIVFREE && p->basis != GMLS_BASIS_STAGGERED)
     return fail(ctx, GMLS_EINVAL, "gmls_stencils: unknown basis");
   if (p->weight != GMLS_WEIGHT_POLY || p->weight_power < 1)
     return fail(ctx, GMLS_EINVAL, "gmls_stencils: weight must be GMLS_WEIGHT_POLY with power >= 1");
@@ -970,7 +971,7 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   }
   if (L > kMaxSolveRows) return fail(ctx, GMLS_EINVAL, "gmls_stencils: too many solve rows");
   s.L = L;
-  const int nc = (p->basis == GMLS_BASIS_SCALAR) ? 1 : dim;
+  const int nc = (p->basis == GMLS_BASIS_DIVFREE) ? dim : 1;
   int max_deg = p->degree;
   if (p->degree_per_target) max_deg = 4;
   const int nmax = gmls_gen::basis_size(p->basis, dim, max_deg);
@@ -1153,7 +1154,9 @@ gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functio
     return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: outputs must be device buffers");
   NbrObj& nb = ctx->objs.at(s.nbrs).nb;
   CK(cudaSetDevice(ctx->device), "gmls_assemble_csr");
-  CsrJob j{nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val};
+  int kcap = 1;
+  while (kcap < nb.cap) kcap <<= 1;
+  CsrJob j{kcap, nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val};
   CK(launch_csr(ctx->launch(), j), "gmls_assemble_csr");
   return GMLS_OK;
 }
@@ -1299,7 +1302,17 @@ gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr,
   if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val) || is_host_ptr(x) || is_host_ptr(y))
     return fail(ctx, GMLS_EINVAL, "gmls_csr_spmv: arrays must be device buffers");
   CK(cudaSetDevice(ctx->device), "gmls_csr_spmv");
-  CK(launch_csr_spmv(ctx->launch(), n_rows, row_ptr, col, val, x, y), "gmls_csr_spmv");
+  int32_t* long_rows = arena_alloc<int32_t>(ctx, std::max<int64_t>(n_rows, 1));
+  int32_t* n_long = arena_alloc<int32_t>(ctx, 1);
+  if (!long_rows || !n_long) {
+    ctx->arena.release(long_rows);
+    ctx->arena.release(n_long);
+    return fail(ctx, GMLS_ENOMEM, "gmls_csr_spmv: arena exhausted");
+  }
+  cudaError_t e = launch_csr_spmv(ctx->launch(), n_rows, row_ptr, col, val, x, y, long_rows, n_long);
+  ctx->arena.release(long_rows);  // stream ordered
+  ctx->arena.release(n_long);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_csr_spmv");
   return GMLS_OK;
 }
 

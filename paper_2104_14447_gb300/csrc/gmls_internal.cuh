@@ -224,6 +224,7 @@ cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* 
 
 // -------------------------------------------------------------------- CSR
 struct CsrJob {
+  int kcap;  // power of two >= the longest neighbour list (<= kMaxK)
   int64_t n_tgt;
   const int64_t* off;
   const int32_t* idx;
@@ -265,7 +266,8 @@ cudaError_t launch_stokes_rowlen(const Launch& L, const StokesJob& j);
 cudaError_t launch_stokes_fill(const Launch& L, const StokesJob& j);
 cudaError_t launch_stokes_rhs(const Launch& L, const StokesJob& j, const double* f, const double* w,
                               const double* div_f, double* b);
+// long_rows: scratch [n_rows] int32, n_long: scratch int32
 cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
-                            const double* val, const double* x, double* y);
+                            const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long);
 
 }  // namespace gmls

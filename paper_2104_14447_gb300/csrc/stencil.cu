@@ -301,6 +301,20 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
     st |= GMLS_T_RANK_DEFICIENT;
     skip = true;
   }
+  // staggered basis: the weights act on p_j - p(x_T); the target's own entry
+  // (its row of the tile is zero) later takes minus the sum of the others
+  int self = -1;
+  if (j.kind == GMLS_BASIS_STAGGERED && !skip) {
+    for (int q = 0; q < k; ++q)
+      if (nbr[q] == (int32_t)t) {
+        self = q;
+        break;
+      }
+    if (self < 0) {
+      st |= GMLS_T_UNSUPPORTED;
+      skip = true;
+    }
+  }
   bool redo = false;
   int used_iters = 0;
 
@@ -567,6 +581,20 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
       w[e] = val;
     }
   }
+  if (self >= 0 && !skip) {  // staggered: weights on point values (Sec. 2.4, Eq. vector-rho)
+    group_sync(g.gid, g.nthr);
+    for (int f = 0; f < j.nout; ++f) {
+      const int R = j.out_rows[f];
+      double* w = j.out_w[f] + o0 * (int64_t)R;
+      for (int r = g.tid; r < R; r += g.nthr) {
+        double* wr = w + (int64_t)r * k;
+        double sum = 0.0;
+        for (int q = 0; q < k; ++q)
+          if (q != self) sum += wr[q];
+        wr[self] = -sum;
+      }
+    }
+  }
   if (g.tid == 0) {
     j.status[to] = st;
     if (j.iters) j.iters[to] = (uint8_t)used_iters;
@@ -718,15 +746,17 @@ cudaError_t launch_bucketing(const Launch& L, const BucketJob& b) {
 // (id, position) pairs in shared memory) and write every row of the target.
 // C (components per neighbour) is a compile-time constant so that the
 // element -> (neighbour, component) split is a multiply-shift.
-constexpr int kCsrWarps = 4;
+// Shared memory per warp is sized from the longest list (j.kcap entries), so
+// short lists keep many warps resident to hide the loads.
+constexpr int kCsrWarps = 8;
 
 template <int C>
 __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
-  __shared__ int32_t sid[kCsrWarps][kMaxK];
-  __shared__ int16_t spos[kCsrWarps][kMaxK];
+  extern __shared__ __align__(16) unsigned char csr_smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t* ids = sid[w];
-  int16_t* pos = spos[w];
+  int32_t* ids = reinterpret_cast<int32_t*>(csr_smem) + (size_t)w * j.kcap;
+  int16_t* pos = reinterpret_cast<int16_t*>(reinterpret_cast<int32_t*>(csr_smem) + (size_t)kCsrWarps * j.kcap) +
+                 (size_t)w * j.kcap;
   for (int64_t t = (int64_t)blockIdx.x * kCsrWarps + w; t < j.n_tgt; t += (int64_t)gridDim.x * kCsrWarps) {
     const int64_t o = j.off[t];
     const int k = (int)(j.off[t + 1] - o);
@@ -780,14 +810,18 @@ cudaError_t launch_csr(const Launch& L, const CsrJob& j) {
   }
   int64_t blocks = (j.n_tgt + kCsrWarps - 1) / kCsrWarps;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  const size_t smem = (size_t)kCsrWarps * j.kcap * (sizeof(int32_t) + sizeof(int16_t));
+  const void* fn = j.nc == 1 ? (const void*)csr_kernel<1> : j.nc == 2 ? (const void*)csr_kernel<2>
+                                                                      : (const void*)csr_kernel<3>;
+  if (j.nc < 1 || j.nc > 3 || j.kcap < 1 || j.kcap > kMaxK) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   if (j.nc == 1)
-    csr_kernel<1><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+    csr_kernel<1><<<(unsigned)blocks, kCsrWarps * 32, smem, L.stream>>>(j);
   else if (j.nc == 2)
-    csr_kernel<2><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
-  else if (j.nc == 3)
-    csr_kernel<3><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+    csr_kernel<2><<<(unsigned)blocks, kCsrWarps * 32, smem, L.stream>>>(j);
   else
-    return cudaErrorInvalidValue;
+    csr_kernel<3><<<(unsigned)blocks, kCsrWarps * 32, smem, L.stream>>>(j);
   *L.counter += 1;
   return cudaGetLastError();
 }

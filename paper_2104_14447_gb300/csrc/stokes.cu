@@ -185,17 +185,55 @@ __global__ void stokes_rhs_kernel(StokesJob j, const double* __restrict__ f, con
   }
 }
 
-// y = A x, FP64, one warp per row (lanes stride the row, then a butterfly)
+// y = A x, FP64.  Pass 1: one warp per row (lanes stride the row, then a
+// butterfly); rows longer than kLongRow (the zero-mean row of the Stokes
+// system holds every pressure column) are queued instead.  Pass 2: one block
+// per queued row, a fixed-order block reduction.  Both passes are
+// deterministic.
+constexpr int64_t kLongRow = 8192;
+constexpr int kSpmvBlock = 1024;
+
 __global__ void csr_spmv_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+                                const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
+                                int32_t* __restrict__ long_rows, int32_t* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n_rows;
        r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t a = row_ptr[r], e = row_ptr[r + 1];
+    if (e - a > kLongRow) {
+      if (lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)r;
+      continue;
+    }
     double s = 0.0;
     for (int64_t p = a + lane; p < e; p += 32) s = fma(val[p], x[col[p]], s);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y[r] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kSpmvBlock) csr_spmv_long_kernel(const int64_t* __restrict__ row_ptr,
+                                                                   const int32_t* __restrict__ col,
+                                                                   const double* __restrict__ val,
+                                                                   const double* __restrict__ x, double* __restrict__ y,
+                                                                   const int32_t* __restrict__ long_rows,
+                                                                   const int32_t* __restrict__ n_long) {
+  __shared__ double part[kSpmvBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cnt = *n_long;
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int64_t r = long_rows[i];
+    const int64_t a = row_ptr[r], e = row_ptr[r + 1];
+    double s = 0.0;
+    for (int64_t p = a + threadIdx.x; p < e; p += kSpmvBlock) s = fma(val[p], x[col[p]], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) part[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+      double t = part[lane];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) y[r] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -232,10 +270,14 @@ cudaError_t launch_stokes_rhs(const Launch& L, const StokesJob& j, const double*
 }
 
 cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
-                            const double* val, const double* x, double* y) {
+                            const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long) {
   if (n_rows <= 0) return cudaSuccess;
-  csr_spmv_kernel<<<grid_for(n_rows * 32, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y);
-  *L.counter += 1;
+  cudaError_t e = cudaMemsetAsync(n_long, 0, sizeof(int32_t), L.stream);
+  if (e != cudaSuccess) return e;
+  csr_spmv_kernel<<<grid_for(n_rows * 32, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y, long_rows,
+                                                                       n_long);
+  csr_spmv_long_kernel<<<152, kSpmvBlock, 0, L.stream>>>(row_ptr, col, val, x, y, long_rows, n_long);
+  *L.counter += 2;
   return cudaGetLastError();
 }
 

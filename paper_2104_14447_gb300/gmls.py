@@ -28,7 +28,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -
 T_OK, T_RANK_DEFICIENT, T_ILL_CONDITIONED, T_REFINE_NOT_CONVERGED = 0, 1, 2, 4
 T_TOO_FEW_NEIGHBOURS, T_FP64_FALLBACK, T_OVERFLOW = 8, 16, 32
 KNN, RADIUS = 0, 1
-SCALAR, DIVFREE = 0, 1
+SCALAR, DIVFREE, STAGGERED = 0, 1, 2
 WEIGHT_POLY = 0
 GRAD, LAPLACIAN, DIV, VEC_LAPLACIAN, CURLCURL = 0, 1, 2, 3, 4
 FP64, FP32_REFINE = 0, 1
