@@ -231,15 +231,42 @@ def run_ours(args, rank, world, local_rank):
     host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
     d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v)
     h2d = x_pin.numel() * x_pin.element_size()
+    # The operators go back to the host on two copy streams while the GPU
+    # computes the rest: the divergence-free stencils and their CSR first,
+    # their copy overlapping the scalar stencils; the two scalar operators
+    # (the smaller ones) last.
+    copy_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+
+    def step_e2e(x_src):
+        cid = ctx.cloud(x_src)
+        n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+        n36 = ctx.neighbors_prefix(n48, K_SCALAR, EPS_FACTOR)
+        s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
+        ctx.assemble_csr(s_df, gmls.VEC_LAPLACIAN, out=bufs["vl"])
+        done_vl = torch.cuda.Event()
+        done_vl.record(stream)
+        s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
+        ctx.assemble_csr(s_sc, gmls.GRAD, out=bufs["grad"])
+        done_grad = torch.cuda.Event()
+        done_grad.record(stream)
+        ctx.assemble_csr(s_sc, gmls.DIV, out=bufs["div"])
+        done_div = torch.cuda.Event()
+        done_div.record(stream)
+        for cs, ev_done, names in ((copy_streams[0], done_vl, ("vl",)), (copy_streams[1], done_grad, ("grad",)),
+                                   (copy_streams[0], done_div, ("div",))):
+            cs.wait_event(ev_done)
+            with torch.cuda.stream(cs):
+                for kname in names:
+                    for dst, src in zip(host_out[kname], bufs[kname]):
+                        dst.copy_(src, non_blocking=True)
+        return cid, n48, n36, s_df, s_sc
+
     e2e_ms = []
     for s in range(max(2, min(args.steps, 5)) + 1):
         flush.fill_(s & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ids = step(x_pin)
-        for kname in bufs:
-            for dst, src in zip(host_out[kname], bufs[kname]):
-                dst.copy_(src, non_blocking=True)
+        ids = step_e2e(x_pin)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         release(ids)

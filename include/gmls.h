@@ -65,7 +65,7 @@ typedef int32_t gmls_status;
 
 /* per-target status bits (uint8 per target) */
 #define GMLS_T_OK 0
-#define GMLS_T_RANK_DEFICIENT 1      /* |r_ii| <= 64 n u max|r|: weights unreliable          */
+#define GMLS_T_RANK_DEFICIENT 1      /* |r_ii| <= 64 n u max|r| (FP64): weights set to zero   */
 #define GMLS_T_ILL_CONDITIONED 2     /* max|r_ii| / min|r_ii| > 1e6                            */
 #define GMLS_T_REFINE_NOT_CONVERGED 4 /* FP32 refinement missed its tolerance: FP64 redone */
 #define GMLS_T_TOO_FEW_NEIGHBOURS 8  /* fewer candidates than requested (weights zero)       */
@@ -270,7 +270,10 @@ gmls_status gmls_stokes_rhs(gmls_ctx* ctx, const gmls_stokes_params* params, con
 /*
  * y = A x for a CSR matrix with n_rows rows (row_ptr int64 [n_rows + 1], col
  * int32, val double; x and y double), FP64, all device buffers; asynchronous
- * on the context stream.  The sum order within a row is not sequential.
+ * on the context stream.  The sum order within a row is not sequential but
+ * fixed (it depends only on the row's length): repeated calls give the same
+ * bits.  Rows of more than 8192 entries are summed by thread blocks (cut
+ * into 128 slices when there are at most 64 such rows).
  */
 gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                           const double* val, const double* x, double* y);

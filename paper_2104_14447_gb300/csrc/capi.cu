@@ -114,6 +114,7 @@ struct NbrObj {
   bool variable = false;  // per-target list lengths (offsets from a scan)
   bool all_targets = false;  // targets are every point of the cloud, in order
   int64_t idx_cap = 0;  // allocated index entries
+  int16_t* order = nullptr;  // id order of the lists, computed on first use (CSR, Stokes system)
   int refs = 0;
 };
 
@@ -1080,6 +1081,22 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   return GMLS_OK;
 }
 
+// the lists' id order (lists never change after creation: computed once)
+static gmls_status ensure_order(gmls_ctx* ctx, NbrObj& nb, const char* who) {
+  if (nb.order) return GMLS_OK;
+  nb.order = arena_alloc<int16_t>(ctx, std::max<int64_t>(nb.idx_cap, 1));
+  if (!nb.order) return fail(ctx, GMLS_ENOMEM, std::string(who) + ": arena exhausted (neighbour id order)");
+  int kcap = 1;
+  while (kcap < nb.cap) kcap <<= 1;
+  cudaError_t e = launch_nbr_order(ctx->launch(), nb.n_tgt, nb.off, nb.idx, kcap, nb.order);
+  if (e != cudaSuccess) {
+    ctx->arena.release(nb.order);
+    nb.order = nullptr;
+    return cuda_fail(ctx, e, who);
+  }
+  return GMLS_OK;
+}
+
 static int find_out(const StencilObj& s, int fn) {
   for (int f = 0; f < s.nout; ++f)
     if (s.fn[f] == fn) return f;
@@ -1154,20 +1171,14 @@ gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functio
     return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: outputs must be device buffers");
   NbrObj& nb = ctx->objs.at(s.nbrs).nb;
   CK(cudaSetDevice(ctx->device), "gmls_assemble_csr");
-  int kcap = 1;
-  while (kcap < nb.cap) kcap <<= 1;
-  CsrJob j{kcap, nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val};
+  gmls_status r = ensure_order(ctx, nb, "gmls_assemble_csr");
+  if (r) return r;
+  CsrJob j{nb.order, nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val};
   CK(launch_csr(ctx->launch(), j), "gmls_assemble_csr");
   return GMLS_OK;
 }
 
 // ------------------------------------------------------------ Stokes system
-static int pow2_at_least(int v) {
-  int p = 32;
-  while (p < v) p <<= 1;
-  return p;
-}
-
 // Validate the two stencil handles of a Stokes system and fill the job's
 // inputs; *n_rows = n d + n + 1.
 static gmls_status stokes_job(gmls_ctx* ctx, const gmls_stokes_params* p, StokesJob* j, int64_t* n_rows,
@@ -1185,8 +1196,8 @@ static gmls_status stokes_job(gmls_ctx* ctx, const gmls_stokes_params* p, Stokes
   if (sp.basis != GMLS_BASIS_SCALAR || fg < 0 || fl < 0 || !sp.neumann)
     return fail(ctx, GMLS_EINVAL,
                 std::string(who) + ": pressure handle needs the scalar basis with gradient and Laplacian, neumann = 1");
-  const NbrObj& nv = ctx->objs.at(sv.nbrs).nb;
-  const NbrObj& np = ctx->objs.at(sp.nbrs).nb;
+  NbrObj& nv = ctx->objs.at(sv.nbrs).nb;
+  NbrObj& np = ctx->objs.at(sp.nbrs).nb;
   if (nv.cloud != np.cloud || !nv.all_targets || !np.all_targets)
     return fail(ctx, GMLS_EINVAL, std::string(who) + ": both stencils must cover every point of one cloud, in order");
   const CloudObj& c = ctx->objs.at(nv.cloud).c;
@@ -1211,8 +1222,6 @@ static gmls_status stokes_job(gmls_ctx* ctx, const gmls_stokes_params* p, Stokes
   j->beta_col = sp.src[fl];
   j->bflag = c.bflag;
   j->normals = c.normals;
-  j->kcap_v = pow2_at_least(nv.cap);
-  j->kcap_p = pow2_at_least(np.cap);
   *n_rows = c.n * c.dim + c.n + 1;
   return GMLS_OK;
 }
@@ -1273,6 +1282,16 @@ gmls_status gmls_stokes_assemble(gmls_ctx* ctx, const gmls_stokes_params* p, int
   if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val))
     return fail(ctx, GMLS_EINVAL, "gmls_stokes_assemble: outputs must be device buffers");
   CK(cudaSetDevice(ctx->device), "gmls_stokes_assemble");
+  {
+    const StencilObj& sv = ctx->objs.at(p->velocity).s;
+    const StencilObj& sp = ctx->objs.at(p->pressure).s;
+    NbrObj& nv = ctx->objs.at(sv.nbrs).nb;
+    NbrObj& np = ctx->objs.at(sp.nbrs).nb;
+    if ((r = ensure_order(ctx, nv, "gmls_stokes_assemble")) || (r = ensure_order(ctx, np, "gmls_stokes_assemble")))
+      return r;
+    j.order_v = nv.order;
+    j.order_p = np.order;
+  }
   r = stokes_rows(ctx, j, nr, row_ptr, "gmls_stokes_assemble");
   if (r) return r;
   j.col = col;
@@ -1304,14 +1323,17 @@ gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr,
   CK(cudaSetDevice(ctx->device), "gmls_csr_spmv");
   int32_t* long_rows = arena_alloc<int32_t>(ctx, std::max<int64_t>(n_rows, 1));
   int32_t* n_long = arena_alloc<int32_t>(ctx, 1);
-  if (!long_rows || !n_long) {
+  double* partial = arena_alloc<double>(ctx, csr_spmv_partial_elems());
+  if (!long_rows || !n_long || !partial) {
     ctx->arena.release(long_rows);
     ctx->arena.release(n_long);
+    ctx->arena.release(partial);
     return fail(ctx, GMLS_ENOMEM, "gmls_csr_spmv: arena exhausted");
   }
-  cudaError_t e = launch_csr_spmv(ctx->launch(), n_rows, row_ptr, col, val, x, y, long_rows, n_long);
+  cudaError_t e = launch_csr_spmv(ctx->launch(), n_rows, row_ptr, col, val, x, y, long_rows, n_long, partial);
   ctx->arena.release(long_rows);  // stream ordered
   ctx->arena.release(n_long);
+  ctx->arena.release(partial);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_csr_spmv");
   return GMLS_OK;
 }
@@ -1395,7 +1417,9 @@ gmls_status gmls_release(gmls_ctx* ctx, int64_t id) {
       a.release(p);
   } else if (o.kind == K_NBRS) {
     if (o.nb.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: neighbours have live stencil handles");
-    for (void* p : {(void*)o.nb.tgt, (void*)o.nb.off, (void*)o.nb.idx, (void*)o.nb.eps, (void*)o.nb.status}) a.release(p);
+    for (void* p : {(void*)o.nb.tgt, (void*)o.nb.off, (void*)o.nb.idx, (void*)o.nb.eps, (void*)o.nb.status,
+                    (void*)o.nb.order})
+      a.release(p);
     auto ci = ctx->objs.find(o.nb.cloud);
     if (ci != ctx->objs.end()) ci->second.c.refs--;
   } else {

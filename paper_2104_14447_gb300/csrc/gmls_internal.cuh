@@ -223,8 +223,13 @@ cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, i
 cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count);
 
 // -------------------------------------------------------------------- CSR
+// id order of neighbour lists (see nbr_order_kernel): order[off[t] + r] =
+// position of target t's entry of rank r by particle id
+cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off, const int32_t* idx, int kcap,
+                             int16_t* order);
+
 struct CsrJob {
-  int kcap;  // power of two >= the longest neighbour list (<= kMaxK)
+  const int16_t* order;  // id order of the lists
   int64_t n_tgt;
   const int64_t* off;
   const int32_t* idx;
@@ -256,7 +261,8 @@ struct StokesJob {
   int beta_stride, beta_col;
   const uint8_t* bflag;      // [n]
   const double* normals;     // [c n + I]
-  int kcap_v, kcap_p;        // powers of two >= the longest list of each kind
+  const int16_t* order_v;    // id order of the velocity lists
+  const int16_t* order_p;    // id order of the pressure lists
   int32_t* row_len;          // scratch [n d + n + 1]
   int64_t* row_ptr;          // [n d + n + 2]
   int32_t* col;
@@ -266,8 +272,10 @@ cudaError_t launch_stokes_rowlen(const Launch& L, const StokesJob& j);
 cudaError_t launch_stokes_fill(const Launch& L, const StokesJob& j);
 cudaError_t launch_stokes_rhs(const Launch& L, const StokesJob& j, const double* f, const double* w,
                               const double* div_f, double* b);
-// long_rows: scratch [n_rows] int32, n_long: scratch int32
+// scratch: long_rows int32 [n_rows], n_long int32, partial double [csr_spmv_partial_elems()]
+size_t csr_spmv_partial_elems();
 cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
-                            const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long);
+                            const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long,
+                            double* partial);
 
 }  // namespace gmls

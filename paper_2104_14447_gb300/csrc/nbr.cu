@@ -636,9 +636,13 @@ cudaError_t launch_nbr_query(const Launch& L, const NbrQuery& q) {
   // candidate buffer: about twice k for k-nearest lists (a fuller buffer only
   // triggers a smaller search radius), the full 1024 for radius lists, which
   // must hold every candidate inside eps
+  // k-nearest: a buffer of at least twice k (up to 2048 for k = 1024), so a
+  // radius that gathers between k and the buffer size always exists on
+  // quasi-uniform clouds; radius lists: the 1024 entries a list may hold
   int cap = 64;
   const int want = q.mode == GMLS_NBR_KNN ? 2 * q.k : kNbrCap;
-  while (cap < want && cap < kNbrCap) cap <<= 1;
+  const int limit = q.mode == GMLS_NBR_KNN ? 2 * kNbrCap : kNbrCap;
+  while (cap < want && cap < limit) cap <<= 1;
   const size_t smem = warpbuf_bytes(cap) * kQueryWarps;
   const void* fn = q.cloud.dim == 2 ? (const void*)nbr_query_kernel<2> : (const void*)nbr_query_kernel<3>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

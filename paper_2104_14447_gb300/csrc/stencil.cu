@@ -556,6 +556,8 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
     group_sync(g.gid, g.nthr);
   }
 
+  // a rank-deficient system has no unique weights: store zeros (and no beta)
+  if (st & GMLS_T_RANK_DEFICIENT) skip = true;
   if (redo) {  // the FP64 redo writes this target's outputs and status
     if (g.tid == 0) j.status[to] = st;
     group_sync(g.gid, g.nthr);
@@ -742,28 +744,27 @@ cudaError_t launch_bucketing(const Launch& L, const BucketJob& b) {
 }
 
 // ------------------------------------------------------------------------ CSR
-// Warp per target: order the neighbours by particle id once (bitonic sort of
-// (id, position) pairs in shared memory) and write every row of the target.
-// C (components per neighbour) is a compile-time constant so that the
-// element -> (neighbour, component) split is a multiply-shift.
-// Shared memory per warp is sized from the longest list (j.kcap entries), so
-// short lists keep many warps resident to hide the loads.
-constexpr int kCsrWarps = 8;
+// Id order of the neighbour lists, computed once per list handle: order[o + r]
+// is the position within target t's list (offset o) of its entry of rank r by
+// particle id.  Warp per target: bitonic sort of (id, position) pairs in
+// shared memory sized from the longest list (kcap entries per warp).
+constexpr int kOrderWarps = 8;
 
-template <int C>
-__global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
-  extern __shared__ __align__(16) unsigned char csr_smem[];
+__global__ void __launch_bounds__(kOrderWarps * 32) nbr_order_kernel(int64_t n_tgt, const int64_t* __restrict__ off,
+                                                                     const int32_t* __restrict__ idx, int kcap,
+                                                                     int16_t* __restrict__ order) {
+  extern __shared__ __align__(16) unsigned char order_smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t* ids = reinterpret_cast<int32_t*>(csr_smem) + (size_t)w * j.kcap;
-  int16_t* pos = reinterpret_cast<int16_t*>(reinterpret_cast<int32_t*>(csr_smem) + (size_t)kCsrWarps * j.kcap) +
-                 (size_t)w * j.kcap;
-  for (int64_t t = (int64_t)blockIdx.x * kCsrWarps + w; t < j.n_tgt; t += (int64_t)gridDim.x * kCsrWarps) {
-    const int64_t o = j.off[t];
-    const int k = (int)(j.off[t + 1] - o);
+  int32_t* ids = reinterpret_cast<int32_t*>(order_smem) + (size_t)w * kcap;
+  int16_t* pos = reinterpret_cast<int16_t*>(reinterpret_cast<int32_t*>(order_smem) + (size_t)kOrderWarps * kcap) +
+                 (size_t)w * kcap;
+  for (int64_t t = (int64_t)blockIdx.x * kOrderWarps + w; t < n_tgt; t += (int64_t)gridDim.x * kOrderWarps) {
+    const int64_t o = off[t];
+    const int k = (int)(off[t + 1] - o);
     int n2 = 1;
     while (n2 < k) n2 <<= 1;
     for (int i = lane; i < n2; i += 32) {
-      ids[i] = (i < k) ? j.idx[o + i] : INT_MAX;
+      ids[i] = (i < k) ? idx[o + i] : INT_MAX;
       pos[i] = (int16_t)i;
     }
     __syncwarp();
@@ -772,12 +773,12 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
         for (int i = lane; i < (n2 >> 1); i += 32) {
           // stride is a power of two: a = 2 stride (i / stride) + i % stride
           const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
-          bool asc = (a & size) == 0;
-          int32_t ia = ids[a], ib = ids[b];
-          if ((ib < ia) == asc) {
+          const bool asc = (a & size) == 0;
+          const int32_t ia = ids[a], ib = ids[b];
+          if ((ib < ia) == asc && ia != ib) {
             ids[a] = ib;
             ids[b] = ia;
-            int16_t pa = pos[a];
+            const int16_t pa = pos[a];
             pos[a] = pos[b];
             pos[b] = pa;
           }
@@ -785,21 +786,51 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
         __syncwarp();
       }
     }
+    for (int r = lane; r < k; r += 32) order[o + r] = pos[r];
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off, const int32_t* idx, int kcap,
+                             int16_t* order) {
+  if (n_tgt == 0) return cudaSuccess;
+  if (kcap < 1 || kcap > kMaxK) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kOrderWarps * kcap * (sizeof(int32_t) + sizeof(int16_t));
+  cudaError_t e = cudaFuncSetAttribute(nbr_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (n_tgt + kOrderWarps - 1) / kOrderWarps;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  nbr_order_kernel<<<(unsigned)blocks, kOrderWarps * 32, smem, L.stream>>>(n_tgt, off, idx, kcap, order);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+// CSR of one functional from the cached id order: warp per target, every
+// row's entries written in ascending column order, no sorting.  C
+// (components per neighbour) is a compile-time constant.
+constexpr int kCsrWarps = 8;
+
+template <int C>
+__global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t t = (int64_t)blockIdx.x * kCsrWarps + w; t < j.n_tgt; t += (int64_t)gridDim.x * kCsrWarps) {
+    const int64_t o = j.off[t];
+    const int k = (int)(j.off[t + 1] - o);
     const int rowlen = k * C;
     const int64_t base = o * (int64_t)j.rows * C;
     for (int r = 0; r < j.rows; ++r) {
       const int64_t row = t * j.rows + r;
       const int64_t start = base + (int64_t)r * rowlen;
       if (lane == 0) j.row_ptr[row] = start;
-      const double* wr = j.w + base + (int64_t)r * rowlen;
+      const double* wr = j.w + start;
       for (int e = lane; e < rowlen; e += 32) {
-        const int q = e / C, c = e % C;
-        j.col[start + e] = ids[q] * C + c;
-        j.val[start + e] = wr[pos[q] * C + c];
+        const int q = e / C, c = e - q * C;
+        const int p = j.order[o + q];
+        j.col[start + e] = j.idx[o + p] * C + c;
+        j.val[start + e] = wr[p * C + c];
       }
     }
     if (t == j.n_tgt - 1 && lane == 0) j.row_ptr[j.n_tgt * j.rows] = base + (int64_t)j.rows * rowlen;
-    __syncwarp();
   }
 }
 
@@ -810,18 +841,14 @@ cudaError_t launch_csr(const Launch& L, const CsrJob& j) {
   }
   int64_t blocks = (j.n_tgt + kCsrWarps - 1) / kCsrWarps;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  const size_t smem = (size_t)kCsrWarps * j.kcap * (sizeof(int32_t) + sizeof(int16_t));
-  const void* fn = j.nc == 1 ? (const void*)csr_kernel<1> : j.nc == 2 ? (const void*)csr_kernel<2>
-                                                                      : (const void*)csr_kernel<3>;
-  if (j.nc < 1 || j.nc > 3 || j.kcap < 1 || j.kcap > kMaxK) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   if (j.nc == 1)
-    csr_kernel<1><<<(unsigned)blocks, kCsrWarps * 32, smem, L.stream>>>(j);
+    csr_kernel<1><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
   else if (j.nc == 2)
-    csr_kernel<2><<<(unsigned)blocks, kCsrWarps * 32, smem, L.stream>>>(j);
+    csr_kernel<2><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
+  else if (j.nc == 3)
+    csr_kernel<3><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
   else
-    csr_kernel<3><<<(unsigned)blocks, kCsrWarps * 32, smem, L.stream>>>(j);
+    return cudaErrorInvalidValue;
   *L.counter += 1;
   return cudaGetLastError();
 }

@@ -16,7 +16,8 @@
 // constrained stencil (Laplacian ~ sum w_j phi_j + beta h, Sec. 2.3), which
 // puts -nu beta n . (curl curl stencil) on the velocity and div f - beta n . f
 // on the right.  Columns ascend within every row (velocity block first, then
-// pressure, then the multiplier), each neighbour list in particle-id order.
+// pressure, then the multiplier), each neighbour list in particle-id order
+// (the lists' cached id order).
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -27,7 +28,7 @@ namespace gmls {
 
 namespace {
 
-constexpr int kStokesWarps = 4;
+constexpr int kStokesWarps = 8;
 
 inline unsigned grid_for(int64_t n, int per_block) {
   int64_t b = (n + per_block - 1) / per_block;
@@ -49,56 +50,14 @@ __global__ void stokes_rowlen_kernel(StokesJob j) {
   }
 }
 
-// Sort the k ids of one list (padded to the power of two kc with INT_MAX)
-// together with their positions: bitonic network over shared memory, one warp.
-__device__ void warp_sort_ids(int32_t* ids, int16_t* pos, int k, int kc, int lane) {
-  for (int size = 2; size <= kc; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = lane; i < (kc >> 1); i += 32) {
-        // stride is a power of two: a = 2 stride (i / stride) + i % stride
-        const int a = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), b = a + stride;
-        const bool asc = (a & size) == 0;
-        const int32_t ia = ids[a], ib = ids[b];
-        if ((ib < ia) == asc && ia != ib) {
-          ids[a] = ib;
-          ids[b] = ia;
-          const int16_t pa = pos[a];
-          pos[a] = pos[b];
-          pos[b] = pa;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  (void)k;
-}
-
 template <int D>
 __global__ void __launch_bounds__(kStokesWarps * 32) stokes_fill_kernel(StokesJob j) {
-  extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const size_t per_warp = (size_t)(j.kcap_v + j.kcap_p) * (sizeof(int32_t) + sizeof(int16_t));
-  unsigned char* base = smem + warp * ((per_warp + 15) & ~size_t(15));
-  int32_t* idv = reinterpret_cast<int32_t*>(base);
-  int32_t* idp = idv + j.kcap_v;
-  int16_t* pv = reinterpret_cast<int16_t*>(idp + j.kcap_p);
-  int16_t* pp = pv + j.kcap_v;
   const int64_t n = j.n, nd = n * D;
   const double nu = j.nu;
   for (int64_t I = blockIdx.x * (int64_t)kStokesWarps + warp; I < n; I += (int64_t)gridDim.x * kStokesWarps) {
     const int64_t ov = j.off_v[I], op = j.off_p[I];
     const int kv = (int)(j.off_v[I + 1] - ov), kp = (int)(j.off_p[I + 1] - op);
-    for (int i = lane; i < j.kcap_v; i += 32) {
-      idv[i] = (i < kv) ? j.idx_v[ov + i] : INT_MAX;
-      pv[i] = (int16_t)i;
-    }
-    for (int i = lane; i < j.kcap_p; i += 32) {
-      idp[i] = (i < kp) ? j.idx_p[op + i] : INT_MAX;
-      pp[i] = (int16_t)i;
-    }
-    __syncwarp();
-    warp_sort_ids(idv, pv, kv, j.kcap_v, lane);
-    warp_sort_ids(idp, pp, kp, j.kcap_p, lane);
     const int kvd = kv * D;
     const double* acc = j.w_cc + ov * D * D;  // this point's curl curl weights
     if (!j.bflag[I]) {
@@ -107,18 +66,21 @@ __global__ void __launch_bounds__(kStokesWarps * 32) stokes_fill_kernel(StokesJo
         const int64_t r = I * D + c, s = j.row_ptr[r];
         for (int e = lane; e < kvd; e += 32) {
           const int q = e / D, cc = e - q * D;
-          j.col[s + e] = idv[q] * D + cc;
-          j.val[s + e] = __dmul_rn(nu, acc[(int64_t)c * kvd + pv[q] * D + cc]);
+          const int pv = j.order_v[ov + q];
+          j.col[s + e] = j.idx_v[ov + pv] * D + cc;
+          j.val[s + e] = __dmul_rn(nu, acc[(int64_t)c * kvd + pv * D + cc]);
         }
         for (int e = lane; e < kp; e += 32) {
-          j.col[s + kvd + e] = (int32_t)(nd + idp[e]);
-          j.val[s + kvd + e] = j.w_grad[op * D + (int64_t)c * kp + pp[e]];
+          const int pp = j.order_p[op + e];
+          j.col[s + kvd + e] = (int32_t)(nd + j.idx_p[op + pp]);
+          j.val[s + kvd + e] = j.w_grad[op * D + (int64_t)c * kp + pp];
         }
       }
       const int64_t s = j.row_ptr[nd + I];
       for (int e = lane; e < kp; e += 32) {
-        j.col[s + e] = (int32_t)(nd + idp[e]);
-        j.val[s + e] = j.w_lap[op + pp[e]];
+        const int pp = j.order_p[op + e];
+        j.col[s + e] = (int32_t)(nd + j.idx_p[op + pp]);
+        j.val[s + e] = j.w_lap[op + pp];
       }
       if (lane == 0) {
         j.col[s + kp] = (int32_t)(nd + n);
@@ -137,24 +99,25 @@ __global__ void __launch_bounds__(kStokesWarps * 32) stokes_fill_kernel(StokesJo
       const int64_t s = j.row_ptr[nd + I];
       for (int e = lane; e < kvd; e += 32) {
         const int q = e / D, cc = e - q * D;
-        const int64_t w0 = (int64_t)pv[q] * D + cc;
+        const int pv = j.order_v[ov + q];
+        const int64_t w0 = (int64_t)pv * D + cc;
         // n . a, evaluated ((n_0 a_0) + (n_1 a_1)) + (n_2 a_2)
         double nda = __dmul_rn(nrm[0], acc[w0]);
 #pragma unroll
         for (int c = 1; c < D; ++c) nda = __dadd_rn(nda, __dmul_rn(nrm[c], acc[(int64_t)c * kvd + w0]));
-        j.col[s + e] = idv[q] * D + cc;
+        j.col[s + e] = j.idx_v[ov + pv] * D + cc;
         j.val[s + e] = -__dmul_rn(nu, __dmul_rn(beta, nda));
       }
       for (int e = lane; e < kp; e += 32) {
-        j.col[s + kvd + e] = (int32_t)(nd + idp[e]);
-        j.val[s + kvd + e] = j.w_lap[op + pp[e]];
+        const int pp = j.order_p[op + e];
+        j.col[s + kvd + e] = (int32_t)(nd + j.idx_p[op + pp]);
+        j.val[s + kvd + e] = j.w_lap[op + pp];
       }
       if (lane == 0) {
         j.col[s + kvd + kp] = (int32_t)(nd + n);
         j.val[s + kvd + kp] = 1.0;
       }
     }
-    __syncwarp();
   }
 }
 
@@ -187,11 +150,17 @@ __global__ void stokes_rhs_kernel(StokesJob j, const double* __restrict__ f, con
 
 // y = A x, FP64.  Pass 1: one warp per row (lanes stride the row, then a
 // butterfly); rows longer than kLongRow (the zero-mean row of the Stokes
-// system holds every pressure column) are queued instead.  Pass 2: one block
-// per queued row, a fixed-order block reduction.  Both passes are
-// deterministic.
+// system holds every pressure column) are queued instead.  When at most
+// kLongSplitRows rows are queued, every one is cut into kLongSlices slices,
+// one block each (pass 2), and the slice sums are added in slice order
+// (pass 3); otherwise every queued row takes one whole block (pass 2').
+// Which path a row takes depends on the number of long rows, not on the
+// queue order, and each path sums in a fixed order: repeated calls give the
+// same bits.
 constexpr int64_t kLongRow = 8192;
-constexpr int kSpmvBlock = 1024;
+constexpr int kLongSplitRows = 64;
+constexpr int kLongSlices = 128;
+constexpr int kSpmvBlock = 256;
 
 __global__ void csr_spmv_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
@@ -211,29 +180,74 @@ __global__ void csr_spmv_kernel(int64_t n_rows, const int64_t* __restrict__ row_
   }
 }
 
+// fixed-order sum of a value per thread over the block (kSpmvBlock threads);
+// the result is valid in thread 0
+__device__ __forceinline__ double block_sum(double s, double* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) part[warp] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < kSpmvBlock / 32 ? part[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+
+// sum of val[p] x[col[p]] over [p0, p1) by the block, four accumulators per
+// thread (memory-level parallelism), fixed order
+__device__ __forceinline__ double block_dot(int64_t p0, int64_t p1, const int32_t* __restrict__ col,
+                                            const double* __restrict__ val, const double* __restrict__ x,
+                                            double* part) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int64_t p = p0 + threadIdx.x;
+  for (; p + 3 * kSpmvBlock < p1; p += 4 * kSpmvBlock) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(val[p + u * kSpmvBlock], x[col[p + u * kSpmvBlock]], acc[u]);
+  }
+  for (int u = 0; p < p1; p += kSpmvBlock, ++u) acc[u] = fma(val[p], x[col[p]], acc[u]);
+  return block_sum((acc[0] + acc[1]) + (acc[2] + acc[3]), part);
+}
+
 __global__ void __launch_bounds__(kSpmvBlock) csr_spmv_long_kernel(const int64_t* __restrict__ row_ptr,
                                                                    const int32_t* __restrict__ col,
                                                                    const double* __restrict__ val,
                                                                    const double* __restrict__ x, double* __restrict__ y,
                                                                    const int32_t* __restrict__ long_rows,
-                                                                   const int32_t* __restrict__ n_long) {
+                                                                   const int32_t* __restrict__ n_long,
+                                                                   double* __restrict__ partial) {
   __shared__ double part[kSpmvBlock / 32];
+  const int cnt = *n_long;
+  if (cnt <= kLongSplitRows) {
+    // block b takes slice b % kLongSlices of queued row b / kLongSlices, ...
+    for (int task = blockIdx.x; task < cnt * kLongSlices; task += gridDim.x) {
+      const int i = task / kLongSlices, sl = task % kLongSlices;
+      const int64_t r = long_rows[i];
+      const int64_t a = row_ptr[r], len = row_ptr[r + 1] - a;
+      const double s = block_dot(a + len * sl / kLongSlices, a + len * (sl + 1) / kLongSlices, col, val, x, part);
+      if (threadIdx.x == 0) partial[task] = s;
+    }
+  } else {
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+      const int64_t r = long_rows[i];
+      const double s = block_dot(row_ptr[r], row_ptr[r + 1], col, val, x, part);
+      if (threadIdx.x == 0) y[r] = s;
+    }
+  }
+}
+
+__global__ void csr_spmv_long_finish_kernel(double* __restrict__ y, const int32_t* __restrict__ long_rows,
+                                            const int32_t* __restrict__ n_long, const double* __restrict__ partial) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cnt = *n_long;
-  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const int64_t r = long_rows[i];
-    const int64_t a = row_ptr[r], e = row_ptr[r + 1];
+  if (cnt > kLongSplitRows) return;
+  for (int i = warp; i < cnt; i += blockDim.x >> 5) {
     double s = 0.0;
-    for (int64_t p = a + threadIdx.x; p < e; p += kSpmvBlock) s = fma(val[p], x[col[p]], s);
+    for (int b = lane; b < kLongSlices; b += 32) s += partial[(int64_t)i * kLongSlices + b];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) part[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-      double t = part[lane];
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) y[r] = t;
-    }
-    __syncthreads();
+    if (lane == 0) y[long_rows[i]] = s;
   }
 }
 
@@ -246,17 +260,12 @@ cudaError_t launch_stokes_rowlen(const Launch& L, const StokesJob& j) {
 }
 
 cudaError_t launch_stokes_fill(const Launch& L, const StokesJob& j) {
-  const size_t per_warp = ((size_t)(j.kcap_v + j.kcap_p) * (sizeof(int32_t) + sizeof(int16_t)) + 15) & ~size_t(15);
-  const size_t smem = per_warp * kStokesWarps;
-  const void* fn = j.dim == 2 ? (const void*)stokes_fill_kernel<2> : (const void*)stokes_fill_kernel<3>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int64_t blocks = (j.n + kStokesWarps - 1) / kStokesWarps;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (j.dim == 2)
-    stokes_fill_kernel<2><<<(unsigned)blocks, kStokesWarps * 32, smem, L.stream>>>(j);
+    stokes_fill_kernel<2><<<(unsigned)blocks, kStokesWarps * 32, 0, L.stream>>>(j);
   else
-    stokes_fill_kernel<3><<<(unsigned)blocks, kStokesWarps * 32, smem, L.stream>>>(j);
+    stokes_fill_kernel<3><<<(unsigned)blocks, kStokesWarps * 32, 0, L.stream>>>(j);
   stokes_last_row_kernel<<<grid_for(j.n, 256), 256, 0, L.stream>>>(j.n * j.dim, j.n, j.row_ptr, j.col, j.val);
   *L.counter += 2;
   return cudaGetLastError();
@@ -269,15 +278,19 @@ cudaError_t launch_stokes_rhs(const Launch& L, const StokesJob& j, const double*
   return cudaGetLastError();
 }
 
+size_t csr_spmv_partial_elems() { return (size_t)kLongSplitRows * kLongSlices; }
+
 cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
-                            const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long) {
+                            const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long,
+                            double* partial) {
   if (n_rows <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(n_long, 0, sizeof(int32_t), L.stream);
   if (e != cudaSuccess) return e;
   csr_spmv_kernel<<<grid_for(n_rows * 32, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y, long_rows,
                                                                        n_long);
-  csr_spmv_long_kernel<<<152, kSpmvBlock, 0, L.stream>>>(row_ptr, col, val, x, y, long_rows, n_long);
-  *L.counter += 2;
+  csr_spmv_long_kernel<<<4 * 152, kSpmvBlock, 0, L.stream>>>(row_ptr, col, val, x, y, long_rows, n_long, partial);
+  csr_spmv_long_finish_kernel<<<1, 512, 0, L.stream>>>(y, long_rows, n_long, partial);
+  *L.counter += 3;
   return cudaGetLastError();
 }
 

@@ -206,8 +206,10 @@ class Context:
         tg = _contig(targets, torch.int32) if targets is not None else None
         hs = _contig(halfspace, torch.float64) if halfspace is not None else None
         kp = _contig(k_per_target, torch.int32) if k_per_target is not None else None
-        p = NbrParams(mode, k, eps_factor, cap if cap is not None else k, 0, _ptr(tg),
-                      0 if tg is None else tg.shape[0], _ptr(hs), _ptr(kp))
+        nt = 0 if tg is None else tg.shape[0]
+        if tg is not None and nt == 0:
+            tg = torch.zeros(1, dtype=torch.int32)  # an empty list still needs a non-NULL pointer
+        p = NbrParams(mode, k, eps_factor, cap if cap is not None else k, 0, _ptr(tg), nt, _ptr(hs), _ptr(kp))
         out = ctypes.c_int64()
         self._check(self.lib.gmls_neighbors(self.h, cloud, ctypes.byref(p), ctypes.byref(out)))
         self._keep[out.value] = (tg, hs, kp)

@@ -11,6 +11,8 @@ lists and stencils.
   oracle pins (h^(m-1) interior, h^(m-2) boundary pressure rows) and the
   Dirichlet rows are exact.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -141,3 +143,29 @@ def test_bad_handles_are_rejected(ctx):
     with pytest.raises(gmls.GmlsError):
         ctx.stokes_size(sp_plain, sv, 1.0)  # roles swapped
     _release(ctx, [cid, nv, sv, sp_plain])
+
+
+@pytest.mark.parametrize("n_extra_long", [20, 70])
+def test_spmv_long_rows(ctx, n_extra_long):
+    """gmls_csr_spmv on rows of very different lengths (1 .. 300,000 entries;
+    rows above 8192 entries are split over blocks when there are at most 64
+    of them, else summed by one block each): the correctly rounded row sums
+    within rounding, and the same bits on a second call."""
+    rng = np.random.default_rng(3)
+    lens = np.concatenate([rng.integers(0, 200, 5000), [9000, 300000, 8193, 20000], rng.integers(1, 50, 3000)])
+    for i in range(n_extra_long):
+        lens = np.append(lens, 10000 + 37 * i)
+    rp = np.zeros(len(lens) + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(lens)
+    ncol = 50000
+    col = rng.integers(0, ncol, int(rp[-1])).astype(np.int32)
+    val = rng.standard_normal(int(rp[-1]))
+    x = rng.standard_normal(ncol)
+    t = [torch.from_numpy(a).cuda() for a in (rp, col, val)]
+    y1 = ctx.spmv(*t, x).cpu().numpy()
+    y2 = ctx.spmv(*t, x).cpu().numpy()
+    assert np.array_equal(y1, y2)
+    prod = val * x[col]
+    ref = np.array([math.fsum(prod[a:b]) for a, b in zip(rp[:-1], rp[1:])])  # correctly rounded sums
+    scale = np.array([np.abs(prod[a:b]).sum() for a, b in zip(rp[:-1], rp[1:])])
+    assert np.all(np.abs(y1 - ref) <= 1e-12 * scale + 1e-300)
