@@ -148,7 +148,7 @@ __global__ void stokes_rhs_kernel(StokesJob j, const double* __restrict__ f, con
   }
 }
 
-// y = A x, FP64.  Pass 1: one warp per row (lanes stride the row, then a
+// y = A x, FP64.  Pass 1: eight lanes per row (they stride the row, then a
 // butterfly); rows longer than kLongRow (the zero-mean row of the Stokes
 // system holds every pressure column) are queued instead.  When at most
 // kLongSplitRows rows are queued, every one is cut into kLongSlices slices,
@@ -162,21 +162,36 @@ constexpr int kLongSplitRows = 64;
 constexpr int kLongSlices = 128;
 constexpr int kSpmvBlock = 256;
 
+// Eight lanes per row: on rows of a few dozen to a few hundred entries the
+// FP64 adds of the final reduction (three levels, shared by four rows per
+// warp instruction) stay small next to the one FMA per entry -- FP64 runs at
+// 1/64 of the FP32 rate on this GPU.
+constexpr int kRowLanes = 8;
+
 __global__ void csr_spmv_kernel(int64_t n_rows, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
                                 int32_t* __restrict__ long_rows, int32_t* __restrict__ n_long) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n_rows;
-       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t a = row_ptr[r], e = row_ptr[r + 1];
-    if (e - a > kLongRow) {
-      if (lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)r;
-      continue;
-    }
+  const int sub = threadIdx.x & (kRowLanes - 1);
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / kRowLanes;
+  // every lane of the warp runs the same number of iterations (the shuffles
+  // below need the whole warp)
+  const int64_t r0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kRowLanes;
+  const int64_t warp_first = r0 - ((threadIdx.x & 31) / kRowLanes);
+  for (int64_t base = warp_first; base < n_rows; base += stride) {
+    const int64_t r = base + ((threadIdx.x & 31) / kRowLanes);
     double s = 0.0;
-    for (int64_t p = a + lane; p < e; p += 32) s = fma(val[p], x[col[p]], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) y[r] = s;
+    bool store = false;
+    if (r < n_rows) {
+      const int64_t a = row_ptr[r], e = row_ptr[r + 1];
+      if (e - a > kLongRow) {
+        if (sub == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)r;
+      } else {
+        for (int64_t p = a + sub; p < e; p += kRowLanes) s = fma(val[p], x[col[p]], s);
+        store = true;
+      }
+    }
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, kRowLanes);
+    if (store && sub == 0) y[r] = s;
   }
 }
 
@@ -286,8 +301,8 @@ cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_
   if (n_rows <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(n_long, 0, sizeof(int32_t), L.stream);
   if (e != cudaSuccess) return e;
-  csr_spmv_kernel<<<grid_for(n_rows * 32, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y, long_rows,
-                                                                       n_long);
+  csr_spmv_kernel<<<grid_for(n_rows * kRowLanes, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y,
+                                                                              long_rows, n_long);
   csr_spmv_long_kernel<<<4 * 152, kSpmvBlock, 0, L.stream>>>(row_ptr, col, val, x, y, long_rows, n_long, partial);
   csr_spmv_long_finish_kernel<<<1, 512, 0, L.stream>>>(y, long_rows, n_long, partial);
   *L.counter += 3;
