@@ -427,3 +427,12 @@ def staggered_stencils(x, targets, nbr_off, nbr_idx, eps, m, functional, wpow=4.
         w[:, self_pos[0]] = -np.sum(w, axis=1)
         out.append(w[:, :, None])
     return np.stack(out), np.asarray(ranks)
+
+
+def stokes_solve(A, b):
+    """Solution of the collocation system (Sec. 3.2) by a sparse direct
+    factorisation (SuperLU through scipy): the reference for the GPU's
+    iterative solve."""
+    import scipy.sparse.linalg as spla
+
+    return spla.spsolve(A.tocsc(), b)

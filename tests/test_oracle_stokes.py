@@ -131,3 +131,41 @@ def test_structure():
         assert np.all(np.diff(cols) > 0)
     last = col[rp[nd + n]:rp[nd + n + 1]]
     assert np.array_equal(last, nd + np.arange(n))
+
+
+def _solve_errors(x, n, A, bflag, nrm, beta, u, p, f, w, div_f):
+    b = oracle.stokes_rhs(2, n, bflag, nrm, f, w, div_f, beta)
+    sol = oracle.stokes_solve(A, b)
+    us = sol[:2 * n].reshape(n, 2).T
+    ps = sol[2 * n:3 * n]
+    eu = np.sqrt(np.mean((us - u) ** 2))
+    # the pressure is fixed up to a constant (the multiplier row sets its
+    # discrete mean): compare mean-free parts
+    ep = np.sqrt(np.mean(((ps - ps.mean()) - (p - p.mean())) ** 2))
+    return eu, ep, sol[-1]
+
+
+@pytest.mark.parametrize("nu", [1.0, 0.37])
+def test_polynomial_solution_is_recovered(nu):
+    """The analogue of the paper's polynomial tables (Sec. 4.1): a velocity
+    and pressure inside the bases are recovered by the solve up to rounding."""
+    x, n, bflag, nrm, A, beta = _system(18, nu)
+    u, p, f, div_f = _polynomial_fields(x, nu)
+    eu, ep, lam = _solve_errors(x, n, A, bflag, nrm, beta, u, p, f, u, div_f)
+    assert eu < 1e-9 * np.abs(u).max() and ep < 1e-8 * np.abs(p).max(), (eu, ep)
+
+
+def test_trigonometric_solution_converges():
+    """Manufactured trigonometric field (Sec. 4.2 in 2D): the RMS error of the
+    solved velocity and pressure decays at about the order of the basis."""
+    hs, eus, eps_ = [], [], []
+    for na in (16, 24, 32):
+        x, n, bflag, nrm, A, beta = _system(na, 1.0)
+        d = inputs.stokes_manufactured_2d(x, 1.0)
+        eu, ep, _ = _solve_errors(x, n, A, bflag, nrm, beta, d["u"], d["p"], d["f"], d["w"], d["div_f"])
+        hs.append(1.0 / na)
+        eus.append(eu)
+        eps_.append(ep)
+    ru = np.polyfit(np.log(hs), np.log(eus), 1)[0]
+    rp = np.polyfit(np.log(hs), np.log(eps_), 1)[0]
+    assert ru > M - 1 and rp > M - 1, (ru, rp, eus, eps_)
