@@ -21,6 +21,7 @@
  *   gmls_stokes_*      the block collocation system of Sec. 3.2 from velocity
  *                      and pressure stencils, its right-hand side, and a CSR
  *                      matrix-vector product to apply it
+ *   gmls_gmres         its global solve (Sec. 3.3) by restarted GMRES
  *
  * Conventions
  *   - Every function returns a gmls_status; 0 is success, negative values are
@@ -277,6 +278,29 @@ gmls_status gmls_stokes_rhs(gmls_ctx* ctx, const gmls_stokes_params* params, con
  */
 gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                           const double* val, const double* x, double* y);
+
+/*
+ * Solve A x = b (square CSR, n rows; FP64) by restarted GMRES(restart) with
+ * right Jacobi preconditioning (diag A; 1 where it is zero or absent) -- the
+ * global solve of the collocation system of Sec. 3.2 (the paper uses a
+ * block-preconditioned Krylov method).  x: device buffer holding the initial
+ * guess on entry and the solution on return.  Synchronous: returns after
+ * ||b - A x|| <= rtol ||b|| (true residual, recomputed at every restart) or
+ * max_iter iterations; *iters and *rel_residual report them (a solve that
+ * stops at max_iter still returns GMLS_OK: check *rel_residual).  Scratch
+ * ((restart + 1) n doubles and a few vectors) comes from the arena
+ * (GMLS_ENOMEM if it does not fit); GMLS_EBUSY during stream capture.  Every
+ * reduction has a fixed order: repeated solves give the same bits.
+ */
+typedef struct {
+  int32_t restart;  /* Krylov basis size, 1..256 */
+  int32_t max_iter; /* iterations over all restarts, >= 0 */
+  double rtol;      /* relative residual target, > 0 */
+} gmls_gmres_params;
+
+gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                       const double* b, double* x, const gmls_gmres_params* params, int32_t* iters,
+                       double* rel_residual);
 
 /*
  * Copy one array of a handle to dst (host or device), `bytes` = capacity of

@@ -2,6 +2,7 @@
 // arena allocator, handles, argument checking and launch orchestration.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1335,6 +1336,126 @@ gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr,
   ctx->arena.release(n_long);
   ctx->arena.release(partial);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_csr_spmv");
+  return GMLS_OK;
+}
+
+// ------------------------------------------------------------------- GMRES
+// Restarted GMRES(m) with right Jacobi preconditioning, A D^-1 y = b,
+// x = D^-1 y (D = diag A, 1 where that is zero).  Arnoldi with classical
+// Gram-Schmidt applied twice; the Hessenberg column and the new norm come to
+// the host once per iteration, where Givens rotations update the residual
+// estimate.  The true residual is recomputed at every restart and at the end.
+gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                       const double* b, double* x, const gmls_gmres_params* p, int32_t* iters, double* rel_residual) {
+  if (!ctx) return GMLS_EINVAL;
+  if (!p || n < 1 || !row_ptr || !col || !val || !b || !x || p->restart < 1 || p->restart > 256 || p->max_iter < 0 ||
+      !(p->rtol > 0.0))
+    return fail(ctx, GMLS_EINVAL, "gmls_gmres: bad argument (restart 1..256, max_iter >= 0, rtol > 0)");
+  if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val) || is_host_ptr(b) || is_host_ptr(x))
+    return fail(ctx, GMLS_EINVAL, "gmls_gmres: arrays must be device buffers");
+  if (capturing(ctx)) return fail(ctx, GMLS_EBUSY, "gmls_gmres reads the device every iteration: not during capture");
+  CK(cudaSetDevice(ctx->device), "gmls_gmres");
+  const int m = p->restart;
+  double* V = arena_alloc<double>(ctx, (size_t)(m + 1) * n);
+  double* z = arena_alloc<double>(ctx, n);
+  double* dinv = arena_alloc<double>(ctx, n);
+  double* part = arena_alloc<double>(ctx, krylov_partial_elems(m + 2));
+  double* hdev = arena_alloc<double>(ctx, 2 * (m + 2));
+  int32_t* long_rows = arena_alloc<int32_t>(ctx, n);
+  int32_t* n_long = arena_alloc<int32_t>(ctx, 1);
+  double* sp_part = arena_alloc<double>(ctx, csr_spmv_partial_elems());
+  void* all[] = {V, z, dinv, part, hdev, long_rows, n_long, sp_part};
+  auto release = [&]() {
+    for (void* q : all) ctx->arena.release(q);
+  };
+  for (void* q : all)
+    if (!q) {
+      release();
+      return fail(ctx, GMLS_ENOMEM, "gmls_gmres: arena exhausted (the basis needs (restart + 1) n doubles)");
+    }
+  Launch L = ctx->launch();
+  cudaError_t e = cudaSuccess;
+  auto spmv = [&](const double* in, double* out) {
+    if (e == cudaSuccess) e = launch_csr_spmv(L, n, row_ptr, col, val, in, out, long_rows, n_long, sp_part);
+  };
+  auto dot_host = [&](const double* a, const double* c, double* out_host) {
+    if (e == cudaSuccess) e = krylov_dots(L, n, 1, a, c, part, hdev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, hdev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  };
+  if (e == cudaSuccess) e = krylov_inverse_diagonal(L, n, row_ptr, col, val, dinv);
+  double bb = 0.0;
+  dot_host(b, b, &bb);
+  const double bnorm = std::sqrt(bb);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), hc(2 * (m + 2), 0.0);
+  int total = 0;
+  double rel = 0.0;
+  while (e == cudaSuccess) {
+    // r = b - A x into V_0
+    spmv(x, V);
+    if (e == cudaSuccess) e = krylov_residual(L, n, b, V);
+    double rr = 0.0;
+    dot_host(V, V, &rr);
+    const double beta = std::sqrt(rr);
+    rel = bnorm > 0.0 ? beta / bnorm : beta;
+    if (e != cudaSuccess || rel <= p->rtol || total >= p->max_iter || !(beta > 0.0)) break;
+    if (e == cudaSuccess) e = krylov_scaled_copy(L, n, V, 1.0 / beta, V);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m && total < p->max_iter && e == cudaSuccess; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* w = V + (size_t)(j + 1) * n;
+      if (e == cudaSuccess) e = krylov_scale(L, n, dinv, vj, z);
+      spmv(z, w);
+      // CGS2: h = V^T w, w -= V h, twice; then |w|
+      if (e == cudaSuccess) e = krylov_dots(L, n, j + 1, V, w, part, hdev);
+      if (e == cudaSuccess) e = krylov_axpy(L, n, j + 1, V, hdev, w);
+      if (e == cudaSuccess) e = krylov_dots(L, n, j + 1, V, w, part, hdev + (m + 2));
+      if (e == cudaSuccess) e = krylov_axpy(L, n, j + 1, V, hdev + (m + 2), w);
+      if (e == cudaSuccess) e = krylov_dots(L, n, 1, w, w, part, hdev + (m + 2) + (j + 1));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hc.data(), hdev, sizeof(double) * 2 * (m + 2), cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) break;
+      std::vector<double> h(j + 2);
+      for (int i = 0; i <= j; ++i) h[i] = hc[i] + hc[(m + 2) + i];
+      const double hn = std::sqrt(std::max(hc[(m + 2) + (j + 1)], 0.0));
+      h[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {  // previous rotations
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+      }
+      const double r = std::hypot(h[j], h[j + 1]);
+      cs[j] = r > 0.0 ? h[j] / r : 1.0;
+      sn[j] = r > 0.0 ? h[j + 1] / r : 0.0;
+      h[j] = r;
+      h[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+      ++total;
+      jdone = j + 1;
+      if (hn > 0.0 && e == cudaSuccess) e = krylov_scaled_copy(L, n, w, 1.0 / hn, w);
+      if (std::fabs(g[j + 1]) <= p->rtol * bnorm || !(hn > 0.0)) break;
+    }
+    if (e != cudaSuccess || jdone == 0) break;
+    // y = H^-1 g (upper triangular), x += D^-1 V y
+    std::vector<double> y(jdone);
+    for (int i = jdone - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int c = i + 1; c < jdone; ++c) s -= H[(size_t)i * m + c] * y[c];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hdev, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = krylov_update(L, n, jdone, V, hdev, dinv, x);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // y (host) stays valid until the copy ran
+  }
+  release();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gmls_gmres");
+  if (iters) *iters = total;
+  if (rel_residual) *rel_residual = rel;
   return GMLS_OK;
 }
 

@@ -278,4 +278,19 @@ cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_
                             const double* val, const double* x, double* y, int32_t* long_rows, int32_t* n_long,
                             double* partial);
 
+// ------------------------------------------------------------- GMRES pieces
+// (krylov.cu) V holds basis vectors [i][n]; partial has
+// krylov_partial_elems(ncols) doubles; every reduction has a fixed order
+size_t krylov_partial_elems(int max_cols);
+cudaError_t krylov_dots(const Launch& L, int64_t n, int ncols, const double* V, const double* w, double* partial,
+                        double* out);
+cudaError_t krylov_axpy(const Launch& L, int64_t n, int ncols, const double* V, const double* h, double* w);
+cudaError_t krylov_update(const Launch& L, int64_t n, int ncols, const double* V, const double* y, const double* dinv,
+                          double* x);
+cudaError_t krylov_scale(const Launch& L, int64_t n, const double* dinv, const double* v, double* z);
+cudaError_t krylov_scaled_copy(const Launch& L, int64_t n, const double* src, double s, double* dst);
+cudaError_t krylov_residual(const Launch& L, int64_t n, const double* b, double* r);
+cudaError_t krylov_inverse_diagonal(const Launch& L, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                    const double* val, double* dinv);
+
 }  // namespace gmls

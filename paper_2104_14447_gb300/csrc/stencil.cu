@@ -746,9 +746,71 @@ cudaError_t launch_bucketing(const Launch& L, const BucketJob& b) {
 // ------------------------------------------------------------------------ CSR
 // Id order of the neighbour lists, computed once per list handle: order[o + r]
 // is the position within target t's list (offset o) of its entry of rank r by
-// particle id.  Warp per target: bitonic sort of (id, position) pairs in
-// shared memory sized from the longest list (kcap entries per warp).
+// particle id (equal ids -- the -1 padding of short lists -- by position).
+// Warp per target: bitonic sort of (id, position) keys, in registers for
+// lists of up to 128 entries, else in shared memory sized from the longest
+// list (kcap entries per warp).
 constexpr int kOrderWarps = 8;
+
+// Bitonic sort of 32 R keys held R per lane (element lane + 32 u in key[u]),
+// ascending: compare-exchanges across lanes by shuffles, within a lane for
+// strides of 32 and more.  Every size and stride is a compile-time constant.
+template <int R>
+__device__ __forceinline__ void warp_bitonic_keys(unsigned long long (&key)[R], int lane) {
+  constexpr int NE = 32 * R;
+#pragma unroll
+  for (int size = 2; size <= NE; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 32) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const int pu = u ^ (stride >> 5);
+          if (pu > u) {  // element lane + 32 u is the lower one of the pair
+            const bool asc = ((lane + 32 * u) & size) == 0;
+            const unsigned long long a = key[u], b = key[pu];
+            const bool swap = asc ? (b < a) : (a < b);
+            key[u] = swap ? b : a;
+            key[pu] = swap ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+          const unsigned long long other = __shfl_xor_sync(0xffffffffu, key[u], stride);
+          const bool lower = (lane & stride) == 0;
+          const bool asc = ((lane + 32 * u) & size) == 0;
+          const unsigned long long lo = other < key[u] ? other : key[u];
+          const unsigned long long hi = other < key[u] ? key[u] : other;
+          key[u] = (lower == asc) ? lo : hi;
+        }
+      }
+    }
+  }
+}
+
+// key of a list entry: the id with its sign bit flipped (unsigned order =
+// signed order) above the position, so equal ids keep their list order
+__device__ __forceinline__ unsigned long long order_key(int32_t id, int pos) {
+  return ((unsigned long long)((uint32_t)id ^ 0x80000000u) << 32) | (uint32_t)pos;
+}
+
+template <int R>
+__device__ __forceinline__ void order_in_registers(const int32_t* __restrict__ idx, int64_t o, int k, int lane,
+                                                   int16_t* __restrict__ order) {
+  unsigned long long key[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int e = lane + 32 * u;
+    key[u] = (e < k) ? order_key(idx[o + e], e) : ~0ull;
+  }
+  warp_bitonic_keys<R>(key, lane);
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int e = lane + 32 * u;
+    if (e < k) order[o + e] = (int16_t)(key[u] & 0xffffffffu);
+  }
+}
 
 __global__ void __launch_bounds__(kOrderWarps * 32) nbr_order_kernel(int64_t n_tgt, const int64_t* __restrict__ off,
                                                                      const int32_t* __restrict__ idx, int kcap,
@@ -761,6 +823,14 @@ __global__ void __launch_bounds__(kOrderWarps * 32) nbr_order_kernel(int64_t n_t
   for (int64_t t = (int64_t)blockIdx.x * kOrderWarps + w; t < n_tgt; t += (int64_t)gridDim.x * kOrderWarps) {
     const int64_t o = off[t];
     const int k = (int)(off[t + 1] - o);
+    if (k <= 64) {  // short lists: keys in registers, no shared memory
+      order_in_registers<2>(idx, o, k, lane, order);
+      continue;
+    }
+    if (k <= 128) {
+      order_in_registers<4>(idx, o, k, lane, order);
+      continue;
+    }
     int n2 = 1;
     while (n2 < k) n2 <<= 1;
     for (int i = lane; i < n2; i += 32) {

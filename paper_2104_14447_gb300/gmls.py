@@ -42,7 +42,7 @@ EXPORTED = [
     "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
     "gmls_server_create", "gmls_server_submit", "gmls_server_wait", "gmls_server_result", "gmls_server_release",
     "gmls_server_stats", "gmls_server_destroy", "gmls_stokes_size", "gmls_stokes_assemble", "gmls_stokes_rhs",
-    "gmls_csr_spmv",
+    "gmls_csr_spmv", "gmls_gmres",
 ]
 NOALLOC_MAX_POINTS = 262144
 OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT = 0, 1, 2, 3
@@ -76,6 +76,10 @@ class Request(ctypes.Structure):
 
 class StokesParams(ctypes.Structure):
     _fields_ = [("velocity", ctypes.c_int64), ("pressure", ctypes.c_int64), ("nu", ctypes.c_double)]
+
+
+class GmresParams(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -131,6 +135,8 @@ def load(path: str = LIB_PATH):
         "gmls_stokes_assemble": [vp, ctypes.POINTER(StokesParams), vp, vp, vp],
         "gmls_stokes_rhs": [vp, ctypes.POINTER(StokesParams), vp, vp, vp, vp],
         "gmls_csr_spmv": [vp, i64, vp, vp, vp, vp, vp],
+        "gmls_gmres": [vp, i64, vp, vp, vp, vp, vp, ctypes.POINTER(GmresParams), ctypes.POINTER(i32),
+                       ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -309,6 +315,18 @@ class Context:
         for a in (row_ptr, col, val, x, y):
             a.record_stream(self.stream)
         return y
+
+    def gmres(self, row_ptr, col, val, b, x0=None, restart: int = 60, max_iter: int = 5000, rtol: float = 1e-10):
+        """Solve A x = b (gmls_gmres); returns (x, iterations, relative residual)."""
+        b = _contig(b, torch.float64).to(self.device)
+        n = row_ptr.shape[0] - 1
+        x = (torch.zeros(n, dtype=torch.float64, device=self.device) if x0 is None
+             else _contig(x0, torch.float64).to(self.device).clone())
+        p = GmresParams(restart, max_iter, rtol)
+        it, rel = ctypes.c_int32(), ctypes.c_double()
+        self._check(self.lib.gmls_gmres(self.h, n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
+                                        ctypes.byref(p), ctypes.byref(it), ctypes.byref(rel)))
+        return x, it.value, rel.value
 
     def release(self, hid: int):
         self._check(self.lib.gmls_release(self.h, hid))

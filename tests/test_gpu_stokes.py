@@ -169,3 +169,58 @@ def test_spmv_long_rows(ctx, n_extra_long):
     ref = np.array([math.fsum(prod[a:b]) for a, b in zip(rp[:-1], rp[1:])])  # correctly rounded sums
     scale = np.array([np.abs(prod[a:b]).sum() for a, b in zip(rp[:-1], rp[1:])])
     assert np.all(np.abs(y1 - ref) <= 1e-12 * scale + 1e-300)
+
+
+def _solve_errors(x, n, sol, u, p):
+    us = sol[:2 * n].reshape(n, 2).T
+    ps = sol[2 * n:3 * n]
+    eu = np.sqrt(np.mean((us - u) ** 2))
+    ep = np.sqrt(np.mean(((ps - ps.mean()) - (p - p.mean())) ** 2))
+    return eu, ep
+
+
+def test_gmres_solution_matches_direct_solve(ctx):
+    """The GPU solve (gmls_gmres on the GPU system) against the oracle's
+    direct solve of the oracle's system, 32 x 32, FP64 stencils."""
+    nu = 1.0
+    x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, 32, gmls.FP64, nu)
+    n = x.shape[1]
+    A, beta = _oracle(x, bflag, nrm, nu)
+    d = inputs.stokes_manufactured_2d(x, nu)
+    b_orc = oracle.stokes_rhs(2, n, bflag, nrm, d["f"], d["w"], d["div_f"], beta)
+    sol_orc = oracle.stokes_solve(A, b_orc)
+    b = ctx.stokes_rhs(ids[3], ids[4], nu, d["f"], d["w"], d["div_f"])
+    sol, its, rel = ctx.gmres(rp, col, val, b, restart=60, max_iter=4000, rtol=1e-12)
+    sol = sol.cpu().numpy()
+    assert rel <= 1e-12 and its > 0
+    # the two systems agree to 1e-10 (stencils); the solution to the
+    # system's conditioning times that
+    assert np.max(np.abs(sol - sol_orc)) <= 1e-6 * np.abs(sol_orc).max()
+    eu, ep = _solve_errors(x, n, sol, d["u"], d["p"])
+    eu_o, ep_o = _solve_errors(x, n, sol_orc, d["u"], d["p"])
+    assert abs(eu - eu_o) <= 1e-3 * eu_o and abs(ep - ep_o) <= 1e-3 * ep_o
+    # reproducible bits
+    sol2, its2, _ = ctx.gmres(rp, col, val, b, restart=60, max_iter=4000, rtol=1e-12)
+    assert its2 == its and np.array_equal(sol2.cpu().numpy(), sol)
+    _release(ctx, ids)
+
+
+def test_gmres_solution_converges_at_scale(ctx):
+    """Solved trigonometric field at 32^2 .. 128^2 (FP32 + refinement
+    stencils): RMS errors decay at about the order of the basis."""
+    hs, eus, eps_ = [], [], []
+    for na in (32, 64, 128):
+        x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, na, gmls.FP32_REFINE, 1.0)
+        n = x.shape[1]
+        d = inputs.stokes_manufactured_2d(x, 1.0)
+        b = ctx.stokes_rhs(ids[3], ids[4], 1.0, d["f"], d["w"], d["div_f"])
+        sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=1e-11)
+        assert rel <= 1e-11, (na, its, rel)
+        eu, ep = _solve_errors(x, n, sol.cpu().numpy(), d["u"], d["p"])
+        hs.append(1.0 / na)
+        eus.append(eu)
+        eps_.append(ep)
+        _release(ctx, ids)
+    ru = np.polyfit(np.log(hs), np.log(eus), 1)[0]
+    rp_ = np.polyfit(np.log(hs), np.log(eps_), 1)[0]
+    assert ru > M - 1 and rp_ > M - 1, (ru, rp_, eus, eps_)
