@@ -456,6 +456,43 @@ def stokes_system(ctx, steps=5):
             "l2": "flushed before each timed step (256 MB write)"}
 
 
+def stokes_solve(ctx, n_axis=128):
+    """Global solve of the Stokes system (Sec. 3.3) on an n_axis^2 grid by
+    GMRES(100) with right Jacobi preconditioning (gmls_gmres), to a relative
+    residual of 1e-10; RMS errors of the solved velocity and (mean-free)
+    pressure against the manufactured field."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    x = inputs.jittered_grid(2, n_axis, seed=0)
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(2, n_axis)
+    d = inputs.stokes_manufactured_2d(x, 1.0)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
+    npr = ctx.neighbors_prefix(nv, K_SCALAR, EPS_FACTOR)
+    sv = ctx.stencils(nv, gmls.DIVFREE, DEGREE, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+    sp = ctx.stencils(npr, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE,
+                      neumann=True)
+    rp, col, val = ctx.stokes_assemble(sv, sp, 1.0)
+    b = ctx.stokes_rhs(sv, sp, 1.0, d["f"], d["w"], d["div_f"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=1e-10)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    s = sol.cpu().numpy()
+    us, ps = s[:2 * n].reshape(n, 2).T, s[2 * n:3 * n]
+    eu = float(np.sqrt(np.mean((us - d["u"]) ** 2)))
+    ep = float(np.sqrt(np.mean(((ps - ps.mean()) - (d["p"] - d["p"].mean())) ** 2)))
+    for hd in (sp, sv, npr, nv, cid):
+        ctx.release(hd)
+    return {"grid": f"{n_axis}x{n_axis}", "unknowns": int(rp.shape[0] - 1), "solver": "GMRES(100), right Jacobi",
+            "iterations": its, "rel_residual": rel, "seconds": el, "rms_error_velocity": eu,
+            "rms_error_pressure": ep}
+
+
 def serving(n_requests, seed=0):
     """Poisson arrivals (200 req/s) of stencil requests -- 2D/3D clouds of
     log-uniform 1e3..5e5 points, degree 2..4, scalar (gradient + Laplacian) or
@@ -669,6 +706,7 @@ def main():
         out["cpu_baseline"] = cpu_baseline(ctx)
     if rank == 0 and world == 1 and not args.no_stokes:
         out["stokes_system"] = stokes_system(ctx)
+        out["stokes_system"]["solve"] = stokes_solve(ctx)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving(args.serve_requests)
     if rank == 0:
