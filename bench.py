@@ -340,7 +340,9 @@ def run_ours(args, rank, world, local_rank):
     tune = {}
     for r in ctx.tune_log():
         key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m={r['degree']} rows<={r['rows']}"
-        name = {-1: "register", -2: "register 16 lanes"}.get(r["variant"], f"{r['variant']} warp(s)/target")
+        v = r["variant"]
+        place = {0: "", 1: ", split tiles", 2: ", global tiles"}[v >> 3] if v > 0 else ""
+        name = {-1: "register", -2: "register 16 lanes"}.get(v, f"{v & 7} warp(s)/target{place}")
         tune.setdefault(key, {})[name] = round(r["ms"], 3)
 
     value = shard.job_throughput(n, args.steps, world, total_ms)

@@ -330,16 +330,21 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
                                     warp-per-target register kernel (testing and tuning)    */
 #define GMLS_OPT_AUTOTUNE 1      /* 1 (default): the first gmls_stencils call for a shape times
                                     the kernel variants (register kernel with a warp or a half
-                                    warp per target; 1, 2 or 4 warps per target) on up to 8192
-                                    targets and caches the fastest; this call waits for the
-                                    stream.  0: heuristic choice                              */
+                                    warp per target; 1, 2 or 4 warps per target, and for tiles
+                                    that leave one block per SM the split and global tile
+                                    placements) on up to 8192 targets and caches the fastest;
+                                    this call waits for the stream.  0: heuristic choice      */
 #define GMLS_OPT_CLEAR_TUNING 2  /* any value: forget the cached choices and timings         */
 #define GMLS_OPT_FORCE_VARIANT 3 /* testing: the kernel variant for shapes with uniform
                                     neighbour counts and degree: -1 / -2 register kernel
-                                    with 32 / 16 lanes per target, 1, 2 or 4 warps per target
-                                    of the shared-memory kernel, 0 (default) no forcing.
-                                    gmls_stencils fails with GMLS_EINVAL where the variant
-                                    does not exist for the shape                             */
+                                    with 32 / 16 lanes per target; G + 8 * P for the
+                                    shared-memory kernel with G = 1, 2 or 4 warps per target
+                                    and tile placement P (0: both tiles in shared memory;
+                                    1, FP32 path only: the FP32 tile in shared memory, its
+                                    float-float copy in global memory; 2: both tiles in
+                                    global memory); 0 (default) no forcing.  gmls_stencils
+                                    fails with GMLS_EINVAL where the variant does not exist
+                                    or does not fit for the shape                            */
 
 /* Set a context option (GMLS_OPT_*); applies to later calls. */
 gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
@@ -374,7 +379,8 @@ gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, int32_t k, d
  * Autotuner record `index` (0-based, in the order taken): fields[9] =
  * {basis, dim, degree, precision, tile rows, solve rows, neumann, bucketed,
  * variant (-1 register kernel with 32 lanes per target, -2 with 16 lanes per
- * target, else warps per target of the shared-memory kernel)}, *ms its time.
+ * target, else G + 8 * P for the shared-memory kernel as in
+ * GMLS_OPT_FORCE_VARIANT)}, *ms its time.
  * GMLS_ENOTFOUND past the last record.
  */
 gmls_status gmls_tune_info(gmls_ctx* ctx, int32_t index, int32_t* fields, float* ms);

@@ -220,18 +220,43 @@ static bool is_host_ptr(const void* p) {
 
 
 // ------------------------------------------------------------- launch planning
-// heuristic warps per target for a tile of ld rows: a warp up to 64 rows, two
-// up to 192, four beyond; more when the tile would not fit.
-static int heuristic_g(int ld, int nmax, bool fp32) {
-  int g = ld <= 64 ? 1 : (ld <= 192 ? 2 : 4);
-  while (g < 4 && (size_t)(4 / g) * tile_bytes(ld, nmax, fp32) > 110 * 1024) g *= 2;
-  if ((size_t)(4 / g) * tile_bytes(ld, nmax, fp32) <= 227 * 1024) return g;
-  // tiles in global memory (one L2-resident slot per target in flight)
-  return tile_bytes(ld, nmax, fp32, true) <= 227 * 1024 ? 4 : 0;
+// Variant code of the shared-memory kernel: warps per target G (1, 2 or 4)
+// plus 8 x the tile placement (kPlaceShared / kPlaceSplit / kPlaceGlobal).
+static int vcode(int G, int place) { return G + 8 * place; }
+static int v_warps(int v) { return v & 7; }
+static int v_place(int v) { return v >> 3; }
+
+static bool variant_fits(int v, int ld, int nmax, bool fp32) {
+  const int G = v_warps(v), place = v_place(v);
+  if (!(G == 1 || G == 2 || G == 4) || place < kPlaceShared || place > kPlaceGlobal) return false;
+  if (place == kPlaceSplit && !fp32) return false;  // the FP64 path has no second tile
+  return (size_t)(4 / G) * tile_bytes(ld, nmax, fp32, place) <= 227 * 1024;
 }
 
-static bool needs_gtile(int G, int ld, int nmax, bool fp32) {
-  return (size_t)(4 / G) * tile_bytes(ld, nmax, fp32) > 227 * 1024;
+// Heuristic variant for a tile of ld rows: a warp per target up to 64 rows,
+// two up to 192, four beyond; more when the tiles would not fit twice in
+// shared memory.  Tiles too big for shared memory move their float-float copy
+// (FP32 path), else both tiles, to an L2-resident global slot.
+static int heuristic_variant(int ld, int nmax, bool fp32) {
+  int g = ld <= 64 ? 1 : (ld <= 192 ? 2 : 4);
+  while (g < 4 && (size_t)(4 / g) * tile_bytes(ld, nmax, fp32) > 110 * 1024) g *= 2;
+  if (variant_fits(vcode(g, kPlaceShared), ld, nmax, fp32)) return vcode(g, kPlaceShared);
+  if (variant_fits(vcode(4, kPlaceSplit), ld, nmax, fp32)) return vcode(4, kPlaceSplit);
+  return variant_fits(vcode(4, kPlaceGlobal), ld, nmax, fp32) ? vcode(4, kPlaceGlobal) : 0;
+}
+
+// Autotuner candidates of the shared-memory kernel: 1, 2 or 4 warps per
+// target with the tiles in shared memory, and, where that leaves at most one
+// block per SM, the split and global placements too.
+static std::vector<int> generic_candidates(int ld, int nmax, bool fp32) {
+  std::vector<int> c;
+  for (int G = 1; G <= 4; G *= 2) {
+    if (variant_fits(vcode(G, kPlaceShared), ld, nmax, fp32)) c.push_back(vcode(G, kPlaceShared));
+    if ((size_t)(4 / G) * tile_bytes(ld, nmax, fp32) <= 110 * 1024) continue;
+    for (int place : {kPlaceSplit, kPlaceGlobal})
+      if (variant_fits(vcode(G, place), ld, nmax, fp32)) c.push_back(vcode(G, place));
+  }
+  return c;
 }
 
 static size_t plan_smem(const BatchPlan& pl, bool fp32) {
@@ -241,16 +266,17 @@ static size_t plan_smem(const BatchPlan& pl, bool fp32) {
   return m;
 }
 
-// global tile slots for the buckets that need them: [blocks][groups][slot]
+// global tile slots for the buckets whose placement needs them:
+// [blocks][groups][slot]
 static bool plan_gscratch(gmls_ctx* ctx, BatchPlan& pl, bool fp32, int grid, void** owned) {
   size_t slot = 0;
   int groups = 1;
   for (int b = 0; b < (pl.single ? 1 : pl.nb); ++b) {
-    pl.gtile[b] = pl.G[b] > 0 && needs_gtile(pl.G[b], pl.ld[b], pl.nmax[b], fp32);
-    if (pl.gtile[b]) {
-      slot = std::max(slot, global_tile_bytes(pl.ld[b], pl.nmax[b], fp32));
-      groups = std::max(groups, 4 / pl.G[b]);
-    }
+    if (pl.G[b] <= 0 || pl.gtile[b] == kPlaceShared) continue;
+    const size_t gb = global_tile_bytes(pl.ld[b], pl.nmax[b], fp32, pl.gtile[b]);
+    if (!gb) continue;
+    slot = std::max(slot, gb);
+    groups = std::max(groups, 4 / pl.G[b]);
   }
   *owned = nullptr;
   pl.gscratch = nullptr;
@@ -289,17 +315,17 @@ static float time_launch(gmls_ctx* ctx, F&& launch) {
   return ms;
 }
 
-static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int G, int ld, int nmax, bool fp32,
+static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int variant, int ld, int nmax, bool fp32,
                                  int32_t* counter, int sms) {
   BatchPlan pl;
   std::memset(&pl, 0, sizeof(pl));
   pl.single = 1;
   pl.nb = 1;
-  pl.G[0] = G;
+  pl.G[0] = v_warps(variant);
   pl.ld[0] = ld;
   pl.nmax[0] = nmax;
   pl.task_counter = counter;
-  pl.gtile[0] = needs_gtile(G, ld, nmax, fp32);
+  pl.gtile[0] = v_place(variant);
   const size_t smem = plan_smem(pl, fp32);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
   if (e != cudaSuccess) return e;
@@ -315,8 +341,9 @@ static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int G, int 
 // Uniform neighbour counts and degree: one shape.  Candidates: the register
 // kernel with a warp (variant -1) or a half warp (variant -2) per target, when
 // this shape is instantiated, and the shared-memory kernel with 1, 2 or 4
-// warps per target; the autotuner times each once on up to 8192 targets and
-// the choice is cached per shape.
+// warps per target and its tile placements (generic_candidates); the
+// autotuner times each once on up to 8192 targets and the choice is cached
+// per shape.
 static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls_stencil_params* p, bool refine,
                                   int ld, int nmax, int sms, int32_t* counter) {
   const int dim = j.dim;
@@ -330,19 +357,15 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
                          : launch_stencils_fast(ctx->launch(), jj, mr32, 32, sms);
   };
   const TuneKey key{p->basis, dim, p->degree, p->precision, ld, j.L, p->neumann, 0};
-  int choice = 0;  // -1 / -2 register kernel (32 / 16 lanes per target), else G
+  int choice = 0;  // -1 / -2 register kernel (32 / 16 lanes per target), else a vcode
   auto it = ctx->tune.find(key);
-  auto generic_fits = [&](int G) {
-    return (size_t)(4 / G) * tile_bytes(ld, nmax, refine) <= 227 * 1024 ||
-           (G == 4 && tile_bytes(ld, nmax, refine, true) <= 227 * 1024);
-  };
   if (ctx->force_variant != 0) {
     const int v = ctx->force_variant;
-    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || ((v == 1 || v == 2 || v == 4) && generic_fits(v));
+    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || (v > 0 && variant_fits(v, ld, nmax, refine));
     if (!ok) return fail(ctx, GMLS_EINVAL, "gmls_stencils: the forced kernel variant is not available for this shape");
     choice = v;
   } else if (ctx->force_generic) {
-    choice = heuristic_g(ld, nmax, refine);
+    choice = heuristic_variant(ld, nmax, refine);
   } else if (it != ctx->tune.end()) {
     choice = it->second;
   } else if (ctx->autotune && !capturing(ctx)) {
@@ -352,8 +375,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     std::vector<int> cands;
     if (ok32) cands.push_back(-1);
     if (ok16) cands.push_back(-2);
-    for (int G = 1; G <= 4; G *= 2)
-      if (generic_fits(G)) cands.push_back(G);
+    for (int v : generic_candidates(ld, nmax, refine)) cands.push_back(v);
     for (int c : cands) {
       float ms = time_launch(ctx, [&]() {
         if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
@@ -371,7 +393,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: no kernel variant fits this shape");
     ctx->tune[key] = choice;
   } else {
-    choice = hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_g(ld, nmax, refine);
+    choice = hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_variant(ld, nmax, refine);
   }
   if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this shape");
   if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
@@ -413,7 +435,9 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
       pl.nmax[bi] = gmls_gen::basis_size(p->basis, dim, m);
       const TuneKey key{p->basis, dim, m, p->precision, pl.ld[bi], j.L, p->neumann, 1};
       auto it = ctx->tune.find(key);
-      pl.G[bi] = (it != ctx->tune.end()) ? it->second : heuristic_g(pl.ld[bi], pl.nmax[bi], refine);
+      const int v = (it != ctx->tune.end()) ? it->second : heuristic_variant(pl.ld[bi], pl.nmax[bi], refine);
+      pl.G[bi] = v_warps(v);
+      pl.gtile[bi] = v_place(v);
     }
   pl.ld[b.nb - 1] = 32;  // targets larger than every class: reported as unsupported
   pl.nmax[b.nb - 1] = 1;
@@ -421,6 +445,7 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
   for (int bi = 0; bi < b.nb; ++bi) {
     if (pl.G[bi] == 0) {  // no variant fits: send these targets to the unsupported bucket
       pl.G[bi] = 1;
+      pl.gtile[bi] = kPlaceShared;
       pl.ld[bi] = 32;
       pl.nmax[bi] = 1;
     }
@@ -472,24 +497,22 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
         js.n_items = nsample;
         float best = 1e30f;
         int choice = 0;
-        for (int G = 1; G <= 4; G *= 2) {
-          if ((size_t)(4 / G) * tile_bytes(pl.ld[bi], pl.nmax[bi], refine) > 227 * 1024 &&
-              !(G == 4 && tile_bytes(pl.ld[bi], pl.nmax[bi], refine, true) <= 227 * 1024))
-            continue;
+        for (int v : generic_candidates(pl.ld[bi], pl.nmax[bi], refine)) {
           float ms = time_launch(ctx, [&]() {
             if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
-            launch_single(ctx, js, G, pl.ld[bi], pl.nmax[bi], refine, counter, sms);
+            launch_single(ctx, js, v, pl.ld[bi], pl.nmax[bi], refine, counter, sms);
           });
-          ctx->tune_log.push_back({key, G, ms});
+          ctx->tune_log.push_back({key, v, ms});
           if (ms < best) {
             best = ms;
-            choice = G;
+            choice = v;
           }
         }
         if (choice) {
           ctx->tune[key] = choice;
-          pl.G[bi] = choice;
-          b.gpb[bi] = 4 / choice;
+          pl.G[bi] = v_warps(choice);
+          pl.gtile[bi] = v_place(choice);
+          b.gpb[bi] = 4 / pl.G[bi];
         }
       }
     // block tasks depend on the chosen G: recompute the plan
@@ -503,7 +526,6 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
   pl.bucket_start = b.bucket_start;
   pl.task_start = b.task_start;
   pl.task_counter = counter;
-  for (int bi = 0; bi < pl.nb; ++bi) pl.gtile[bi] = needs_gtile(pl.G[bi], pl.ld[bi], pl.nmax[bi], refine);
   const size_t smem = plan_smem(pl, refine);
   const int grid = sms * stencil_blocks_per_sm(refine, smem);
   void* owned = nullptr;
@@ -534,7 +556,7 @@ static gmls_status plan_and_launch(gmls_ctx* ctx, const StencilJob& j0, const gm
     jf.items = s.fb_items;
     jf.n_items = s.fb_count;
     jf.fallback_run = 1;
-    const int gf = heuristic_g(ld, nmax, false);
+    const int gf = heuristic_variant(ld, nmax, false);
     if (gf) {
       cudaError_t e = launch_single(ctx, jf, gf, ld, nmax, false, counter + 1, sms);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "gmls_stencils FP64 redo");
@@ -614,8 +636,10 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
     case GMLS_OPT_FORCE_GENERIC: ctx->force_generic = value != 0; return GMLS_OK;
     case GMLS_OPT_AUTOTUNE: ctx->autotune = value != 0; return GMLS_OK;
     case GMLS_OPT_FORCE_VARIANT:
-      if (value != 0 && value != -1 && value != -2 && value != 1 && value != 2 && value != 4)
-        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2, 1, 2 or 4");
+      if (value != 0 && value != -1 && value != -2 &&
+          !(value > 0 && value < 24 && (v_warps((int)value) == 1 || v_warps((int)value) == 2 ||
+                                        v_warps((int)value) == 4)))
+        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2 or G + 8 * P (G 1, 2, 4; P 0, 1, 2)");
       ctx->force_variant = (int)value;
       return GMLS_OK;
     case GMLS_OPT_CLEAR_TUNING:

@@ -185,7 +185,7 @@ struct BatchPlan {
   int G[kMaxBuckets];           // warps per target
   int ld[kMaxBuckets];          // tile rows
   int nmax[kMaxBuckets];        // tile columns
-  int gtile[kMaxBuckets];       // 1: the tiles live in global memory (too big for shared)
+  int gtile[kMaxBuckets];       // tile placement (kPlaceShared / kPlaceSplit / kPlaceGlobal)
   unsigned char* gscratch;      // [grid blocks][4 / G][gslot_bytes] global tiles
   size_t gslot_bytes;
 };
@@ -208,8 +208,10 @@ struct BucketJob {
   int32_t* items;
 };
 
-size_t tile_bytes(int ld, int nmax, bool fp32_refine, bool ext = false);
-size_t global_tile_bytes(int ld, int nmax, bool fp32_refine);
+// tile placement of the shared-memory kernel (BatchPlan::gtile)
+constexpr int kPlaceShared = 0, kPlaceSplit = 1, kPlaceGlobal = 2;
+size_t tile_bytes(int ld, int nmax, bool fp32_refine, int place = kPlaceShared);
+size_t global_tile_bytes(int ld, int nmax, bool fp32_refine, int place);
 int stencil_blocks_per_sm(bool fp32_refine, size_t smem);
 cudaError_t launch_stencils(const Launch& L, const StencilJob& j, const BatchPlan& plan, bool fp32_refine,
                             size_t smem, int grid_blocks);

@@ -80,12 +80,6 @@ class SliceAlloc {
     }
     free_[off] = sz;
   }
-  size_t largest_free() const {
-    size_t m = 0;
-    for (auto& kv : free_) m = std::max(m, kv.second);
-    return m;
-  }
-
  private:
   char* base_ = nullptr;
   std::map<size_t, size_t> free_, live_;

@@ -83,6 +83,23 @@ __device__ __forceinline__ ff warp_sum_ff(float h, float l) {
   return quick_two_sum(h, l);
 }
 
+// float-float all-reduce across the warp of R independent accumulators
+// (rows >= L untouched); the R reduction chains interleave
+template <int R>
+__device__ __forceinline__ void warp_sum_ff_rows(Dot2 (&acc)[R], int L) {
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (q >= L) continue;
+      const float oh = __shfl_xor_sync(0xffffffffu, acc[q].h, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, acc[q].l, o);
+      const ff s = two_sum(acc[q].h, oh);
+      acc[q].h = s.h;
+      acc[q].l = __fadd_rn(acc[q].l, __fadd_rn(ol, s.l));
+    }
+  }
+}
+
 __device__ __forceinline__ void group_sync(int gid, int nthr) {
   if (nthr == 32)
     __syncwarp();
@@ -99,18 +116,36 @@ struct Lay {
   size_t A, HB, gtotal, tau, dots, sw, lam, S, Y, Z, D, pt, misc, total;
 };
 
+// Leading dimension of the tiles: the row capacity made odd, so that a row of
+// R (stride ld) falls in distinct shared-memory banks across a warp.
+__host__ __device__ inline int pad_ld(int ld) { return ld | 1; }
+
 // tqs: bytes of TQ; hps: bytes of HP; hb: separate high-precision tile (FP32
-// path); ext: the tiles A and HB live in a global-memory slot (offsets A, HB
-// there, gtotal its size) and the shared-memory part starts at tau
-__host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool hb, bool ext = false) {
+// path).  place: where the two tiles live --
+//   kPlaceShared  both in shared memory (offsets A, HB in the shared slice);
+//   kPlaceSplit   the working tile A in shared memory, the float-float copy HB
+//                 in a global-memory slot (offset HB there, gtotal its size);
+//                 HB is only read by the refinement passes, A by every QR step;
+//   kPlaceGlobal  both in a global-memory slot (offsets A, HB there).
+// The per-target vectors (tau, S, Y, ...) always stay in shared memory.
+__host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool hb, int place = kPlaceShared) {
+  ld = pad_ld(ld);
   Lay l;
   size_t o = 0;
-  l.A = o;
-  o += align16((size_t)nmax * ld * tqs);
-  l.HB = o;
-  if (hb) o += align16((size_t)nmax * ld * hps);
-  l.gtotal = o;
-  if (ext) o = 0;
+  const size_t a_bytes = align16((size_t)nmax * ld * tqs);
+  const size_t hb_bytes = hb ? align16((size_t)nmax * ld * hps) : 0;
+  if (place == kPlaceSplit && hb) {
+    l.HB = 0;
+    l.gtotal = hb_bytes;
+    l.A = 0;
+    o = a_bytes;
+  } else {
+    l.A = 0;
+    l.HB = a_bytes;
+    o = a_bytes + hb_bytes;
+    l.gtotal = place == kPlaceGlobal ? o : 0;
+    if (place == kPlaceGlobal) o = 0;
+  }
   l.tau = o;
   o += align16((size_t)nmax * tqs);
   l.dots = o;
@@ -135,24 +170,28 @@ __host__ __device__ inline Lay make_lay(int ld, int nmax, int tqs, int hps, bool
   return l;
 }
 
-size_t tile_bytes(int ld, int nmax, bool fp32_refine, bool ext) {
-  return fp32_refine ? make_lay(ld, nmax, 4, 8, true, ext).total : make_lay(ld, nmax, 8, 8, false, ext).total;
+size_t tile_bytes(int ld, int nmax, bool fp32_refine, int place) {
+  return fp32_refine ? make_lay(ld, nmax, 4, 8, true, place).total : make_lay(ld, nmax, 8, 8, false, place).total;
 }
-size_t global_tile_bytes(int ld, int nmax, bool fp32_refine) {
-  return fp32_refine ? make_lay(ld, nmax, 4, 8, true, true).gtotal : make_lay(ld, nmax, 8, 8, false, true).gtotal;
+size_t global_tile_bytes(int ld, int nmax, bool fp32_refine, int place) {
+  return fp32_refine ? make_lay(ld, nmax, 4, 8, true, place).gtotal : make_lay(ld, nmax, 8, 8, false, place).gtotal;
 }
 
 // ---------------------------------------------------------------- QR (in TQ)
 // Householder QR of the M x n tile A (column-major, leading dimension ld).
 // Column k below the diagonal keeps v_k (v_k[k] = 1 implied), tau[k] its scale.
-// Per column: warp 0 forms the reflector; then each warp takes whole trailing
-// columns, computing the dot product and applying the update in one pass.
+// Per column: warp 0 forms the reflector; then each warp takes the trailing
+// columns kQrCols at a time, so that one load of the reflector feeds that many
+// independent dot-product chains and their warp reductions interleave.
+constexpr int kQrCols = 4;
+
 template <typename TQ>
 __device__ void tile_qr(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
   for (int k = 0; k < n; ++k) {
     TQ* a = A + (size_t)k * ld;
     if (g.wg == 0) {
       TQ sig = 0;
+#pragma unroll 4
       for (int r = k + 1 + g.lane; r < M; r += 32) sig += a[r] * a[r];
       sig = warp_sum(sig);
       const TQ alpha = a[k];
@@ -162,6 +201,7 @@ __device__ void tile_qr(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
         const TQ nrm = sqrt(alpha * alpha + sig);
         const TQ beta = alpha >= TQ(0) ? -nrm : nrm;
         const TQ scale = TQ(1) / (alpha - beta);
+#pragma unroll 4
         for (int r = k + 1 + g.lane; r < M; r += 32) a[r] *= scale;
         __syncwarp();
         if (g.lane == 0) {
@@ -173,13 +213,36 @@ __device__ void tile_qr(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
     group_sync(g.gid, g.nthr);
     const TQ tk = tau[k];
     if (tk != TQ(0) && k + 1 < n) {
-      for (int jc = k + 1 + g.wg; jc < n; jc += g.G) {
-        TQ* aj = A + (size_t)jc * ld;
-        TQ s = (g.lane == 0) ? aj[k] : TQ(0);
-        for (int r = k + 1 + g.lane; r < M; r += 32) s += a[r] * aj[r];
-        s = warp_sum(s) * tk;
-        for (int r = k + 1 + g.lane; r < M; r += 32) aj[r] -= s * a[r];
-        if (g.lane == 0) aj[k] -= s;
+      for (int j0 = k + 1 + g.wg * kQrCols; j0 < n; j0 += g.G * kQrCols) {
+        const int nc = min(kQrCols, n - j0);
+        TQ* aj = A + (size_t)j0 * ld;
+        TQ s[kQrCols];
+#pragma unroll
+        for (int c = 0; c < kQrCols; ++c) s[c] = (g.lane == 0 && c < nc) ? aj[(size_t)c * ld + k] : TQ(0);
+#pragma unroll 4
+        for (int r = k + 1 + g.lane; r < M; r += 32) {
+          const TQ ar = a[r];
+#pragma unroll
+          for (int c = 0; c < kQrCols; ++c)
+            if (c < nc) s[c] += ar * aj[(size_t)c * ld + r];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int c = 0; c < kQrCols; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+#pragma unroll
+        for (int c = 0; c < kQrCols; ++c) s[c] *= tk;
+#pragma unroll 4
+        for (int r = k + 1 + g.lane; r < M; r += 32) {
+          const TQ ar = a[r];
+#pragma unroll
+          for (int c = 0; c < kQrCols; ++c)
+            if (c < nc) aj[(size_t)c * ld + r] -= s[c] * ar;
+        }
+        if (g.lane == 0)
+#pragma unroll
+          for (int c = 0; c < kQrCols; ++c)
+            if (c < nc) aj[(size_t)c * ld + k] -= s[c];
       }
       group_sync(g.gid, g.nthr);
     }
@@ -230,13 +293,241 @@ __device__ void apply_q(const Group& g, const TQ* A, int ld, int M, int n, const
       if (tk == TQ(0)) continue;
       const TQ* a = A + (size_t)k * ld;
       TQ d = (g.lane == 0) ? zl[k] : TQ(0);
+#pragma unroll 4
       for (int r = k + 1 + g.lane; r < M; r += 32) d += a[r] * zl[r];
       d = warp_sum(d) * tk;
+#pragma unroll 4
       for (int r = k + 1 + g.lane; r < M; r += 32) zl[r] -= d * a[r];
       if (g.lane == 0) zl[k] -= d;
       __syncwarp();
     }
   }
+}
+
+// ------------------------------------------------ register-chunked variants
+// For tiles of at most 32 RPL rows: lane owns rows lane + 32 t (t < RPL), so
+// the row loops unroll at compile time, the reflector and the columns being
+// updated sit in registers for a whole column step (one load and one store
+// per element and step) and the vector that Q acts on stays in registers for
+// all n reflectors.  Same arithmetic as tile_qr / apply_q; only the order of
+// the partial sums in apply_q's dot products differs.
+// QC columns per warp pass (fewer for FP64: twice the registers per element)
+template <typename TQ, int RPL, int QC = (sizeof(TQ) == 8 ? 2 : kQrCols)>
+__device__ void tile_qr_rows(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
+  for (int k = 0; k < n; ++k) {
+    TQ* a = A + k * ld;
+    bool live[RPL];  // row below the diagonal and inside the tile
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = g.lane + 32 * t;
+      live[t] = r > k && r < M;
+    }
+    TQ v[RPL];
+    if (g.wg == 0) {
+      TQ sig = 0;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        v[t] = live[t] ? a[g.lane + 32 * t] : TQ(0);
+        sig += v[t] * v[t];
+      }
+      sig = warp_sum(sig);
+      const TQ alpha = a[k];
+      if (sig == TQ(0)) {
+        if (g.lane == 0) tau[k] = 0;
+      } else {
+        const TQ nrm = sqrt(alpha * alpha + sig);
+        const TQ beta = alpha >= TQ(0) ? -nrm : nrm;
+        const TQ scale = TQ(1) / (alpha - beta);
+#pragma unroll
+        for (int t = 0; t < RPL; ++t)
+          if (live[t]) a[g.lane + 32 * t] = v[t] * scale;
+        __syncwarp();
+        if (g.lane == 0) {
+          tau[k] = (beta - alpha) / beta;
+          a[k] = beta;
+        }
+      }
+    }
+    group_sync(g.gid, g.nthr);
+    const TQ tk = tau[k];
+    if (tk != TQ(0) && k + 1 < n) {
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) v[t] = live[t] ? a[g.lane + 32 * t] : TQ(0);
+      for (int j0 = k + 1 + g.wg * QC; j0 < n; j0 += g.G * QC) {
+        const int nc = min(QC, n - j0);
+        TQ* aj = A + j0 * ld;
+        TQ c[QC][RPL], s[QC];
+#pragma unroll
+        for (int q = 0; q < QC; ++q) {
+          s[q] = (g.lane == 0 && q < nc) ? aj[q * ld + k] : TQ(0);
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            c[q][t] = (live[t] && q < nc) ? aj[q * ld + g.lane + 32 * t] : TQ(0);
+            s[q] += v[t] * c[q][t];
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int q = 0; q < QC; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+#pragma unroll
+        for (int q = 0; q < QC; ++q) {
+          s[q] *= tk;
+          if (q < nc) {
+#pragma unroll
+            for (int t = 0; t < RPL; ++t)
+              if (live[t]) aj[q * ld + g.lane + 32 * t] = c[q][t] - s[q] * v[t];
+            if (g.lane == 0) aj[q * ld + k] -= s[q];
+          }
+        }
+      }
+      group_sync(g.gid, g.nthr);
+    }
+  }
+}
+
+template <typename TQ, bool TRANS, int RPL>
+__device__ void apply_q_rows(const Group& g, const TQ* A, int ld, int M, int n, const TQ* tau, int L, TQ* z) {
+  for (int l = g.wg; l < L; l += g.G) {
+    TQ* zl = z + l * ld;
+    TQ zr[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) zr[t] = (g.lane + 32 * t < M) ? zl[g.lane + 32 * t] : TQ(0);
+    for (int s = 0; s < n; ++s) {
+      const int k = TRANS ? s : n - 1 - s;
+      const TQ tk = tau[k];
+      if (tk == TQ(0)) continue;
+      const TQ* a = A + k * ld;
+      TQ av[RPL], d = 0;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int r = g.lane + 32 * t;
+        av[t] = (r > k && r < M) ? a[r] : (r == k ? TQ(1) : TQ(0));  // v_k[k] = 1
+        d += av[t] * zr[t];
+      }
+      d = warp_sum(d) * tk;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) zr[t] -= d * av[t];
+    }
+#pragma unroll
+    for (int t = 0; t < RPL; ++t)
+      if (g.lane + 32 * t < M) zl[g.lane + 32 * t] = zr[t];
+  }
+}
+
+// Triangular solves with the right-hand side in registers (lane owns entries
+// lane + 32 u, u < NPL; n <= 32 NPL), column-oriented: after x_i is known it
+// is broadcast and every later entry takes its update, one shuffle and one
+// multiply-add per step instead of a warp reduction.  rdiag[i] = 1 / R_ii.
+template <typename TQ, int NPL>
+__device__ __forceinline__ TQ pick(const TQ (&x)[NPL], int u) {
+  TQ v = x[0];
+#pragma unroll
+  for (int w = 1; w < NPL; ++w)
+    if (u == w) v = x[w];
+  return v;
+}
+
+// y = R^{-T} b for the L rows (b and y: [L][nmax], may alias)
+template <typename TQ, typename TB, int NPL>
+__device__ void solve_rt_regs(const Group& g, const TQ* A, int ld, int n, int L, int nmax, const TQ* rdiag,
+                              const TB* b, TQ* y) {
+  for (int l = g.wg; l < L; l += g.G) {
+    TQ yr[NPL];
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      const int q = g.lane + 32 * u;
+      yr[u] = q < n ? TQ(b[l * nmax + q]) : TQ(0);
+    }
+    for (int i = 0; i < n; ++i) {
+      const TQ yi = __shfl_sync(0xffffffffu, pick<TQ, NPL>(yr, i >> 5), i & 31) * rdiag[i];
+#pragma unroll
+      for (int u = 0; u < NPL; ++u) {
+        const int q = g.lane + 32 * u;
+        if (q > i && q < n)
+          yr[u] -= A[q * ld + i] * yi;  // R[i][q]
+        else if (q == i)
+          yr[u] = yi;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      const int q = g.lane + 32 * u;
+      if (q < n) y[l * nmax + q] = yr[u];
+    }
+  }
+}
+
+// x = R^{-1} x in place on [L][nmax] rows
+template <typename TQ, int NPL>
+__device__ void solve_r_regs(const Group& g, const TQ* A, int ld, int n, int L, int nmax, const TQ* rdiag, TQ* x) {
+  for (int l = g.wg; l < L; l += g.G) {
+    TQ xr[NPL];
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      const int q = g.lane + 32 * u;
+      xr[u] = q < n ? x[l * nmax + q] : TQ(0);
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      const TQ xi = __shfl_sync(0xffffffffu, pick<TQ, NPL>(xr, i >> 5), i & 31) * rdiag[i];
+      const TQ* ri = A + i * ld;  // column i: R[q][i] = ri[q], q <= i
+#pragma unroll
+      for (int u = 0; u < NPL; ++u) {
+        const int q = g.lane + 32 * u;
+        if (q < i)
+          xr[u] -= ri[q] * xi;
+        else if (q == i)
+          xr[u] = xi;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      const int q = g.lane + 32 * u;
+      if (q < n) x[l * nmax + q] = xr[u];
+    }
+  }
+}
+
+constexpr int kSolveNpl = 3;  // register solves for up to 96 basis functions
+
+// dispatch on the tile's rows: register-chunked up to 256 rows, else the loops
+template <typename TQ>
+__device__ void qr_any(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
+  if (M <= 64)
+    tile_qr_rows<TQ, 2>(g, A, ld, M, n, tau);
+  else if (M <= 128)
+    tile_qr_rows<TQ, 4>(g, A, ld, M, n, tau);
+  else if (M <= 256)
+    tile_qr_rows<TQ, 8>(g, A, ld, M, n, tau);
+  else
+    tile_qr<TQ>(g, A, ld, M, n, tau);
+}
+template <typename TQ, bool TRANS>
+__device__ void apply_q_any(const Group& g, const TQ* A, int ld, int M, int n, const TQ* tau, int L, TQ* z) {
+  if (M <= 64)
+    apply_q_rows<TQ, TRANS, 2>(g, A, ld, M, n, tau, L, z);
+  else if (M <= 128)
+    apply_q_rows<TQ, TRANS, 4>(g, A, ld, M, n, tau, L, z);
+  else if (M <= 256)
+    apply_q_rows<TQ, TRANS, 8>(g, A, ld, M, n, tau, L, z);
+  else
+    apply_q<TQ, TRANS>(g, A, ld, M, n, tau, L, z);
+}
+template <typename TQ, typename TB>
+__device__ void solve_rt_any(const Group& g, const TQ* A, int ld, int n, int L, int nmax, const TQ* rdiag,
+                             const TB* b, TQ* y) {
+  if (n <= 32 * kSolveNpl)
+    solve_rt_regs<TQ, TB, kSolveNpl>(g, A, ld, n, L, nmax, rdiag, b, y);
+  else
+    solve_rt<TQ, TB>(g, A, ld, n, L, nmax, b, y);
+}
+template <typename TQ>
+__device__ void solve_r_any(const Group& g, const TQ* A, int ld, int n, int L, int nmax, const TQ* rdiag, TQ* x) {
+  if (n <= 32 * kSolveNpl)
+    solve_r_regs<TQ, kSolveNpl>(g, A, ld, n, L, nmax, rdiag, x);
+  else
+    solve_r<TQ>(g, A, ld, n, L, nmax, x);
 }
 
 // per-row offset of neighbour q from the target, in HP, and |x_j - x_T|^2
@@ -263,12 +554,14 @@ __device__ __forceinline__ ff sqrt_weight(ff u, const StencilJob& j) {
 // ------------------------------------------------------------ one target
 template <typename TQ, typename HP, bool REFINE>
 __device__ void process_target(const StencilJob& j, const Group& g, unsigned char* base, unsigned char* gbase,
-                               int ld, int nmax, int64_t to) {
-  const Lay lay = make_lay(ld, nmax, (int)sizeof(TQ), (int)sizeof(HP), REFINE, gbase != nullptr);
-  unsigned char* tb = gbase ? gbase : base;  // where the tiles A and HB live
-  TQ* A = reinterpret_cast<TQ*>(tb + lay.A);
-  HP* HB = REFINE ? reinterpret_cast<HP*>(tb + lay.HB) : reinterpret_cast<HP*>(tb + lay.A);
+                               int place, int ld, int nmax, int64_t to) {
+  const Lay lay = make_lay(ld, nmax, (int)sizeof(TQ), (int)sizeof(HP), REFINE, place);
+  const int ld_rows = ld;  // row capacity; the tiles use the padded stride
+  ld = pad_ld(ld);
+  TQ* A = reinterpret_cast<TQ*>((place == kPlaceGlobal ? gbase : base) + lay.A);
+  HP* HB = REFINE ? reinterpret_cast<HP*>((place == kPlaceShared ? base : gbase) + lay.HB) : reinterpret_cast<HP*>(A);
   TQ* tau = reinterpret_cast<TQ*>(base + lay.tau);
+  TQ* rdiag = reinterpret_cast<TQ*>(base + lay.dots);  // 1 / R_ii
   HP* sw = reinterpret_cast<HP*>(base + lay.sw);
   HP* lam = reinterpret_cast<HP*>(base + lay.lam);
   HP* S = reinterpret_cast<HP*>(base + lay.S);
@@ -295,8 +588,8 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
   uint8_t st = j.nbr_status ? j.nbr_status[to] : 0;
   if (j.fallback_run)  // FP64 redo of an FP32 target: keep why it was redone
     st |= GMLS_T_FP64_FALLBACK | (j.status[to] & (GMLS_T_ILL_CONDITIONED | GMLS_T_REFINE_NOT_CONVERGED));
-  bool skip = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || nb <= 0 || M > ld || nb > nmax || !(eps > 0.0);
-  if (!(st & GMLS_T_TOO_FEW_NEIGHBOURS) && k > 0 && (M > ld || nb > nmax)) st |= GMLS_T_UNSUPPORTED;
+  bool skip = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || nb <= 0 || M > ld_rows || nb > nmax || !(eps > 0.0);
+  if (!(st & GMLS_T_TOO_FEW_NEIGHBOURS) && k > 0 && (M > ld_rows || nb > nmax)) st |= GMLS_T_UNSUPPORTED;
   if (!skip && M < n) {
     st |= GMLS_T_RANK_DEFICIENT;
     skip = true;
@@ -391,13 +684,17 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
     }
 
     if (REFINE) {  // FP32 working copy of the tile
-      for (int i = 0; i < n; ++i)
-        for (int r = g.tid; r < M; r += g.nthr) A[(size_t)i * ld + r] = (TQ)hp_hi_f(reinterpret_cast<ff*>(HB)[(size_t)i * ld + r]);
+#pragma unroll 4
+      for (int e = g.tid; e < n * M; e += g.nthr) {
+        const int i = e / M, r = e - i * M;
+        A[i * ld + r] = (TQ)hp_hi_f(reinterpret_cast<ff*>(HB)[i * ld + r]);
+      }
       group_sync(g.gid, g.nthr);
     }
 
     // ---- 2. QR
-    tile_qr<TQ>(g, A, ld, M, n, tau);
+    qr_any<TQ>(g, A, ld, M, n, tau);
+    for (int i = g.tid; i < n; i += g.nthr) rdiag[i] = TQ(1) / A[i * ld + i];
     if (g.wg == 0) {
       TQ rmax = 0, rmin = TQ(3.0e38);
       for (int i = g.lane; i < n; i += 32) {
@@ -422,14 +719,14 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
     // ---- 4. s = Q [R^{-T} lambda; 0]
     for (int e = g.tid; e < L * n; e += g.nthr) D[(e / n) * nmax + e % n] = (TQ)hp_to_double(lam[(e / n) * nmax + e % n]);
     group_sync(g.gid, g.nthr);
-    solve_rt<TQ, TQ>(g, A, ld, n, L, nmax, D, D);
+    solve_rt_any<TQ, TQ>(g, A, ld, n, L, nmax, rdiag, D, D);
     group_sync(g.gid, g.nthr);
     for (int e = g.tid; e < L * M; e += g.nthr) {
       const int l = e / M, r = e % M;
       Z[(size_t)l * ld + r] = (r < n) ? D[l * nmax + r] : TQ(0);
     }
     group_sync(g.gid, g.nthr);
-    apply_q<TQ, false>(g, A, ld, M, n, tau, L, Z);
+    apply_q_any<TQ, false>(g, A, ld, M, n, tau, L, Z);
     group_sync(g.gid, g.nthr);
     for (int e = g.tid; e < L * M; e += g.nthr) {
       const int l = e / M, r = e % M;
@@ -441,7 +738,7 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
       ff* Yf = reinterpret_cast<ff*>(Y);
       ff* lamf = reinterpret_cast<ff*>(lam);
       // y = R^{-1} R^{-T} lambda (the least-squares coefficients)
-      solve_r<TQ>(g, A, ld, n, L, nmax, D);
+      solve_r_any<TQ>(g, A, ld, n, L, nmax, rdiag, D);
       group_sync(g.gid, g.nthr);
       for (int e = g.tid; e < L * n; e += g.nthr) Yf[(e / n) * nmax + e % n] = ff((float)D[(e / n) * nmax + e % n], 0.f);
       group_sync(g.gid, g.nthr);
@@ -449,30 +746,54 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
       float prev = 0.0f;
       const bool ill = (st & GMLS_T_ILL_CONDITIONED) != 0;  // ill-conditioned: straight to FP64
       for (int iter = 0; iter < j.max_refine && !ill; ++iter) {
-        // f = B y - s (into Z), compensated float-float
-        for (int e = g.tid; e < L * M; e += g.nthr) {
-          const int l = e / M, r = e % M;
-          Dot2 acc;
-          acc.init(-Sf[(size_t)l * ld + r]);
-          const ff* yl = Yf + l * nmax;
-          for (int i = 0; i < n; ++i) acc.add_prod(B[(size_t)i * ld + r], yl[i]);
-          Z[(size_t)l * ld + r] = (TQ)__fadd_rn(acc.h, acc.l);
+        // f = B y - s (into Z), compensated float-float; a thread per tile row,
+        // all L functional rows at once (one load of B feeds L chains)
+        for (int r = g.tid; r < M; r += g.nthr) {
+          Dot2 acc[kMaxSolveRows];
+#pragma unroll
+          for (int l = 0; l < kMaxSolveRows; ++l)
+            if (l < L) acc[l].init(-Sf[(size_t)l * ld + r]);
+#pragma unroll 4
+          for (int i = 0; i < n; ++i) {
+            const ff b = B[(size_t)i * ld + r];
+#pragma unroll
+            for (int l = 0; l < kMaxSolveRows; ++l)
+              if (l < L) acc[l].add_prod(b, Yf[l * nmax + i]);
+          }
+#pragma unroll
+          for (int l = 0; l < kMaxSolveRows; ++l)
+            if (l < L) Z[(size_t)l * ld + r] = (TQ)__fadd_rn(acc[l].h, acc[l].l);
         }
-        // g = lambda - B^T s (into D), one warp per (l, i)
-        for (int p = g.wg; p < L * n; p += g.G) {
-          const int l = p / n, i = p % n;
+        // g = lambda - B^T s (into D); a warp per basis column i, all L rows
+        for (int i = g.wg; i < n; i += g.G) {
           const ff* bi = B + (size_t)i * ld;
-          const ff* sl = Sf + (size_t)l * ld;
-          Dot2 acc;
-          for (int r = g.lane; r < M; r += 32) acc.add_prod(-bi[r], sl[r]);
-          const ff tot = warp_sum_ff(acc.h, acc.l) + lamf[l * nmax + i];
-          if (g.lane == 0) D[l * nmax + i] = (TQ)__fadd_rn(tot.h, tot.l);
+          Dot2 acc[kMaxSolveRows];
+#pragma unroll 2
+          for (int r = g.lane; r < M; r += 32) {
+            const ff b = -bi[r];
+#pragma unroll
+            for (int l = 0; l < kMaxSolveRows; ++l)
+              if (l < L) acc[l].add_prod(b, Sf[(size_t)l * ld + r]);
+          }
+          warp_sum_ff_rows<kMaxSolveRows>(acc, L);
+          if (g.lane < L) {
+            const int l = g.lane;
+            float h = 0.f, lo = 0.f;
+#pragma unroll
+            for (int q = 0; q < kMaxSolveRows; ++q)
+              if (q == l) {
+                h = acc[q].h;
+                lo = acc[q].l;
+              }
+            const ff tot = quick_two_sum(h, lo) + lamf[l * nmax + i];
+            D[l * nmax + i] = (TQ)__fadd_rn(tot.h, tot.l);
+          }
         }
         group_sync(g.gid, g.nthr);
         // d = Q^T f; a = R^{-T} g; dy = R^{-1}(a - d_1); ds = Q [a; d_2]
-        apply_q<TQ, true>(g, A, ld, M, n, tau, L, Z);
+        apply_q_any<TQ, true>(g, A, ld, M, n, tau, L, Z);
         group_sync(g.gid, g.nthr);
-        solve_rt<TQ, TQ>(g, A, ld, n, L, nmax, D, D);
+        solve_rt_any<TQ, TQ>(g, A, ld, n, L, nmax, rdiag, D, D);
         group_sync(g.gid, g.nthr);
         for (int e = g.tid; e < L * n; e += g.nthr) {
           const int l = e / n, i = e % n;
@@ -482,8 +803,8 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
           Z[(size_t)l * ld + i] = a;
         }
         group_sync(g.gid, g.nthr);
-        solve_r<TQ>(g, A, ld, n, L, nmax, D);
-        apply_q<TQ, false>(g, A, ld, M, n, tau, L, Z);
+        solve_r_any<TQ>(g, A, ld, n, L, nmax, rdiag, D);
+        apply_q_any<TQ, false>(g, A, ld, M, n, tau, L, Z);
         group_sync(g.gid, g.nthr);
         float dmax = 0.0f, smax = 0.0f;
         for (int e = g.tid; e < L * M; e += g.nthr) {
@@ -654,12 +975,12 @@ __global__ void __launch_bounds__(kBlock) stencil_kernel(StencilJob j, BatchPlan
     }
     if (item < end) {
       const int64_t to = plan.items ? (int64_t)plan.items[item] : (j.items ? (int64_t)j.items[item] : item);
-      const bool ext = plan.gtile[b] != 0;
-      const size_t slice = (REFINE ? make_lay(plan.ld[b], plan.nmax[b], 4, 8, true, ext)
-                                   : make_lay(plan.ld[b], plan.nmax[b], 8, 8, false, ext)).total;
+      const int place = plan.gtile[b];
+      const size_t slice = (REFINE ? make_lay(plan.ld[b], plan.nmax[b], 4, 8, true, place)
+                                   : make_lay(plan.ld[b], plan.nmax[b], 8, 8, false, place)).total;
       unsigned char* gslot =
-          ext ? plan.gscratch + ((size_t)blockIdx.x * gpb + g.gid) * plan.gslot_bytes : nullptr;
-      process_target<TQ, HP, REFINE>(j, g, smem + (size_t)g.gid * slice, gslot, plan.ld[b], plan.nmax[b], to);
+          place != kPlaceShared ? plan.gscratch + ((size_t)blockIdx.x * gpb + g.gid) * plan.gslot_bytes : nullptr;
+      process_target<TQ, HP, REFINE>(j, g, smem + (size_t)g.gid * slice, gslot, place, plan.ld[b], plan.nmax[b], to);
     }
   }
 }

@@ -142,12 +142,15 @@ NAMES = {gmls.GRAD: "grad", gmls.LAPLACIAN: "laplacian", gmls.DIV: "div", gmls.V
          gmls.CURLCURL: "curlcurl"}
 
 
-VARIANT = {"reg32": -1, "reg16": -2}
+# forced variants: register kernel (-1, -2); shared-memory kernel G + 8 * placement
+# (split: float-float tile in global memory; global: both tiles there)
+VARIANT = {"reg32": -1, "reg16": -2, "split4": 4 + 8, "global1": 1 + 16, "global2": 2 + 16}
 
 
 @pytest.mark.parametrize("precision,kernel", [(gmls.FP64, "generic"), (gmls.FP32_REFINE, "generic"),
                                               (gmls.FP32_REFINE, "auto"), (gmls.FP32_REFINE, "reg32"),
-                                              (gmls.FP32_REFINE, "reg16")])
+                                              (gmls.FP32_REFINE, "reg16"), (gmls.FP32_REFINE, "split4"),
+                                              (gmls.FP32_REFINE, "global1"), (gmls.FP64, "global2")])
 @pytest.mark.parametrize("dim,n_axis,basis,m,k,fns", CASES)
 def test_stencils_match_oracle(ctx, dim, n_axis, basis, m, k, fns, precision, kernel):
     x = inputs.jittered_grid(dim, n_axis, seed=m)
@@ -160,7 +163,7 @@ def test_stencils_match_oracle(ctx, dim, n_axis, basis, m, k, fns, precision, ke
     except gmls.GmlsError as e:
         _release(ctx, cid, nid)
         if e.code == gmls.EINVAL and kernel in VARIANT:
-            pytest.skip(f"no {kernel} register kernel for this shape")
+            pytest.skip(f"no {kernel} variant for this shape")
         raise
     finally:
         ctx.set_option(gmls.OPT_FORCE_GENERIC, 0)
