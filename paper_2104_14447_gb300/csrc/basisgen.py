@@ -217,8 +217,8 @@ def gen():
                 summary.append((kind, d, m, nb, nc, nterms))
                 L.append(f"// {name}: {nb} functions, {nc} component(s), {nterms} terms")
                 L.append(f"// out[i * ld + c] = s * psi_i,c(xi)")
-                L.append("template <typename T>")
-                L.append(f"__device__ __forceinline__ void eval_{name}(const T* xi, T* out, int ld, const T s) {{")
+                L.append("template <typename T, typename O = T*>")
+                L.append(f"__device__ __forceinline__ void eval_{name}(const T* xi, O out, int ld, const T s) {{")
                 ind = "  "
                 emit_monomials(d, m + 1 if kind == "staggered" else m, L, ind)
                 used = {mi for f in funcs for (_, mi, _) in f}
@@ -267,12 +267,13 @@ def gen():
         L.append(f"    (kind == {KID[kind]} && d == {d} && m == {m}) ? {nb} :")
     L.append("    0;")
     L.append("}")
-    L.append("template <typename T>")
-    L.append("__device__ __forceinline__ void eval_basis(int kind, int d, int m, const T* xi, T* out, int ld, const T s) {")
+    L.append("// O: the output (T* or any type whose operator[] returns an assignable element)")
+    L.append("template <typename T, typename O = T*>")
+    L.append("__device__ __forceinline__ void eval_basis(int kind, int d, int m, const T* xi, O out, int ld, const T s) {")
     L.append("  switch (kind * 100 + d * 10 + m) {")
     for kind, d, m, nb, nc, _ in summary:
         name = f"{kind}_{d}d_m{m}"
-        L.append(f"    case {KID[kind] * 100 + d * 10 + m}: eval_{name}<T>(xi, out, ld, s); break;")
+        L.append(f"    case {KID[kind] * 100 + d * 10 + m}: eval_{name}<T, O>(xi, out, ld, s); break;")
     L.append("    default: break;")
     L.append("  }")
     L.append("}")
@@ -282,8 +283,8 @@ def gen():
         name = f"{kind}_{d}d_m{m}"
         kid = KID[kind]
         L.append(f"template <> struct BasisEval<{kid}, {d}, {m}> {{")
-        L.append("  template <typename T>")
-        L.append(f"  __device__ __forceinline__ static void run(const T* xi, T* out, int ld, const T s) {{ eval_{name}<T>(xi, out, ld, s); }}")
+        L.append("  template <typename T, typename O = T*>")
+        L.append(f"  __device__ __forceinline__ static void run(const T* xi, O out, int ld, const T s) {{ eval_{name}<T, O>(xi, out, ld, s); }}")
         L.append("};")
     L.append("// functional row coefficient (before the eps^{-|beta|} factor)")
     L.append("// fn: 0 grad (d rows), 1 laplacian (1 row), 2 vector Laplacian (d rows),")

@@ -311,6 +311,35 @@ __device__ void apply_q(const Group& g, const TQ* A, int ld, int M, int n, const
 // per element and step) and the vector that Q acts on stays in registers for
 // all n reflectors.  Same arithmetic as tile_qr / apply_q; only the order of
 // the partial sums in apply_q's dot products differs.
+// Warp all-reduce of Q independent partial sums (Q a power of two <= 32) by
+// recursive halving: at each of the first log2 Q steps a lane keeps half of
+// its values and adds the partner's copy of them, so one value is left per
+// lane after Q - 1 shuffles; five minus log2 Q plain butterfly steps finish
+// it, and lane q << (5 - log2 Q) then holds sum q, which is broadcast.
+// Q - 1 + 5 - log2 Q + Q shuffles instead of 5 Q.
+template <typename T, int Q>
+__device__ __forceinline__ void warp_sum_halving(T (&s)[Q], int lane) {
+  constexpr int LOGQ = Q <= 1 ? 0 : Q <= 2 ? 1 : Q <= 4 ? 2 : Q <= 8 ? 3 : Q <= 16 ? 4 : 5;
+  static_assert((1 << LOGQ) == Q, "Q must be a power of two");
+  T v[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) v[i] = s[i];
+#pragma unroll
+  for (int h = Q / 2, off = 16; h >= 1; h /= 2, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+#pragma unroll
+  for (int off = 16 >> LOGQ; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) s[q] = __shfl_sync(0xffffffffu, v[0], q << (5 - LOGQ));
+}
+
 // QC columns per warp pass (fewer for FP64: twice the registers per element)
 template <typename TQ, int RPL, int QC = (sizeof(TQ) == 8 ? 2 : kQrCols)>
 __device__ void tile_qr_rows(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
@@ -366,10 +395,7 @@ __device__ void tile_qr_rows(const Group& g, TQ* A, int ld, int M, int n, TQ* ta
             s[q] += v[t] * c[q][t];
           }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int q = 0; q < QC; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+        warp_sum_halving<TQ, QC>(s, g.lane);
 #pragma unroll
         for (int q = 0; q < QC; ++q) {
           s[q] *= tk;
@@ -384,6 +410,131 @@ __device__ void tile_qr_rows(const Group& g, TQ* A, int ld, int M, int n, TQ* ta
       group_sync(g.gid, g.nthr);
     }
   }
+}
+
+// Householder QR of an FP32 tile held in registers (M <= 32 RPL rows,
+// n <= CPW G columns): warp w owns the columns j = w + u G (u < CPW), lane
+// owns rows lane + 32 t.  Per column step the reflector v_k is published in
+// shared memory (vbuf, two buffers of 32 RPL floats: rows < k zero, row k
+// one) and each warp applies it to its own trailing columns, four at a time
+// with one halving reduction.  The owner of column k + 1 updates that column
+// first and publishes reflector k + 1 before its other columns (look-ahead),
+// so a step costs one barrier.  The factor goes back to A at the end, in the
+// layout tile_qr leaves.
+template <int RPL, int CPW>
+__device__ void tile_qr_regs(const Group& g, float* A, int ld, int M, int n, float* tau, float* vbuf) {
+  constexpr int NR = 32 * RPL;
+  float c[CPW][RPL];
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int j = g.wg + u * g.G;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = g.lane + 32 * t;
+      c[u][t] = (j < n && r < M) ? A[j * ld + r] : 0.0f;
+    }
+  }
+  // reflector of the column held in x (column k): x becomes [R part; beta;
+  // v below]; the published copy has zeros above k and one at k
+  auto reflect = [&](float (&x)[RPL], int k) {
+    float sig = 0.0f, alpha = 0.0f;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = g.lane + 32 * t;
+      if (r > k && r < M) sig += x[t] * x[t];
+      if (r == k) alpha = x[t];
+    }
+    sig = warp_sum(sig);
+    alpha = __shfl_sync(0xffffffffu, alpha, k & 31);
+    float* vb = vbuf + (k & 1) * NR;
+    float tk = 0.0f;
+    if (sig != 0.0f) {
+      const float nrm = sqrtf(alpha * alpha + sig);
+      const float beta = alpha >= 0.0f ? -nrm : nrm;
+      const float scale = 1.0f / (alpha - beta);
+      tk = (beta - alpha) / beta;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int r = g.lane + 32 * t;
+        if (r > k && r < M) x[t] *= scale;
+        if (r == k) x[t] = beta;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = g.lane + 32 * t;
+      vb[r] = (r > k && r < M) ? x[t] : (r == k ? 1.0f : 0.0f);
+    }
+    if (g.lane == 0) tau[k] = tk;
+  };
+  // column k's owner forms reflector 0 before the loop
+  if (g.wg == 0 && n > 0) reflect(c[0], 0);
+  group_sync(g.gid, g.nthr);
+  for (int k = 0; k < n; ++k) {
+    const float* vb = vbuf + (k & 1) * NR;
+    float v[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) v[t] = vb[g.lane + 32 * t];
+    const float tk = tau[k];
+    const int la = k + 1;  // look-ahead column
+    const bool own_la = la < n && (la % g.G) == g.wg;
+    const int u_la = la / g.G;
+    if (own_la) {
+#pragma unroll
+      for (int u = 0; u < CPW; ++u)
+        if (u == u_la) {
+          if (tk != 0.0f) {
+            float s = 0.0f;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) s += v[t] * c[u][t];
+            s = warp_sum(s) * tk;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) c[u][t] -= s * v[t];
+          }
+          reflect(c[u], la);
+        }
+    }
+    if (tk != 0.0f) {
+#pragma unroll
+      for (int ub = 0; ub < CPW; ub += 4) {
+        if (g.wg + (ub + 3) * g.G <= la) continue;  // every column of the group finished or handled
+        float sq[4];
+        bool act[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = ub + q;
+          const int j = g.wg + u * g.G;
+          act[q] = u < CPW && j > la && j < n;
+          sq[q] = 0.0f;
+          if (u < CPW) {
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) sq[q] += v[t] * c[u][t];
+          }
+        }
+        warp_sum_halving<float, 4>(sq, g.lane);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = ub + q;
+          if (u < CPW && act[q]) {
+            const float sk = sq[q] * tk;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) c[u][t] -= sk * v[t];
+          }
+        }
+      }
+    }
+    group_sync(g.gid, g.nthr);
+  }
+#pragma unroll
+  for (int u = 0; u < CPW; ++u) {
+    const int j = g.wg + u * g.G;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = g.lane + 32 * t;
+      if (j < n && r < M) A[j * ld + r] = c[u][t];
+    }
+  }
+  group_sync(g.gid, g.nthr);
 }
 
 template <typename TQ, bool TRANS, int RPL>
@@ -489,7 +640,8 @@ __device__ void solve_r_regs(const Group& g, const TQ* A, int ld, int n, int L, 
   }
 }
 
-constexpr int kSolveNpl = 3;  // register solves for up to 96 basis functions
+constexpr int kSolveNpl = 3;   // register solves for up to 96 basis functions
+constexpr int kQrRegCols = 13;  // register QR: up to 52 columns over four warps
 
 // dispatch on the tile's rows: register-chunked up to 256 rows, else the loops
 template <typename TQ>
@@ -550,6 +702,21 @@ __device__ __forceinline__ ff sqrt_weight(ff u, const StencilJob& j) {
   for (int p = 0; p < reps; ++p) s = s * base;
   return s;
 }
+
+// Basis output into the float-float tile and its FP32 working copy at once.
+struct DualOut {
+  ff* hb;
+  float* a;
+  struct Ref {
+    ff* h;
+    float* f;
+    __device__ __forceinline__ void operator=(const ff& v) const {
+      *h = v;
+      *f = v.h;
+    }
+  };
+  __device__ __forceinline__ Ref operator[](int i) const { return Ref{hb + i, a + i}; }
+};
 
 // ------------------------------------------------------------ one target
 template <typename TQ, typename HP, bool REFINE>
@@ -625,7 +792,11 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
       }
       const HP u = hp_one(HP()) - hp_sqrt(r2) * inv_eps;
       const HP s = hp_pos(u) ? sqrt_weight(u, j) : hz;
-      gmls_gen::eval_basis<HP>(j.kind, dim, m, xi, HB + q * nc, ld, s);
+      if constexpr (REFINE) {  // the FP32 tile too (rewritten after a Neumann step edits HB)
+        gmls_gen::eval_basis<HP>(j.kind, dim, m, xi, DualOut{HB + q * nc, A + q * nc}, ld, s);
+      } else {
+        gmls_gen::eval_basis<HP>(j.kind, dim, m, xi, HB + q * nc, ld, s);
+      }
       for (int c = 0; c < nc; ++c) sw[q * nc + c] = s;
     }
     // ---- 3. functional rows lambda (before Neumann)
@@ -683,7 +854,7 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
       group_sync(g.gid, g.nthr);
     }
 
-    if (REFINE) {  // FP32 working copy of the tile
+    if (REFINE && neu) {  // FP32 working copy of the tile after the Neumann step
 #pragma unroll 4
       for (int e = g.tid; e < n * M; e += g.nthr) {
         const int i = e / M, r = e - i * M;
@@ -693,7 +864,16 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
     }
 
     // ---- 2. QR
-    qr_any<TQ>(g, A, ld, M, n, tau);
+    if constexpr (REFINE) {  // FP32 tile: in registers where it fits four warps
+      if (g.G == 4 && M > 64 && M <= 128 && n <= 4 * kQrRegCols)
+        tile_qr_regs<4, kQrRegCols>(g, A, ld, M, n, tau, Z);
+      else if (g.G == 4 && M > 128 && M <= 256 && n <= 4 * kQrRegCols)
+        tile_qr_regs<8, kQrRegCols>(g, A, ld, M, n, tau, Z);
+      else
+        qr_any<TQ>(g, A, ld, M, n, tau);
+    } else {
+      qr_any<TQ>(g, A, ld, M, n, tau);
+    }
     for (int i = g.tid; i < n; i += g.nthr) rdiag[i] = TQ(1) / A[i * ld + i];
     if (g.wg == 0) {
       TQ rmax = 0, rmin = TQ(3.0e38);
@@ -929,7 +1109,7 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
 
 // -------------------------------------------------------- persistent kernel
 template <typename TQ, typename HP, bool REFINE>
-__global__ void __launch_bounds__(kBlock) stencil_kernel(StencilJob j, BatchPlan plan) {
+__global__ void __launch_bounds__(kBlock, 3) stencil_kernel(StencilJob j, BatchPlan plan) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_task, s_bucket;
   const int warp = threadIdx.x >> 5;
