@@ -458,6 +458,124 @@ def stokes_system(ctx, steps=5):
             "l2": "flushed before each timed step (256 MB write)"}
 
 
+def porous_3d(ctx, n_axis=128, steps=3, n_sample=48):
+    """The 3D porous-medium workload: a jittered n_axis^3 lattice in the unit
+    cube minus 64 random non-overlapping spheres, boundary targets on the
+    sphere surfaces and cube faces with their geometric normals.  Per step:
+    kNN-80 lists and their 40-nearest prefix, degree-3 scalar stencils
+    (gradient, Laplacian; Neumann constraint at boundary targets), degree-3
+    divergence-free stencils (vector Laplacian, 240 x 50 systems), FP32 with
+    float-float refinement, and the three CSR operators.  Device-timed per
+    stage with CUDA events on the context stream, inputs resident, L2 flushed
+    before each step; stencil errors on a sample of boundary and interior
+    targets against the oracle."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    pc = inputs.porous_cube(n_axis=n_axis)
+    x = pc["x"]
+    n = x.shape[1]
+    stream = ctx.stream
+    cid = ctx.cloud(x, normals=pc["normals"], bflags=pc["bflag"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=ctx.device)
+    prec = gmls.FP32_REFINE
+
+    def step(ev=None):
+        rec = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
+        rec(0)
+        n80 = ctx.neighbors(cid, 80, EPS_FACTOR)
+        n40 = ctx.neighbors_prefix(n80, 40, EPS_FACTOR)
+        rec(1)
+        ssc = ctx.stencils(n40, gmls.SCALAR, 3, [gmls.GRAD, gmls.LAPLACIAN], precision=prec, neumann=True)
+        rec(2)
+        sdf = ctx.stencils(n80, gmls.DIVFREE, 3, [gmls.VEC_LAPLACIAN], precision=prec)
+        rec(3)
+        csr = [ctx.assemble_csr(ssc, gmls.GRAD), ctx.assemble_csr(ssc, gmls.LAPLACIAN),
+               ctx.assemble_csr(sdf, gmls.VEC_LAPLACIAN)]
+        rec(4)
+        return n80, n40, ssc, sdf, csr
+
+    def release(h):
+        for hd in (h[3], h[2], h[1], h[0]):
+            ctx.release(hd)
+
+    release(step())  # warm-up (autotunes the two shapes)
+    torch.cuda.synchronize()
+    times = []
+    for s in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        h = step(ev)
+        torch.cuda.synchronize()
+        times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+        if s < steps - 1:
+            release(h)
+    med = np.median(np.array(times), axis=0)
+    step_ms = float(np.sum(med))
+    st_sc = ctx.export(h[2], gmls.X_STATUS, torch.uint8).cpu().numpy()
+    st_df = ctx.export(h[3], gmls.X_STATUS, torch.uint8).cpu().numpy()
+    # GPU outputs of a sample of boundary and interior targets, for the
+    # oracle comparison of the CPU-baseline leg (porous_oracle_errors)
+    bidx = np.flatnonzero(pc["bflag"])
+    iidx = np.flatnonzero(pc["bflag"] == 0)
+    half = n_sample // 2
+    sample = np.unique(np.concatenate([bidx[(inputs.uniform(2, 96, half) * len(bidx)).astype(np.int64)],
+                                       iidx[(inputs.uniform(2, 97, half) * len(iidx)).astype(np.int64)]]))
+    sample = sample.astype(np.int32)
+    gpu_sample = {"x": x, "bflag": pc["bflag"], "normals": pc["normals"], "sample": sample, "ops": []}
+    for key, nh, sh, k, kind, code in (("grad", h[1], h[2], 40, "scalar", gmls.GRAD),
+                                       ("laplacian", h[1], h[2], 40, "scalar", gmls.LAPLACIAN),
+                                       ("vec_laplacian", h[0], h[3], 80, "divfree", gmls.VEC_LAPLACIAN)):
+        idx = ctx.export(nh, gmls.X_NBR_INDEX, torch.int32).cpu().numpy().reshape(n, k)[sample]
+        _, rows, nc, _ = ctx.stencil_info(sh, code)
+        wg = ctx.weights(sh, code).cpu().numpy().reshape(n, rows, k, nc)[sample]
+        gpu_sample["ops"].append((key, k, kind, idx, wg))
+    release(h)
+    ctx.release(cid)
+    tune = {}
+    for r in ctx.tune_log():
+        if r["dim"] == 3 and r["degree"] == 3 and not r["bucketed"]:
+            v = r["variant"]
+            place = {0: "", 1: ", split tiles", 2: ", global tiles"}[v >> 3] if v > 0 else ""
+            name = {-1: "register", -2: "register 16 lanes"}.get(v, f"{v & 7} warp(s)/target{place}")
+            key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m=3 rows<={r['rows']}"
+            tune.setdefault(key, {})[name] = round(r["ms"], 3)
+    qr_flops = 2 * 240 * 50 ** 2 - 2 * 50 ** 3 / 3  # Householder QR of one 240 x 50 system
+    return {"workload": f"porous cube {n_axis}^3 lattice minus 64 spheres: {n} points, "
+                        f"{int(pc['bflag'].sum())} on a boundary, degree 3, k = 40 / 80, FP32 + refinement",
+            "targets": n, "porosity": float(pc["porosity"]), "step_ms": step_ms, "targets_per_s": n / step_ms * 1e3,
+            "stage_ms": {"neighbours": float(med[0]), "scalar_stencils": float(med[1]),
+                         "divfree_stencils": float(med[2]), "csr": float(med[3])},
+            "divfree_targets_per_s": n / float(med[2]) * 1e3,
+            "divfree_qr_tflops": qr_flops * n / float(med[2]) / 1e9,
+            "fp64_redo": {"scalar": int(np.sum((st_sc & gmls.T_FP64_FALLBACK) != 0)),
+                          "divfree": int(np.sum((st_df & gmls.T_FP64_FALLBACK) != 0))},
+            "tune_ms": tune, "l2": "flushed before each timed step (256 MB write)"}, gpu_sample
+
+
+def porous_oracle_errors(gs):
+    """CPU-baseline leg of the porous section: the oracle's kNN lists and
+    stencils on the sampled targets against the GPU's."""
+    import oracle
+
+    x, sample = gs["x"], gs["sample"]
+    errs, lists_equal = {}, True
+    for key, k, kind, idx, wg in gs["ops"]:
+        oi, oe = oracle.knn(x, sample, k, EPS_FACTOR, method="grid")
+        lists_equal &= bool(np.array_equal(idx, oi))
+        off = np.arange(0, len(sample) * k + 1, k)
+        extra = dict(bflag=gs["bflag"][sample], normals=gs["normals"].T[sample]) if kind == "scalar" else {}
+        wo, _, _ = oracle.stencils(x, sample, off, oi.reshape(-1), oe, kind, 3, key, **extra)
+        w = wg.reshape(wo.shape)
+        a = np.abs(w - wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
+        b = np.abs(wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
+        errs[key] = float(np.max(a / np.where(b > 0, b, 1.0)))
+    return {"sample": f"{len(sample)} targets, half drawn from the boundary, half from the interior",
+            "neighbour_lists_equal_oracle": lists_equal, "max_rel_err_vs_oracle": errs}
+
+
 def stokes_solve(ctx, n_axis=128):
     """Global solve of the Stokes system (Sec. 3.3) on an n_axis^2 grid by
     GMRES(100) with right Jacobi preconditioning (gmls_gmres), to a relative
@@ -685,6 +803,7 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stokes", action="store_true", help="skip the Stokes-system section")
+    ap.add_argument("--no-porous", action="store_true", help="skip the 3D porous-medium section")
     ap.add_argument("--n-axis", type=int, default=512, help="profiling only; the benchmark is 512")
     ap.add_argument("--serve-requests", type=int, default=60, help="serving sample size (0: skip)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
@@ -709,6 +828,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_stokes:
         out["stokes_system"] = stokes_system(ctx)
         out["stokes_system"]["solve"] = stokes_solve(ctx)
+    if rank == 0 and world == 1 and not args.no_porous:
+        out["porous_3d"], gs = porous_3d(ctx)
+        if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
+            out["porous_3d"]["oracle_check"] = porous_oracle_errors(gs)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving(args.serve_requests)
     if rank == 0:

@@ -378,7 +378,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     for (int v : generic_candidates(ld, nmax, refine)) cands.push_back(v);
     for (int c : cands) {
       float ms = time_launch(ctx, [&]() {
-        if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
+        if (refine) cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream);
         if (c < 0)
           launch_fast(js, c);
         else
@@ -396,10 +396,17 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     choice = hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_variant(ld, nmax, refine);
   }
   if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this shape");
-  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
-  if (choice < 0)
+  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  if (choice < 0) {
     CK(launch_fast(j, choice), "gmls_stencils fast launch");
-  else
+    // targets the register kernel handed off (Neumann rows, tile misfits):
+    // the shared-memory FP32 kernel, whose failures join the FP64 redo list
+    StencilJob jg = j;
+    jg.items = j.gen_items;
+    jg.n_items = j.gen_count;
+    const int vg = heuristic_variant(ld, nmax, true);
+    if (vg) CK(launch_single(ctx, jg, vg, ld, nmax, true, counter, sms), "gmls_stencils hand-off launch");
+  } else
     CK(launch_single(ctx, j, choice, ld, nmax, refine, counter, sms), "gmls_stencils launch");
   return GMLS_OK;
 }
@@ -499,7 +506,7 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
         int choice = 0;
         for (int v : generic_candidates(pl.ld[bi], pl.nmax[bi], refine)) {
           float ms = time_launch(ctx, [&]() {
-            if (refine) cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream);
+            if (refine) cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream);
             launch_single(ctx, js, v, pl.ld[bi], pl.nmax[bi], refine, counter, sms);
           });
           ctx->tune_log.push_back({key, v, ms});
@@ -533,7 +540,7 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
     release();
     return fail(ctx, GMLS_ENOMEM, "gmls_stencils: arena exhausted (global tiles)");
   }
-  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
   e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
   if (e == cudaSuccess) e = launch_stencils(L, j, pl, refine, smem, grid);
   ctx->arena.release(owned);
@@ -1018,8 +1025,8 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   int8_t* deg = p->degree_per_target ? arena_alloc<int8_t>(ctx, std::max<int64_t>(nt, 1)) : nullptr;
   const bool refine = p->precision == GMLS_FP32_REFINE;
   if (refine) {
-    s.fb_items = arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1));
-    s.fb_count = arena_alloc<int32_t>(ctx, 1);
+    s.fb_items = arena_alloc<int32_t>(ctx, 2 * std::max<int64_t>(nt, 1));  // FP64 redo list, then the
+    s.fb_count = arena_alloc<int32_t>(ctx, 2);                               // register kernel's hand-off
   }
   oom |= !s.beta || !s.status || !s.iters || (p->degree_per_target && !deg) || (refine && (!s.fb_items || !s.fb_count));
   auto release_all = [&]() {
@@ -1084,6 +1091,8 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.tol = p->refine_tol > 0.0 ? p->refine_tol : 1e-10;
   j.fb_items = s.fb_items;
   j.fb_count = s.fb_count;
+  j.gen_items = refine ? s.fb_items + std::max<int64_t>(nt, 1) : nullptr;
+  j.gen_count = refine ? s.fb_count + 1 : nullptr;
   j.ld = ld;
   j.nmax = nmax;
 

@@ -165,6 +165,8 @@ struct StencilJob {
   double tol;
   int32_t* fb_items;       // FP32 path: targets to redo in FP64
   int32_t* fb_count;
+  int32_t* gen_items;      // register kernel: targets it does not cover (Neumann
+  int32_t* gen_count;      // constraint, tile misfit), for the shared-memory FP32 kernel
   int fallback_run;        // 1: this FP64 launch redoes targets of the FP32 path
   // launch shape
   int ld;                  // tile leading dimension (>= max rows)

@@ -23,9 +23,10 @@
 //  * w = sqrt(W) s is rounded to FP64 only when stored.
 //
 // Targets this path does not cover (Neumann constraint, a basis size other
-// than the instantiation's, more rows than the tile holds, an ill-conditioned
-// FP32 factor or a refinement that misses its tolerance) are appended to the
-// redo list for the FP64 kernel.
+// than the instantiation's, more rows than the tile holds) are appended to the
+// list of the shared-memory FP32 kernel; those whose FP32 factor is
+// ill-conditioned or whose refinement misses its tolerance to the redo list
+// of the FP64 kernel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -319,10 +320,11 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
     const bool neu = j.neumann && j.bflag && j.bflag[t];
     const bool too_few = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || !(j.eps[to] > 0.0);
     if (!too_few && (neu || M > ROWS || M < N)) {
-      // not for this path: the FP64 kernel takes it (and writes every output)
+      // not for this path: the shared-memory FP32 kernel takes it (and writes
+      // every output)
       if (lane == 0) {
-        const int slot = atomicAdd(j.fb_count, 1);
-        j.fb_items[slot] = (int32_t)to;
+        const int slot = atomicAdd(j.gen_count, 1);
+        j.gen_items[slot] = (int32_t)to;
         j.status[to] = 0;
       }
       continue;
