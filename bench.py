@@ -507,7 +507,9 @@ def porous_3d(ctx, n_axis=128, steps=3, n_sample=48):
         with torch.cuda.stream(stream):
             flush.fill_(s & 0xFF)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        torch.cuda.nvtx.range_push("porous_step")  # lets a profiler select the timed launches
         h = step(ev)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
         if s < steps - 1:
@@ -574,6 +576,148 @@ def porous_oracle_errors(gs):
         errs[key] = float(np.max(a / np.where(b > 0, b, 1.0)))
     return {"sample": f"{len(sample)} targets, half drawn from the boundary, half from the interior",
             "neighbour_lists_equal_oracle": lists_equal, "max_rel_err_vs_oracle": errs}
+
+
+BASIS_SIZE = {(2, 2): 6, (2, 3): 10, (2, 4): 15, (3, 2): 10, (3, 3): 20, (3, 4): 35}
+
+
+def batched_uneven(ctx, n_per_dim=500_000, steps=3, n_sample=32):
+    """The uneven batch: a 2D and a 3D jittered cloud of n_per_dim targets
+    each, degree U{2,3,4} per target, radius lists at 1.8 x the distance of
+    the Q(d, m)-th nearest neighbour (Q the basis size, at most 160 entries),
+    20 % one-sided targets (half-space filter).  Per cloud one bucketed
+    persistent stencil launch (scalar basis; gradient and Laplacian) and the
+    gradient CSR; FP32 + refinement timed per stage over `steps` steps (L2
+    flushed before each), one FP64 step beside it."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    clouds = inputs.mixed_batch(n_per_dim)
+    stream = ctx.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=ctx.device)
+    prepared = []
+    for c in clouds:
+        d = c["dim"]
+        kpt = np.array([BASIS_SIZE[(d, int(m))] for m in c["degree"]], dtype=np.int32)
+        cid = ctx.cloud(c["x"])
+        prepared.append((c, cid, torch.from_numpy(c["halfspace"]).to(ctx.device),
+                         torch.from_numpy(kpt).to(ctx.device), torch.from_numpy(c["degree"]).to(ctx.device)))
+
+    def step(prec, ev=None):
+        rec = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
+        hs_out = []
+        rec(0)
+        for c, cid, hs, kpt, deg in prepared:
+            nid = ctx.neighbors(cid, 35 if c["dim"] == 3 else 15, 1.8, mode=gmls.RADIUS, cap=160, halfspace=hs,
+                                k_per_target=kpt)
+            hs_out.append([nid])
+        rec(1)
+        for (c, cid, hs, kpt, deg), h in zip(prepared, hs_out):
+            h.append(ctx.stencils(h[0], gmls.SCALAR, 0, [gmls.GRAD, gmls.LAPLACIAN], precision=prec,
+                                  degree_per_target=deg))
+        rec(2)
+        for h in hs_out:
+            h.append(ctx.assemble_csr(h[1], gmls.GRAD))
+        rec(3)
+        return hs_out
+
+    def release(hs_out):
+        for h in hs_out:
+            ctx.release(h[1])
+            ctx.release(h[0])
+
+    release(step(gmls.FP32_REFINE))  # warm-up: autotunes every (degree, row class) bucket
+    torch.cuda.synchronize()
+    res = {}
+    for name, prec, nsteps in (("fp32_refine", gmls.FP32_REFINE, steps), ("fp64", gmls.FP64, 1)):
+        if prec == gmls.FP64:
+            release(step(prec))  # its own warm-up (bucket choices of the FP64 kernel)
+        times = []
+        for s in range(nsteps):
+            with torch.cuda.stream(stream):
+                flush.fill_(s & 0xFF)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.nvtx.range_push("batched_step")
+            h = step(prec, ev)
+            torch.cuda.nvtx.range_pop()
+            torch.cuda.synchronize()
+            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+            if not (prec == gmls.FP32_REFINE and s == nsteps - 1):
+                release(h)
+        med = np.median(np.array(times), axis=0)
+        res[name] = {"step_ms": float(np.sum(med)), "targets_per_s": 2 * n_per_dim / float(np.sum(med)) * 1e3,
+                     "stage_ms": {"neighbours": float(med[0]), "stencils": float(med[1]), "csr": float(med[2])}}
+        if prec == gmls.FP32_REFINE:
+            keep = h
+    stats, gpu_sample = {}, []
+    for (c, cid, hs, kpt, deg), h in zip(prepared, keep):
+        d = c["dim"]
+        off = ctx.export(h[0], gmls.X_NBR_OFFSETS, torch.int64).cpu().numpy()
+        nst = ctx.export(h[0], gmls.X_NBR_STATUS, torch.uint8).cpu().numpy()
+        st = ctx.export(h[1], gmls.X_STATUS, torch.uint8).cpu().numpy()
+        cnt = np.diff(off)
+        stats[f"{d}d"] = {"neighbours_min": int(cnt.min()), "neighbours_mean": float(cnt.mean()),
+                          "neighbours_max": int(cnt.max()),
+                          "too_few_neighbours": int(np.sum((nst & gmls.T_TOO_FEW_NEIGHBOURS) != 0)),
+                          "rank_deficient": int(np.sum((st & gmls.T_RANK_DEFICIENT) != 0)),
+                          "fp64_redo": int(np.sum((st & gmls.T_FP64_FALLBACK) != 0)),
+                          "one_sided": int(c["one_sided"].sum())}
+        # GPU outputs of a sample (half one-sided) for the CPU-baseline leg's oracle check
+        ok = np.flatnonzero((nst == 0) & ((st & (gmls.T_RANK_DEFICIENT | gmls.T_UNSUPPORTED)) == 0))
+        os_ = ok[c["one_sided"][ok]]
+        ins = ok[~c["one_sided"][ok]]
+        half = n_sample // 2
+        sample = np.unique(np.concatenate([os_[(inputs.uniform(3, 90 + d, half) * len(os_)).astype(np.int64)],
+                                           ins[(inputs.uniform(3, 92 + d, half) * len(ins)).astype(np.int64)]]))
+        idx = ctx.export(h[0], gmls.X_NBR_INDEX, torch.int32).cpu().numpy()
+        wgrad = ctx.weights(h[1], gmls.GRAD).cpu().numpy()
+        lists = [idx[off[t]:off[t + 1]] for t in sample]
+        ws = [wgrad[off[t] * d:off[t + 1] * d] for t in sample]
+        gpu_sample.append({"dim": d, "x": c["x"], "degree": c["degree"], "halfspace": c["halfspace"],
+                           "sample": sample.astype(np.int32), "lists": lists, "w": ws})
+    release(keep)
+    for _, cid, _, _, _ in prepared:
+        ctx.release(cid)
+    tune = {}
+    for r in ctx.tune_log():
+        if r["bucketed"]:
+            v = r["variant"]
+            place = {0: "", 1: ", split", 2: ", global"}[v >> 3]
+            key = f"{r['dim']}d m={r['degree']} rows<={r['rows']}{' fp64' if r['precision'] == gmls.FP64 else ''}"
+            tune.setdefault(key, {})[f"{v & 7}w{place}"] = round(r["ms"], 3)
+    return {"workload": f"uneven batch: 2D and 3D jittered clouds of {n_per_dim} targets each, degree U{{2,3,4}}, "
+                        "radius lists at 1.8 x the Q(d,m)-th neighbour distance (<= 160), 20 % one-sided, "
+                        "scalar basis (gradient, Laplacian), one bucketed launch per cloud",
+            "targets": 2 * n_per_dim, **res, "speedup_vs_fp64": res["fp64"]["step_ms"] / res["fp32_refine"]["step_ms"],
+            "stats": stats, "tune_ms": tune, "l2": "flushed before each timed step (256 MB write)"}, gpu_sample
+
+
+def batched_oracle_errors(gsamples):
+    """CPU-baseline leg of the uneven batch: the oracle's radius lists and
+    gradient stencils of the sampled targets against the GPU's."""
+    import oracle
+
+    out = {}
+    for g in gsamples:
+        d, x, sample = g["dim"], g["x"], g["sample"]
+        lists_equal, worst = True, 0.0
+        for m in (2, 3, 4):
+            qs = np.flatnonzero(g["degree"][sample] == m)
+            if len(qs) == 0:
+                continue
+            tg = sample[qs]
+            hs = g["halfspace"][tg]
+            _, oe = oracle.knn(x, tg, BASIS_SIZE[(d, m)], 1.8, halfspace=hs, method="grid")
+            ooff, oidx = oracle.radius(x, tg, oe, 160, halfspace=hs, method="grid")
+            wo, _, _ = oracle.stencils(x, tg, ooff, oidx, oe, "scalar", m, "grad")
+            for r, q in enumerate(qs):
+                lists_equal &= bool(np.array_equal(oidx[ooff[r]:ooff[r + 1]], g["lists"][q]))
+                w = g["w"][q].reshape(wo[r].shape)
+                worst = max(worst, float(np.max(np.abs(w - wo[r])) / np.max(np.abs(wo[r]))))
+        out[f"{d}d"] = {"sample": f"{len(sample)} targets, half one-sided", "lists_equal_oracle": lists_equal,
+                        "max_rel_err_vs_oracle": worst}
+    return out
 
 
 def stokes_solve(ctx, n_axis=128):
@@ -804,6 +948,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stokes", action="store_true", help="skip the Stokes-system section")
     ap.add_argument("--no-porous", action="store_true", help="skip the 3D porous-medium section")
+    ap.add_argument("--porous-n-axis", type=int, default=128, help="lattice of the porous section (profiling)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch section")
+    ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
+    ap.add_argument("--only", choices=["porous", "batched"], default=None,
+                    help="profiling: run only this section (--steps timed steps) and print it")
     ap.add_argument("--n-axis", type=int, default=512, help="profiling only; the benchmark is 512")
     ap.add_argument("--serve-requests", type=int, default=60, help="serving sample size (0: skip)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
@@ -817,6 +966,18 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
+    if args.only:
+        from paper_2104_14447_gb300 import build, gmls
+
+        build.build()
+        ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
+        if args.only == "porous":
+            res = porous_3d(ctx, n_axis=args.porous_n_axis, steps=args.steps)[0]
+        else:
+            res = batched_uneven(ctx, n_per_dim=args.batched_n, steps=args.steps)[0]
+        print(json.dumps(res), flush=True)
+        ctx.close()
+        return
     if world > 1:
         import torch
 
@@ -829,9 +990,13 @@ def main():
         out["stokes_system"] = stokes_system(ctx)
         out["stokes_system"]["solve"] = stokes_solve(ctx)
     if rank == 0 and world == 1 and not args.no_porous:
-        out["porous_3d"], gs = porous_3d(ctx)
+        out["porous_3d"], gs = porous_3d(ctx, n_axis=args.porous_n_axis)
         if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
             out["porous_3d"]["oracle_check"] = porous_oracle_errors(gs)
+    if rank == 0 and world == 1 and not args.no_batched:
+        out["batched_uneven"], gsb = batched_uneven(ctx, n_per_dim=args.batched_n)
+        if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
+            out["batched_uneven"]["oracle_check"] = batched_oracle_errors(gsb)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving(args.serve_requests)
     if rank == 0:

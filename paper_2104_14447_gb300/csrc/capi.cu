@@ -404,8 +404,11 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     StencilJob jg = j;
     jg.items = j.gen_items;
     jg.n_items = j.gen_count;
+    // (with uniform neighbour counts only Neumann rows or a tile with fewer
+    // rows than basis functions are handed off)
     const int vg = heuristic_variant(ld, nmax, true);
-    if (vg) CK(launch_single(ctx, jg, vg, ld, nmax, true, counter, sms), "gmls_stencils hand-off launch");
+    if (vg && (p->neumann || ld < nmax))
+      CK(launch_single(ctx, jg, vg, ld, nmax, true, counter, sms), "gmls_stencils hand-off launch");
   } else
     CK(launch_single(ctx, j, choice, ld, nmax, refine, counter, sms), "gmls_stencils launch");
   return GMLS_OK;

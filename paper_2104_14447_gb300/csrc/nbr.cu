@@ -440,10 +440,16 @@ __device__ int gather_exact(const CloudDev& cl, const GridParams& g, const int* 
 // the FP64 pipe sees about the ball's share of the box.  If the survivors do
 // not fit the buffer the box is searched again with exact distances only.
 // Returns the number that passed (may exceed wb.cap: overflow).
+// The half-space filter is applied in the FP32 pass too (kept side
+// n . dx <= 0): with unit-roundoff u = 2^-24, the float coordinates, their
+// difference, the float normal and the float dot product together err by at
+// most |n|_1 2^-23 (max_c |x_T,c| + 4 Rbox), so the pass keeps every particle
+// whose float dot product is at most 8 times that bound (hs_scale is
+// |n|_1 2^-20) and the exact test decides.
 template <int D>
 __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const QueryGeo& gq, const double* xT,
                                  const float* xTf, float Rbox, double R2, bool use_hs, const double* nrm,
-                                 WarpBuf& wb) {
+                                 const float* nrmf, float hs_scale, WarpBuf& wb) {
   const int lane = threadIdx.x & 31;
   constexpr int dim = D;
   int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -452,6 +458,9 @@ __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const 
   const int nrows = ny * (hi[2] - lo[2] + 1);
   float bf = Rbox + gq.e2;
   bf = bf * bf * (1.0f + 0x1p-19f);
+  float xmax = 0.0f;
+  for (int c = 0; c < dim; ++c) xmax = fmaxf(xmax, fabsf(xTf[c]));
+  const float hs_tol = hs_scale * (xmax + 4.0f * Rbox);
   // pass 1: FP32 pre-filter, positions of the survivors into wb.id
   int staged = 0;
   for (int r0 = 0; r0 < nrows; r0 += 32) {
@@ -462,12 +471,13 @@ __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const 
       int32_t pos = 0;
       if (p < total) {
         pos = (int32_t)row_position(wb, p);
-        float d2f = 0.0f;
+        float d2f = 0.0f, dotf = 0.0f;
         for (int c = 0; c < dim; ++c) {
           const float dxf = cl.xsf[c * cl.n + pos] - xTf[c];
           d2f = fmaf(dxf, dxf, d2f);
+          dotf = fmaf(nrmf[c], dxf, dotf);
         }
-        pass = d2f <= bf;
+        pass = d2f <= bf && (!use_hs || dotf <= hs_tol);
       }
       unsigned m = __ballot_sync(0xffffffffu, pass);
       if (pass) {
@@ -555,9 +565,19 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
   const double ball = (dim == 1) ? 2.0 : (dim == 2) ? 3.141592653589793 : 4.1887902047863905;
   const double dens = (double)cl.n / (g.volume > 0.0 ? g.volume : 1.0);
   const float inv_dens_ball = (float)(1.0 / (dens * ball));
-  double span = 0.0;
-  for (int c = 0; c < dim; ++c) span += g.h[c] * g.nc[c];
-  const float big = __double2float_ru(2.0 * span + 1.0);
+  // no two points of the grid box are farther apart than the sum of its
+  // extents: a search radius above it has seen every particle
+  double span = 0.0, ext_min = 1e300;
+  for (int c = 0; c < dim; ++c) {
+    span += g.h[c] * g.nc[c];
+    ext_min = fmin(ext_min, g.h[c] * g.nc[c]);
+  }
+  const float big = __double2float_ru(1.001 * span + 1e-30);
+  // a search that still lacks neighbours once its box spans half the grid in
+  // some direction goes straight to the whole grid (one more pass, not a
+  // chain of ever larger boxes -- targets whose kept half-space holds too few
+  // particles would otherwise rescan most of the cloud several times)
+  const float jump = (float)(0.25 * ext_min);
   for (int64_t to = blockIdx.x * (int64_t)kQueryWarps + (threadIdx.x >> 5); to < q.n_tgt;
        to += (int64_t)gridDim.x * kQueryWarps) {
     const int64_t t = q.tgt ? q.tgt[to] : to;
@@ -568,11 +588,15 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
       xTf[c] = cl.xh ? cl.xh[c * cl.n + t] : __double2float_rn(xT[c]);
     }
     bool use_hs = false;
+    float nrmf[3] = {0.0f, 0.0f, 0.0f}, hs_scale = 0.0f;
     if (q.halfspace) {
       for (int c = 0; c < dim; ++c) {
         nrm[c] = q.halfspace[to * dim + c];
         use_hs |= (nrm[c] != 0.0);
+        nrmf[c] = __double2float_rn(nrm[c]);
+        hs_scale += fabsf(nrmf[c]);
       }
+      hs_scale *= 0x1p-20f * 1.0001f;
     }
     uint8_t st = GMLS_T_OK;
     int kq = q.k_pt ? q.k_pt[to] : q.k;  // per-target k is clamped to 1..cap
@@ -582,16 +606,24 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     // box half-width R (1 + 2^-20) covers sqrt(R2)
     float R = powf(1.2f * (float)kq * inv_dens_ball, 1.0f / (float)dim);
     int count = 0;
+    float r_lo = 0.0f, r_hi = INFINITY;  // radii known to give too few / too many
     for (int attempt = 0; attempt < 64; ++attempt) {
-      count = gather_candidates<D>(cl, g, gq, xT, xTf, R * (1.0f + 0x1p-20f), (double)(R * R), use_hs, nrm, wb);
-      // rescale R by the count it gave (ball volume ~ R^dim), within bounds
+      count = gather_candidates<D>(cl, g, gq, xT, xTf, R * (1.0f + 0x1p-20f), (double)(R * R), use_hs, nrm, nrmf,
+                                   hs_scale, wb);
+      // rescale R by the count it gave (ball volume ~ R^dim), within bounds,
+      // and inside the bracket (r_lo, r_hi) the earlier attempts established
       if (count > wb.cap) {
+        r_hi = R;
         R *= fmaxf(0.5f, fminf(0.9f, powf(0.8f * (float)wb.cap / (float)count, 1.0f / (float)dim)));
+        if (R <= r_lo) R = 0.5f * (r_lo + r_hi);
         continue;
       }
       if (count >= kq) break;
       if (R > big) break;  // whole cloud inside: too few exist
+      r_lo = R;
       R *= (count > 0) ? fminf(2.0f, fmaxf(1.1f, powf(1.3f * (float)kq / (float)count, 1.0f / (float)dim))) : 2.0f;
+      if (R > jump) R = fmaxf(R, big * 1.001f);
+      if (R >= r_hi) R = 0.5f * (r_lo + r_hi);
     }
     if (count > wb.cap) {  // could not bring the candidate set under the buffer size
       st |= GMLS_T_OVERFLOW;
@@ -612,7 +644,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
       if (kk == kq) {
         __syncwarp();
         count = gather_candidates<D>(cl, g, gq, xT, xTf, __double2float_ru(eps) * (1.0f + 0x1p-20f),
-                                  __dmul_rn(eps, eps), use_hs, nrm, wb);
+                                     __dmul_rn(eps, eps), use_hs, nrm, nrmf, hs_scale, wb);
         if (count > wb.cap) {
           st |= GMLS_T_OVERFLOW;
           count = wb.cap;
