@@ -297,21 +297,27 @@ static bool capturing(gmls_ctx* ctx) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
-// time one launch on the context stream (ms), for the autotuner
+// time a launch on the context stream (ms), for the autotuner: one warm-up,
+// then the faster of two timed runs
 template <typename F>
 static float time_launch(gmls_ctx* ctx, F&& launch) {
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
+  cudaEvent_t ev[3];
+  for (auto& e : ev) cudaEventCreate(&e);
   launch();  // warm
-  cudaEventRecord(a, ctx->stream);
+  cudaEventRecord(ev[0], ctx->stream);
   launch();
-  cudaEventRecord(b, ctx->stream);
-  cudaEventSynchronize(b);
+  cudaEventRecord(ev[1], ctx->stream);
+  launch();
+  cudaEventRecord(ev[2], ctx->stream);
+  cudaEventSynchronize(ev[2]);
   float ms = 1e30f;
-  if (cudaGetLastError() == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  if (cudaGetLastError() == cudaSuccess) {
+    float t0 = 1e30f, t1 = 1e30f;
+    cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    ms = std::min(t0, t1);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
   return ms;
 }
 
@@ -499,7 +505,11 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
       for (int rc = 0; rc < b.n_classes; ++rc) {
         const int bi = (m - 1) * b.n_classes + rc;
         const TuneKey key{p->basis, dim, m, p->precision, b.class_rows[rc], j.L, p->neumann, 1};
-        if (ctx->tune.count(key) || cnt[bi] == 0) continue;
+        if (ctx->tune.count(key)) continue;
+        if (cnt[bi] == 0) {  // nothing to time: keep the heuristic (later calls skip this pass)
+          ctx->tune[key] = heuristic_variant(b.class_rows[rc], gmls_gen::basis_size(p->basis, dim, m), refine);
+          continue;
+        }
         const int32_t ns = std::min<int32_t>(cnt[bi], 4096);
         cudaMemcpyAsync(nsample, &ns, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
         StencilJob js = j;

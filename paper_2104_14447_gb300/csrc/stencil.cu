@@ -341,7 +341,7 @@ __device__ __forceinline__ void warp_sum_halving(T (&s)[Q], int lane) {
 }
 
 // QC columns per warp pass (fewer for FP64: twice the registers per element)
-template <typename TQ, int RPL, int QC = (sizeof(TQ) == 8 ? 2 : kQrCols)>
+template <typename TQ, int RPL, int QC = (sizeof(TQ) == 8 ? (RPL >= 16 ? 1 : 2) : kQrCols)>
 __device__ void tile_qr_rows(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
   for (int k = 0; k < n; ++k) {
     TQ* a = A + k * ld;
@@ -643,7 +643,7 @@ __device__ void solve_r_regs(const Group& g, const TQ* A, int ld, int n, int L, 
 constexpr int kSolveNpl = 3;   // register solves for up to 96 basis functions
 constexpr int kQrRegCols = 13;  // register QR: up to 52 columns over four warps
 
-// dispatch on the tile's rows: register-chunked up to 256 rows, else the loops
+// dispatch on the tile's rows: register-chunked up to 512 rows, else the loops
 template <typename TQ>
 __device__ void qr_any(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
   if (M <= 64)
@@ -652,6 +652,8 @@ __device__ void qr_any(const Group& g, TQ* A, int ld, int M, int n, TQ* tau) {
     tile_qr_rows<TQ, 4>(g, A, ld, M, n, tau);
   else if (M <= 256)
     tile_qr_rows<TQ, 8>(g, A, ld, M, n, tau);
+  else if (M <= 512)
+    tile_qr_rows<TQ, 16>(g, A, ld, M, n, tau);
   else
     tile_qr<TQ>(g, A, ld, M, n, tau);
 }
@@ -663,6 +665,8 @@ __device__ void apply_q_any(const Group& g, const TQ* A, int ld, int M, int n, c
     apply_q_rows<TQ, TRANS, 4>(g, A, ld, M, n, tau, L, z);
   else if (M <= 256)
     apply_q_rows<TQ, TRANS, 8>(g, A, ld, M, n, tau, L, z);
+  else if (M <= 512)
+    apply_q_rows<TQ, TRANS, 16>(g, A, ld, M, n, tau, L, z);
   else
     apply_q<TQ, TRANS>(g, A, ld, M, n, tau, L, z);
 }
