@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 N_AXIS = 512
 K_SCALAR, K_DIVFREE, EPS_FACTOR, DEGREE = 36, 48, 1.5, 4
+E2E_CHUNKS = 4  # target ranges of the end-to-end pipeline (copies overlap compute)
 METRIC = "GMLS targets/sec"
 WORKLOAD = "stokes2d-512x512: scalar m=4 (36 nbrs; grad, div) + div-free m=4 (48 nbrs; vector Laplacian) + CSR"
 
@@ -230,36 +231,63 @@ def run_ours(args, rank, world, local_rank):
     x_pin = torch.from_numpy(x_host).pin_memory()
     host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
     d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v)
+    d2h += 8 * 3 * (E2E_CHUNKS - 1)  # the row pointer shared by two ranges goes back twice
     h2d = x_pin.numel() * x_pin.element_size()
-    # The operators go back to the host on two copy streams while the GPU
-    # computes the rest: the divergence-free stencils and their CSR first,
-    # their copy overlapping the scalar stencils; the two scalar operators
-    # (the smaller ones) last.
+    # The targets are processed in E2E_CHUNKS contiguous ranges so that the
+    # operators of the first ranges travel to the host (on two copy streams)
+    # while the GPU computes the rest: per range the 48-nearest lists, the
+    # divergence-free stencils and their CSR rows; then per range the
+    # 36-nearest prefix lists, the scalar stencils and the gradient and
+    # divergence CSR rows.  Each range writes its rows in place in the
+    # operator (gmls_assemble_csr_at), so the host receives the operators
+    # themselves.
     copy_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    bounds = [n * c // E2E_CHUNKS for c in range(E2E_CHUNKS + 1)]
+    chunk_tg = [torch.arange(a, b, dtype=torch.int32, device=dev) for a, b in zip(bounds[:-1], bounds[1:])]
+    per_target = {"vl": (2, K_DIVFREE * 2), "grad": (2, K_SCALAR), "div": (1, K_SCALAR * 2)}  # rows, nnz per row
+
+    def chunk_views(kname, c):
+        """(device views, host views, nonzero offset) of range c's rows."""
+        rows, per_row = per_target[kname]
+        a, b = bounds[c], bounds[c + 1]
+        lo, hi = a * rows * per_row, b * rows * per_row
+        rp, col, val = bufs[kname]
+        hrp, hcol, hval = host_out[kname]
+        sl_r, sl_n = slice(a * rows, b * rows + 1), slice(lo, hi)
+        return (rp[sl_r], col[sl_n], val[sl_n]), (hrp[sl_r], hcol[sl_n], hval[sl_n]), lo
+
+    def assemble_and_ship(sid, fn, kname, c, which):
+        dev_out, host_dst, lo = chunk_views(kname, c)
+        ctx.assemble_csr(sid, fn, out=dev_out, nnz_offset=lo)
+        done = torch.cuda.Event()
+        done.record(stream)
+        cs = copy_streams[which]
+        cs.wait_event(done)
+        with torch.cuda.stream(cs):
+            for dst, src in zip(host_dst, dev_out):
+                dst.copy_(src, non_blocking=True)
 
     def step_e2e(x_src):
         cid = ctx.cloud(x_src)
-        n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR)
-        n36 = ctx.neighbors_prefix(n48, K_SCALAR, EPS_FACTOR)
-        s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
-        ctx.assemble_csr(s_df, gmls.VEC_LAPLACIAN, out=bufs["vl"])
-        done_vl = torch.cuda.Event()
-        done_vl.record(stream)
-        s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
-        ctx.assemble_csr(s_sc, gmls.GRAD, out=bufs["grad"])
-        done_grad = torch.cuda.Event()
-        done_grad.record(stream)
-        ctx.assemble_csr(s_sc, gmls.DIV, out=bufs["div"])
-        done_div = torch.cuda.Event()
-        done_div.record(stream)
-        for cs, ev_done, names in ((copy_streams[0], done_vl, ("vl",)), (copy_streams[1], done_grad, ("grad",)),
-                                   (copy_streams[0], done_div, ("div",))):
-            cs.wait_event(ev_done)
-            with torch.cuda.stream(cs):
-                for kname in names:
-                    for dst, src in zip(host_out[kname], bufs[kname]):
-                        dst.copy_(src, non_blocking=True)
-        return cid, n48, n36, s_df, s_sc
+        ids = [cid]
+        n48s = []
+        for c in range(E2E_CHUNKS):
+            n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR, targets=chunk_tg[c])
+            s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
+            assemble_and_ship(s_df, gmls.VEC_LAPLACIAN, "vl", c, c & 1)
+            n48s.append(n48)
+            ids += [n48, s_df]
+        for c in range(E2E_CHUNKS):
+            n36 = ctx.neighbors_prefix(n48s[c], K_SCALAR, EPS_FACTOR)
+            s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
+            assemble_and_ship(s_sc, gmls.GRAD, "grad", c, c & 1)
+            assemble_and_ship(s_sc, gmls.DIV, "div", c, (c + 1) & 1)
+            ids += [n36, s_sc]
+        return ids
+
+    def release_e2e(ids):
+        for h in reversed(ids):
+            ctx.release(h)
 
     e2e_ms = []
     for s in range(max(2, min(args.steps, 5)) + 1):
@@ -269,8 +297,13 @@ def run_ours(args, rank, world, local_rank):
         ids = step_e2e(x_pin)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        release(ids)
+        release_e2e(ids)
     e2e_ms = e2e_ms[1:]
+    # the host operators equal the device step's (checked once, untimed)
+    ids = step(x_dev)
+    torch.cuda.synchronize()
+    e2e_equal = all(torch.equal(h, d.cpu()) for k in bufs for h, d in zip(host_out[k], bufs[k]))
+    release(ids)
 
     # roofline of the dominant kernel (the divergence-free stencil launch)
     M_df, n_df, rows_df = K_DIVFREE * 2, 20, 2
@@ -358,7 +391,8 @@ def run_ours(args, rank, world, local_rank):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": n * world / (float(np.mean(e2e_ms)) * 1e-3), "unit": "targets/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.mean(e2e_ms))},
+                "ms_per_step": float(np.mean(e2e_ms)), "target_ranges": E2E_CHUNKS,
+                "host_operators_equal_device_step": e2e_equal},
         "gpu_launches": int(launches),
         "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
         "roofline": roofline,

@@ -222,6 +222,19 @@ gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functio
                               double* val);
 
 /*
+ * As gmls_assemble_csr, with nnz_offset (>= 0) added to every row pointer.
+ * For an operator assembled in target ranges (one neighbour handle per
+ * contiguous range of targets, in order): pass row_ptr + the range's first
+ * operator row, col + nnz_offset and val + nnz_offset, nnz_offset being the
+ * nonzeros of the ranges before it.  The last row pointer a range writes is
+ * the first of the next range (the same value).  For a handle without
+ * targets only row_ptr[0] is written and col / val may be NULL.
+ * Asynchronous; GMLS_EINVAL for a negative offset.
+ */
+gmls_status gmls_assemble_csr_at(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t nnz_offset,
+                                 int64_t* row_ptr, int32_t* col, double* val);
+
+/*
  * Stokes collocation system (Sec. 3.2, Eq. stokes-block-system) of the
  * problem of Sec. 3.1 (nu curl curl v + grad phi = f in the interior,
  * v = w on the boundary, Laplacian phi = div f with the Neumann condition

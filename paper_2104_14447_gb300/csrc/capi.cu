@@ -1205,24 +1205,31 @@ gmls_status gmls_csr_size(gmls_ctx* ctx, int64_t stencil_id, int32_t functional,
   return GMLS_OK;
 }
 
-gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t* row_ptr, int32_t* col,
-                              double* val) {
+gmls_status gmls_assemble_csr_at(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t nnz_offset,
+                                 int64_t* row_ptr, int32_t* col, double* val) {
   if (!ctx) return GMLS_EINVAL;
   auto it = ctx->objs.find(stencil_id);
   if (it == ctx->objs.end() || it->second.kind != K_STENCIL) return fail(ctx, GMLS_ENOTFOUND, "gmls_assemble_csr: no such stencil handle");
-  if (!row_ptr || !col || !val) return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: NULL output");
+  if (nnz_offset < 0) return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr_at: negative nnz_offset");
   StencilObj& s = it->second.s;
   int f = find_out(s, functional);
   if (f < 0) return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: functional not computed");
-  if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val))
-    return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: outputs must be device buffers");
   NbrObj& nb = ctx->objs.at(s.nbrs).nb;
+  // col and val may be NULL for a handle without targets (nothing is written there)
+  if (!row_ptr || (nb.n_tgt > 0 && (!col || !val))) return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: NULL output");
+  if (is_host_ptr(row_ptr) || (col && is_host_ptr(col)) || (val && is_host_ptr(val)))
+    return fail(ctx, GMLS_EINVAL, "gmls_assemble_csr: outputs must be device buffers");
   CK(cudaSetDevice(ctx->device), "gmls_assemble_csr");
   gmls_status r = ensure_order(ctx, nb, "gmls_assemble_csr");
   if (r) return r;
-  CsrJob j{nb.order, nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val};
+  CsrJob j{nb.order, nb.n_tgt, nb.off, nb.idx, s.w[f], s.rows[f], s.ncomp[f], row_ptr, col, val, nnz_offset};
   CK(launch_csr(ctx->launch(), j), "gmls_assemble_csr");
   return GMLS_OK;
+}
+
+gmls_status gmls_assemble_csr(gmls_ctx* ctx, int64_t stencil_id, int32_t functional, int64_t* row_ptr, int32_t* col,
+                              double* val) {
+  return gmls_assemble_csr_at(ctx, stencil_id, functional, 0, row_ptr, col, val);
 }
 
 // ------------------------------------------------------------ Stokes system

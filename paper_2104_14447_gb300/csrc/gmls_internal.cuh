@@ -243,6 +243,7 @@ struct CsrJob {
   int64_t* row_ptr;
   int32_t* col;
   double* val;
+  int64_t nnz_base;  // added to every row pointer (ranges of one larger operator)
 };
 cudaError_t launch_csr(const Launch& L, const CsrJob& j);
 

@@ -1396,7 +1396,7 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
     for (int r = 0; r < j.rows; ++r) {
       const int64_t row = t * j.rows + r;
       const int64_t start = base + (int64_t)r * rowlen;
-      if (lane == 0) j.row_ptr[row] = start;
+      if (lane == 0) j.row_ptr[row] = j.nnz_base + start;
       const double* wr = j.w + start;
       for (int e = lane; e < rowlen; e += 32) {
         const int q = e / C, c = e - q * C;
@@ -1405,13 +1405,17 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
         j.val[start + e] = wr[p * C + c];
       }
     }
-    if (t == j.n_tgt - 1 && lane == 0) j.row_ptr[j.n_tgt * j.rows] = base + (int64_t)j.rows * rowlen;
+    if (t == j.n_tgt - 1 && lane == 0) j.row_ptr[j.n_tgt * j.rows] = j.nnz_base + base + (int64_t)j.rows * rowlen;
   }
 }
 
+// row_ptr[0] of an operator with no rows
+__global__ void csr_empty_kernel(int64_t* row_ptr, int64_t nnz_base) { row_ptr[0] = nnz_base; }
+
 cudaError_t launch_csr(const Launch& L, const CsrJob& j) {
   if (j.n_tgt == 0) {
-    cudaMemsetAsync(j.row_ptr, 0, sizeof(int64_t), L.stream);
+    csr_empty_kernel<<<1, 1, 0, L.stream>>>(j.row_ptr, j.nnz_base);
+    *L.counter += 1;
     return cudaGetLastError();
   }
   int64_t blocks = (j.n_tgt + kCsrWarps - 1) / kCsrWarps;

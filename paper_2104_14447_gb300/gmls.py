@@ -37,7 +37,7 @@ X_NBR_OFFSETS, X_NBR_INDEX, X_NBR_EPS, X_NBR_STATUS, X_WEIGHTS, X_BETA, X_STATUS
 EXPORTED = [
     "gmls_create", "gmls_destroy", "gmls_set_stream", "gmls_cloud", "gmls_neighbors", "gmls_neighbors_prefix",
     "gmls_stencils",
-    "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_export", "gmls_export_size", "gmls_release",
+    "gmls_stencil_info", "gmls_csr_size", "gmls_assemble_csr", "gmls_assemble_csr_at", "gmls_export", "gmls_export_size", "gmls_release",
     "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
     "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
     "gmls_server_create", "gmls_server_submit", "gmls_server_wait", "gmls_server_result", "gmls_server_release",
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "gmls_stencil_info": [vp, i64, i32, P64, ctypes.POINTER(i32), ctypes.POINTER(i32), P64],
         "gmls_csr_size": [vp, i64, i32, P64, P64, P64],
         "gmls_assemble_csr": [vp, i64, i32, vp, vp, vp],
+        "gmls_assemble_csr_at": [vp, i64, i32, i64, vp, vp, vp],
         "gmls_export": [vp, i64, i32, i32, vp, sz],
         "gmls_export_size": [vp, i64, i32, i32, ctypes.POINTER(sz)],
         "gmls_release": [vp, i64],
@@ -266,15 +267,18 @@ class Context:
                                            ctypes.byref(z)))
         return r.value, c.value, z.value
 
-    def assemble_csr(self, sid: int, functional: int, out=None):
-        """CSR of one operator into torch device tensors (row_ptr, col, val)."""
+    def assemble_csr(self, sid: int, functional: int, out=None, nnz_offset: int = 0):
+        """CSR of one operator into torch device tensors (row_ptr, col, val);
+        with nnz_offset, the rows of a target range of a larger operator
+        (gmls_assemble_csr_at: out = views at the range's first row / nonzero)."""
         if out is None:
             nr, _, nnz = self.csr_size(sid, functional)
             out = (torch.empty(nr + 1, dtype=torch.int64, device=self.device),
                    torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device),
                    torch.empty(max(nnz, 1), dtype=torch.float64, device=self.device))
         rp, col, val = out
-        self._check(self.lib.gmls_assemble_csr(self.h, sid, functional, _ptr(rp), _ptr(col), _ptr(val)))
+        self._check(self.lib.gmls_assemble_csr_at(self.h, sid, functional, nnz_offset, _ptr(rp), _ptr(col),
+                                                  _ptr(val)))
         return out
 
     # ------------------------------------------------------- Stokes system

@@ -251,6 +251,39 @@ def test_csr_structure_bit_exact(ctx, basis, m, k, fn):
     _release(ctx, cid, nid, sid)
 
 
+def test_csr_assembled_in_target_ranges(ctx):
+    """gmls_assemble_csr_at: an operator assembled range by range (one
+    neighbour handle per contiguous target range, uneven range sizes, radius
+    lists) equals the operator assembled at once, bit for bit."""
+    x = inputs.jittered_grid(2, 28, seed=4)
+    n = x.shape[1]
+    cid = ctx.cloud(x)
+    whole = ctx.neighbors(cid, 12, 1.6, mode=gmls.RADIUS, cap=40)
+    sw = ctx.stencils(whole, gmls.SCALAR, 2, [gmls.GRAD])
+    rp, col, val = (t.cpu().numpy() for t in ctx.assemble_csr(sw, gmls.GRAD))
+    out = (torch.full((len(rp),), -7, dtype=torch.int64, device=ctx.device),
+           torch.full((len(col),), -7, dtype=torch.int32, device=ctx.device),
+           torch.full((len(val),), -7.0, dtype=torch.float64, device=ctx.device))
+    bounds = [0, 1, 300, 300, 301, 560, n]  # includes an empty range
+    nnz = 0
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        tg = torch.arange(a, b, dtype=torch.int32, device=ctx.device)
+        nid = ctx.neighbors(cid, 12, 1.6, mode=gmls.RADIUS, cap=40, targets=tg)
+        sid = ctx.stencils(nid, gmls.SCALAR, 2, [gmls.GRAD])
+        _, _, z = ctx.csr_size(sid, gmls.GRAD)
+        ctx.assemble_csr(sid, gmls.GRAD, out=(out[0][2 * a:2 * b + 1], out[1][nnz:nnz + z], out[2][nnz:nnz + z]),
+                         nnz_offset=nnz)
+        nnz += z
+        _release(ctx, nid, sid)
+    assert nnz == len(col)
+    assert np.array_equal(out[0].cpu().numpy(), rp)
+    assert np.array_equal(out[1].cpu().numpy(), col) and np.array_equal(out[2].cpu().numpy(), val)
+    with pytest.raises(gmls.GmlsError) as e:
+        ctx.assemble_csr(sw, gmls.GRAD, out=out, nnz_offset=-1)
+    assert e.value.code == gmls.EINVAL
+    _release(ctx, cid, whole, sw)
+
+
 # ----------------------------------------------------- full-size configuration
 def test_full_size_512x512_sampled(ctx):
     """The benchmark's workload (262,144 targets on a 512 x 512 jittered grid,
