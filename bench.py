@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 N_AXIS = 512
 K_SCALAR, K_DIVFREE, EPS_FACTOR, DEGREE = 36, 48, 1.5, 4
-E2E_CHUNKS = 4  # target ranges of the end-to-end pipeline (copies overlap compute)
+E2E_CHUNKS = 4  # default target ranges of the end-to-end pipeline (copies overlap compute)
 METRIC = "GMLS targets/sec"
 WORKLOAD = "stokes2d-512x512: scalar m=4 (36 nbrs; grad, div) + div-free m=4 (48 nbrs; vector Laplacian) + CSR"
 
@@ -231,9 +231,9 @@ def run_ours(args, rank, world, local_rank):
     x_pin = torch.from_numpy(x_host).pin_memory()
     host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
     d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v)
-    d2h += 8 * 3 * (E2E_CHUNKS - 1)  # the row pointer shared by two ranges goes back twice
+    d2h += 8 * 3 * (args.e2e_ranges - 1)  # the row pointer shared by two ranges goes back twice
     h2d = x_pin.numel() * x_pin.element_size()
-    # The targets are processed in E2E_CHUNKS contiguous ranges so that the
+    # The targets are processed in --e2e-ranges contiguous ranges so that the
     # operators of the first ranges travel to the host (on two copy streams)
     # while the GPU computes the rest: per range the 48-nearest lists, the
     # divergence-free stencils and their CSR rows; then per range the
@@ -242,7 +242,8 @@ def run_ours(args, rank, world, local_rank):
     # operator (gmls_assemble_csr_at), so the host receives the operators
     # themselves.
     copy_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    bounds = [n * c // E2E_CHUNKS for c in range(E2E_CHUNKS + 1)]
+    n_ranges = args.e2e_ranges
+    bounds = [n * c // n_ranges for c in range(n_ranges + 1)]
     chunk_tg = [torch.arange(a, b, dtype=torch.int32, device=dev) for a, b in zip(bounds[:-1], bounds[1:])]
     per_target = {"vl": (2, K_DIVFREE * 2), "grad": (2, K_SCALAR), "div": (1, K_SCALAR * 2)}  # rows, nnz per row
 
@@ -271,13 +272,13 @@ def run_ours(args, rank, world, local_rank):
         cid = ctx.cloud(x_src)
         ids = [cid]
         n48s = []
-        for c in range(E2E_CHUNKS):
+        for c in range(n_ranges):
             n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR, targets=chunk_tg[c])
             s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
             assemble_and_ship(s_df, gmls.VEC_LAPLACIAN, "vl", c, c & 1)
             n48s.append(n48)
             ids += [n48, s_df]
-        for c in range(E2E_CHUNKS):
+        for c in range(n_ranges):
             n36 = ctx.neighbors_prefix(n48s[c], K_SCALAR, EPS_FACTOR)
             s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
             assemble_and_ship(s_sc, gmls.GRAD, "grad", c, c & 1)
@@ -391,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": n * world / (float(np.mean(e2e_ms)) * 1e-3), "unit": "targets/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.mean(e2e_ms)), "target_ranges": E2E_CHUNKS,
+                "ms_per_step": float(np.mean(e2e_ms)), "target_ranges": args.e2e_ranges,
                 "host_operators_equal_device_step": e2e_equal},
         "gpu_launches": int(launches),
         "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
@@ -984,6 +985,7 @@ def main():
     ap.add_argument("--no-porous", action="store_true", help="skip the 3D porous-medium section")
     ap.add_argument("--porous-n-axis", type=int, default=128, help="lattice of the porous section (profiling)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch section")
+    ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipeline")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
     ap.add_argument("--only", choices=["porous", "batched"], default=None,
                     help="profiling: run only this section (--steps timed steps) and print it")
