@@ -134,7 +134,7 @@ CASES = [
     (2, 24, gmls.DIVFREE, 2, 22, [gmls.VEC_LAPLACIAN]),
     (3, 12, gmls.SCALAR, 3, 40, [gmls.GRAD, gmls.LAPLACIAN]),
     (3, 12, gmls.DIVFREE, 3, 80, [gmls.VEC_LAPLACIAN]),
-    (3, 9, gmls.SCALAR, 4, 84, [gmls.LAPLACIAN]),
+    (3, 9, gmls.SCALAR, 4, 84, [gmls.GRAD, gmls.LAPLACIAN]),
     (3, 9, gmls.DIVFREE, 2, 42, [gmls.CURLCURL]),
     (3, 9, gmls.DIVFREE, 4, 136, [gmls.VEC_LAPLACIAN]),  # 408 x 85: tiles in global memory
 ]
