@@ -291,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
             ctx.release(h)
 
     e2e_ms = []
-    for s in range(max(2, min(args.steps, 5)) + 1):
+    for s in range(max(3, min(args.steps, 7)) + 1):
         flush.fill_(s & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -390,9 +390,9 @@ def run_ours(args, rank, world, local_rank):
                    "weight": "(1-r/eps)_+^4", "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"independent replicas x{world}" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "e2e": {"value": n * world / (float(np.mean(e2e_ms)) * 1e-3), "unit": "targets/s",
+        "e2e": {"value": n * world / (float(np.median(e2e_ms)) * 1e-3), "unit": "targets/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.mean(e2e_ms)), "target_ranges": args.e2e_ranges,
+                "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms], "target_ranges": args.e2e_ranges,
                 "host_operators_equal_device_step": e2e_equal},
         "gpu_launches": int(launches),
         "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
@@ -491,6 +491,64 @@ def stokes_system(ctx, steps=5):
             "residual_max": {"momentum_interior": float(mom[~bf].max()), "pressure_interior": float(pr[~bf].max()),
                              "pressure_boundary": float(pr[bf].max()), "dirichlet": float(mom[bf].max())},
             "l2": "flushed before each timed step (256 MB write)"}
+
+
+def shapes(ctx):
+    """Stencil stage of every (dimension, basis, degree) shape the serving
+    stream draws, on one cloud per dimension (2D: 400 x 400 jittered grid,
+    160,000 targets; 3D: 50^3, 125,000), FP32 + refinement against plain
+    FP64 (the same launch path with GMLS_FP64), CUDA events around one
+    gmls_stencils call after a warm-up call; the kernel variant the
+    autotuner chose for the FP32 path."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    out = {}
+    for dim, n_axis in ((2, 400), (3, 50)):
+        x = inputs.jittered_grid(dim, n_axis, seed=1)
+        n = x.shape[1]
+        cid = ctx.cloud(x)
+        for (d, b, m), k in SERVE_K.items():
+            if d != dim:
+                continue
+            fns = [gmls.GRAD, gmls.LAPLACIAN] if b == gmls.SCALAR else [gmls.VEC_LAPLACIAN]
+            nid = ctx.neighbors(cid, k, EPS_FACTOR)
+            ms = {}
+            for name, prec in (("fp32_refine", gmls.FP32_REFINE), ("fp64", gmls.FP64)):
+                ctx.release(ctx.stencils(nid, b, m, fns, precision=prec))  # warm-up / autotune
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ctx.stream)
+                sid = ctx.stencils(nid, b, m, fns, precision=prec)
+                e1.record(ctx.stream)
+                torch.cuda.synchronize()
+                ms[name] = e0.elapsed_time(e1)
+                ctx.release(sid)
+            ctx.release(nid)
+            rows = k * (1 if b == gmls.SCALAR else d)
+            tl = [r for r in ctx.tune_log() if r["dim"] == d and r["basis"] == b and r["degree"] == m
+                  and r["precision"] == gmls.FP32_REFINE and r["rows"] == rows and not r["bucketed"]]
+            v = min(tl, key=lambda r: r["ms"])["variant"] if tl else None
+            name = None if v is None else ({-1: "register", -2: "register 16 lanes"}.get(v) or
+                                           f"{v & 7} warp(s)/target" + {0: "", 1: ", split tiles",
+                                                                        2: ", global tiles"}[v >> 3])
+            key = f"{d}d {'scalar' if b == gmls.SCALAR else 'divfree'} m={m} k={k}"
+            out[key] = {"targets": n, "system": f"{rows} x {gmls_basis_size(d, b, m)}",
+                        "fp32_refine_Mtargets_s": n / ms["fp32_refine"] / 1e3, "fp64_Mtargets_s": n / ms["fp64"] / 1e3,
+                        "speedup": ms["fp64"] / ms["fp32_refine"], "fp32_variant": name}
+        ctx.release(cid)
+    return out
+
+
+def gmls_basis_size(d, b, m):
+    """Number of basis functions: scalar Taylor C(m + d, d); divergence-free
+    vector polynomials of degree <= m in d dimensions."""
+    from math import comb
+
+    if b == 0:
+        return comb(m + d, d)
+    full = d * comb(m + d, d)
+    return full - (comb(m - 1 + d, d))  # minus the divergence map's rank (onto degree m - 1)
 
 
 def porous_3d(ctx, n_axis=128, steps=3, n_sample=48):
@@ -985,6 +1043,7 @@ def main():
     ap.add_argument("--no-porous", action="store_true", help="skip the 3D porous-medium section")
     ap.add_argument("--porous-n-axis", type=int, default=128, help="lattice of the porous section (profiling)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch section")
+    ap.add_argument("--no-shapes", action="store_true", help="skip the per-shape FP32 / FP64 section")
     ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipeline")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
     ap.add_argument("--only", choices=["porous", "batched"], default=None,
@@ -1029,6 +1088,8 @@ def main():
         out["porous_3d"], gs = porous_3d(ctx, n_axis=args.porous_n_axis)
         if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
             out["porous_3d"]["oracle_check"] = porous_oracle_errors(gs)
+    if rank == 0 and world == 1 and not args.no_shapes:
+        out["shapes"] = shapes(ctx)
     if rank == 0 and world == 1 and not args.no_batched:
         out["batched_uneven"], gsb = batched_uneven(ctx, n_per_dim=args.batched_n)
         if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
