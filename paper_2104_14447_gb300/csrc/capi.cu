@@ -297,13 +297,24 @@ static bool capturing(gmls_ctx* ctx) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
+// Holds the stream for a fixed number of SM clock cycles (bounded: it waits
+// on nothing), so that the host can queue the launches the autotuner times
+// behind it and their events measure GPU time only, not the host's
+// launch-preparation time between them.
+__global__ void tune_delay_kernel(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+
 // time a launch on the context stream (ms), for the autotuner: one warm-up,
-// then the faster of two timed runs
+// then the faster of two timed runs queued behind a short delay kernel
 template <typename F>
 static float time_launch(gmls_ctx* ctx, F&& launch) {
   cudaEvent_t ev[3];
   for (auto& e : ev) cudaEventCreate(&e);
   launch();  // warm
+  tune_delay_kernel<<<1, 1, 0, ctx->stream>>>(2000000LL);  // about 1 ms at 2 GHz
   cudaEventRecord(ev[0], ctx->stream);
   launch();
   cudaEventRecord(ev[1], ctx->stream);
