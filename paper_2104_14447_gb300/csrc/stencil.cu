@@ -707,6 +707,94 @@ __device__ __forceinline__ ff sqrt_weight(ff u, const StencilJob& j) {
   return s;
 }
 
+// ------------------------------------------------ refinement residuals
+// f = B y - s for the L functional rows: a thread takes tile rows r and
+// r + nthr together, so two independent streams of loads of B are in flight;
+// per row the products are accumulated in column order (Dot2).
+template <typename TQ>
+__device__ void resid_f(const Group& g, const ff* B, int ld, int M, int n, int L, int nmax, const ff* Sf,
+                        const ff* Yf, TQ* Z) {
+  for (int r0 = g.tid; r0 < M; r0 += 2 * g.nthr) {
+    const int r1 = r0 + g.nthr;
+    const bool two = r1 < M;
+    Dot2 a0[kMaxSolveRows], a1[kMaxSolveRows];
+#pragma unroll
+    for (int l = 0; l < kMaxSolveRows; ++l)
+      if (l < L) {
+        a0[l].init(-Sf[l * ld + r0]);
+        if (two) a1[l].init(-Sf[l * ld + r1]);
+      }
+#pragma unroll 8
+    for (int i = 0; i < n; ++i) {
+      const ff b0 = B[i * ld + r0];
+      const ff b1 = two ? B[i * ld + r1] : ff(0.0f, 0.0f);
+#pragma unroll
+      for (int l = 0; l < kMaxSolveRows; ++l)
+        if (l < L) {
+          const ff y = Yf[l * nmax + i];
+          a0[l].add_prod(b0, y);
+          a1[l].add_prod(b1, y);
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < kMaxSolveRows; ++l)
+      if (l < L) {
+        Z[l * ld + r0] = (TQ)__fadd_rn(a0[l].h, a0[l].l);
+        if (two) Z[l * ld + r1] = (TQ)__fadd_rn(a1[l].h, a1[l].l);
+      }
+  }
+}
+
+// g = lambda - B^T s: a warp per basis column; with RPL > 0 the column's rows
+// lane + 32 t (t < RPL, M <= 32 RPL) are loaded together before the
+// products; RPL = 0: a plain row loop.  Per lane the rows are accumulated in
+// ascending order, then the L sums are all-reduced together.
+template <typename TQ, int RPL>
+__device__ void resid_g(const Group& g, const ff* B, int ld, int M, int n, int L, int nmax, const ff* Sf,
+                        const ff* lamf, TQ* D) {
+  for (int i = g.wg; i < n; i += g.G) {
+    const ff* bi = B + i * ld;
+    Dot2 acc[kMaxSolveRows];
+    if constexpr (RPL > 0) {
+      ff bv[RPL];
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int r = g.lane + 32 * t;
+        bv[t] = r < M ? bi[r] : ff(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int r = g.lane + 32 * t;
+        if (r < M) {
+#pragma unroll
+          for (int l = 0; l < kMaxSolveRows; ++l)
+            if (l < L) acc[l].add_prod(-bv[t], Sf[l * ld + r]);
+        }
+      }
+    } else {
+      for (int r = g.lane; r < M; r += 32) {
+        const ff b = -bi[r];
+#pragma unroll
+        for (int l = 0; l < kMaxSolveRows; ++l)
+          if (l < L) acc[l].add_prod(b, Sf[l * ld + r]);
+      }
+    }
+    warp_sum_ff_rows<kMaxSolveRows>(acc, L);
+    if (g.lane < L) {
+      const int l = g.lane;
+      float h = 0.f, lo = 0.f;
+#pragma unroll
+      for (int q = 0; q < kMaxSolveRows; ++q)
+        if (q == l) {
+          h = acc[q].h;
+          lo = acc[q].l;
+        }
+      const ff tot = quick_two_sum(h, lo) + lamf[l * nmax + i];
+      D[l * nmax + i] = (TQ)__fadd_rn(tot.h, tot.l);
+    }
+  }
+}
+
 // Basis output into the float-float tile and its FP32 working copy at once.
 struct DualOut {
   ff* hb;
@@ -930,49 +1018,11 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
       float prev = 0.0f;
       const bool ill = (st & GMLS_T_ILL_CONDITIONED) != 0;  // ill-conditioned: straight to FP64
       for (int iter = 0; iter < j.max_refine && !ill; ++iter) {
-        // f = B y - s (into Z), compensated float-float; a thread per tile row,
-        // all L functional rows at once (one load of B feeds L chains)
-        for (int r = g.tid; r < M; r += g.nthr) {
-          Dot2 acc[kMaxSolveRows];
-#pragma unroll
-          for (int l = 0; l < kMaxSolveRows; ++l)
-            if (l < L) acc[l].init(-Sf[(size_t)l * ld + r]);
-#pragma unroll 4
-          for (int i = 0; i < n; ++i) {
-            const ff b = B[(size_t)i * ld + r];
-#pragma unroll
-            for (int l = 0; l < kMaxSolveRows; ++l)
-              if (l < L) acc[l].add_prod(b, Yf[l * nmax + i]);
-          }
-#pragma unroll
-          for (int l = 0; l < kMaxSolveRows; ++l)
-            if (l < L) Z[(size_t)l * ld + r] = (TQ)__fadd_rn(acc[l].h, acc[l].l);
-        }
-        // g = lambda - B^T s (into D); a warp per basis column i, all L rows
-        for (int i = g.wg; i < n; i += g.G) {
-          const ff* bi = B + (size_t)i * ld;
-          Dot2 acc[kMaxSolveRows];
-#pragma unroll 2
-          for (int r = g.lane; r < M; r += 32) {
-            const ff b = -bi[r];
-#pragma unroll
-            for (int l = 0; l < kMaxSolveRows; ++l)
-              if (l < L) acc[l].add_prod(b, Sf[(size_t)l * ld + r]);
-          }
-          warp_sum_ff_rows<kMaxSolveRows>(acc, L);
-          if (g.lane < L) {
-            const int l = g.lane;
-            float h = 0.f, lo = 0.f;
-#pragma unroll
-            for (int q = 0; q < kMaxSolveRows; ++q)
-              if (q == l) {
-                h = acc[q].h;
-                lo = acc[q].l;
-              }
-            const ff tot = quick_two_sum(h, lo) + lamf[l * nmax + i];
-            D[l * nmax + i] = (TQ)__fadd_rn(tot.h, tot.l);
-          }
-        }
+        // f = B y - s (into Z) and g = lambda - B^T s (into D), compensated
+        // float-float (the float-float tile may sit in global memory: the
+        // loads of several rows / columns are issued before they are used)
+        resid_f<TQ>(g, B, ld, M, n, L, nmax, Sf, Yf, Z);
+        resid_g<TQ, 0>(g, B, ld, M, n, L, nmax, Sf, lamf, D);
         group_sync(g.gid, g.nthr);
         // d = Q^T f; a = R^{-T} g; dy = R^{-1}(a - d_1); ds = Q [a; d_2]
         apply_q_any<TQ, true>(g, A, ld, M, n, tau, L, Z);
