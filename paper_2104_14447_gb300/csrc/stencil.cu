@@ -745,39 +745,22 @@ __device__ void resid_f(const Group& g, const ff* B, int ld, int M, int n, int L
   }
 }
 
-// g = lambda - B^T s: a warp per basis column; with RPL > 0 the column's rows
-// lane + 32 t (t < RPL, M <= 32 RPL) are loaded together before the
-// products; RPL = 0: a plain row loop.  Per lane the rows are accumulated in
-// ascending order, then the L sums are all-reduced together.
-template <typename TQ, int RPL>
+// g = lambda - B^T s: a warp per basis column; per lane the rows are
+// accumulated in ascending order, then the L sums are all-reduced together.
+// (Loading a lane's whole column slice into registers before the products
+// raised the kernel's register demand and slowed every phase.)
+template <typename TQ>
 __device__ void resid_g(const Group& g, const ff* B, int ld, int M, int n, int L, int nmax, const ff* Sf,
                         const ff* lamf, TQ* D) {
   for (int i = g.wg; i < n; i += g.G) {
     const ff* bi = B + i * ld;
     Dot2 acc[kMaxSolveRows];
-    if constexpr (RPL > 0) {
-      ff bv[RPL];
+#pragma unroll 2
+    for (int r = g.lane; r < M; r += 32) {
+      const ff b = -bi[r];
 #pragma unroll
-      for (int t = 0; t < RPL; ++t) {
-        const int r = g.lane + 32 * t;
-        bv[t] = r < M ? bi[r] : ff(0.0f, 0.0f);
-      }
-#pragma unroll
-      for (int t = 0; t < RPL; ++t) {
-        const int r = g.lane + 32 * t;
-        if (r < M) {
-#pragma unroll
-          for (int l = 0; l < kMaxSolveRows; ++l)
-            if (l < L) acc[l].add_prod(-bv[t], Sf[l * ld + r]);
-        }
-      }
-    } else {
-      for (int r = g.lane; r < M; r += 32) {
-        const ff b = -bi[r];
-#pragma unroll
-        for (int l = 0; l < kMaxSolveRows; ++l)
-          if (l < L) acc[l].add_prod(b, Sf[l * ld + r]);
-      }
+      for (int l = 0; l < kMaxSolveRows; ++l)
+        if (l < L) acc[l].add_prod(b, Sf[l * ld + r]);
     }
     warp_sum_ff_rows<kMaxSolveRows>(acc, L);
     if (g.lane < L) {
@@ -1022,7 +1005,7 @@ __device__ void process_target(const StencilJob& j, const Group& g, unsigned cha
         // float-float (the float-float tile may sit in global memory: the
         // loads of several rows / columns are issued before they are used)
         resid_f<TQ>(g, B, ld, M, n, L, nmax, Sf, Yf, Z);
-        resid_g<TQ, 0>(g, B, ld, M, n, L, nmax, Sf, lamf, D);
+        resid_g<TQ>(g, B, ld, M, n, L, nmax, Sf, lamf, D);
         group_sync(g.gid, g.nthr);
         // d = Q^T f; a = R^{-T} g; dy = R^{-1}(a - d_1); ds = Q [a; d_2]
         apply_q_any<TQ, true>(g, A, ld, M, n, tau, L, Z);
