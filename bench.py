@@ -231,7 +231,7 @@ def run_ours(args, rank, world, local_rank):
     x_pin = torch.from_numpy(x_host).pin_memory()
     host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
     d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v)
-    d2h += 8 * 3 * (args.e2e_ranges - 1)  # the row pointer shared by two ranges goes back twice
+    d2h += 8 * 3 * ((len(args.e2e_fractions.split(",")) if args.e2e_fractions else args.e2e_ranges) - 1)  # shared row pointers
     h2d = x_pin.numel() * x_pin.element_size()
     # The targets are processed in --e2e-ranges contiguous ranges so that the
     # operators of the first ranges travel to the host (on two copy streams)
@@ -242,8 +242,12 @@ def run_ours(args, rank, world, local_rank):
     # operator (gmls_assemble_csr_at), so the host receives the operators
     # themselves.
     copy_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    n_ranges = args.e2e_ranges
-    bounds = [n * c // n_ranges for c in range(n_ranges + 1)]
+    if args.e2e_fractions:
+        fr = np.array([float(v) for v in args.e2e_fractions.split(",")])
+        bounds = [0] + [int(round(n * v)) for v in np.cumsum(fr / fr.sum())[:-1]] + [n]
+    else:
+        bounds = [n * c // args.e2e_ranges for c in range(args.e2e_ranges + 1)]
+    n_ranges = len(bounds) - 1
     chunk_tg = [torch.arange(a, b, dtype=torch.int32, device=dev) for a, b in zip(bounds[:-1], bounds[1:])]
     per_target = {"vl": (2, K_DIVFREE * 2), "grad": (2, K_SCALAR), "div": (1, K_SCALAR * 2)}  # rows, nnz per row
 
@@ -392,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "e2e": {"value": n * world / (float(np.median(e2e_ms)) * 1e-3), "unit": "targets/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms], "target_ranges": args.e2e_ranges,
+                "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms], "target_ranges": n_ranges, "range_bounds": bounds,
                 "host_operators_equal_device_step": e2e_equal},
         "gpu_launches": int(launches),
         "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
@@ -1045,6 +1049,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch section")
     ap.add_argument("--no-shapes", action="store_true", help="skip the per-shape FP32 / FP64 section")
     ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipeline")
+    ap.add_argument("--e2e-fractions", default=None, help="relative sizes of the end-to-end ranges, e.g. 4,3,2,1")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
     ap.add_argument("--only", choices=["porous", "batched"], default=None,
                     help="profiling: run only this section (--steps timed steps) and print it")
