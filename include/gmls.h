@@ -72,7 +72,7 @@ typedef int32_t gmls_status;
 #define GMLS_T_TOO_FEW_NEIGHBOURS 8  /* fewer candidates than requested (weights zero)       */
 #define GMLS_T_FP64_FALLBACK 16      /* result recomputed by the FP64 path                    */
 #define GMLS_T_OVERFLOW 32           /* candidate buffer exceeded (neighbour list truncated) */
-#define GMLS_T_UNSUPPORTED 64        /* rows x basis size exceed every tile of this build (weights zero) */
+#define GMLS_T_UNSUPPORTED 64        /* rows x basis size exceed every tile the library has (weights zero) */
 
 /* neighbour modes */
 #define GMLS_NBR_KNN 0    /* k nearest by (d^2, index); eps = eps_factor * d_k                */
