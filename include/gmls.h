@@ -358,6 +358,10 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
                                     global memory); 0 (default) no forcing.  gmls_stencils
                                     fails with GMLS_EINVAL where the variant does not exist
                                     or does not fit for the shape                            */
+#define GMLS_OPT_POISON 4        /* testing: 1 = gmls_stencils first fills the arrays it
+                                    returns (weights, beta, status, iteration counts) with
+                                    all-ones bytes (NaN weights), so that an entry no kernel
+                                    writes cannot pass for a result left in reused memory    */
 
 /* Set a context option (GMLS_OPT_*); applies to later calls. */
 gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);

@@ -176,6 +176,7 @@ struct gmls_ctx {
   int64_t launches = 0;
   bool force_generic = false;  // testing: use the generic tile kernel for every shape
   int force_variant = 0;       // testing: this kernel variant for uniform shapes (0: off)
+  bool poison = false;         // testing: fill stencil outputs with all-ones bytes first
   bool autotune = true;
   std::map<TuneKey, int> tune;        // chosen variant per shape
   std::vector<TuneRecord> tune_log;   // every timing the autotuner took
@@ -673,6 +674,9 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
         return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2 or G + 8 * P (G 1, 2, 4; P 0, 1, 2)");
       ctx->force_variant = (int)value;
       return GMLS_OK;
+    case GMLS_OPT_POISON:
+      ctx->poison = value != 0;
+      return GMLS_OK;
     case GMLS_OPT_CLEAR_TUNING:
       ctx->tune.clear();
       ctx->tune_log.clear();
@@ -1067,6 +1071,15 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
     return fail(ctx, GMLS_ENOMEM, "gmls_stencils: arena exhausted");
   }
   if (deg) CK(copy_in(ctx, deg, p->degree_per_target, nt), "gmls_stencils copy degrees");
+  if (ctx->poison) {  // testing: every entry must be written by the kernels
+    for (int f = 0; f < s.nout; ++f)
+      CK(cudaMemsetAsync(s.w[f], 0xFF, sizeof(double) * std::max<int64_t>(nb.idx_cap * s.rows[f] * s.ncomp[f], 1),
+                         ctx->stream), "gmls_stencils poison");
+    CK(cudaMemsetAsync(s.beta, 0xFF, sizeof(double) * std::max<int64_t>(nt * std::max(L, 1), 1), ctx->stream),
+       "gmls_stencils poison");
+    CK(cudaMemsetAsync(s.status, 0xFF, std::max<int64_t>(nt, 1), ctx->stream), "gmls_stencils poison");
+    CK(cudaMemsetAsync(s.iters, 0xFF, std::max<int64_t>(nt, 1), ctx->stream), "gmls_stencils poison");
+  }
 
   j.dim = dim;
   j.n = c.n;

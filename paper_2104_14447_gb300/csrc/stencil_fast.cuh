@@ -279,7 +279,7 @@ template <int KIND, int D, int DEG, int MR, int L, int HW>
 __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()))
     stencil_fast_kernel(StencilJob j) {
   constexpr int N = gmls_gen::basis_size(KIND, D, DEG);
-  constexpr int NC = (KIND == GMLS_BASIS_SCALAR) ? 1 : D;
+  constexpr int NC = (KIND == GMLS_BASIS_DIVFREE) ? D : 1;  // components per neighbour (staggered: 1)
   constexpr int ROWS = HW * MR;
   constexpr int NT = (N + HW - 1) / HW;
   using Lay = FastLay<HW, MR, N, NC>;
@@ -319,7 +319,22 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
     uint8_t st = j.nbr_status ? j.nbr_status[to] : 0;
     const bool neu = j.neumann && j.bflag && j.bflag[t];
     const bool too_few = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || !(j.eps[to] > 0.0);
-    if (!too_few && (neu || M > ROWS || M < N)) {
+    // staggered basis: the weights act on p_j - p(x_T); the target's own
+    // entry (a zero row of the tile) later takes minus the sum of the others
+    int self = -1;
+    if constexpr (KIND == GMLS_BASIS_STAGGERED) {
+      if (!too_few) {
+        const int32_t* nb = j.idx + o0;
+        int first = 0x7fffffff;
+        for (int q = lane; q < k; q += HW)
+          if (nb[q] == (int32_t)t) first = min(first, q);
+#pragma unroll
+        for (int o = HW / 2; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(mask, first, o, HW));
+        self = first == 0x7fffffff ? -1 : first;
+      }
+    }
+    const bool no_self = KIND == GMLS_BASIS_STAGGERED && !too_few && self < 0;
+    if (!too_few && (neu || M > ROWS || M < N || no_self)) {
       // not for this path: the shared-memory FP32 kernel takes it (and writes
       // every output)
       if (lane == 0) {
@@ -573,6 +588,7 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
       const bool div_scalar = (j.out_fn[f] == GMLS_F_DIV) && (KIND == GMLS_BASIS_SCALAR);
       const float sgn = (float)j.out_sign[f];
       for (int rr = 0; rr < R; ++rr) {
+        double others = 0.0;  // staggered: sum of the row's weights but the target's own
         for (int e = lane; e < per_row; e += HW) {
           double val = 0.0;
           if (src >= 0) {
@@ -585,7 +601,16 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
               val = to_double(ff(sgn * s.h, sgn * s.l));
             }
           }
+          if constexpr (KIND == GMLS_BASIS_STAGGERED) {
+            if (e == self) continue;  // written below
+            others += val;
+          }
           wo[(int64_t)rr * per_row + e] = val;
+        }
+        if constexpr (KIND == GMLS_BASIS_STAGGERED) {
+#pragma unroll
+          for (int o = HW / 2; o > 0; o >>= 1) others += __shfl_xor_sync(mask, others, o, HW);
+          if (lane == 0) wo[(int64_t)rr * per_row + self] = src >= 0 ? -others : 0.0;
         }
       }
     }
@@ -609,7 +634,7 @@ struct FastEntry {
 #define GMLS_FAST(KIND, D, DEG, MR, L, HW)                                                                            \
   FastEntry {                                                                                                          \
     KIND, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L, HW>,                                \
-        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 0 ? 1 : D)>::bytes                               \
+        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 1 ? D : 1)>::bytes                               \
   }
 
 }  // namespace gmls

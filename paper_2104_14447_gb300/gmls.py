@@ -45,7 +45,7 @@ EXPORTED = [
     "gmls_csr_spmv", "gmls_gmres",
 ]
 NOALLOC_MAX_POINTS = 262144
-OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT = 0, 1, 2, 3
+OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT, OPT_POISON = 0, 1, 2, 3, 4
 T_UNSUPPORTED = 64
 
 

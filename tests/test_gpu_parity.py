@@ -26,6 +26,7 @@ def ctx():
 
     build.build()
     c = gmls.Context(0, arena_bytes=16 << 30)
+    c.set_option(gmls.OPT_POISON, 1)  # outputs start as NaN: unwritten entries cannot pass
     yield c
     c.close()
 

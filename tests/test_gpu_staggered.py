@@ -25,18 +25,38 @@ def ctx():
 
     build.build()
     c = gmls.Context(0, arena_bytes=8 << 30)
+    c.set_option(gmls.OPT_POISON, 1)  # outputs start as NaN: unwritten entries cannot pass
     yield c
     c.close()
 
 
-@pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
+# kernel: "auto" (autotuner), "generic" (shared-memory kernel), or a forced
+# register kernel with 32 / 16 lanes per target (skipped where not instantiated)
+VARIANT = {"reg32": -1, "reg16": -2}
+
+
+@pytest.mark.parametrize("precision,kernel", [(gmls.FP64, "generic"), (gmls.FP32_REFINE, "generic"),
+                                              (gmls.FP32_REFINE, "auto"), (gmls.FP32_REFINE, "reg32"),
+                                              (gmls.FP32_REFINE, "reg16")])
 @pytest.mark.parametrize("dim,na,m,k", [(2, 24, 2, 24), (2, 24, 3, 36), (2, 24, 4, 48), (3, 9, 2, 40)])
-def test_staggered_matches_oracle(ctx, dim, na, m, k, precision):
+def test_staggered_matches_oracle(ctx, dim, na, m, k, precision, kernel):
     x = inputs.jittered_grid(dim, na, seed=m)
     n = x.shape[1]
     cid = ctx.cloud(x)
     nid = ctx.neighbors(cid, k, 1.5)
-    sid = ctx.stencils(nid, gmls.STAGGERED, m, [gmls.LAPLACIAN, gmls.GRAD], precision=precision)
+    ctx.set_option(gmls.OPT_FORCE_GENERIC, int(kernel == "generic"))
+    ctx.set_option(gmls.OPT_FORCE_VARIANT, VARIANT.get(kernel, 0))
+    try:
+        sid = ctx.stencils(nid, gmls.STAGGERED, m, [gmls.LAPLACIAN, gmls.GRAD], precision=precision)
+    except gmls.GmlsError as e:
+        ctx.release(nid)
+        ctx.release(cid)
+        if e.code == gmls.EINVAL and kernel in VARIANT:
+            pytest.skip(f"no {kernel} variant for this shape")
+        raise
+    finally:
+        ctx.set_option(gmls.OPT_FORCE_GENERIC, 0)
+        ctx.set_option(gmls.OPT_FORCE_VARIANT, 0)
     idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).cpu().numpy()
     eps = ctx.export(nid, gmls.X_NBR_EPS, torch.float64).cpu().numpy()
     st = ctx.export(sid, gmls.X_STATUS, torch.uint8).cpu().numpy()
