@@ -24,12 +24,14 @@ extern const FastEntry kFastS3c[];
 extern const int kFastS3cCount;
 extern const FastEntry kFastG2[];
 extern const int kFastG2Count;
+extern const FastEntry kFastG3[];
+extern const int kFastG3Count;
 
 struct FastTable {
   const FastEntry* e;
   const int* n;
 };
-static const FastTable kTables[] = {{kFastS2a, &kFastS2aCount}, {kFastS2b, &kFastS2bCount}, {kFastS2c, &kFastS2cCount}, {kFastS3a, &kFastS3aCount}, {kFastS3b, &kFastS3bCount}, {kFastD2, &kFastD2Count}, {kFastD3, &kFastD3Count}, {kFastS3c, &kFastS3cCount}, {kFastG2, &kFastG2Count}};
+static const FastTable kTables[] = {{kFastS2a, &kFastS2aCount}, {kFastS2b, &kFastS2bCount}, {kFastS2c, &kFastS2cCount}, {kFastS3a, &kFastS3aCount}, {kFastS3b, &kFastS3bCount}, {kFastD2, &kFastD2Count}, {kFastD3, &kFastD3Count}, {kFastS3c, &kFastS3cCount}, {kFastG2, &kFastG2Count}, {kFastG3, &kFastG3Count}};
 
 template <typename F>
 static void for_each_entry(F&& f) {
