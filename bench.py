@@ -241,7 +241,7 @@ def run_ours(args, rank, world, local_rank):
     # divergence CSR rows.  Each range writes its rows in place in the
     # operator (gmls_assemble_csr_at), so the host receives the operators
     # themselves.
-    copy_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    copy_streams = [torch.cuda.Stream(dev) for _ in range(args.e2e_copy_streams)]
     if args.e2e_fractions:
         fr = np.array([float(v) for v in args.e2e_fractions.split(",")])
         bounds = [0] + [int(round(n * v)) for v in np.cumsum(fr / fr.sum())[:-1]] + [n]
@@ -279,14 +279,14 @@ def run_ours(args, rank, world, local_rank):
         for c in range(n_ranges):
             n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR, targets=chunk_tg[c])
             s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
-            assemble_and_ship(s_df, gmls.VEC_LAPLACIAN, "vl", c, c & 1)
+            assemble_and_ship(s_df, gmls.VEC_LAPLACIAN, "vl", c, c % len(copy_streams))
             n48s.append(n48)
             ids += [n48, s_df]
         for c in range(n_ranges):
             n36 = ctx.neighbors_prefix(n48s[c], K_SCALAR, EPS_FACTOR)
             s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
-            assemble_and_ship(s_sc, gmls.GRAD, "grad", c, c & 1)
-            assemble_and_ship(s_sc, gmls.DIV, "div", c, (c + 1) & 1)
+            assemble_and_ship(s_sc, gmls.GRAD, "grad", c, (2 * c) % len(copy_streams))
+            assemble_and_ship(s_sc, gmls.DIV, "div", c, (2 * c + 1) % len(copy_streams))
             ids += [n36, s_sc]
         return ids
 
@@ -499,7 +499,7 @@ def stokes_system(ctx, steps=5):
 
 def shapes(ctx):
     """Stencil stage of every (dimension, basis, degree) shape the serving
-    stream draws, on one cloud per dimension (2D: 400 x 400 jittered grid,
+    stream draws, and of the staggered basis, on one cloud per dimension (2D: 400 x 400 jittered grid,
     160,000 targets; 3D: 50^3, 125,000), FP32 + refinement against plain
     FP64 (the same launch path with GMLS_FP64), CUDA events around one
     gmls_stencils call after a warm-up call; the kernel variant the
@@ -513,10 +513,15 @@ def shapes(ctx):
         x = inputs.jittered_grid(dim, n_axis, seed=1)
         n = x.shape[1]
         cid = ctx.cloud(x)
-        for (d, b, m), k in SERVE_K.items():
+        # the serving shapes, then the staggered basis (Sec. 2.4; gradient and
+        # Laplacian of the line-integral potential)
+        cases = [((d, b, m), k) for (d, b, m), k in SERVE_K.items()]
+        cases += [((2, gmls.STAGGERED, 2), 24), ((2, gmls.STAGGERED, 3), 36), ((2, gmls.STAGGERED, 4), 48),
+                  ((3, gmls.STAGGERED, 2), 40)]
+        for (d, b, m), k in cases:
             if d != dim:
                 continue
-            fns = [gmls.GRAD, gmls.LAPLACIAN] if b == gmls.SCALAR else [gmls.VEC_LAPLACIAN]
+            fns = [gmls.VEC_LAPLACIAN] if b == gmls.DIVFREE else [gmls.GRAD, gmls.LAPLACIAN]
             nid = ctx.neighbors(cid, k, EPS_FACTOR)
             ms = {}
             for name, prec in (("fp32_refine", gmls.FP32_REFINE), ("fp64", gmls.FP64)):
@@ -529,14 +534,14 @@ def shapes(ctx):
                 ms[name] = e0.elapsed_time(e1)
                 ctx.release(sid)
             ctx.release(nid)
-            rows = k * (1 if b == gmls.SCALAR else d)
+            rows = k * (d if b == gmls.DIVFREE else 1)
             tl = [r for r in ctx.tune_log() if r["dim"] == d and r["basis"] == b and r["degree"] == m
                   and r["precision"] == gmls.FP32_REFINE and r["rows"] == rows and not r["bucketed"]]
             v = min(tl, key=lambda r: r["ms"])["variant"] if tl else None
             name = None if v is None else ({-1: "register", -2: "register 16 lanes"}.get(v) or
                                            f"{v & 7} warp(s)/target" + {0: "", 1: ", split tiles",
                                                                         2: ", global tiles"}[v >> 3])
-            key = f"{d}d {'scalar' if b == gmls.SCALAR else 'divfree'} m={m} k={k}"
+            key = f"{d}d {['scalar', 'divfree', 'staggered'][b]} m={m} k={k}"
             out[key] = {"targets": n, "system": f"{rows} x {gmls_basis_size(d, b, m)}",
                         "fp32_refine_Mtargets_s": n / ms["fp32_refine"] / 1e3, "fp64_Mtargets_s": n / ms["fp64"] / 1e3,
                         "speedup": ms["fp64"] / ms["fp32_refine"], "fp32_variant": name}
@@ -546,11 +551,14 @@ def shapes(ctx):
 
 def gmls_basis_size(d, b, m):
     """Number of basis functions: scalar Taylor C(m + d, d); divergence-free
-    vector polynomials of degree <= m in d dimensions."""
+    vector polynomials of degree <= m in d dimensions; staggered: monomials of
+    degree 1..m+1 (the span of the line integrals of the vector monomials)."""
     from math import comb
 
     if b == 0:
         return comb(m + d, d)
+    if b == 2:
+        return comb(m + 1 + d, d) - 1
     full = d * comb(m + d, d)
     return full - (comb(m - 1 + d, d))  # minus the divergence map's rank (onto degree m - 1)
 
@@ -1050,6 +1058,7 @@ def main():
     ap.add_argument("--no-shapes", action="store_true", help="skip the per-shape FP32 / FP64 section")
     ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipeline")
     ap.add_argument("--e2e-fractions", default=None, help="relative sizes of the end-to-end ranges, e.g. 4,3,2,1")
+    ap.add_argument("--e2e-copy-streams", type=int, default=2, help="copy streams of the end-to-end pipeline")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
     ap.add_argument("--only", choices=["porous", "batched"], default=None,
                     help="profiling: run only this section (--steps timed steps) and print it")
