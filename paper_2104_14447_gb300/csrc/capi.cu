@@ -116,6 +116,7 @@ struct NbrObj {
   bool all_targets = false;  // targets are every point of the cloud, in order
   int64_t idx_cap = 0;  // allocated index entries
   int16_t* order = nullptr;  // id order of the lists, computed on first use (CSR, Stokes system)
+  int64_t parent = 0;        // the longer fixed-k list this one is a prefix of (0: none)
   int refs = 0;
 };
 
@@ -920,6 +921,7 @@ gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, dou
   nb.k = k;
   nb.cap = k;
   nb.idx_cap = src.n_tgt * (int64_t)k;
+  nb.parent = nbrs_id;
   const int64_t nt = src.n_tgt;
   nb.tgt = arena_alloc<int32_t>(ctx, std::max<int64_t>(nt, 1));
   nb.off = arena_alloc<int64_t>(ctx, nt + 1);
@@ -1155,11 +1157,25 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
 // the lists' id order (lists never change after creation: computed once)
 static gmls_status ensure_order(gmls_ctx* ctx, NbrObj& nb, const char* who) {
   if (nb.order) return GMLS_OK;
+  // a prefix list takes its order from the longer list's (computed here if
+  // missing): the positions below k, in that order, are its id order
+  NbrObj* par = nullptr;
+  if (nb.parent) {
+    auto pit = ctx->objs.find(nb.parent);
+    if (pit != ctx->objs.end() && pit->second.kind == K_NBRS && !pit->second.nb.variable &&
+        pit->second.nb.n_tgt == nb.n_tgt && pit->second.nb.k >= nb.k)
+      par = &pit->second.nb;
+  }
+  if (par) {
+    gmls_status r = ensure_order(ctx, *par, who);
+    if (r) return r;
+  }
   nb.order = arena_alloc<int16_t>(ctx, std::max<int64_t>(nb.idx_cap, 1));
   if (!nb.order) return fail(ctx, GMLS_ENOMEM, std::string(who) + ": arena exhausted (neighbour id order)");
   int kcap = 1;
   while (kcap < nb.cap) kcap <<= 1;
-  cudaError_t e = launch_nbr_order(ctx->launch(), nb.n_tgt, nb.off, nb.idx, kcap, nb.order);
+  cudaError_t e = par ? launch_nbr_order_prefix(ctx->launch(), nb.n_tgt, par->order, par->k, nb.k, nb.order)
+                      : launch_nbr_order(ctx->launch(), nb.n_tgt, nb.off, nb.idx, kcap, nb.order);
   if (e != cudaSuccess) {
     ctx->arena.release(nb.order);
     nb.order = nullptr;

@@ -231,6 +231,10 @@ cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* 
 // position of target t's entry of rank r by particle id
 cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off, const int32_t* idx, int kcap,
                              int16_t* order);
+// id order of the k-prefix of fixed-k lists from the order of the full lists
+// (kp entries per target): the positions below k, kept in their order
+cudaError_t launch_nbr_order_prefix(const Launch& L, int64_t n_tgt, const int16_t* parent_order, int kp, int k,
+                                    int16_t* order);
 
 struct CsrJob {
   const int16_t* order;  // id order of the lists

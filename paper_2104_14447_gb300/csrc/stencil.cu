@@ -1413,6 +1413,38 @@ cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off,
   return cudaGetLastError();
 }
 
+// Order of the k-prefix lists: warp per target; the parent's positions are
+// scanned in order, 32 at a time, and those below k are compacted (ballot).
+__global__ void nbr_order_prefix_kernel(int64_t n_tgt, const int16_t* __restrict__ parent_order, int kp, int k,
+                                        int16_t* __restrict__ order) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tgt;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int16_t* po = parent_order + t * kp;
+    int16_t* out = order + t * k;
+    int filled = 0;
+    for (int i0 = 0; i0 < kp; i0 += 32) {
+      const int i = i0 + lane;
+      const int pos = i < kp ? (int)po[i] : k;
+      const bool keep = pos < k;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) out[filled + __popc(m & ((1u << lane) - 1u))] = (int16_t)pos;
+      filled += __popc(m);
+    }
+  }
+}
+
+cudaError_t launch_nbr_order_prefix(const Launch& L, int64_t n_tgt, const int16_t* parent_order, int kp, int k,
+                                    int16_t* order) {
+  if (n_tgt == 0) return cudaSuccess;
+  if (k < 1 || k > kp) return cudaErrorInvalidValue;
+  int64_t blocks = (n_tgt * 32 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  nbr_order_prefix_kernel<<<(unsigned)blocks, 256, 0, L.stream>>>(n_tgt, parent_order, kp, k, order);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
 // CSR of one functional from the cached id order: warp per target, every
 // row's entries written in ascending column order, no sorting.  C
 // (components per neighbour) is a compile-time constant.

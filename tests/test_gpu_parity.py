@@ -252,6 +252,28 @@ def test_csr_structure_bit_exact(ctx, basis, m, k, fn):
     _release(ctx, cid, nid, sid)
 
 
+@pytest.mark.parametrize("parent_first", [False, True])
+def test_csr_of_prefix_lists_equals_direct_lists(ctx, parent_first):
+    """The id order of a prefix list is derived from its parent's: CSR of the
+    36-prefix of 48-nearest lists equals CSR of the 36-nearest lists, bit for
+    bit, whether or not the parent's CSR was assembled first."""
+    x = inputs.jittered_grid(2, 40, seed=6)
+    cid = ctx.cloud(x)
+    n48 = ctx.neighbors(cid, 48, 1.5)
+    n36p = ctx.neighbors_prefix(n48, 36, 1.5)
+    n36 = ctx.neighbors(cid, 36, 1.5)
+    s48 = ctx.stencils(n48, gmls.SCALAR, 4, [gmls.GRAD])
+    if parent_first:
+        ctx.assemble_csr(s48, gmls.GRAD)
+    sp = ctx.stencils(n36p, gmls.SCALAR, 4, [gmls.GRAD, gmls.DIV])
+    sd = ctx.stencils(n36, gmls.SCALAR, 4, [gmls.GRAD, gmls.DIV])
+    for fn in (gmls.GRAD, gmls.DIV):
+        a = [t.cpu().numpy() for t in ctx.assemble_csr(sp, fn)]
+        b = [t.cpu().numpy() for t in ctx.assemble_csr(sd, fn)]
+        assert all(np.array_equal(u, v) for u, v in zip(a, b))
+    _release(ctx, cid, n48, n36p, n36, s48, sp, sd)
+
+
 def test_csr_assembled_in_target_ranges(ctx):
     """gmls_assemble_csr_at: an operator assembled range by range (one
     neighbour handle per contiguous target range, uneven range sizes, radius
