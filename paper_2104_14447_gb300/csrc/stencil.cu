@@ -1458,16 +1458,20 @@ __global__ void __launch_bounds__(kCsrWarps * 32) csr_kernel(CsrJob j) {
     const int k = (int)(j.off[t + 1] - o);
     const int rowlen = k * C;
     const int64_t base = o * (int64_t)j.rows * C;
-    for (int r = 0; r < j.rows; ++r) {
-      const int64_t row = t * j.rows + r;
-      const int64_t start = base + (int64_t)r * rowlen;
-      if (lane == 0) j.row_ptr[row] = j.nnz_base + start;
-      const double* wr = j.w + start;
-      for (int e = lane; e < rowlen; e += 32) {
-        const int q = e / C, c = e - q * C;
-        const int p = j.order[o + q];
-        j.col[start + e] = j.idx[o + p] * C + c;
-        j.val[start + e] = wr[p * C + c];
+    for (int r = lane; r < j.rows; r += 32) j.row_ptr[t * j.rows + r] = j.nnz_base + base + (int64_t)r * rowlen;
+    // the target's rows are contiguous: one pass over rows x rowlen entries,
+    // row r and in-row position e carried along instead of divided
+    const int total = j.rows * rowlen;
+    int r = rowlen > 0 ? lane / rowlen : 0, e = lane - r * rowlen;  // (no entries: the loop below is empty)
+    for (int g = lane; g < total; g += 32) {
+      const int q = e / C, c = e - q * C;
+      const int p = j.order[o + q];
+      j.col[base + g] = j.idx[o + p] * C + c;
+      j.val[base + g] = j.w[base + (int64_t)r * rowlen + p * C + c];
+      e += 32;
+      while (e >= rowlen) {
+        e -= rowlen;
+        ++r;
       }
     }
     if (t == j.n_tgt - 1 && lane == 0) j.row_ptr[j.n_tgt * j.rows] = j.nnz_base + base + (int64_t)j.rows * rowlen;
