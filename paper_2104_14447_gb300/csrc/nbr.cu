@@ -389,6 +389,14 @@ __device__ __forceinline__ int64_t row_position(const WarpBuf& wb, int32_t p) {
   return wb.row_begin[lo_r] + (p - start);
 }
 
+// the cell box covers every cell of the grid
+template <int D>
+__device__ __forceinline__ bool box_is_whole_grid(const GridParams& g, const int* lo, const int* hi) {
+  for (int c = 0; c < D; ++c)
+    if (lo[c] != 0 || hi[c] != g.nc[c] - 1) return false;
+  return true;
+}
+
 // Every particle with exact FP64 d2 < R2 (and on the kept side of the
 // half-space) from the cells of the box, computing d2 for every particle in
 // the box.  Returns the number that passed (may exceed wb.cap: overflow).
@@ -400,6 +408,32 @@ __device__ int gather_exact(const CloudDev& cl, const GridParams& g, const int* 
   const int ny = hi[1] - lo[1] + 1;
   const int nrows = ny * (hi[2] - lo[2] + 1);
   int count = 0;
+  if (box_is_whole_grid<D>(g, lo, hi)) {
+    for (int64_t p0 = 0; p0 < cl.n; p0 += 32) {
+      const int64_t pos = p0 + lane;
+      bool pass = false;
+      int32_t j = 0;
+      double d2 = 0.0;
+      if (pos < cl.n) {
+        double dx[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < dim; ++c) dx[c] = __dsub_rn(cl.xs[c * cl.n + pos], xT[c]);
+        d2 = exact_d2(dim, dx);
+        pass = nonneg_less(d2, R2);
+        if (pass && use_hs) pass = nonpositive(exact_dot(dim, nrm, dx));
+        j = cl.sorted[pos];
+      }
+      unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        int slot = count + __popc(m & ((1u << lane) - 1u));
+        if (slot < wb.cap) {
+          wb.d2[slot] = d2;
+          wb.id[slot] = j;
+        }
+      }
+      count += __popc(m);
+    }
+    return count;
+  }
   for (int r0 = 0; r0 < nrows; r0 += 32) {
     const int32_t total = load_rows(cl, g, lo, hi, ny, nrows, r0, wb);
     for (int32_t p0 = 0; p0 < total; p0 += 32) {
@@ -463,7 +497,29 @@ __device__ int gather_candidates(const CloudDev& cl, const GridParams& g, const 
   const float hs_tol = hs_scale * (xmax + 4.0f * Rbox);
   // pass 1: FP32 pre-filter, positions of the survivors into wb.id
   int staged = 0;
-  for (int r0 = 0; r0 < nrows; r0 += 32) {
+  if (box_is_whole_grid<D>(g, lo, hi)) {
+    // every particle: the cell-ordered arrays in one coalesced sweep
+    for (int64_t p0 = 0; p0 < cl.n; p0 += 32) {
+      const int64_t pos = p0 + lane;
+      bool pass = false;
+      if (pos < cl.n) {
+        float d2f = 0.0f, dotf = 0.0f;
+        for (int c = 0; c < dim; ++c) {
+          const float dxf = cl.xsf[c * cl.n + pos] - xTf[c];
+          d2f = fmaf(dxf, dxf, d2f);
+          dotf = fmaf(nrmf[c], dxf, dotf);
+        }
+        pass = d2f <= bf && (!use_hs || dotf <= hs_tol);
+      }
+      unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) {
+        int slot = staged + __popc(m & ((1u << lane) - 1u));
+        if (slot < wb.cap) wb.id[slot] = (int32_t)pos;
+      }
+      staged += __popc(m);
+    }
+  }
+  for (int r0 = 0; r0 < (box_is_whole_grid<D>(g, lo, hi) ? 0 : nrows); r0 += 32) {
     const int32_t total = load_rows(cl, g, lo, hi, ny, nrows, r0, wb);
     for (int32_t p0 = 0; p0 < total; p0 += 32) {
       const int32_t p = p0 + lane;
