@@ -677,7 +677,12 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
       if (count >= kq) break;
       if (R > big) break;  // whole cloud inside: too few exist
       r_lo = R;
-      R *= (count > 0) ? fminf(2.0f, fmaxf(1.1f, powf(1.3f * (float)kq / (float)count, 1.0f / (float)dim))) : 2.0f;
+      // grow by the count's shortfall (ball volume ~ R^dim), at least 10 %; from
+      // the fourth attempt on at least 50 % (targets whose kept half-space is
+      // nearly empty: fewer rescans of ever larger boxes)
+      const float min_growth = attempt >= 3 ? 1.5f : 1.1f;
+      R *= (count > 0) ? fminf(2.0f, fmaxf(min_growth, powf(1.3f * (float)kq / (float)count, 1.0f / (float)dim)))
+                       : 2.0f;
       if (R > jump) R = fmaxf(R, big * 1.001f);
       if (R >= r_hi) R = 0.5f * (r_lo + r_hi);
     }
