@@ -133,6 +133,7 @@ CASES = [
     (2, 40, gmls.SCALAR, 4, 36, [gmls.GRAD, gmls.DIV, gmls.LAPLACIAN]),
     (2, 40, gmls.DIVFREE, 4, 48, [gmls.VEC_LAPLACIAN, gmls.CURLCURL, gmls.DIV]),
     (2, 24, gmls.DIVFREE, 2, 22, [gmls.VEC_LAPLACIAN]),
+    (2, 30, gmls.DIVFREE, 3, 34, [gmls.VEC_LAPLACIAN, gmls.CURLCURL]),
     (3, 12, gmls.SCALAR, 3, 40, [gmls.GRAD, gmls.LAPLACIAN]),
     (3, 12, gmls.DIVFREE, 3, 80, [gmls.VEC_LAPLACIAN]),
     (3, 9, gmls.SCALAR, 4, 84, [gmls.GRAD, gmls.LAPLACIAN]),
