@@ -245,7 +245,7 @@ def apply_q(A, tau, z):
 
 
 # ------------------------------------------------------------ Stokes system
-def stokes_system(dim, n, bflag, normals, vel, pres, nu):
+def stokes_system(dim, n, bflag, normals, vel, pres, nu, pres_int=None):
     """Collocation system of the Stokes problem (Sec. 3.2, Eq.
     stokes-block-system), assembled from per-point stencils.
 
@@ -269,7 +269,13 @@ def stokes_system(dim, n, bflag, normals, vel, pres, nu):
            rows, input components), targets = all points in order;
     pres = (off, idx, w_grad, w_lap, beta_lap) with w_grad[I] [dim, k_I, 1],
            w_lap[I] [1, k_I, 1] (constrained at boundary points) and
-           beta_lap[I] the Laplacian row's beta (zero at interior points).
+           beta_lap[I] the Laplacian row's beta (zero at interior points);
+    pres_int = None, or (off, idx, w_lap) of staggered Laplacian stencils
+           (Sec. 2.4, w_lap[I] [1, k_I, 1], the target in its own list):
+           the interior pressure rows then take these weights on their own
+           neighbour list, as Sec. 3.2 prescribes for points inside the
+           domain (Eq. laplacian-pressure-stencil); boundary rows keep the
+           Neumann-constrained scalar stencil.
     Returns scipy.sparse.csr_matrix with ascending columns in every row."""
     import scipy.sparse as sp
 
@@ -304,6 +310,10 @@ def stokes_system(dim, n, bflag, normals, vel, pres, nu):
                 rows.append(np.full(len(vcol) + len(pcol), r))
                 cols.append(np.concatenate([vcol, pcol]))
                 vals.append(np.concatenate([nu * a3[c].reshape(-1), a1[c]]))
+            if pres_int is not None:
+                off_s, idx_s, w_s = pres_int
+                pcol = nd + np.asarray(idx_s[off_s[I]:off_s[I + 1]], dtype=np.int64)
+                a2 = np.asarray(w_s[I])[0, :, 0]
             r = nd + I
             rows.append(np.full(len(pcol) + 1, r))
             cols.append(np.concatenate([pcol, [nd + n]]))

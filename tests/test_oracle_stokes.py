@@ -14,6 +14,9 @@ Neumann pressure condition at the outermost lattice layer.
   boundary pressure rows (beta ~ 1/eps multiplies an O(h^(m-1)) error).
 * Structure: Dirichlet rows are unit rows, every pressure row couples to the
   multiplier, the last row sums the pressures, columns ascend.
+* The same three checks, and the solve, with the staggered Laplacian of
+  degree m - 1 (Sec. 2.4; exact for pressures of degree <= m) on the interior
+  pressure rows, as Sec. 3.2 prescribes for points inside the domain.
 """
 import numpy as np
 import pytest
@@ -24,10 +27,11 @@ import oracle
 from paper_2104_14447_gb300 import inputs
 
 M = 4
+MS = 3  # staggered interior pressure Laplacian: exact to degree MS + 1 = M, rate MS = M - 1
 KV, KP = 48, 36
 
 
-def _system(na, nu, seed=0):
+def _system(na, nu, seed=0, staggered=False):
     x = inputs.jittered_grid(2, na, seed=seed)
     n = x.shape[1]
     bflag, nrm = inputs.box_boundary(2, na)
@@ -40,8 +44,12 @@ def _system(na, nu, seed=0):
     wg, _, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "grad", bflag=bflag, normals=nrm.T)
     wl, bl, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "laplacian", bflag=bflag,
                                 normals=nrm.T)
+    pint = None
+    if staggered:
+        ws, _ = oracle.staggered_stencils(x, tg, offp, ip.reshape(-1), ep, MS, "laplacian")
+        pint = (offp, ip.reshape(-1), ws)
     A = oracle.stokes_system(2, n, bflag, nrm, (offv, iv.reshape(-1), wcc),
-                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu)
+                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu, pres_int=pint)
     return x, n, bflag, nrm, A, bl[:, 0]
 
 
@@ -65,9 +73,10 @@ def _residual(A, n, bflag, nrm, beta, u, p, f, w, div_f):
     return A @ xe - b, np.abs(A) @ np.abs(xe) + np.abs(b)
 
 
+@pytest.mark.parametrize("staggered", [False, True])
 @pytest.mark.parametrize("nu", [1.0, 0.37])
-def test_polynomial_fields_are_reproduced(nu):
-    x, n, bflag, nrm, A, beta = _system(18, nu)
+def test_polynomial_fields_are_reproduced(nu, staggered):
+    x, n, bflag, nrm, A, beta = _system(18, nu, staggered=staggered)
     u, p, f, div_f = _polynomial_fields(x, nu)
     r, scale = _residual(A, n, bflag, nrm, beta, u, p, f, u, div_f)
     rows = slice(0, 3 * n)  # all but the zero-mean row
@@ -145,22 +154,24 @@ def _solve_errors(x, n, A, bflag, nrm, beta, u, p, f, w, div_f):
     return eu, ep, sol[-1]
 
 
+@pytest.mark.parametrize("staggered", [False, True])
 @pytest.mark.parametrize("nu", [1.0, 0.37])
-def test_polynomial_solution_is_recovered(nu):
+def test_polynomial_solution_is_recovered(nu, staggered):
     """The analogue of the paper's polynomial tables (Sec. 4.1): a velocity
     and pressure inside the bases are recovered by the solve up to rounding."""
-    x, n, bflag, nrm, A, beta = _system(18, nu)
+    x, n, bflag, nrm, A, beta = _system(18, nu, staggered=staggered)
     u, p, f, div_f = _polynomial_fields(x, nu)
     eu, ep, lam = _solve_errors(x, n, A, bflag, nrm, beta, u, p, f, u, div_f)
     assert eu < 1e-9 * np.abs(u).max() and ep < 1e-8 * np.abs(p).max(), (eu, ep)
 
 
-def test_trigonometric_solution_converges():
+@pytest.mark.parametrize("staggered", [False, True])
+def test_trigonometric_solution_converges(staggered):
     """Manufactured trigonometric field (Sec. 4.2 in 2D): the RMS error of the
     solved velocity and pressure decays at about the order of the basis."""
     hs, eus, eps_ = [], [], []
     for na in (16, 24, 32):
-        x, n, bflag, nrm, A, beta = _system(na, 1.0)
+        x, n, bflag, nrm, A, beta = _system(na, 1.0, staggered=staggered)
         d = inputs.stokes_manufactured_2d(x, 1.0)
         eu, ep, _ = _solve_errors(x, n, A, bflag, nrm, beta, d["u"], d["p"], d["f"], d["w"], d["div_f"])
         hs.append(1.0 / na)
@@ -169,3 +180,49 @@ def test_trigonometric_solution_converges():
     ru = np.polyfit(np.log(hs), np.log(eus), 1)[0]
     rp = np.polyfit(np.log(hs), np.log(eps_), 1)[0]
     assert ru > M - 1 and rp > M - 1, (ru, rp, eus, eps_)
+
+
+def test_staggered_interior_rows():
+    """With the staggered interior Laplacian only the interior pressure rows
+    change; their weights sum to zero (the target's own weight is minus the
+    sum of the others); dropping that self weight (a planted slip) breaks the
+    reproduction of a pressure with a constant part."""
+    import scipy.sparse as sp
+
+    x, n, bflag, nrm, A0, beta = _system(18, 1.0)
+    _, _, _, _, A1, _ = _system(18, 1.0, staggered=True)
+    nd = 2 * n
+    bf = bflag.astype(bool)
+    D = (A1 - A0).tocsr()
+    D.eliminate_zeros()
+    changed = np.unique(D.tocoo().row)
+    assert np.all(changed >= nd) and np.all(changed < nd + n) and np.all(~bf[changed - nd])
+    assert len(changed) == np.count_nonzero(~bf)
+    Ai = A1[nd:nd + n, nd:nd + n].tocsr()
+    rs = np.asarray(Ai.sum(axis=1)).ravel()
+    sc = np.asarray(abs(Ai).sum(axis=1)).ravel()
+    assert np.all(np.abs(rs[~bf]) <= 1e-12 * sc[~bf])
+    u, p, f, div_f = _polynomial_fields(x, 1.0)
+    C = A1.tocoo()
+    drop = (C.row >= nd) & (C.row < nd + n) & (C.col == C.row)
+    drop &= ~bf[np.clip(C.row - nd, 0, n - 1)]
+    Af = sp.csr_matrix((np.where(drop, 0.0, C.data), (C.row, C.col)), shape=A1.shape)
+    r, scale = _residual(Af, n, bflag, nrm, beta, u, p, f, u, div_f)
+    assert np.max(np.abs(r[nd:nd + n]) / scale[nd:nd + n]) > 1e-3
+
+
+def test_manufactured_field_converges_staggered():
+    hs, res = [], {"mom": [], "p_int": [], "p_bdry": []}
+    for na in (20, 28, 40):
+        x, n, bflag, nrm, A, beta = _system(na, 1.0, staggered=True)
+        d = inputs.stokes_manufactured_2d(x, 1.0)
+        r, _ = _residual(A, n, bflag, nrm, beta, d["u"], d["p"], d["f"], d["w"], d["div_f"])
+        bf = bflag.astype(bool)
+        pr = np.abs(r[2 * n:3 * n])
+        hs.append(1.0 / na)
+        res["mom"].append(np.abs(r[:2 * n]).reshape(n, 2)[~bf].max())
+        res["p_int"].append(pr[~bf].max())
+        res["p_bdry"].append(pr[bf].max())
+    slope = {k: np.polyfit(np.log(hs), np.log(v), 1)[0] for k, v in res.items()}
+    assert slope["p_int"] > MS - 0.7, (slope, res)
+    assert slope["mom"] > M - 1 - 0.7 and slope["p_bdry"] > M - 2 - 0.7, (slope, res)
