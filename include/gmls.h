@@ -251,7 +251,10 @@ gmls_status gmls_assemble_csr_at(gmls_ctx* ctx, int64_t stencil_id, int32_t func
  *   I d + c, interior I:  nu * curl curl weights (velocity columns), then the
  *                         gradient row c (pressure columns)
  *   I d + c, boundary I:  1 at column I d + c (Dirichlet)
- *   n d + I, interior I:  Laplacian weights, then 1 at the multiplier
+ *   n d + I, interior I:  Laplacian weights, then 1 at the multiplier; with
+ *                         pressure_interior != 0 the staggered Laplacian
+ *                         weights on that handle's neighbour lists
+ *                         (Sec. 3.2, Eq. laplacian-pressure-stencil)
  *   n d + I, boundary I:  -nu * beta_I * (n_I . curl curl weights) on the
  *                         velocity columns (n . a evaluated
  *                         ((n_0 a_0) + (n_1 a_1)) + (n_2 a_2), then
@@ -267,12 +270,17 @@ gmls_status gmls_assemble_csr_at(gmls_ctx* ctx, int64_t stencil_id, int32_t func
  * then passes device buffers row_ptr (int64 [n_rows + 1]), col (int32 [nnz])
  * and val (double [nnz]) to gmls_stokes_assemble, which is asynchronous.
  * GMLS_EINVAL for handles of the wrong kind, different clouds, target lists,
- * a cloud without flags or normals, or more than 2^31 unknowns.
+ * a cloud without flags or normals, or more than 2^31 unknowns;
+ * GMLS_ENOTFOUND for a handle that does not exist.
  */
 typedef struct {
-  int64_t velocity; /* stencil handle (divergence-free basis, curl curl) */
-  int64_t pressure; /* stencil handle (scalar basis, gradient + Laplacian, neumann = 1) */
-  double nu;        /* kinematic viscosity, >= 0 */
+  int64_t velocity;          /* stencil handle (divergence-free basis, curl curl) */
+  int64_t pressure;          /* stencil handle (scalar basis, gradient + Laplacian, neumann = 1) */
+  double nu;                 /* kinematic viscosity, >= 0 */
+  int64_t pressure_interior; /* 0, or a stencil handle (staggered basis, Laplacian; every point
+                                of the same cloud in order) whose weights form the interior
+                                pressure rows; the boundary rows keep the scalar handle's
+                                constrained Laplacian.  The right-hand side does not depend on it. */
 } gmls_stokes_params;
 
 gmls_status gmls_stokes_size(gmls_ctx* ctx, const gmls_stokes_params* params, int64_t* n_rows, int64_t* nnz);

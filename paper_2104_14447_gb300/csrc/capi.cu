@@ -1300,6 +1300,22 @@ static gmls_status stokes_job(gmls_ctx* ctx, const gmls_stokes_params* p, Stokes
   if ((int64_t)c.n * (c.dim + 1) + 1 >= INT32_MAX)
     return fail(ctx, GMLS_EINVAL, std::string(who) + ": too many unknowns for 32-bit column indices");
   if (!(p->nu >= 0.0)) return fail(ctx, GMLS_EINVAL, std::string(who) + ": nu must be >= 0");
+  const StencilObj* ss = nullptr;
+  const NbrObj* ns = nullptr;
+  int fs = -1;
+  if (p->pressure_interior != 0) {
+    auto is = ctx->objs.find(p->pressure_interior);
+    if (is == ctx->objs.end() || is->second.kind != K_STENCIL)
+      return fail(ctx, GMLS_ENOTFOUND, std::string(who) + ": no such stencil handle (pressure_interior)");
+    ss = &is->second.s;
+    fs = find_out(*ss, GMLS_F_LAPLACIAN);
+    if (ss->basis != GMLS_BASIS_STAGGERED || fs < 0)
+      return fail(ctx, GMLS_EINVAL, std::string(who) + ": pressure_interior needs the staggered basis with the Laplacian");
+    ns = &ctx->objs.at(ss->nbrs).nb;
+    if (ns->cloud != nv.cloud || !ns->all_targets)
+      return fail(ctx, GMLS_EINVAL,
+                  std::string(who) + ": the staggered stencils must cover every point of the same cloud, in order");
+  }
   std::memset(j, 0, sizeof(*j));
   j->dim = c.dim;
   j->n = c.n;
@@ -1316,6 +1332,11 @@ static gmls_status stokes_job(gmls_ctx* ctx, const gmls_stokes_params* p, Stokes
   j->beta_col = sp.src[fl];
   j->bflag = c.bflag;
   j->normals = c.normals;
+  if (ss) {
+    j->off_s = ns->off;
+    j->idx_s = ns->idx;
+    j->w_stag = ss->w[fs];
+  }
   *n_rows = c.n * c.dim + c.n + 1;
   return GMLS_OK;
 }
@@ -1385,6 +1406,11 @@ gmls_status gmls_stokes_assemble(gmls_ctx* ctx, const gmls_stokes_params* p, int
       return r;
     j.order_v = nv.order;
     j.order_p = np.order;
+    if (p->pressure_interior != 0) {
+      NbrObj& ns = ctx->objs.at(ctx->objs.at(p->pressure_interior).s.nbrs).nb;
+      if ((r = ensure_order(ctx, ns, "gmls_stokes_assemble"))) return r;
+      j.order_s = ns.order;
+    }
   }
   r = stokes_rows(ctx, j, nr, row_ptr, "gmls_stokes_assemble");
   if (r) return r;

@@ -270,8 +270,12 @@ struct StokesJob {
   int beta_stride, beta_col;
   const uint8_t* bflag;      // [n]
   const double* normals;     // [c n + I]
+  const int64_t* off_s;      // staggered interior Laplacian lists (nullptr: interior
+  const int32_t* idx_s;      //   pressure rows take w_lap on the pressure lists)
+  const double* w_stag;      // [off_s[I] + j]
   const int16_t* order_v;    // id order of the velocity lists
   const int16_t* order_p;    // id order of the pressure lists
+  const int16_t* order_s;    // id order of the staggered lists
   int32_t* row_len;          // scratch [n d + n + 1]
   int64_t* row_ptr;          // [n d + n + 2]
   int32_t* col;

@@ -7,7 +7,8 @@
 // stokes-pressure-neumann-target):
 //   interior point I, component c:  nu (curl curl stencil) v + (gradient stencil) phi
 //   boundary point I, component c:  v_{I,c}                            (delta rows)
-//   interior point I, pressure:     (Laplacian stencil) phi + lambda
+//   interior point I, pressure:     (Laplacian stencil) phi + lambda, the
+//                                   staggered one (Sec. 2.4) when given
 //   boundary point I, pressure:     -nu beta_I n_I . (curl curl stencil) v
 //                                   + (Neumann-constrained Laplacian stencil) phi + lambda
 //   last row:                       sum_J phi_J                        (zero mean)
@@ -45,7 +46,8 @@ __global__ void stokes_rowlen_kernel(StokesJob j) {
     const int kp = (int)(j.off_p[I + 1] - j.off_p[I]);
     const bool bnd = j.bflag[I] != 0;
     for (int c = 0; c < d; ++c) j.row_len[I * d + c] = bnd ? 1 : kv * d + kp;
-    j.row_len[nd + I] = bnd ? kv * d + kp + 1 : kp + 1;
+    const int kl = j.off_s ? (int)(j.off_s[I + 1] - j.off_s[I]) : kp;  // interior Laplacian row
+    j.row_len[nd + I] = bnd ? kv * d + kp + 1 : kl + 1;
     if (I == 0) j.row_len[nd + j.n] = (int32_t)j.n;
   }
 }
@@ -76,15 +78,23 @@ __global__ void __launch_bounds__(kStokesWarps * 32) stokes_fill_kernel(StokesJo
           j.val[s + kvd + e] = j.w_grad[op * D + (int64_t)c * kp + pp];
         }
       }
+      // Laplacian row: the staggered stencil on its own list, else the
+      // scalar one on the pressure list
       const int64_t s = j.row_ptr[nd + I];
-      for (int e = lane; e < kp; e += 32) {
-        const int pp = j.order_p[op + e];
-        j.col[s + e] = (int32_t)(nd + j.idx_p[op + pp]);
-        j.val[s + e] = j.w_lap[op + pp];
+      const bool stag = j.off_s != nullptr;
+      const int64_t ol = stag ? j.off_s[I] : op;
+      const int kl = stag ? (int)(j.off_s[I + 1] - ol) : kp;
+      const int16_t* ord = stag ? j.order_s : j.order_p;
+      const int32_t* idx = stag ? j.idx_s : j.idx_p;
+      const double* wl = stag ? j.w_stag : j.w_lap;
+      for (int e = lane; e < kl; e += 32) {
+        const int pp = ord[ol + e];
+        j.col[s + e] = (int32_t)(nd + idx[ol + pp]);
+        j.val[s + e] = wl[ol + pp];
       }
       if (lane == 0) {
-        j.col[s + kp] = (int32_t)(nd + n);
-        j.val[s + kp] = 1.0;
+        j.col[s + kl] = (int32_t)(nd + n);
+        j.val[s + kl] = 1.0;
       }
     } else {
       if (lane < D) {

@@ -75,7 +75,8 @@ class Request(ctypes.Structure):
 
 
 class StokesParams(ctypes.Structure):
-    _fields_ = [("velocity", ctypes.c_int64), ("pressure", ctypes.c_int64), ("nu", ctypes.c_double)]
+    _fields_ = [("velocity", ctypes.c_int64), ("pressure", ctypes.c_int64), ("nu", ctypes.c_double),
+                ("pressure_interior", ctypes.c_int64)]
 
 
 class GmresParams(ctypes.Structure):
@@ -282,20 +283,22 @@ class Context:
         return out
 
     # ------------------------------------------------------- Stokes system
-    def stokes_size(self, velocity: int, pressure: int, nu: float):
-        """(n_rows, nnz) of the collocation system (gmls_stokes_size)."""
-        p = StokesParams(velocity, pressure, nu)
+    def stokes_size(self, velocity: int, pressure: int, nu: float, pressure_interior: int = 0):
+        """(n_rows, nnz) of the collocation system (gmls_stokes_size);
+        pressure_interior: 0, or staggered Laplacian stencils for the interior
+        pressure rows."""
+        p = StokesParams(velocity, pressure, nu, pressure_interior)
         r, z = ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.gmls_stokes_size(self.h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(z)))
         return r.value, z.value
 
-    def stokes_assemble(self, velocity: int, pressure: int, nu: float):
+    def stokes_assemble(self, velocity: int, pressure: int, nu: float, pressure_interior: int = 0):
         """The collocation system as device CSR tensors (row_ptr, col, val)."""
-        nr, nnz = self.stokes_size(velocity, pressure, nu)
+        nr, nnz = self.stokes_size(velocity, pressure, nu, pressure_interior)
         rp = torch.empty(nr + 1, dtype=torch.int64, device=self.device)
         col = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
         val = torch.empty(max(nnz, 1), dtype=torch.float64, device=self.device)
-        p = StokesParams(velocity, pressure, nu)
+        p = StokesParams(velocity, pressure, nu, pressure_interior)
         self._check(self.lib.gmls_stokes_assemble(self.h, ctypes.byref(p), _ptr(rp), _ptr(col), _ptr(val)))
         return rp, col, val
 

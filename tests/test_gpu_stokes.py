@@ -9,7 +9,9 @@ lists and stencils.
   the oracle's, relative to sum |a| |x| + |b|;
 * at GPU scale, the manufactured-field residual decays at the rates the
   oracle pins (h^(m-1) interior, h^(m-2) boundary pressure rows) and the
-  Dirichlet rows are exact.
+  Dirichlet rows are exact;
+* each with the interior pressure rows taken either from the scalar
+  Laplacian or from the staggered one of degree m - 1 (Sec. 3.2).
 """
 import math
 
@@ -23,6 +25,7 @@ from paper_2104_14447_gb300 import gmls, inputs
 pytestmark = pytest.mark.gpu
 
 M, KV, KP = 4, 48, 36
+MS = 3  # staggered interior Laplacian degree
 TOL = {gmls.FP64: 1e-10, gmls.FP32_REFINE: 1e-9}
 
 
@@ -39,7 +42,7 @@ def ctx():
     c.close()
 
 
-def _gpu(ctx, na, precision, nu):
+def _gpu(ctx, na, precision, nu, staggered=False):
     x = inputs.jittered_grid(2, na, seed=0)
     bflag, nrm = inputs.box_boundary(2, na)
     cid = ctx.cloud(x, normals=nrm, bflags=bflag)
@@ -47,8 +50,13 @@ def _gpu(ctx, na, precision, nu):
     npr = ctx.neighbors_prefix(nv, KP, 1.5)
     sv = ctx.stencils(nv, gmls.DIVFREE, M, [gmls.CURLCURL], precision=precision)
     sp = ctx.stencils(npr, gmls.SCALAR, M, [gmls.GRAD, gmls.LAPLACIAN], precision=precision, neumann=True)
-    rp, col, val = ctx.stokes_assemble(sv, sp, nu)
-    return x, bflag, nrm, (cid, nv, npr, sv, sp), (rp, col, val)
+    ids = (cid, nv, npr, sv, sp)
+    ss = 0
+    if staggered:
+        ss = ctx.stencils(npr, gmls.STAGGERED, MS, [gmls.LAPLACIAN], precision=precision)
+        ids += (ss,)
+    rp, col, val = ctx.stokes_assemble(sv, sp, nu, ss)
+    return x, bflag, nrm, ids, (rp, col, val)
 
 
 def _release(ctx, ids):
@@ -56,7 +64,7 @@ def _release(ctx, ids):
         ctx.release(h)
 
 
-def _oracle(x, bflag, nrm, nu):
+def _oracle(x, bflag, nrm, nu, staggered=False):
     n = x.shape[1]
     tg = np.arange(n, dtype=np.int32)
     iv, ev = oracle.knn(x, tg, KV, 1.5, method="grid")
@@ -67,18 +75,23 @@ def _oracle(x, bflag, nrm, nu):
     wg, _, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "grad", bflag=bflag, normals=nrm.T)
     wl, bl, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M, "laplacian", bflag=bflag,
                                 normals=nrm.T)
+    pint = None
+    if staggered:
+        ws, _ = oracle.staggered_stencils(x, tg, offp, ip.reshape(-1), ep, MS, "laplacian")
+        pint = (offp, ip.reshape(-1), ws)
     A = oracle.stokes_system(2, n, bflag, nrm, (offv, iv.reshape(-1), wcc),
-                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu)
+                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu, pres_int=pint)
     return A, bl[:, 0]
 
 
+@pytest.mark.parametrize("staggered", [False, True])
 @pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
-def test_system_matches_oracle(ctx, precision):
+def test_system_matches_oracle(ctx, precision, staggered):
     nu = 0.7
-    x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, 30, precision, nu)
+    x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, 30, precision, nu, staggered)
     n = x.shape[1]
     nd = 2 * n
-    A, beta = _oracle(x, bflag, nrm, nu)
+    A, beta = _oracle(x, bflag, nrm, nu, staggered)
     rp, col, val = rp.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
     assert np.array_equal(rp, A.indptr) and np.array_equal(col, A.indices)
     tol = TOL[precision]
@@ -143,7 +156,18 @@ def test_bad_handles_are_rejected(ctx):
     assert e.value.code == gmls.EINVAL
     with pytest.raises(gmls.GmlsError):
         ctx.stokes_size(sp_plain, sv, 1.0)  # roles swapped
-    _release(ctx, [cid, nv, sv, sp_plain])
+    sp = ctx.stencils(nv, gmls.SCALAR, M, [gmls.GRAD, gmls.LAPLACIAN], neumann=True)
+    with pytest.raises(gmls.GmlsError) as e:
+        ctx.stokes_size(sv, sp, 1.0, sp_plain)  # interior rows from a non-staggered handle
+    assert e.value.code == gmls.EINVAL
+    with pytest.raises(gmls.GmlsError) as e:
+        ctx.stokes_size(sv, sp, 1.0, 10 ** 9)  # no such handle
+    assert e.value.code == gmls.ENOTFOUND
+    sg = ctx.stencils(nv, gmls.STAGGERED, MS, [gmls.GRAD])  # no Laplacian
+    with pytest.raises(gmls.GmlsError) as e:
+        ctx.stokes_size(sv, sp, 1.0, sg)
+    assert e.value.code == gmls.EINVAL
+    _release(ctx, [cid, nv, sv, sp_plain, sp, sg])
 
 
 @pytest.mark.parametrize("n_extra_long", [20, 70])
@@ -180,13 +204,14 @@ def _solve_errors(x, n, sol, u, p):
     return eu, ep
 
 
-def test_gmres_solution_matches_direct_solve(ctx):
+@pytest.mark.parametrize("staggered", [False, True])
+def test_gmres_solution_matches_direct_solve(ctx, staggered):
     """The GPU solve (gmls_gmres on the GPU system) against the oracle's
     direct solve of the oracle's system, 32 x 32, FP64 stencils."""
     nu = 1.0
-    x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, 32, gmls.FP64, nu)
+    x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, 32, gmls.FP64, nu, staggered)
     n = x.shape[1]
-    A, beta = _oracle(x, bflag, nrm, nu)
+    A, beta = _oracle(x, bflag, nrm, nu, staggered)
     d = inputs.stokes_manufactured_2d(x, nu)
     b_orc = oracle.stokes_rhs(2, n, bflag, nrm, d["f"], d["w"], d["div_f"], beta)
     sol_orc = oracle.stokes_solve(A, b_orc)
@@ -206,12 +231,13 @@ def test_gmres_solution_matches_direct_solve(ctx):
     _release(ctx, ids)
 
 
-def test_gmres_solution_converges_at_scale(ctx):
+@pytest.mark.parametrize("staggered", [False, True])
+def test_gmres_solution_converges_at_scale(ctx, staggered):
     """Solved trigonometric field at 32^2 .. 128^2 (FP32 + refinement
     stencils): RMS errors decay at about the order of the basis."""
     hs, eus, eps_ = [], [], []
     for na in (32, 64, 128):
-        x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, na, gmls.FP32_REFINE, 1.0)
+        x, bflag, nrm, ids, (rp, col, val) = _gpu(ctx, na, gmls.FP32_REFINE, 1.0, staggered)
         n = x.shape[1]
         d = inputs.stokes_manufactured_2d(x, 1.0)
         b = ctx.stokes_rhs(ids[3], ids[4], 1.0, d["f"], d["w"], d["div_f"])
