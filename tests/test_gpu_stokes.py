@@ -251,3 +251,62 @@ def test_gmres_solution_converges_at_scale(ctx, staggered):
     ru = np.polyfit(np.log(hs), np.log(eus), 1)[0]
     rp_ = np.polyfit(np.log(hs), np.log(eps_), 1)[0]
     assert ru > M - 1 and rp_ > M - 1, (ru, rp_, eus, eps_)
+
+
+M3, KV3, KP3 = 3, 80, 40
+
+
+@pytest.mark.parametrize("staggered", [False, True])
+@pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
+def test_system_matches_oracle_3d(ctx, precision, staggered):
+    """The 3D system (div-free degree 3 on 80 neighbours: 240 x 50; scalar
+    degree 3 on the 40-prefix with the Neumann constraint on the cube's
+    faces, edges and corners; optionally the staggered degree-2 Laplacian on
+    the interior pressure rows) against the oracle's, and its A x."""
+    nu = 0.6
+    na = 9
+    x = inputs.jittered_grid(3, na, seed=1)
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(3, na)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, KV3, 1.5)
+    npr = ctx.neighbors_prefix(nv, KP3, 1.5)
+    sv = ctx.stencils(nv, gmls.DIVFREE, M3, [gmls.CURLCURL], precision=precision)
+    sp = ctx.stencils(npr, gmls.SCALAR, M3, [gmls.GRAD, gmls.LAPLACIAN], precision=precision, neumann=True)
+    ids = [cid, nv, npr, sv, sp]
+    ss = 0
+    if staggered:
+        ss = ctx.stencils(npr, gmls.STAGGERED, M3 - 1, [gmls.LAPLACIAN], precision=precision)
+        ids.append(ss)
+    rp, col, val = (t.cpu().numpy() for t in ctx.stokes_assemble(sv, sp, nu, ss))
+    tg = np.arange(n, dtype=np.int32)
+    iv, ev = oracle.knn(x, tg, KV3, 1.5)
+    ip, ep = oracle.knn(x, tg, KP3, 1.5)
+    offv = np.arange(0, n * KV3 + 1, KV3)
+    offp = np.arange(0, n * KP3 + 1, KP3)
+    wcc, _, _ = oracle.stencils(x, tg, offv, iv.reshape(-1), ev, "divfree", M3, "curlcurl")
+    wg, _, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M3, "grad", bflag=bflag, normals=nrm.T)
+    wl, bl, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M3, "laplacian", bflag=bflag,
+                                normals=nrm.T)
+    pint = None
+    if staggered:
+        ws, _ = oracle.staggered_stencils(x, tg, offp, ip.reshape(-1), ep, M3 - 1, "laplacian")
+        pint = (offp, ip.reshape(-1), ws)
+    A = oracle.stokes_system(3, n, bflag, nrm, (offv, iv.reshape(-1), wcc),
+                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu, pres_int=pint)
+    assert np.array_equal(rp, A.indptr) and np.array_equal(col, A.indices)
+    nd = 3 * n
+    block = np.where(A.indices < nd, 0, np.where(A.indices < nd + n, 1, 2))
+    row = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    key = row * 3 + block
+    scale = np.zeros(A.shape[0] * 3)
+    np.maximum.at(scale, key, np.abs(A.data))
+    err = np.abs(val - A.data) / np.where(scale[key] > 0, scale[key], 1.0)
+    tol = TOL[precision]
+    assert err.max() <= tol, err.max()
+    rng = np.random.default_rng(5)
+    xr = rng.standard_normal(A.shape[0])
+    y_gpu = ctx.spmv(torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), torch.from_numpy(val).cuda(),
+                     xr).cpu().numpy()
+    assert np.all(np.abs(y_gpu - A @ xr) <= tol * (np.abs(A) @ np.abs(xr)) + 1e-300)
+    _release(ctx, ids)

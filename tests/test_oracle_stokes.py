@@ -226,3 +226,104 @@ def test_manufactured_field_converges_staggered():
     slope = {k: np.polyfit(np.log(hs), np.log(v), 1)[0] for k, v in res.items()}
     assert slope["p_int"] > MS - 0.7, (slope, res)
     assert slope["mom"] > M - 1 - 0.7 and slope["p_bdry"] > M - 2 - 0.7, (slope, res)
+
+
+# ------------------------------------------------------------------- 3D
+M3, KV3, KP3 = 3, 80, 40  # the porous-medium stencils: div-free 240 x 50, scalar 40 x 20
+
+
+def _system3(na, nu, staggered=False):
+    x = inputs.jittered_grid(3, na, seed=1)
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(3, na)
+    tg = np.arange(n, dtype=np.int32)
+    iv, ev = oracle.knn(x, tg, KV3, 1.5)
+    ip, ep = oracle.knn(x, tg, KP3, 1.5)
+    offv = np.arange(0, n * KV3 + 1, KV3)
+    offp = np.arange(0, n * KP3 + 1, KP3)
+    wcc, _, _ = oracle.stencils(x, tg, offv, iv.reshape(-1), ev, "divfree", M3, "curlcurl")
+    wg, _, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M3, "grad", bflag=bflag, normals=nrm.T)
+    wl, bl, _ = oracle.stencils(x, tg, offp, ip.reshape(-1), ep, "scalar", M3, "laplacian", bflag=bflag,
+                                normals=nrm.T)
+    pint = None
+    if staggered:
+        ws, _ = oracle.staggered_stencils(x, tg, offp, ip.reshape(-1), ep, M3 - 1, "laplacian")
+        pint = (offp, ip.reshape(-1), ws)
+    A = oracle.stokes_system(3, n, bflag, nrm, (offv, iv.reshape(-1), wcc),
+                             (offp, ip.reshape(-1), wg, wl, bl[:, 0]), nu, pres_int=pint)
+    return x, n, bflag, nrm, A, bl[:, 0]
+
+
+def _polynomial_fields_3d(x, nu):
+    """v = curl a (a of degree 4, so v is divergence-free of degree 3),
+    p of degree 3; f = nu curl curl v + grad p, div f = Laplacian p."""
+    X, Y, Z = sympy.symbols("x y z")
+    V = (X, Y, Z)
+    a = [X ** 2 * Y * Z - 2 * Y ** 3 * Z + X * Z ** 3,
+         X ** 3 * Z - X * Y ** 2 * Z + 3 * Y * Z ** 3 - X ** 4,
+         X * Y ** 3 - 2 * X ** 2 * Z ** 2 + Y ** 2 * Z ** 2 + Z ** 4]
+
+    def curl(u):
+        return [sympy.diff(u[2], Y) - sympy.diff(u[1], Z), sympy.diff(u[0], Z) - sympy.diff(u[2], X),
+                sympy.diff(u[1], X) - sympy.diff(u[0], Y)]
+
+    v = curl(a)
+    cc = curl(curl(v))
+    p = X ** 3 - 2 * X * Y * Z + 3 * Y ** 2 * Z - Z ** 3 + X * Y - 1
+    f = [nu * cc[c] + sympy.diff(p, V[c]) for c in range(3)]
+    div_f = sum(sympy.diff(f[c], V[c]) for c in range(3))
+    assert sympy.simplify(sum(sympy.diff(v[c], V[c]) for c in range(3))) == 0
+    ev = lambda e: np.asarray(sympy.lambdify(V, e, "numpy")(x[0], x[1], x[2]), dtype=np.float64) * np.ones(x.shape[1])
+    return np.stack([ev(e) for e in v]), ev(p), np.stack([ev(e) for e in f]), ev(div_f)
+
+
+@pytest.mark.parametrize("staggered", [False, True])
+def test_polynomial_fields_are_reproduced_3d(staggered):
+    """The 3D system (div-free degree 3 on 80 neighbours, scalar degree 3 on
+    40, unit-cube boundary with edge and corner normals): every row but the
+    zero-mean one holds for a divergence-free cubic velocity and a cubic
+    pressure."""
+    nu = 0.6
+    x, n, bflag, nrm, A, beta = _system3(7, nu, staggered)
+    u, p, f, div_f = _polynomial_fields_3d(x, nu)
+    xe = np.concatenate([u.T.reshape(-1), p, [0.0]])
+    b = oracle.stokes_rhs(3, n, bflag, nrm, f, u, div_f, beta)
+    r = A @ xe - b
+    scale = np.abs(A) @ np.abs(xe) + np.abs(b)
+    rows = slice(0, 4 * n)
+    assert np.max(np.abs(r[rows]) / scale[rows]) < 1e-10
+    bf = bflag.astype(bool)
+    assert 0 < bf.sum() < n and np.all(beta[bf] != 0.0) and np.all(beta[~bf] == 0.0)
+
+
+def test_planted_normal_mixup_is_caught_3d():
+    """The same check with the boundary rows assembled from normals whose y
+    and z components are swapped fails on the boundary pressure rows."""
+    nu = 0.6
+    x, n, bflag, nrm, A, beta = _system3(7, nu)
+    u, p, f, div_f = _polynomial_fields_3d(x, nu)
+    tg = np.arange(n, dtype=np.int32)
+    iv, ev = oracle.knn(x, tg, KV3, 1.5)
+    offv = np.arange(0, n * KV3 + 1, KV3)
+    wcc, _, _ = oracle.stencils(x, tg, offv, iv.reshape(-1), ev, "divfree", M3, "curlcurl")
+    # rebuild with mixed-up normals in the coupling only (the stencils keep the right ones)
+    C = A.tocoo()
+    keep = ~((C.row >= 3 * n) & (C.row < 4 * n) & (C.col < 3 * n))
+    bad = nrm[[0, 2, 1]]
+    rows, cols, vals = [C.row[keep]], [C.col[keep]], [C.data[keep]]
+    for I in np.flatnonzero(bflag):
+        a3 = np.asarray(wcc[I])
+        nda = bad[0][I] * a3[0] + bad[1][I] * a3[1] + bad[2][I] * a3[2]
+        jv = iv[I].astype(np.int64)
+        rows.append(np.full(3 * KV3, 3 * n + I))
+        cols.append((jv[:, None] * 3 + np.arange(3)[None, :]).reshape(-1))
+        vals.append(-(nu * (beta[I] * nda)).reshape(-1))
+    import scipy.sparse as sp
+
+    Af = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=A.shape)
+    xe = np.concatenate([u.T.reshape(-1), p, [0.0]])
+    b = oracle.stokes_rhs(3, n, bflag, nrm, f, u, div_f, beta)
+    r = Af @ xe - b
+    scale = np.abs(Af) @ np.abs(xe) + np.abs(b)
+    pr = slice(3 * n, 4 * n)
+    assert np.max(np.abs(r[pr]) / scale[pr]) > 1e-3
