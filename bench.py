@@ -563,7 +563,87 @@ def gmls_basis_size(d, b, m):
     return full - (comb(m - 1 + d, d))  # minus the divergence map's rank (onto degree m - 1)
 
 
-def porous_3d(ctx, n_axis=128, steps=3, n_sample=48):
+def porous_stokes(ctx, pc, n80, n40, ssc, flush, steps=3, nu=1.0):
+    """The 3D Stokes collocation system (Sec. 3.2) on the porous cube, from
+    the porous step's neighbour lists and Neumann-constrained scalar stencils
+    plus degree-3 divergence-free curl curl stencils: assembly + right-hand
+    side and one A x, CUDA events on the context stream, L2 flushed, bytes
+    against the measured HBM rate; then, at full size, the residual of the
+    cubic Stokes data (inputs.stokes_cubic_3d, inside the degree-3 bases, so
+    every row but the zero-mean one holds up to the stencils' rounding),
+    relative to sum |a| |x| + |b| per row."""
+    import ctypes
+
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    x = pc["x"]
+    n = x.shape[1]
+    stream = ctx.stream
+    scc = ctx.stencils(n80, gmls.DIVFREE, 3, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+    n_rows, nnz = ctx.stokes_size(scc, ssc, nu)
+    rp = torch.empty(n_rows + 1, dtype=torch.int64, device=ctx.device)
+    col = torch.empty(nnz, dtype=torch.int32, device=ctx.device)
+    val = torch.empty(nnz, dtype=torch.float64, device=ctx.device)
+    d = inputs.stokes_cubic_3d(x, nu)
+    f, w, div_f = (torch.from_numpy(np.ascontiguousarray(a)).to(ctx.device) for a in (d["f"], d["w"], d["div_f"]))
+    xe = torch.from_numpy(np.concatenate([d["u"].T.reshape(-1), d["p"], [0.0]])).to(ctx.device)
+    b = torch.empty(n_rows, dtype=torch.float64, device=ctx.device)
+    y = torch.empty(n_rows, dtype=torch.float64, device=ctx.device)
+    P = gmls.StokesParams(scc, ssc, nu)
+    lib, h = ctx.lib, ctx.h
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    def assemble():
+        ctx._check(lib.gmls_stokes_assemble(h, ctypes.byref(P), ptr(rp), ptr(col), ptr(val)))
+        ctx._check(lib.gmls_stokes_rhs(h, ctypes.byref(P), ptr(f), ptr(w), ptr(div_f), ptr(b)))
+
+    def spmv(v, xv, out):
+        ctx._check(lib.gmls_csr_spmv(h, n_rows, ptr(rp), ptr(col), ptr(v), ptr(xv), ptr(out)))
+
+    assemble()
+    spmv(val, xe, y)
+    ta, tm = [], []
+    for s in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            assemble()
+            e[1].record(stream)
+            spmv(val, xe, y)
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        ta.append(e[0].elapsed_time(e[1]))
+        tm.append(e[1].elapsed_time(e[2]))
+    with torch.cuda.stream(stream):
+        scale = torch.empty_like(y)
+        aval = val.abs()
+        spmv(aval, xe.abs(), scale)
+        del aval
+        rel = (y - b).abs() / (scale + b.abs())
+        bf = torch.from_numpy(pc["bflag"].astype(bool)).to(ctx.device)
+        mom = rel[:3 * n].reshape(n, 3).amax(dim=1)
+        pr = rel[3 * n:4 * n]
+        res = {"momentum_interior": float(mom[~bf].max()), "dirichlet": float(mom[bf].max()),
+               "pressure_interior": float(pr[~bf].max()), "pressure_boundary": float(pr[bf].max())}
+    torch.cuda.synchronize()
+    ctx.release(scc)
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    asm_bytes = nnz * (8 + 4 + 8) + (n_rows + 1) * 8 + n * (80 + 40) * 4 + n_rows * 8
+    spmv_bytes = nnz * (8 + 4) + (n_rows + 1) * 8 + 2 * n_rows * 8
+    ta_m, tm_m = float(np.median(ta)), float(np.median(tm))
+    return {"system": f"{n_rows} rows ({n} points x 3 velocity + pressure + multiplier), nu = {nu}",
+            "n_rows": n_rows, "nnz": nnz, "assemble_ms": ta_m, "spmv_ms": tm_m,
+            "assemble_gbs": asm_bytes / ta_m / 1e6, "spmv_gbs": spmv_bytes / tm_m / 1e6,
+            "spmv_frac_hbm": spmv_bytes / tm_m / 1e6 / hbm, "peak_source": src,
+            "cubic_data_max_rel_residual": res,
+            "l2": "flushed before each timed step (256 MB write)"}
+
+
+def porous_3d(ctx, n_axis=128, steps=3, n_sample=48, stokes=True):
     """The 3D porous-medium workload: a jittered n_axis^3 lattice in the unit
     cube minus 64 random non-overlapping spheres, boundary targets on the
     sphere surfaces and cube faces with their geometric normals.  Per step:
@@ -639,7 +719,15 @@ def porous_3d(ctx, n_axis=128, steps=3, n_sample=48):
         _, rows, nc, _ = ctx.stencil_info(sh, code)
         wg = ctx.weights(sh, code).cpu().numpy().reshape(n, rows, k, nc)[sample]
         gpu_sample["ops"].append((key, k, kind, idx, wg))
-    release(h)
+    stokes_out = None
+    if stokes:
+        ctx.release(h[3])  # the vector Laplacian stencils and the step's CSR operators: room for the system
+        h[4].clear()
+        stokes_out = porous_stokes(ctx, pc, h[0], h[1], h[2], flush)
+        for hd in (h[2], h[1], h[0]):
+            ctx.release(hd)
+    else:
+        release(h)
     ctx.release(cid)
     tune = {}
     for r in ctx.tune_log():
@@ -659,7 +747,8 @@ def porous_3d(ctx, n_axis=128, steps=3, n_sample=48):
             "divfree_qr_tflops": qr_flops * n / float(med[2]) / 1e9,
             "fp64_redo": {"scalar": int(np.sum((st_sc & gmls.T_FP64_FALLBACK) != 0)),
                           "divfree": int(np.sum((st_df & gmls.T_FP64_FALLBACK) != 0))},
-            "tune_ms": tune, "l2": "flushed before each timed step (256 MB write)"}, gpu_sample
+            "tune_ms": tune, "l2": "flushed before each timed step (256 MB write)",
+            "stokes_system": stokes_out}, gpu_sample
 
 
 def porous_oracle_errors(gs):
@@ -1100,7 +1189,7 @@ def main():
         build.build()
         ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
         if args.only == "porous":
-            res = porous_3d(ctx, n_axis=args.porous_n_axis, steps=args.steps)[0]
+            res = porous_3d(ctx, n_axis=args.porous_n_axis, steps=args.steps, stokes=False)[0]
         else:
             res = batched_uneven(ctx, n_per_dim=args.batched_n, steps=args.steps)[0]
         print(json.dumps(res), flush=True)

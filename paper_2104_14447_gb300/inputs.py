@@ -150,6 +150,23 @@ def stokes_manufactured_2d(x: np.ndarray, nu: float = 1.0):
     return {"u": m["u"], "p": m["p"], "f": f, "w": m["u"], "div_f": m["lap_p"], "curlcurl_u": curlcurl}
 
 
+def stokes_cubic_3d(x: np.ndarray, nu: float = 1.0):
+    """Data of a 3D Stokes problem (Sec. 3.1) whose solution is a
+    divergence-free cubic velocity and a cubic pressure (inside the degree-3
+    bases, so degree-3 stencils reproduce it):
+    u = (y^3 + y z^2, x^2 z + z^3, x y^2 - x^3) (no component depends on its
+    own coordinate: div u = 0), curl curl u = -lap u = (-8 y, -8 z, 4 x),
+    p = x^3 - 2 x y z + 3 y^2 z - z^3 + x y - 1, lap p = 6 x;
+    f = nu curl curl u + grad p, w = u, div f = lap p."""
+    X, Y, Z = (np.asarray(c, dtype=np.float64) for c in x[:3])
+    u = np.stack([Y ** 3 + Y * Z ** 2, X ** 2 * Z + Z ** 3, X * Y ** 2 - X ** 3])
+    cc = np.stack([-8.0 * Y, -8.0 * Z, 4.0 * X])
+    p = X ** 3 - 2.0 * X * Y * Z + 3.0 * Y ** 2 * Z - Z ** 3 + X * Y - 1.0
+    gp = np.stack([3.0 * X ** 2 - 2.0 * Y * Z + Y, -2.0 * X * Z + 6.0 * Y * Z + X, -2.0 * X * Y + 3.0 * Y ** 2 - 3.0 * Z ** 2])
+    f = nu * cc + gp
+    return {"u": u, "p": p, "f": f, "w": u, "div_f": 6.0 * X, "curlcurl_u": cc}
+
+
 def unit_vectors(seed: int, stream: int, n: int, dim: int) -> np.ndarray:
     """n random unit vectors (dim, n) from normalised uniform cube samples."""
     out = np.zeros((dim, n), dtype=np.float64)

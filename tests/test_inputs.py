@@ -80,3 +80,31 @@ def test_request_stream_recipe():
     assert abs(np.mean(np.log(n)) - 0.5 * (np.log(1e3) + np.log(5e5))) < 0.1  # log-uniform
     assert {r["degree"] for r in reqs} == {2, 3, 4} and {r["dim"] for r in reqs} == {2, 3}
     assert {r["basis"] for r in reqs} == {"scalar", "divfree"}
+
+
+def test_stokes_cubic_3d_fields():
+    """The hand-derived cubic Stokes data against symbolic differentiation."""
+    sympy = __import__("pytest").importorskip("sympy")
+    X, Y, Z = sympy.symbols("x y z")
+    V = (X, Y, Z)
+    u = [Y ** 3 + Y * Z ** 2, X ** 2 * Z + Z ** 3, X * Y ** 2 - X ** 3]
+    p = X ** 3 - 2 * X * Y * Z + 3 * Y ** 2 * Z - Z ** 3 + X * Y - 1
+
+    def curl(a):
+        return [sympy.diff(a[2], Y) - sympy.diff(a[1], Z), sympy.diff(a[0], Z) - sympy.diff(a[2], X),
+                sympy.diff(a[1], X) - sympy.diff(a[0], Y)]
+
+    assert sympy.expand(sum(sympy.diff(u[c], V[c]) for c in range(3))) == 0
+    nu = 0.45
+    cc = curl(curl(u))
+    f = [nu * cc[c] + sympy.diff(p, V[c]) for c in range(3)]
+    div_f = sum(sympy.diff(f[c], V[c]) for c in range(3))
+    x = inputs.jittered_grid(3, 5, seed=3)
+    d = inputs.stokes_cubic_3d(x, nu)
+    ev = lambda e: np.asarray(sympy.lambdify(V, e, "numpy")(*x), dtype=np.float64) * np.ones(x.shape[1])
+    for c in range(3):
+        assert np.allclose(d["u"][c], ev(u[c]), rtol=0, atol=1e-13)
+        assert np.allclose(d["curlcurl_u"][c], ev(cc[c]), rtol=0, atol=1e-13)
+        assert np.allclose(d["f"][c], ev(f[c]), rtol=0, atol=1e-13)
+    assert np.allclose(d["p"], ev(p), rtol=0, atol=1e-13)
+    assert np.allclose(d["div_f"], ev(div_f), rtol=0, atol=1e-13)
