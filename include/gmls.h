@@ -280,7 +280,8 @@ typedef struct {
   int64_t pressure_interior; /* 0, or a stencil handle (staggered basis, Laplacian; every point
                                 of the same cloud in order) whose weights form the interior
                                 pressure rows; the boundary rows keep the scalar handle's
-                                constrained Laplacian.  The right-hand side does not depend on it. */
+                                constrained Laplacian.  The right-hand side does not depend on it.
+                                Zero-initialise the struct: 0 keeps the scalar Laplacian. */
 } gmls_stokes_params;
 
 gmls_status gmls_stokes_size(gmls_ctx* ctx, const gmls_stokes_params* params, int64_t* n_rows, int64_t* nnz);
