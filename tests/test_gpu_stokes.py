@@ -343,3 +343,37 @@ def test_porous_cube_cubic_data_residual(ctx, staggered):
     assert np.all(rel[:3 * n].reshape(n, 3)[bf] == 0.0)  # Dirichlet rows
     assert rel.max() <= 1e-8, (rel[:3 * n].max(), rel[3 * n:].max())
     _release(ctx, ids)
+
+
+@pytest.mark.parametrize("staggered", [False, True])
+def test_gmres_recovers_cubic_solution_3d(ctx, staggered):
+    """The GPU solve of the 3D system (9^3 cube, FP32 + refinement stencils)
+    with the cubic Stokes data: the velocity and the mean-free pressure are
+    recovered up to the stencils' rounding (the 3D analogue of the paper's
+    polynomial tables, Sec. 4.1)."""
+    nu = 0.6
+    na = 9
+    x = inputs.jittered_grid(3, na, seed=1)
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(3, na)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, KV3, 1.5)
+    npr = ctx.neighbors_prefix(nv, KP3, 1.5)
+    sv = ctx.stencils(nv, gmls.DIVFREE, M3, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+    sp = ctx.stencils(npr, gmls.SCALAR, M3, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE, neumann=True)
+    ids = [cid, nv, npr, sv, sp]
+    ss = 0
+    if staggered:
+        ss = ctx.stencils(npr, gmls.STAGGERED, M3 - 1, [gmls.LAPLACIAN], precision=gmls.FP32_REFINE)
+        ids.append(ss)
+    rp, col, val = ctx.stokes_assemble(sv, sp, nu, ss)
+    d = inputs.stokes_cubic_3d(x, nu)
+    b = ctx.stokes_rhs(sv, sp, nu, d["f"], d["w"], d["div_f"])
+    sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=4000, rtol=1e-12)
+    assert rel <= 1e-12 and its > 0, (its, rel)
+    s = sol.cpu().numpy()
+    us, ps = s[:3 * n].reshape(n, 3).T, s[3 * n:4 * n]
+    eu = np.abs(us - d["u"]).max()
+    ep = np.abs((ps - ps.mean()) - (d["p"] - d["p"].mean())).max()
+    assert eu < 1e-7 * np.abs(d["u"]).max() and ep < 1e-6 * np.abs(d["p"]).max(), (eu, ep)
+    _release(ctx, ids)
