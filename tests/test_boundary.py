@@ -1,0 +1,76 @@
+"""The product path and the oracle stay apart (CPU only).
+
+* no module of the package imports the oracle, and importing the binding
+  does not load it;
+* bench.py imports it only inside the functions of its CPU-baseline and
+  reference legs (and the oracle side of its sampled comparisons);
+* without the built library, or without a GPU, the binding raises instead
+  of computing anything on the host.
+"""
+import ast
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_2104_14447_gb300")
+
+ORACLE_LEGS = {"porous_oracle_errors", "batched_oracle_errors", "oracle_pipeline", "cpu_baseline", "run_reference"}
+
+
+def _oracle_imports(tree):
+    """(enclosing top-level function or None, line) of every import of the oracle."""
+    out = []
+    for top in tree.body:
+        for node in ast.walk(top):
+            names = []
+            if isinstance(node, ast.Import):
+                names = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                names = [node.module or ""]
+            if any(n == "oracle" or n.startswith("oracle.") for n in names):
+                out.append((top.name if isinstance(top, ast.FunctionDef) else None, node.lineno))
+    return out
+
+
+def test_package_never_imports_the_oracle():
+    for dirpath, _, files in os.walk(PKG):
+        if "_build" in dirpath:
+            continue
+        for fn in files:
+            if fn.endswith(".py"):
+                path = os.path.join(dirpath, fn)
+                assert _oracle_imports(ast.parse(open(path).read())) == [], path
+
+
+def test_binding_import_does_not_load_the_oracle():
+    code = ("import sys; import paper_2104_14447_gb300.gmls, paper_2104_14447_gb300.inputs; "
+            "assert 'oracle' not in sys.modules")
+    subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
+
+
+def test_bench_uses_the_oracle_only_in_its_cpu_legs():
+    found = _oracle_imports(ast.parse(open(os.path.join(ROOT, "bench.py")).read()))
+    assert found, "the CPU-baseline leg should time the oracle"
+    for fn, line in found:
+        assert fn in ORACLE_LEGS, (fn, line)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    code = ("from paper_2104_14447_gb300 import gmls; "
+            f"gmls.load({str(tmp_path / 'missing' / 'libgmls.so')!r})")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode != 0 and "libgmls not built" in r.stderr
+
+
+def test_context_fails_loudly_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2104_14447_gb300 import build, gmls
+
+    build.build()
+    with pytest.raises(Exception):
+        gmls.Context(0, arena_bytes=1 << 30)
