@@ -74,3 +74,31 @@ def test_context_fails_loudly_without_gpu():
     build.build()
     with pytest.raises(Exception):
         gmls.Context(0, arena_bytes=1 << 30)
+
+
+def test_oracle_shares_no_code_with_the_cuda_path():
+    """The oracle's C source includes system headers only, its Python modules
+    import nothing from the package, and no native source or build script of
+    the package refers to the oracle."""
+    import re
+
+    odir = os.path.join(ROOT, "oracle")
+    for fn in os.listdir(odir):
+        path = os.path.join(odir, fn)
+        if fn.endswith((".c", ".h")):
+            for inc in re.findall(r'^\s*#\s*include\s*([<"][^>"]+[>"])', open(path).read(), re.M):
+                assert inc.startswith("<"), (fn, inc)
+        elif fn.endswith(".py"):
+            tree = ast.parse(open(path).read())
+            for node in ast.walk(tree):
+                mods = []
+                if isinstance(node, ast.Import):
+                    mods = [a.name for a in node.names]
+                elif isinstance(node, ast.ImportFrom) and node.level == 0:
+                    mods = [node.module or ""]
+                assert not any(m.startswith("paper_2104_14447_gb300") for m in mods), (fn, mods)
+    csrc = os.path.join(PKG, "csrc")
+    for fn in os.listdir(csrc):
+        if fn.endswith((".cu", ".cuh", ".h", ".cpp", ".py")):
+            assert "oracle" not in open(os.path.join(csrc, fn)).read(), fn
+    assert "oracle" not in open(os.path.join(PKG, "build.py")).read()
