@@ -914,13 +914,15 @@ def batched_oracle_errors(gsamples):
     return out
 
 
-def stokes_solve(ctx, n_axis=128):
+def stokes_solve(ctx, n_axis=128, full=True):
     """Global solve of the Stokes system (Sec. 3.3) on an n_axis^2 grid by
     GMRES(100) with right Jacobi preconditioning (gmls_gmres), to a relative
     residual of 1e-10; RMS errors of the solved velocity and (mean-free)
-    pressure against the manufactured field.  Solved twice: interior
-    pressure rows from the scalar Laplacian, then from the staggered one
-    (Sec. 3.2; its stencil time is that of a first call)."""
+    pressure against the manufactured field.  full: solved three times --
+    interior pressure rows from the scalar Laplacian, then from the
+    staggered one (Sec. 3.2; its stencil time is that of a first call), then
+    the first system on its equilibrated rows (row_scaling); else only the
+    last of these."""
     import torch
 
     from paper_2104_14447_gb300 import gmls, inputs
@@ -937,11 +939,11 @@ def stokes_solve(ctx, n_axis=128):
                       neumann=True)
     b = ctx.stokes_rhs(sv, sp, 1.0, d["f"], d["w"], d["div_f"])
 
-    def solve(ss):
+    def solve(ss, row_scaling=False):
         rp, col, val = ctx.stokes_assemble(sv, sp, 1.0, ss)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=1e-10)
+        sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=1e-10, row_scaling=row_scaling)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         s = sol.cpu().numpy()
@@ -951,9 +953,17 @@ def stokes_solve(ctx, n_axis=128):
         return {"unknowns": int(rp.shape[0] - 1), "nnz": int(col.shape[0]), "iterations": its, "rel_residual": rel,
                 "seconds": el, "rms_error_velocity": eu, "rms_error_pressure": ep}
 
+    if not full:
+        out = {"grid": f"{n_axis}x{n_axis}", "solver": "GMRES(100), row equilibration + right Jacobi",
+               "interior_pressure_laplacian": "scalar GMLS, degree 4"}
+        out.update(solve(0, True))
+        for hd in (sp, sv, npr, nv, cid):
+            ctx.release(hd)
+        return out
     out = {"grid": f"{n_axis}x{n_axis}", "solver": "GMRES(100), right Jacobi",
            "interior_pressure_laplacian": "scalar GMLS, degree 4"}
     out.update(solve(0))
+    out["row_scaled"] = solve(0, True)
     # the paper's choice for points inside the domain: the staggered
     # Laplacian (Sec. 2.4) of degree 3, on the scalar neighbour lists
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -1206,6 +1216,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_stokes:
         out["stokes_system"] = stokes_system(ctx)
         out["stokes_system"]["solve"] = stokes_solve(ctx)
+        out["stokes_system"]["solve_256"] = stokes_solve(ctx, 256, full=False)
     if rank == 0 and world == 1 and not args.no_porous:
         out["porous_3d"], gs = porous_3d(ctx, n_axis=args.porous_n_axis)
         if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison

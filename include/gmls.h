@@ -315,9 +315,16 @@ gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr,
  * reduction has a fixed order: repeated solves give the same bits.
  */
 typedef struct {
-  int32_t restart;  /* Krylov basis size, 1..256 */
-  int32_t max_iter; /* iterations over all restarts, >= 0 */
-  double rtol;      /* relative residual target, > 0 */
+  int32_t restart;     /* Krylov basis size, 1..256 */
+  int32_t max_iter;    /* iterations over all restarts, >= 0 */
+  double rtol;         /* relative residual target, > 0 */
+  int32_t row_scaling; /* 0: as above.  1: GMRES on R A D y = R b, x = D y, with R the
+                          row equilibration (1 / largest |entry| of each row) and D the
+                          Jacobi scaling of R A; residuals (rtol, *rel_residual) are then
+                          |R (b - A x)| / |R b|.  Rows of very different magnitudes (the
+                          Stokes system's pressure rows against its Dirichlet rows) make
+                          the unscaled residual norm stall restarted GMRES. */
+  int32_t reserved;    /* must be 0 */
 } gmls_gmres_params;
 
 gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,

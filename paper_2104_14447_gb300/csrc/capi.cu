@@ -1468,8 +1468,9 @@ gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const i
                        const double* b, double* x, const gmls_gmres_params* p, int32_t* iters, double* rel_residual) {
   if (!ctx) return GMLS_EINVAL;
   if (!p || n < 1 || !row_ptr || !col || !val || !b || !x || p->restart < 1 || p->restart > 256 || p->max_iter < 0 ||
-      !(p->rtol > 0.0))
-    return fail(ctx, GMLS_EINVAL, "gmls_gmres: bad argument (restart 1..256, max_iter >= 0, rtol > 0)");
+      !(p->rtol > 0.0) || (p->row_scaling != 0 && p->row_scaling != 1) || p->reserved != 0)
+    return fail(ctx, GMLS_EINVAL,
+                "gmls_gmres: bad argument (restart 1..256, max_iter >= 0, rtol > 0, row_scaling 0 or 1, reserved 0)");
   if (is_host_ptr(row_ptr) || is_host_ptr(col) || is_host_ptr(val) || is_host_ptr(b) || is_host_ptr(x))
     return fail(ctx, GMLS_EINVAL, "gmls_gmres: arrays must be device buffers");
   if (capturing(ctx)) return fail(ctx, GMLS_EBUSY, "gmls_gmres reads the device every iteration: not during capture");
@@ -1483,12 +1484,15 @@ gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const i
   int32_t* long_rows = arena_alloc<int32_t>(ctx, n);
   int32_t* n_long = arena_alloc<int32_t>(ctx, 1);
   double* sp_part = arena_alloc<double>(ctx, csr_spmv_partial_elems());
-  void* all[] = {V, z, dinv, part, hdev, long_rows, n_long, sp_part};
+  const bool rs = p->row_scaling != 0;
+  double* rinv = rs ? arena_alloc<double>(ctx, n) : nullptr;
+  void* all[] = {V, z, dinv, part, hdev, long_rows, n_long, sp_part, rinv};
   auto release = [&]() {
     for (void* q : all) ctx->arena.release(q);
   };
-  for (void* q : all)
-    if (!q) {
+  const int n_need = rs ? 9 : 8;  // rinv (the last entry) only with row scaling
+  for (int i = 0; i < n_need; ++i)
+    if (!all[i]) {
       release();
       return fail(ctx, GMLS_ENOMEM, "gmls_gmres: arena exhausted (the basis needs (restart + 1) n doubles)");
     }
@@ -1502,9 +1506,17 @@ gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const i
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, hdev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   };
-  if (e == cudaSuccess) e = krylov_inverse_diagonal(L, n, row_ptr, col, val, dinv);
+  // with row scaling R (rinv): GMRES on R A D y = R b, x = D y, and the
+  // residual norms are those of R (b - A x)
   double bb = 0.0;
-  dot_host(b, b, &bb);
+  if (rs) {
+    if (e == cudaSuccess) e = krylov_row_equilibration(L, n, row_ptr, col, val, rinv, dinv);
+    if (e == cudaSuccess) e = krylov_scale(L, n, rinv, b, z);
+    dot_host(z, z, &bb);
+  } else {
+    if (e == cudaSuccess) e = krylov_inverse_diagonal(L, n, row_ptr, col, val, dinv);
+    dot_host(b, b, &bb);
+  }
   const double bnorm = std::sqrt(bb);
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), hc(2 * (m + 2), 0.0);
   int total = 0;
@@ -1513,6 +1525,7 @@ gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const i
     // r = b - A x into V_0
     spmv(x, V);
     if (e == cudaSuccess) e = krylov_residual(L, n, b, V);
+    if (rs && e == cudaSuccess) e = krylov_scale_in_place(L, n, rinv, V);
     double rr = 0.0;
     dot_host(V, V, &rr);
     const double beta = std::sqrt(rr);
@@ -1527,6 +1540,7 @@ gmls_status gmls_gmres(gmls_ctx* ctx, int64_t n, const int64_t* row_ptr, const i
       double* w = V + (size_t)(j + 1) * n;
       if (e == cudaSuccess) e = krylov_scale(L, n, dinv, vj, z);
       spmv(z, w);
+      if (rs && e == cudaSuccess) e = krylov_scale_in_place(L, n, rinv, w);
       // CGS2: h = V^T w, w -= V h, twice; then |w|
       if (e == cudaSuccess) e = krylov_dots(L, n, j + 1, V, w, part, hdev);
       if (e == cudaSuccess) e = krylov_axpy(L, n, j + 1, V, hdev, w);

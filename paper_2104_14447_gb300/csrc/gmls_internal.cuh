@@ -303,6 +303,11 @@ cudaError_t krylov_update(const Launch& L, int64_t n, int ncols, const double* V
 cudaError_t krylov_scale(const Launch& L, int64_t n, const double* dinv, const double* v, double* z);
 cudaError_t krylov_scaled_copy(const Launch& L, int64_t n, const double* src, double s, double* dst);
 cudaError_t krylov_residual(const Launch& L, int64_t n, const double* b, double* r);
+// rinv = 1 / (largest |entry| of each row), dinv = 1 / diagonal of the
+// row-scaled matrix (1 where either is absent or zero)
+cudaError_t krylov_row_equilibration(const Launch& L, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                     const double* val, double* rinv, double* dinv);
+cudaError_t krylov_scale_in_place(const Launch& L, int64_t n, const double* d, double* v);
 cudaError_t krylov_inverse_diagonal(const Launch& L, int64_t n, const int64_t* row_ptr, const int32_t* col,
                                     const double* val, double* dinv);
 

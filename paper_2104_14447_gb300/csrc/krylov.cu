@@ -1,7 +1,7 @@
 // krylov.cu -- restarted GMRES on the GPU for the collocation system of
 // Sec. 3.2 (the global solve of Sec. 3.3; the paper uses a block-
 // preconditioned Krylov method, this is a plain right-Jacobi-preconditioned
-// GMRES(m)).
+// GMRES(m), optionally on the row-equilibrated system R A D y = R b).
 //
 // Vectors are FP64 device arrays.  The Krylov basis V ([m + 1][n], basis
 // vector i contiguous) lives in the context arena.  Orthogonalisation is
@@ -130,6 +130,31 @@ __global__ void inverse_diagonal_kernel(int64_t n, const int64_t* __restrict__ r
   }
 }
 
+// row equilibration: rinv[r] = 1 / max_j |A[r][j]| (1 for an empty or zero
+// row), and dinv[r] = 1 / (rinv[r] A[r][r]), the Jacobi scaling of the
+// equilibrated matrix (1 where that diagonal entry is absent or zero)
+__global__ void row_equilibration_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
+                                         const int32_t* __restrict__ col, const double* __restrict__ val,
+                                         double* __restrict__ rinv, double* __restrict__ dinv) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double amax = 0.0, d = 0.0;
+    for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      amax = fmax(amax, fabs(val[p]));
+      if (col[p] == (int32_t)r) d = val[p];
+    }
+    const double ri = amax > 0.0 ? 1.0 / amax : 1.0;
+    const double ds = ri * d;
+    rinv[r] = ri;
+    dinv[r] = ds != 0.0 ? 1.0 / ds : 1.0;
+  }
+}
+
+// v = d .* v
+__global__ void scale_in_place_kernel(int64_t n, const double* __restrict__ d, double* v) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    v[p] = d[p] * v[p];
+}
+
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -183,6 +208,19 @@ cudaError_t krylov_residual(const Launch& L, int64_t n, const double* b, double*
 cudaError_t krylov_inverse_diagonal(const Launch& L, int64_t n, const int64_t* row_ptr, const int32_t* col,
                                     const double* val, double* dinv) {
   inverse_diagonal_kernel<<<grid_for(n), 256, 0, L.stream>>>(n, row_ptr, col, val, dinv);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t krylov_row_equilibration(const Launch& L, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                     const double* val, double* rinv, double* dinv) {
+  row_equilibration_kernel<<<grid_for(n), 256, 0, L.stream>>>(n, row_ptr, col, val, rinv, dinv);
+  *L.counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t krylov_scale_in_place(const Launch& L, int64_t n, const double* d, double* v) {
+  scale_in_place_kernel<<<grid_for(n), 256, 0, L.stream>>>(n, d, v);
   *L.counter += 1;
   return cudaGetLastError();
 }

@@ -80,7 +80,8 @@ class StokesParams(ctypes.Structure):
 
 
 class GmresParams(ctypes.Structure):
-    _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double)]
+    _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("row_scaling", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -323,13 +324,16 @@ class Context:
             a.record_stream(self.stream)
         return y
 
-    def gmres(self, row_ptr, col, val, b, x0=None, restart: int = 60, max_iter: int = 5000, rtol: float = 1e-10):
-        """Solve A x = b (gmls_gmres); returns (x, iterations, relative residual)."""
+    def gmres(self, row_ptr, col, val, b, x0=None, restart: int = 60, max_iter: int = 5000, rtol: float = 1e-10,
+              row_scaling: bool = False):
+        """Solve A x = b (gmls_gmres); returns (x, iterations, relative
+        residual).  row_scaling: GMRES on the row-equilibrated system (the
+        residual is then that of the scaled rows)."""
         b = _contig(b, torch.float64).to(self.device)
         n = row_ptr.shape[0] - 1
         x = (torch.zeros(n, dtype=torch.float64, device=self.device) if x0 is None
              else _contig(x0, torch.float64).to(self.device).clone())
-        p = GmresParams(restart, max_iter, rtol)
+        p = GmresParams(restart, max_iter, rtol, int(row_scaling))
         it, rel = ctypes.c_int32(), ctypes.c_double()
         self._check(self.lib.gmls_gmres(self.h, n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
                                         ctypes.byref(p), ctypes.byref(it), ctypes.byref(rel)))
