@@ -303,11 +303,13 @@ gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr,
 
 /*
  * Solve A x = b (square CSR, n rows; FP64) by restarted GMRES(restart) with
- * right Jacobi preconditioning (diag A; 1 where it is zero or absent) -- the
- * global solve of the collocation system of Sec. 3.2 (the paper uses a
+ * right Jacobi preconditioning (diag A; 1 where it is zero or absent), on
+ * the row-equilibrated system when params->row_scaling = 1 -- the global
+ * solve of the collocation system of Sec. 3.2 (the paper uses a
  * block-preconditioned Krylov method).  x: device buffer holding the initial
  * guess on entry and the solution on return.  Synchronous: returns after
- * ||b - A x|| <= rtol ||b|| (true residual, recomputed at every restart) or
+ * ||b - A x|| <= rtol ||b|| (with row scaling ||R (b - A x)|| <= rtol ||R b||;
+ * the true residual, recomputed at every restart) or
  * max_iter iterations; *iters and *rel_residual report them (a solve that
  * stops at max_iter still returns GMLS_OK: check *rel_residual).  Scratch
  * ((restart + 1) n doubles and a few vectors) comes from the arena
