@@ -395,7 +395,9 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);
  * Same results as gmls_cloud + gmls_neighbors(GMLS_NBR_KNN, k, eps_factor)
  * with every particle a target: out_idx [n][k] sorted by (d^2, id), out_eps
  * [n], out_status [n] (GMLS_T_* bits).  xyz (FP64 SoA [dim][n]) and the
- * outputs are caller-owned DEVICE buffers; work is queued on cuda_stream.
+ * outputs are caller-owned buffers in the memory of the CURRENT device
+ * (GMLS_EINVAL for host memory or another device's); work is queued on
+ * cuda_stream.
  * No context is needed and nothing is allocated or freed: the cell-list
  * scratch is one static device array of about 14 MB that every GPU loading
  * the library holds until exit, sized for at most GMLS_NOALLOC_MAX_POINTS

@@ -89,8 +89,6 @@ struct CloudObj {
   int dim = 0;
   int64_t n = 0;
   double* x = nullptr;
-  float* xh = nullptr;  // float-float split of x
-  float* xl = nullptr;
   double* normals = nullptr;
   uint8_t* bflag = nullptr;
   double* xs = nullptr;
@@ -759,8 +757,6 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   const int n_part = (int)std::min<int64_t>(256, (n + 255) / 256);
   const int64_t scan_elems = scan_scratch_elems(ncell);
   c.x = arena_alloc<double>(ctx, (size_t)dim * n);
-  c.xh = arena_alloc<float>(ctx, (size_t)dim * n);
-  c.xl = arena_alloc<float>(ctx, (size_t)dim * n);
   c.xs = arena_alloc<double>(ctx, (size_t)dim * n);
   c.xsf = arena_alloc<float>(ctx, (size_t)dim * n);
   c.sorted = arena_alloc<int32_t>(ctx, n);
@@ -773,7 +769,7 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   int32_t* counts = arena_alloc<int32_t>(ctx, ncell);
   int32_t* fill = arena_alloc<int32_t>(ctx, ncell);
   int32_t* scan_tmp = arena_alloc<int32_t>(ctx, scan_elems);
-  void* all[] = {c.x, c.xh, c.xl, c.xs, c.xsf, c.sorted, c.cell_start, c.grid, part, cell_of, counts, fill, scan_tmp};
+  void* all[] = {c.x, c.xs, c.xsf, c.sorted, c.cell_start, c.grid, part, cell_of, counts, fill, scan_tmp};
   bool oom = false;
   for (void* p : all) oom |= (p == nullptr);
   oom |= (normals && !c.normals) || (bflags && !c.bflag);
@@ -789,11 +785,10 @@ gmls_status gmls_cloud(gmls_ctx* ctx, int dim, int64_t n, const double* xyz, con
   if (bflags) CK(copy_in(ctx, c.bflag, bflags, n), "gmls_cloud copy flags");
   CK(cudaMemsetAsync(counts, 0, sizeof(int32_t) * ncell, ctx->stream), "gmls_cloud memset");
   CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * ncell, ctx->stream), "gmls_cloud memset");
-  CK(launch_split_ff(L, c.x, c.xh, c.xl, (int64_t)dim * n), "gmls_cloud split");
   CK(launch_bbox_and_grid(L, dim, n, c.x, nc_axis, c.grid, part, n_part), "gmls_cloud bbox");
   CK(launch_cell_count(L, dim, n, c.x, c.grid, cell_of, counts), "gmls_cloud count");
   CK(launch_scan_i32(L, counts, c.cell_start, ncell, scan_tmp, scan_elems), "gmls_cloud scan");
-  CK(launch_cell_scatter(L, dim, n, c.x, cell_of, c.cell_start, fill, c.sorted, c.xs, c.xsf), "gmls_cloud scatter");
+  CK(launch_cell_scatter(L, dim, n, c.x, c.grid, cell_of, c.cell_start, fill, c.sorted, c.xs, c.xsf), "gmls_cloud scatter");
   ctx->arena.release(part);
   ctx->arena.release(cell_of);
   ctx->arena.release(counts);
@@ -867,7 +862,7 @@ gmls_status gmls_neighbors(gmls_ctx* ctx, int64_t cloud_id, const gmls_nbr_param
   if (hs) CK(copy_in(ctx, hs, p->halfspace, sizeof(double) * nt * c.dim), "gmls_neighbors copy halfspace");
   if (kpt) CK(copy_in(ctx, kpt, p->k_per_target, sizeof(int32_t) * nt), "gmls_neighbors copy k");
   NbrQuery q;
-  q.cloud = CloudDev{c.dim, c.n, c.x, c.xs, c.sorted, c.cell_start, c.grid, c.ncell, c.xsf, c.xh};
+  q.cloud = CloudDev{c.dim, c.n, c.x, c.xs, c.sorted, c.cell_start, c.grid, c.ncell, c.xsf};
   q.n_tgt = nt;
   q.tgt = nb.tgt;
   q.halfspace = hs;
@@ -1086,8 +1081,6 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.dim = dim;
   j.n = c.n;
   j.x = c.x;
-  j.xh = c.xh;
-  j.xl = c.xl;
   j.normals = c.normals;
   j.bflag = c.bflag;
   j.n_tgt = nt;
@@ -1135,8 +1128,7 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.ld = ld;
   j.nmax = nmax;
 
-  int dev_sms = 152;
-  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int dev_sms = device_sm_count();
   gmls_status rc = GMLS_OK;
   if (nt > 0) {
     rc = plan_and_launch(ctx, j, p, nb, s, refine, ld, nmax, dev_sms);
@@ -1666,7 +1658,7 @@ gmls_status gmls_release(gmls_ctx* ctx, int64_t id) {
     cudaGraphExecDestroy(o.exec);
   } else if (o.kind == K_CLOUD) {
     if (o.c.refs) return fail(ctx, GMLS_EBUSY, "gmls_release: cloud has live neighbour handles");
-    for (void* p : {(void*)o.c.x, (void*)o.c.xh, (void*)o.c.xl, (void*)o.c.normals, (void*)o.c.bflag,
+    for (void* p : {(void*)o.c.x, (void*)o.c.normals, (void*)o.c.bflag,
                     (void*)o.c.xs, (void*)o.c.xsf, (void*)o.c.sorted, (void*)o.c.cell_start, (void*)o.c.grid})
       a.release(p);
   } else if (o.kind == K_NBRS) {

@@ -116,12 +116,29 @@ __device__ __forceinline__ double to_double(ff a) { return f2d_exact(a.h) + f2d_
 __device__ __forceinline__ ff gmls_cst(ff, double, float h, float l) { return ff(h, l); }
 __device__ __forceinline__ ff gmls_scale2(ff x, float p) { return ff(x.h * p, x.l * p); }
 
-// (a_h + a_l) - (b_h + b_l) for coordinates stored as float pairs
-__device__ __forceinline__ ff sub_pair(float ah, float al, float bh, float bl) {
-  ff s = two_sum(ah, -bh);
-  float e = __fadd_rn(s.l, __fsub_rn(al, bl));
-  return quick_two_sum(s.h, e);
+// Float-float split of a double without FP64 conversions: h is d cut to 24
+// significant bits (exact in a float), l the remaining 29 bits rounded to a
+// float by an integer -> float conversion, so |d - (h + l)| <= 2^-48 |d| and
+// |l| < ulp(h).  The integer path covers 2^-74 <= |d| < 2^127 (h and the scale
+// 2^(e - 1075) are then normal floats); other values take the conversions.
+__device__ __forceinline__ ff split_d(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if (e < 949u || e > 1150u) {
+    const float h = __double2float_rn(d);
+    return ff(h, __double2float_rn(d - (double)h));
+  }
+  const unsigned s = (unsigned)(b >> 63) << 31;
+  const float h = __uint_as_float(s | ((e - 896u) << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  const float lo = __uint2float_rn((unsigned)(b & 0x1fffffffu));
+  const float sc = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075)
+  return ff(h, __uint_as_float(__float_as_uint(__fmul_rn(lo, sc)) | s));
 }
+
+// x_j - x_T as float-float: the FP64 difference (the same rounded value the
+// exact neighbour distances use) split by split_d.  Independent of where the
+// cloud sits: no float copy of the absolute coordinates is involved.
+__device__ __forceinline__ ff diff_ff(double xj, double xt) { return split_d(__dsub_rn(xj, xt)); }
 
 // Compensated accumulation of products (Ogita-Rump-Oishi Dot2 with
 // float-float factors): acc_h + acc_l tracks sum(a_i * b_i) to about 2^-48.

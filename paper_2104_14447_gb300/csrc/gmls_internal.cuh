@@ -54,6 +54,7 @@ __device__ __forceinline__ bool nonpositive(double s) { return __double_as_longl
 // ----------------------------------------------------------------- grid state
 struct GridParams {
   double lo[kMaxDim];
+  double org[kMaxDim];  // bounding-box centre: origin of the FP32 coordinate copies
   double inv_h[kMaxDim];
   double h[kMaxDim];
   int32_t nc[kMaxDim];
@@ -69,11 +70,14 @@ struct CloudDev {
   const int32_t* cell_start;  // [ncell + 1]
   const GridParams* grid;
   int64_t ncell;
-  const float* xsf;        // SoA [dim][n], fl32 of xs (the query's FP32 pre-filter)
-  const float* xh;         // SoA [dim][n], fl32 of x, or NULL
+  const float* xsf;        // SoA [dim][n], fl32(xs - org) (the query's FP32 pre-filter)
 };
 
 // ------------------------------------------------------------ launch helpers
+// streaming multiprocessors of the current device (queried once per device);
+// grid sizes are multiples of it
+int device_sm_count();
+
 struct Launch {
   cudaStream_t stream;
   int64_t* counter;  // kernels launched
@@ -88,8 +92,9 @@ cudaError_t launch_scan_i32(const Launch& L, const int32_t* in, int32_t* out_exc
 cudaError_t launch_scan_i64_from_i32(const Launch& L, const int32_t* in, int64_t* out_excl, int64_t n,
                                      int64_t* scratch, int64_t scratch_elems);
 int64_t scan_scratch_elems(int64_t n);
-cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const int32_t* cell_of,
-                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs, float* xsf);
+cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const GridParams* grid,
+                                const int32_t* cell_of, const int32_t* cell_start, int32_t* fill, int32_t* sorted,
+                                double* xs, float* xsf);
 
 struct NbrQuery {
   CloudDev cloud;
@@ -122,8 +127,6 @@ struct StencilJob {
   int dim;
   int64_t n;
   const double* x;
-  const float* xh;         // float-float split of x (x = xh + xl), SoA
-  const float* xl;
   const double* normals;   // SoA [dim][n] or NULL
   const uint8_t* bflag;    // [n] or NULL
   // neighbours
@@ -224,7 +227,6 @@ bool fast_path_available(int kind, int dim, int deg, int rows, int L, int hw, in
 // the preferred group width for a shape: fewest padded row slots, then 32
 int fast_path_preferred(int kind, int dim, int deg, int rows, int L, int* mr_out);
 cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms);
-cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count);
 
 // -------------------------------------------------------------------- CSR
 // id order of neighbour lists (see nbr_order_kernel): order[off[t] + r] =

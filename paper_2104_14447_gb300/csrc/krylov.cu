@@ -22,7 +22,10 @@ namespace gmls {
 
 namespace {
 
-constexpr int kDotBlocks = 2 * 152;
+// Fixed partition of the batched dot products (304 block partials, two per SM
+// of a GB300): the summation order, and so the result, does not depend on
+// the device
+constexpr int kDotBlocks = 304;
 constexpr int kDotThreads = 256;
 constexpr int kDotChunk = 8;  // basis vectors per pass of a thread
 
@@ -158,7 +161,7 @@ __global__ void scale_in_place_kernel(int64_t n, const double* __restrict__ d, d
 unsigned grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b < 1) b = 1;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > (int64_t)device_sm_count() * 16) b = (int64_t)device_sm_count() * 16;
   return (unsigned)b;
 }
 

@@ -8,14 +8,41 @@
 // identical on every run and machine.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "gmls_internal.cuh"
 
 namespace gmls {
 
-static inline unsigned blocks_for(int64_t n, int per_block, unsigned cap = 152u * 32u) {
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev < 0 || dev >= 64) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+// grid-stride launches: at most 32 blocks per SM
+static inline unsigned blocks_for(int64_t n, int per_block, int per_sm = 32) {
   int64_t b = (n + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)device_sm_count() * per_sm;
   if (b < 1) b = 1;
-  if (b > (int64_t)cap) b = cap;
+  if (b > cap) b = cap;
   return (unsigned)b;
 }
 
@@ -78,12 +105,14 @@ __global__ void grid_finalize_kernel(int dim, int nparts, const double* __restri
   for (int c = 0; c < kMaxDim; ++c) {
     if (c >= dim) {
       g->lo[c] = 0.0;
+      g->org[c] = 0.0;
       g->h[c] = 1.0;
       g->inv_h[c] = 0.0;
       g->nc[c] = 1;
       continue;
     }
     const double lo = lo3[c], hi = hi3[c];
+    g->org[c] = 0.5 * lo + 0.5 * hi;
     double ext = hi - lo;
     int nc = ncs[c];
     if (!(ext > 0.0)) {  // flat axis: one cell, every point maps to it
@@ -135,10 +164,15 @@ cudaError_t launch_cell_count(const Launch& L, int dim, int64_t n, const double*
   return cudaGetLastError();
 }
 
-__global__ void cell_scatter_kernel(int dim, int64_t n, const double* __restrict__ x, const int32_t* __restrict__ cell_of,
-                                    const int32_t* __restrict__ cell_start, int32_t* __restrict__ fill,
-                                    int32_t* __restrict__ sorted, double* __restrict__ xs,
+// xsf holds the FP32 rounding of the coordinates relative to the bounding-box
+// centre, so that the pre-filter's rounding bound scales with the cloud's
+// extent, not with its distance from the coordinate origin
+__global__ void cell_scatter_kernel(int dim, int64_t n, const double* __restrict__ x, const GridParams* __restrict__ gp,
+                                    const int32_t* __restrict__ cell_of, const int32_t* __restrict__ cell_start,
+                                    int32_t* __restrict__ fill, int32_t* __restrict__ sorted, double* __restrict__ xs,
                                     float* __restrict__ xsf) {
+  double org[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < dim; ++c) org[c] = gp->org[c];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t cell = cell_of[i];
     int32_t pos = cell_start[cell] + atomicAdd(&fill[cell], 1);
@@ -146,35 +180,20 @@ __global__ void cell_scatter_kernel(int dim, int64_t n, const double* __restrict
     for (int c = 0; c < dim; ++c) {
       const double v = x[c * n + i];
       xs[c * n + pos] = v;
-      xsf[c * n + pos] = __double2float_rn(v);
+      xsf[c * n + pos] = __double2float_rn(__dsub_rn(v, org[c]));
     }
   }
 }
 
-cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const int32_t* cell_of,
-                                const int32_t* cell_start, int32_t* fill, int32_t* sorted, double* xs, float* xsf) {
-  cell_scatter_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(dim, n, x, cell_of, cell_start, fill, sorted, xs,
-                                                                xsf);
+cudaError_t launch_cell_scatter(const Launch& L, int dim, int64_t n, const double* x, const GridParams* grid,
+                                const int32_t* cell_of, const int32_t* cell_start, int32_t* fill, int32_t* sorted,
+                                double* xs, float* xsf) {
+  cell_scatter_kernel<<<blocks_for(n, 256), 256, 0, L.stream>>>(dim, n, x, grid, cell_of, cell_start, fill, sorted,
+                                                                xs, xsf);
   *L.counter += 1;
   return cudaGetLastError();
 }
 
-// x = xh + xl with xh = fl32(x): the float-float coordinates of the FP32 path
-__global__ void split_ff_kernel(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
-                                int64_t count) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float h = __double2float_rn(v);
-    xh[i] = h;
-    xl[i] = __double2float_rn(v - (double)h);
-  }
-}
-
-cudaError_t launch_split_ff(const Launch& L, const double* x, float* xh, float* xl, int64_t count) {
-  split_ff_kernel<<<blocks_for(count, 256), 256, 0, L.stream>>>(x, xh, xl, count);
-  *L.counter += 1;
-  return cudaGetLastError();
-}
 
 // ----------------------------------------------------------------------- scan
 // Exclusive scan in three passes: tile sums, a one-block scan of the tile
@@ -315,10 +334,12 @@ __device__ inline WarpBuf warpbuf_at(unsigned char* base, int cap) {
 }
 
 // Query-side grid constants in FP32, derived once per warp from the FP64 grid.
+// FP32 view of the grid in coordinates relative to the bounding-box centre
+// (the frame of the pre-filter copies xsf)
 struct QueryGeo {
   float lo[3], inv_h[3];
   int32_t nc[3];
-  float A;   // >= max |coordinate| of the cloud
+  float A;   // >= max |coordinate - centre| over the grid box
   float e2;  // 2 * 2^-23 * A: twice the bound on |fl32(x_j) - fl32(x_T) - (x_j - x_T)|
 };
 
@@ -331,10 +352,10 @@ __device__ inline QueryGeo make_query_geo(const GridParams& g, int dim) {
     q.nc[c] = 1;
   }
   for (int c = 0; c < dim; ++c) {
-    q.lo[c] = __double2float_rn(g.lo[c]);
+    q.lo[c] = __double2float_rn(g.lo[c] - g.org[c]);
     q.inv_h[c] = __double2float_rn(g.inv_h[c]);
     q.nc[c] = g.nc[c];
-    a = fmax(a, fmax(fabs(g.lo[c]), fabs(g.lo[c] + g.h[c] * g.nc[c])));
+    a = fmax(a, fmax(fabs(g.lo[c] - g.org[c]), fabs(g.lo[c] + g.h[c] * g.nc[c] - g.org[c])));
   }
   q.A = __double2float_ru(a) * (1.0f + 0x1p-20f);
   q.e2 = q.A * 0x1p-22f;
@@ -641,7 +662,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     float xTf[3] = {0.0f, 0.0f, 0.0f};
     for (int c = 0; c < dim; ++c) {
       xT[c] = cl.x[c * cl.n + t];
-      xTf[c] = cl.xh ? cl.xh[c * cl.n + t] : __double2float_rn(xT[c]);
+      xTf[c] = __double2float_rn(__dsub_rn(xT[c], g.org[c]));
     }
     bool use_hs = false;
     float nrmf[3] = {0.0f, 0.0f, 0.0f}, hs_scale = 0.0f;
@@ -741,7 +762,7 @@ cudaError_t launch_nbr_query(const Launch& L, const NbrQuery& q) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t blocks = (q.n_tgt + kQueryWarps - 1) / kQueryWarps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   if (q.cloud.dim == 2)
     nbr_query_kernel<2><<<(unsigned)blocks, kQueryWarps * 32, smem, L.stream>>>(q, cap);
   else

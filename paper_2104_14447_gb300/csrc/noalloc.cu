@@ -69,13 +69,15 @@ gmls_status err(gmls_status code, const std::string& msg) {
   return code;
 }
 
-bool on_device(const void* p) {
+// device (or managed) memory of device dev: the kernels run on the current
+// device and must not reach into a peer's memory
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -89,8 +91,14 @@ extern "C" gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, i
                                 " particles (the static scratch array is sized for that); got " + std::to_string(n));
   if (!xyz || !out_idx || !out_eps || !out_status)
     return err(GMLS_EINVAL, "gmls_knn_noalloc: NULL pointer");
-  if (!on_device(xyz) || !on_device(out_idx) || !on_device(out_eps) || !on_device(out_status))
-    return err(GMLS_EINVAL, "gmls_knn_noalloc: coordinates and outputs must be device memory");
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return err(GMLS_ECUDA, "gmls_knn_noalloc: no current CUDA device");
+  }
+  if (!on_device(xyz, cur) || !on_device(out_idx, cur) || !on_device(out_eps, cur) || !on_device(out_status, cur))
+    return err(GMLS_EINVAL, "gmls_knn_noalloc: coordinates and outputs must be device memory of the current device (" +
+                                std::to_string(cur) + ")");
   int32_t nc_axis[3] = {1, 1, 1};
   const double per_axis = std::pow(std::max(1.0, n / 2.0), 1.0 / dim);
   int64_t ncell = 1;
@@ -138,11 +146,11 @@ extern "C" gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, i
       (e = launch_bbox_and_grid(L, dim, n, xyz, nc_axis, grid, part, n_part)) != cudaSuccess ||
       (e = launch_cell_count(L, dim, n, xyz, grid, cell_of, counts)) != cudaSuccess ||
       (e = launch_scan_i32(L, counts, cell_start, ncell, scan_tmp, scan_elems)) != cudaSuccess ||
-      (e = launch_cell_scatter(L, dim, n, xyz, cell_of, cell_start, fill, sorted, xs, xsf)) != cudaSuccess)
+      (e = launch_cell_scatter(L, dim, n, xyz, grid, cell_of, cell_start, fill, sorted, xs, xsf)) != cudaSuccess)
     return err(GMLS_ECUDA, std::string("gmls_knn_noalloc: cell list: ") + cudaGetErrorString(e));
   NbrQuery q;
   std::memset(&q, 0, sizeof(q));
-  q.cloud = CloudDev{dim, n, xyz, xs, sorted, cell_start, grid, ncell, xsf, nullptr};
+  q.cloud = CloudDev{dim, n, xyz, xs, sorted, cell_start, grid, ncell, xsf};
   q.n_tgt = n;
   q.tgt = nullptr;
   q.halfspace = nullptr;

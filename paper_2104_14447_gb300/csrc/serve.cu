@@ -33,6 +33,7 @@
 
 namespace gmls {
 void set_global_error(const std::string& msg);
+int device_sm_count();
 }
 
 namespace {
@@ -107,7 +108,7 @@ struct Request {
 size_t estimate_bytes(const gmls_request& r) {
   const int64_t n = r.n, k = r.k, d = r.dim;
   const int nc = r.basis == GMLS_BASIS_SCALAR ? 1 : (int)d;
-  size_t cloud = (size_t)n * (d * (8 + 4 + 4 + 8 + 4) + 4 + 4 + 2 * 4 * 3) + 64 * 1024;
+  size_t cloud = (size_t)n * (d * (8 + 8 + 4) + 4 + 4 + 2 * 4 * 3) + 64 * 1024;
   size_t nbrs = (size_t)n * (k * 4 * 2 + 8 + 8 + 4 + 1 + 16) + 64 * 1024;
   size_t weights = 0;
   for (int f = 0; f < r.n_functionals; ++f) {
@@ -117,11 +118,11 @@ size_t estimate_bytes(const gmls_request& r) {
     weights += (size_t)n * k * rows * comp * 8;
   }
   size_t stencils = weights + (size_t)n * (4 * 8 + 2 + 4 + 16);
-  // global tiles of shapes too big for shared memory: at most 152 SMs x 4 groups
+  // global tiles of shapes too big for shared memory: at most (SMs x 4) groups
   const int nb = gmls_gen::basis_size(r.basis, (int)d, r.degree);
   const size_t rows = (size_t)k * nc;
   size_t tiles = 0;
-  if ((size_t)nb * rows * 12 > 100 * 1024) tiles = (size_t)152 * 4 * ((size_t)nb * rows * 12 + 4096);
+  if ((size_t)nb * rows * 12 > 100 * 1024) tiles = (size_t)gmls::device_sm_count() * 4 * ((size_t)nb * rows * 12 + 4096);
   const size_t total = cloud + nbrs + stencils + tiles;
   return total + total / 8 + (16u << 20);
 }

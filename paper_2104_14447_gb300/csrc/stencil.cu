@@ -692,7 +692,7 @@ __device__ __forceinline__ void offsets(const StencilJob& j, int64_t t, int32_t 
 }
 __device__ __forceinline__ void offsets(const StencilJob& j, int64_t t, int32_t jj, ff* dx) {
   for (int c = 0; c < j.dim; ++c)
-    dx[c] = sub_pair(j.xh[c * j.n + jj], j.xl[c * j.n + jj], j.xh[c * j.n + t], j.xl[c * j.n + t]);
+    dx[c] = diff_ff(j.x[c * j.n + jj], j.x[c * j.n + t]);
 }
 
 // sqrt(W) = u^(p/2), u = 1 - r/eps > 0
@@ -1271,7 +1271,7 @@ __global__ void bucket_scatter_kernel(BucketJob b) {
 }
 
 cudaError_t launch_bucketing(const Launch& L, const BucketJob& b) {
-  const unsigned blocks = (unsigned)std::min<int64_t>(152 * 8, (b.n_tgt + 255) / 256 + 1);
+  const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)device_sm_count() * 8, (b.n_tgt + 255) / 256 + 1);
   cudaError_t e = cudaMemsetAsync(b.counts, 0, sizeof(int32_t) * b.nb, L.stream);
   if (e != cudaSuccess) return e;
   bucket_count_kernel<<<blocks, 256, 0, L.stream>>>(b);
@@ -1407,7 +1407,7 @@ cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off,
   cudaError_t e = cudaFuncSetAttribute(nbr_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t blocks = (n_tgt + kOrderWarps - 1) / kOrderWarps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   nbr_order_kernel<<<(unsigned)blocks, kOrderWarps * 32, smem, L.stream>>>(n_tgt, off, idx, kcap, order);
   *L.counter += 1;
   return cudaGetLastError();
@@ -1439,7 +1439,7 @@ cudaError_t launch_nbr_order_prefix(const Launch& L, int64_t n_tgt, const int16_
   if (n_tgt == 0) return cudaSuccess;
   if (k < 1 || k > kp) return cudaErrorInvalidValue;
   int64_t blocks = (n_tgt * 32 + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   nbr_order_prefix_kernel<<<(unsigned)blocks, 256, 0, L.stream>>>(n_tgt, parent_order, kp, k, order);
   *L.counter += 1;
   return cudaGetLastError();
@@ -1488,7 +1488,7 @@ cudaError_t launch_csr(const Launch& L, const CsrJob& j) {
     return cudaGetLastError();
   }
   int64_t blocks = (j.n_tgt + kCsrWarps - 1) / kCsrWarps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   if (j.nc == 1)
     csr_kernel<1><<<(unsigned)blocks, kCsrWarps * 32, 0, L.stream>>>(j);
   else if (j.nc == 2)

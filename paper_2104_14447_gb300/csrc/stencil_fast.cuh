@@ -14,8 +14,10 @@
 //    neutral for Householder reflections.  Half-warp groups suit systems of
 //    a few dozen rows (36 rows: 48 slots on 16 lanes instead of 64 on 32),
 //    and every cross-lane reduction then serves two targets at once;
-//  * the tile B is built directly in float-float (hi + lo, ~48 bits) from
-//    float-float coordinates, so no FP64 instruction runs in the hot loop;
+//  * the tile B is built directly in float-float (hi + lo, ~48 bits) from the
+//    FP64 offsets x_j - x_T (one FP64 subtraction per coordinate, split into
+//    float-float with integer operations), so the result does not depend on
+//    where the cloud sits and no other FP64 instruction runs in the hot loop;
 //  * refinement of the augmented system [[I, B], [B^T, 0]] [s; -y] =
 //    [0; lambda^T] (Bjorck) computes its residuals f = B y - s and
 //    g = lambda - B^T s with compensated float-float dot products and its
@@ -362,12 +364,9 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
     // ---- 1. float-float tile B = sqrt(W) P, rows (neighbour, component)
     const ff eps(j.eps[to]);
     const ff inv_eps = recip(eps);
-    float xth[3] = {0.f, 0.f, 0.f}, xtl[3] = {0.f, 0.f, 0.f};
+    double xt[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      xth[c] = j.xh[c * n + t];
-      xtl[c] = j.xl[c * n + t];
-    }
+    for (int c = 0; c < D; ++c) xt[c] = j.x[c * n + t];
     const int half_p = j.wpow_half;
     for (int q = lane; q < ROWS / NC; q += HW) {
       if (q < k) {
@@ -376,7 +375,7 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
         ff r2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          dx[c] = sub_pair(j.xh[c * n + jj], j.xl[c * n + jj], xth[c], xtl[c]);
+          dx[c] = diff_ff(j.x[c * n + jj], xt[c]);
           xi[c] = dx[c] * inv_eps;
           r2 = r2 + dx[c] * dx[c];
         }

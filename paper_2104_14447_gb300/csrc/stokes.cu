@@ -34,7 +34,7 @@ constexpr int kStokesWarps = 8;
 inline unsigned grid_for(int64_t n, int per_block) {
   int64_t b = (n + per_block - 1) / per_block;
   if (b < 1) b = 1;
-  if (b > 152 * 32) b = 152 * 32;
+  if (b > (int64_t)device_sm_count() * 32) b = (int64_t)device_sm_count() * 32;
   return (unsigned)b;
 }
 
@@ -286,7 +286,7 @@ cudaError_t launch_stokes_rowlen(const Launch& L, const StokesJob& j) {
 
 cudaError_t launch_stokes_fill(const Launch& L, const StokesJob& j) {
   int64_t blocks = (j.n + kStokesWarps - 1) / kStokesWarps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
   if (j.dim == 2)
     stokes_fill_kernel<2><<<(unsigned)blocks, kStokesWarps * 32, 0, L.stream>>>(j);
   else
@@ -313,7 +313,7 @@ cudaError_t launch_csr_spmv(const Launch& L, int64_t n_rows, const int64_t* row_
   if (e != cudaSuccess) return e;
   csr_spmv_kernel<<<grid_for(n_rows * kRowLanes, 256), 256, 0, L.stream>>>(n_rows, row_ptr, col, val, x, y,
                                                                               long_rows, n_long);
-  csr_spmv_long_kernel<<<4 * 152, kSpmvBlock, 0, L.stream>>>(row_ptr, col, val, x, y, long_rows, n_long, partial);
+  csr_spmv_long_kernel<<<4 * device_sm_count(), kSpmvBlock, 0, L.stream>>>(row_ptr, col, val, x, y, long_rows, n_long, partial);
   csr_spmv_long_finish_kernel<<<1, 512, 0, L.stream>>>(y, long_rows, n_long, partial);
   *L.counter += 3;
   return cudaGetLastError();

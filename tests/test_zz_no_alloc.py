@@ -72,3 +72,20 @@ def test_noalloc_rejects_clouds_beyond_its_scratch():
                               ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(st.data_ptr()), None)
     assert rc == gmls.EINVAL
     assert b"at most 262144" in lib.gmls_last_error(None)
+
+
+def test_noalloc_rejects_host_memory():
+    """Coordinates or outputs that are not memory of the current device are
+    an argument error, not a kernel fault."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    lib = gmls.load()
+    x_host = torch.from_numpy(inputs.jittered_grid(2, 8, seed=1))
+    n, k = x_host.shape[1], 4
+    idx = torch.zeros(n * k, dtype=torch.int32, device="cuda")
+    eps = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    rc = lib.gmls_knn_noalloc(2, n, ctypes.c_void_p(x_host.data_ptr()), k, 1.5, ctypes.c_void_p(idx.data_ptr()),
+                              ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(st.data_ptr()), None)
+    assert rc == gmls.EINVAL
+    assert b"current device" in lib.gmls_last_error(None)
