@@ -380,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
         key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m={r['degree']} rows<={r['rows']}"
         v = r["variant"]
         place = {0: "", 1: ", split tiles", 2: ", global tiles"}[v >> 3] if v > 0 else ""
-        name = {-1: "register", -2: "register 16 lanes"}.get(v, f"{v & 7} warp(s)/target{place}")
+        name = {-1: "register", -2: "register 16 lanes", -3: "factored div-free"}.get(v, f"{v & 7} warp(s)/target{place}")
         tune.setdefault(key, {})[name] = round(r["ms"], 3)
 
     value = shard.job_throughput(n, args.steps, world, total_ms)
@@ -734,7 +734,7 @@ def porous_3d(ctx, n_axis=128, steps=3, n_sample=48, stokes=True):
         if r["dim"] == 3 and r["degree"] == 3 and not r["bucketed"]:
             v = r["variant"]
             place = {0: "", 1: ", split tiles", 2: ", global tiles"}[v >> 3] if v > 0 else ""
-            name = {-1: "register", -2: "register 16 lanes"}.get(v, f"{v & 7} warp(s)/target{place}")
+            name = {-1: "register", -2: "register 16 lanes", -3: "factored div-free"}.get(v, f"{v & 7} warp(s)/target{place}")
             key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m=3 rows<={r['rows']}"
             tune.setdefault(key, {})[name] = round(r["ms"], 3)
     qr_flops = 2 * 240 * 50 ** 2 - 2 * 50 ** 3 / 3  # Householder QR of one 240 x 50 system

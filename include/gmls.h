@@ -361,14 +361,17 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
                                     warp-per-target register kernel (testing and tuning)    */
 #define GMLS_OPT_AUTOTUNE 1      /* 1 (default): the first gmls_stencils call for a shape times
                                     the kernel variants (register kernel with a warp or a half
-                                    warp per target; 1, 2 or 4 warps per target, and for tiles
+                                    warp per target; for the divergence-free basis the
+                                    factored kernel; 1, 2 or 4 warps per target, and for tiles
                                     that leave one block per SM the split and global tile
                                     placements) on up to 8192 targets and caches the fastest;
                                     this call waits for the stream.  0: heuristic choice      */
 #define GMLS_OPT_CLEAR_TUNING 2  /* any value: forget the cached choices and timings         */
 #define GMLS_OPT_FORCE_VARIANT 3 /* testing: the kernel variant for shapes with uniform
                                     neighbour counts and degree: -1 / -2 register kernel
-                                    with 32 / 16 lanes per target; G + 8 * P for the
+                                    with 32 / 16 lanes per target; -3 the factored
+                                    divergence-free kernel (div-free basis, FP32 path);
+                                    G + 8 * P for the
                                     shared-memory kernel with G = 1, 2 or 4 warps per target
                                     and tile placement P (0: both tiles in shared memory;
                                     1, FP32 path only: the FP32 tile in shared memory, its
@@ -416,7 +419,8 @@ gmls_status gmls_knn_noalloc(int dim, int64_t n, const double* xyz, int32_t k, d
  * Autotuner record `index` (0-based, in the order taken): fields[9] =
  * {basis, dim, degree, precision, tile rows, solve rows, neumann, bucketed,
  * variant (-1 register kernel with 32 lanes per target, -2 with 16 lanes per
- * target, else G + 8 * P for the shared-memory kernel as in
+ * target, -3 factored divergence-free kernel, else G + 8 * P for the
+ * shared-memory kernel as in
  * GMLS_OPT_FORCE_VARIANT)}, *ms its time.
  * GMLS_ENOTFOUND past the last record.
  */

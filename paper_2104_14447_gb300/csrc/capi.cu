@@ -369,16 +369,24 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
   const bool ok32 = fast_allowed && fast_path_available(p->basis, dim, p->degree, ld, j.L, 32, &mr32);
   const bool ok16 = fast_allowed && fast_path_available(p->basis, dim, p->degree, ld, j.L, 16, &mr16);
   const int hw_pref = fast_allowed ? fast_path_preferred(p->basis, dim, p->degree, ld, j.L, &mr_pref) : 0;
+  // factored divergence-free kernel (variant -3): lists of at least Q and at
+  // most its capacity of neighbours
+  const int kmax = ld / j.nc;
+  const bool okdfx = fast_allowed && p->basis == GMLS_BASIS_DIVFREE &&
+                     kmax >= gmls_gen::basis_size(GMLS_BASIS_SCALAR, dim, p->degree) &&
+                     dfx_path_available(dim, p->degree, kmax, j.L);
   auto launch_fast = [&](const StencilJob& jj, int variant) {
+    if (variant == -3) return launch_stencils_dfx(ctx->launch(), jj, sms);
     return variant == -2 ? launch_stencils_fast(ctx->launch(), jj, mr16, 16, sms)
                          : launch_stencils_fast(ctx->launch(), jj, mr32, 32, sms);
   };
   const TuneKey key{p->basis, dim, p->degree, p->precision, ld, j.L, p->neumann, 0};
-  int choice = 0;  // -1 / -2 register kernel (32 / 16 lanes per target), else a vcode
+  int choice = 0;  // -1 / -2 register kernel (32 / 16 lanes per target), -3 factored div-free, else a vcode
   auto it = ctx->tune.find(key);
   if (ctx->force_variant != 0) {
     const int v = ctx->force_variant;
-    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || (v > 0 && variant_fits(v, ld, nmax, refine));
+    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || (v == -3 && okdfx) ||
+                    (v > 0 && variant_fits(v, ld, nmax, refine));
     if (!ok) return fail(ctx, GMLS_EINVAL, "gmls_stencils: the forced kernel variant is not available for this shape");
     choice = v;
   } else if (ctx->force_generic) {
@@ -392,6 +400,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     std::vector<int> cands;
     if (ok32) cands.push_back(-1);
     if (ok16) cands.push_back(-2);
+    if (okdfx) cands.push_back(-3);
     for (int v : generic_candidates(ld, nmax, refine)) cands.push_back(v);
     for (int c : cands) {
       float ms = time_launch(ctx, [&]() {
@@ -410,7 +419,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: no kernel variant fits this shape");
     ctx->tune[key] = choice;
   } else {
-    choice = hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_variant(ld, nmax, refine);
+    choice = okdfx ? -3 : hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_variant(ld, nmax, refine);
   }
   if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this shape");
   if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
@@ -424,7 +433,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     // (with uniform neighbour counts only Neumann rows or a tile with fewer
     // rows than basis functions are handed off)
     const int vg = heuristic_variant(ld, nmax, true);
-    if (vg && (p->neumann || ld < nmax))
+    if (vg && (p->neumann || ld < nmax || choice == -3))
       CK(launch_single(ctx, jg, vg, ld, nmax, true, counter, sms), "gmls_stencils hand-off launch");
   } else
     CK(launch_single(ctx, j, choice, ld, nmax, refine, counter, sms), "gmls_stencils launch");
@@ -667,10 +676,10 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
     case GMLS_OPT_FORCE_GENERIC: ctx->force_generic = value != 0; return GMLS_OK;
     case GMLS_OPT_AUTOTUNE: ctx->autotune = value != 0; return GMLS_OK;
     case GMLS_OPT_FORCE_VARIANT:
-      if (value != 0 && value != -1 && value != -2 &&
+      if (value != 0 && value != -1 && value != -2 && value != -3 &&
           !(value > 0 && value < 24 && (v_warps((int)value) == 1 || v_warps((int)value) == 2 ||
                                         v_warps((int)value) == 4)))
-        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2 or G + 8 * P (G 1, 2, 4; P 0, 1, 2)");
+        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2, -3 or G + 8 * P (G 1, 2, 4; P 0, 1, 2)");
       ctx->force_variant = (int)value;
       return GMLS_OK;
     case GMLS_OPT_POISON:

@@ -227,6 +227,10 @@ bool fast_path_available(int kind, int dim, int deg, int rows, int L, int hw, in
 // the preferred group width for a shape: fewest padded row slots, then 32
 int fast_path_preferred(int kind, int dim, int deg, int rows, int L, int* mr_out);
 cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms);
+// factored divergence-free kernel (dfx.cu): is (dim, degree) instantiated for
+// lists of at most kmax neighbours and L solve rows, and its launch
+bool dfx_path_available(int dim, int deg, int kmax, int L);
+cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, int sms);
 
 // -------------------------------------------------------------------- CSR
 // id order of neighbour lists (see nbr_order_kernel): order[off[t] + r] =

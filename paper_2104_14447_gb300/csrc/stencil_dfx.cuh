@@ -1,0 +1,780 @@
+// stencil_dfx.cuh -- divergence-free GMLS stencils through a factored QR.
+// (kernel template; instantiations and dispatch in dfx.cu)
+//
+// Sec. 2.2 of the paper builds the divergence-free reconstruction on a basis
+// of pi^div_m = {v in (pi_m)^d : div v = 0}.  Every component of such a field
+// is a scalar polynomial of degree <= m, so with the scaled Taylor monomials
+// p_g(xi) = xi^g / g! (Eq. basis-functions-3d) the weighted basis matrix of a
+// target factors exactly as
+//
+//     B[(j, c), i] = sum_g A[j, g] C[(c, g), i],   A = diag(sqrt(W)) P_scalar,
+//
+// A being the k x Q scalar Taylor tile of degree m (Q = C(m + d, d)) and C a
+// constant 0 / +-1 matrix.  The basis used here (any basis of the span gives
+// the same stencils) is, with d/dxi_k p_g = p_{g - e_k}:
+//
+//     phi_{c,g} = e_c p_g - e_0 p_{g - e_c + e_0}    c = 1..d-1, |g| <= m
+//                 (second term only when g_c >= 1), div phi = p_{g-e_c} - p_{g-e_c} = 0;
+//     phi_{0,g} = e_0 p_g                            g_0 = 0.
+//
+// That is (d - 1) Q + #{g : g_0 = 0} functions: 9 / 14 / 20 in 2D and 26 / 50
+// in 3D for m = 2 / 3 / 4, the dimension of pi^div_m.
+//
+// Least squares through two QR factorisations (FP32, one warp per target):
+//   1. A = Q_A R_A (Householder, the tile in registers);
+//   2. G = (I_d (x) R_A) C, rows ordered (components 1..d-1 | component 0),
+//      columns (phi_{1,.} .. phi_{d-1,.} | phi_{0,.}).  Its top (d - 1) Q rows
+//      are diag(R_A, .., R_A) (upper triangular, zero in the phi_0 columns);
+//      only the Q bottom rows need eliminating: column j < (d-1) Q by a
+//      reflector on (top row j, bottom rows), the last columns by a dense QR
+//      of what is left of the bottom block;
+//   3. B = (I (x) Q_A) Q_G R_G is a QR factorisation of B, so R_G is its R
+//      factor and Q_B = (I (x) Q_A) Q_G.
+// For the 240 x 50 systems of the 3D degree-3 basis this is about 0.17 MFLOP
+// of factorisation instead of 1.12 MFLOP for a QR of B.
+//
+// Refinement (Bjorck) of the augmented system as in the other FP32 kernels,
+// with the float-float residuals taken through the factored form:
+//   f = B y - s:   u = C y (Q per (l, c)), f_(l,c,j) = A_j . u_(l,c) - s_(l,c,j);
+//   g = lambda - B^T s:   v_(l,c) = A^T s_(l,c),  g = lambda - C^T v,
+// 2 k Q d L compensated products per pass instead of 2 k d n L, and a
+// correction ds = f + Q_B [R^-T g - d_1; 0], dy = R^-1 (R^-T g - d_1),
+// d_1 = the first n entries of Q_B^T f.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <utility>
+
+#include "stencil_fast.cuh"
+
+namespace gmls {
+
+// ------------------------------------------------------------ basis tables
+// Scalar Taylor monomials of degree <= M, in the order of the generated
+// evaluators (degree ascending; within a degree g_x descending, then g_y).
+template <int D, int M>
+struct DfxMono {
+  static constexpr int Q = D == 2 ? (M + 1) * (M + 2) / 2 : (M + 1) * (M + 2) * (M + 3) / 6;
+  int e[Q][3];
+  constexpr DfxMono() : e() {
+    int i = 0;
+    for (int s = 0; s <= M; ++s) {
+      if (D == 2) {
+        for (int gx = s; gx >= 0; --gx) {
+          e[i][0] = gx;
+          e[i][1] = s - gx;
+          e[i][2] = 0;
+          ++i;
+        }
+      } else {
+        for (int gx = s; gx >= 0; --gx)
+          for (int gy = s - gx; gy >= 0; --gy) {
+            e[i][0] = gx;
+            e[i][1] = gy;
+            e[i][2] = s - gx - gy;
+            ++i;
+          }
+      }
+    }
+  }
+  constexpr int index(int a, int b, int c) const {
+    for (int i = 0; i < Q; ++i)
+      if (e[i][0] == a && e[i][1] == b && e[i][2] == c) return i;
+    return -1;
+  }
+};
+
+template <int D, int M>
+struct DfxDims {
+  static constexpr int Q = DfxMono<D, M>::Q;
+  static constexpr int NTOP = (D - 1) * Q;                                  // phi_{c,g}, c >= 1
+  static constexpr int N0 = D == 2 ? M + 1 : (M + 1) * (M + 2) / 2;        // phi_{0,g}, g_0 = 0
+  static constexpr int N = NTOP + N0;
+  static constexpr int L = D;   // solve rows: the vector Laplacian, one per component
+  static constexpr int LC = L * D;
+};
+
+// Lookup tables with run-time indices (a kernel parameter: constant bank).
+//   src[i]:    column i < NTOP (phi_{c,g}): monomial g - e_c + e_0, or -1;
+//              column i >= NTOP (phi_{0,g}): monomial g;
+//   fidx[g]:   g_0 = 0: position of phi_{0,g} among the phi_0 columns, else -1;
+//   ush[c][g]: c >= 1, g_0 >= 1: monomial g + e_c - e_0 (whose phi_{c,.}
+//              puts -p_g into component 0), else -1;
+//   lam[l][i]: vector Laplacian row l on basis function i, times eps^2.
+struct DfxTab {
+  int8_t src[64];
+  int8_t fidx[32];
+  int8_t ush[3][32];
+  int8_t lam[3][64];
+};
+
+template <int D, int M>
+DfxTab make_dfx_tab() {
+  constexpr DfxMono<D, M> mo{};
+  using Dm = DfxDims<D, M>;
+  DfxTab t;
+  for (auto& v : t.src) v = -1;
+  for (auto& v : t.fidx) v = -1;
+  for (auto& r : t.ush)
+    for (auto& v : r) v = -1;
+  for (auto& r : t.lam)
+    for (auto& v : r) v = 0;
+  auto is2 = [&](int g) {  // g = 2 e_k for some k
+    int two = 0, zero = 0;
+    for (int q = 0; q < 3; ++q) {
+      two += mo.e[g][q] == 2;
+      zero += mo.e[g][q] == 0;
+    }
+    return two == 1 && zero == 2;
+  };
+  int f = 0;
+  for (int g = 0; g < Dm::Q; ++g)
+    if (mo.e[g][0] == 0) {
+      t.fidx[g] = (int8_t)f;
+      t.src[Dm::NTOP + f] = (int8_t)g;
+      if (is2(g)) t.lam[0][Dm::NTOP + f] += 1;
+      ++f;
+    }
+  for (int c = 1; c < D; ++c)
+    for (int g = 0; g < Dm::Q; ++g) {
+      const int i = (c - 1) * Dm::Q + g;
+      int e[3] = {mo.e[g][0], mo.e[g][1], mo.e[g][2]};
+      if (is2(g)) t.lam[c][i] += 1;
+      if (e[c] >= 1) {
+        e[c] -= 1;
+        e[0] += 1;
+        const int s = mo.index(e[0], e[1], e[2]);
+        t.src[i] = (int8_t)s;
+        t.ush[c][s] = (int8_t)g;
+        if (is2(s)) t.lam[0][i] -= 1;
+      }
+    }
+  return t;
+}
+
+// Shared memory of one warp (one target in flight).  KS: neighbour capacity.
+template <int D, int M, int KS>
+struct DfxLay {
+  using Dm = DfxDims<D, M>;
+  static constexpr int Q = Dm::Q, N = Dm::N, NTOP = Dm::NTOP, N0 = Dm::N0, L = Dm::L, LC = Dm::LC;
+  static constexpr int LDA = KS + 1;  // odd: rows of different columns in different banks
+  static constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
+  static constexpr size_t AFF = 0;                                      // ff [Q][LDA]  A = sqrt(W) P
+  static constexpr size_t S = al16(AFF + sizeof(ff) * Q * LDA);         // ff [LC][LDA] s iterates (R_A first)
+  static constexpr size_t Y = al16(S + sizeof(ff) * LC * LDA);          // ff [L][N]
+  static constexpr size_t UV = al16(Y + sizeof(ff) * L * N);            // ff [LC][Q]   u = C y, then v = A^T s
+  static constexpr size_t RG = al16(UV + sizeof(ff) * LC * Q);          // float [N(N+1)/2] R_G, rows packed
+  static constexpr size_t IDG = al16(RG + sizeof(float) * N * (N + 1) / 2);  // float [N] 1 / r_ii
+  static constexpr size_t V1 = al16(IDG + sizeof(float) * N);           // float [NTOP][Q] stage-1 reflectors
+  static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * Q);     // float [N0][Q] stage-2 reflectors
+  static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * Q);     // float [N]
+  static constexpr size_t TAUA = al16(TAUG + sizeof(float) * N);        // float [Q]
+  static constexpr size_t SW = al16(TAUA + sizeof(float) * Q);          // ff [KS] sqrt(W)
+  static constexpr size_t IEPS = al16(SW + sizeof(ff) * KS);            // ff 1 / eps
+  static constexpr size_t BYTES = al16(IEPS + sizeof(ff));
+  static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(ff) * LC * LDA, "R_A must fit in the s slot");
+};
+
+// x[sl] += v / x[sl] for a run-time slot index (static register indices)
+template <int S>
+__device__ __forceinline__ void dfx_add_slot(float (&x)[S], int sl, float v) {
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+    if (i == sl) x[i] += v;
+}
+template <int S>
+__device__ __forceinline__ float dfx_get_slot(const float (&x)[S], int sl) {
+  float v = x[0];
+#pragma unroll
+  for (int i = 1; i < S; ++i)
+    if (i == sl) v = x[i];
+  return v;
+}
+
+// z <- Q_A^T z (REV false) or Q_A z (REV true) for V row-distributed vectors
+// (row lane + 32 t in z[q][t]); reflector k is column k of the register tile
+// below the diagonal (v_k[k] = 1).  The V dot products of a reflector are
+// all-reduced together (recursive halving).
+template <int MR, int Q, int V, bool REV>
+__device__ __forceinline__ void dfx_apply_qa(const float (&a)[MR][Q], const float* tau, float (&z)[V][MR], int lane,
+                                             unsigned mask) {
+#pragma unroll
+  for (int s = 0; s < Q; ++s) {
+    const int k = REV ? Q - 1 - s : s;
+    const float tk = tau[k];
+    float v[MR];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+      const int r = lane + 32 * i;
+      v[i] = (r > k) ? a[i][k] : (r == k ? 1.0f : 0.0f);
+    }
+    float d[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      d[q] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < MR; ++i) d[q] = fmaf(v[i], z[q][i], d[q]);
+    }
+    allreduce_tail<32, V, 0>(d, lane, mask);
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const float dq = d[q] * tk;
+#pragma unroll
+      for (int i = 0; i < MR; ++i) z[q][i] = fmaf(-dq, v[i], z[q][i]);
+    }
+  }
+}
+
+// z <- Q_G^T z (FWD) or Q_G z in the row space of G: top rows p < NTOP at
+// lane p % 32, slot p / 32 of zt; bottom rows r < Q at lane r of zb.
+// Stage-1 reflector jst acts on (top row jst, bottom rows) with vector
+// (1, V1[jst][.]); stage-2 reflector j2 on the bottom rows with V2[j2][.]
+// (one at row j2, zero above).
+template <int L, int TS, int Q, int NTOP, int N0, bool FWD>
+__device__ __forceinline__ void dfx_apply_qg(float (&zt)[L][TS], float (&zb)[L], const float* V1, const float* V2,
+                                             const float* taug, int lane, unsigned mask) {
+  auto stage1 = [&](int jst) {
+    const float v = lane < Q ? V1[jst * Q + lane] : 0.0f;
+    const float tk = taug[jst];
+    const int own = jst & 31, sl = jst >> 5;
+    float d[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) d[l] = fmaf(v, zb[l], lane == own ? dfx_get_slot<TS>(zt[l], sl) : 0.0f);
+    allreduce_tail<32, L, 0>(d, lane, mask);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const float dl = d[l] * tk;
+      zb[l] = fmaf(-dl, v, zb[l]);
+      if (lane == own) dfx_add_slot<TS>(zt[l], sl, -dl);
+    }
+  };
+  auto stage2 = [&](int j2) {
+    const float v = lane < Q ? V2[j2 * Q + lane] : 0.0f;
+    const float tk = taug[NTOP + j2];
+    float d[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) d[l] = v * zb[l];
+    allreduce_tail<32, L, 0>(d, lane, mask);
+#pragma unroll
+    for (int l = 0; l < L; ++l) zb[l] = fmaf(-d[l] * tk, v, zb[l]);
+  };
+  if (FWD) {
+#pragma unroll 1
+    for (int jst = 0; jst < NTOP; ++jst) stage1(jst);
+#pragma unroll 1
+    for (int j2 = 0; j2 < N0; ++j2) stage2(j2);
+  } else {
+#pragma unroll 1
+    for (int j2 = N0 - 1; j2 >= 0; --j2) stage2(j2);
+#pragma unroll 1
+    for (int jst = NTOP - 1; jst >= 0; --jst) stage1(jst);
+  }
+}
+
+// Householder reflector of a column held by one lane: alpha the diagonal
+// entry, x[r] for r in (lo, Q) the entries below it.  Writes the reflector
+// vector (vout[r]: 1 at r == lo when lo >= 0, zero above), tau and beta.
+template <int Q>
+__device__ __forceinline__ void dfx_reflect(float alpha, const float (&x)[Q], int lo, float* vout, float* tau_out,
+                                            float* beta_out) {
+  float sig = 0.0f;
+#pragma unroll
+  for (int r = 0; r < Q; ++r)
+    if (r > lo) sig = fmaf(x[r], x[r], sig);
+  float tk = 0.0f, beta = alpha, scale = 0.0f;
+  if (sig > 0.0f) {
+    const float nrm = sqrtf(fmaf(alpha, alpha, sig));
+    beta = alpha >= 0.0f ? -nrm : nrm;
+    scale = __fdividef(1.0f, alpha - beta);
+    tk = __fdividef(beta - alpha, beta);
+  }
+#pragma unroll
+  for (int r = 0; r < Q; ++r) vout[r] = r > lo ? x[r] * scale : (r == lo ? 1.0f : 0.0f);
+  *tau_out = tk;
+  *beta_out = beta;
+}
+
+template <int D, int M, int MRA, int KS>
+__global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const DfxTab tab) {
+  using Dm = DfxDims<D, M>;
+  constexpr int Q = Dm::Q, N = Dm::N, NTOP = Dm::NTOP, N0 = Dm::N0, L = Dm::L, LC = Dm::LC;
+  constexpr int NT = (N + 31) / 32;     // slots of an N-vector (solve layout)
+  constexpr int TS = (NTOP + 31) / 32;  // slots of the top rows of G
+  static_assert(Q <= 32 && N <= 64 && NTOP <= 64 && KS <= 32 * MRA && N0 <= Q, "tile outside this kernel's layout");
+  static_assert(N == gmls_gen::basis_size(GMLS_BASIS_DIVFREE, D, M), "dimension of the divergence-free span");
+  using Lay = DfxLay<D, M, KS>;
+  constexpr int LDA = Lay::LDA;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const unsigned mask = 0xffffffffu;
+  unsigned char* base = smem + (size_t)wid * Lay::BYTES;
+  ff* Aff = reinterpret_cast<ff*>(base + Lay::AFF);
+  ff* Ss = reinterpret_cast<ff*>(base + Lay::S);
+  float* RA = reinterpret_cast<float*>(base + Lay::S);  // R_A, packed rows (before s exists)
+  ff* Ys = reinterpret_cast<ff*>(base + Lay::Y);
+  ff* UV = reinterpret_cast<ff*>(base + Lay::UV);
+  float* RG = reinterpret_cast<float*>(base + Lay::RG);
+  float* IDG = reinterpret_cast<float*>(base + Lay::IDG);
+  float* V1 = reinterpret_cast<float*>(base + Lay::V1);
+  float* V2 = reinterpret_cast<float*>(base + Lay::V2);
+  float* TAUG = reinterpret_cast<float*>(base + Lay::TAUG);
+  float* TAUA = reinterpret_cast<float*>(base + Lay::TAUA);
+  ff* SWs = reinterpret_cast<ff*>(base + Lay::SW);
+  const int64_t n = j.n;
+  const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
+  const float tolf = (float)j.tol;
+
+  for (int64_t it = (int64_t)blockIdx.x * wpb + wid; it < n_items; it += (int64_t)gridDim.x * wpb) {
+    const int64_t to = j.items ? (int64_t)j.items[it] : it;
+    const int64_t t = j.tgt[to];
+    const int64_t o0 = j.off[to];
+    const int k = (int)(j.off[to + 1] - o0);
+    uint8_t st = j.nbr_status ? j.nbr_status[to] : 0;
+    const bool too_few = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || !(j.eps[to] > 0.0);
+    if (!too_few && (k < Q || k > KS || j.L != L)) {
+      // not for this path: the shared-memory FP32 kernel takes it
+      if (lane == 0) {
+        const int slot = atomicAdd(j.gen_count, 1);
+        j.gen_items[slot] = (int32_t)to;
+        j.status[to] = 0;
+      }
+      continue;
+    }
+    if (too_few) {
+      for (int f = 0; f < j.nout; ++f) {
+        const int64_t cnt = (int64_t)j.out_rows[f] * k * j.out_ncomp[f];
+        double* w = j.out_w[f] + o0 * (int64_t)j.out_rows[f] * j.out_ncomp[f];
+        for (int64_t e = lane; e < cnt; e += 32) w[e] = 0.0;
+      }
+      if (j.beta)
+        for (int l = lane; l < j.L; l += 32) j.beta[to * j.L + l] = 0.0;
+      if (lane == 0) {
+        j.status[to] = st;
+        if (j.iters) j.iters[to] = 0;
+      }
+      continue;
+    }
+
+    // ---- 1. A = sqrt(W) P (scalar Taylor tile) in float-float, FP32 copy in registers
+    const ff eps(j.eps[to]);
+    const ff inv_eps = recip(eps);
+    const ff ie2 = inv_eps * inv_eps;
+    double xt[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < D; ++c) xt[c] = j.x[c * n + t];
+    const int half_p = j.wpow_half;
+    float a[MRA][Q];
+#pragma unroll
+    for (int tt = 0; tt < MRA; ++tt) {
+      const int q = lane + 32 * tt;
+      ff p[Q];
+      if (q < k) {
+        const int32_t jj = j.idx[o0 + q];
+        ff dx[3], xi[3];
+        ff r2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          dx[c] = diff_ff(j.x[c * n + jj], xt[c]);
+          xi[c] = dx[c] * inv_eps;
+          r2 = r2 + dx[c] * dx[c];
+        }
+        const ff u = ff(1.f, 0.f) - sqrt_ff(r2) * inv_eps;
+        ff sw(0.f, 0.f);
+        if (u.h > 0.0f) {
+          sw = u;
+          for (int pp = 1; pp < half_p; ++pp) sw = sw * u;
+        }
+        gmls_gen::BasisEval<GMLS_BASIS_SCALAR, D, M>::template run<ff>(xi, p, 1, sw);
+#pragma unroll
+        for (int g = 0; g < Q; ++g) Aff[g * LDA + q] = p[g];
+        SWs[q] = sw;
+      } else {
+#pragma unroll
+        for (int g = 0; g < Q; ++g) p[g] = ff(0.f, 0.f);
+      }
+#pragma unroll
+      for (int g = 0; g < Q; ++g) a[tt][g] = p[g].h;
+    }
+    __syncwarp(mask);
+
+    // ---- 2. A = Q_A R_A in registers; R_A row r (lane r) packed into RA
+    qr_columns<32, MRA, Q>(a, TAUA, lane, mask, std::make_integer_sequence<int, Q>{});
+    if (lane < Q) {
+#pragma unroll
+      for (int c = 0; c < Q; ++c)
+        if (c >= lane) RA[rpk<Q>(lane, c)] = a[0][c];
+    }
+    __syncwarp(mask);
+
+    // ---- 3. G = (I (x) R_A) C: the bottom block (component 0 rows), one
+    //         column per lane and slot (column lane + 32 s)
+    float xg[2][Q];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int col = lane + 32 * s;
+      const int src = col < N ? (int)tab.src[col] : -1;
+      const float sgn = col < NTOP ? -1.0f : 1.0f;
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        xg[s][r] = 0.0f;
+        if (src >= r) xg[s][r] = sgn * RA[rpk<Q>(r, src)];  // R_A is upper triangular
+      }
+    }
+    // stage 1: column jst < NTOP against top row jst (R_A row al of block blk)
+#pragma unroll 1
+    for (int jst = 0; jst < NTOP; ++jst) {
+      const int blk = jst / Q, al = jst - blk * Q;
+      if (lane == (jst & 31)) {
+        float beta, tk;
+        const float alpha = RA[rpk<Q>(al, al)];
+        if (jst < 32)
+          dfx_reflect<Q>(alpha, xg[0], -1, V1 + jst * Q, &tk, &beta);
+        else
+          dfx_reflect<Q>(alpha, xg[1], -1, V1 + jst * Q, &tk, &beta);
+        TAUG[jst] = tk;
+        RG[rpk<N>(jst, jst)] = beta;
+      }
+      __syncwarp(mask);
+      const float tk = TAUG[jst];
+      float v[Q];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) v[r] = V1[jst * Q + r];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int col = lane + 32 * s;
+        if (col > jst && col < N) {
+          const int cb = col / Q, cg = col - cb * Q;
+          float tc = 0.0f;  // T[jst][col]: R_A row al within the same block
+          if (col < NTOP && cb == blk && cg >= al) tc = RA[rpk<Q>(al, cg)];
+          float dot = tc;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) dot = fmaf(v[r], xg[s][r], dot);
+          dot *= tk;
+          RG[rpk<N>(jst, col)] = tc - dot;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) xg[s][r] = fmaf(-dot, v[r], xg[s][r]);
+        }
+      }
+      __syncwarp(mask);
+    }
+    // stage 2: dense QR of the remaining bottom-block columns
+#pragma unroll 1
+    for (int j2 = 0; j2 < N0; ++j2) {
+      const int colk = NTOP + j2;
+      if (lane == (colk & 31)) {
+        float beta, tk;
+        float alpha = 0.0f;
+        if (colk < 32) {
+#pragma unroll
+          for (int r = 0; r < Q; ++r)
+            if (r == j2) alpha = xg[0][r];
+          dfx_reflect<Q>(alpha, xg[0], j2, V2 + j2 * Q, &tk, &beta);
+        } else {
+#pragma unroll
+          for (int r = 0; r < Q; ++r)
+            if (r == j2) alpha = xg[1][r];
+          dfx_reflect<Q>(alpha, xg[1], j2, V2 + j2 * Q, &tk, &beta);
+        }
+        TAUG[colk] = tk;
+        RG[rpk<N>(colk, colk)] = beta;
+      }
+      __syncwarp(mask);
+      const float tk = TAUG[colk];
+      float v[Q];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) v[r] = V2[j2 * Q + r];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int col = lane + 32 * s;
+        if (col > colk && col < N) {
+          float dot = 0.0f;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) dot = fmaf(v[r], xg[s][r], dot);
+          dot *= tk;
+          float rrow = 0.0f;
+#pragma unroll
+          for (int r = 0; r < Q; ++r) {
+            xg[s][r] = fmaf(-dot, v[r], xg[s][r]);
+            if (r == j2) rrow = xg[s][r];
+          }
+          RG[rpk<N>(colk, col)] = rrow;
+        }
+      }
+      __syncwarp(mask);
+    }
+    // 1 / r_ii and the conditioning of the factor
+    float rmax = 0.0f, rmin = 3.0e38f;
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+      const int p = lane + 32 * s;
+      if (p < N) {
+        const float d = RG[rpk<N>(p, p)];
+        IDG[p] = 1.0f / d;
+        rmax = fmaxf(rmax, fabsf(d));
+        rmin = fminf(rmin, fabsf(d));
+      }
+    }
+    rmax = wmax<32>(rmax, mask);
+    rmin = -wmax<32>(-rmin, mask);
+    const bool ill = !(rmin * 1.0e6f >= rmax) || !(rmin > 0.0f);
+    if (lane == 0) reinterpret_cast<ff*>(base + Lay::IEPS)[0] = inv_eps;
+    __syncwarp(mask);
+
+    // ---- 4. solve and refinement (pass 0 = the plain FP32 solve)
+    auto lam = [&](int l, int i) {  // vector Laplacian row l at basis function i (float-float)
+      const int c = tab.lam[l][i];
+      return c == 0 ? ff(0.f, 0.f) : mul_f(ie2, (float)c);
+    };
+    float f[LC][MRA];
+    bool conv = false;
+    int used = 0;
+    float prev = 0.0f;
+#pragma unroll 1
+    for (int itr = 0; itr <= j.max_refine; ++itr) {
+      float w[L][NT], d1[L][NT];
+      if (itr > 0) {
+        if (ill) break;
+        // u = C y
+        for (int e = lane; e < LC * Q; e += 32) {
+          const int lc = e / Q, g = e - lc * Q, l = lc / D, c = lc - l * D;
+          ff uv(0.f, 0.f);
+          if (c >= 1) {
+            uv = Ys[l * N + (c - 1) * Q + g];
+          } else if (tab.fidx[g] >= 0) {
+            uv = Ys[l * N + NTOP + tab.fidx[g]];
+          } else {
+#pragma unroll
+            for (int c2 = 1; c2 < D; ++c2) {
+              const int ug = tab.ush[c2][g];
+              if (ug >= 0) uv = uv - Ys[l * N + (c2 - 1) * Q + ug];
+            }
+          }
+          UV[e] = uv;
+        }
+        __syncwarp(mask);
+        // f = B y - s: row (l, c, j) = A_j . u_(l,c) - s_(l,c,j)
+#pragma unroll
+        for (int tt = 0; tt < MRA; ++tt) {
+          const int q = lane + 32 * tt;
+          if (q < k) {
+            ff ar[Q];
+#pragma unroll
+            for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
+#pragma unroll
+            for (int lc = 0; lc < LC; ++lc) {
+              Dot2 acc;
+              acc.init(-Ss[lc * LDA + q]);
+#pragma unroll
+              for (int g = 0; g < Q; ++g) acc.add_prod(ar[g], UV[lc * Q + g]);
+              f[lc][tt] = __fadd_rn(acc.h, acc.l);
+            }
+          } else {
+#pragma unroll
+            for (int lc = 0; lc < LC; ++lc) f[lc][tt] = 0.0f;
+          }
+        }
+        __syncwarp(mask);
+        // v = (I (x) A^T) s, two interleaved compensated chains per entry
+        for (int e = lane; e < LC * Q; e += 32) {
+          const int lc = e / Q, g = e - lc * Q;
+          const ff* ag = Aff + g * LDA;
+          const ff* sl = Ss + lc * LDA;
+          Dot2 c0, c1;
+          int q = 0;
+          for (; q + 1 < k; q += 2) {
+            c0.add_prod(ag[q], sl[q]);
+            c1.add_prod(ag[q + 1], sl[q + 1]);
+          }
+          if (q < k) c0.add_prod(ag[q], sl[q]);
+          UV[e] = c0.value() + c1.value();
+        }
+        __syncwarp(mask);
+        // g = lambda - C^T v in the solve layout
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int s = 0; s < NT; ++s) {
+            const int i = lane + 32 * s;
+            float gv = 0.0f;
+            if (i < N) {
+              ff ct(0.f, 0.f);
+              if (i < NTOP) ct = UV[(l * D + 1 + i / Q) * Q + i % Q];
+              const int src = tab.src[i];
+              if (src >= 0) {
+                const ff v0 = UV[(l * D) * Q + src];
+                ct = i < NTOP ? ct - v0 : ct + v0;
+              }
+              const ff gg = lam(l, i) - ct;
+              gv = __fadd_rn(gg.h, gg.l);
+            }
+            w[l][s] = gv;
+          }
+        // d_1 = first N entries of Q_G^T gather(Q_A^T f)
+        float z[LC][MRA];
+#pragma unroll
+        for (int lc = 0; lc < LC; ++lc)
+#pragma unroll
+          for (int tt = 0; tt < MRA; ++tt) z[lc][tt] = f[lc][tt];
+        dfx_apply_qa<MRA, Q, LC, false>(a, TAUA, z, lane, mask);
+        float zt[L][TS], zb[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          zb[l] = lane < Q ? z[l * D][0] : 0.0f;
+#pragma unroll
+          for (int s = 0; s < TS; ++s) {
+            const int p = lane + 32 * s;
+            const int cb = p / Q, al = p - cb * Q;  // top row p: component cb + 1, R_A row al
+            float val = 0.0f;
+#pragma unroll
+            for (int c = 1; c < D; ++c) {
+              const float sh = __shfl_sync(mask, z[l * D + c][0], al < 32 ? al : 0);
+              if (cb + 1 == c) val = sh;
+            }
+            zt[l][s] = p < NTOP ? val : 0.0f;
+          }
+        }
+        dfx_apply_qg<L, TS, Q, NTOP, N0, true>(zt, zb, V1, V2, TAUG, lane, mask);
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int s = 0; s < NT; ++s) {
+            const int p = lane + 32 * s;
+            const float fromb = __shfl_sync(mask, zb[l], (p - NTOP) & 31);
+            d1[l][s] = p < NTOP ? (s < TS ? zt[l][s < TS ? s : 0] : 0.0f) : (p < N ? fromb : 0.0f);
+          }
+      } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+          for (int s = 0; s < NT; ++s) {
+            const int p = lane + 32 * s;
+            w[l][s] = p < N ? lam(l, p).h : 0.0f;
+            d1[l][s] = 0.0f;
+          }
+      }
+      solve_rt_lanes<32, N, L>(RG, IDG, w, lane, mask);  // a = R^-T g
+      float dyv[L][NT];
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int s = 0; s < NT; ++s) {
+          dyv[l][s] = w[l][s] - d1[l][s];  // delta
+          w[l][s] = dyv[l][s];
+        }
+      solve_r_lanes<32, N, L>(RG, IDG, dyv, lane, mask);  // dy = R^-1 delta
+      // ds = f + Q_B [delta; 0]: Q_G in the row space of G, then Q_A per (l, c)
+      float zt[L][TS], zb[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+#pragma unroll
+        for (int s = 0; s < TS; ++s) {
+          const int p = lane + 32 * s;
+          zt[l][s] = p < NTOP ? w[l][s < NT ? s : 0] : 0.0f;
+        }
+        // bottom row r < N0 holds delta[NTOP + r]
+        const int p = NTOP + lane;
+        float b0 = __shfl_sync(mask, w[l][0], p & 31);
+        float b1 = NT > 1 ? __shfl_sync(mask, w[l][NT - 1], p & 31) : 0.0f;
+        zb[l] = lane < N0 ? ((p >> 5) == 0 ? b0 : b1) : 0.0f;
+      }
+      dfx_apply_qg<L, TS, Q, NTOP, N0, false>(zt, zb, V1, V2, TAUG, lane, mask);
+      float z[LC][MRA];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        z[l * D][0] = lane < Q ? zb[l] : 0.0f;
+#pragma unroll
+        for (int c = 1; c < D; ++c) {
+          const int p = (c - 1) * Q + lane;  // top row of (component c, R_A row lane)
+          const float s0 = __shfl_sync(mask, zt[l][0], p & 31);
+          const float s1 = TS > 1 ? __shfl_sync(mask, zt[l][TS - 1], p & 31) : 0.0f;
+          z[l * D + c][0] = lane < Q ? ((p >> 5) == 0 ? s0 : s1) : 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int tt = 1; tt < MRA; ++tt) z[l * D + c][tt] = 0.0f;
+      }
+      dfx_apply_qa<MRA, Q, LC, true>(a, TAUA, z, lane, mask);
+      // s += ds, y += dy; the size of the correction for the stopping rule
+      float dmax = 0.0f, smax = 0.0f;
+#pragma unroll
+      for (int lc = 0; lc < LC; ++lc)
+#pragma unroll
+        for (int tt = 0; tt < MRA; ++tt) {
+          const int q = lane + 32 * tt;
+          if (q < k) {
+            const float ds = itr > 0 ? z[lc][tt] + f[lc][tt] : z[lc][tt];
+            const ff s1 = itr > 0 ? add_f(Ss[lc * LDA + q], ds) : ff(ds, 0.0f);
+            Ss[lc * LDA + q] = s1;
+            dmax = fmaxf(dmax, fabsf(ds));
+            smax = fmaxf(smax, fabsf(s1.h));
+          }
+        }
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int s = 0; s < NT; ++s) {
+          const int p = lane + 32 * s;
+          if (p < N) Ys[l * N + p] = itr > 0 ? add_f(Ys[l * N + p], dyv[l][s]) : ff(dyv[l][s], 0.0f);
+        }
+      dmax = wmax<32>(dmax, mask);
+      smax = wmax<32>(smax, mask);
+      __syncwarp(mask);
+      if (itr == 0) continue;
+      used = itr;
+      const float rho = (itr == 1) ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
+      const float est = dmax * fminf(1.0f, rho);
+      conv = est <= tolf * smax;
+      prev = dmax;
+      if (conv) break;
+    }
+    if (!conv) {
+      if (lane == 0) {
+        const int slot = atomicAdd(j.fb_count, 1);
+        j.fb_items[slot] = (int32_t)to;
+        j.status[to] = ill ? GMLS_T_ILL_CONDITIONED : GMLS_T_REFINE_NOT_CONVERGED;
+      }
+      __syncwarp(mask);
+      continue;
+    }
+
+    // ---- 5. w = sqrt(W) s (FP64) in [row][neighbour][component]
+    for (int fo = 0; fo < j.nout; ++fo) {
+      const int R = j.out_rows[fo], C = j.out_ncomp[fo], src = j.out_src[fo];
+      double* wo = j.out_w[fo] + o0 * (int64_t)R * C;
+      const int per_row = k * C;
+      const float sgn = (float)j.out_sign[fo];
+      for (int rr = 0; rr < R; ++rr) {
+        for (int e = lane; e < per_row; e += 32) {
+          double val = 0.0;
+          if (src >= 0) {
+            const int q = e / C, c = e - q * C;
+            const ff s = Ss[((src + rr) * D + c) * LDA + q] * SWs[q];
+            val = to_double(ff(sgn * s.h, sgn * s.l));
+          }
+          wo[(int64_t)rr * per_row + e] = val;
+        }
+      }
+    }
+    if (j.beta)
+      for (int l = lane; l < j.L; l += 32) j.beta[to * j.L + l] = 0.0;
+    if (lane == 0) {
+      j.status[to] = st;
+      if (j.iters) j.iters[to] = (uint8_t)used;
+    }
+    __syncwarp(mask);
+  }
+}
+
+// ----------------------------------------------------------------- dispatch
+struct DfxEntry {
+  int dim, deg, mra, ks;
+  const void* fn;
+  size_t bytes;  // shared memory per warp
+  DfxTab (*tab)();
+};
+
+#define GMLS_DFX(D, M, MRA, KS) \
+  DfxEntry { D, M, MRA, KS, (const void*)stencil_dfx_kernel<D, M, MRA, KS>, DfxLay<D, M, KS>::BYTES, &make_dfx_tab<D, M> }
+
+}  // namespace gmls
