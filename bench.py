@@ -1,20 +1,26 @@
 """GMLS stencil-generation benchmark (one JSON line on rank 0).
 
-Workload (the 2D Stokes operators of the compatible GMLS scheme, arXiv
-2104.14447 Sec. 3): 262,144 targets on a 512 x 512 jittered grid in the unit
-square (h = 1/512, jitter +-h/4, seed 0), sources = targets.  One step is the
-whole hot path:
+Headline workload (the 3D porous medium, the largest configuration that fits
+one GPU): a jittered 128^3 lattice in the unit cube minus 64 random
+non-overlapping spheres of radius 0.05-0.12 (1,763,183 points; 142,894 of
+them on a sphere surface or cube face, with the geometric normal), sources =
+targets.  One step is the whole hot path:
 
-  cell-list build -> 36- and 48-nearest-neighbour lists (eps = 1.5 d_k) ->
-  scalar Taylor degree-4 stencils (15 terms; pressure gradient and the
-  component-wise divergence) -> divergence-free degree-4 stencils (20 terms,
-  96 x 20 systems; vector Laplacian) -> three CSR operators.
+  cell-list build -> 80-nearest lists (eps = 1.5 d_k) and their 40-nearest
+  prefix -> scalar Taylor degree-3 stencils (20 terms; gradient and
+  Laplacian, with the Neumann constraint of Sec. 2.3 at boundary targets) ->
+  divergence-free degree-3 stencils (50 terms, 240 x 50 systems; vector
+  Laplacian) -> three CSR operators.
 
-value: targets/s of the whole job (every target gets all three operators).
-The default precision is FP32 Householder QR with refinement against
-float-float (FP64-class) residuals; ``--precision fp64`` times the plain FP64
-path.  The 36-nearest lists are the first 36 entries of the 48-nearest lists
-(one search; both are prefixes of the same (d^2, id) order).
+value: targets/s of the whole job (every target gets all three operators),
+inputs resident on the device, L2 flushed between timed steps.  FP32
+Householder QR with refinement against float-float (FP64-class) residuals.
+
+Secondary sections: the 2D Stokes operators on a 512 x 512 grid (262,144
+targets, scalar m = 4 and div-free m = 4, FP32 + refinement and FP64), the
+1,024-target 2D FP64 case, the uneven batch (1,000,000 mixed targets, one
+bucketed launch per cloud), the serving stream, every serving shape, and the
+Stokes block systems and solve.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 it runs under torch.distributed.run, one rank per GPU; every rank
@@ -24,6 +30,7 @@ no data-path collective; only the timing is reduced).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -36,11 +43,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "GMLS targets/sec"
+# headline: 3D porous medium
+P_N_AXIS = 128
+P_K_SCALAR, P_K_DIVFREE, P_DEGREE = 40, 80, 3
+WORKLOAD = ("porous3d-128: 128^3 jittered lattice minus 64 spheres; scalar m=3 (40 nbrs; grad, Laplacian, "
+            "Neumann at boundary targets) + div-free m=3 (80 nbrs, 240x50; vector Laplacian) + CSR")
+# secondary: 2D Stokes operators on the 512 x 512 grid
 N_AXIS = 512
 K_SCALAR, K_DIVFREE, EPS_FACTOR, DEGREE = 36, 48, 1.5, 4
-E2E_CHUNKS = 4  # default target ranges of the end-to-end pipeline (copies overlap compute)
-METRIC = "GMLS targets/sec"
-WORKLOAD = "stokes2d-512x512: scalar m=4 (36 nbrs; grad, div) + div-free m=4 (48 nbrs; vector Laplacian) + CSR"
+E2E_CHUNKS = 4  # default target ranges of the end-to-end pipelines (copies overlap compute)
+WORKLOAD_2D = "stokes2d-512x512: scalar m=4 (36 nbrs; grad, div) + div-free m=4 (48 nbrs; vector Laplacian) + CSR"
 
 
 def _peaks():
@@ -52,41 +65,44 @@ def _peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-# ALU peaks of one GB300 from unit counts and the maximum SM clock (2070 MHz):
-#   FP32: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s
-#   FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz     = 1.26 TFLOP/s
-P32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-P64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+def alu_peaks(dev):
+    """FP32 / FP64 pipe peaks of the device (TFLOP/s) from its SM count and the
+    maximum SM clock: 128 FP32 FMA lanes and 2 FP64 FMA units per SM, 2 flop
+    per FMA.  MEASURED_PEAKS.json holds HBM and bf16 figures only, so these
+    are unit counts (the clock from that file, else 2070 MHz)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, src = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    p32 = sms * 128 * 2 * mhz * 1e6 / 1e12
+    p64 = sms * 2 * 2 * mhz * 1e6 / 1e12
+    return p32, p64, f"unit counts: {sms} SMs x 128 FP32 lanes (FP64: x 2 units) x 2 flop x {mhz:.0f} MHz ({src} clock)"
 
 
-# FP32 operations of one compensated float-float product-accumulate (Dot2 step):
-# TwoProd (1 mul + 1 fma), two cross-term fmas, TwoSum (6 adds), 2 adds;
-# an fma counts as 2.
-DOT2_FLOPS = 15
+def alg_flops(M, n, L, iters):
+    """Algorithmic flops of one target (the scope table's count): Householder
+    QR of the M x n tile 2Mn^2 - 2n^3/3; per functional row the apply
+    n^2 + 4Mn; per refinement iteration and row the residual 4Mn.  The
+    float-float emulation, the basis evaluation and the padding are not
+    counted."""
+    return 2 * M * n * n - 2 * n ** 3 / 3 + L * (n * n + 4 * M * n) + iters * L * 4 * M * n
 
 
-# DRAM bytes (read + write) per target of the divergence-free register-kernel
-# launch, from ncu on the 384 x 384 grid (147,456 targets: 33.95 MB read,
-# 168.58 MB written); the algorithmic floor is the 1,536 B of FP64 weights
-# per target (2 rows x 48 neighbours x 2 components), some of which is still
-# in L2 when the kernel ends
-DIVFREE_DRAM_BYTES_PER_TARGET = (33.947648e6 + 168.576256e6) / 147456
+def src_sha(*names):
+    """Short hash of kernel sources, to tie a stored ncu figure to the code it measured."""
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2104_14447_gb300", "csrc", nm), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def flops_per_target(M, n, rows, iters):
-    """Algorithmic FP32 flops of one target of the float-float kernel:
-    QR 2Mn^2 - 2n^3/3; per functional row the initial solve (2n^2 triangular +
-    4Mn for Q); per refinement iteration and row the residuals f = By - s and
-    g = lambda - B^T s (2Mn compensated products) and the correction
-    (2n^2 + 8Mn).  The float-float tile build is not counted."""
-    f32 = (2 * M * n * n - 2 * n ** 3 / 3 + rows * (2 * n * n + 4 * M * n)
-           + iters * rows * (2 * M * n * DOT2_FLOPS + 8 * M * n + 2 * n * n))
-    return f32, 0.0
-
-
-def flops_per_target_fp64(M, n, rows):
-    """FP64 path: QR and the initial solve, all on the FP64 pipe."""
-    return 2 * M * n * n - 2 * n ** 3 / 3 + rows * (2 * n * n + 4 * M * n)
+# DRAM bytes (read + write) per launch measured by ncu on the timed launch
+# (dram__bytes_read.sum + dram__bytes_write.sum, one pass), with the hash of
+# the kernel sources it was taken on; a different hash reports null
+DFX_TRAFFIC = {"bytes": None, "sha": None, "sources": ("stencil_dfx.cuh", "stencil_fast.cuh", "ff.cuh"),
+               "command": None}
 
 
 class Clocks:
@@ -147,11 +163,44 @@ def set_n_axis(v):
     N_AXIS = int(v)
 
 
-# ---------------------------------------------------------------- our arm
-def run_ours(args, rank, world, local_rank):
+# ------------------------------------------------------ headline: porous 3D
+def porous_step_fn(ctx, prec, bufs):
+    """One step of the porous-medium hot path on the context (cloud given as
+    (x, normals, bflags) tensors, device or pinned host); returns the handles."""
+    from paper_2104_14447_gb300 import gmls
+
+    stream = ctx.stream
+
+    def step(src, ev=None):
+        rec = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
+        rec(0)
+        cid = ctx.cloud(src[0], normals=src[1], bflags=src[2])
+        rec(1)
+        n80 = ctx.neighbors(cid, P_K_DIVFREE, EPS_FACTOR)
+        n40 = ctx.neighbors_prefix(n80, P_K_SCALAR, EPS_FACTOR)  # the 40 nearest = first 40 of the 80
+        rec(2)
+        ssc = ctx.stencils(n40, gmls.SCALAR, P_DEGREE, [gmls.GRAD, gmls.LAPLACIAN], precision=prec, neumann=True)
+        rec(3)
+        sdf = ctx.stencils(n80, gmls.DIVFREE, P_DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
+        rec(4)
+        ctx.assemble_csr(ssc, gmls.GRAD, out=bufs["grad"])
+        ctx.assemble_csr(ssc, gmls.LAPLACIAN, out=bufs["lap"])
+        ctx.assemble_csr(sdf, gmls.VEC_LAPLACIAN, out=bufs["vl"])
+        rec(5)
+        return cid, n80, n40, ssc, sdf
+
+    return step
+
+
+def run_headline(args, rank, world, local_rank):
+    """The 3D porous-medium step: device-timed throughput (inputs resident),
+    stage times, the roofline of the dominant kernel (the divergence-free
+    stencil launch), the same step end to end through the C ABI from pinned
+    host input to host CSR operators, and the GPU outputs of a seeded 5 %
+    target sample for the oracle comparison."""
     import torch
 
-    from paper_2104_14447_gb300 import build, gmls, shard
+    from paper_2104_14447_gb300 import build, gmls, inputs, shard
 
     if rank == 0 or world == 1:
         build.build()
@@ -159,21 +208,321 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    prec = gmls.FP64 if args.precision == "fp64" else gmls.FP32_REFINE
+    prec = gmls.FP32_REFINE
+    pc = inputs.porous_cube(n_axis=args.porous_n_axis)
+    n = pc["x"].shape[1]
+    host = (torch.from_numpy(pc["x"]), torch.from_numpy(np.ascontiguousarray(pc["normals"])),
+            torch.from_numpy(pc["bflag"]))
+    dsrc = tuple(t.to(dev) for t in host)
+    ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
+    stream = ctx.stream
+    # operators: gradient (3 rows x 40), Laplacian (1 x 40), vector Laplacian (3 x 80 x 3 components)
+    per_target = {"grad": (3, P_K_SCALAR), "lap": (1, P_K_SCALAR), "vl": (3, 3 * P_K_DIVFREE)}
+    bufs = {}
+    for name, (rows, per_row) in per_target.items():
+        nnz = n * rows * per_row
+        bufs[name] = (torch.empty(n * rows + 1, dtype=torch.int64, device=dev),
+                      torch.empty(nnz, dtype=torch.int32, device=dev),
+                      torch.empty(nnz, dtype=torch.float64, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    step = porous_step_fn(ctx, prec, bufs)
+
+    def release(ids):
+        for h in reversed(ids):
+            ctx.release(h)
+
+    for _ in range(args.warmup):
+        release(step(dsrc))
+    torch.cuda.synchronize()
+    # refinement statistics of this workload (one untimed step)
+    ids = step(dsrc)
+    it_sc = ctx.export(ids[3], gmls.X_ITERS, torch.uint8).float()
+    it_df = ctx.export(ids[4], gmls.X_ITERS, torch.uint8).float()
+    st_sc = ctx.export(ids[3], gmls.X_STATUS, torch.uint8)
+    st_df = ctx.export(ids[4], gmls.X_STATUS, torch.uint8)
+    redo = {"scalar": int(((st_sc & gmls.T_FP64_FALLBACK) != 0).sum()),
+            "divfree": int(((st_df & gmls.T_FP64_FALLBACK) != 0).sum())}
+    mean_it_sc, mean_it_df = float(it_sc.mean()), float(it_df.mean())
+    iters_hist = {str(i): int((it_df == i).sum()) for i in range(5) if int((it_df == i).sum())}
+    release(ids)
+    torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    launches0 = ctx.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local_rank) as clk:
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(s & 0xFF)  # evict L2 between timed steps (outside the events)
+            torch.cuda.nvtx.range_push("porous_step")  # lets a profiler select the timed launches
+            ids = step(dsrc, evs[s])
+            torch.cuda.nvtx.range_pop()
+            release(ids)
+        torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    stage = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(5)] for e in evs])
+    step_ms = [float(e[0].elapsed_time(e[5])) for e in evs]
+    total_ms = shard.max_over_ranks(float(np.sum(step_ms)), dev)
+
+    # roofline of the dominant kernel: the divergence-free stencil launch
+    # (240 x 50 systems, 3 functional rows), CUDA events on the context stream
+    k_avg = float(np.mean(stage[:, 3])) * 1e-3
+    p32, p64, peak_src = alu_peaks(dev)
+    f_t = alg_flops(3 * P_K_DIVFREE, 50, 3, mean_it_df)
+    achieved = n * f_t / k_avg / 1e12
+    sha = src_sha(*DFX_TRAFFIC["sources"])
+    traffic = DFX_TRAFFIC["bytes"] if DFX_TRAFFIC["sha"] == sha else None
+    out_bytes = n * 3 * P_K_DIVFREE * 3 * 8  # FP64 weights written
+    roofline = {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s", "frac": achieved / p32,
+                "traffic": traffic,
+                "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the timed launch "
+                                 f"({DFX_TRAFFIC['command']})") if traffic else
+                                "null: no ncu figure for the current kernel sources",
+                "algorithmic_output_bytes": out_bytes,
+                "kernel": "stencil_dfx_kernel<3, 3> (factored div-free QR, FP32 + float-float refinement; "
+                          "240 x 50 systems)",
+                "pipe": "fp32", "flops_per_target": f_t, "mean_refine_iters": mean_it_df,
+                "flop_count": "2Mn^2 - 2n^3/3 + L (n^2 + 4Mn) + iters L 4Mn, M = 240, n = 50, L = 3",
+                "peak_source": peak_src, "kernel_ms": k_avg * 1e3}
+
+    # end to end through the C ABI: pinned host coordinates, normals and
+    # flags in; the three CSR operators back in pinned host memory.  The
+    # targets go through in ranges so that the operators of the first ranges
+    # travel to the host (on copy streams) while the GPU computes the rest:
+    # per range the 80-nearest lists, the divergence-free stencils and their
+    # operator rows, written in place by gmls_assemble_csr_at; then per range
+    # the 40-nearest prefix lists, the scalar stencils and their two operators.
+    e2e = None
+    if not args.no_e2e:
+        pin = tuple(t.pin_memory() for t in host)
+        host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
+        n_ranges = args.e2e_ranges
+        bounds = [n * c // n_ranges for c in range(n_ranges + 1)]
+        d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v) + 8 * 3 * (n_ranges - 1)
+        h2d = sum(t.numel() * t.element_size() for t in pin)
+        copy_streams = [torch.cuda.Stream(dev) for _ in range(args.e2e_copy_streams)]
+        chunk_tg = [torch.arange(a, b, dtype=torch.int32, device=dev) for a, b in zip(bounds[:-1], bounds[1:])]
+
+        def ship(sid, fn, kname, c, which):
+            rows, per_row = per_target[kname]
+            a, b = bounds[c], bounds[c + 1]
+            lo, hi = a * rows * per_row, b * rows * per_row
+            sl = (slice(a * rows, b * rows + 1), slice(lo, hi), slice(lo, hi))
+            dev_out = tuple(t[q] for t, q in zip(bufs[kname], sl))
+            ctx.assemble_csr(sid, fn, out=dev_out, nnz_offset=lo)
+            done = torch.cuda.Event()
+            done.record(stream)
+            cs = copy_streams[which % len(copy_streams)]
+            cs.wait_event(done)
+            with torch.cuda.stream(cs):
+                for dst, src, q in zip(host_out[kname], dev_out, sl):
+                    dst[q].copy_(src, non_blocking=True)
+
+        def step_e2e():
+            cid = ctx.cloud(pin[0], normals=pin[1], bflags=pin[2])
+            ids, n80s = [cid], []
+            for c in range(n_ranges):
+                n80 = ctx.neighbors(cid, P_K_DIVFREE, EPS_FACTOR, targets=chunk_tg[c])
+                sdf = ctx.stencils(n80, gmls.DIVFREE, P_DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
+                ship(sdf, gmls.VEC_LAPLACIAN, "vl", c, c)
+                n80s.append(n80)
+                ids += [n80, sdf]
+            for c in range(n_ranges):
+                n40 = ctx.neighbors_prefix(n80s[c], P_K_SCALAR, EPS_FACTOR)
+                ssc = ctx.stencils(n40, gmls.SCALAR, P_DEGREE, [gmls.GRAD, gmls.LAPLACIAN], precision=prec,
+                                   neumann=True)
+                ship(ssc, gmls.GRAD, "grad", c, 2 * c)
+                ship(ssc, gmls.LAPLACIAN, "lap", c, 2 * c + 1)
+                ids += [n40, ssc]
+            return ids
+
+        e2e_ms = []
+        for s in range(max(3, min(args.steps, 5)) + 1):
+            with torch.cuda.stream(stream):
+                flush.fill_(s & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ids = step_e2e()
+            torch.cuda.synchronize()  # every range's copies done: the operators are on the host
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            release(ids)
+        e2e_ms = e2e_ms[1:]
+        # the host operators equal the device step's, bit for bit (checked once, untimed, on the device)
+        ids = step(dsrc)
+        torch.cuda.synchronize()
+        equal = all(torch.equal(h.to(dev, non_blocking=True), d) for k in bufs for h, d in zip(host_out[k], bufs[k]))
+        release(ids)
+        e2e = {"value": n * world / (float(np.median(e2e_ms)) * 1e-3), "unit": "targets/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms],
+               "target_ranges": n_ranges, "copy_streams": len(copy_streams),
+               "host_operators_equal_device_step": equal}
+        del host_out, pin
+
+    # GPU outputs of a seeded 5 % target sample for the oracle comparison
+    ids = step(dsrc)
+    m = max(1, int(round(0.05 * n)))
+    sample = np.unique((inputs.uniform(7, 131, m) * n).astype(np.int64)).astype(np.int32)
+    sdev = torch.from_numpy(sample.astype(np.int64)).to(dev)
+    gs = {"pc": pc, "sample": sample, "ops": []}
+    for key, nh, sh, k, kind, code in (("grad", ids[2], ids[3], P_K_SCALAR, "scalar", gmls.GRAD),
+                                       ("laplacian", ids[2], ids[3], P_K_SCALAR, "scalar", gmls.LAPLACIAN),
+                                       ("vec_laplacian", ids[1], ids[4], P_K_DIVFREE, "divfree", gmls.VEC_LAPLACIAN)):
+        idx = ctx.export(nh, gmls.X_NBR_INDEX, torch.int32).view(n, k)[sdev].cpu().numpy()
+        _, rows, nc, _ = ctx.stencil_info(sh, code)
+        wg = ctx.weights(sh, code).view(n, rows, k, nc)[sdev].cpu().numpy()
+        gs["ops"].append((key, k, kind, idx, wg))
+    release(ids)
+
+    tune = tune_names(ctx, lambda r: r["dim"] == 3 and not r["bucketed"])
+    value = shard.job_throughput(n, args.steps, world, total_ms)
+    med = np.median(stage, axis=0)
+    out = {
+        "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+ff", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "targets_per_gpu": n, "points": n,
+                   "boundary_targets": int(pc["bflag"].sum()), "porosity": float(pc["porosity"]),
+                   "precision": "fp32 QR + float-float refinement (FP64 redo of flagged targets)",
+                   "degree": P_DEGREE, "neighbours": [P_K_SCALAR, P_K_DIVFREE], "eps_factor": EPS_FACTOR,
+                   "weight": "(1-r/eps)_+^4", "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"independent replicas x{world}" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "stage_ms": {"cell_list": float(med[0]), "neighbours": float(med[1]), "scalar_stencils": float(med[2]),
+                     "divfree_stencils": float(med[3]), "csr": float(med[4])},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df,
+                       "divfree_iters_histogram": iters_hist, "fp64_redo_targets": redo},
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "autotune_ms": tune,
+    }
+    return out, ctx, gs
+
+
+def tune_names(ctx, keep):
+    """The autotuner's timings (ms) by shape and kernel variant."""
+    tune = {}
+    for r in ctx.tune_log():
+        if not keep(r):
+            continue
+        key = (f"{r['dim']}d {['scalar', 'divfree', 'staggered'][r['basis']]} m={r['degree']} rows<={r['rows']}"
+               f"{' fp64' if r['precision'] == 0 else ''}{' bucketed' if r['bucketed'] else ''}")
+        tune.setdefault(key, {})[variant_name(r["variant"])] = round(r["ms"], 3)
+    return tune
+
+
+def variant_name(v):
+    if v is None:
+        return None
+    if v < 0:
+        return {-1: "register", -2: "register 16 lanes", -3: "factored div-free"}.get(v, str(v))
+    place = {0: "", 1: ", split tiles", 2: ", global tiles"}.get(v >> 3, "")
+    return f"{v & 7} warp(s)/target{place}"
+
+
+def porous_cpu_baseline(gs, threads_all=None):
+    """The oracle as it stands on the host cores over the seeded 5 % target
+    sample of the porous workload (kNN lists, both prefix-free scalar and
+    div-free stencils, CSR), all cores; a 0.5 % sample on one core; and the
+    GPU outputs of the same 5 % sample against the oracle's (every target,
+    every functional row: max relative error and the error over the bar
+    max(1e-9, 1e-15 kappa))."""
+    import oracle
+
+    oracle.build()
+    pc, sample = gs["pc"], gs["sample"]
+    x = pc["x"]
+    n = x.shape[1]
+    cores = os.cpu_count() or 1
+
+    def run(tg):
+        ns = len(tg)
+        i80, e80 = oracle.knn(x, tg, P_K_DIVFREE, EPS_FACTOR, method="grid")
+        i40, e40 = oracle.knn(x, tg, P_K_SCALAR, EPS_FACTOR, method="grid")
+        off40, off80 = np.arange(0, ns * P_K_SCALAR + 1, P_K_SCALAR), np.arange(0, ns * P_K_DIVFREE + 1, P_K_DIVFREE)
+        extra = dict(bflag=pc["bflag"][tg], normals=pc["normals"].T[tg])
+        res = {}
+        for key, kind, i, o, e, ex in (("grad", "scalar", i40, off40, e40, extra),
+                                        ("laplacian", "scalar", i40, off40, e40, extra),
+                                        ("vec_laplacian", "divfree", i80, off80, e80, {})):
+            w, _, diag = oracle.stencils(x, tg, o, i.reshape(-1), e, kind, P_DEGREE, key, **ex)
+            oracle.csr(o, i.reshape(-1), w, n)
+            res[key] = (i, w, diag)
+        return res
+
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    res = run(sample)
+    dt = time.perf_counter() - t0
+    one = sample[::10]
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    run(one)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    errs, scaled, lists_equal = {}, {}, True
+    for key, k, kind, idx, wg in gs["ops"]:
+        oi, wo, diag = res[key]
+        lists_equal &= bool(np.array_equal(idx, oi))
+        w = wg.reshape(wo.shape)
+        a = np.abs(w - wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
+        b = np.abs(wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
+        rel = a / np.where(b > 0, b, 1.0)
+        kap = diag[:, 0] / np.maximum(diag[:, 1], 1e-300)
+        errs[key] = float(rel.max())
+        scaled[key] = float((rel / np.maximum(1e-9, 1e-15 * kap)[:, None]).max())
+    return {"value": len(sample) / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
+            "sample": (f"seeded 5 % of the targets ({len(sample)} of {n}), full pipeline incl. kNN and CSR; "
+                       "the rate extrapolates linearly to the whole workload"),
+            "seconds": dt, "cpu_model": cpu_model(),
+            "single_core": {"value": len(one) / dt1, "unit": "targets/s", "sample": f"{len(one)} targets (every "
+                            "10th of the 5 % sample)", "seconds": dt1},
+            "gpu_vs_oracle": {"targets_compared": int(len(sample)), "neighbour_lists_equal": lists_equal,
+                              "max_rel_err": errs, "max_err_over_bar": scaled,
+                              "bar": "max(1e-9, 1e-15 kappa) per (target, row), kappa from the oracle's FP64 factor"}}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+# --------------------------------------------- secondary: 2D Stokes operators
+def stokes2d_section(ctx, args, prec_name="fp32_refine"):
+    """The 2D Stokes operators on the 512 x 512 grid (262,144 targets): cell
+    list, 48-nearest lists and their 36-nearest prefix, scalar degree-4
+    stencils (gradient, divergence), divergence-free degree-4 stencils (96 x
+    20 systems, vector Laplacian), three CSR operators.  Device-timed
+    throughput, the roofline of the divergence-free stencil launch, the same
+    step end to end (pinned host input to host operators) and captured as a
+    CUDA graph (FP32 path), and the GPU error against the oracle on a sample."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls
+
+    dev = ctx.device
+    prec = gmls.FP64 if prec_name == "fp64" else gmls.FP32_REFINE
     x_host = workload_points()
     n = x_host.shape[1]
     x_dev = torch.from_numpy(x_host).to(dev)
-    ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
     stream = ctx.stream
-    # output buffers of the three operators (sizes are fixed by k)
     nnz_grad, nnz_div, nnz_vl = n * K_SCALAR * 2, n * K_SCALAR * 2, n * K_DIVFREE * 2 * 2
     bufs = {}
     for name, rows, nnz in (("grad", 2 * n, nnz_grad), ("div", n, nnz_div), ("vl", 2 * n, nnz_vl)):
         bufs[name] = (torch.empty(rows + 1, dtype=torch.int64, device=dev),
                       torch.empty(nnz, dtype=torch.int32, device=dev),
                       torch.empty(nnz, dtype=torch.float64, device=dev))
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    ev_k = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step(x_src, k_events=None):
         cid = ctx.cloud(x_src)
@@ -197,7 +546,6 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         release(step(x_dev))
     torch.cuda.synchronize()
-    # refinement statistics of this workload (one untimed step)
     ids = step(x_dev)
     it_sc = ctx.export(ids[3], gmls.X_ITERS, torch.uint8).float()
     it_df = ctx.export(ids[4], gmls.X_ITERS, torch.uint8).float()
@@ -211,66 +559,66 @@ def run_ours(args, rank, world, local_rank):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     launches0 = ctx.launch_count()
-    if world > 1:
-        torch.distributed.barrier()
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
+        ids = step(x_dev, kev[s])
+        ev[s][1].record(stream)
+        release(ids)
     torch.cuda.synchronize()
-    with Clocks(local_rank) as clk:
-        for s in range(args.steps):
-            flush.fill_(s & 0xFF)  # evict L2 between timed steps (outside the events)
-            ev[s][0].record(stream)
-            ids = step(x_dev, kev[s])
-            ev[s][1].record(stream)
-            release(ids)
-        torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kern_ms = [a.elapsed_time(b) for a, b in kev]
-    total_ms = shard.max_over_ranks(float(np.sum(step_ms)), dev)
+    total_ms = float(np.sum(step_ms))
+    k_avg = float(np.mean(kern_ms)) * 1e-3
+    p32, p64, peak_src = alu_peaks(dev)
+    if prec == gmls.FP32_REFINE:
+        f_t, peak, pipe = alg_flops(2 * K_DIVFREE, 20, 2, mean_it_df), p32, "fp32"
+    else:
+        f_t, peak, pipe = alg_flops(2 * K_DIVFREE, 20, 2, 0), p64, "fp64"
+    achieved = n * f_t / k_avg / 1e12
+    tl = [r for r in ctx.tune_log() if r["dim"] == 2 and r["basis"] == gmls.DIVFREE and r["degree"] == DEGREE
+          and r["precision"] == prec and not r["bucketed"]]
+    chosen = variant_name(min(tl, key=lambda r: r["ms"])["variant"]) if tl else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"divergence-free stencil launch, 96 x 20 systems ({chosen or 'heuristic'})",
+                "pipe": pipe, "flops_per_target": f_t, "mean_refine_iters": mean_it_df if prec != gmls.FP64 else 0,
+                "flop_count": "2Mn^2 - 2n^3/3 + L (n^2 + 4Mn) + iters L 4Mn, M = 96, n = 20, L = 2",
+                "peak_source": peak_src, "kernel_ms": k_avg * 1e3}
+    out = {"workload": WORKLOAD_2D, "targets": n, "precision": prec_name, "value": n * args.steps / total_ms * 1e3,
+           "unit": "targets/s", "ms_per_step": total_ms / args.steps, "gpu_launches": int(launches),
+           "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df,
+                          "fp64_fallback_targets": fb} if prec != gmls.FP64 else None,
+           "roofline": roofline}
+    if prec == gmls.FP64:
+        return out
 
     # e2e: the same step through the C ABI from pinned host input to host operators
     x_pin = torch.from_numpy(x_host).pin_memory()
     host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
-    d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v)
-    d2h += 8 * 3 * ((len(args.e2e_fractions.split(",")) if args.e2e_fractions else args.e2e_ranges) - 1)  # shared row pointers
+    n_ranges = args.e2e_ranges
+    d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v) + 8 * 3 * (n_ranges - 1)
     h2d = x_pin.numel() * x_pin.element_size()
-    # The targets are processed in --e2e-ranges contiguous ranges so that the
-    # operators of the first ranges travel to the host (on two copy streams)
-    # while the GPU computes the rest: per range the 48-nearest lists, the
-    # divergence-free stencils and their CSR rows; then per range the
-    # 36-nearest prefix lists, the scalar stencils and the gradient and
-    # divergence CSR rows.  Each range writes its rows in place in the
-    # operator (gmls_assemble_csr_at), so the host receives the operators
-    # themselves.
     copy_streams = [torch.cuda.Stream(dev) for _ in range(args.e2e_copy_streams)]
-    if args.e2e_fractions:
-        fr = np.array([float(v) for v in args.e2e_fractions.split(",")])
-        bounds = [0] + [int(round(n * v)) for v in np.cumsum(fr / fr.sum())[:-1]] + [n]
-    else:
-        bounds = [n * c // args.e2e_ranges for c in range(args.e2e_ranges + 1)]
-    n_ranges = len(bounds) - 1
+    bounds = [n * c // n_ranges for c in range(n_ranges + 1)]
     chunk_tg = [torch.arange(a, b, dtype=torch.int32, device=dev) for a, b in zip(bounds[:-1], bounds[1:])]
     per_target = {"vl": (2, K_DIVFREE * 2), "grad": (2, K_SCALAR), "div": (1, K_SCALAR * 2)}  # rows, nnz per row
 
-    def chunk_views(kname, c):
-        """(device views, host views, nonzero offset) of range c's rows."""
+    def assemble_and_ship(sid, fn, kname, c, which):
         rows, per_row = per_target[kname]
         a, b = bounds[c], bounds[c + 1]
         lo, hi = a * rows * per_row, b * rows * per_row
-        rp, col, val = bufs[kname]
-        hrp, hcol, hval = host_out[kname]
-        sl_r, sl_n = slice(a * rows, b * rows + 1), slice(lo, hi)
-        return (rp[sl_r], col[sl_n], val[sl_n]), (hrp[sl_r], hcol[sl_n], hval[sl_n]), lo
-
-    def assemble_and_ship(sid, fn, kname, c, which):
-        dev_out, host_dst, lo = chunk_views(kname, c)
+        sl = (slice(a * rows, b * rows + 1), slice(lo, hi), slice(lo, hi))
+        dev_out = tuple(t[q] for t, q in zip(bufs[kname], sl))
         ctx.assemble_csr(sid, fn, out=dev_out, nnz_offset=lo)
         done = torch.cuda.Event()
         done.record(stream)
-        cs = copy_streams[which]
+        cs = copy_streams[which % len(copy_streams)]
         cs.wait_event(done)
         with torch.cuda.stream(cs):
-            for dst, src in zip(host_dst, dev_out):
-                dst.copy_(src, non_blocking=True)
+            for dst, src, q in zip(host_out[kname], dev_out, sl):
+                dst[q].copy_(src, non_blocking=True)
 
     def step_e2e(x_src):
         cid = ctx.cloud(x_src)
@@ -279,65 +627,43 @@ def run_ours(args, rank, world, local_rank):
         for c in range(n_ranges):
             n48 = ctx.neighbors(cid, K_DIVFREE, EPS_FACTOR, targets=chunk_tg[c])
             s_df = ctx.stencils(n48, gmls.DIVFREE, DEGREE, [gmls.VEC_LAPLACIAN], precision=prec)
-            assemble_and_ship(s_df, gmls.VEC_LAPLACIAN, "vl", c, c % len(copy_streams))
+            assemble_and_ship(s_df, gmls.VEC_LAPLACIAN, "vl", c, c)
             n48s.append(n48)
             ids += [n48, s_df]
         for c in range(n_ranges):
             n36 = ctx.neighbors_prefix(n48s[c], K_SCALAR, EPS_FACTOR)
             s_sc = ctx.stencils(n36, gmls.SCALAR, DEGREE, [gmls.GRAD, gmls.DIV], precision=prec)
-            assemble_and_ship(s_sc, gmls.GRAD, "grad", c, (2 * c) % len(copy_streams))
-            assemble_and_ship(s_sc, gmls.DIV, "div", c, (2 * c + 1) % len(copy_streams))
+            assemble_and_ship(s_sc, gmls.GRAD, "grad", c, 2 * c)
+            assemble_and_ship(s_sc, gmls.DIV, "div", c, 2 * c + 1)
             ids += [n36, s_sc]
         return ids
 
-    def release_e2e(ids):
-        for h in reversed(ids):
-            ctx.release(h)
-
     e2e_ms = []
     for s in range(max(3, min(args.steps, 7)) + 1):
-        flush.fill_(s & 0xFF)
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ids = step_e2e(x_pin)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        release_e2e(ids)
+        release(ids)
     e2e_ms = e2e_ms[1:]
-    # the host operators equal the device step's (checked once, untimed)
     ids = step(x_dev)
     torch.cuda.synchronize()
     e2e_equal = all(torch.equal(h, d.cpu()) for k in bufs for h, d in zip(host_out[k], bufs[k]))
     release(ids)
+    out["e2e"] = {"value": n / (float(np.median(e2e_ms)) * 1e-3), "unit": "targets/s",
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                  "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms],
+                  "target_ranges": n_ranges, "host_operators_equal_device_step": e2e_equal}
 
-    # roofline of the dominant kernel (the divergence-free stencil launch)
-    M_df, n_df, rows_df = K_DIVFREE * 2, 20, 2
-    k_avg = float(np.mean(kern_ms)) * 1e-3
-    if prec == gmls.FP32_REFINE:
-        f32, _ = flops_per_target(M_df, n_df, rows_df, mean_it_df)
-        flops, peak, pipe = n * f32, P32_TFLOPS, "fp32"
-    else:
-        f64 = flops_per_target_fp64(M_df, n_df, rows_df)
-        flops, peak, pipe = n * f64, P64_TFLOPS, "fp64"
-    achieved = flops / k_avg / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": n * DIVFREE_DRAM_BYTES_PER_TARGET if prec == gmls.FP32_REFINE else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
-                                  "384 x 384 grid, per target, times the targets of this launch",
-                "kernel": "stencil_fast_kernel<divfree, 2D, m=4> (96x20 systems)"
-                if prec == gmls.FP32_REFINE else "stencil_kernel<double> (96x20 systems)",
-                "pipe": pipe, "flops_per_target": flops / n, "mean_refine_iters": mean_it_df,
-                "peak_source": "unit counts x 2070 MHz (152 SMs x 128 FP32 lanes; FP64 1/64 of that)",
-                "kernel_ms": k_avg * 1e3}
     # the same step captured once as a CUDA graph and replayed
-    graph_ms = None
     if args.graph:
         gstream = torch.cuda.Stream(dev)
-        gctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30, stream=gstream)
+        gctx = type(ctx)(ctx.device.index or 0, arena_bytes=args.arena_gb << 30, stream=gstream)
         with torch.cuda.stream(gstream):
             ids_g = None
-            ctx_save = ctx
-            # one eager run on this context fills its autotuner cache, then capture
             for capture in (False, True):
                 if capture:
                     gctx.capture_begin()
@@ -373,40 +699,9 @@ def run_ours(args, rank, world, local_rank):
             for h in reversed(ids_g):
                 gctx.release(h)
         gctx.close()
-        del ctx_save
-
-    tune = {}
-    for r in ctx.tune_log():
-        key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m={r['degree']} rows<={r['rows']}"
-        v = r["variant"]
-        place = {0: "", 1: ", split tiles", 2: ", global tiles"}[v >> 3] if v > 0 else ""
-        name = {-1: "register", -2: "register 16 lanes", -3: "factored div-free"}.get(v, f"{v & 7} warp(s)/target{place}")
-        tune.setdefault(key, {})[name] = round(r["ms"], 3)
-
-    value = shard.job_throughput(n, args.steps, world, total_ms)
-    out = {
-        "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == gmls.FP32_REFINE else "f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "targets_per_gpu": n, "precision": args.precision,
-                   "degree": DEGREE, "neighbours": [K_SCALAR, K_DIVFREE], "eps_factor": EPS_FACTOR,
-                   "weight": "(1-r/eps)_+^4", "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"independent replicas x{world}" if world > 1 else "1 GPU"},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "e2e": {"value": n * world / (float(np.median(e2e_ms)) * 1e-3), "unit": "targets/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms], "target_ranges": n_ranges, "range_bounds": bounds,
-                "host_operators_equal_device_step": e2e_equal},
-        "gpu_launches": int(launches),
-        "refinement": {"mean_iters_scalar": mean_it_sc, "mean_iters_divfree": mean_it_df, "fp64_fallback_targets": fb},
-        "roofline": roofline,
-        "clocks": clk.summary(),
-        "autotune_ms": tune,
-    }
-    if graph_ms is not None:
-        out["graph"] = {"ms_per_step": graph_ms, "targets_per_s": n * world / (graph_ms * 1e-3)}
-    return out, ctx
+        out["graph"] = {"ms_per_step": graph_ms, "targets_per_s": n / (graph_ms * 1e-3)}
+    out["autotune_ms"] = tune_names(ctx, lambda r: r["dim"] == 2 and not r["bucketed"])
+    return out
 
 
 SERVE_K = {(2, 0, 2): 12, (2, 0, 3): 20, (2, 0, 4): 36, (2, 1, 2): 22, (2, 1, 3): 34, (2, 1, 4): 48,
@@ -538,9 +833,7 @@ def shapes(ctx):
             tl = [r for r in ctx.tune_log() if r["dim"] == d and r["basis"] == b and r["degree"] == m
                   and r["precision"] == gmls.FP32_REFINE and r["rows"] == rows and not r["bucketed"]]
             v = min(tl, key=lambda r: r["ms"])["variant"] if tl else None
-            name = None if v is None else ({-1: "register", -2: "register 16 lanes"}.get(v) or
-                                           f"{v & 7} warp(s)/target" + {0: "", 1: ", split tiles",
-                                                                        2: ", global tiles"}[v >> 3])
+            name = variant_name(v)
             key = f"{d}d {['scalar', 'divfree', 'staggered'][b]} m={m} k={k}"
             out[key] = {"targets": n, "system": f"{rows} x {gmls_basis_size(d, b, m)}",
                         "fp32_refine_Mtargets_s": n / ms["fp32_refine"] / 1e3, "fp64_Mtargets_s": n / ms["fp64"] / 1e3,
@@ -561,6 +854,25 @@ def gmls_basis_size(d, b, m):
         return comb(m + 1 + d, d) - 1
     full = d * comb(m + d, d)
     return full - (comb(m - 1 + d, d))  # minus the divergence map's rank (onto degree m - 1)
+
+
+def porous_stokes_section(ctx, pc):
+    """Lists and Neumann-constrained scalar stencils of the headline step,
+    then the 3D Stokes block system on them (porous_stokes)."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=ctx.device)
+    cid = ctx.cloud(pc["x"], normals=pc["normals"], bflags=pc["bflag"])
+    n80 = ctx.neighbors(cid, P_K_DIVFREE, EPS_FACTOR)
+    n40 = ctx.neighbors_prefix(n80, P_K_SCALAR, EPS_FACTOR)
+    ssc = ctx.stencils(n40, gmls.SCALAR, P_DEGREE, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE,
+                       neumann=True)
+    res = porous_stokes(ctx, pc, n80, n40, ssc, flush)
+    for h in (ssc, n40, n80, cid):
+        ctx.release(h)
+    return res
 
 
 def porous_stokes(ctx, pc, n80, n40, ssc, flush, steps=3, nu=1.0):
@@ -641,135 +953,6 @@ def porous_stokes(ctx, pc, n80, n40, ssc, flush, steps=3, nu=1.0):
             "spmv_frac_hbm": spmv_bytes / tm_m / 1e6 / hbm, "peak_source": src,
             "cubic_data_max_rel_residual": res,
             "l2": "flushed before each timed step (256 MB write)"}
-
-
-def porous_3d(ctx, n_axis=128, steps=3, n_sample=48, stokes=True):
-    """The 3D porous-medium workload: a jittered n_axis^3 lattice in the unit
-    cube minus 64 random non-overlapping spheres, boundary targets on the
-    sphere surfaces and cube faces with their geometric normals.  Per step:
-    kNN-80 lists and their 40-nearest prefix, degree-3 scalar stencils
-    (gradient, Laplacian; Neumann constraint at boundary targets), degree-3
-    divergence-free stencils (vector Laplacian, 240 x 50 systems), FP32 with
-    float-float refinement, and the three CSR operators.  Device-timed per
-    stage with CUDA events on the context stream, inputs resident, L2 flushed
-    before each step; stencil errors on a sample of boundary and interior
-    targets against the oracle."""
-    import torch
-
-    from paper_2104_14447_gb300 import gmls, inputs
-
-    pc = inputs.porous_cube(n_axis=n_axis)
-    x = pc["x"]
-    n = x.shape[1]
-    stream = ctx.stream
-    cid = ctx.cloud(x, normals=pc["normals"], bflags=pc["bflag"])
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=ctx.device)
-    prec = gmls.FP32_REFINE
-
-    def step(ev=None):
-        rec = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
-        rec(0)
-        n80 = ctx.neighbors(cid, 80, EPS_FACTOR)
-        n40 = ctx.neighbors_prefix(n80, 40, EPS_FACTOR)
-        rec(1)
-        ssc = ctx.stencils(n40, gmls.SCALAR, 3, [gmls.GRAD, gmls.LAPLACIAN], precision=prec, neumann=True)
-        rec(2)
-        sdf = ctx.stencils(n80, gmls.DIVFREE, 3, [gmls.VEC_LAPLACIAN], precision=prec)
-        rec(3)
-        csr = [ctx.assemble_csr(ssc, gmls.GRAD), ctx.assemble_csr(ssc, gmls.LAPLACIAN),
-               ctx.assemble_csr(sdf, gmls.VEC_LAPLACIAN)]
-        rec(4)
-        return n80, n40, ssc, sdf, csr
-
-    def release(h):
-        for hd in (h[3], h[2], h[1], h[0]):
-            ctx.release(hd)
-
-    release(step())  # warm-up (autotunes the two shapes)
-    torch.cuda.synchronize()
-    times = []
-    for s in range(steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(s & 0xFF)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        torch.cuda.nvtx.range_push("porous_step")  # lets a profiler select the timed launches
-        h = step(ev)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
-        if s < steps - 1:
-            release(h)
-    med = np.median(np.array(times), axis=0)
-    step_ms = float(np.sum(med))
-    st_sc = ctx.export(h[2], gmls.X_STATUS, torch.uint8).cpu().numpy()
-    st_df = ctx.export(h[3], gmls.X_STATUS, torch.uint8).cpu().numpy()
-    # GPU outputs of a sample of boundary and interior targets, for the
-    # oracle comparison of the CPU-baseline leg (porous_oracle_errors)
-    bidx = np.flatnonzero(pc["bflag"])
-    iidx = np.flatnonzero(pc["bflag"] == 0)
-    half = n_sample // 2
-    sample = np.unique(np.concatenate([bidx[(inputs.uniform(2, 96, half) * len(bidx)).astype(np.int64)],
-                                       iidx[(inputs.uniform(2, 97, half) * len(iidx)).astype(np.int64)]]))
-    sample = sample.astype(np.int32)
-    gpu_sample = {"x": x, "bflag": pc["bflag"], "normals": pc["normals"], "sample": sample, "ops": []}
-    for key, nh, sh, k, kind, code in (("grad", h[1], h[2], 40, "scalar", gmls.GRAD),
-                                       ("laplacian", h[1], h[2], 40, "scalar", gmls.LAPLACIAN),
-                                       ("vec_laplacian", h[0], h[3], 80, "divfree", gmls.VEC_LAPLACIAN)):
-        idx = ctx.export(nh, gmls.X_NBR_INDEX, torch.int32).cpu().numpy().reshape(n, k)[sample]
-        _, rows, nc, _ = ctx.stencil_info(sh, code)
-        wg = ctx.weights(sh, code).cpu().numpy().reshape(n, rows, k, nc)[sample]
-        gpu_sample["ops"].append((key, k, kind, idx, wg))
-    stokes_out = None
-    if stokes:
-        ctx.release(h[3])  # the vector Laplacian stencils and the step's CSR operators: room for the system
-        h[4].clear()
-        stokes_out = porous_stokes(ctx, pc, h[0], h[1], h[2], flush)
-        for hd in (h[2], h[1], h[0]):
-            ctx.release(hd)
-    else:
-        release(h)
-    ctx.release(cid)
-    tune = {}
-    for r in ctx.tune_log():
-        if r["dim"] == 3 and r["degree"] == 3 and not r["bucketed"]:
-            v = r["variant"]
-            place = {0: "", 1: ", split tiles", 2: ", global tiles"}[v >> 3] if v > 0 else ""
-            name = {-1: "register", -2: "register 16 lanes", -3: "factored div-free"}.get(v, f"{v & 7} warp(s)/target{place}")
-            key = f"{'scalar' if r['basis'] == 0 else 'divfree'} m=3 rows<={r['rows']}"
-            tune.setdefault(key, {})[name] = round(r["ms"], 3)
-    qr_flops = 2 * 240 * 50 ** 2 - 2 * 50 ** 3 / 3  # Householder QR of one 240 x 50 system
-    return {"workload": f"porous cube {n_axis}^3 lattice minus 64 spheres: {n} points, "
-                        f"{int(pc['bflag'].sum())} on a boundary, degree 3, k = 40 / 80, FP32 + refinement",
-            "targets": n, "porosity": float(pc["porosity"]), "step_ms": step_ms, "targets_per_s": n / step_ms * 1e3,
-            "stage_ms": {"neighbours": float(med[0]), "scalar_stencils": float(med[1]),
-                         "divfree_stencils": float(med[2]), "csr": float(med[3])},
-            "divfree_targets_per_s": n / float(med[2]) * 1e3,
-            "divfree_qr_tflops": qr_flops * n / float(med[2]) / 1e9,
-            "fp64_redo": {"scalar": int(np.sum((st_sc & gmls.T_FP64_FALLBACK) != 0)),
-                          "divfree": int(np.sum((st_df & gmls.T_FP64_FALLBACK) != 0))},
-            "tune_ms": tune, "l2": "flushed before each timed step (256 MB write)",
-            "stokes_system": stokes_out}, gpu_sample
-
-
-def porous_oracle_errors(gs):
-    """CPU-baseline leg of the porous section: the oracle's kNN lists and
-    stencils on the sampled targets against the GPU's."""
-    import oracle
-
-    x, sample = gs["x"], gs["sample"]
-    errs, lists_equal = {}, True
-    for key, k, kind, idx, wg in gs["ops"]:
-        oi, oe = oracle.knn(x, sample, k, EPS_FACTOR, method="grid")
-        lists_equal &= bool(np.array_equal(idx, oi))
-        off = np.arange(0, len(sample) * k + 1, k)
-        extra = dict(bflag=gs["bflag"][sample], normals=gs["normals"].T[sample]) if kind == "scalar" else {}
-        wo, _, _ = oracle.stencils(x, sample, off, oi.reshape(-1), oe, kind, 3, key, **extra)
-        w = wg.reshape(wo.shape)
-        a = np.abs(w - wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
-        b = np.abs(wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
-        errs[key] = float(np.max(a / np.where(b > 0, b, 1.0)))
-    return {"sample": f"{len(sample)} targets, half drawn from the boundary, half from the interior",
-            "neighbour_lists_equal_oracle": lists_equal, "max_rel_err_vs_oracle": errs}
 
 
 BASIS_SIZE = {(2, 2): 6, (2, 3): 10, (2, 4): 15, (3, 2): 10, (3, 3): 20, (3, 4): 35}
@@ -1063,99 +1246,130 @@ def serving(n_requests, seed=0):
             "note": "bounded sample of the serving stream (first requests of the seeded Poisson sequence)"}
 
 
-def oracle_pipeline(x, targets, threads=None):
-    """The oracle as it stands on the same workload (a sample of targets)."""
+def stokes2d_oracle_check(ctx, n_sample=2000):
+    """The 2D section's GPU weights (FP32 + refinement) on a seeded sample of
+    targets against the oracle's, with the oracle's neighbour lists."""
+    import torch
+
     import oracle
-
-    n = x.shape[1]
-    i36, e36 = oracle.knn(x, targets, K_SCALAR, EPS_FACTOR, method="grid")
-    i48, e48 = oracle.knn(x, targets, K_DIVFREE, EPS_FACTOR, method="grid")
-    nt = len(targets)
-    off36 = np.arange(0, nt * K_SCALAR + 1, K_SCALAR)
-    off48 = np.arange(0, nt * K_DIVFREE + 1, K_DIVFREE)
-    wg, _, _ = oracle.stencils(x, targets, off36, i36.reshape(-1), e36, "scalar", DEGREE, "grad")
-    wd, _, _ = oracle.stencils(x, targets, off36, i36.reshape(-1), e36, "scalar", DEGREE, "div")
-    wv, _, _ = oracle.stencils(x, targets, off48, i48.reshape(-1), e48, "divfree", DEGREE, "vec_laplacian")
-    oracle.csr(off36, i36.reshape(-1), wg, n)
-    oracle.csr(off36, i36.reshape(-1), wd, n)
-    oracle.csr(off48, i48.reshape(-1), wv, n)
-    return {"grad": wg, "div": wd, "vl": wv, "idx36": i36, "idx48": i48}
-
-
-def cpu_baseline(ctx=None, sample_stride=1):
-    """Time the oracle on the host cores; with a GPU context also report the
-    GPU path's error against it on a sample of targets."""
-    import oracle
+    from paper_2104_14447_gb300 import gmls, inputs
 
     oracle.build()
     x = workload_points()
     n = x.shape[1]
-    targets = np.arange(0, n, sample_stride, dtype=np.int32)
-    t0 = time.perf_counter()
-    res = oracle_pipeline(x, targets)
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    out = {"value": len(targets) / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
-           "sample": f"{len(targets)} of {n} targets (every {sample_stride}th), full pipeline incl. kNN and CSR",
-           "seconds": dt}
-    if ctx is not None:
-        out["max_rel_err_vs_oracle"] = gpu_error(ctx, x, res, targets)
-    return out
-
-
-def gpu_error(ctx, x, res, targets):
-    """max over sampled (target, row) of |w_gpu - w_oracle|_inf / |w_oracle|_inf."""
-    import torch
-
-    from paper_2104_14447_gb300 import gmls
-
-    n = x.shape[1]
-    samp = np.arange(len(targets))  # every target the oracle computed
-    errs = {}
-    cid = ctx.cloud(torch.from_numpy(x).to(ctx.device))
-    for key, k, basis, fn in (("grad", K_SCALAR, gmls.SCALAR, gmls.GRAD), ("div", K_SCALAR, gmls.SCALAR, gmls.DIV),
-                              ("vl", K_DIVFREE, gmls.DIVFREE, gmls.VEC_LAPLACIAN)):
+    sample = np.unique((inputs.uniform(9, 5, n_sample) * n).astype(np.int64)).astype(np.int32)
+    sdev = torch.from_numpy(sample.astype(np.int64)).to(ctx.device)
+    cid = ctx.cloud(x)
+    errs, lists_equal = {}, True
+    for key, k, basis, fn, kind in (("grad", K_SCALAR, gmls.SCALAR, gmls.GRAD, "scalar"),
+                                    ("div", K_SCALAR, gmls.SCALAR, gmls.DIV, "scalar"),
+                                    ("vec_laplacian", K_DIVFREE, gmls.DIVFREE, gmls.VEC_LAPLACIAN, "divfree")):
         nid = ctx.neighbors(cid, k, EPS_FACTOR)
         sid = ctx.stencils(nid, basis, DEGREE, [fn], precision=gmls.FP32_REFINE)
         _, rows, nc, _ = ctx.stencil_info(sid, fn)
-        wg = ctx.weights(sid, fn).cpu().numpy().reshape(n, rows, k, nc)[targets[samp]]
-        wo = res[key][samp]
-        a = np.abs(wg - wo).reshape(len(samp), rows, -1).max(axis=2)
-        b = np.abs(wo).reshape(len(samp), rows, -1).max(axis=2)
+        wg = ctx.weights(sid, fn).view(n, rows, k, nc)[sdev].cpu().numpy()
+        idx = ctx.export(nid, gmls.X_NBR_INDEX, torch.int32).view(n, k)[sdev].cpu().numpy()
+        oi, oe = oracle.knn(x, sample, k, EPS_FACTOR, method="grid")
+        lists_equal &= bool(np.array_equal(idx, oi))
+        off = np.arange(0, len(sample) * k + 1, k)
+        wo, _, _ = oracle.stencils(x, sample, off, oi.reshape(-1), oe, kind, DEGREE, key)
+        a = np.abs(wg.reshape(wo.shape) - wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
+        b = np.abs(wo).reshape(len(sample), wo.shape[1], -1).max(axis=2)
         errs[key] = float(np.max(a / np.where(b > 0, b, 1.0)))
         ctx.release(sid)
         ctx.release(nid)
     ctx.release(cid)
-    return errs
+    return {"sample": f"{len(sample)} seeded targets", "neighbour_lists_equal": lists_equal,
+            "max_rel_err_vs_oracle": errs}
+
+
+def small_2d(ctx, steps=20):
+    """The 1,024-target case: 32 x 32 jittered grid in the unit square (seed
+    0), 12 nearest neighbours, eps = 1.5 d_12, degree-2 scalar basis,
+    Laplacian and gradient, plain FP64 on one stream; launch- and
+    latency-bound (1,024 targets cannot fill the GPU)."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    x = torch.from_numpy(inputs.jittered_grid(2, 32, seed=0)).to(ctx.device)
+    n = x.shape[1]
+
+    def step():
+        cid = ctx.cloud(x)
+        nid = ctx.neighbors(cid, 12, EPS_FACTOR)
+        sid = ctx.stencils(nid, gmls.SCALAR, 2, [gmls.LAPLACIAN, gmls.GRAD], precision=gmls.FP64)
+        csr = [ctx.assemble_csr(sid, gmls.LAPLACIAN), ctx.assemble_csr(sid, gmls.GRAD)]
+        return (cid, nid, sid), csr
+
+    for _ in range(3):
+        h, _ = step()
+        for hd in reversed(h):
+            ctx.release(hd)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        h, _ = step()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        for hd in reversed(h):
+            ctx.release(hd)
+    med = float(np.median(ms))
+    return {"workload": "2D 32x32 jittered grid, 12 nbrs, scalar m=2, Laplacian + gradient, FP64, one stream",
+            "targets": n, "ms_per_step": med, "targets_per_s": n / med * 1e3,
+            "roofline": "not meaningful: launch- and latency-bound"}
 
 
 # --------------------------------------------------------- reference arm
 def run_reference(args):
-    """The oracle, as it stands, on the host cores (this workload's CPU program)."""
+    """The oracle, as it stands, on the host cores: the headline workload (the
+    porous cube), each step a seeded 1 % sample of its targets through the
+    whole pipeline (kNN lists, scalar and div-free stencils, CSR)."""
     import oracle
+    from paper_2104_14447_gb300 import inputs
 
     oracle.build()
-    x = workload_points()
+    pc = inputs.porous_cube(n_axis=args.porous_n_axis)
+    x = pc["x"]
     n = x.shape[1]
-    stride = args.ref_stride
-    targets = np.arange(0, n, stride, dtype=np.int32)
+    m = max(1, int(round(0.01 * n)))
+    targets = np.unique((inputs.uniform(7, 133, m) * n).astype(np.int64)).astype(np.int32)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+
+    def run():
+        ns = len(targets)
+        i80, e80 = oracle.knn(x, targets, P_K_DIVFREE, EPS_FACTOR, method="grid")
+        i40, e40 = oracle.knn(x, targets, P_K_SCALAR, EPS_FACTOR, method="grid")
+        off40, off80 = np.arange(0, ns * P_K_SCALAR + 1, P_K_SCALAR), np.arange(0, ns * P_K_DIVFREE + 1, P_K_DIVFREE)
+        extra = dict(bflag=pc["bflag"][targets], normals=pc["normals"].T[targets])
+        for kind, key, i, o, e, ex in (("scalar", "grad", i40, off40, e40, extra),
+                                        ("scalar", "laplacian", i40, off40, e40, extra),
+                                        ("divfree", "vec_laplacian", i80, off80, e80, {})):
+            w, _, _ = oracle.stencils(x, targets, o, i.reshape(-1), e, kind, P_DEGREE, key, **ex)
+            oracle.csr(o, i.reshape(-1), w, n)
+
     for _ in range(args.warmup):
-        oracle_pipeline(x, targets)
+        run()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_pipeline(x, targets)
+        run()
         times.append(time.perf_counter() - t0)
     total = float(np.sum(times))
     value = len(targets) * args.steps / total
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"{len(targets)} of {n} targets per step (every {stride}th), full pipeline incl. kNN and CSR"
+    sample = (f"seeded 1 % of the targets per step ({len(targets)} of {n}), full pipeline incl. kNN and CSR; "
+              "the rate extrapolates linearly to the whole workload")
     return {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "targets_per_gpu": n, "precision": "fp64 (oracle)",
-                       "degree": DEGREE, "neighbours": [K_SCALAR, K_DIVFREE], "eps_factor": EPS_FACTOR},
-            "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle", "sample": sample},
+                       "degree": P_DEGREE, "neighbours": [P_K_SCALAR, P_K_DIVFREE], "eps_factor": EPS_FACTOR},
+            "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -1165,23 +1379,21 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32_refine", "fp64"], default="fp32_refine")
-    ap.add_argument("--arena-gb", type=int, default=24)
-    ap.add_argument("--ref-stride", type=int, default=4)
+    ap.add_argument("--arena-gb", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-stokes", action="store_true", help="skip the Stokes-system section")
-    ap.add_argument("--no-porous", action="store_true", help="skip the 3D porous-medium section")
-    ap.add_argument("--porous-n-axis", type=int, default=128, help="lattice of the porous section (profiling)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement of the headline")
+    ap.add_argument("--no-secondary", action="store_true", help="headline only")
+    ap.add_argument("--no-stokes", action="store_true", help="skip the Stokes-system sections")
+    ap.add_argument("--porous-n-axis", type=int, default=P_N_AXIS, help="lattice of the headline (profiling only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the uneven-batch section")
     ap.add_argument("--no-shapes", action="store_true", help="skip the per-shape FP32 / FP64 section")
-    ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipeline")
-    ap.add_argument("--e2e-fractions", default=None, help="relative sizes of the end-to-end ranges, e.g. 4,3,2,1")
-    ap.add_argument("--e2e-copy-streams", type=int, default=2, help="copy streams of the end-to-end pipeline")
+    ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipelines")
+    ap.add_argument("--e2e-copy-streams", type=int, default=2, help="copy streams of the end-to-end pipelines")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
-    ap.add_argument("--only", choices=["porous", "batched"], default=None,
-                    help="profiling: run only this section (--steps timed steps) and print it")
-    ap.add_argument("--n-axis", type=int, default=512, help="profiling only; the benchmark is 512")
-    ap.add_argument("--serve-requests", type=int, default=60, help="serving sample size (0: skip)")
+    ap.add_argument("--only", choices=["batched", "stokes2d"], default=None,
+                    help="profiling: run only this secondary section (--steps timed steps) and print it")
+    ap.add_argument("--n-axis", type=int, default=512, help="2D section grid (profiling only; the benchmark is 512)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="serving stream length (0: skip)")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     args = ap.parse_args()
     set_n_axis(args.n_axis)
@@ -1198,8 +1410,8 @@ def main():
 
         build.build()
         ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
-        if args.only == "porous":
-            res = porous_3d(ctx, n_axis=args.porous_n_axis, steps=args.steps, stokes=False)[0]
+        if args.only == "stokes2d":
+            res = stokes2d_section(ctx, args)
         else:
             res = batched_uneven(ctx, n_per_dim=args.batched_n, steps=args.steps)[0]
         print(json.dumps(res), flush=True)
@@ -1210,25 +1422,31 @@ def main():
 
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    out, ctx = run_ours(args, rank, world, local_rank)
+    out, ctx, gs = run_headline(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(ctx)
-    if rank == 0 and world == 1 and not args.no_stokes:
-        out["stokes_system"] = stokes_system(ctx)
-        out["stokes_system"]["solve"] = stokes_solve(ctx)
-        out["stokes_system"]["solve_256"] = stokes_solve(ctx, 256, full=False)
-    if rank == 0 and world == 1 and not args.no_porous:
-        out["porous_3d"], gs = porous_3d(ctx, n_axis=args.porous_n_axis)
-        if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
-            out["porous_3d"]["oracle_check"] = porous_oracle_errors(gs)
-    if rank == 0 and world == 1 and not args.no_shapes:
-        out["shapes"] = shapes(ctx)
-    if rank == 0 and world == 1 and not args.no_batched:
-        out["batched_uneven"], gsb = batched_uneven(ctx, n_per_dim=args.batched_n)
-        if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
-            out["batched_uneven"]["oracle_check"] = batched_oracle_errors(gsb)
-    if rank == 0 and world == 1 and args.serve_requests > 0:
-        out["serving"] = serving(args.serve_requests)
+        out["cpu_baseline"] = porous_cpu_baseline(gs)
+    pc = gs["pc"]
+    del gs
+    if rank == 0 and world == 1 and not args.no_secondary:
+        if not args.no_stokes:
+            out["porous_stokes_system"] = porous_stokes_section(ctx, pc)
+        sec = {"fp32_refine": stokes2d_section(ctx, args), "fp64": stokes2d_section(ctx, args, "fp64")}
+        if not args.no_cpu_baseline:
+            sec["oracle_check"] = stokes2d_oracle_check(ctx)
+        if not args.no_stokes:
+            sec["stokes_system"] = stokes_system(ctx)
+            sec["stokes_system"]["solve"] = stokes_solve(ctx)
+            sec["stokes_system"]["solve_256"] = stokes_solve(ctx, 256, full=False)
+        out["stokes2d_512"] = sec
+        out["small_2d_1024"] = small_2d(ctx)
+        if not args.no_shapes:
+            out["shapes"] = shapes(ctx)
+        if not args.no_batched:
+            out["batched_uneven"], gsb = batched_uneven(ctx, n_per_dim=args.batched_n)
+            if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
+                out["batched_uneven"]["oracle_check"] = batched_oracle_errors(gsb)
+        if args.serve_requests > 0:
+            out["serving"] = serving(args.serve_requests)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

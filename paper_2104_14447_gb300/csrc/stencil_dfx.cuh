@@ -169,8 +169,8 @@ struct DfxLay {
   static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * Q);     // float [N0][Q] stage-2 reflectors
   static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * Q);     // float [N]
   static constexpr size_t TAUA = al16(TAUG + sizeof(float) * N);        // float [Q]
-  static constexpr size_t SW = al16(TAUA + sizeof(float) * Q);          // ff [KS] sqrt(W)
-  static constexpr size_t IEPS = al16(SW + sizeof(ff) * KS);            // ff 1 / eps
+  static constexpr size_t F = al16(TAUA + sizeof(float) * Q);           // float [LC][KS] residual f
+  static constexpr size_t IEPS = al16(F + sizeof(float) * LC * KS);     // ff 1 / eps
   static constexpr size_t BYTES = al16(IEPS + sizeof(ff));
   static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(ff) * LC * LDA, "R_A must fit in the s slot");
 };
@@ -191,22 +191,25 @@ __device__ __forceinline__ float dfx_get_slot(const float (&x)[S], int sl) {
   return v;
 }
 
-// z <- Q_A^T z (REV false) or Q_A z (REV true) for V row-distributed vectors
+// z <- Q_A^T z (rev false) or Q_A z (rev true) for V row-distributed vectors
 // (row lane + 32 t in z[q][t]); reflector k is column k of the register tile
 // below the diagonal (v_k[k] = 1).  The V dot products of a reflector are
-// all-reduced together (recursive halving).
-template <int MR, int Q, int V, bool REV>
+// all-reduced together (recursive halving).  One copy of the code serves both
+// directions: step s takes column s or Q - 1 - s by a select (the kernel is
+// large enough for instruction fetch to matter).
+template <int MR, int Q, int V>
 __device__ __forceinline__ void dfx_apply_qa(const float (&a)[MR][Q], const float* tau, float (&z)[V][MR], int lane,
-                                             unsigned mask) {
+                                             unsigned mask, bool rev) {
 #pragma unroll
   for (int s = 0; s < Q; ++s) {
-    const int k = REV ? Q - 1 - s : s;
+    const int k = rev ? Q - 1 - s : s;
     const float tk = tau[k];
     float v[MR];
 #pragma unroll
     for (int i = 0; i < MR; ++i) {
       const int r = lane + 32 * i;
-      v[i] = (r > k) ? a[i][k] : (r == k ? 1.0f : 0.0f);
+      const float ak = rev ? a[i][Q - 1 - s] : a[i][s];
+      v[i] = (r > k) ? ak : (r == k ? 1.0f : 0.0f);
     }
     float d[V];
 #pragma unroll
@@ -221,6 +224,34 @@ __device__ __forceinline__ void dfx_apply_qa(const float (&a)[MR][Q], const floa
       const float dq = d[q] * tk;
 #pragma unroll
       for (int i = 0; i < MR; ++i) z[q][i] = fmaf(-dq, v[i], z[q][i]);
+    }
+  }
+}
+
+// Triangular solves with the packed rows of R in shared memory (R(i, p) at
+// rpk<N>(i, p)), right-hand sides in the solve layout (entry p at lane p % 32,
+// slot p / 32), loops over the pivot rolled: w <- R^-T w (TRANS) or R^-1 w.
+template <int N, int L, int NT, bool TRANS>
+__device__ __forceinline__ void dfx_solve(const float* Rs, const float* idg, float (&w)[L][NT], int lane,
+                                          unsigned mask) {
+#pragma unroll 1
+  for (int s = 0; s < N; ++s) {
+    const int i = TRANS ? s : N - 1 - s;
+    const float inv = idg[i];
+    const int src = i & 31, sl = i >> 5;
+    float yi[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) yi[l] = __shfl_sync(mask, dfx_get_slot<NT>(w[l], sl), src) * inv;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int p = lane + 32 * t;
+      const bool upd = TRANS ? (p > i && p < N) : (p < i);
+      const float r = upd ? Rs[TRANS ? rpk<N>(i, p) : rpk<N>(p, i)] : 0.0f;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if (p == i) w[l][t] = yi[l];
+        w[l][t] = fmaf(-r, yi[l], w[l][t]);
+      }
     }
   }
 }
@@ -268,6 +299,26 @@ __device__ __forceinline__ void dfx_apply_qg(float (&zt)[L][TS], float (&zb)[L],
     for (int j2 = N0 - 1; j2 >= 0; --j2) stage2(j2);
 #pragma unroll 1
     for (int jst = NTOP - 1; jst >= 0; --jst) stage1(jst);
+  }
+}
+
+// v[0..Q) = row[0..Q): 16-byte loads when Q is a multiple of 4 (rows of a
+// [.][Q] float array at a 16-byte aligned base)
+template <int Q>
+__device__ __forceinline__ void dfx_load_row(const float* row, float (&v)[Q]) {
+  if constexpr (Q % 4 == 0) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int i = 0; i < Q / 4; ++i) {
+      const float4 t = r4[i];
+      v[4 * i] = t.x;
+      v[4 * i + 1] = t.y;
+      v[4 * i + 2] = t.z;
+      v[4 * i + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = row[i];
   }
 }
 
@@ -319,7 +370,8 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
   float* V2 = reinterpret_cast<float*>(base + Lay::V2);
   float* TAUG = reinterpret_cast<float*>(base + Lay::TAUG);
   float* TAUA = reinterpret_cast<float*>(base + Lay::TAUA);
-  ff* SWs = reinterpret_cast<ff*>(base + Lay::SW);
+  // sqrt(W_j) = A[j][0]: the first monomial is the constant
+  float* Fs = reinterpret_cast<float*>(base + Lay::F);
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
   const float tolf = (float)j.tol;
@@ -363,39 +415,33 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
 #pragma unroll
     for (int c = 0; c < D; ++c) xt[c] = j.x[c * n + t];
     const int half_p = j.wpow_half;
+#pragma unroll 1
+    for (int q = lane; q < k; q += 32) {
+      const int32_t jj = j.idx[o0 + q];
+      ff dx[3], xi[3];
+      ff r2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        dx[c] = diff_ff(j.x[c * n + jj], xt[c]);
+        xi[c] = dx[c] * inv_eps;
+        r2 = r2 + dx[c] * dx[c];
+      }
+      const ff u = ff(1.f, 0.f) - sqrt_ff(r2) * inv_eps;
+      ff sw(0.f, 0.f);
+      if (u.h > 0.0f) {
+        sw = u;
+        for (int pp = 1; pp < half_p; ++pp) sw = sw * u;
+      }
+      gmls_gen::BasisEval<GMLS_BASIS_SCALAR, D, M>::template run<ff>(xi, Aff + q, LDA, sw);
+    }
+    __syncwarp(mask);
     float a[MRA][Q];
 #pragma unroll
     for (int tt = 0; tt < MRA; ++tt) {
       const int q = lane + 32 * tt;
-      ff p[Q];
-      if (q < k) {
-        const int32_t jj = j.idx[o0 + q];
-        ff dx[3], xi[3];
-        ff r2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          dx[c] = diff_ff(j.x[c * n + jj], xt[c]);
-          xi[c] = dx[c] * inv_eps;
-          r2 = r2 + dx[c] * dx[c];
-        }
-        const ff u = ff(1.f, 0.f) - sqrt_ff(r2) * inv_eps;
-        ff sw(0.f, 0.f);
-        if (u.h > 0.0f) {
-          sw = u;
-          for (int pp = 1; pp < half_p; ++pp) sw = sw * u;
-        }
-        gmls_gen::BasisEval<GMLS_BASIS_SCALAR, D, M>::template run<ff>(xi, p, 1, sw);
-#pragma unroll
-        for (int g = 0; g < Q; ++g) Aff[g * LDA + q] = p[g];
-        SWs[q] = sw;
-      } else {
-#pragma unroll
-        for (int g = 0; g < Q; ++g) p[g] = ff(0.f, 0.f);
-      }
-#pragma unroll
-      for (int g = 0; g < Q; ++g) a[tt][g] = p[g].h;
+      for (int g = 0; g < Q; ++g) a[tt][g] = q < k ? Aff[g * LDA + q].h : 0.0f;
     }
-    __syncwarp(mask);
 
     // ---- 2. A = Q_A R_A in registers; R_A row r (lane r) packed into RA
     qr_columns<32, MRA, Q>(a, TAUA, lane, mask, std::make_integer_sequence<int, Q>{});
@@ -437,8 +483,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       __syncwarp(mask);
       const float tk = TAUG[jst];
       float v[Q];
-#pragma unroll
-      for (int r = 0; r < Q; ++r) v[r] = V1[jst * Q + r];
+      dfx_load_row<Q>(V1 + jst * Q, v);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const int col = lane + 32 * s;
@@ -481,8 +526,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       __syncwarp(mask);
       const float tk = TAUG[colk];
       float v[Q];
-#pragma unroll
-      for (int r = 0; r < Q; ++r) v[r] = V2[j2 * Q + r];
+      dfx_load_row<Q>(V2 + j2 * Q, v);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const int col = lane + 32 * s;
@@ -525,7 +569,6 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       const int c = tab.lam[l][i];
       return c == 0 ? ff(0.f, 0.f) : mul_f(ie2, (float)c);
     };
-    float f[LC][MRA];
     bool conv = false;
     int used = 0;
     float prev = 0.0f;
@@ -552,41 +595,41 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
           UV[e] = uv;
         }
         __syncwarp(mask);
-        // f = B y - s: row (l, c, j) = A_j . u_(l,c) - s_(l,c,j)
+        // f = B y - s: row (l, c, j) = A_j . u_(l,c) - s_(l,c,j), into F;
+        // HG (l, c) chains at a time
+        constexpr int HG = LC % 3 == 0 ? 3 : 2;
+        static_assert(LC % HG == 0, "(l, c) pairs in groups");
+        for (int q = lane; q < k; q += 32) {
+          ff ar[Q];
 #pragma unroll
-        for (int tt = 0; tt < MRA; ++tt) {
-          const int q = lane + 32 * tt;
-          if (q < k) {
-            ff ar[Q];
+          for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
+#pragma unroll 1
+          for (int lc = 0; lc < LC; lc += HG) {
+            Dot2 acc[HG];
 #pragma unroll
-            for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
+            for (int h = 0; h < HG; ++h) acc[h].init(-Ss[(lc + h) * LDA + q]);
 #pragma unroll
-            for (int lc = 0; lc < LC; ++lc) {
-              Dot2 acc;
-              acc.init(-Ss[lc * LDA + q]);
+            for (int g = 0; g < Q; ++g)
 #pragma unroll
-              for (int g = 0; g < Q; ++g) acc.add_prod(ar[g], UV[lc * Q + g]);
-              f[lc][tt] = __fadd_rn(acc.h, acc.l);
-            }
-          } else {
+              for (int h = 0; h < HG; ++h) acc[h].add_prod(ar[g], UV[(lc + h) * Q + g]);
 #pragma unroll
-            for (int lc = 0; lc < LC; ++lc) f[lc][tt] = 0.0f;
+            for (int h = 0; h < HG; ++h) Fs[(lc + h) * KS + q] = __fadd_rn(acc[h].h, acc[h].l);
           }
         }
         __syncwarp(mask);
-        // v = (I (x) A^T) s, two interleaved compensated chains per entry
+        // v = (I (x) A^T) s, four interleaved compensated chains per entry
         for (int e = lane; e < LC * Q; e += 32) {
           const int lc = e / Q, g = e - lc * Q;
           const ff* ag = Aff + g * LDA;
           const ff* sl = Ss + lc * LDA;
-          Dot2 c0, c1;
+          Dot2 c[4];
           int q = 0;
-          for (; q + 1 < k; q += 2) {
-            c0.add_prod(ag[q], sl[q]);
-            c1.add_prod(ag[q + 1], sl[q + 1]);
+          for (; q + 3 < k; q += 4) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) c[h].add_prod(ag[q + h], sl[q + h]);
           }
-          if (q < k) c0.add_prod(ag[q], sl[q]);
-          UV[e] = c0.value() + c1.value();
+          for (; q < k; ++q) c[0].add_prod(ag[q], sl[q]);
+          UV[e] = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
         }
         __syncwarp(mask);
         // g = lambda - C^T v in the solve layout
@@ -614,8 +657,11 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
 #pragma unroll
         for (int lc = 0; lc < LC; ++lc)
 #pragma unroll
-          for (int tt = 0; tt < MRA; ++tt) z[lc][tt] = f[lc][tt];
-        dfx_apply_qa<MRA, Q, LC, false>(a, TAUA, z, lane, mask);
+          for (int tt = 0; tt < MRA; ++tt) {
+            const int q = lane + 32 * tt;
+            z[lc][tt] = q < k ? Fs[lc * KS + q] : 0.0f;
+          }
+        dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, false);
         float zt[L][TS], zb[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) {
@@ -652,7 +698,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
             d1[l][s] = 0.0f;
           }
       }
-      solve_rt_lanes<32, N, L>(RG, IDG, w, lane, mask);  // a = R^-T g
+      dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);  // a = R^-T g
       float dyv[L][NT];
 #pragma unroll
       for (int l = 0; l < L; ++l)
@@ -661,7 +707,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
           dyv[l][s] = w[l][s] - d1[l][s];  // delta
           w[l][s] = dyv[l][s];
         }
-      solve_r_lanes<32, N, L>(RG, IDG, dyv, lane, mask);  // dy = R^-1 delta
+      dfx_solve<N, L, NT, false>(RG, IDG, dyv, lane, mask);  // dy = R^-1 delta
       // ds = f + Q_B [delta; 0]: Q_G in the row space of G, then Q_A per (l, c)
       float zt[L][TS], zb[L];
 #pragma unroll
@@ -694,7 +740,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
 #pragma unroll
           for (int tt = 1; tt < MRA; ++tt) z[l * D + c][tt] = 0.0f;
       }
-      dfx_apply_qa<MRA, Q, LC, true>(a, TAUA, z, lane, mask);
+      dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, true);
       // s += ds, y += dy; the size of the correction for the stopping rule
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
@@ -703,7 +749,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
         for (int tt = 0; tt < MRA; ++tt) {
           const int q = lane + 32 * tt;
           if (q < k) {
-            const float ds = itr > 0 ? z[lc][tt] + f[lc][tt] : z[lc][tt];
+            const float ds = itr > 0 ? z[lc][tt] + Fs[lc * KS + q] : z[lc][tt];
             const ff s1 = itr > 0 ? add_f(Ss[lc * LDA + q], ds) : ff(ds, 0.0f);
             Ss[lc * LDA + q] = s1;
             dmax = fmaxf(dmax, fabsf(ds));
@@ -749,7 +795,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
           double val = 0.0;
           if (src >= 0) {
             const int q = e / C, c = e - q * C;
-            const ff s = Ss[((src + rr) * D + c) * LDA + q] * SWs[q];
+            const ff s = Ss[((src + rr) * D + c) * LDA + q] * Aff[q];
             val = to_double(ff(sgn * s.h, sgn * s.l));
           }
           wo[(int64_t)rr * per_row + e] = val;

@@ -17,7 +17,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = os.path.join(ROOT, "paper_2104_14447_gb300")
 
-ORACLE_LEGS = {"porous_oracle_errors", "batched_oracle_errors", "oracle_pipeline", "cpu_baseline", "run_reference"}
+ORACLE_LEGS = {"porous_cpu_baseline", "batched_oracle_errors", "stokes2d_oracle_check", "run_reference"}
 
 
 def _oracle_imports(tree):
