@@ -60,9 +60,11 @@ typedef int32_t gmls_status;
 #define GMLS_EINVAL (-1)    /* bad argument or unsupported (d, m, basis)      */
 #define GMLS_ENOMEM (-2)    /* the arena cannot hold the request             */
 #define GMLS_ECUDA (-3)     /* a CUDA call failed (message in last_error)    */
-#define GMLS_ETIMEOUT (-4)  /* a bounded device wait gave up                 */
+#define GMLS_ETIMEOUT (-4)  /* reserved: no call returns it (no kernel of this
+                               library waits on a device flag or a peer)   */
 #define GMLS_EBUSY (-5)     /* handle still in use                           */
 #define GMLS_ENOTFOUND (-6) /* unknown handle                                */
+#define GMLS_ECANCELED (-7) /* the server request was cancelled before it ran */
 
 /* per-target status bits (uint8 per target) */
 #define GMLS_T_OK 0
@@ -303,7 +305,9 @@ gmls_status gmls_csr_spmv(gmls_ctx* ctx, int64_t n_rows, const int64_t* row_ptr,
 
 /*
  * Solve A x = b (square CSR, n rows; FP64) by restarted GMRES(restart) with
- * right Jacobi preconditioning (diag A; 1 where it is zero or absent), on
+ * right Jacobi preconditioning (diag A: the sum of the row's entries in
+ * column r when the column appears more than once, as A x adds them; 1 where
+ * it is zero or absent), on
  * the row-equilibrated system when params->row_scaling = 1 -- the global
  * solve of the collocation system of Sec. 3.2 (the paper uses a
  * block-preconditioned Krylov method).  x: device buffer holding the initial
@@ -379,6 +383,10 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
                                     global memory); 0 (default) no forcing.  gmls_stencils
                                     fails with GMLS_EINVAL where the variant does not exist
                                     or does not fit for the shape                            */
+#define GMLS_OPT_FAIL_ALLOC 5    /* testing: n >= 1 makes the n-th next sub-allocation from
+                                    the context's arena fail as if the arena were full (the
+                                    call that makes it returns GMLS_ENOMEM and releases what
+                                    it had taken); 0 (default) disarms                        */
 #define GMLS_OPT_POISON 4        /* testing: 1 = gmls_stencils first fills the arrays it
                                     returns (weights, beta, status, iteration counts) with
                                     all-ones bytes (NaN weights), so that an entry no kernel
@@ -487,6 +495,12 @@ gmls_status gmls_server_wait(gmls_server* s, int64_t ticket, int32_t timeout_ms,
    dst (host or device, `bytes` capacity); dst NULL only reports *needed. */
 gmls_status gmls_server_result(gmls_server* s, int64_t ticket, int32_t what, int32_t functional, void* dst,
                                size_t bytes, size_t* needed);
+/* Cancel a request that waits for admission: GMLS_OK and it never runs
+   (wait then reports it done with GMLS_ECANCELED, result returns
+   GMLS_ECANCELED, release frees its record); GMLS_EBUSY once it has been
+   admitted or has finished; GMLS_ENOTFOUND for an unknown ticket.  The
+   paper has no counterpart (serving is not part of its method). */
+gmls_status gmls_server_cancel(gmls_server* s, int64_t ticket);
 /* Free a finished request's device memory (GMLS_EBUSY while it runs). */
 gmls_status gmls_server_release(gmls_server* s, int64_t ticket);
 gmls_status gmls_server_stats(gmls_server* s, gmls_serve_stats* out);

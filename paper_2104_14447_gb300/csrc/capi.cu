@@ -13,75 +13,16 @@
 
 #include "basis_tables.cuh"
 #include "gmls_internal.cuh"
+#include "host_alloc.h"
 
 using namespace gmls;
 
 namespace {
 
-// First-fit allocator over the caller's device buffer.  256-byte granularity;
-// neighbouring free blocks are merged on release.  Frees are stream ordered
-// with the context's single stream, so a block can be reused by later work on
-// that stream as soon as it is released.
-class Arena {
- public:
-  void init(void* base, size_t bytes) {
-    uintptr_t b = reinterpret_cast<uintptr_t>(base);
-    uintptr_t a = (b + 255) & ~uintptr_t(255);
-    base_ = reinterpret_cast<char*>(a);
-    cap_ = (bytes > (a - b)) ? ((bytes - (a - b)) & ~size_t(255)) : 0;
-    free_.clear();
-    live_.clear();
-    if (cap_) free_[0] = cap_;
-    used_ = peak_ = 0;
-  }
-  void* alloc(size_t bytes) {
-    if (bytes == 0) bytes = 256;
-    bytes = (bytes + 255) & ~size_t(255);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        size_t off = it->first, sz = it->second;
-        free_.erase(it);
-        if (sz > bytes) free_[off + bytes] = sz - bytes;
-        live_[off] = bytes;
-        used_ += bytes;
-        if (used_ > peak_) peak_ = used_;
-        return base_ + off;
-      }
-    }
-    return nullptr;
-  }
-  void release(void* p) {
-    if (!p) return;
-    size_t off = static_cast<char*>(p) - base_;
-    auto it = live_.find(off);
-    if (it == live_.end()) return;
-    size_t sz = it->second;
-    live_.erase(it);
-    used_ -= sz;
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && off + sz == nx->first) {
-      sz += nx->second;
-      free_.erase(nx);
-    }
-    auto pv = free_.lower_bound(off);
-    if (pv != free_.begin()) {
-      --pv;
-      if (pv->first + pv->second == off) {
-        pv->second += sz;
-        return;
-      }
-    }
-    free_[off] = sz;
-  }
-  size_t used() const { return used_; }
-  size_t peak() const { return peak_; }
-  size_t cap() const { return cap_; }
-
- private:
-  char* base_ = nullptr;
-  size_t cap_ = 0, used_ = 0, peak_ = 0;
-  std::map<size_t, size_t> free_, live_;
-};
+// First-fit allocator over the caller's device buffer (host_alloc.h).  Frees
+// are stream ordered with the context's single stream, so a block can be
+// reused by later work on that stream as soon as it is released.
+using Arena = gmls::host::FirstFit;
 
 enum Kind { K_CLOUD = 1, K_NBRS = 2, K_STENCIL = 3, K_GRAPH = 4 };
 
@@ -189,6 +130,12 @@ static gmls_status fail(gmls_ctx* c, gmls_status code, const std::string& msg) {
 }
 
 static gmls_status cuda_fail(gmls_ctx* c, cudaError_t e, const char* where) {
+  // the launch helpers report an arena sub-allocation that failed as
+  // cudaErrorMemoryAllocation (the library itself never calls cudaMalloc)
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, GMLS_ENOMEM, std::string(where) + ": arena exhausted");
+  }
   return fail(c, GMLS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -674,6 +621,10 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
   if (!ctx) return GMLS_EINVAL;
   switch (option) {
     case GMLS_OPT_FORCE_GENERIC: ctx->force_generic = value != 0; return GMLS_OK;
+    case GMLS_OPT_FAIL_ALLOC:
+      if (value < 0) return fail(ctx, GMLS_EINVAL, "gmls_set_option: GMLS_OPT_FAIL_ALLOC needs n >= 0");
+      ctx->arena.fail_after(value);
+      return GMLS_OK;
     case GMLS_OPT_AUTOTUNE: ctx->autotune = value != 0; return GMLS_OK;
     case GMLS_OPT_FORCE_VARIANT:
       if (value != 0 && value != -1 && value != -2 && value != -3 &&

@@ -118,17 +118,16 @@ __global__ void residual_kernel(int64_t n, const double* __restrict__ b, double*
     r[p] = b[p] - r[p];
 }
 
-// dinv[r] = 1 / A[r][r] (1 where the diagonal entry is absent or zero)
+// dinv[r] = 1 / A[r][r] (1 where the diagonal entry is absent or zero).  A
+// row may list column r more than once; as in A x, the entries add up, so
+// the diagonal is their sum (the same in both scalings).
 __global__ void inverse_diagonal_kernel(int64_t n, const int64_t* __restrict__ row_ptr,
                                         const int32_t* __restrict__ col, const double* __restrict__ val,
                                         double* __restrict__ dinv) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     double d = 0.0;
     for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p)
-      if (col[p] == (int32_t)r) {
-        d = val[p];
-        break;
-      }
+      if (col[p] == (int32_t)r) d += val[p];
     dinv[r] = (d != 0.0) ? 1.0 / d : 1.0;
   }
 }
@@ -143,7 +142,7 @@ __global__ void row_equilibration_kernel(int64_t n, const int64_t* __restrict__ 
     double amax = 0.0, d = 0.0;
     for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
       amax = fmax(amax, fabs(val[p]));
-      if (col[p] == (int32_t)r) d = val[p];
+      if (col[p] == (int32_t)r) d += val[p];
     }
     const double ri = amax > 0.0 ? 1.0 / amax : 1.0;
     const double ds = ri * d;

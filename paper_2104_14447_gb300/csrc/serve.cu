@@ -30,6 +30,7 @@
 
 #include "../../include/gmls.h"
 #include "basis_tables.cuh"
+#include "host_alloc.h"
 
 namespace gmls {
 void set_global_error(const std::string& msg);
@@ -40,53 +41,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// first-fit allocator over the server arena (256-byte granularity)
-class SliceAlloc {
- public:
-  void init(char* base, size_t cap) {
-    base_ = base;
-    free_.clear();
-    free_[0] = cap;
-  }
-  char* alloc(size_t bytes) {
-    bytes = (bytes + 255) & ~size_t(255);
-    for (auto it = free_.begin(); it != free_.end(); ++it)
-      if (it->second >= bytes) {
-        size_t off = it->first, sz = it->second;
-        free_.erase(it);
-        if (sz > bytes) free_[off + bytes] = sz - bytes;
-        live_[off] = bytes;
-        return base_ + off;
-      }
-    return nullptr;
-  }
-  void release(char* p) {
-    size_t off = p - base_;
-    auto it = live_.find(off);
-    if (it == live_.end()) return;
-    size_t sz = it->second;
-    live_.erase(it);
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && off + sz == nx->first) {
-      sz += nx->second;
-      free_.erase(nx);
-    }
-    auto pv = free_.lower_bound(off);
-    if (pv != free_.begin()) {
-      --pv;
-      if (pv->first + pv->second == off) {
-        pv->second += sz;
-        return;
-      }
-    }
-    free_[off] = sz;
-  }
- private:
-  char* base_ = nullptr;
-  std::map<size_t, size_t> free_, live_;
-};
-
-enum ReqState { PENDING = 0, RUNNING = 1, DONE = 2, FAILED = 3 };
+enum ReqState { PENDING = 0, RUNNING = 1, DONE = 2, FAILED = 3, CANCELLED = 4 };
 
 struct Request {
   int64_t ticket = 0;
@@ -133,13 +88,13 @@ struct gmls_server {
   int device = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
-  SliceAlloc slices;
+  gmls::host::FirstFit slices;  // first-fit slices of the server arena
   std::vector<cudaStream_t> streams;
   std::vector<int> stream_load;
   int max_inflight = 8;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<int64_t> pending;
+  gmls::host::AdmissionQueue pending;
   std::map<int64_t, Request> reqs;
   int64_t next_ticket = 1;
   int inflight = 0;
@@ -225,24 +180,20 @@ static void scheduler(gmls_server* s) {
     }
     // admissions: first pending requests that fit (a look-ahead of 8 lets
     // small requests pass one that waits for memory)
-    int looked = 0;
-    for (auto it = s->pending.begin(); it != s->pending.end() && s->inflight < s->max_inflight && looked < 8;) {
-      ++looked;
-      Request& r = s->reqs.at(*it);
+    const int admitted = s->pending.admit(8, [&](int64_t t) -> int {
+      if (s->inflight >= s->max_inflight) return -1;
+      Request& r = s->reqs.at(t);
       r.slice_bytes = estimate_bytes(r.req);
-      r.slice = s->slices.alloc(r.slice_bytes);
+      r.slice = static_cast<char*>(s->slices.alloc(r.slice_bytes));
       if (!r.slice) {
         if (r.slice_bytes > s->arena_bytes) {  // can never fit
           r.state = FAILED;
           r.error = GMLS_ENOMEM;
           r.message = "request needs more memory than the server arena";
           r.done_at = Clock::now();
-          it = s->pending.erase(it);
-          progress = true;
-          continue;
+          return 2;
         }
-        ++it;
-        continue;
+        return 0;
       }
       int best = 0;
       for (int i = 1; i < (int)s->streams.size(); ++i)
@@ -255,9 +206,9 @@ static void scheduler(gmls_server* s) {
         s->inflight--;
         s->stream_load[best]--;
       }
-      it = s->pending.erase(it);
-      progress = true;
-    }
+      return 1;
+    });
+    progress |= admitted > 0;
     if (!progress) s->cv.wait_for(lock, std::chrono::microseconds(50));
   }
 }
@@ -316,7 +267,7 @@ gmls_status gmls_server_submit(gmls_server* s, const gmls_request* q, int64_t* t
       s->have_first = true;
     }
     *ticket = r.ticket;
-    s->pending.push_back(r.ticket);
+    s->pending.push(r.ticket);
     s->reqs.emplace(r.ticket, std::move(r));
   }
   s->cv.notify_one();
@@ -331,9 +282,10 @@ gmls_status gmls_server_wait(gmls_server* s, int64_t ticket, int32_t timeout_ms,
       std::lock_guard<std::mutex> lock(s->mu);
       auto it = s->reqs.find(ticket);
       if (it == s->reqs.end()) return GMLS_ENOTFOUND;
-      if (it->second.state == DONE || it->second.state == FAILED) {
+      const ReqState st = it->second.state;
+      if (st == DONE || st == FAILED || st == CANCELLED) {
         *done = 1;
-        return it->second.state == DONE ? GMLS_OK : it->second.error;
+        return st == DONE ? GMLS_OK : st == CANCELLED ? GMLS_ECANCELED : it->second.error;
       }
     }
     if (Clock::now() >= until) {
@@ -351,7 +303,7 @@ gmls_status gmls_server_result(gmls_server* s, int64_t ticket, int32_t what, int
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return GMLS_ENOTFOUND;
   Request& r = it->second;
-  if (r.state != DONE) return r.state == FAILED ? r.error : GMLS_EBUSY;
+  if (r.state != DONE) return r.state == FAILED ? r.error : r.state == CANCELLED ? GMLS_ECANCELED : GMLS_EBUSY;
   const int64_t id = (what == GMLS_X_NBR_INDEX || what == GMLS_X_NBR_EPS || what == GMLS_X_NBR_OFFSETS ||
                       what == GMLS_X_NBR_STATUS)
                          ? r.nbrs
@@ -362,6 +314,22 @@ gmls_status gmls_server_result(gmls_server* s, int64_t ticket, int32_t what, int
   if (needed) *needed = need;
   if (!dst) return GMLS_OK;
   return gmls_export(r.ctx, id, what, functional, dst, bytes);
+}
+
+gmls_status gmls_server_cancel(gmls_server* s, int64_t ticket) {
+  if (!s) return GMLS_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return GMLS_ENOTFOUND;
+    Request& r = it->second;
+    if (r.state != PENDING || !s->pending.cancel(ticket)) return GMLS_EBUSY;  // admitted or finished
+    r.state = CANCELLED;
+    r.error = GMLS_ECANCELED;
+    r.done_at = Clock::now();
+  }
+  s->cv.notify_one();
+  return GMLS_OK;
 }
 
 gmls_status gmls_server_release(gmls_server* s, int64_t ticket) {

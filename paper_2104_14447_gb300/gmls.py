@@ -24,7 +24,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgmls.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
 T_OK, T_RANK_DEFICIENT, T_ILL_CONDITIONED, T_REFINE_NOT_CONVERGED = 0, 1, 2, 4
 T_TOO_FEW_NEIGHBOURS, T_FP64_FALLBACK, T_OVERFLOW = 8, 16, 32
 KNN, RADIUS = 0, 1
@@ -41,11 +41,11 @@ EXPORTED = [
     "gmls_sync", "gmls_arena_usage", "gmls_launch_count", "gmls_set_option", "gmls_knn_noalloc", "gmls_last_error",
     "gmls_version", "gmls_tune_info", "gmls_capture_begin", "gmls_capture_end", "gmls_graph_launch",
     "gmls_server_create", "gmls_server_submit", "gmls_server_wait", "gmls_server_result", "gmls_server_release",
-    "gmls_server_stats", "gmls_server_destroy", "gmls_stokes_size", "gmls_stokes_assemble", "gmls_stokes_rhs",
+    "gmls_server_cancel", "gmls_server_stats", "gmls_server_destroy", "gmls_stokes_size", "gmls_stokes_assemble", "gmls_stokes_rhs",
     "gmls_csr_spmv", "gmls_gmres",
 ]
 NOALLOC_MAX_POINTS = 262144
-OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT, OPT_POISON = 0, 1, 2, 3, 4
+OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT, OPT_POISON, OPT_FAIL_ALLOC = 0, 1, 2, 3, 4, 5
 T_UNSUPPORTED = 64
 
 
@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
         "gmls_server_wait": [vp, i64, i32, ctypes.POINTER(i32)],
         "gmls_server_result": [vp, i64, i32, i32, vp, sz, ctypes.POINTER(sz)],
         "gmls_server_release": [vp, i64],
+        "gmls_server_cancel": [vp, i64],
         "gmls_server_stats": [vp, ctypes.POINTER(ServerStats)],
         "gmls_server_destroy": [vp],
         "gmls_stokes_size": [vp, ctypes.POINTER(StokesParams), P64, P64],
@@ -435,6 +436,14 @@ class Server:
         if rc != OK:
             raise GmlsError(rc, f"result of request {ticket}")
         return out
+
+    def cancel(self, ticket: int) -> int:
+        """Cancel a request still waiting for admission: returns OK, or EBUSY
+        once it was admitted or finished (no exception: both are normal)."""
+        rc = self.lib.gmls_server_cancel(self.h, ticket)
+        if rc not in (OK, EBUSY):
+            raise GmlsError(rc, f"cancel of request {ticket}")
+        return rc
 
     def release(self, ticket: int):
         rc = self.lib.gmls_server_release(self.h, ticket)
