@@ -990,13 +990,13 @@ def batched_uneven(ctx, n_per_dim=500_000, steps=3, n_sample=32):
                                 k_per_target=kpt)
             hs_out.append([nid])
         rec(1)
-        for (c, cid, hs, kpt, deg), h in zip(prepared, hs_out):
+        for i, ((c, cid, hs, kpt, deg), h) in enumerate(zip(prepared, hs_out)):
             h.append(ctx.stencils(h[0], gmls.SCALAR, 0, [gmls.GRAD, gmls.LAPLACIAN], precision=prec,
                                   degree_per_target=deg))
-        rec(2)
+            rec(2 + i)  # one bucketed launch per cloud
         for h in hs_out:
             h.append(ctx.assemble_csr(h[1], gmls.GRAD))
-        rec(3)
+        rec(4)
         return hs_out
 
     def release(hs_out):
@@ -1014,26 +1014,40 @@ def batched_uneven(ctx, n_per_dim=500_000, steps=3, n_sample=32):
         for s in range(nsteps):
             with torch.cuda.stream(stream):
                 flush.fill_(s & 0xFF)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             torch.cuda.nvtx.range_push("batched_step")
             h = step(prec, ev)
             torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
-            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
+            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
             if not (prec == gmls.FP32_REFINE and s == nsteps - 1):
                 release(h)
         med = np.median(np.array(times), axis=0)
         res[name] = {"step_ms": float(np.sum(med)), "targets_per_s": 2 * n_per_dim / float(np.sum(med)) * 1e3,
-                     "stage_ms": {"neighbours": float(med[0]), "stencils": float(med[1]), "csr": float(med[2])}}
+                     "stage_ms": {"neighbours": float(med[0]), "stencils": float(med[1] + med[2]),
+                                  "stencils_2d": float(med[1]), "stencils_3d": float(med[2]), "csr": float(med[3])}}
         if prec == gmls.FP32_REFINE:
             keep = h
+            stencil_ms = (float(med[1]), float(med[2]))
     stats, gpu_sample = {}, []
+    classes = np.array([32, 64, 96, 128, 160, 192, 256, 384, 512, 768, 1024])  # the bucketing's row classes
+    flops_alg, flops_pad = [], []
     for (c, cid, hs, kpt, deg), h in zip(prepared, keep):
         d = c["dim"]
         off = ctx.export(h[0], gmls.X_NBR_OFFSETS, torch.int64).cpu().numpy()
         nst = ctx.export(h[0], gmls.X_NBR_STATUS, torch.uint8).cpu().numpy()
         st = ctx.export(h[1], gmls.X_STATUS, torch.uint8).cpu().numpy()
+        its = ctx.export(h[1], gmls.X_ITERS, torch.uint8).cpu().numpy().astype(np.float64)
         cnt = np.diff(off)
+        # scope-table flops per target on the unpadded rows (M = k, n = Q(d, m),
+        # L = d + 1 solve rows: gradient and Laplacian) and on the row class
+        # the target was bucketed into (the tile it ran in)
+        ok = (nst & gmls.T_TOO_FEW_NEIGHBOURS) == 0
+        qn = np.array([BASIS_SIZE[(d, int(m))] for m in c["degree"]], dtype=np.float64)
+        M = cnt.astype(np.float64)
+        Mp = classes[np.minimum(np.searchsorted(classes, cnt), len(classes) - 1)].astype(np.float64)
+        flops_alg.append(float(np.sum(alg_flops(M, qn, d + 1, its)[ok])))
+        flops_pad.append(float(np.sum(alg_flops(Mp, qn, d + 1, its)[ok])))
         stats[f"{d}d"] = {"neighbours_min": int(cnt.min()), "neighbours_mean": float(cnt.mean()),
                           "neighbours_max": int(cnt.max()),
                           "too_few_neighbours": int(np.sum((nst & gmls.T_TOO_FEW_NEIGHBOURS) != 0)),
@@ -1063,10 +1077,27 @@ def batched_uneven(ctx, n_per_dim=500_000, steps=3, n_sample=32):
             place = {0: "", 1: ", split", 2: ", global"}[v >> 3]
             key = f"{r['dim']}d m={r['degree']} rows<={r['rows']}{' fp64' if r['precision'] == gmls.FP64 else ''}"
             tune.setdefault(key, {})[f"{v & 7}w{place}"] = round(r["ms"], 3)
+    import torch as _t
+
+    p32, _, peak_src = alu_peaks(_t.device("cuda", _t.cuda.current_device()))
+    roof = {}
+    for i, d in enumerate((2, 3)):
+        a = flops_alg[i] / (stencil_ms[i] * 1e-3) / 1e12
+        roof[f"{d}d"] = {"achieved": a, "frac": a / p32, "kernel_ms": stencil_ms[i],
+                         "padding_waste": flops_pad[i] / flops_alg[i] - 1.0}
+    a_all = sum(flops_alg) / (sum(stencil_ms) * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": a_all, "peak": p32, "unit": "TFLOP/s", "frac": a_all / p32,
+                "traffic": None, "kernel": "bucketed persistent stencil launches (one per cloud), FP32 + refinement",
+                "flop_count": "sum over targets of 2Mn^2 - 2n^3/3 + L (n^2 + 4Mn) + iters L 4Mn with the unpadded "
+                              "M = k, n = Q(d, m), L = d + 1",
+                "padding_waste": sum(flops_pad) / sum(flops_alg) - 1.0,
+                "padding_note": "flops on the row class each target was bucketed into over the unpadded flops, minus 1",
+                "per_cloud": roof, "peak_source": peak_src}
     return {"workload": f"uneven batch: 2D and 3D jittered clouds of {n_per_dim} targets each, degree U{{2,3,4}}, "
                         "radius lists at 1.8 x the Q(d,m)-th neighbour distance (<= 160), 20 % one-sided, "
                         "scalar basis (gradient, Laplacian), one bucketed launch per cloud",
             "targets": 2 * n_per_dim, **res, "speedup_vs_fp64": res["fp64"]["step_ms"] / res["fp32_refine"]["step_ms"],
+            "roofline": roofline,
             "stats": stats, "tune_ms": tune, "l2": "flushed before each timed step (256 MB write)"}, gpu_sample
 
 
@@ -1097,10 +1128,12 @@ def batched_oracle_errors(gsamples):
     return out
 
 
-def stokes_solve(ctx, n_axis=128, full=True):
+def stokes_solve(ctx, n_axis=128, full=True, rtol=1e-10):
     """Global solve of the Stokes system (Sec. 3.3) on an n_axis^2 grid by
     GMRES(100) with right Jacobi preconditioning (gmls_gmres), to a relative
-    residual of 1e-10; RMS errors of the solved velocity and (mean-free)
+    residual of rtol (for the row-equilibrated legs: of R (b - A x); the
+    unscaled residual is reported beside it, and "converged" says whether the
+    target was met); RMS errors of the solved velocity and (mean-free)
     pressure against the manufactured field.  full: solved three times --
     interior pressure rows from the scalar Laplacian, then from the
     staggered one (Sec. 3.2; its stencil time is that of a first call), then
@@ -1126,14 +1159,20 @@ def stokes_solve(ctx, n_axis=128, full=True):
         rp, col, val = ctx.stokes_assemble(sv, sp, 1.0, ss)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=1e-10, row_scaling=row_scaling)
+        sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=rtol, row_scaling=row_scaling)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        # the unscaled relative residual ||b - A x|| / ||b|| (with row scaling,
+        # rel_residual is that of the equilibrated rows R (b - A x))
+        ax = ctx.spmv(rp, col, val, sol)
+        ctx.sync()
+        true_rel = float(torch.linalg.norm(b - ax) / torch.linalg.norm(b))
         s = sol.cpu().numpy()
         us, ps = s[:2 * n].reshape(n, 2).T, s[2 * n:3 * n]
         eu = float(np.sqrt(np.mean((us - d["u"]) ** 2)))
         ep = float(np.sqrt(np.mean(((ps - ps.mean()) - (d["p"] - d["p"].mean())) ** 2)))
         return {"unknowns": int(rp.shape[0] - 1), "nnz": int(col.shape[0]), "iterations": its, "rel_residual": rel,
+                "unscaled_rel_residual": true_rel, "converged": bool(np.isfinite(rel) and rel <= rtol),
                 "seconds": el, "rms_error_velocity": eu, "rms_error_pressure": ep}
 
     if not full:
@@ -1163,39 +1202,41 @@ def stokes_solve(ctx, n_axis=128, full=True):
     return out
 
 
-def serving(n_requests, seed=0):
-    """Poisson arrivals (200 req/s) of stencil requests -- 2D/3D clouds of
-    log-uniform 1e3..5e5 points, degree 2..4, scalar (gradient + Laplacian) or
-    divergence-free (vector Laplacian) basis -- through the continuous-batching
-    server (FP32 + refinement), and the same stream through the plain
-    per-request FP64 path (one request at a time, in arrival order)."""
+def serving(n_requests, nmax=5e4, rates=(100.0, 200.0), seed=0):
+    """The serving stream: Poisson arrivals of stencil requests -- 2D/3D
+    clouds of log-uniform nmin..nmax points, degree 2..4, scalar (gradient +
+    Laplacian) or divergence-free (vector Laplacian) basis -- through the
+    continuous-batching server (FP32 + refinement) and through the plain
+    per-request FP64 path (one request at a time, in arrival order), at each
+    offered rate.  The same requests at every rate (arrival times scale as
+    1 / rate).  Latency = arrival to completion; targets/s = completed
+    targets over the time from the first arrival to the last completion."""
     import threading
 
     import torch
 
     from paper_2104_14447_gb300 import gmls, inputs
 
-    reqs = inputs.request_stream(n_requests, 200.0, seed)
+    base = inputs.request_stream(n_requests, 1.0, seed, nmax=nmax)  # arrival times at 1 request/s
     clouds = []
-    for r in reqs:
+    for r in base:
         n_axis = max(3, int(round(r["n"] ** (1.0 / r["dim"]))))
         clouds.append(inputs.jittered_grid(r["dim"], n_axis, seed=r["seed"]))
     spec = []
-    for r in reqs:
+    for r in base:
         b = gmls.SCALAR if r["basis"] == "scalar" else gmls.DIVFREE
         fns = [gmls.GRAD, gmls.LAPLACIAN] if b == gmls.SCALAR else [gmls.VEC_LAPLACIAN]
         spec.append((b, r["degree"], SERVE_K[(r["dim"], b, r["degree"])], fns))
-    total_targets = sum(c.shape[1] for c in clouds)
-    offered = total_targets / max(reqs[-1]["t"], 1e-9)
+    total_targets = int(sum(c.shape[1] for c in clouds))
 
-    def run_server():
+    def run_server(rate):
         srv = gmls.Server(torch.cuda.current_device(), arena_bytes=48 << 30, streams=4, max_inflight=8)
-        tickets = [None] * len(reqs)
+        tickets = [None] * len(base)
         t0 = time.perf_counter()
 
         def client():
-            for i, r in enumerate(reqs):
-                dt = r["t"] - (time.perf_counter() - t0)
+            for i, r in enumerate(base):
+                dt = r["t"] / rate - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
                 b, m, k, fns = spec[i]
@@ -1203,7 +1244,7 @@ def serving(n_requests, seed=0):
 
         th = threading.Thread(target=client)
         th.start()
-        pending = set(range(len(reqs)))
+        pending = set(range(len(base)))
         while pending:
             for i in list(pending):
                 if tickets[i] is not None and srv.wait(tickets[i], 0):
@@ -1213,14 +1254,15 @@ def serving(n_requests, seed=0):
         th.join()
         st = srv.stats()
         srv.close()
-        return st
+        return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                "targets_per_s": st["targets_per_s"], "elapsed_s": st["elapsed_s"]}
 
-    def run_plain_fp64():
+    def run_plain_fp64(rate):
         ctx = gmls.Context(torch.cuda.current_device(), arena_bytes=48 << 30)
         ctx.set_option(gmls.OPT_AUTOTUNE, 0)
         lat, t0 = [], time.perf_counter()
-        for i, r in enumerate(reqs):
-            dt = r["t"] - (time.perf_counter() - t0)
+        for i, r in enumerate(base):
+            dt = r["t"] / rate - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
             b, m, k, fns = spec[i]
@@ -1228,22 +1270,31 @@ def serving(n_requests, seed=0):
             nid = ctx.neighbors(cid, k, 1.5)
             sid = ctx.stencils(nid, b, m, fns, precision=gmls.FP64)
             ctx.sync()
-            lat.append((time.perf_counter() - t0 - r["t"]) * 1e3)
+            lat.append((time.perf_counter() - t0 - r["t"] / rate) * 1e3)
             for h in (sid, nid, cid):
                 ctx.release(h)
-        el = time.perf_counter() - t0
+        el = time.perf_counter() - t0 - base[0]["t"] / rate
         ctx.close()
         return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "targets_per_s": total_targets / el, "elapsed_s": el}
+                "mean_ms": float(np.mean(lat)), "targets_per_s": total_targets / el, "elapsed_s": el}
 
-    srv = run_server()
-    plain = run_plain_fp64()
-    return {"requests": n_requests, "rate_per_s": 200.0, "targets": int(total_targets),
+    out = {"requests": n_requests, "targets": total_targets,
+           "request_mix": f"2D/3D (p = 1/2), n log-uniform in [1e3, {nmax:.0e}], degree U{{2,3,4}}, scalar or "
+                          "div-free basis (p = 1/2), k from the fixed-k table",
+           "size_cap": (f"n <= {nmax:.0e} instead of 5e5, so that {n_requests} requests run in about a minute "
+                        "per arm" if nmax < 5e5 else None),
+           "rates": {}}
+    for rate in rates:
+        offered = total_targets / (base[-1]["t"] / rate)
+        srv = run_server(rate)
+        plain = run_plain_fp64(rate)
+        out["rates"][f"{rate:g}_per_s"] = {
             "offered_targets_per_s": offered,
-            "continuous_batching_fp32_refine": {"p50_ms": srv["p50_ms"], "p99_ms": srv["p99_ms"],
-                                                "targets_per_s": srv["targets_per_s"], "elapsed_s": srv["elapsed_s"]},
-            "plain_per_request_fp64": plain,
-            "note": "bounded sample of the serving stream (first requests of the seeded Poisson sequence)"}
+            "continuous_batching_fp32_refine": srv, "plain_per_request_fp64": plain,
+            "regime": "below capacity (latency)" if srv["targets_per_s"] >= 0.95 * offered else "backlog",
+            "p99_speedup_vs_fp64": plain["p99_ms"] / srv["p99_ms"] if srv["p99_ms"] > 0 else None,
+            "throughput_speedup_vs_fp64": srv["targets_per_s"] / plain["targets_per_s"]}
+    return out
 
 
 def stokes2d_oracle_check(ctx, n_sample=2000):
@@ -1394,7 +1445,9 @@ def main():
                     help="profiling: run only this secondary section (--steps timed steps) and print it")
     ap.add_argument("--n-axis", type=int, default=512, help="2D section grid (profiling only; the benchmark is 512)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="serving stream length (0: skip)")
+    ap.add_argument("--serve-nmax", type=float, default=5e4, help="largest request (points) of the serving stream")
     ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--solve-512", action="store_true", help="also solve the 512 x 512 Stokes system (rtol 1e-10, 1e-12)")
     args = ap.parse_args()
     set_n_axis(args.n_axis)
     args.warmup = max(args.warmup, 3)
@@ -1437,6 +1490,9 @@ def main():
             sec["stokes_system"] = stokes_system(ctx)
             sec["stokes_system"]["solve"] = stokes_solve(ctx)
             sec["stokes_system"]["solve_256"] = stokes_solve(ctx, 256, full=False)
+            if args.solve_512:  # opt-in: about 5 s of GMRES
+                sec["stokes_system"]["solve_512"] = stokes_solve(ctx, 512, full=False)
+                sec["stokes_system"]["solve_512_rtol_1e-12"] = stokes_solve(ctx, 512, full=False, rtol=1e-12)
         out["stokes2d_512"] = sec
         out["small_2d_1024"] = small_2d(ctx)
         if not args.no_shapes:
@@ -1446,7 +1502,7 @@ def main():
             if not args.no_cpu_baseline:  # the oracle's side of the sampled comparison
                 out["batched_uneven"]["oracle_check"] = batched_oracle_errors(gsb)
         if args.serve_requests > 0:
-            out["serving"] = serving(args.serve_requests)
+            out["serving"] = serving(args.serve_requests, nmax=args.serve_nmax)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
