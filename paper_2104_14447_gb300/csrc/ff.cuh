@@ -156,6 +156,14 @@ struct Dot2 {
     h = s.h;
     l = __fadd_rn(l, __fadd_rn(s.l, e));
   }
+  // a * b with b a plain float (one product term fewer)
+  __device__ __forceinline__ void add_prod_f(ff a, float b) {
+    ff p = two_prod(a.h, b);
+    float e = __fmaf_rn(a.l, b, p.l);
+    ff s = two_sum(h, p.h);
+    h = s.h;
+    l = __fadd_rn(l, __fadd_rn(s.l, e));
+  }
   __device__ __forceinline__ ff value() const { return quick_two_sum(h, l); }
 };
 

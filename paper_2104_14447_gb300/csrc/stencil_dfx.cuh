@@ -160,19 +160,17 @@ struct DfxLay {
   static constexpr int LDA = KS + 1;  // odd: rows of different columns in different banks
   static constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
   static constexpr size_t AFF = 0;                                      // ff [Q][LDA]  A = sqrt(W) P
-  static constexpr size_t S = al16(AFF + sizeof(ff) * Q * LDA);         // ff [LC][LDA] s iterates (R_A first)
-  static constexpr size_t Y = al16(S + sizeof(ff) * LC * LDA);          // ff [L][N]
-  static constexpr size_t UV = al16(Y + sizeof(ff) * L * N);            // ff [LC][Q]   u = C y, then v = A^T s
+  static constexpr size_t S = al16(AFF + sizeof(ff) * Q * LDA);         // float [LC][LDA] s0 (R_A before it)
+  static constexpr size_t Y = al16(S + sizeof(float) * LC * LDA);       // float [L][N] y0
+  static constexpr size_t UV = al16(Y + sizeof(float) * L * N);         // ff [LC][Q]   u = C y0, then v = A^T s0
   static constexpr size_t RG = al16(UV + sizeof(ff) * LC * Q);          // float [N(N+1)/2] R_G, rows packed
   static constexpr size_t IDG = al16(RG + sizeof(float) * N * (N + 1) / 2);  // float [N] 1 / r_ii
   static constexpr size_t V1 = al16(IDG + sizeof(float) * N);           // float [NTOP][Q] stage-1 reflectors
   static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * Q);     // float [N0][Q] stage-2 reflectors
   static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * Q);     // float [N]
   static constexpr size_t TAUA = al16(TAUG + sizeof(float) * N);        // float [Q]
-  static constexpr size_t F = al16(TAUA + sizeof(float) * Q);           // float [LC][KS] residual f
-  static constexpr size_t IEPS = al16(F + sizeof(float) * LC * KS);     // ff 1 / eps
-  static constexpr size_t BYTES = al16(IEPS + sizeof(ff));
-  static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(ff) * LC * LDA, "R_A must fit in the s slot");
+  static constexpr size_t BYTES = al16(TAUA + sizeof(float) * Q);
+  static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(float) * LC * LDA, "R_A must fit in the s slot");
 };
 
 // x[sl] += v / x[sl] for a run-time slot index (static register indices)
@@ -360,9 +358,9 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
   const unsigned mask = 0xffffffffu;
   unsigned char* base = smem + (size_t)wid * Lay::BYTES;
   ff* Aff = reinterpret_cast<ff*>(base + Lay::AFF);
-  ff* Ss = reinterpret_cast<ff*>(base + Lay::S);
-  float* RA = reinterpret_cast<float*>(base + Lay::S);  // R_A, packed rows (before s exists)
-  ff* Ys = reinterpret_cast<ff*>(base + Lay::Y);
+  float* S0 = reinterpret_cast<float*>(base + Lay::S);  // s0 of pass 0 (FP32)
+  float* RA = reinterpret_cast<float*>(base + Lay::S);  // R_A, packed rows (before s0 exists)
+  float* Y0 = reinterpret_cast<float*>(base + Lay::Y);  // y0 of pass 0 (FP32)
   ff* UV = reinterpret_cast<ff*>(base + Lay::UV);
   float* RG = reinterpret_cast<float*>(base + Lay::RG);
   float* IDG = reinterpret_cast<float*>(base + Lay::IDG);
@@ -371,7 +369,6 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
   float* TAUG = reinterpret_cast<float*>(base + Lay::TAUG);
   float* TAUA = reinterpret_cast<float*>(base + Lay::TAUA);
   // sqrt(W_j) = A[j][0]: the first monomial is the constant
-  float* Fs = reinterpret_cast<float*>(base + Lay::F);
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
   const float tolf = (float)j.tol;
@@ -561,107 +558,176 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
     rmax = wmax<32>(rmax, mask);
     rmin = -wmax<32>(-rmin, mask);
     const bool ill = !(rmin * 1.0e6f >= rmax) || !(rmin > 0.0f);
-    if (lane == 0) reinterpret_cast<ff*>(base + Lay::IEPS)[0] = inv_eps;
     __syncwarp(mask);
 
-    // ---- 4. solve and refinement (pass 0 = the plain FP32 solve)
+    // ---- 4. pass 0 (the plain FP32 solve) and one refinement pass.  A
+    //         target whose correction misses the tolerance after that pass
+    //         is redone by the FP64 kernel (about 1e-5 of the targets of the
+    //         porous workload), so s0 and y0 stay FP32 and s = s0 + ds is
+    //         formed only when the weights are stored.
     auto lam = [&](int l, int i) {  // vector Laplacian row l at basis function i (float-float)
       const int c = tab.lam[l][i];
       return c == 0 ? ff(0.f, 0.f) : mul_f(ie2, (float)c);
     };
-    bool conv = false;
-    int used = 0;
-    float prev = 0.0f;
-#pragma unroll 1
-    for (int itr = 0; itr <= j.max_refine; ++itr) {
-      float w[L][NT], d1[L][NT];
-      if (itr > 0) {
-        if (ill) break;
-        // u = C y
-        for (int e = lane; e < LC * Q; e += 32) {
-          const int lc = e / Q, g = e - lc * Q, l = lc / D, c = lc - l * D;
-          ff uv(0.f, 0.f);
-          if (c >= 1) {
-            uv = Ys[l * N + (c - 1) * Q + g];
-          } else if (tab.fidx[g] >= 0) {
-            uv = Ys[l * N + NTOP + tab.fidx[g]];
-          } else {
+    // z = Q_B [dl; 0] for L vectors dl in the solve layout: Q_G in the row
+    // space of G, then Q_A on each (l, c) vector (row layout)
+    auto apply_qb = [&](const float (&dl)[L][NT], float (&z)[LC][MRA]) {
+      float zt[L][TS], zb[L];
 #pragma unroll
-            for (int c2 = 1; c2 < D; ++c2) {
-              const int ug = tab.ush[c2][g];
-              if (ug >= 0) uv = uv - Ys[l * N + (c2 - 1) * Q + ug];
-            }
-          }
-          UV[e] = uv;
+      for (int l = 0; l < L; ++l) {
+#pragma unroll
+        for (int s = 0; s < TS; ++s) {
+          const int p = lane + 32 * s;
+          zt[l][s] = p < NTOP ? dl[l][s < NT ? s : 0] : 0.0f;
         }
-        __syncwarp(mask);
-        // f = B y - s: row (l, c, j) = A_j . u_(l,c) - s_(l,c,j), into F;
-        // HG (l, c) chains at a time
-        constexpr int HG = LC % 3 == 0 ? 3 : 2;
-        static_assert(LC % HG == 0, "(l, c) pairs in groups");
-        for (int q = lane; q < k; q += 32) {
+        // bottom row r < N0 holds dl[NTOP + r]
+        const int p = NTOP + lane;
+        const float b0 = __shfl_sync(mask, dl[l][0], p & 31);
+        const float b1 = NT > 1 ? __shfl_sync(mask, dl[l][NT - 1], p & 31) : 0.0f;
+        zb[l] = lane < N0 ? ((p >> 5) == 0 ? b0 : b1) : 0.0f;
+      }
+      dfx_apply_qg<L, TS, Q, NTOP, N0, false>(zt, zb, V1, V2, TAUG, lane, mask);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        z[l * D][0] = lane < Q ? zb[l] : 0.0f;
+#pragma unroll
+        for (int c = 1; c < D; ++c) {
+          const int p = (c - 1) * Q + lane;  // top row of (component c, R_A row lane)
+          const float s0 = __shfl_sync(mask, zt[l][0], p & 31);
+          const float s1 = TS > 1 ? __shfl_sync(mask, zt[l][TS - 1], p & 31) : 0.0f;
+          z[l * D + c][0] = lane < Q ? ((p >> 5) == 0 ? s0 : s1) : 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int tt = 1; tt < MRA; ++tt) z[l * D + c][tt] = 0.0f;
+      }
+      dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, true);
+    };
+
+    // pass 0: a = R^-T lambda, s0 = Q_B [a; 0], y0 = R^-1 a
+    float w[L][NT];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int s = 0; s < NT; ++s) {
+        const int p = lane + 32 * s;
+        w[l][s] = p < N ? lam(l, p).h : 0.0f;
+      }
+    dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);
+    float z[LC][MRA];
+    apply_qb(w, z);
+    dfx_solve<N, L, NT, false>(RG, IDG, w, lane, mask);
+#pragma unroll
+    for (int lc = 0; lc < LC; ++lc)
+#pragma unroll
+      for (int tt = 0; tt < MRA; ++tt) {
+        const int q = lane + 32 * tt;
+        if (q < k) S0[lc * LDA + q] = z[lc][tt];
+      }
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int s = 0; s < NT; ++s) {
+        const int p = lane + 32 * s;
+        if (p < N) Y0[l * N + p] = w[l][s];
+      }
+    __syncwarp(mask);
+
+    bool conv = false;
+    if (!ill && j.max_refine >= 1) {
+      // u = C y0 (exact in float-float: sums of at most d FP32 values)
+      for (int e = lane; e < LC * Q; e += 32) {
+        const int lc = e / Q, g = e - lc * Q, l = lc / D, c = lc - l * D;
+        ff uv(0.f, 0.f);
+        if (c >= 1) {
+          uv = ff(Y0[l * N + (c - 1) * Q + g], 0.f);
+        } else if (tab.fidx[g] >= 0) {
+          uv = ff(Y0[l * N + NTOP + tab.fidx[g]], 0.f);
+        } else {
+#pragma unroll
+          for (int c2 = 1; c2 < D; ++c2) {
+            const int ug = tab.ush[c2][g];
+            if (ug >= 0) uv = uv - ff(Y0[l * N + (c2 - 1) * Q + ug], 0.f);
+          }
+        }
+        UV[e] = uv;
+      }
+      __syncwarp(mask);
+      // f = B y0 - s0 in the row layout: row (l, c, j) = A_j . u_(l,c) - s0_(l,c,j);
+      // rows of one slot at a time, the (l, c) chains side by side
+      float fr[LC][MRA];
+#pragma unroll 1
+      for (int tt = 0; tt < MRA; ++tt) {
+        const int q = lane + 32 * tt;
+        float ft[LC];
+        if (q < k) {
           ff ar[Q];
 #pragma unroll
           for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
-#pragma unroll 1
-          for (int lc = 0; lc < LC; lc += HG) {
-            Dot2 acc[HG];
 #pragma unroll
-            for (int h = 0; h < HG; ++h) acc[h].init(-Ss[(lc + h) * LDA + q]);
+          for (int lc = 0; lc < LC; ++lc) {
+            Dot2 acc;
+            acc.init(ff(-S0[lc * LDA + q], 0.f));
 #pragma unroll
-            for (int g = 0; g < Q; ++g)
-#pragma unroll
-              for (int h = 0; h < HG; ++h) acc[h].add_prod(ar[g], UV[(lc + h) * Q + g]);
-#pragma unroll
-            for (int h = 0; h < HG; ++h) Fs[(lc + h) * KS + q] = __fadd_rn(acc[h].h, acc[h].l);
+            for (int g = 0; g < Q; ++g) acc.add_prod(ar[g], UV[lc * Q + g]);
+            ft[lc] = __fadd_rn(acc.h, acc.l);
           }
-        }
-        __syncwarp(mask);
-        // v = (I (x) A^T) s, four interleaved compensated chains per entry
-        for (int e = lane; e < LC * Q; e += 32) {
-          const int lc = e / Q, g = e - lc * Q;
-          const ff* ag = Aff + g * LDA;
-          const ff* sl = Ss + lc * LDA;
-          Dot2 c[4];
-          int q = 0;
-          for (; q + 3 < k; q += 4) {
+        } else {
 #pragma unroll
-            for (int h = 0; h < 4; ++h) c[h].add_prod(ag[q + h], sl[q + h]);
+          for (int lc = 0; lc < LC; ++lc) ft[lc] = 0.0f;
+        }
+#pragma unroll
+        for (int t2 = 0; t2 < MRA; ++t2)
+          if (t2 == tt) {
+#pragma unroll
+            for (int lc = 0; lc < LC; ++lc) fr[lc][t2] = ft[lc];
           }
-          for (; q < k; ++q) c[0].add_prod(ag[q], sl[q]);
-          UV[e] = (c[0].value() + c[1].value()) + (c[2].value() + c[3].value());
+      }
+      __syncwarp(mask);
+      // v = (I (x) A^T) s0, four interleaved compensated chains per entry
+      for (int e = lane; e < LC * Q; e += 32) {
+        const int lc = e / Q, g = e - lc * Q;
+        const ff* ag = Aff + g * LDA;
+        const float* sl = S0 + lc * LDA;
+        Dot2 c4[4];
+        int q = 0;
+        for (; q + 3 < k; q += 4) {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) c4[h].add_prod_f(ag[q + h], sl[q + h]);
         }
-        __syncwarp(mask);
-        // g = lambda - C^T v in the solve layout
+        for (; q < k; ++q) c4[0].add_prod_f(ag[q], sl[q]);
+        UV[e] = (c4[0].value() + c4[1].value()) + (c4[2].value() + c4[3].value());
+      }
+      __syncwarp(mask);
+      // g = lambda - C^T v in the solve layout
 #pragma unroll
-        for (int l = 0; l < L; ++l)
+      for (int l = 0; l < L; ++l)
 #pragma unroll
-          for (int s = 0; s < NT; ++s) {
-            const int i = lane + 32 * s;
-            float gv = 0.0f;
-            if (i < N) {
-              ff ct(0.f, 0.f);
-              if (i < NTOP) ct = UV[(l * D + 1 + i / Q) * Q + i % Q];
-              const int src = tab.src[i];
-              if (src >= 0) {
-                const ff v0 = UV[(l * D) * Q + src];
-                ct = i < NTOP ? ct - v0 : ct + v0;
-              }
-              const ff gg = lam(l, i) - ct;
-              gv = __fadd_rn(gg.h, gg.l);
+        for (int s = 0; s < NT; ++s) {
+          const int i = lane + 32 * s;
+          float gv = 0.0f;
+          if (i < N) {
+            ff ct(0.f, 0.f);
+            if (i < NTOP) ct = UV[(l * D + 1 + i / Q) * Q + i % Q];
+            const int src = tab.src[i];
+            if (src >= 0) {
+              const ff v0 = UV[(l * D) * Q + src];
+              ct = i < NTOP ? ct - v0 : ct + v0;
             }
-            w[l][s] = gv;
+            const ff gg = lam(l, i) - ct;
+            gv = __fadd_rn(gg.h, gg.l);
           }
-        // d_1 = first N entries of Q_G^T gather(Q_A^T f)
-        float z[LC][MRA];
+          w[l][s] = gv;
+        }
+      // d_1 = first N entries of Q_G^T gather(Q_A^T f)
 #pragma unroll
-        for (int lc = 0; lc < LC; ++lc)
+      for (int lc = 0; lc < LC; ++lc)
 #pragma unroll
-          for (int tt = 0; tt < MRA; ++tt) {
-            const int q = lane + 32 * tt;
-            z[lc][tt] = q < k ? Fs[lc * KS + q] : 0.0f;
-          }
-        dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, false);
+        for (int tt = 0; tt < MRA; ++tt) z[lc][tt] = fr[lc][tt];
+      dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, false);
+      float d1[L][NT];
+      {
         float zt[L][TS], zb[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) {
@@ -688,91 +754,31 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
             const float fromb = __shfl_sync(mask, zb[l], (p - NTOP) & 31);
             d1[l][s] = p < NTOP ? (s < TS ? zt[l][s < TS ? s : 0] : 0.0f) : (p < N ? fromb : 0.0f);
           }
-      } else {
-#pragma unroll
-        for (int l = 0; l < L; ++l)
-#pragma unroll
-          for (int s = 0; s < NT; ++s) {
-            const int p = lane + 32 * s;
-            w[l][s] = p < N ? lam(l, p).h : 0.0f;
-            d1[l][s] = 0.0f;
-          }
       }
       dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);  // a = R^-T g
-      float dyv[L][NT];
 #pragma unroll
       for (int l = 0; l < L; ++l)
 #pragma unroll
-        for (int s = 0; s < NT; ++s) {
-          dyv[l][s] = w[l][s] - d1[l][s];  // delta
-          w[l][s] = dyv[l][s];
-        }
-      dfx_solve<N, L, NT, false>(RG, IDG, dyv, lane, mask);  // dy = R^-1 delta
-      // ds = f + Q_B [delta; 0]: Q_G in the row space of G, then Q_A per (l, c)
-      float zt[L][TS], zb[L];
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-#pragma unroll
-        for (int s = 0; s < TS; ++s) {
-          const int p = lane + 32 * s;
-          zt[l][s] = p < NTOP ? w[l][s < NT ? s : 0] : 0.0f;
-        }
-        // bottom row r < N0 holds delta[NTOP + r]
-        const int p = NTOP + lane;
-        float b0 = __shfl_sync(mask, w[l][0], p & 31);
-        float b1 = NT > 1 ? __shfl_sync(mask, w[l][NT - 1], p & 31) : 0.0f;
-        zb[l] = lane < N0 ? ((p >> 5) == 0 ? b0 : b1) : 0.0f;
-      }
-      dfx_apply_qg<L, TS, Q, NTOP, N0, false>(zt, zb, V1, V2, TAUG, lane, mask);
-      float z[LC][MRA];
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        z[l * D][0] = lane < Q ? zb[l] : 0.0f;
-#pragma unroll
-        for (int c = 1; c < D; ++c) {
-          const int p = (c - 1) * Q + lane;  // top row of (component c, R_A row lane)
-          const float s0 = __shfl_sync(mask, zt[l][0], p & 31);
-          const float s1 = TS > 1 ? __shfl_sync(mask, zt[l][TS - 1], p & 31) : 0.0f;
-          z[l * D + c][0] = lane < Q ? ((p >> 5) == 0 ? s0 : s1) : 0.0f;
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-#pragma unroll
-          for (int tt = 1; tt < MRA; ++tt) z[l * D + c][tt] = 0.0f;
-      }
-      dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, true);
-      // s += ds, y += dy; the size of the correction for the stopping rule
+        for (int s = 0; s < NT; ++s) w[l][s] -= d1[l][s];  // delta (dy = R^-1 delta is not needed)
+      apply_qb(w, z);
+      // ds = f + Q_B [delta; 0]; error left ~ |ds| times the contraction
+      // factor, estimated by the relative size of the correction
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
       for (int lc = 0; lc < LC; ++lc)
 #pragma unroll
         for (int tt = 0; tt < MRA; ++tt) {
           const int q = lane + 32 * tt;
+          z[lc][tt] += fr[lc][tt];
           if (q < k) {
-            const float ds = itr > 0 ? z[lc][tt] + Fs[lc * KS + q] : z[lc][tt];
-            const ff s1 = itr > 0 ? add_f(Ss[lc * LDA + q], ds) : ff(ds, 0.0f);
-            Ss[lc * LDA + q] = s1;
-            dmax = fmaxf(dmax, fabsf(ds));
-            smax = fmaxf(smax, fabsf(s1.h));
+            dmax = fmaxf(dmax, fabsf(z[lc][tt]));
+            smax = fmaxf(smax, fabsf(S0[lc * LDA + q] + z[lc][tt]));
           }
-        }
-#pragma unroll
-      for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int s = 0; s < NT; ++s) {
-          const int p = lane + 32 * s;
-          if (p < N) Ys[l * N + p] = itr > 0 ? add_f(Ys[l * N + p], dyv[l][s]) : ff(dyv[l][s], 0.0f);
         }
       dmax = wmax<32>(dmax, mask);
       smax = wmax<32>(smax, mask);
-      __syncwarp(mask);
-      if (itr == 0) continue;
-      used = itr;
-      const float rho = (itr == 1) ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
-      const float est = dmax * fminf(1.0f, rho);
-      conv = est <= tolf * smax;
-      prev = dmax;
-      if (conv) break;
+      const float rho = dmax / fmaxf(smax, 1e-37f);
+      conv = dmax * fminf(1.0f, rho) <= tolf * smax;
     }
     if (!conv) {
       if (lane == 0) {
@@ -784,21 +790,32 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       continue;
     }
 
-    // ---- 5. w = sqrt(W) s (FP64) in [row][neighbour][component]
+    // ---- 5. w = sqrt(W) (s0 + ds) (FP64) in [row][neighbour][component],
+    //         from the row layout (s0 + ds exact as float-float)
     for (int fo = 0; fo < j.nout; ++fo) {
       const int R = j.out_rows[fo], C = j.out_ncomp[fo], src = j.out_src[fo];
       double* wo = j.out_w[fo] + o0 * (int64_t)R * C;
-      const int per_row = k * C;
+      if (src < 0) {
+        for (int e = lane; e < R * k * C; e += 32) wo[e] = 0.0;
+        continue;
+      }
       const float sgn = (float)j.out_sign[fo];
-      for (int rr = 0; rr < R; ++rr) {
-        for (int e = lane; e < per_row; e += 32) {
-          double val = 0.0;
-          if (src >= 0) {
-            const int q = e / C, c = e - q * C;
-            const ff s = Ss[((src + rr) * D + c) * LDA + q] * Aff[q];
-            val = to_double(ff(sgn * s.h, sgn * s.l));
-          }
-          wo[(int64_t)rr * per_row + e] = val;
+#pragma unroll
+      for (int tt = 0; tt < MRA; ++tt) {
+        const int q = lane + 32 * tt;
+        if (q < k) {
+          const ff swq = Aff[q];  // sqrt(W_q): the constant column of A
+#pragma unroll
+          for (int l = 0; l < L; ++l)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              const int rr = l - src;
+              if (rr >= 0 && rr < R && c < C) {
+                const ff sv = two_sum(S0[(l * D + c) * LDA + q], z[l * D + c][tt]);
+                const ff wv = sv * swq;
+                wo[((int64_t)rr * k + q) * C + c] = to_double(ff(sgn * wv.h, sgn * wv.l));
+              }
+            }
         }
       }
     }
@@ -806,7 +823,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       for (int l = lane; l < j.L; l += 32) j.beta[to * j.L + l] = 0.0;
     if (lane == 0) {
       j.status[to] = st;
-      if (j.iters) j.iters[to] = (uint8_t)used;
+      if (j.iters) j.iters[to] = 1;
     }
     __syncwarp(mask);
   }
