@@ -341,8 +341,25 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
   } else if (it != ctx->tune.end()) {
     choice = it->second;
   } else if (ctx->autotune && !capturing(ctx)) {
+    // the timed sample: up to 8192 targets spread evenly over the list (the
+    // first ones may all be of one kind -- e.g. a cube face of boundary
+    // targets that the register kernel hands off without work)
     StencilJob js = j;
-    js.n_tgt = std::min<int64_t>(j.n_tgt, 8192);
+    constexpr int64_t kTuneTargets = 8192;
+    int32_t* sample = nullptr;
+    if (!j.items && j.n_tgt > kTuneTargets) {
+      sample = arena_alloc<int32_t>(ctx, kTuneTargets + 1);
+      if (sample) {
+        std::vector<int32_t> h(kTuneTargets + 1);
+        for (int64_t i = 0; i < kTuneTargets; ++i) h[i] = (int32_t)(i * j.n_tgt / kTuneTargets);
+        h[kTuneTargets] = (int32_t)kTuneTargets;
+        CK(cudaMemcpyAsync(sample, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, ctx->stream),
+           "gmls_stencils tuning sample");
+        js.items = sample;
+        js.n_items = sample + kTuneTargets;
+      }
+    }
+    if (!js.items) js.n_tgt = std::min<int64_t>(j.n_tgt, kTuneTargets);
     float best = 1e30f;
     std::vector<int> cands;
     if (ok32) cands.push_back(-1);
@@ -363,6 +380,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
         choice = c;
       }
     }
+    ctx->arena.release(sample);  // the timed launches have finished (time_launch waits for them)
     if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: no kernel variant fits this shape");
     ctx->tune[key] = choice;
   } else {
