@@ -33,13 +33,17 @@
 // For the 240 x 50 systems of the 3D degree-3 basis this is about 0.17 MFLOP
 // of factorisation instead of 1.12 MFLOP for a QR of B.
 //
-// Refinement (Bjorck) of the augmented system as in the other FP32 kernels,
-// with the float-float residuals taken through the factored form:
-//   f = B y - s:   u = C y (Q per (l, c)), f_(l,c,j) = A_j . u_(l,c) - s_(l,c,j);
-//   g = lambda - B^T s:   v_(l,c) = A^T s_(l,c),  g = lambda - C^T v,
-// 2 k Q d L compensated products per pass instead of 2 k d n L, and a
-// correction ds = f + Q_B [R^-T g - d_1; 0], dy = R^-1 (R^-T g - d_1),
-// d_1 = the first n entries of Q_B^T f.
+// Solve and refinement: y0 = R^-1 R^-T lambda (FP32), then one Bjorck step on
+// the augmented system [[I, B], [B^T, 0]] [s; -y] = [0; lambda^T] starting
+// from s0 = B y0 evaluated in float-float, so that f = B y0 - s0 = 0 and the
+// correction needs a single application of Q_B:
+//   g = lambda - B^T s0 (float-float),  delta = R^-T g,  ds = Q_B [delta; 0].
+// s0 = B y0 carries an error of order kappa u_32 (as Q_B [R^-T lambda; 0]
+// would) and the step contracts it by about kappa u_32.  B y0 and B^T s0 go
+// through the factored form -- u = C y0, s0_(l,c,j) = A_j . u_(l,c);
+// v_(l,c) = A^T s0_(l,c), B^T s0 = C^T v -- 2 k Q d L compensated products
+// instead of 2 k d n L.  Targets whose correction misses the tolerance, or
+// whose factor is ill-conditioned, go to the FP64 redo list.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -160,8 +164,8 @@ struct DfxLay {
   static constexpr int LDA = KS + 1;  // odd: rows of different columns in different banks
   static constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
   static constexpr size_t AFF = 0;                                      // ff [Q][LDA]  A = sqrt(W) P
-  static constexpr size_t S = al16(AFF + sizeof(ff) * Q * LDA);         // float [LC][LDA] s0 (R_A before it)
-  static constexpr size_t Y = al16(S + sizeof(float) * LC * LDA);       // float [L][N] y0
+  static constexpr size_t S = al16(AFF + sizeof(ff) * Q * LDA);         // ff [LC][LDA] s0 = B y0 (R_A before it)
+  static constexpr size_t Y = al16(S + sizeof(ff) * LC * LDA);          // float [L][N] y0
   static constexpr size_t UV = al16(Y + sizeof(float) * L * N);         // ff [LC][Q]   u = C y0, then v = A^T s0
   static constexpr size_t RG = al16(UV + sizeof(ff) * LC * Q);          // float [N(N+1)/2] R_G, rows packed
   static constexpr size_t IDG = al16(RG + sizeof(float) * N * (N + 1) / 2);  // float [N] 1 / r_ii
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
   const unsigned mask = 0xffffffffu;
   unsigned char* base = smem + (size_t)wid * Lay::BYTES;
   ff* Aff = reinterpret_cast<ff*>(base + Lay::AFF);
-  float* S0 = reinterpret_cast<float*>(base + Lay::S);  // s0 of pass 0 (FP32)
+  ff* S0 = reinterpret_cast<ff*>(base + Lay::S);  // s0 = B y0 (float-float)
   float* RA = reinterpret_cast<float*>(base + Lay::S);  // R_A, packed rows (before s0 exists)
   float* Y0 = reinterpret_cast<float*>(base + Lay::Y);  // y0 of pass 0 (FP32)
   ff* UV = reinterpret_cast<ff*>(base + Lay::UV);
@@ -605,7 +609,12 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, true);
     };
 
-    // pass 0: a = R^-T lambda, s0 = Q_B [a; 0], y0 = R^-1 a
+    // pass 0: y0 = R^-1 R^-T lambda (FP32).  The refinement starts from
+    // s0 = B y0 evaluated in float-float, so that f = B y0 - s0 = 0 exactly
+    // and the Bjorck correction needs one application of Q_B:
+    //   g = lambda - B^T s0,  delta = R^-T g,  ds = Q_B [delta; 0].
+    // (s0 = B y0 is as accurate as Q_B [R^-T lambda; 0] -- its error is of
+    // order kappa u_32 -- and the correction contracts it by about kappa u_32.)
     float w[L][NT];
 #pragma unroll
     for (int l = 0; l < L; ++l)
@@ -615,16 +624,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
         w[l][s] = p < N ? lam(l, p).h : 0.0f;
       }
     dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);
-    float z[LC][MRA];
-    apply_qb(w, z);
     dfx_solve<N, L, NT, false>(RG, IDG, w, lane, mask);
-#pragma unroll
-    for (int lc = 0; lc < LC; ++lc)
-#pragma unroll
-      for (int tt = 0; tt < MRA; ++tt) {
-        const int q = lane + 32 * tt;
-        if (q < k) S0[lc * LDA + q] = z[lc][tt];
-      }
 #pragma unroll
     for (int l = 0; l < L; ++l)
 #pragma unroll
@@ -635,6 +635,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
     __syncwarp(mask);
 
     bool conv = false;
+    float z[LC][MRA];
     if (!ill && j.max_refine >= 1) {
       // u = C y0 (exact in float-float: sums of at most d FP32 values)
       for (int e = lane; e < LC * Q; e += 32) {
@@ -654,49 +655,38 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
         UV[e] = uv;
       }
       __syncwarp(mask);
-      // f = B y0 - s0 in the row layout: row (l, c, j) = A_j . u_(l,c) - s0_(l,c,j);
-      // rows of one slot at a time, the (l, c) chains side by side
-      float fr[LC][MRA];
+      // s0 = B y0: row (l, c, j) = A_j . u_(l,c), compensated, into S0
 #pragma unroll 1
-      for (int tt = 0; tt < MRA; ++tt) {
-        const int q = lane + 32 * tt;
-        float ft[LC];
-        if (q < k) {
-          ff ar[Q];
+      for (int q = lane; q < k; q += 32) {
+        ff ar[Q];
 #pragma unroll
-          for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
+        for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
+        constexpr int HG = LC % 3 == 0 ? 3 : 2;
+        static_assert(LC % HG == 0, "(l, c) pairs in groups");
+#pragma unroll 1
+        for (int lc = 0; lc < LC; lc += HG) {
+          Dot2 acc[HG];
 #pragma unroll
-          for (int lc = 0; lc < LC; ++lc) {
-            Dot2 acc;
-            acc.init(ff(-S0[lc * LDA + q], 0.f));
+          for (int g = 0; g < Q; ++g)
 #pragma unroll
-            for (int g = 0; g < Q; ++g) acc.add_prod(ar[g], UV[lc * Q + g]);
-            ft[lc] = __fadd_rn(acc.h, acc.l);
-          }
-        } else {
+            for (int h = 0; h < HG; ++h) acc[h].add_prod(ar[g], UV[(lc + h) * Q + g]);
 #pragma unroll
-          for (int lc = 0; lc < LC; ++lc) ft[lc] = 0.0f;
+          for (int h = 0; h < HG; ++h) S0[(lc + h) * LDA + q] = acc[h].value();
         }
-#pragma unroll
-        for (int t2 = 0; t2 < MRA; ++t2)
-          if (t2 == tt) {
-#pragma unroll
-            for (int lc = 0; lc < LC; ++lc) fr[lc][t2] = ft[lc];
-          }
       }
       __syncwarp(mask);
       // v = (I (x) A^T) s0, four interleaved compensated chains per entry
       for (int e = lane; e < LC * Q; e += 32) {
         const int lc = e / Q, g = e - lc * Q;
         const ff* ag = Aff + g * LDA;
-        const float* sl = S0 + lc * LDA;
+        const ff* sl = S0 + lc * LDA;
         Dot2 c4[4];
         int q = 0;
         for (; q + 3 < k; q += 4) {
 #pragma unroll
-          for (int h = 0; h < 4; ++h) c4[h].add_prod_f(ag[q + h], sl[q + h]);
+          for (int h = 0; h < 4; ++h) c4[h].add_prod(ag[q + h], sl[q + h]);
         }
-        for (; q < k; ++q) c4[0].add_prod_f(ag[q], sl[q]);
+        for (; q < k; ++q) c4[0].add_prod(ag[q], sl[q]);
         UV[e] = (c4[0].value() + c4[1].value()) + (c4[2].value() + c4[3].value());
       }
       __syncwarp(mask);
@@ -720,59 +710,19 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
           }
           w[l][s] = gv;
         }
-      // d_1 = first N entries of Q_G^T gather(Q_A^T f)
-#pragma unroll
-      for (int lc = 0; lc < LC; ++lc)
-#pragma unroll
-        for (int tt = 0; tt < MRA; ++tt) z[lc][tt] = fr[lc][tt];
-      dfx_apply_qa<MRA, Q, LC>(a, TAUA, z, lane, mask, false);
-      float d1[L][NT];
-      {
-        float zt[L][TS], zb[L];
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-          zb[l] = lane < Q ? z[l * D][0] : 0.0f;
-#pragma unroll
-          for (int s = 0; s < TS; ++s) {
-            const int p = lane + 32 * s;
-            const int cb = p / Q, al = p - cb * Q;  // top row p: component cb + 1, R_A row al
-            float val = 0.0f;
-#pragma unroll
-            for (int c = 1; c < D; ++c) {
-              const float sh = __shfl_sync(mask, z[l * D + c][0], al < 32 ? al : 0);
-              if (cb + 1 == c) val = sh;
-            }
-            zt[l][s] = p < NTOP ? val : 0.0f;
-          }
-        }
-        dfx_apply_qg<L, TS, Q, NTOP, N0, true>(zt, zb, V1, V2, TAUG, lane, mask);
-#pragma unroll
-        for (int l = 0; l < L; ++l)
-#pragma unroll
-          for (int s = 0; s < NT; ++s) {
-            const int p = lane + 32 * s;
-            const float fromb = __shfl_sync(mask, zb[l], (p - NTOP) & 31);
-            d1[l][s] = p < NTOP ? (s < TS ? zt[l][s < TS ? s : 0] : 0.0f) : (p < N ? fromb : 0.0f);
-          }
-      }
-      dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);  // a = R^-T g
-#pragma unroll
-      for (int l = 0; l < L; ++l)
-#pragma unroll
-        for (int s = 0; s < NT; ++s) w[l][s] -= d1[l][s];  // delta (dy = R^-1 delta is not needed)
-      apply_qb(w, z);
-      // ds = f + Q_B [delta; 0]; error left ~ |ds| times the contraction
-      // factor, estimated by the relative size of the correction
+      dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);  // delta = R^-T g
+      apply_qb(w, z);                                      // ds = Q_B [delta; 0]
+      // error left ~ |ds| times the contraction factor, estimated by the
+      // relative size of the correction
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
       for (int lc = 0; lc < LC; ++lc)
 #pragma unroll
         for (int tt = 0; tt < MRA; ++tt) {
           const int q = lane + 32 * tt;
-          z[lc][tt] += fr[lc][tt];
           if (q < k) {
             dmax = fmaxf(dmax, fabsf(z[lc][tt]));
-            smax = fmaxf(smax, fabsf(S0[lc * LDA + q] + z[lc][tt]));
+            smax = fmaxf(smax, fabsf(S0[lc * LDA + q].h + z[lc][tt]));
           }
         }
       dmax = wmax<32>(dmax, mask);
@@ -791,7 +741,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
     }
 
     // ---- 5. w = sqrt(W) (s0 + ds) (FP64) in [row][neighbour][component],
-    //         from the row layout (s0 + ds exact as float-float)
+    //         from the row layout
     for (int fo = 0; fo < j.nout; ++fo) {
       const int R = j.out_rows[fo], C = j.out_ncomp[fo], src = j.out_src[fo];
       double* wo = j.out_w[fo] + o0 * (int64_t)R * C;
@@ -811,7 +761,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
             for (int c = 0; c < D; ++c) {
               const int rr = l - src;
               if (rr >= 0 && rr < R && c < C) {
-                const ff sv = two_sum(S0[(l * D + c) * LDA + q], z[l * D + c][tt]);
+                const ff sv = add_f(S0[(l * D + c) * LDA + q], z[l * D + c][tt]);
                 const ff wv = sv * swq;
                 wo[((int64_t)rr * k + q) * C + c] = to_double(ff(sgn * wv.h, sgn * wv.l));
               }
