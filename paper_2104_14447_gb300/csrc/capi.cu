@@ -341,9 +341,11 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
   } else if (it != ctx->tune.end()) {
     choice = it->second;
   } else if (ctx->autotune && !capturing(ctx)) {
-    // the timed sample: up to 8192 targets spread evenly over the list (the
-    // first ones may all be of one kind -- e.g. a cube face of boundary
-    // targets that the register kernel hands off without work)
+    // the timed sample: up to 8192 targets in 8 runs of 1024 consecutive
+    // ones spread evenly over the list (the first ones may all be of one
+    // kind -- e.g. a cube face of boundary targets that the register kernel
+    // hands off without work -- and isolated targets would time the kernels
+    // without the cache reuse of neighbouring targets)
     StencilJob js = j;
     constexpr int64_t kTuneTargets = 8192;
     int32_t* sample = nullptr;
@@ -351,7 +353,11 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
       sample = arena_alloc<int32_t>(ctx, kTuneTargets + 1);
       if (sample) {
         std::vector<int32_t> h(kTuneTargets + 1);
-        for (int64_t i = 0; i < kTuneTargets; ++i) h[i] = (int32_t)(i * j.n_tgt / kTuneTargets);
+        constexpr int64_t kRuns = 8, kRun = kTuneTargets / kRuns;
+        for (int64_t r = 0; r < kRuns; ++r) {
+          const int64_t start = r * (j.n_tgt - kRun) / (kRuns - 1);
+          for (int64_t i = 0; i < kRun; ++i) h[r * kRun + i] = (int32_t)(start + i);
+        }
         h[kTuneTargets] = (int32_t)kTuneTargets;
         CK(cudaMemcpyAsync(sample, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, ctx->stream),
            "gmls_stencils tuning sample");

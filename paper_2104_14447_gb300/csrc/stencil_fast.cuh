@@ -18,10 +18,10 @@
 //    FP64 offsets x_j - x_T (one FP64 subtraction per coordinate, split into
 //    float-float with integer operations), so the result does not depend on
 //    where the cloud sits and no other FP64 instruction runs in the hot loop;
-//  * refinement of the augmented system [[I, B], [B^T, 0]] [s; -y] =
-//    [0; lambda^T] (Bjorck) computes its residuals f = B y - s and
-//    g = lambda - B^T s with compensated float-float dot products and its
-//    corrections with the FP32 factors;
+//  * one refinement step on the augmented system [[I, B], [B^T, 0]] [s; -y]
+//    = [0; lambda^T] (Bjorck), started from s0 = B y0 in float-float (so the
+//    residual f = B y0 - s0 vanishes) with g = lambda - B^T s0 in
+//    compensated float-float and the correction from the FP32 factors;
 //  * w = sqrt(W) s is rounded to FP64 only when stored.
 //
 // Targets this path does not cover (Neumann constraint, a basis size other
@@ -281,6 +281,11 @@ template <int KIND, int D, int DEG, int MR, int L, int HW>
 __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()))
     stencil_fast_kernel(StencilJob j) {
   constexpr int N = gmls_gen::basis_size(KIND, D, DEG);
+  // refinement scheme: one Q application from s0 = B y0 (scalar and staggered
+  // bases, measured faster there), or Bjorck steps from s0 = Q [R^-T lambda; 0]
+  // with both residuals (divergence-free: its one-Q variant was slower, with
+  // more FP64 redos, on the 96 x 20 systems)
+  constexpr bool ONEQ = KIND != GMLS_BASIS_DIVFREE;
   constexpr int NC = (KIND == GMLS_BASIS_DIVFREE) ? D : 1;  // components per neighbour (staggered: 1)
   constexpr int ROWS = HW * MR;
   constexpr int NT = (N + HW - 1) / HW;
@@ -435,6 +440,143 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
     __syncwarp(mask);
     const bool ill = !(rmin * 1.0e6f >= rmax) || !(rmin > 0.0f);
 
+    int used = 0;
+    if constexpr (ONEQ) {
+    // ---- 3./4. solve and one refinement step.  y0 = R^-1 R^-T lambda in
+    // FP32; the Bjorck step on [[I, B], [B^T, 0]] [s; -y] = [0; lambda^T]
+    // starts from s0 = B y0 evaluated in float-float, so that f = B y0 - s0
+    // = 0 and the correction needs one application of Q:
+    //   g = lambda - B^T s0,  delta = R^-T g,  ds = Q [delta; 0].
+    // (s0 = B y0 is as accurate as Q [R^-T lambda; 0], an error of order
+    // kappa u_32, and the step contracts it by about kappa u_32.)  Targets
+    // whose correction misses the tolerance, or whose factor is
+    // ill-conditioned, go to the FP64 redo list.
+    float w[L][NT];
+    float z[L][MR];
+    bool conv = false;
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) {
+        const int p = lane + HW * tt;
+        w[l][tt] = (p < N) ? lam(l, p).h : 0.0f;
+      }
+    solve_rt_lanes<HW, N, L>(Rs, IDs, w, lane, mask);  // a = R^-T lambda
+    solve_r_lanes<HW, N, L>(Rs, IDs, w, lane, mask);   // y0 = R^-1 a
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int tt = 0; tt < NT; ++tt) {
+        const int p = lane + HW * tt;
+        if (p < N) Ys[l * N + p] = ff(w[l][tt], 0.0f);
+      }
+    __syncwarp(mask);
+    if (!ill && j.max_refine >= 1) {
+      // s0 = B y0 (compensated; y0 is FP32), lanes over rows
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const int r = lane + HW * i;
+          Dot2 acc;
+#pragma unroll
+          for (int c = 0; c < N; ++c) acc.add_prod_f(Bs[c * LD + r], Ys[l * N + c].h);
+          Ss[l * LD + r] = acc.value();
+        }
+      }
+      __syncwarp(mask);
+      // g = lambda - B^T s0 over the L*N (l, c) pairs: whole pairs per lane
+      // in full rounds of HW, the remaining pairs split into row blocks so
+      // that every lane does about the same number of terms
+      {
+        constexpr int pairs = L * N, full = pairs / HW, rem = pairs % HW;
+        for (int u = 0; u < full; ++u) {
+          const int e = u * HW + lane, l = e / N, c = e % N;
+          // four independent compensated chains over interleaved rows (ILP)
+          Dot2 acc[4];
+          acc[0].init(lam(l, c));
+          const ff* bc = Bs + c * LD;
+          const ff* sl = Ss + l * LD;
+#pragma unroll 2
+          for (int r = 0; r < ROWS; r += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (r + q < ROWS) acc[q].add_prod(-bc[r + q], sl[r + q]);
+          }
+          const ff tot = (acc[0].value() + acc[1].value()) + (acc[2].value() + acc[3].value());
+          Gs[l * N + c] = __fadd_rn(tot.h, tot.l);
+        }
+        if constexpr (rem > 0) {
+          // pair e is split over the lanes blk * rem + (e - full HW), blk <
+          // nblk; lane e - full HW gathers the partial sums by shuffles
+          constexpr int nblk = HW / rem, chunk = (ROWS + nblk - 1) / nblk;
+          const int e = full * HW + lane % rem, blk = lane / rem;
+          const int l = e / N, c = e % N;
+          Dot2 acc;
+          if (blk < nblk) {
+            const ff* bc = Bs + c * LD;
+            const ff* sl = Ss + l * LD;
+            const int r1 = min(ROWS, (blk + 1) * chunk);
+            for (int r = blk * chunk; r < r1; ++r) acc.add_prod(-bc[r], sl[r]);
+          }
+          const ff part = (blk < nblk) ? acc.value() : ff(0.f, 0.f);
+          ff sum = (lane < rem) ? lam(l, c) : ff(0.f, 0.f);
+#pragma unroll
+          for (int b = 0; b < nblk; ++b) {
+            const int src = b * rem + lane % rem;
+            const ff v(__shfl_sync(mask, part.h, src, HW), __shfl_sync(mask, part.l, src, HW));
+            sum = sum + v;
+          }
+          if (lane < rem) Gs[l * N + c] = __fadd_rn(sum.h, sum.l);
+        }
+      }
+      __syncwarp(mask);
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int tt = 0; tt < NT; ++tt) {
+          const int p = lane + HW * tt;
+          w[l][tt] = (p < N) ? Gs[l * N + p] : 0.0f;
+        }
+      solve_rt_lanes<HW, N, L>(Rs, IDs, w, lane, mask);  // delta = R^-T g
+      // z = [delta; 0]: rows r < N of z sit in the same lane / slot as entry p = r
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const int r = lane + HW * i;
+          z[l][i] = (r < N && i < NT) ? w[l][i < NT ? i : 0] : 0.0f;
+        }
+      apply_q_regs<HW, MR, N, L, true>(a, TAUs, z, lane, mask);  // ds = Q [delta; 0]
+      float dmax = 0.0f, smax = 0.0f;
+#pragma unroll
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+          const int r = lane + HW * i;
+          const ff s1 = add_f(Ss[l * LD + r], z[l][i]);
+          Ss[l * LD + r] = s1;
+          dmax = fmaxf(dmax, fabsf(z[l][i]));
+          smax = fmaxf(smax, fabsf(s1.h));
+        }
+      dmax = wmax<HW>(dmax, mask);
+      smax = wmax<HW>(smax, mask);
+      __syncwarp(mask);
+      // error left after the correction ~ |ds| times the contraction factor,
+      // estimated by the relative size of the correction
+      const float rho = dmax / fmaxf(smax, 1e-37f);
+      conv = dmax * fminf(1.0f, rho) <= tolf * smax;
+    }
+    if (!conv) {
+      if (lane == 0) {
+        const int slot = atomicAdd(j.fb_count, 1);
+        j.fb_items[slot] = (int32_t)to;
+        j.status[to] = ill ? GMLS_T_ILL_CONDITIONED : GMLS_T_REFINE_NOT_CONVERGED;
+      }
+      continue;
+    }
+    used = 1;
+    } else {
     // ---- 3./4. solve and refinement with float-float residuals.  Pass 0 is
     // the plain FP32 solve, i.e. a refinement step from s = y = 0 (f = 0,
     // g = lambda): a = R^{-T} lambda, s0 = Q [a; 0], y0 = R^{-1} a.  Passes
@@ -445,7 +587,6 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
     float w[L][NT];
     float z[L][MR];
     bool conv = false;
-    int used = 0;
     float prev = 0.0f;
 #pragma unroll 1
     for (int it = 0; it <= j.max_refine; ++it) {
@@ -579,6 +720,7 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
       continue;
     }
 
+    }
     // ---- 5. store w = sqrt(W) s (FP64) in [row][neighbour][component]
     for (int f = 0; f < j.nout; ++f) {
       const int R = j.out_rows[f], C = j.out_ncomp[f], src = j.out_src[f];
