@@ -323,7 +323,18 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
                      kmax >= gmls_gen::basis_size(GMLS_BASIS_SCALAR, dim, p->degree) &&
                      dfx_path_available(dim, p->degree, kmax, j.L);
   auto launch_fast = [&](const StencilJob& jj, int variant) {
-    if (variant == -3) return launch_stencils_dfx(ctx->launch(), jj, sms);
+    if (variant == -3) {
+      DfxShape sh;
+      cudaError_t e = dfx_launch_shape(jj, sms, &sh);
+      if (e != cudaSuccess) return e;
+      void* scr = ctx->arena.alloc(sh.scratch);
+      if (!scr) return cudaErrorMemoryAllocation;
+      StencilJob jd = jj;
+      jd.dscratch = static_cast<unsigned char*>(scr);
+      e = launch_stencils_dfx(ctx->launch(), jd, sh);
+      ctx->arena.release(scr);  // stream ordered: later work on this stream runs after the kernel
+      return e;
+    }
     return variant == -2 ? launch_stencils_fast(ctx->launch(), jj, mr16, 16, sms)
                          : launch_stencils_fast(ctx->launch(), jj, mr32, 32, sms);
   };

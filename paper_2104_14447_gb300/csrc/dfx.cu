@@ -23,12 +23,17 @@ bool dfx_path_available(int dim, int deg, int kmax, int L) {
   return e && kmax <= e->ks && L == dim;
 }
 
-cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, int sms) {
+// warps per block (up to the kernel's limit): the choice with the most
+// resident warps per SM, the largest block among equals; a grid of the
+// resident blocks, each warp looping over targets
+cudaError_t dfx_launch_shape(const StencilJob& j, int sms, DfxShape* s) {
   const DfxEntry* ent = dfx_entry(j.dim, j.degree);
   if (!ent || j.L != j.dim) return cudaErrorInvalidValue;
-  // warps per block: the choice with the most resident warps per SM
+  cudaFuncAttributes fa;
+  cudaError_t ea = cudaFuncGetAttributes(&fa, ent->fn);
+  if (ea != cudaSuccess) return ea;
   int best_w = 1, best_warps = 0, best_blocks = 1;
-  for (int w = 1; w <= 8; ++w) {
+  for (int w = 1; w <= 12 && 32 * w <= fa.maxThreadsPerBlock; ++w) {
     const size_t smem = (size_t)w * ent->bytes;
     if (smem > 227 * 1024) break;
     cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -36,22 +41,30 @@ cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, int sms) {
     int blocks = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, ent->fn, 32 * w, smem);
     if (e != cudaSuccess) return e;
-    if (blocks * w > best_warps) {
+    if (blocks * w >= best_warps) {  // ties: the larger block
       best_warps = blocks * w;
       best_w = w;
       best_blocks = blocks;
     }
   }
   if (best_warps == 0) return cudaErrorInvalidConfiguration;
-  const size_t smem = (size_t)best_w * ent->bytes;
-  cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int64_t want = (j.n_tgt + best_w - 1) / best_w;
   const int64_t cap = (int64_t)sms * best_blocks;
-  const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  s->grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+  s->warps = best_w;
+  s->smem = (size_t)best_w * ent->bytes;
+  s->scratch = (size_t)s->grid * best_w * ent->slot;
+  return cudaSuccess;
+}
+
+cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, const DfxShape& s) {
+  const DfxEntry* ent = dfx_entry(j.dim, j.degree);
+  if (!ent || j.L != j.dim || !j.dscratch) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+  if (e != cudaSuccess) return e;
   const DfxTab tab = ent->tab();
   void* args[] = {(void*)&j, (void*)&tab};
-  e = cudaLaunchKernel(ent->fn, dim3(grid), dim3(32 * best_w), args, smem, L.stream);
+  e = cudaLaunchKernel(ent->fn, dim3(s.grid), dim3(32 * s.warps), args, s.smem, L.stream);
   *L.counter += 1;
   return e;
 }

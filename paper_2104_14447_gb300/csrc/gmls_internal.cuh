@@ -175,6 +175,7 @@ struct StencilJob {
   int ld;                  // tile leading dimension (>= max rows)
   int nmax;                // max basis size
   int warps_per_target;    // 1, 2 or 4 (block = 128 threads)
+  unsigned char* dscratch; // factored div-free kernel: [grid blocks * warps][slot] (DfxShape)
 };
 
 constexpr int kMaxBuckets = 48;
@@ -230,7 +231,13 @@ cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, i
 // factored divergence-free kernel (dfx.cu): is (dim, degree) instantiated for
 // lists of at most kmax neighbours and L solve rows, and its launch
 bool dfx_path_available(int dim, int deg, int kmax, int L);
-cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, int sms);
+struct DfxShape {
+  int grid, warps;  // blocks, warps (targets in flight) per block
+  size_t smem;      // shared bytes per block
+  size_t scratch;   // global bytes the launch needs in StencilJob::dscratch
+};
+cudaError_t dfx_launch_shape(const StencilJob& j, int sms, DfxShape* s);
+cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, const DfxShape& s);
 
 // -------------------------------------------------------------------- CSR
 // id order of neighbour lists (see nbr_order_kernel): order[off[t] + r] =

@@ -157,25 +157,59 @@ DfxTab make_dfx_tab() {
 }
 
 // Shared memory of one warp (one target in flight).  KS: neighbour capacity.
+// The float-float tile A and the factors of G are never needed at the same
+// time: A while the basis is evaluated (phase A) and while the refinement
+// forms s0 = A u and v = A^T s0 (D); the factors during the QR (B), the FP32
+// solve (C) and the correction (E).  Both live in the first region; the one
+// not in use waits in the warp's slot of a global scratch (written once and
+// read once, it stays in L2).  s0 is formed HG (l, c) pairs at a time in a
+// small buffer and kept in the slot, as is sqrt(W): the lane that stores
+// them is the lane that reads them back.  A target of the 3D degree-3 basis
+// holds about 16 KB of shared memory instead of 30 KB.
 template <int D, int M, int KS>
 struct DfxLay {
   using Dm = DfxDims<D, M>;
   static constexpr int Q = Dm::Q, N = Dm::N, NTOP = Dm::NTOP, N0 = Dm::N0, L = Dm::L, LC = Dm::LC;
   static constexpr int LDA = KS + 1;  // odd: rows of different columns in different banks
   static constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
-  static constexpr size_t AFF = 0;                                      // ff [Q][LDA]  A = sqrt(W) P
-  static constexpr size_t S = al16(AFF + sizeof(ff) * Q * LDA);         // ff [LC][LDA] s0 = B y0 (R_A before it)
-  static constexpr size_t Y = al16(S + sizeof(ff) * LC * LDA);          // float [L][N] y0
-  static constexpr size_t UV = al16(Y + sizeof(float) * L * N);         // ff [LC][Q]   u = C y0, then v = A^T s0
-  static constexpr size_t RG = al16(UV + sizeof(ff) * LC * Q);          // float [N(N+1)/2] R_G, rows packed
+  // the factor block (offsets within the first region)
+  static constexpr size_t RG = 0;                                             // float [N(N+1)/2] R_G, rows packed
   static constexpr size_t IDG = al16(RG + sizeof(float) * N * (N + 1) / 2);  // float [N] 1 / r_ii
-  static constexpr size_t V1 = al16(IDG + sizeof(float) * N);           // float [NTOP][Q] stage-1 reflectors
-  static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * Q);     // float [N0][Q] stage-2 reflectors
-  static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * Q);     // float [N]
-  static constexpr size_t TAUA = al16(TAUG + sizeof(float) * N);        // float [Q]
-  static constexpr size_t BYTES = al16(TAUA + sizeof(float) * Q);
-  static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(float) * LC * LDA, "R_A must fit in the s slot");
+  static constexpr size_t V1 = al16(IDG + sizeof(float) * N);                // float [NTOP][Q] stage-1 reflectors
+  static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * Q);          // float [N0][Q] stage-2 reflectors
+  static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * Q);          // float [N]
+  static constexpr size_t TAUA = al16(TAUG + sizeof(float) * N);             // float [Q]
+  static constexpr size_t FAC = al16(TAUA + sizeof(float) * Q);              // bytes of the factor block
+  static constexpr size_t ABYTES = al16(sizeof(ff) * Q * LDA);               // ff [Q][LDA] A = sqrt(W) P
+  static constexpr size_t AFF = 0;
+  static constexpr int HG = LC % 3 == 0 ? 3 : 2;            // (l, c) pairs of s0 formed together
+  static constexpr size_t S = ABYTES > FAC ? ABYTES : FAC;  // ff [HG][LDA] a group of s0 (R_A, then y0, before it)
+  static constexpr size_t UV = al16(S + sizeof(ff) * HG * LDA);              // ff [LC][Q] u = C y0, then v = A^T s0
+  static constexpr size_t BYTES = al16(UV + sizeof(ff) * LC * Q);
+  // global scratch of one warp: A, the factor block, s0 ff [LC][LDA], sqrt(W) ff [LDA]
+  static constexpr size_t GF = ABYTES;
+  static constexpr size_t GS = GF + FAC;
+  static constexpr size_t GW = GS + al16(sizeof(ff) * LC * LDA);
+  static constexpr size_t SLOT = (GW + sizeof(ff) * LDA + 255) & ~size_t(255);
+  static_assert(LC % HG == 0, "(l, c) pairs in groups");
+  static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(ff) * HG * LDA, "R_A must fit in the s buffer");
+  static_assert(sizeof(float) * L * N <= sizeof(ff) * HG * LDA, "y0 must fit in the s buffer");
 };
+
+// copy of a 16-byte-aligned block by the 32 lanes of a warp, global side
+// cached in L2 only; every lane moves the same vectors in both directions
+template <size_t BYTES>
+__device__ __forceinline__ void dfx_park(float4* __restrict__ g, const float4* __restrict__ sm, int lane) {
+  static_assert(BYTES % 16 == 0, "whole vectors");
+#pragma unroll 4
+  for (int e = lane; e < (int)(BYTES / 16); e += 32) __stcg(g + e, sm[e]);
+}
+template <size_t BYTES>
+__device__ __forceinline__ void dfx_unpark(float4* __restrict__ sm, const float4* __restrict__ g, int lane) {
+  static_assert(BYTES % 16 == 0, "whole vectors");
+#pragma unroll 4
+  for (int e = lane; e < (int)(BYTES / 16); e += 32) sm[e] = __ldcg(g + e);
+}
 
 // x[sl] += v / x[sl] for a run-time slot index (static register indices)
 template <int S>
@@ -347,8 +381,13 @@ __device__ __forceinline__ void dfx_reflect(float alpha, const float (&x)[Q], in
   *beta_out = beta;
 }
 
+// Up to twelve warps (targets) per block, each on its own: at most 168
+// registers a thread, so that twelve warps of the 3D degree-3 basis (about
+// 16 KB of shared memory each) fit on an SM.  The warps of a block take
+// consecutive targets (shared neighbours in L1) and their scratch slots are
+// adjacent.
 template <int D, int M, int MRA, int KS>
-__global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const DfxTab tab) {
+__global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const DfxTab tab) {
   using Dm = DfxDims<D, M>;
   constexpr int Q = Dm::Q, N = Dm::N, NTOP = Dm::NTOP, N0 = Dm::N0, L = Dm::L, LC = Dm::LC;
   constexpr int NT = (N + 31) / 32;     // slots of an N-vector (solve layout)
@@ -361,18 +400,22 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const unsigned mask = 0xffffffffu;
   unsigned char* base = smem + (size_t)wid * Lay::BYTES;
-  ff* Aff = reinterpret_cast<ff*>(base + Lay::AFF);
-  ff* S0 = reinterpret_cast<ff*>(base + Lay::S);  // s0 = B y0 (float-float)
-  float* RA = reinterpret_cast<float*>(base + Lay::S);  // R_A, packed rows (before s0 exists)
-  float* Y0 = reinterpret_cast<float*>(base + Lay::Y);  // y0 of pass 0 (FP32)
+  ff* Aff = reinterpret_cast<ff*>(base + Lay::AFF);      // phases A and D (see DfxLay)
+  ff* SG = reinterpret_cast<ff*>(base + Lay::S);         // a group of s0 = B y0 (float-float)
+  float* RA = reinterpret_cast<float*>(base + Lay::S);   // R_A, packed rows (phase B)
+  float* Y0 = reinterpret_cast<float*>(base + Lay::S);   // y0 of pass 0 (FP32; phases C, D)
   ff* UV = reinterpret_cast<ff*>(base + Lay::UV);
+  // the factor block: phases B, C and E
   float* RG = reinterpret_cast<float*>(base + Lay::RG);
   float* IDG = reinterpret_cast<float*>(base + Lay::IDG);
   float* V1 = reinterpret_cast<float*>(base + Lay::V1);
   float* V2 = reinterpret_cast<float*>(base + Lay::V2);
   float* TAUG = reinterpret_cast<float*>(base + Lay::TAUG);
   float* TAUA = reinterpret_cast<float*>(base + Lay::TAUA);
-  // sqrt(W_j) = A[j][0]: the first monomial is the constant
+  float4* gA = reinterpret_cast<float4*>(j.dscratch + ((size_t)blockIdx.x * wpb + wid) * Lay::SLOT);
+  float4* gF = gA + Lay::GF / 16;
+  float2* gS = reinterpret_cast<float2*>(gA + Lay::GS / 16);  // s0, ff [LC][LDA]
+  float2* gW = reinterpret_cast<float2*>(gA + Lay::GW / 16);  // sqrt(W), ff [LDA]
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
   const float tolf = (float)j.tol;
@@ -434,6 +477,7 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
         for (int pp = 1; pp < half_p; ++pp) sw = sw * u;
       }
       gmls_gen::BasisEval<GMLS_BASIS_SCALAR, D, M>::template run<ff>(xi, Aff + q, LDA, sw);
+      __stcg(gW + q, make_float2(sw.h, sw.l));  // the constant column of A
     }
     __syncwarp(mask);
     float a[MRA][Q];
@@ -443,6 +487,9 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
 #pragma unroll
       for (int g = 0; g < Q; ++g) a[tt][g] = q < k ? Aff[g * LDA + q].h : 0.0f;
     }
+    // A waits in global memory while the factor block takes its place
+    dfx_park<Lay::ABYTES>(gA, reinterpret_cast<const float4*>(Aff), lane);
+    __syncwarp(mask);
 
     // ---- 2. A = Q_A R_A in registers; R_A row r (lane r) packed into RA
     qr_columns<32, MRA, Q>(a, TAUA, lane, mask, std::make_integer_sequence<int, Q>{});
@@ -637,6 +684,10 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
     bool conv = false;
     float z[LC][MRA];
     if (!ill && j.max_refine >= 1) {
+      // the factor block out, A back in
+      dfx_park<Lay::FAC>(gF, reinterpret_cast<const float4*>(RG), lane);
+      __syncwarp(mask);
+      dfx_unpark<Lay::ABYTES>(reinterpret_cast<float4*>(Aff), gA, lane);
       // u = C y0 (exact in float-float: sums of at most d FP32 values)
       for (int e = lane; e < LC * Q; e += 32) {
         const int lc = e / Q, g = e - lc * Q, l = lc / D, c = lc - l * D;
@@ -655,40 +706,46 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
         UV[e] = uv;
       }
       __syncwarp(mask);
-      // s0 = B y0: row (l, c, j) = A_j . u_(l,c), compensated, into S0
+      // per group of HG (l, c) pairs: s0 = B y0, row (l, c, j) = A_j . u_(l,c)
+      // (compensated; into the buffer and the slot), then v_(l,c) = A^T s0_(l,c)
+      // over it (four interleaved compensated chains per entry), in place of u
+      constexpr int HG = Lay::HG;
 #pragma unroll 1
-      for (int q = lane; q < k; q += 32) {
-        ff ar[Q];
-#pragma unroll
-        for (int g = 0; g < Q; ++g) ar[g] = Aff[g * LDA + q];
-        constexpr int HG = LC % 3 == 0 ? 3 : 2;
-        static_assert(LC % HG == 0, "(l, c) pairs in groups");
+      for (int lg = 0; lg < LC; lg += HG) {
 #pragma unroll 1
-        for (int lc = 0; lc < LC; lc += HG) {
+        for (int q = lane; q < k; q += 32) {
           Dot2 acc[HG];
 #pragma unroll
-          for (int g = 0; g < Q; ++g)
+          for (int g = 0; g < Q; ++g) {
+            const ff ag = Aff[g * LDA + q];
 #pragma unroll
-            for (int h = 0; h < HG; ++h) acc[h].add_prod(ar[g], UV[(lc + h) * Q + g]);
+            for (int h = 0; h < HG; ++h) acc[h].add_prod(ag, UV[(lg + h) * Q + g]);
+          }
 #pragma unroll
-          for (int h = 0; h < HG; ++h) S0[(lc + h) * LDA + q] = acc[h].value();
+          for (int h = 0; h < HG; ++h) {
+            const ff sv = acc[h].value();
+            SG[h * LDA + q] = sv;
+            __stcg(gS + (lg + h) * LDA + q, make_float2(sv.h, sv.l));
+          }
         }
-      }
-      __syncwarp(mask);
-      // v = (I (x) A^T) s0, four interleaved compensated chains per entry
-      for (int e = lane; e < LC * Q; e += 32) {
-        const int lc = e / Q, g = e - lc * Q;
-        const ff* ag = Aff + g * LDA;
-        const ff* sl = S0 + lc * LDA;
-        Dot2 c4[4];
-        int q = 0;
-        for (; q + 3 < k; q += 4) {
+        __syncwarp(mask);
+        for (int e = lane; e < HG * Q; e += 32) {
+          const int h = e / Q, g = e - h * Q;
+          const ff* ag = Aff + g * LDA;
+          const ff* sl = SG + h * LDA;
+          Dot2 c4[4];
+          int q = 0;
+          for (; q + 3 < k; q += 4) {
 #pragma unroll
-          for (int h = 0; h < 4; ++h) c4[h].add_prod(ag[q + h], sl[q + h]);
+            for (int i = 0; i < 4; ++i) c4[i].add_prod(ag[q + i], sl[q + i]);
+          }
+          for (; q < k; ++q) c4[0].add_prod(ag[q], sl[q]);
+          UV[(lg + h) * Q + g] = (c4[0].value() + c4[1].value()) + (c4[2].value() + c4[3].value());
         }
-        for (; q < k; ++q) c4[0].add_prod(ag[q], sl[q]);
-        UV[e] = (c4[0].value() + c4[1].value()) + (c4[2].value() + c4[3].value());
+        __syncwarp(mask);
       }
+      // A is no longer needed: the factor block back
+      dfx_unpark<Lay::FAC>(reinterpret_cast<float4*>(RG), gF, lane);
       __syncwarp(mask);
       // g = lambda - C^T v in the solve layout
 #pragma unroll
@@ -713,7 +770,8 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);  // delta = R^-T g
       apply_qb(w, z);                                      // ds = Q_B [delta; 0]
       // error left ~ |ds| times the contraction factor, estimated by the
-      // relative size of the correction
+      // relative size of the correction (this lane's rows of s0 come back
+      // from the slot)
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
       for (int lc = 0; lc < LC; ++lc)
@@ -721,8 +779,9 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
         for (int tt = 0; tt < MRA; ++tt) {
           const int q = lane + 32 * tt;
           if (q < k) {
+            const float s0h = __ldcg(gS + lc * LDA + q).x;
             dmax = fmaxf(dmax, fabsf(z[lc][tt]));
-            smax = fmaxf(smax, fabsf(S0[lc * LDA + q].h + z[lc][tt]));
+            smax = fmaxf(smax, fabsf(s0h + z[lc][tt]));
           }
         }
       dmax = wmax<32>(dmax, mask);
@@ -754,16 +813,17 @@ __global__ void __launch_bounds__(256, 1) stencil_dfx_kernel(StencilJob j, const
       for (int tt = 0; tt < MRA; ++tt) {
         const int q = lane + 32 * tt;
         if (q < k) {
-          const ff swq = Aff[q];  // sqrt(W_q): the constant column of A
+          const float2 swv = __ldcg(gW + q);
+          const ff swq(swv.x, swv.y);
 #pragma unroll
           for (int l = 0; l < L; ++l)
 #pragma unroll
             for (int c = 0; c < D; ++c) {
               const int rr = l - src;
               if (rr >= 0 && rr < R && c < C) {
-                const ff sv = add_f(S0[(l * D + c) * LDA + q], z[l * D + c][tt]);
-                const ff wv = sv * swq;
-                wo[((int64_t)rr * k + q) * C + c] = to_double(ff(sgn * wv.h, sgn * wv.l));
+                const float2 s0v = __ldcg(gS + (l * D + c) * LDA + q);
+                const ff wv = add_f(ff(s0v.x, s0v.y), z[l * D + c][tt]) * swq;
+                __stcs(wo + ((int64_t)rr * k + q) * C + c, to_double(ff(sgn * wv.h, sgn * wv.l)));
               }
             }
         }
@@ -784,10 +844,14 @@ struct DfxEntry {
   int dim, deg, mra, ks;
   const void* fn;
   size_t bytes;  // shared memory per warp
+  size_t slot;   // global scratch per warp
   DfxTab (*tab)();
 };
 
-#define GMLS_DFX(D, M, MRA, KS) \
-  DfxEntry { D, M, MRA, KS, (const void*)stencil_dfx_kernel<D, M, MRA, KS>, DfxLay<D, M, KS>::BYTES, &make_dfx_tab<D, M> }
+#define GMLS_DFX(D, M, MRA, KS)                                                                              \
+  DfxEntry {                                                                                                 \
+    D, M, MRA, KS, (const void*)stencil_dfx_kernel<D, M, MRA, KS>, DfxLay<D, M, KS>::BYTES,                  \
+        DfxLay<D, M, KS>::SLOT, &make_dfx_tab<D, M>                                                          \
+  }
 
 }  // namespace gmls
