@@ -71,11 +71,15 @@ cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, i
     if (e.kind == j.kind && e.dim == j.dim && e.deg == j.degree && e.mr == mr && e.L == j.L && e.hw == hw) ent = &e;
   });
   if (!ent) return cudaErrorInvalidValue;
-  // warps per block: the choice with the most resident groups per SM
+  // warps per block (up to the kernel's limit): the choice with the most
+  // resident groups per SM, the largest block among equals
   const int gpw = 32 / hw;  // groups (targets in flight) per warp
   const size_t per_group = ent->bytes(j.L);
+  cudaFuncAttributes fa;
+  cudaError_t ea = cudaFuncGetAttributes(&fa, ent->fn);
+  if (ea != cudaSuccess) return ea;
   int best_w = 1, best_groups = 0, best_blocks = 1;
-  for (int w = 1; w <= 4; ++w) {
+  for (int w = 1; w <= 12 && 32 * w <= fa.maxThreadsPerBlock; ++w) {
     const size_t smem = (size_t)w * gpw * per_group;
     if (smem > 227 * 1024) break;
     cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -270,15 +270,18 @@ __device__ __forceinline__ void solve_r_lanes(const float* Rs, const float* idg,
   }
 }
 
-// Small register tiles keep three 4-warp blocks resident (at most 168
-// registers per thread); larger ones are left to the register allocator.
+// Block size limit: small register tiles keep twelve warps resident (at
+// most 168 registers per thread, blocks of up to 12 warps); larger ones are
+// left to the register allocator (blocks of up to 8 warps).  The launcher
+// takes the largest block among the shapes with the most resident warps, so
+// that an SM works on consecutive targets (neighbours shared in L1).
 template <int HW, int MR, int N, int L>
-constexpr int fast_min_blocks() {
-  return MR * N * L <= 90 ? 3 : 1;
+constexpr int fast_max_threads() {
+  return MR * N * L <= 90 ? 384 : 256;
 }
 
 template <int KIND, int D, int DEG, int MR, int L, int HW>
-__global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()))
+__global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()), 1)
     stencil_fast_kernel(StencilJob j) {
   constexpr int N = gmls_gen::basis_size(KIND, D, DEG);
   // refinement scheme: one Q application from s0 = B y0 (scalar and staggered
@@ -746,7 +749,7 @@ __global__ void __launch_bounds__(128, (fast_min_blocks<HW, MR, gmls_gen::basis_
             if (e == self) continue;  // written below
             others += val;
           }
-          wo[(int64_t)rr * per_row + e] = val;
+          __stcs(wo + (int64_t)rr * per_row + e, val);  // written once: evict first
         }
         if constexpr (KIND == GMLS_BASIS_STAGGERED) {
 #pragma unroll
