@@ -187,13 +187,19 @@ struct DfxLay {
   static constexpr size_t UV = al16(S + sizeof(ff) * HG * LDA);              // ff [LC][Q] u = C y0, then v = A^T s0
   static constexpr size_t BYTES = al16(UV + sizeof(ff) * LC * Q);
   // global scratch of one warp: A, the factor block, s0 ff [LC][LDA], sqrt(W) ff [LDA]
+  static constexpr size_t S0BYTES = al16(sizeof(ff) * LC * LDA), SWBYTES = al16(sizeof(ff) * LDA);
   static constexpr size_t GF = ABYTES;
   static constexpr size_t GS = GF + FAC;
-  static constexpr size_t GW = GS + al16(sizeof(ff) * LC * LDA);
-  static constexpr size_t SLOT = (GW + sizeof(ff) * LDA + 255) & ~size_t(255);
+  static constexpr size_t GW = GS + S0BYTES;
+  static constexpr size_t SLOT = (GW + SWBYTES + 255) & ~size_t(255);
+  // s0 and sqrt(W) back for the store (end of phase E, when the factor
+  // block, the s0 buffer and u / v are no longer needed)
+  static constexpr size_t FS0 = 0, FSW = S0BYTES;
+  static_assert(S0BYTES + SWBYTES <= BYTES, "s0 and sqrt(W) fit in the warp's shared memory");
   static_assert(LC % HG == 0, "(l, c) pairs in groups");
   static_assert(sizeof(float) * Q * (Q + 1) / 2 <= sizeof(ff) * HG * LDA, "R_A must fit in the s buffer");
   static_assert(sizeof(float) * L * N <= sizeof(ff) * HG * LDA, "y0 must fit in the s buffer");
+  static_assert(D <= HG, "the offsets (ff [D][LDA]) must fit in the s buffer");
 };
 
 // copy of a 16-byte-aligned block by the 32 lanes of a warp, global side
@@ -270,11 +276,20 @@ __device__ __forceinline__ void dfx_apply_qa(const float (&a)[MR][Q], const floa
 template <int N, int L, int NT, bool TRANS>
 __device__ __forceinline__ void dfx_solve(const float* Rs, const float* idg, float (&w)[L][NT], int lane,
                                           unsigned mask) {
+  // R^T: row i of R (packed from rpk(i, 0)) updates entries p > i;
+  // R: column i, entry (p, i) at rpk(p, 0) + i for this lane's rows p
+  int pb[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int p = lane + 32 * t;
+    pb[t] = rpk<N>(p < N ? p : N - 1, 0);
+  }
 #pragma unroll 1
   for (int s = 0; s < N; ++s) {
     const int i = TRANS ? s : N - 1 - s;
     const float inv = idg[i];
     const int src = i & 31, sl = i >> 5;
+    const int ri = TRANS ? rpk<N>(i, 0) : 0;
     float yi[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) yi[l] = __shfl_sync(mask, dfx_get_slot<NT>(w[l], sl), src) * inv;
@@ -282,7 +297,7 @@ __device__ __forceinline__ void dfx_solve(const float* Rs, const float* idg, flo
     for (int t = 0; t < NT; ++t) {
       const int p = lane + 32 * t;
       const bool upd = TRANS ? (p > i && p < N) : (p < i);
-      const float r = upd ? Rs[TRANS ? rpk<N>(i, p) : rpk<N>(p, i)] : 0.0f;
+      const float r = upd ? Rs[TRANS ? ri + p : pb[t] + i] : 0.0f;
 #pragma unroll
       for (int l = 0; l < L; ++l) {
         if (p == i) w[l][t] = yi[l];
@@ -361,13 +376,23 @@ __device__ __forceinline__ void dfx_load_row(const float* row, float (&v)[Q]) {
 // Householder reflector of a column held by one lane: alpha the diagonal
 // entry, x[r] for r in (lo, Q) the entries below it.  Writes the reflector
 // vector (vout[r]: 1 at r == lo when lo >= 0, zero above), tau and beta.
+// c + v . x in four interleaved chains
+template <int Q>
+__device__ __forceinline__ float dfx_dot4(const float (&v)[Q], const float (&x)[Q], float c) {
+  float d[4] = {c, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int r = 0; r < Q; ++r) d[r & 3] = fmaf(v[r], x[r], d[r & 3]);
+  return (d[0] + d[1]) + (d[2] + d[3]);
+}
+
 template <int Q>
 __device__ __forceinline__ void dfx_reflect(float alpha, const float (&x)[Q], int lo, float* vout, float* tau_out,
                                             float* beta_out) {
-  float sig = 0.0f;
+  float sg[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // four chains (latency)
 #pragma unroll
   for (int r = 0; r < Q; ++r)
-    if (r > lo) sig = fmaf(x[r], x[r], sig);
+    if (r > lo) sg[r & 3] = fmaf(x[r], x[r], sg[r & 3]);
+  const float sig = (sg[0] + sg[1]) + (sg[2] + sg[3]);
   float tk = 0.0f, beta = alpha, scale = 0.0f;
   if (sig > 0.0f) {
     const float nrm = sqrtf(fmaf(alpha, alpha, sig));
@@ -416,6 +441,8 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
   float4* gF = gA + Lay::GF / 16;
   float2* gS = reinterpret_cast<float2*>(gA + Lay::GS / 16);  // s0, ff [LC][LDA]
   float2* gW = reinterpret_cast<float2*>(gA + Lay::GW / 16);  // sqrt(W), ff [LDA]
+  const ff* S0F = reinterpret_cast<const ff*>(base + Lay::FS0);  // phase E: s0 (all pairs)
+  const ff* SWF = reinterpret_cast<const ff*>(base + Lay::FSW);  // phase E: sqrt(W)
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
   const float tolf = (float)j.tol;
@@ -459,14 +486,33 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
 #pragma unroll
     for (int c = 0; c < D; ++c) xt[c] = j.x[c * n + t];
     const int half_p = j.wpow_half;
+    // offsets x_j - x_T of this lane's rows into the s0 buffer (the loads of
+    // all rows in flight together)
+    ff* DX = SG;  // ff [D][LDA]
+    {
+      double xv[MRA][D];
+#pragma unroll
+      for (int tt = 0; tt < MRA; ++tt) {
+        const int q = lane + 32 * tt;
+        const int32_t jj = q < k ? j.idx[o0 + q] : (int32_t)t;
+#pragma unroll
+        for (int c = 0; c < D; ++c) xv[tt][c] = j.x[c * n + jj];
+      }
+#pragma unroll
+      for (int tt = 0; tt < MRA; ++tt) {
+        const int q = lane + 32 * tt;
+        if (q < k)
+#pragma unroll
+          for (int c = 0; c < D; ++c) DX[c * LDA + q] = diff_ff(xv[tt][c], xt[c]);
+      }
+    }
 #pragma unroll 1
     for (int q = lane; q < k; q += 32) {
-      const int32_t jj = j.idx[o0 + q];
       ff dx[3], xi[3];
       ff r2(0.f, 0.f);
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        dx[c] = diff_ff(j.x[c * n + jj], xt[c]);
+        dx[c] = DX[c * LDA + q];
         xi[c] = dx[c] * inv_eps;
         r2 = r2 + dx[c] * dx[c];
       }
@@ -539,10 +585,7 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
           const int cb = col / Q, cg = col - cb * Q;
           float tc = 0.0f;  // T[jst][col]: R_A row al within the same block
           if (col < NTOP && cb == blk && cg >= al) tc = RA[rpk<Q>(al, cg)];
-          float dot = tc;
-#pragma unroll
-          for (int r = 0; r < Q; ++r) dot = fmaf(v[r], xg[s][r], dot);
-          dot *= tk;
+          const float dot = dfx_dot4<Q>(v, xg[s], tc) * tk;
           RG[rpk<N>(jst, col)] = tc - dot;
 #pragma unroll
           for (int r = 0; r < Q; ++r) xg[s][r] = fmaf(-dot, v[r], xg[s][r]);
@@ -579,10 +622,7 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
       for (int s = 0; s < 2; ++s) {
         const int col = lane + 32 * s;
         if (col > colk && col < N) {
-          float dot = 0.0f;
-#pragma unroll
-          for (int r = 0; r < Q; ++r) dot = fmaf(v[r], xg[s][r], dot);
-          dot *= tk;
+          const float dot = dfx_dot4<Q>(v, xg[s], 0.0f) * tk;
           float rrow = 0.0f;
 #pragma unroll
           for (int r = 0; r < Q; ++r) {
@@ -769,9 +809,14 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
         }
       dfx_solve<N, L, NT, true>(RG, IDG, w, lane, mask);  // delta = R^-T g
       apply_qb(w, z);                                      // ds = Q_B [delta; 0]
+      // s0 and sqrt(W) back from the slot in one batch of loads, in place
+      // of the factor block
+      __syncwarp(mask);
+      dfx_unpark<Lay::S0BYTES>(reinterpret_cast<float4*>(base + Lay::FS0), reinterpret_cast<const float4*>(gS), lane);
+      dfx_unpark<Lay::SWBYTES>(reinterpret_cast<float4*>(base + Lay::FSW), reinterpret_cast<const float4*>(gW), lane);
+      __syncwarp(mask);
       // error left ~ |ds| times the contraction factor, estimated by the
-      // relative size of the correction (this lane's rows of s0 come back
-      // from the slot)
+      // relative size of the correction
       float dmax = 0.0f, smax = 0.0f;
 #pragma unroll
       for (int lc = 0; lc < LC; ++lc)
@@ -779,7 +824,7 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
         for (int tt = 0; tt < MRA; ++tt) {
           const int q = lane + 32 * tt;
           if (q < k) {
-            const float s0h = __ldcg(gS + lc * LDA + q).x;
+            const float s0h = S0F[lc * LDA + q].h;
             dmax = fmaxf(dmax, fabsf(z[lc][tt]));
             smax = fmaxf(smax, fabsf(s0h + z[lc][tt]));
           }
@@ -813,16 +858,14 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
       for (int tt = 0; tt < MRA; ++tt) {
         const int q = lane + 32 * tt;
         if (q < k) {
-          const float2 swv = __ldcg(gW + q);
-          const ff swq(swv.x, swv.y);
+          const ff swq = SWF[q];
 #pragma unroll
           for (int l = 0; l < L; ++l)
 #pragma unroll
             for (int c = 0; c < D; ++c) {
               const int rr = l - src;
               if (rr >= 0 && rr < R && c < C) {
-                const float2 s0v = __ldcg(gS + (l * D + c) * LDA + q);
-                const ff wv = add_f(ff(s0v.x, s0v.y), z[l * D + c][tt]) * swq;
+                const ff wv = add_f(S0F[(l * D + c) * LDA + q], z[l * D + c][tt]) * swq;
                 __stcs(wo + ((int64_t)rr * k + q) * C + c, to_double(ff(sgn * wv.h, sgn * wv.l)));
               }
             }
