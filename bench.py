@@ -101,7 +101,7 @@ def src_sha(*names):
 # DRAM bytes (read + write) per launch measured by ncu on the timed launch
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass), with the hash of
 # the kernel sources it was taken on; a different hash reports null
-DFX_TRAFFIC = {"bytes": 696868608 + 10150222848, "sha": "f06bdddf6ff6dc3a",
+DFX_TRAFFIC = {"bytes": 700712704 + 10456942080, "sha": "a32a567edc57bc15",
                "sources": ("stencil_dfx.cuh", "stencil_fast.cuh", "ff.cuh"),
                "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none --nvtx "
                           "--nvtx-include porous_step/ -k regex:stencil_dfx -c 1 python bench.py --no-secondary "

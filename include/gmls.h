@@ -203,6 +203,11 @@ gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, dou
  * neighbour offsets), ordered [row][neighbour][component], neighbours in list
  * order.  Weight w satisfies, for every polynomial field q of the basis span,
  * sum w q(x_j) = (L q)(x_T) (plus beta * h for Neumann targets).
+ * Besides the weights, a launch takes temporary scratch from the arena for
+ * the duration of the kernel: the factored divergence-free kernel about
+ * 29 KB per resident warp (3D degree 3: 152 SMs x 12 warps, 53 MB), the
+ * shared-memory kernel its global tiles for shapes too large for shared
+ * memory; GMLS_ENOMEM when the arena cannot hold them.
  */
 gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_params* params, int64_t* stencil_id);
 

@@ -2,6 +2,8 @@
 // stencil kernel (stencil_dfx.cuh).
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "stencil_dfx.cuh"
 
 namespace gmls {
@@ -55,6 +57,17 @@ cudaError_t dfx_launch_shape(const StencilJob& j, int sms, DfxShape* s) {
   s->smem = (size_t)best_w * ent->bytes;
   s->scratch = (size_t)s->grid * best_w * ent->slot;
   return cudaSuccess;
+}
+
+size_t dfx_scratch_bytes(int dim, int deg, int64_t n_tgt, int sms) {
+  StencilJob j;
+  std::memset(&j, 0, sizeof(j));
+  j.dim = dim;
+  j.degree = deg;
+  j.L = dim;
+  j.n_tgt = n_tgt;
+  DfxShape s;
+  return dfx_launch_shape(j, sms, &s) == cudaSuccess ? s.scratch : 0;
 }
 
 cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, const DfxShape& s) {

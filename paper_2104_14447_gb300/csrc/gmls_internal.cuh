@@ -237,6 +237,8 @@ struct DfxShape {
   size_t scratch;   // global bytes the launch needs in StencilJob::dscratch
 };
 cudaError_t dfx_launch_shape(const StencilJob& j, int sms, DfxShape* s);
+// global scratch of a launch over n_tgt targets (0 if the shape is not instantiated)
+size_t dfx_scratch_bytes(int dim, int deg, int64_t n_tgt, int sms);
 cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, const DfxShape& s);
 
 // -------------------------------------------------------------------- CSR

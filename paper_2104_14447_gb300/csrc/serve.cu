@@ -35,6 +35,8 @@
 namespace gmls {
 void set_global_error(const std::string& msg);
 int device_sm_count();
+bool dfx_path_available(int dim, int deg, int kmax, int L);
+size_t dfx_scratch_bytes(int dim, int deg, int64_t n_tgt, int sms);
 }
 
 namespace {
@@ -78,6 +80,9 @@ size_t estimate_bytes(const gmls_request& r) {
   const size_t rows = (size_t)k * nc;
   size_t tiles = 0;
   if ((size_t)nb * rows * 12 > 100 * 1024) tiles = (size_t)gmls::device_sm_count() * 4 * ((size_t)nb * rows * 12 + 4096);
+  // per-warp slots of the factored divergence-free kernel (during its launch)
+  if (r.basis == GMLS_BASIS_DIVFREE && gmls::dfx_path_available((int)d, r.degree, (int)k, (int)d))
+    tiles += gmls::dfx_scratch_bytes((int)d, r.degree, n, gmls::device_sm_count()) + 4096;
   const size_t total = cloud + nbrs + stencils + tiles;
   return total + total / 8 + (16u << 20);
 }

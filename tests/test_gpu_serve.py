@@ -112,3 +112,16 @@ def test_request_larger_than_arena_fails_cleanly(built):
         srv.wait(t, 60000)
     srv.release(t)
     srv.close()
+
+
+def test_divfree_request_slice_covers_kernel_scratch(built):
+    """A 3D degree-3 divergence-free request runs through the factored kernel,
+    whose per-warp scratch (tens of MB) comes out of the request's slice."""
+    srv = gmls.Server(0, arena_bytes=1 << 30, streams=1, max_inflight=1)
+    x = inputs.jittered_grid(3, 24, seed=5)  # 13,824 points
+    t = srv.submit(x, gmls.DIVFREE, 3, 80, [gmls.VEC_LAPLACIAN])
+    assert srv.wait(t, 60000)
+    w = srv.result(t, gmls.X_WEIGHTS, torch.float64, gmls.VEC_LAPLACIAN).numpy()
+    assert w.size == x.shape[1] * 80 * 9 and np.all(np.isfinite(w))
+    srv.release(t)
+    srv.close()
