@@ -385,7 +385,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     for (int v : generic_candidates(ld, nmax, refine)) cands.push_back(v);
     for (int c : cands) {
       float ms = time_launch(ctx, [&]() {
-        if (refine) cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream);
+        if (refine) cudaMemsetAsync(j.fb_count, 0, 3 * sizeof(int32_t), ctx->stream);
         if (c < 0)
           launch_fast(js, c);
         else
@@ -404,11 +404,26 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     choice = okdfx ? -3 : hw_pref == 16 ? -2 : hw_pref == 32 ? -1 : heuristic_variant(ld, nmax, refine);
   }
   if (choice == 0) return fail(ctx, GMLS_EINVAL, "gmls_stencils: tile does not fit in shared memory for this shape");
-  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 3 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
   if (choice < 0) {
-    CK(launch_fast(j, choice), "gmls_stencils fast launch");
-    // targets the register kernel handed off (Neumann rows, tile misfits):
-    // the shared-memory FP32 kernel, whose failures join the FP64 redo list
+    // Neumann targets: the register kernel's Neumann instantiation for this
+    // shape when there is one (a second launch over the list the first one
+    // fills), else the shared-memory kernel
+    const int mr = choice == -2 ? mr16 : mr32, hw = choice == -2 ? 16 : 32;
+    const bool neu_fast = choice != -3 && j.neu_items && fast_neu_available(dim, p->degree, mr, j.L, hw);
+    StencilJob jf = j;
+    if (!neu_fast) jf.neu_items = jf.neu_count = nullptr;
+    CK(launch_fast(jf, choice), "gmls_stencils fast launch");
+    if (neu_fast) {
+      StencilJob jn = jf;
+      jn.items = jf.neu_items;
+      jn.n_items = jf.neu_count;
+      jn.neu_items = jn.neu_count = nullptr;
+      CK(launch_stencils_fast(ctx->launch(), jn, mr, hw, sms, true), "gmls_stencils Neumann launch");
+    }
+    // targets the register kernels handed off (tile misfits; Neumann rows
+    // without a Neumann instantiation): the shared-memory FP32 kernel, whose
+    // failures join the FP64 redo list
     StencilJob jg = j;
     jg.items = j.gen_items;
     jg.n_items = j.gen_count;
@@ -521,7 +536,7 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
         int choice = 0;
         for (int v : generic_candidates(pl.ld[bi], pl.nmax[bi], refine)) {
           float ms = time_launch(ctx, [&]() {
-            if (refine) cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream);
+            if (refine) cudaMemsetAsync(j.fb_count, 0, 3 * sizeof(int32_t), ctx->stream);
             launch_single(ctx, js, v, pl.ld[bi], pl.nmax[bi], refine, counter, sms);
           });
           ctx->tune_log.push_back({key, v, ms});
@@ -555,7 +570,7 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
     release();
     return fail(ctx, GMLS_ENOMEM, "gmls_stencils: arena exhausted (global tiles)");
   }
-  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 2 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
+  if (refine) CK(cudaMemsetAsync(j.fb_count, 0, 3 * sizeof(int32_t), ctx->stream), "gmls_stencils memset");
   e = cudaMemsetAsync(counter, 0, sizeof(int32_t), ctx->stream);
   if (e == cudaSuccess) e = launch_stencils(L, j, pl, refine, smem, grid);
   ctx->arena.release(owned);
@@ -1045,8 +1060,10 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   int8_t* deg = p->degree_per_target ? arena_alloc<int8_t>(ctx, std::max<int64_t>(nt, 1)) : nullptr;
   const bool refine = p->precision == GMLS_FP32_REFINE;
   if (refine) {
-    s.fb_items = arena_alloc<int32_t>(ctx, 2 * std::max<int64_t>(nt, 1));  // FP64 redo list, then the
-    s.fb_count = arena_alloc<int32_t>(ctx, 2);                               // register kernel's hand-off
+    // the FP64 redo list, the register kernel's hand-off to the shared-memory
+    // kernel, and (Neumann targets) its list for the Neumann instantiation
+    s.fb_items = arena_alloc<int32_t>(ctx, (p->neumann ? 3 : 2) * std::max<int64_t>(nt, 1));
+    s.fb_count = arena_alloc<int32_t>(ctx, 3);
   }
   oom |= !s.beta || !s.status || !s.iters || (p->degree_per_target && !deg) || (refine && (!s.fb_items || !s.fb_count));
   auto release_all = [&]() {
@@ -1120,6 +1137,8 @@ gmls_status gmls_stencils(gmls_ctx* ctx, int64_t nbrs_id, const gmls_stencil_par
   j.fb_count = s.fb_count;
   j.gen_items = refine ? s.fb_items + std::max<int64_t>(nt, 1) : nullptr;
   j.gen_count = refine ? s.fb_count + 1 : nullptr;
+  j.neu_items = refine && p->neumann ? s.fb_items + 2 * std::max<int64_t>(nt, 1) : nullptr;
+  j.neu_count = refine && p->neumann ? s.fb_count + 2 : nullptr;
   j.ld = ld;
   j.nmax = nmax;
 

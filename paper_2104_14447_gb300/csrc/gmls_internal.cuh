@@ -168,8 +168,10 @@ struct StencilJob {
   double tol;
   int32_t* fb_items;       // FP32 path: targets to redo in FP64
   int32_t* fb_count;
-  int32_t* gen_items;      // register kernel: targets it does not cover (Neumann
-  int32_t* gen_count;      // constraint, tile misfit), for the shared-memory FP32 kernel
+  int32_t* gen_items;      // register kernel: targets it does not cover (tile
+  int32_t* gen_count;      // misfit), for the shared-memory FP32 kernel
+  int32_t* neu_items;      // register kernel: Neumann targets, for its Neumann
+  int32_t* neu_count;      // instantiation (NULL: they go to gen_items)
   int fallback_run;        // 1: this FP64 launch redoes targets of the FP32 path
   // launch shape
   int ld;                  // tile leading dimension (>= max rows)
@@ -227,7 +229,9 @@ cudaError_t launch_bucketing(const Launch& L, const BucketJob& b);
 bool fast_path_available(int kind, int dim, int deg, int rows, int L, int hw, int* mr_out);
 // the preferred group width for a shape: fewest padded row slots, then 32
 int fast_path_preferred(int kind, int dim, int deg, int rows, int L, int* mr_out);
-cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms);
+cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms, bool neu = false);
+// is the Neumann instantiation of this register-kernel shape built
+bool fast_neu_available(int dim, int deg, int mr, int L, int hw);
 // factored divergence-free kernel (dfx.cu): is (dim, degree) instantiated for
 // lists of at most kmax neighbours and L solve rows, and its launch
 bool dfx_path_available(int dim, int deg, int kmax, int L);

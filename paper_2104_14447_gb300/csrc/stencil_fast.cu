@@ -26,12 +26,14 @@ extern const FastEntry kFastG2[];
 extern const int kFastG2Count;
 extern const FastEntry kFastG3[];
 extern const int kFastG3Count;
+extern const FastEntry kFastN[];
+extern const int kFastNCount;
 
 struct FastTable {
   const FastEntry* e;
   const int* n;
 };
-static const FastTable kTables[] = {{kFastS2a, &kFastS2aCount}, {kFastS2b, &kFastS2bCount}, {kFastS2c, &kFastS2cCount}, {kFastS3a, &kFastS3aCount}, {kFastS3b, &kFastS3bCount}, {kFastD2, &kFastD2Count}, {kFastD3, &kFastD3Count}, {kFastS3c, &kFastS3cCount}, {kFastG2, &kFastG2Count}, {kFastG3, &kFastG3Count}};
+static const FastTable kTables[] = {{kFastS2a, &kFastS2aCount}, {kFastS2b, &kFastS2bCount}, {kFastS2c, &kFastS2cCount}, {kFastS3a, &kFastS3aCount}, {kFastS3b, &kFastS3bCount}, {kFastD2, &kFastD2Count}, {kFastD3, &kFastD3Count}, {kFastS3c, &kFastS3cCount}, {kFastG2, &kFastG2Count}, {kFastG3, &kFastG3Count}, {kFastN, &kFastNCount}};
 
 template <typename F>
 static void for_each_entry(F&& f) {
@@ -42,7 +44,7 @@ static void for_each_entry(F&& f) {
 bool fast_path_available(int kind, int dim, int deg, int rows, int L, int hw, int* mr_out) {
   int best = 0;
   for_each_entry([&](const FastEntry& e) {
-    if (e.kind == kind && e.dim == dim && e.deg == deg && e.L == L && e.hw == hw && e.hw * e.mr >= rows &&
+    if (!e.neu && e.kind == kind && e.dim == dim && e.deg == deg && e.L == L && e.hw == hw && e.hw * e.mr >= rows &&
         (best == 0 || e.mr < best))
       best = e.mr;
   });
@@ -65,10 +67,20 @@ int fast_path_preferred(int kind, int dim, int deg, int rows, int L, int* mr_out
   return 0;
 }
 
-cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms) {
+bool fast_neu_available(int dim, int deg, int mr, int L, int hw) {
+  bool found = false;
+  for_each_entry([&](const FastEntry& e) {
+    found |= e.neu && e.dim == dim && e.deg == deg && e.mr == mr && e.L == L && e.hw == hw;
+  });
+  return found;
+}
+
+cudaError_t launch_stencils_fast(const Launch& L, const StencilJob& j, int mr, int hw, int sms, bool neu) {
   const FastEntry* ent = nullptr;
   for_each_entry([&](const FastEntry& e) {
-    if (e.kind == j.kind && e.dim == j.dim && e.deg == j.degree && e.mr == mr && e.L == j.L && e.hw == hw) ent = &e;
+    if (e.neu == neu && e.kind == j.kind && e.dim == j.dim && e.deg == j.degree && e.mr == mr && e.L == j.L &&
+        e.hw == hw)
+      ent = &e;
   });
   if (!ent) return cudaErrorInvalidValue;
   // warps per block (up to the kernel's limit): the choice with the most

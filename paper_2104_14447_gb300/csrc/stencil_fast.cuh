@@ -24,11 +24,16 @@
 //    compensated float-float and the correction from the FP32 factors;
 //  * w = sqrt(W) s is rounded to FP64 only when stored.
 //
-// Targets this path does not cover (Neumann constraint, a basis size other
-// than the instantiation's, more rows than the tile holds) are appended to the
-// list of the shared-memory FP32 kernel; those whose FP32 factor is
-// ill-conditioned or whose refinement misses its tolerance to the redo list
-// of the FP64 kernel.
+// Neumann targets (Sec. 2.3, scalar basis) run in their own instantiation
+// (NEU): the constraint F^T c = h, F = grad p(x_T)^T n, is eliminated with a
+// reflector H_F on the linear columns, the pivot column moves to the end and
+// the least-squares problem runs on the other N - 1 columns; beta =
+// (lambda~_piv - s^T p~) / rho.  The plain instantiation appends them to the
+// Neumann list when the launch has one.  Targets this path does not cover (a
+// basis size other than the instantiation's, more rows than the tile holds)
+// are appended to the list of the shared-memory FP32 kernel; those whose FP32
+// factor is ill-conditioned or whose refinement misses its tolerance to the
+// redo list of the FP64 kernel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -42,7 +47,7 @@ namespace gmls {
 
 // Shared memory of one group (one target in flight), kept small so that
 // twelve warps fit on an SM for the 96 x 20 systems.
-template <int HW, int MR, int N, int NC>
+template <int HW, int MR, int N, int NC, bool NEU = false>
 struct FastLay {
   static constexpr int LD = HW * MR + 1;  // odd: column walks by different lanes avoid bank conflicts
   static constexpr int NQ = (HW * MR + NC - 1) / NC;            // neighbour slots
@@ -57,7 +62,12 @@ struct FastLay {
   // the rest depends on the number of solve rows L
   __host__ __device__ static size_t Y(int L) { return S + sizeof(ff) * L * LD; }      // ff [L][N]
   __host__ __device__ static size_t G(int L) { return Y(L) + sizeof(ff) * L * N; }    // float [L][N]
-  __host__ __device__ static size_t bytes(int L) { return (G(L) + sizeof(float) * L * N + 15) & ~size_t(15); }
+  // Neumann targets: lambda~ ff [L][N] after the reflection and the pivot
+  // swap (entry N - 1: lambda~_piv), then rho
+  __host__ __device__ static size_t LAMT(int L) { return (G(L) + sizeof(float) * L * N + 15) & ~size_t(15); }
+  __host__ __device__ static size_t bytes(int L) {
+    return NEU ? ((LAMT(L) + sizeof(ff) * (L * N + 1) + 15) & ~size_t(15)) : LAMT(L);
+  }
 };
 
 // position of R(i, c), c >= i, in the packed rows of an N-column factor
@@ -280,10 +290,12 @@ constexpr int fast_max_threads() {
   return MR * N * L <= 90 ? 384 : 256;
 }
 
-template <int KIND, int D, int DEG, int MR, int L, int HW>
+template <int KIND, int D, int DEG, int MR, int L, int HW, bool NEU = false>
 __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()), 1)
     stencil_fast_kernel(StencilJob j) {
-  constexpr int N = gmls_gen::basis_size(KIND, D, DEG);
+  constexpr int NB = gmls_gen::basis_size(KIND, D, DEG);  // basis functions
+  constexpr int N = NB - (NEU ? 1 : 0);                    // least-squares columns
+  static_assert(!NEU || KIND == GMLS_BASIS_SCALAR, "the Neumann constraint is for the scalar basis");
   // refinement scheme: one Q application from s0 = B y0 (scalar and staggered
   // bases, measured faster there), or Bjorck steps from s0 = Q [R^-T lambda; 0]
   // with both residuals (divergence-free: its one-Q variant was slower, with
@@ -292,7 +304,7 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
   constexpr int NC = (KIND == GMLS_BASIS_DIVFREE) ? D : 1;  // components per neighbour (staggered: 1)
   constexpr int ROWS = HW * MR;
   constexpr int NT = (N + HW - 1) / HW;
-  using Lay = FastLay<HW, MR, N, NC>;
+  using Lay = FastLay<HW, MR, NB, NC, NEU>;
   constexpr int LD = Lay::LD;
   extern __shared__ __align__(16) unsigned char smem[];
   const int grp = threadIdx.x / HW, lane = threadIdx.x & (HW - 1);
@@ -309,12 +321,19 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
   float* TAUs = reinterpret_cast<float*>(base + Lay::TAU);
   float* Gs = reinterpret_cast<float*>(base + Lay::G(L));
   // functional row l at basis column c (float-float): integer coefficient
-  // times eps^-order
-  auto lam = [&](int l, int c) {
+  // times eps^-order; Neumann targets read lambda~ from its table
+  auto lam0 = [&](int l, int c) {
     ff f(gmls_gen::lam_coef_f(KIND, D, DEG, j.lam_fn[l], j.lam_row[l], c), 0.0f);
     const ff ie = IEPSs[0];
     for (int p = 0; p < j.lam_order[l]; ++p) f = f * ie;
     return f;
+  };
+  ff* LAMT = NEU ? reinterpret_cast<ff*>(base + Lay::LAMT(L)) : nullptr;
+  auto lam = [&](int l, int c) {
+    if constexpr (NEU)
+      return LAMT[l * NB + c];
+    else
+      return lam0(l, c);
   };
   const int64_t n = j.n;
   const int64_t n_items = j.items ? (int64_t)(*j.n_items) : j.n_tgt;
@@ -327,7 +346,7 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
     const int k = (int)(j.off[to + 1] - o0);
     const int M = k * NC;
     uint8_t st = j.nbr_status ? j.nbr_status[to] : 0;
-    const bool neu = j.neumann && j.bflag && j.bflag[t];
+    const bool neu = KIND == GMLS_BASIS_SCALAR && j.neumann && j.bflag && j.bflag[t] && j.normals;
     const bool too_few = (st & GMLS_T_TOO_FEW_NEIGHBOURS) || k <= 0 || !(j.eps[to] > 0.0);
     // staggered basis: the weights act on p_j - p(x_T); the target's own
     // entry (a zero row of the tile) later takes minus the sum of the others
@@ -344,12 +363,18 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
       }
     }
     const bool no_self = KIND == GMLS_BASIS_STAGGERED && !too_few && self < 0;
-    if (!too_few && (neu || M > ROWS || M < N || no_self)) {
-      // not for this path: the shared-memory FP32 kernel takes it (and writes
-      // every output)
+    if (!too_few && (neu != NEU || M > ROWS || M < N || no_self)) {
+      // not for this instantiation: a Neumann target to the Neumann list when
+      // the launch has one, anything else to the shared-memory FP32 kernel
+      // (which writes every output)
       if (lane == 0) {
-        const int slot = atomicAdd(j.gen_count, 1);
-        j.gen_items[slot] = (int32_t)to;
+        if (!NEU && neu && j.neu_items) {
+          const int slot = atomicAdd(j.neu_count, 1);
+          j.neu_items[slot] = (int32_t)to;
+        } else {
+          const int slot = atomicAdd(j.gen_count, 1);
+          j.gen_items[slot] = (int32_t)to;
+        }
         j.status[to] = 0;
       }
       continue;
@@ -400,7 +425,7 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
 #pragma unroll
-          for (int i = 0; i < N; ++i) Bs[i * LD + q * NC + c] = ff(0.f, 0.f);
+          for (int i = 0; i < NB; ++i) Bs[i * LD + q * NC + c] = ff(0.f, 0.f);
         }
       }
     }
@@ -408,10 +433,72 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
     for (int r = (ROWS / NC) * NC + lane; r < ROWS; r += HW) {
       if (r % NC == 0) SWs[r / NC] = ff(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < N; ++i) Bs[i * LD + r] = ff(0.f, 0.f);
+      for (int i = 0; i < NB; ++i) Bs[i * LD + r] = ff(0.f, 0.f);
     }
     if (lane == 0) IEPSs[0] = inv_eps;
     __syncwarp(mask);
+
+    if constexpr (NEU) {
+      // ---- Neumann (Sec. 2.3): H_F = I - 2 v v^T / v^T v with v = F - rho
+      // e_piv, F = n / eps on the linear columns 1..D (d/dx_c of the scaled
+      // monomial xi_c at x_T), rho = -sign(n_piv) |F|; H_F on the linear
+      // columns of every row, then columns 1 + piv and NB - 1 swap places.
+      // lambda~ = H_F lambda, swapped the same way, into the table.
+      int piv = 0;
+      double npiv = 0.0;  // n_piv
+      ff v[3], fn2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const double nc = j.normals[c * n + t];
+        if (c == 0 || fabs(nc) > fabs(npiv)) {
+          piv = c;
+          npiv = nc;
+        }
+        v[c] = ff(nc) * inv_eps;
+        fn2 = fn2 + v[c] * v[c];
+      }
+      const ff fn = sqrt_ff(fn2);
+      const ff rho = npiv >= 0.0 ? ff(-fn.h, -fn.l) : fn;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (c == piv) v[c] = v[c] - rho;
+      ff vv(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < D; ++c) vv = vv + v[c] * v[c];
+      const ff two_vv = ff(2.f, 0.f) * recip(vv);
+#pragma unroll
+      for (int i = 0; i < MR; ++i) {
+        const int r = lane + HW * i;
+        ff d(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < D; ++c) d = d + Bs[(1 + c) * LD + r] * v[c];
+        d = d * two_vv;
+#pragma unroll
+        for (int c = 0; c < D; ++c) Bs[(1 + c) * LD + r] = Bs[(1 + c) * LD + r] - d * v[c];
+        const ff pc = Bs[(1 + piv) * LD + r];
+        Bs[(1 + piv) * LD + r] = Bs[(NB - 1) * LD + r];
+        Bs[(NB - 1) * LD + r] = pc;
+      }
+      for (int e = lane; e < L * NB; e += HW) {
+        const int l = e / NB, c = e - l * NB;
+        const int cs = c == 1 + piv ? NB - 1 : (c == NB - 1 ? 1 + piv : c);
+        ff lv = lam0(l, cs);
+        if (cs >= 1 && cs <= D) {
+          ff dl(0.f, 0.f);
+#pragma unroll
+          for (int c2 = 0; c2 < D; ++c2) dl = dl + lam0(l, 1 + c2) * v[c2];
+          dl = dl * two_vv;
+          ff vc = v[0];
+#pragma unroll
+          for (int c2 = 1; c2 < D; ++c2)
+            if (cs - 1 == c2) vc = v[c2];
+          lv = lv - dl * vc;
+        }
+        LAMT[e] = lv;
+      }
+      if (lane == 0) LAMT[L * NB] = rho;
+      __syncwarp(mask);
+    }
 
     // ---- 2. FP32 Householder QR in registers
     float a[MR][N];
@@ -758,8 +845,29 @@ __global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size
         }
       }
     }
-    if (j.beta)
-      for (int l = lane; l < L; l += HW) j.beta[to * L + l] = 0.0;
+    if (j.beta) {
+      if constexpr (NEU) {
+        // coefficient of h: beta = (lambda~_piv - s^T p~) / rho, p~ the
+        // reflected pivot column (the tile's column NB - 1)
+        const ff rinv = recip(LAMT[L * NB]);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          Dot2 acc;
+#pragma unroll
+          for (int i = 0; i < MR; ++i) {
+            const int r = lane + HW * i;
+            acc.add_prod(Ss[l * LD + r], Bs[(NB - 1) * LD + r]);
+          }
+          ff part = acc.value();
+#pragma unroll
+          for (int o = HW / 2; o > 0; o >>= 1)
+            part = part + ff(__shfl_xor_sync(mask, part.h, o, HW), __shfl_xor_sync(mask, part.l, o, HW));
+          if (lane == 0) j.beta[to * L + l] = to_double((LAMT[l * NB + NB - 1] - part) * rinv);
+        }
+      } else {
+        for (int l = lane; l < L; l += HW) j.beta[to * L + l] = 0.0;
+      }
+    }
     if (lane == 0) {
       j.status[to] = st;
       if (j.iters) j.iters[to] = (uint8_t)used;
@@ -773,12 +881,18 @@ struct FastEntry {
   int kind, dim, deg, mr, L, hw;
   const void* fn;
   size_t (*bytes)(int L);  // shared memory per group (target)
+  bool neu;                // the Neumann instantiation
 };
 
 #define GMLS_FAST(KIND, D, DEG, MR, L, HW)                                                                            \
   FastEntry {                                                                                                          \
     KIND, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L, HW>,                                \
-        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 1 ? D : 1)>::bytes                               \
+        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 1 ? D : 1)>::bytes, false                        \
+  }
+#define GMLS_FAST_NEU(D, DEG, MR, L, HW)                                                                              \
+  FastEntry {                                                                                                          \
+    0, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<0, D, DEG, MR, L, HW, true>,                                \
+        &FastLay<HW, MR, gmls_gen::basis_size(0, D, DEG), 1, true>::bytes, true                                        \
   }
 
 }  // namespace gmls

@@ -314,6 +314,19 @@ def test_neumann_matches_oracle(ctx, dim, n_axis, m, k, precision):
     _release(ctx, cid, nid, sid)
 
 
+@pytest.mark.parametrize("variant", [-1, -2])
+@pytest.mark.parametrize("dim,n_axis,m,k", [(2, 24, 4, 36), (3, 10, 3, 40)])
+def test_neumann_register_kernel_matches_oracle(ctx, dim, n_axis, m, k, variant):
+    """The register kernel's Neumann instantiation (boundary targets in a
+    second launch over the list the first one fills), a warp (-1) or half a
+    warp (-2) per target."""
+    ctx.set_option(gmls.OPT_FORCE_VARIANT, variant)
+    try:
+        test_neumann_matches_oracle(ctx, dim, n_axis, m, k, gmls.FP32_REFINE)
+    finally:
+        ctx.set_option(gmls.OPT_FORCE_VARIANT, 0)
+
+
 # ------------------------------------------------------------------------ CSR
 @pytest.mark.parametrize("basis,m,k,fn", [(gmls.SCALAR, 4, 36, gmls.GRAD), (gmls.DIVFREE, 4, 48, gmls.VEC_LAPLACIAN),
                                           (gmls.SCALAR, 4, 36, gmls.DIV)])
