@@ -5,7 +5,7 @@
 #include "stencil_fast.cuh"
 
 namespace gmls {
-extern const FastEntry kFastN[] = {GMLS_FAST_NEU(3, 3, 3, 4, 16), GMLS_FAST_NEU(3, 3, 2, 4, 32),
+extern const FastEntry kFastN[] = {GMLS_FAST_NEU_T(3, 3, 3, 4, 16, 384), GMLS_FAST_NEU(3, 3, 2, 4, 32),
                                    GMLS_FAST_NEU(2, 4, 3, 3, 16), GMLS_FAST_NEU(2, 4, 2, 3, 32)};
 extern const int kFastNCount = sizeof(kFastN) / sizeof(kFastN[0]);
 }  // namespace gmls

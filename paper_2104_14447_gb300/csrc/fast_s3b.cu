@@ -3,6 +3,6 @@
 #include "stencil_fast.cuh"
 
 namespace gmls {
-extern const FastEntry kFastS3b[] = {GMLS_FAST(0, 3, 3, 2, 3, 32), GMLS_FAST(0, 3, 3, 2, 4, 32), GMLS_FAST(0, 3, 3, 3, 3, 32), GMLS_FAST(0, 3, 3, 3, 4, 32), GMLS_FAST(0, 3, 3, 3, 3, 16), GMLS_FAST(0, 3, 3, 3, 4, 16)};
+extern const FastEntry kFastS3b[] = {GMLS_FAST(0, 3, 3, 2, 3, 32), GMLS_FAST(0, 3, 3, 2, 4, 32), GMLS_FAST(0, 3, 3, 3, 3, 32), GMLS_FAST(0, 3, 3, 3, 4, 32), GMLS_FAST(0, 3, 3, 3, 3, 16), GMLS_FAST_T(0, 3, 3, 3, 4, 16, 384)};
 extern const int kFastS3bCount = sizeof(kFastS3b) / sizeof(kFastS3b[0]);
 }  // namespace gmls

@@ -282,17 +282,21 @@ __device__ __forceinline__ void solve_r_lanes(const float* Rs, const float* idg,
 
 // Block size limit: small register tiles keep twelve warps resident (at
 // most 168 registers per thread, blocks of up to 12 warps); larger ones are
-// left to the register allocator (blocks of up to 8 warps).  The launcher
-// takes the largest block among the shapes with the most resident warps, so
-// that an SM works on consecutive targets (neighbours shared in L1).
+// left to the register allocator (blocks of up to 8 warps).  An instantiation
+// may set its own limit (GMLS_FAST_T): the 40 x 20 half-warp tile of the 3D
+// degree-3 scalar basis runs faster capped at 168 registers (nine warps per
+// SM, shared memory deciding, a few hundred bytes of spills) than at 254
+// (eight).  The launcher takes the largest block among the shapes with the
+// most resident warps, so that an SM works on consecutive targets
+// (neighbours shared in L1).
 template <int HW, int MR, int N, int L>
 constexpr int fast_max_threads() {
   return MR * N * L <= 90 ? 384 : 256;
 }
 
-template <int KIND, int D, int DEG, int MR, int L, int HW, bool NEU = false>
-__global__ void __launch_bounds__((fast_max_threads<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()), 1)
-    stencil_fast_kernel(StencilJob j) {
+template <int KIND, int D, int DEG, int MR, int L, int HW, bool NEU = false,
+          int MAXT = fast_max_threads<HW, MR, gmls_gen::basis_size(KIND, D, DEG), L>()>
+__global__ void __launch_bounds__(MAXT, 1) stencil_fast_kernel(StencilJob j) {
   constexpr int NB = gmls_gen::basis_size(KIND, D, DEG);  // basis functions
   constexpr int N = NB - (NEU ? 1 : 0);                    // least-squares columns
   static_assert(!NEU || KIND == GMLS_BASIS_SCALAR, "the Neumann constraint is for the scalar basis");
@@ -889,9 +893,19 @@ struct FastEntry {
     KIND, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L, HW>,                                \
         &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 1 ? D : 1)>::bytes, false                        \
   }
+#define GMLS_FAST_T(KIND, D, DEG, MR, L, HW, MAXT)                                                                    \
+  FastEntry {                                                                                                          \
+    KIND, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<KIND, D, DEG, MR, L, HW, false, MAXT>,                   \
+        &FastLay<HW, MR, gmls_gen::basis_size(KIND, D, DEG), (KIND == 1 ? D : 1)>::bytes, false                        \
+  }
 #define GMLS_FAST_NEU(D, DEG, MR, L, HW)                                                                              \
   FastEntry {                                                                                                          \
     0, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<0, D, DEG, MR, L, HW, true>,                                \
+        &FastLay<HW, MR, gmls_gen::basis_size(0, D, DEG), 1, true>::bytes, true                                        \
+  }
+#define GMLS_FAST_NEU_T(D, DEG, MR, L, HW, MAXT)                                                                      \
+  FastEntry {                                                                                                          \
+    0, D, DEG, MR, L, HW, (const void*)stencil_fast_kernel<0, D, DEG, MR, L, HW, true, MAXT>,                          \
         &FastLay<HW, MR, gmls_gen::basis_size(0, D, DEG), 1, true>::bytes, true                                        \
   }
 
