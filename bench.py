@@ -32,6 +32,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import mmap
 import os
 import subprocess
 import tempfile
@@ -101,11 +102,51 @@ def src_sha(*names):
 # DRAM bytes (read + write) per launch measured by ncu on the timed launch
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass), with the hash of
 # the kernel sources it was taken on; a different hash reports null
-DFX_TRAFFIC = {"bytes": 700712704 + 10456942080, "sha": "a32a567edc57bc15",
+DFX_TRAFFIC = {"bytes": 701959680 + 10556833536, "sha": "ef0397d326b3331a",
                "sources": ("stencil_dfx.cuh", "stencil_fast.cuh", "ff.cuh"),
                "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none --nvtx "
                           "--nvtx-include porous_step/ -k regex:stencil_dfx -c 1 python bench.py --no-secondary "
                           "--no-e2e --no-cpu-baseline --steps 1 --warmup 3"}
+
+
+class HostBuffers:
+    """Page-locked host buffers for the end-to-end results.  With
+    ``huge=True``: anonymous memory advised as transparent huge pages,
+    touched, then registered with CUDA (cudaHostRegister); else the usual
+    page-locked allocation (pin_memory).  On a host whose memory has been in
+    use a while the usual allocation ends up in scattered base pages, and
+    device-to-host copies into it then run at a fraction of the link's rate."""
+
+    def __init__(self, huge):
+        self.huge = huge
+        self.regs = []
+
+    def empty(self, shape, dtype):
+        import torch
+
+        if self.huge:
+            nbytes = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+            try:
+                mm = mmap.mmap(-1, max(nbytes, 1))
+                mm.madvise(mmap.MADV_HUGEPAGE)
+                t = torch.frombuffer(mm, dtype=torch.uint8, count=max(nbytes, 1))[:nbytes]
+                t.fill_(0)  # touch: the pages exist before they are locked
+                rc = torch.cuda.cudart().cudaHostRegister(t.data_ptr(), max(nbytes, 1), 0)
+                if int(rc) == 0:
+                    self.regs.append(t.data_ptr())
+                    return t.view(dtype).view(shape)
+            except (OSError, ValueError, RuntimeError, AttributeError):
+                pass
+        return torch.empty(shape, dtype=dtype, pin_memory=True)
+
+    def close(self):
+        """Unlock the registered buffers (call with no copy in flight, before
+        the tensors go)."""
+        import torch
+
+        for p in self.regs:
+            torch.cuda.cudart().cudaHostUnregister(p)
+        self.regs = []
 
 
 class Clocks:
@@ -300,7 +341,8 @@ def run_headline(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         pin = tuple(t.pin_memory() for t in host)
-        host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
+        hb = HostBuffers(args.e2e_host == "huge")
+        host_out = {k: tuple(hb.empty(v.shape, v.dtype) for v in bufs[k]) for k in bufs}
         n_ranges = args.e2e_ranges
         bounds = [n * c // n_ranges for c in range(n_ranges + 1)]
         d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v) + 8 * 3 * (n_ranges - 1)
@@ -342,7 +384,7 @@ def run_headline(args, rank, world, local_rank):
             return ids
 
         e2e_ms = []
-        for s in range(max(3, min(args.steps, 5)) + 1):
+        for s in range(max(3, min(args.steps, 9)) + 1):
             with torch.cuda.stream(stream):
                 flush.fill_(s & 0xFF)
             torch.cuda.synchronize()
@@ -362,6 +404,8 @@ def run_headline(args, rank, world, local_rank):
                "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms],
                "target_ranges": n_ranges, "copy_streams": len(copy_streams),
                "host_operators_equal_device_step": equal}
+        torch.cuda.synchronize()
+        hb.close()
         del host_out, pin
 
     # GPU outputs of a seeded 5 % target sample for the oracle comparison
@@ -599,7 +643,8 @@ def stokes2d_section(ctx, args, prec_name="fp32_refine"):
 
     # e2e: the same step through the C ABI from pinned host input to host operators
     x_pin = torch.from_numpy(x_host).pin_memory()
-    host_out = {k: tuple(torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for v in bufs[k]) for k in bufs}
+    hb = HostBuffers(args.e2e_host == "huge")
+    host_out = {k: tuple(hb.empty(v.shape, v.dtype) for v in bufs[k]) for k in bufs}
     n_ranges = args.e2e_ranges
     d2h = sum(t.numel() * t.element_size() for v in bufs.values() for t in v) + 8 * 3 * (n_ranges - 1)
     h2d = x_pin.numel() * x_pin.element_size()
@@ -656,6 +701,9 @@ def stokes2d_section(ctx, args, prec_name="fp32_refine"):
     torch.cuda.synchronize()
     e2e_equal = all(torch.equal(h, d.cpu()) for k in bufs for h, d in zip(host_out[k], bufs[k]))
     release(ids)
+    torch.cuda.synchronize()
+    hb.close()
+    del host_out
     out["e2e"] = {"value": n / (float(np.median(e2e_ms)) * 1e-3), "unit": "targets/s",
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                   "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms],
@@ -1443,6 +1491,8 @@ def main():
     ap.add_argument("--no-shapes", action="store_true", help="skip the per-shape FP32 / FP64 section")
     ap.add_argument("--e2e-ranges", type=int, default=E2E_CHUNKS, help="target ranges of the end-to-end pipelines")
     ap.add_argument("--e2e-copy-streams", type=int, default=2, help="copy streams of the end-to-end pipelines")
+    ap.add_argument("--e2e-host", choices=["huge", "pinned"], default="huge",
+                    help="host result buffers: huge-page memory registered with CUDA, or pin_memory")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
     ap.add_argument("--only", choices=["batched", "stokes2d"], default=None,
                     help="profiling: run only this secondary section (--steps timed steps) and print it")
