@@ -759,6 +759,62 @@ SERVE_K = {(2, 0, 2): 12, (2, 0, 3): 20, (2, 0, 4): 36, (2, 1, 2): 22, (2, 1, 3)
            (3, 0, 2): 20, (3, 0, 3): 40, (3, 0, 4): 84, (3, 1, 2): 42, (3, 1, 3): 80, (3, 1, 4): 136}
 
 
+def polynomial_tables_3d(ctx, sizes=(6, 12, 24, 48, 96), degrees=(2, 4), rtol=1e-12):
+    """The polynomial tests of Sec. 4.1 through the GPU operators: the 3D
+    Stokes problem on [-1, 1]^3 (jittered lattice of N points per axis, the
+    box's outer layer Dirichlet, Neumann pressure rows there) whose solution
+    is a quadratic (degree-2 bases) or quartic (degree-4 bases)
+    divergence-free velocity and pressure, which the bases reproduce
+    exactly; degree-m stencils (FP32 + refinement) on the fixed-k lists,
+    GMRES(100) with row equilibration to rtol.  Per (degree, N): unknowns,
+    iterations, seconds, and the L2 (RMS) and max errors of the solved
+    velocity and mean-free pressure -- the paper's tables report L2 errors
+    of 6.8e-12 to 2.1e-9 (quadratic) and 1.6e-12 to 9.2e-9 (quartic) for
+    N = 6 to 96."""
+    import torch
+
+    from paper_2104_14447_gb300 import gmls, inputs
+
+    k_tab = {2: (42, 20), 4: (136, 84)}  # (div-free, scalar) neighbours
+    out = {"domain": "[-1, 1]^3, jittered lattice, outer layer Dirichlet", "solver": f"GMRES(100), row "
+           f"equilibration + right Jacobi, rtol {rtol:g}", "nu": 1.0, "precision": "fp32 + float-float refinement",
+           "tables": {}}
+    for m in degrees:
+        kv, kp = k_tab[m]
+        rows = []
+        for na in sizes:
+            x = inputs.jittered_grid(3, na, seed=na) * 2.0 - 1.0
+            n = x.shape[1]
+            bflag, nrm = inputs.box_boundary(3, na)
+            d = inputs.stokes_polynomial_3d(x, m, 1.0)
+            cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+            nv = ctx.neighbors(cid, kv, EPS_FACTOR)
+            npr = ctx.neighbors_prefix(nv, kp, EPS_FACTOR)
+            sv = ctx.stencils(nv, gmls.DIVFREE, m, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+            sp = ctx.stencils(npr, gmls.SCALAR, m, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE,
+                              neumann=True)
+            rp, col, val = ctx.stokes_assemble(sv, sp, 1.0, 0)
+            b = ctx.stokes_rhs(sv, sp, 1.0, d["f"], d["w"], d["div_f"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=rtol, row_scaling=True)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            s = sol.cpu().numpy()
+            eu = s[:3 * n].reshape(n, 3).T - d["u"]
+            ep = (s[3 * n:4 * n] - s[3 * n:4 * n].mean()) - (d["p"] - d["p"].mean())
+            rows.append({"N": na, "points": n, "unknowns": int(rp.shape[0] - 1), "nnz": int(col.shape[0]),
+                         "iterations": its, "rel_residual": rel, "converged": bool(np.isfinite(rel) and rel <= rtol),
+                         "seconds": el, "l2_error_velocity": float(np.sqrt(np.mean(eu ** 2))),
+                         "l2_error_pressure": float(np.sqrt(np.mean(ep ** 2))),
+                         "max_error_velocity": float(np.abs(eu).max()), "max_error_pressure": float(np.abs(ep).max())})
+            del rp, col, val, b, sol
+            for hd in (sp, sv, npr, nv, cid):
+                ctx.release(hd)
+        out["tables"]["quadratic" if m == 2 else "quartic"] = rows
+    return out
+
+
 def stokes_system(ctx, steps=5):
     """The Stokes collocation system (Sec. 3.2) on the benchmark grid with the
     outermost lattice layer as the Dirichlet / Neumann boundary: stencils
@@ -1494,7 +1550,9 @@ def main():
     ap.add_argument("--e2e-host", choices=["huge", "pinned"], default="huge",
                     help="host result buffers: huge-page memory registered with CUDA, or pin_memory")
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
-    ap.add_argument("--only", choices=["batched", "stokes2d"], default=None,
+    ap.add_argument("--poly-sizes", type=int, nargs="+", default=[6, 12, 24, 48, 96],
+                    help="points per axis of the 3D polynomial tables (Sec. 4.1)")
+    ap.add_argument("--only", choices=["batched", "stokes2d", "poly3d"], default=None,
                     help="profiling: run only this secondary section (--steps timed steps) and print it")
     ap.add_argument("--n-axis", type=int, default=512, help="2D section grid (profiling only; the benchmark is 512)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="serving stream length (0: skip)")
@@ -1518,6 +1576,8 @@ def main():
         ctx = gmls.Context(local_rank, arena_bytes=args.arena_gb << 30)
         if args.only == "stokes2d":
             res = stokes2d_section(ctx, args)
+        elif args.only == "poly3d":
+            res = polynomial_tables_3d(ctx, sizes=tuple(args.poly_sizes))
         else:
             res = batched_uneven(ctx, n_per_dim=args.batched_n, steps=args.steps)[0]
         print(json.dumps(res), flush=True)
@@ -1547,6 +1607,8 @@ def main():
                 sec["stokes_system"]["solve_512"] = stokes_solve(ctx, 512, full=False)
                 sec["stokes_system"]["solve_512_rtol_1e-12"] = stokes_solve(ctx, 512, full=False, rtol=1e-12)
         out["stokes2d_512"] = sec
+        if not args.no_stokes:
+            out["polynomial_3d"] = polynomial_tables_3d(ctx, sizes=tuple(args.poly_sizes))
         out["small_2d_1024"] = small_2d(ctx)
         if not args.no_shapes:
             out["shapes"] = shapes(ctx)

@@ -167,6 +167,43 @@ def stokes_cubic_3d(x: np.ndarray, nu: float = 1.0):
     return {"u": u, "p": p, "f": f, "w": u, "div_f": 6.0 * X, "curlcurl_u": cc}
 
 
+def stokes_polynomial_3d(x: np.ndarray, degree: int, nu: float = 1.0):
+    """Data of a 3D Stokes problem (Sec. 3.1) whose solution is a
+    divergence-free velocity and a pressure of the given degree (2 or 4;
+    the polynomial tests of Sec. 4.1, which degree-2 or degree-4 bases
+    reproduce exactly).  No velocity component depends on its own coordinate
+    (div u = 0).  Degree 2:
+      u = (y^2 + y z, x^2 + z^2, x y + x^2), lap u = (2, 4, 2),
+      p = x^2 - y z + 2 x z + y - 1, lap p = 2;
+    degree 4:
+      u = (y^4 + y^2 z^2 + y z^3, x^3 z + z^4 - x^2 z^2, x^2 y^2 + x y^3 - y^4),
+      lap u = (14 y^2 + 2 z^2 + 6 y z, 6 x z + 10 z^2 - 2 x^2, 2 x^2 - 10 y^2 + 6 x y),
+      p = x^4 - 2 x^2 y z + y^3 z + x z^2 - y^2 + 1, lap p = 12 x^2 + 2 y z + 2 x - 2;
+    curl curl u = -lap u, f = nu curl curl u + grad p, w = u, div f = lap p."""
+    X, Y, Z = (np.asarray(c, dtype=np.float64) for c in x[:3])
+    one = np.ones_like(X)
+    if degree == 2:
+        u = np.stack([Y ** 2 + Y * Z, X ** 2 + Z ** 2, X * Y + X ** 2])
+        lap_u = np.stack([2.0 * one, 4.0 * one, 2.0 * one])
+        p = X ** 2 - Y * Z + 2.0 * X * Z + Y - 1.0
+        gp = np.stack([2.0 * X + 2.0 * Z, -Z + 1.0, -Y + 2.0 * X])
+        lap_p = 2.0 * one
+    elif degree == 4:
+        u = np.stack([Y ** 4 + Y ** 2 * Z ** 2 + Y * Z ** 3, X ** 3 * Z + Z ** 4 - X ** 2 * Z ** 2,
+                      X ** 2 * Y ** 2 + X * Y ** 3 - Y ** 4])
+        lap_u = np.stack([14.0 * Y ** 2 + 2.0 * Z ** 2 + 6.0 * Y * Z, 6.0 * X * Z + 10.0 * Z ** 2 - 2.0 * X ** 2,
+                          2.0 * X ** 2 - 10.0 * Y ** 2 + 6.0 * X * Y])
+        p = X ** 4 - 2.0 * X ** 2 * Y * Z + Y ** 3 * Z + X * Z ** 2 - Y ** 2 + 1.0
+        gp = np.stack([4.0 * X ** 3 - 4.0 * X * Y * Z + Z ** 2, -2.0 * X ** 2 * Z + 3.0 * Y ** 2 * Z - 2.0 * Y,
+                       -2.0 * X ** 2 * Y + Y ** 3 + 2.0 * X * Z])
+        lap_p = 12.0 * X ** 2 + 2.0 * Y * Z + 2.0 * X - 2.0
+    else:
+        raise ValueError("degree 2 or 4")
+    cc = -lap_u
+    f = nu * cc + gp
+    return {"u": u, "p": p, "f": f, "w": u, "div_f": lap_p, "curlcurl_u": cc}
+
+
 def unit_vectors(seed: int, stream: int, n: int, dim: int) -> np.ndarray:
     """n random unit vectors (dim, n) from normalised uniform cube samples."""
     out = np.zeros((dim, n), dtype=np.float64)

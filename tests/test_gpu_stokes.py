@@ -379,6 +379,34 @@ def test_gmres_recovers_cubic_solution_3d(ctx, staggered):
     _release(ctx, ids)
 
 
+@pytest.mark.parametrize("degree,kv,kp", [(2, 42, 20), (4, 136, 84)])
+def test_gmres_recovers_polynomial_solution_3d(ctx, degree, kv, kp):
+    """Sec. 4.1's polynomial tests through the GPU operators on [-1, 1]^3
+    (6^3 lattice): a quadratic / quartic divergence-free velocity and
+    pressure, reproduced exactly by the degree-2 / degree-4 bases, recovered
+    by the row-equilibrated GMRES solve up to the stencils' rounding."""
+    na = 6
+    x = inputs.jittered_grid(3, na, seed=2) * 2.0 - 1.0
+    n = x.shape[1]
+    bflag, nrm = inputs.box_boundary(3, na)
+    cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+    nv = ctx.neighbors(cid, kv, 1.5)
+    npr = ctx.neighbors_prefix(nv, kp, 1.5)
+    sv = ctx.stencils(nv, gmls.DIVFREE, degree, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+    sp = ctx.stencils(npr, gmls.SCALAR, degree, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE, neumann=True)
+    rp, col, val = ctx.stokes_assemble(sv, sp, 1.0, 0)
+    d = inputs.stokes_polynomial_3d(x, degree, 1.0)
+    b = ctx.stokes_rhs(sv, sp, 1.0, d["f"], d["w"], d["div_f"])
+    sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=4000, rtol=1e-12, row_scaling=True)
+    assert rel <= 1e-12 and its > 0, (its, rel)
+    s = sol.cpu().numpy()
+    us, ps = s[:3 * n].reshape(n, 3).T, s[3 * n:4 * n]
+    eu = np.abs(us - d["u"]).max()
+    ep = np.abs((ps - ps.mean()) - (d["p"] - d["p"].mean())).max()
+    assert eu < 1e-6 * np.abs(d["u"]).max() and ep < 1e-5 * np.abs(d["p"]).max(), (eu, ep)
+    _release(ctx, [cid, nv, npr, sv, sp])
+
+
 def test_gmres_row_scaling_matches_direct_solve(ctx):
     """GMRES on the row-equilibrated system (row_scaling = 1), 32 x 32, FP64
     stencils, against the oracle's direct solve of the oracle's system; the

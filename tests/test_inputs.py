@@ -108,3 +108,37 @@ def test_stokes_cubic_3d_fields():
         assert np.allclose(d["f"][c], ev(f[c]), rtol=0, atol=1e-13)
     assert np.allclose(d["p"], ev(p), rtol=0, atol=1e-13)
     assert np.allclose(d["div_f"], ev(div_f), rtol=0, atol=1e-13)
+
+
+def test_stokes_polynomial_3d_fields():
+    """The hand-derived quadratic and quartic Stokes data against symbolic
+    differentiation (divergence-free velocity, curl curl, f, div f)."""
+    sympy = __import__("pytest").importorskip("sympy")
+    X, Y, Z = sympy.symbols("x y z")
+    V = (X, Y, Z)
+    fields = {
+        2: ([Y ** 2 + Y * Z, X ** 2 + Z ** 2, X * Y + X ** 2], X ** 2 - Y * Z + 2 * X * Z + Y - 1),
+        4: ([Y ** 4 + Y ** 2 * Z ** 2 + Y * Z ** 3, X ** 3 * Z + Z ** 4 - X ** 2 * Z ** 2,
+             X ** 2 * Y ** 2 + X * Y ** 3 - Y ** 4], X ** 4 - 2 * X ** 2 * Y * Z + Y ** 3 * Z + X * Z ** 2 - Y ** 2 + 1),
+    }
+
+    def curl(a):
+        return [sympy.diff(a[2], Y) - sympy.diff(a[1], Z), sympy.diff(a[0], Z) - sympy.diff(a[2], X),
+                sympy.diff(a[1], X) - sympy.diff(a[0], Y)]
+
+    x = inputs.jittered_grid(3, 5, seed=4) * 2.0 - 1.0
+    ev = lambda e: np.asarray(sympy.lambdify(V, e, "numpy")(*x), dtype=np.float64) * np.ones(x.shape[1])
+    nu = 0.7
+    for degree, (u, p) in fields.items():
+        assert all(sympy.Poly(c, *V).total_degree() == degree for c in u) and sympy.Poly(p, *V).total_degree() == degree
+        assert sympy.expand(sum(sympy.diff(u[c], V[c]) for c in range(3))) == 0
+        cc = curl(curl(u))
+        f = [nu * cc[c] + sympy.diff(p, V[c]) for c in range(3)]
+        div_f = sum(sympy.diff(f[c], V[c]) for c in range(3))
+        d = inputs.stokes_polynomial_3d(x, degree, nu)
+        for c in range(3):
+            assert np.allclose(d["u"][c], ev(u[c]), rtol=0, atol=1e-13)
+            assert np.allclose(d["curlcurl_u"][c], ev(cc[c]), rtol=0, atol=1e-12)
+            assert np.allclose(d["f"][c], ev(f[c]), rtol=0, atol=1e-12)
+        assert np.allclose(d["p"], ev(p), rtol=0, atol=1e-13)
+        assert np.allclose(d["div_f"], ev(div_f), rtol=0, atol=1e-12)
