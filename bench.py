@@ -760,58 +760,67 @@ SERVE_K = {(2, 0, 2): 12, (2, 0, 3): 20, (2, 0, 4): 36, (2, 1, 2): 22, (2, 1, 3)
 
 
 def polynomial_tables_3d(ctx, sizes=(6, 12, 24, 48, 96), degrees=(2, 4), rtol=1e-12):
-    """The polynomial tests of Sec. 4.1 through the GPU operators: the 3D
-    Stokes problem on [-1, 1]^3 (jittered lattice of N points per axis, the
-    box's outer layer Dirichlet, Neumann pressure rows there) whose solution
-    is a quadratic (degree-2 bases) or quartic (degree-4 bases)
-    divergence-free velocity and pressure, which the bases reproduce
-    exactly; degree-m stencils (FP32 + refinement) on the fixed-k lists,
-    GMRES(100) with row equilibration to rtol.  Per (degree, N): unknowns,
-    iterations, seconds, and the L2 (RMS) and max errors of the solved
-    velocity and mean-free pressure -- the paper's tables report L2 errors
-    of 6.8e-12 to 2.1e-9 (quadratic) and 1.6e-12 to 9.2e-9 (quartic) for
-    N = 6 to 96."""
+    """The 3D tests of Sec. 4.1 through the GPU operators: the Stokes problem
+    on [-1, 1]^3 (jittered lattice of N points per axis, the box's outer
+    layer Dirichlet, Neumann pressure rows there) with degree-m stencils (FP32
+    + refinement) on the fixed-k lists and GMRES(100) with row equilibration
+    to rtol.  Data: a quadratic (m = 2) or quartic (m = 4) divergence-free
+    velocity and pressure, which the bases reproduce exactly (the paper's
+    tables report L2 errors of 6.8e-12 to 2.1e-9 and 1.6e-12 to 9.2e-9 for
+    N = 6 to 96); and the trigonometric field of the paper's convergence
+    study, with the observed order between successive N.  Per case:
+    unknowns, iterations, seconds, L2 (RMS) and max errors of the solved
+    velocity and mean-free pressure."""
     import torch
 
     from paper_2104_14447_gb300 import gmls, inputs
 
     k_tab = {2: (42, 20), 4: (136, 84)}  # (div-free, scalar) neighbours
-    out = {"domain": "[-1, 1]^3, jittered lattice, outer layer Dirichlet", "solver": f"GMRES(100), row "
-           f"equilibration + right Jacobi, rtol {rtol:g}", "nu": 1.0, "precision": "fp32 + float-float refinement",
-           "tables": {}}
-    for m in degrees:
+
+    def solve_case(m, na, data):
         kv, kp = k_tab[m]
-        rows = []
-        for na in sizes:
-            x = inputs.jittered_grid(3, na, seed=na) * 2.0 - 1.0
-            n = x.shape[1]
-            bflag, nrm = inputs.box_boundary(3, na)
-            d = inputs.stokes_polynomial_3d(x, m, 1.0)
-            cid = ctx.cloud(x, normals=nrm, bflags=bflag)
-            nv = ctx.neighbors(cid, kv, EPS_FACTOR)
-            npr = ctx.neighbors_prefix(nv, kp, EPS_FACTOR)
-            sv = ctx.stencils(nv, gmls.DIVFREE, m, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
-            sp = ctx.stencils(npr, gmls.SCALAR, m, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE,
-                              neumann=True)
-            rp, col, val = ctx.stokes_assemble(sv, sp, 1.0, 0)
-            b = ctx.stokes_rhs(sv, sp, 1.0, d["f"], d["w"], d["div_f"])
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=rtol, row_scaling=True)
-            torch.cuda.synchronize()
-            el = time.perf_counter() - t0
-            s = sol.cpu().numpy()
-            eu = s[:3 * n].reshape(n, 3).T - d["u"]
-            ep = (s[3 * n:4 * n] - s[3 * n:4 * n].mean()) - (d["p"] - d["p"].mean())
-            rows.append({"N": na, "points": n, "unknowns": int(rp.shape[0] - 1), "nnz": int(col.shape[0]),
-                         "iterations": its, "rel_residual": rel, "converged": bool(np.isfinite(rel) and rel <= rtol),
-                         "seconds": el, "l2_error_velocity": float(np.sqrt(np.mean(eu ** 2))),
-                         "l2_error_pressure": float(np.sqrt(np.mean(ep ** 2))),
-                         "max_error_velocity": float(np.abs(eu).max()), "max_error_pressure": float(np.abs(ep).max())})
-            del rp, col, val, b, sol
-            for hd in (sp, sv, npr, nv, cid):
-                ctx.release(hd)
-        out["tables"]["quadratic" if m == 2 else "quartic"] = rows
+        x = inputs.jittered_grid(3, na, seed=na) * 2.0 - 1.0
+        n = x.shape[1]
+        bflag, nrm = inputs.box_boundary(3, na)
+        d = data(x)
+        cid = ctx.cloud(x, normals=nrm, bflags=bflag)
+        nv = ctx.neighbors(cid, kv, EPS_FACTOR)
+        npr = ctx.neighbors_prefix(nv, kp, EPS_FACTOR)
+        sv = ctx.stencils(nv, gmls.DIVFREE, m, [gmls.CURLCURL], precision=gmls.FP32_REFINE)
+        sp = ctx.stencils(npr, gmls.SCALAR, m, [gmls.GRAD, gmls.LAPLACIAN], precision=gmls.FP32_REFINE, neumann=True)
+        rp, col, val = ctx.stokes_assemble(sv, sp, 1.0, 0)
+        b = ctx.stokes_rhs(sv, sp, 1.0, d["f"], d["w"], d["div_f"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol, its, rel = ctx.gmres(rp, col, val, b, restart=100, max_iter=20000, rtol=rtol, row_scaling=True)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s = sol.cpu().numpy()
+        eu = s[:3 * n].reshape(n, 3).T - d["u"]
+        ep = (s[3 * n:4 * n] - s[3 * n:4 * n].mean()) - (d["p"] - d["p"].mean())
+        row = {"N": na, "points": n, "unknowns": int(rp.shape[0] - 1), "nnz": int(col.shape[0]), "iterations": its,
+               "rel_residual": rel, "converged": bool(np.isfinite(rel) and rel <= rtol), "seconds": el,
+               "l2_error_velocity": float(np.sqrt(np.mean(eu ** 2))),
+               "l2_error_pressure": float(np.sqrt(np.mean(ep ** 2))),
+               "max_error_velocity": float(np.abs(eu).max()), "max_error_pressure": float(np.abs(ep).max())}
+        del rp, col, val, b, sol
+        for hd in (sp, sv, npr, nv, cid):
+            ctx.release(hd)
+        return row
+
+    out = {"domain": "[-1, 1]^3, jittered lattice, outer layer Dirichlet",
+           "solver": f"GMRES(100), row equilibration + right Jacobi, rtol {rtol:g}", "nu": 1.0,
+           "precision": "fp32 + float-float refinement", "tables": {}}
+    for m in degrees:
+        out["tables"]["quadratic" if m == 2 else "quartic"] = [
+            solve_case(m, na, lambda x, m=m: inputs.stokes_polynomial_3d(x, m, 1.0)) for na in sizes]
+    for m in degrees:
+        rows = [solve_case(m, na, lambda x: inputs.stokes_trig_3d(x, 1.0)) for na in sizes if na >= 12]
+        for prev, row in zip(rows[:-1], rows[1:]):  # h = 2 / (N - 1)
+            hr = np.log((row["N"] - 1) / (prev["N"] - 1))
+            row["order_velocity"] = float(np.log(prev["l2_error_velocity"] / row["l2_error_velocity"]) / hr)
+            row["order_pressure"] = float(np.log(prev["l2_error_pressure"] / row["l2_error_pressure"]) / hr)
+        out["tables"][f"trigonometric_degree{m}"] = rows
     return out
 
 

@@ -204,6 +204,20 @@ def stokes_polynomial_3d(x: np.ndarray, degree: int, nu: float = 1.0):
     return {"u": u, "p": p, "f": f, "w": u, "div_f": lap_p, "curlcurl_u": cc}
 
 
+def stokes_trig_3d(x: np.ndarray, nu: float = 1.0):
+    """Data of the 3D Stokes problem of the paper's convergence study
+    (Sec. 4.1): u = (sin y sin z, sin x sin z, sin x sin y) (div u = 0,
+    lap u = -2 u, curl curl u = 2 u), p = sin x sin y sin z (lap p = -3 p);
+    f = nu curl curl u + grad p, w = u, div f = lap p."""
+    X, Y, Z = (np.asarray(c, dtype=np.float64) for c in x[:3])
+    sx, sy, sz, cx, cy, cz = np.sin(X), np.sin(Y), np.sin(Z), np.cos(X), np.cos(Y), np.cos(Z)
+    u = np.stack([sy * sz, sx * sz, sx * sy])
+    p = sx * sy * sz
+    gp = np.stack([cx * sy * sz, sx * cy * sz, sx * sy * cz])
+    cc = 2.0 * u
+    return {"u": u, "p": p, "f": nu * cc + gp, "w": u, "div_f": -3.0 * p, "curlcurl_u": cc}
+
+
 def unit_vectors(seed: int, stream: int, n: int, dim: int) -> np.ndarray:
     """n random unit vectors (dim, n) from normalised uniform cube samples."""
     out = np.zeros((dim, n), dtype=np.float64)

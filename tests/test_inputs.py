@@ -142,3 +142,31 @@ def test_stokes_polynomial_3d_fields():
             assert np.allclose(d["f"][c], ev(f[c]), rtol=0, atol=1e-12)
         assert np.allclose(d["p"], ev(p), rtol=0, atol=1e-13)
         assert np.allclose(d["div_f"], ev(div_f), rtol=0, atol=1e-12)
+
+
+def test_stokes_trig_3d_fields():
+    """The trigonometric Stokes data against symbolic differentiation."""
+    sympy = __import__("pytest").importorskip("sympy")
+    X, Y, Z = sympy.symbols("x y z")
+    V = (X, Y, Z)
+    u = [sympy.sin(Y) * sympy.sin(Z), sympy.sin(X) * sympy.sin(Z), sympy.sin(X) * sympy.sin(Y)]
+    p = sympy.sin(X) * sympy.sin(Y) * sympy.sin(Z)
+
+    def curl(a):
+        return [sympy.diff(a[2], Y) - sympy.diff(a[1], Z), sympy.diff(a[0], Z) - sympy.diff(a[2], X),
+                sympy.diff(a[1], X) - sympy.diff(a[0], Y)]
+
+    assert sympy.simplify(sum(sympy.diff(u[c], V[c]) for c in range(3))) == 0
+    nu = 1.3
+    cc = curl(curl(u))
+    f = [nu * cc[c] + sympy.diff(p, V[c]) for c in range(3)]
+    div_f = sum(sympy.diff(f[c], V[c]) for c in range(3))
+    x = inputs.jittered_grid(3, 5, seed=6) * 2.0 - 1.0
+    ev = lambda e: np.asarray(sympy.lambdify(V, e, "numpy")(*x), dtype=np.float64) * np.ones(x.shape[1])
+    d = inputs.stokes_trig_3d(x, nu)
+    for c in range(3):
+        assert np.allclose(d["u"][c], ev(u[c]), rtol=0, atol=1e-14)
+        assert np.allclose(d["curlcurl_u"][c], ev(cc[c]), rtol=0, atol=1e-13)
+        assert np.allclose(d["f"][c], ev(f[c]), rtol=0, atol=1e-13)
+    assert np.allclose(d["p"], ev(p), rtol=0, atol=1e-14)
+    assert np.allclose(d["div_f"], ev(div_f), rtol=0, atol=1e-13)
