@@ -300,10 +300,11 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_fast_kernel(StencilJob j) {
   constexpr int NB = gmls_gen::basis_size(KIND, D, DEG);  // basis functions
   constexpr int N = NB - (NEU ? 1 : 0);                    // least-squares columns
   static_assert(!NEU || KIND == GMLS_BASIS_SCALAR, "the Neumann constraint is for the scalar basis");
-  // refinement scheme: one Q application from s0 = B y0 (scalar and staggered
-  // bases, measured faster there), or Bjorck steps from s0 = Q [R^-T lambda; 0]
-  // with both residuals (divergence-free: its one-Q variant was slower, with
-  // more FP64 redos, on the 96 x 20 systems)
+  // refinement scheme: steps of one Q application each from s0 = B y0
+  // (scalar and staggered bases, measured faster there), or Bjorck steps from
+  // s0 = Q [R^-T lambda; 0] with both residuals (divergence-free: its one-Q
+  // variant was slower on the 96 x 20 systems, 0.222 vs 0.183 ms on 8,192
+  // targets, with the same number of steps allowed)
   constexpr bool ONEQ = KIND != GMLS_BASIS_DIVFREE;
   constexpr int NC = (KIND == GMLS_BASIS_DIVFREE) ? D : 1;  // components per neighbour (staggered: 1)
   constexpr int ROWS = HW * MR;
@@ -536,15 +537,15 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_fast_kernel(StencilJob j) {
 
     int used = 0;
     if constexpr (ONEQ) {
-    // ---- 3./4. solve and one refinement step.  y0 = R^-1 R^-T lambda in
-    // FP32; the Bjorck step on [[I, B], [B^T, 0]] [s; -y] = [0; lambda^T]
-    // starts from s0 = B y0 evaluated in float-float, so that f = B y0 - s0
-    // = 0 and the correction needs one application of Q:
-    //   g = lambda - B^T s0,  delta = R^-T g,  ds = Q [delta; 0].
+    // ---- 3./4. solve and refinement.  y0 = R^-1 R^-T lambda in FP32; the
+    // Bjorck steps on [[I, B], [B^T, 0]] [s; -y] = [0; lambda^T] start from
+    // s0 = B y0 evaluated in float-float, so that f = B y0 - s0 = 0 and each
+    // correction needs one application of Q:
+    //   g = lambda - B^T s,  delta = R^-T g,  ds = Q [delta; 0],  s += ds.
     // (s0 = B y0 is as accurate as Q [R^-T lambda; 0], an error of order
-    // kappa u_32, and the step contracts it by about kappa u_32.)  Targets
-    // whose correction misses the tolerance, or whose factor is
-    // ill-conditioned, go to the FP64 redo list.
+    // kappa u_32, and each step contracts it by about kappa u_32.)  Up to
+    // max_refine steps; targets whose correction still misses the
+    // tolerance, or whose factor is ill-conditioned, go to the FP64 redo list.
     float w[L][NT];
     float z[L][MR];
     bool conv = false;
@@ -579,7 +580,10 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_fast_kernel(StencilJob j) {
         }
       }
       __syncwarp(mask);
-      // g = lambda - B^T s0 over the L*N (l, c) pairs: whole pairs per lane
+      float prev = 0.0f;
+#pragma unroll 1
+      for (int it = 1; it <= j.max_refine; ++it) {
+      // g = lambda - B^T s over the L*N (l, c) pairs: whole pairs per lane
       // in full rounds of HW, the remaining pairs split into row blocks so
       // that every lane does about the same number of terms
       {
@@ -657,9 +661,15 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_fast_kernel(StencilJob j) {
       smax = wmax<HW>(smax, mask);
       __syncwarp(mask);
       // error left after the correction ~ |ds| times the contraction factor,
-      // estimated by the relative size of the correction
-      const float rho = dmax / fmaxf(smax, 1e-37f);
+      // estimated by the relative size of the correction (first pass) or by
+      // the ratio of successive corrections (later ones: s = s_prev + ds keeps
+      // B y - s at the rounding of ds, so each pass repeats the same step)
+      const float rho = it == 1 ? dmax / fmaxf(smax, 1e-37f) : dmax / fmaxf(prev, 1e-37f);
       conv = dmax * fminf(1.0f, rho) <= tolf * smax;
+      prev = dmax;
+      used = it;
+      if (conv) break;
+      }
     }
     if (!conv) {
       if (lane == 0) {
@@ -669,7 +679,6 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_fast_kernel(StencilJob j) {
       }
       continue;
     }
-    used = 1;
     } else {
     // ---- 3./4. solve and refinement with float-float residuals.  Pass 0 is
     // the plain FP32 solve, i.e. a refinement step from s = y = 0 (f = 0,
