@@ -205,7 +205,8 @@ gmls_status gmls_neighbors_prefix(gmls_ctx* ctx, int64_t nbrs_id, int32_t k, dou
  * sum w q(x_j) = (L q)(x_T) (plus beta * h for Neumann targets).
  * Besides the weights, a launch takes temporary scratch from the arena for
  * the duration of the kernel: the factored divergence-free kernel about
- * 29 KB per resident warp (3D degree 3: 152 SMs x 12 warps, 53 MB), the
+ * 29 KB per resident warp (3D degree 3: 152 SMs x 12 warps, 53 MB; on a
+ * smaller arena it runs a smaller grid, down to one block of 12 warps), the
  * shared-memory kernel its global tiles for shapes too large for shared
  * memory; GMLS_ENOMEM when the arena cannot hold them.
  */

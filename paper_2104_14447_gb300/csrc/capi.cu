@@ -327,7 +327,15 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
       DfxShape sh;
       cudaError_t e = dfx_launch_shape(jj, sms, &sh);
       if (e != cudaSuccess) return e;
+      // per-warp slots for the resident grid; on a small arena a smaller grid
+      // (the warps loop over the targets, so any grid is correct)
+      const size_t per_block = sh.grid > 0 ? sh.scratch / (size_t)sh.grid : sh.scratch;
       void* scr = ctx->arena.alloc(sh.scratch);
+      while (!scr && sh.grid > 1) {
+        sh.grid = (sh.grid + 1) / 2;
+        sh.scratch = per_block * (size_t)sh.grid;
+        scr = ctx->arena.alloc(sh.scratch);
+      }
       if (!scr) return cudaErrorMemoryAllocation;
       StencilJob jd = jj;
       jd.dscratch = static_cast<unsigned char*>(scr);

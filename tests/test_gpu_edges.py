@@ -126,3 +126,28 @@ def test_argument_errors(ctx):
     with pytest.raises(gmls.GmlsError) as e:
         ctx.release(cid)
     assert e.value.code == gmls.ENOTFOUND
+
+
+def test_factored_divfree_kernel_on_a_small_arena(ctx):
+    """The factored divergence-free kernel takes per-warp scratch from the
+    arena (53 MB for a full grid of the 3D degree-3 basis); on an arena that
+    cannot hold it the launch runs a smaller grid, with the same weights
+    bit for bit."""
+    x = inputs.jittered_grid(3, 12, seed=4)
+    small = gmls.Context(0, arena_bytes=48 << 20)
+    small.set_option(gmls.OPT_FORCE_VARIANT, -3)
+    ctx.set_option(gmls.OPT_FORCE_VARIANT, -3)
+    try:
+        out = []
+        for c in (ctx, small):
+            cid = c.cloud(x)
+            nid = c.neighbors(cid, 80, 1.5)
+            sid = c.stencils(nid, gmls.DIVFREE, 3, [gmls.VEC_LAPLACIAN], precision=gmls.FP32_REFINE)
+            out.append(c.weights(sid, gmls.VEC_LAPLACIAN).cpu().numpy())
+            c.sync()
+            for h in (sid, nid, cid):
+                c.release(h)
+        assert np.all(np.isfinite(out[0])) and np.array_equal(out[0], out[1])
+    finally:
+        ctx.set_option(gmls.OPT_FORCE_VARIANT, 0)
+        small.close()
