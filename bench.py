@@ -19,8 +19,9 @@ Householder QR with refinement against float-float (FP64-class) residuals.
 Secondary sections: the 2D Stokes operators on a 512 x 512 grid (262,144
 targets, scalar m = 4 and div-free m = 4, FP32 + refinement and FP64), the
 1,024-target 2D FP64 case, the uneven batch (1,000,000 mixed targets, one
-bucketed launch per cloud), the serving stream, every serving shape, and the
-Stokes block systems and solve.
+bucketed launch per cloud), the serving stream, every serving shape, the
+Stokes block systems and solves, and the 3D polynomial and trigonometric
+Stokes tests of Sec. 4.1 through the GPU operators (N = 6..96 per axis).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 it runs under torch.distributed.run, one rank per GPU; every rank
@@ -102,7 +103,7 @@ def src_sha(*names):
 # DRAM bytes (read + write) per launch measured by ncu on the timed launch
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass), with the hash of
 # the kernel sources it was taken on; a different hash reports null
-DFX_TRAFFIC = {"bytes": 699883008 + 10559485440, "sha": "c4f0290184236994",
+DFX_TRAFFIC = {"bytes": 699756032 + 10553133824, "sha": "819b3ba045a8d720",
                "sources": ("stencil_dfx.cuh", "stencil_fast.cuh", "ff.cuh"),
                "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none --nvtx "
                           "--nvtx-include porous_step/ -k regex:stencil_dfx -c 1 python bench.py --no-secondary "
@@ -152,10 +153,13 @@ class HostBuffers:
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
+    _count = 0
+
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"gmls_clocks_{os.getpid()}.csv")
+        Clocks._count += 1  # one file per sampler: several may be read in one process
+        self.path = os.path.join(tempfile.gettempdir(), f"gmls_clocks_{os.getpid()}_{Clocks._count}.csv")
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -384,15 +388,16 @@ def run_headline(args, rank, world, local_rank):
             return ids
 
         e2e_ms = []
-        for s in range(max(3, min(args.steps, 9)) + 1):
-            with torch.cuda.stream(stream):
-                flush.fill_(s & 0xFF)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ids = step_e2e()
-            torch.cuda.synchronize()  # every range's copies done: the operators are on the host
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-            release(ids)
+        with Clocks(local_rank) as e2e_clk:
+            for s in range(max(3, min(args.steps, 9)) + 1):
+                with torch.cuda.stream(stream):
+                    flush.fill_(s & 0xFF)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ids = step_e2e()
+                torch.cuda.synchronize()  # every range's copies done: the operators are on the host
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+                release(ids)
         e2e_ms = e2e_ms[1:]
         # the host operators equal the device step's, bit for bit (checked once, untimed, on the device)
         ids = step(dsrc)
@@ -403,7 +408,8 @@ def run_headline(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": float(np.median(e2e_ms)), "ms_steps": [round(v, 3) for v in e2e_ms],
                "target_ranges": n_ranges, "copy_streams": len(copy_streams),
-               "host_operators_equal_device_step": equal}
+               "host_operators_equal_device_step": equal, "host_buffers": args.e2e_host,
+               "clocks": e2e_clk.summary()}
         torch.cuda.synchronize()
         hb.close()
         del host_out, pin
@@ -1127,21 +1133,23 @@ def batched_uneven(ctx, n_per_dim=500_000, steps=3, n_sample=32):
         if prec == gmls.FP64:
             release(step(prec))  # its own warm-up (bucket choices of the FP64 kernel)
         times = []
-        for s in range(nsteps):
-            with torch.cuda.stream(stream):
-                flush.fill_(s & 0xFF)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-            torch.cuda.nvtx.range_push("batched_step")
-            h = step(prec, ev)
-            torch.cuda.nvtx.range_pop()
-            torch.cuda.synchronize()
-            times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
-            if not (prec == gmls.FP32_REFINE and s == nsteps - 1):
-                release(h)
+        with Clocks(torch.cuda.current_device()) as clk:
+            for s in range(nsteps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(s & 0xFF)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+                torch.cuda.nvtx.range_push("batched_step")
+                h = step(prec, ev)
+                torch.cuda.nvtx.range_pop()
+                torch.cuda.synchronize()
+                times.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+                if not (prec == gmls.FP32_REFINE and s == nsteps - 1):
+                    release(h)
         med = np.median(np.array(times), axis=0)
         res[name] = {"step_ms": float(np.sum(med)), "targets_per_s": 2 * n_per_dim / float(np.sum(med)) * 1e3,
                      "stage_ms": {"neighbours": float(med[0]), "stencils": float(med[1] + med[2]),
-                                  "stencils_2d": float(med[1]), "stencils_3d": float(med[2]), "csr": float(med[3])}}
+                                  "stencils_2d": float(med[1]), "stencils_3d": float(med[2]), "csr": float(med[3])},
+                     "stencils_3d_steps_ms": [round(t[2], 3) for t in times], "clocks": clk.summary()}
         if prec == gmls.FP32_REFINE:
             keep = h
             stencil_ms = (float(med[1]), float(med[2]))

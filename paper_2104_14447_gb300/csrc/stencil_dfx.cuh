@@ -653,9 +653,9 @@ __global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const
 
     // ---- 4. pass 0 (the plain FP32 solve) and one refinement pass.  A
     //         target whose correction misses the tolerance after that pass
-    //         is redone by the FP64 kernel (about 1e-5 of the targets of the
-    //         porous workload), so s0 and y0 stay FP32 and s = s0 + ds is
-    //         formed only when the weights are stored.
+    //         is redone by the FP64 kernel (about 2e-4 of the targets of the
+    //         porous workload); s = s0 + ds is formed only when the weights
+    //         are stored.
     auto lam = [&](int l, int i) {  // vector Laplacian row l at basis function i (float-float)
       const int c = tab.lam[l][i];
       return c == 0 ? ff(0.f, 0.f) : mul_f(ie2, (float)c);
