@@ -8,11 +8,14 @@
 
 namespace gmls {
 
-// (dimension, degree, rows of A per lane, neighbour capacity): the default
-// neighbour counts of the divergence-free bases (2D m = 2/3/4: 22/34/48; 3D
-// m = 2/3: 42/80) fit; a larger list goes to the shared-memory kernel.
-static const DfxEntry kDfx[] = {GMLS_DFX(2, 2, 1, 32), GMLS_DFX(2, 3, 2, 64), GMLS_DFX(2, 4, 2, 64),
-                                GMLS_DFX(3, 2, 2, 64), GMLS_DFX(3, 3, 3, 80)};
+// (dimension, degree, rows of A per lane, neighbour capacity, block limit):
+// the default neighbour counts of the divergence-free bases (2D m = 2/3/4:
+// 22/34/48; 3D m = 2/3: 42/80) fit; a larger list goes to the shared-memory
+// kernel.  Block limits: the most warps per SM the registers allow without
+// spills (ptxas), within the shared memory (2D m = 4: 20 warps of 9.3 KB;
+// 3D m = 2: 24 of 7.5 KB; 3D m = 3: 12 of 16.4 KB).
+static const DfxEntry kDfx[] = {GMLS_DFX(2, 2, 1, 32, 768), GMLS_DFX(2, 3, 2, 64, 768), GMLS_DFX(2, 4, 2, 64, 640),
+                                GMLS_DFX(3, 2, 2, 64, 768), GMLS_DFX(3, 3, 3, 80, 384)};
 
 static const DfxEntry* dfx_entry(int dim, int deg) {
   for (const DfxEntry& e : kDfx)
@@ -35,7 +38,7 @@ cudaError_t dfx_launch_shape(const StencilJob& j, int sms, DfxShape* s) {
   cudaError_t ea = cudaFuncGetAttributes(&fa, ent->fn);
   if (ea != cudaSuccess) return ea;
   int best_w = 1, best_warps = 0, best_blocks = 1;
-  for (int w = 1; w <= 12 && 32 * w <= fa.maxThreadsPerBlock; ++w) {
+  for (int w = 1; w <= 32 && 32 * w <= fa.maxThreadsPerBlock; ++w) {
     const size_t smem = (size_t)w * ent->bytes;
     if (smem > 227 * 1024) break;
     cudaError_t e = cudaFuncSetAttribute(ent->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -406,13 +406,14 @@ __device__ __forceinline__ void dfx_reflect(float alpha, const float (&x)[Q], in
   *beta_out = beta;
 }
 
-// Up to twelve warps (targets) per block, each on its own: at most 168
-// registers a thread, so that twelve warps of the 3D degree-3 basis (about
-// 16 KB of shared memory each) fit on an SM.  The warps of a block take
-// consecutive targets (shared neighbours in L1) and their scratch slots are
-// adjacent.
-template <int D, int M, int MRA, int KS>
-__global__ void __launch_bounds__(384, 1) stencil_dfx_kernel(StencilJob j, const DfxTab tab) {
+// Up to MAXT / 32 warps (targets) per block, each on its own; the bound caps
+// the registers so that that many warps fit on an SM: 384 threads (168
+// registers) for the 3D degree-3 basis (about 16 KB of shared memory a
+// warp), more for the smaller bases (their instantiations in dfx.cu).  The
+// warps of a block take consecutive targets (shared neighbours in L1) and
+// their scratch slots are adjacent.
+template <int D, int M, int MRA, int KS, int MAXT = 384>
+__global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, const DfxTab tab) {
   using Dm = DfxDims<D, M>;
   constexpr int Q = Dm::Q, N = Dm::N, NTOP = Dm::NTOP, N0 = Dm::N0, L = Dm::L, LC = Dm::LC;
   constexpr int NT = (N + 31) / 32;     // slots of an N-vector (solve layout)
@@ -891,9 +892,9 @@ struct DfxEntry {
   DfxTab (*tab)();
 };
 
-#define GMLS_DFX(D, M, MRA, KS)                                                                              \
+#define GMLS_DFX(D, M, MRA, KS, MAXT)                                                                        \
   DfxEntry {                                                                                                 \
-    D, M, MRA, KS, (const void*)stencil_dfx_kernel<D, M, MRA, KS>, DfxLay<D, M, KS>::BYTES,                  \
+    D, M, MRA, KS, (const void*)stencil_dfx_kernel<D, M, MRA, KS, MAXT>, DfxLay<D, M, KS>::BYTES,            \
         DfxLay<D, M, KS>::SLOT, &make_dfx_tab<D, M>                                                          \
   }
 
