@@ -522,6 +522,24 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
       if (!ctx->tune.count(key)) need = true;
     }
   if (need && ctx->autotune && !ctx->force_generic && !capturing(ctx)) {
+    // The launch gives every bucket the shared memory of its largest one: a
+    // variant that lifts it past the most the kernel's full count of blocks
+    // per SM allows would slow every other bucket down (a tiny bucket's
+    // choice once cost the 3D uneven batch 80 -> 111 ms).  So a bucket takes
+    // the fastest variant within that footprint when it is within 1.25 x of
+    // its fastest overall.
+    const int bmax = stencil_blocks_per_sm(refine, 0);
+    size_t fit = 0;
+    for (size_t lo = 0, hi = 227 * 1024; lo <= hi;) {
+      const size_t mid = (lo + hi) / 2;
+      if (stencil_blocks_per_sm(refine, mid) >= bmax) {
+        fit = mid;
+        lo = mid + 1;
+      } else {
+        if (mid == 0) break;
+        hi = mid - 1;
+      }
+    }
     std::vector<int32_t> cnt(b.nb), start(b.nb + 1);
     cudaMemcpyAsync(cnt.data(), b.counts, sizeof(int32_t) * b.nb, cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(start.data(), b.bucket_start, sizeof(int32_t) * (b.nb + 1), cudaMemcpyDeviceToHost, ctx->stream);
@@ -540,8 +558,8 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
         StencilJob js = j;
         js.items = b.items + start[bi];
         js.n_items = nsample;
-        float best = 1e30f;
-        int choice = 0;
+        float best = 1e30f, best_fit = 1e30f;
+        int choice = 0, choice_fit = 0;
         for (int v : generic_candidates(pl.ld[bi], pl.nmax[bi], refine)) {
           float ms = time_launch(ctx, [&]() {
             if (refine) cudaMemsetAsync(j.fb_count, 0, 3 * sizeof(int32_t), ctx->stream);
@@ -552,7 +570,13 @@ static gmls_status launch_bucketed(gmls_ctx* ctx, const StencilJob& j, const gml
             best = ms;
             choice = v;
           }
+          const size_t sv = (size_t)(4 / v_warps(v)) * tile_bytes(pl.ld[bi], pl.nmax[bi], refine, v_place(v));
+          if (sv <= fit && ms < best_fit) {
+            best_fit = ms;
+            choice_fit = v;
+          }
         }
+        if (choice_fit && best_fit <= 1.25f * best) choice = choice_fit;
         if (choice) {
           ctx->tune[key] = choice;
           pl.G[bi] = v_warps(choice);
