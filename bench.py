@@ -1569,7 +1569,7 @@ def main():
     ap.add_argument("--batched-n", type=int, default=500_000, help="targets per cloud of the uneven batch")
     ap.add_argument("--poly-sizes", type=int, nargs="+", default=[6, 12, 24, 48, 96],
                     help="points per axis of the 3D polynomial tables (Sec. 4.1)")
-    ap.add_argument("--only", choices=["batched", "stokes2d", "poly3d"], default=None,
+    ap.add_argument("--only", choices=["batched", "stokes2d", "poly3d", "shapes"], default=None,
                     help="profiling: run only this secondary section (--steps timed steps) and print it")
     ap.add_argument("--n-axis", type=int, default=512, help="2D section grid (profiling only; the benchmark is 512)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="serving stream length (0: skip)")
@@ -1595,6 +1595,8 @@ def main():
             res = stokes2d_section(ctx, args)
         elif args.only == "poly3d":
             res = polynomial_tables_3d(ctx, sizes=tuple(args.poly_sizes))
+        elif args.only == "shapes":
+            res = shapes(ctx)
         else:
             res = batched_uneven(ctx, n_per_dim=args.batched_n, steps=args.steps)[0]
         print(json.dumps(res), flush=True)

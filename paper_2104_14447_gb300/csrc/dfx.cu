@@ -11,11 +11,12 @@ namespace gmls {
 // (dimension, degree, rows of A per lane, neighbour capacity, block limit):
 // the default neighbour counts of the divergence-free bases (2D m = 2/3/4:
 // 22/34/48; 3D m = 2/3: 42/80) fit; a larger list goes to the shared-memory
-// kernel.  Block limits: the most warps per SM the registers allow without
-// spills (ptxas), within the shared memory (2D m = 4: 20 warps of 9.3 KB;
-// 3D m = 2: 24 of 7.5 KB; 3D m = 3: 12 of 16.4 KB).
+// kernel.  Block limits, measured: 2D m = 4 at 20 warps per SM (640 threads,
+// no spills; 0.165 vs 0.204 ms at 12 warps on 8,192 targets); 3D m = 2 and
+// m = 3 at 12 (3D m = 2 at 24 warps ran at less than half the speed);
+// 2D m = 2, 3 at 24 (the register kernel takes those shapes).
 static const DfxEntry kDfx[] = {GMLS_DFX(2, 2, 1, 32, 768), GMLS_DFX(2, 3, 2, 64, 768), GMLS_DFX(2, 4, 2, 64, 640),
-                                GMLS_DFX(3, 2, 2, 64, 768), GMLS_DFX(3, 3, 3, 80, 384)};
+                                GMLS_DFX(3, 2, 2, 64, 384), GMLS_DFX(3, 3, 3, 80, 384)};
 
 static const DfxEntry* dfx_entry(int dim, int deg) {
   for (const DfxEntry& e : kDfx)
