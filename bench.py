@@ -616,7 +616,9 @@ def stokes2d_section(ctx, args, prec_name="fp32_refine"):
         with torch.cuda.stream(stream):
             flush.fill_(s & 0xFF)
         ev[s][0].record(stream)
+        torch.cuda.nvtx.range_push("stokes2d_step")  # lets a profiler select the timed launches
         ids = step(x_dev, kev[s])
+        torch.cuda.nvtx.range_pop()
         ev[s][1].record(stream)
         release(ids)
     torch.cuda.synchronize()

@@ -430,8 +430,9 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
       CK(launch_stencils_fast(ctx->launch(), jn, mr, hw, sms, true), "gmls_stencils Neumann launch");
     }
     // targets the register kernels handed off (tile misfits; Neumann rows
-    // without a Neumann instantiation): the shared-memory FP32 kernel, whose
-    // failures join the FP64 redo list
+    // without a Neumann instantiation; the factored kernel's well-conditioned
+    // targets that one refinement pass left short of the tolerance): the
+    // shared-memory FP32 kernel, whose failures join the FP64 redo list
     StencilJob jg = j;
     jg.items = j.gen_items;
     jg.n_items = j.gen_count;

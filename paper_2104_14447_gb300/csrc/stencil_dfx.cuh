@@ -654,9 +654,10 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
 
     // ---- 4. pass 0 (the plain FP32 solve) and one refinement pass.  A
     //         target whose correction misses the tolerance after that pass
-    //         is redone by the FP64 kernel (about 2e-4 of the targets of the
-    //         porous workload); s = s0 + ds is formed only when the weights
-    //         are stored.
+    //         (about 2e-4 of the targets of the porous workload) goes on to
+    //         the shared-memory FP32 kernel, or to the FP64 kernel when its
+    //         factor is ill conditioned; s = s0 + ds is formed only when the
+    //         weights are stored.
     auto lam = [&](int l, int i) {  // vector Laplacian row l at basis function i (float-float)
       const int c = tab.lam[l][i];
       return c == 0 ? ff(0.f, 0.f) : mul_f(ie2, (float)c);
@@ -837,9 +838,18 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
     }
     if (!conv) {
       if (lane == 0) {
-        const int slot = atomicAdd(j.fb_count, 1);
-        j.fb_items[slot] = (int32_t)to;
-        j.status[to] = ill ? GMLS_T_ILL_CONDITIONED : GMLS_T_REFINE_NOT_CONVERGED;
+        if (!ill && j.max_refine > 1) {
+          // well conditioned, but one pass was not enough: the
+          // shared-memory FP32 kernel, which refines further (its own
+          // misses go to the FP64 kernel)
+          const int slot = atomicAdd(j.gen_count, 1);
+          j.gen_items[slot] = (int32_t)to;
+          j.status[to] = 0;
+        } else {
+          const int slot = atomicAdd(j.fb_count, 1);
+          j.fb_items[slot] = (int32_t)to;
+          j.status[to] = ill ? GMLS_T_ILL_CONDITIONED : GMLS_T_REFINE_NOT_CONVERGED;
+        }
       }
       __syncwarp(mask);
       continue;
