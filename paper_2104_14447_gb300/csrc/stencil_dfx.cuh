@@ -171,13 +171,14 @@ struct DfxLay {
   using Dm = DfxDims<D, M>;
   static constexpr int Q = Dm::Q, N = Dm::N, NTOP = Dm::NTOP, N0 = Dm::N0, L = Dm::L, LC = Dm::LC;
   static constexpr int LDA = KS + 1;  // odd: rows of different columns in different banks
+  static constexpr int QV = (Q + 3) & ~3;  // row stride of the reflector blocks: 16-byte rows
   static constexpr size_t al16(size_t v) { return (v + 15) & ~size_t(15); }
   // the factor block (offsets within the first region)
   static constexpr size_t RG = 0;                                             // float [N(N+1)/2] R_G, rows packed
   static constexpr size_t IDG = al16(RG + sizeof(float) * N * (N + 1) / 2);  // float [N] 1 / r_ii
-  static constexpr size_t V1 = al16(IDG + sizeof(float) * N);                // float [NTOP][Q] stage-1 reflectors
-  static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * Q);          // float [N0][Q] stage-2 reflectors
-  static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * Q);          // float [N]
+  static constexpr size_t V1 = al16(IDG + sizeof(float) * N);                // float [NTOP][QV] stage-1 reflectors
+  static constexpr size_t V2 = al16(V1 + sizeof(float) * NTOP * QV);         // float [N0][QV] stage-2 reflectors
+  static constexpr size_t TAUG = al16(V2 + sizeof(float) * N0 * QV);         // float [N]
   static constexpr size_t TAUA = al16(TAUG + sizeof(float) * N);             // float [Q]
   static constexpr size_t FAC = al16(TAUA + sizeof(float) * Q);              // bytes of the factor block
   static constexpr size_t ABYTES = al16(sizeof(ff) * Q * LDA);               // ff [Q][LDA] A = sqrt(W) P
@@ -311,12 +312,13 @@ __device__ __forceinline__ void dfx_solve(const float* Rs, const float* idg, flo
 // lane p % 32, slot p / 32 of zt; bottom rows r < Q at lane r of zb.
 // Stage-1 reflector jst acts on (top row jst, bottom rows) with vector
 // (1, V1[jst][.]); stage-2 reflector j2 on the bottom rows with V2[j2][.]
+// (rows QV floats apart)
 // (one at row j2, zero above).
-template <int L, int TS, int Q, int NTOP, int N0, bool FWD>
+template <int L, int TS, int Q, int QV, int NTOP, int N0, bool FWD>
 __device__ __forceinline__ void dfx_apply_qg(float (&zt)[L][TS], float (&zb)[L], const float* V1, const float* V2,
                                              const float* taug, int lane, unsigned mask) {
   auto stage1 = [&](int jst) {
-    const float v = lane < Q ? V1[jst * Q + lane] : 0.0f;
+    const float v = lane < Q ? V1[jst * QV + lane] : 0.0f;
     const float tk = taug[jst];
     const int own = jst & 31, sl = jst >> 5;
     float d[L];
@@ -331,7 +333,7 @@ __device__ __forceinline__ void dfx_apply_qg(float (&zt)[L][TS], float (&zb)[L],
     }
   };
   auto stage2 = [&](int j2) {
-    const float v = lane < Q ? V2[j2 * Q + lane] : 0.0f;
+    const float v = lane < Q ? V2[j2 * QV + lane] : 0.0f;
     const float tk = taug[NTOP + j2];
     float d[L];
 #pragma unroll
@@ -353,23 +355,19 @@ __device__ __forceinline__ void dfx_apply_qg(float (&zt)[L][TS], float (&zb)[L],
   }
 }
 
-// v[0..Q) = row[0..Q): 16-byte loads when Q is a multiple of 4 (rows of a
-// [.][Q] float array at a 16-byte aligned base)
+// v[0..Q) = row[0..Q) in 16-byte loads: a row of a [.][QV] float array
+// (QV = Q rounded up to a multiple of 4) at a 16-byte aligned base; the
+// padding entries are loaded and dropped
 template <int Q>
 __device__ __forceinline__ void dfx_load_row(const float* row, float (&v)[Q]) {
-  if constexpr (Q % 4 == 0) {
-    const float4* r4 = reinterpret_cast<const float4*>(row);
+  const float4* r4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
-    for (int i = 0; i < Q / 4; ++i) {
-      const float4 t = r4[i];
-      v[4 * i] = t.x;
-      v[4 * i + 1] = t.y;
-      v[4 * i + 2] = t.z;
-      v[4 * i + 3] = t.w;
-    }
-  } else {
+  for (int i = 0; i < (Q + 3) / 4; ++i) {
+    const float4 t = r4[i];
+    const float e[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = row[i];
+    for (int u = 0; u < 4; ++u)
+      if (4 * i + u < Q) v[4 * i + u] = e[u];
   }
 }
 
@@ -421,7 +419,7 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
   static_assert(Q <= 32 && N <= 64 && NTOP <= 64 && KS <= 32 * MRA && N0 <= Q, "tile outside this kernel's layout");
   static_assert(N == gmls_gen::basis_size(GMLS_BASIS_DIVFREE, D, M), "dimension of the divergence-free span");
   using Lay = DfxLay<D, M, KS>;
-  constexpr int LDA = Lay::LDA;
+  constexpr int LDA = Lay::LDA, QV = Lay::QV;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const unsigned mask = 0xffffffffu;
@@ -549,9 +547,9 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
 
     // ---- 3. G = (I (x) R_A) C: the bottom block (component 0 rows), one
     //         column per lane and slot (column lane + 32 s)
-    float xg[2][Q];
+    float xg[NT][Q];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NT; ++s) {
       const int col = lane + 32 * s;
       const int src = col < N ? (int)tab.src[col] : -1;
       const float sgn = col < NTOP ? -1.0f : 1.0f;
@@ -568,19 +566,19 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
       if (lane == (jst & 31)) {
         float beta, tk;
         const float alpha = RA[rpk<Q>(al, al)];
-        if (jst < 32)
-          dfx_reflect<Q>(alpha, xg[0], -1, V1 + jst * Q, &tk, &beta);
+        if (NT == 1 || jst < 32)
+          dfx_reflect<Q>(alpha, xg[0], -1, V1 + jst * QV, &tk, &beta);
         else
-          dfx_reflect<Q>(alpha, xg[1], -1, V1 + jst * Q, &tk, &beta);
+          dfx_reflect<Q>(alpha, xg[NT - 1], -1, V1 + jst * QV, &tk, &beta);
         TAUG[jst] = tk;
         RG[rpk<N>(jst, jst)] = beta;
       }
       __syncwarp(mask);
       const float tk = TAUG[jst];
       float v[Q];
-      dfx_load_row<Q>(V1 + jst * Q, v);
+      dfx_load_row<Q>(V1 + jst * QV, v);
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < NT; ++s) {
         const int col = lane + 32 * s;
         if (col > jst && col < N) {
           const int cb = col / Q, cg = col - cb * Q;
@@ -601,16 +599,16 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
       if (lane == (colk & 31)) {
         float beta, tk;
         float alpha = 0.0f;
-        if (colk < 32) {
+        if (NT == 1 || colk < 32) {
 #pragma unroll
           for (int r = 0; r < Q; ++r)
             if (r == j2) alpha = xg[0][r];
-          dfx_reflect<Q>(alpha, xg[0], j2, V2 + j2 * Q, &tk, &beta);
+          dfx_reflect<Q>(alpha, xg[0], j2, V2 + j2 * QV, &tk, &beta);
         } else {
 #pragma unroll
           for (int r = 0; r < Q; ++r)
-            if (r == j2) alpha = xg[1][r];
-          dfx_reflect<Q>(alpha, xg[1], j2, V2 + j2 * Q, &tk, &beta);
+            if (r == j2) alpha = xg[NT - 1][r];
+          dfx_reflect<Q>(alpha, xg[NT - 1], j2, V2 + j2 * QV, &tk, &beta);
         }
         TAUG[colk] = tk;
         RG[rpk<N>(colk, colk)] = beta;
@@ -618,9 +616,9 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
       __syncwarp(mask);
       const float tk = TAUG[colk];
       float v[Q];
-      dfx_load_row<Q>(V2 + j2 * Q, v);
+      dfx_load_row<Q>(V2 + j2 * QV, v);
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < NT; ++s) {
         const int col = lane + 32 * s;
         if (col > colk && col < N) {
           const float dot = dfx_dot4<Q>(v, xg[s], 0.0f) * tk;
@@ -679,7 +677,7 @@ __global__ void __launch_bounds__(MAXT, 1) stencil_dfx_kernel(StencilJob j, cons
         const float b1 = NT > 1 ? __shfl_sync(mask, dl[l][NT - 1], p & 31) : 0.0f;
         zb[l] = lane < N0 ? ((p >> 5) == 0 ? b0 : b1) : 0.0f;
       }
-      dfx_apply_qg<L, TS, Q, NTOP, N0, false>(zt, zb, V1, V2, TAUG, lane, mask);
+      dfx_apply_qg<L, TS, Q, QV, NTOP, N0, false>(zt, zb, V1, V2, TAUG, lane, mask);
 #pragma unroll
       for (int l = 0; l < L; ++l) {
         z[l * D][0] = lane < Q ? zb[l] : 0.0f;

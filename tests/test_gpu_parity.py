@@ -284,6 +284,37 @@ def test_refinement_iterations_and_fallback_flags(ctx):
     _release(ctx, cid, nid, sid)
 
 
+def test_factored_kernel_hands_refinement_misses_to_fp32_kernel(ctx):
+    """The factored div-free kernel refines once.  A well-conditioned target
+    whose one step misses the tolerance goes on to the shared-memory FP32
+    kernel, which refines further: with max_refine = 1 such targets are FP64
+    redos (flagged), with the default they are not, and their weights meet
+    the bar against the oracle."""
+    x = inputs.jittered_grid(2, 160, seed=11)
+    n = x.shape[1]
+    cid, nid, idx, eps, st = _gpu_knn(ctx, x, 48, 1.5)
+    ctx.set_option(gmls.OPT_FORCE_VARIANT, -3)
+    try:
+        s1 = ctx.stencils(nid, gmls.DIVFREE, 4, [gmls.VEC_LAPLACIAN], precision=gmls.FP32_REFINE, max_refine=1)
+        st1 = ctx.export(s1, gmls.X_STATUS, torch.uint8).cpu().numpy()
+        ctx.release(s1)
+        s3 = ctx.stencils(nid, gmls.DIVFREE, 4, [gmls.VEC_LAPLACIAN], precision=gmls.FP32_REFINE)
+    finally:
+        ctx.set_option(gmls.OPT_FORCE_VARIANT, 0)
+    st3 = ctx.export(s3, gmls.X_STATUS, torch.uint8).cpu().numpy()
+    miss = ((st1 & gmls.T_REFINE_NOT_CONVERGED) != 0) & ((st1 & gmls.T_ILL_CONDITIONED) == 0)
+    assert np.all((st1[miss] & gmls.T_FP64_FALLBACK) != 0)
+    assert miss.sum() > 0  # the case exercises the hand-off
+    assert not np.any(st3[miss] & gmls.T_FP64_FALLBACK)
+    tg = np.nonzero(miss)[0].astype(np.int32)
+    k = 48
+    wo, _, diag = oracle.stencils(x, tg, np.arange(0, tg.size * k + 1, k), idx.reshape(n, k)[tg].ravel(), eps[tg],
+                                  "divfree", 4, NAMES[gmls.VEC_LAPLACIAN])
+    wg = ctx.weights(s3, gmls.VEC_LAPLACIAN).cpu().numpy().reshape((n,) + wo.shape[1:])[tg]
+    assert _scaled_err(wg, wo, diag[:, 0] / diag[:, 1], TOL32) <= 1.0
+    _release(ctx, cid, nid, s3)
+
+
 # ------------------------------------------------------------------- Neumann
 @pytest.mark.parametrize("precision", [gmls.FP64, gmls.FP32_REFINE])
 @pytest.mark.parametrize("dim,n_axis,m,k", [(2, 24, 2, 12), (2, 24, 4, 36), (3, 10, 3, 40)])
