@@ -628,12 +628,13 @@ __device__ void warp_sort_candidates(WarpBuf& wb, int count) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q, int buf_cap) {
+__global__ void __launch_bounds__(kQueryWarps * 32, 7) nbr_query_kernel(NbrQuery q, int buf_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpBuf wb = warpbuf_at(smem_raw + (size_t)(threadIdx.x >> 5) * warpbuf_bytes(buf_cap), buf_cap);
   const int lane = threadIdx.x & 31;
   const CloudDev& cl = q.cloud;
   const GridParams g = *cl.grid;
+  const double* org = cl.grid->org;
   constexpr int dim = D;
   const QueryGeo gq = make_query_geo(g, dim);
   // unit-ball volume and the initial radius: about 1.2 k particles expected
@@ -660,9 +661,15 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     const int64_t t = q.tgt ? q.tgt[to] : to;
     double xT[3] = {0.0, 0.0, 0.0}, nrm[3] = {0.0, 0.0, 0.0};
     float xTf[3] = {0.0f, 0.0f, 0.0f};
-    for (int c = 0; c < dim; ++c) {
-      xT[c] = cl.x[c * cl.n + t];
-      xTf[c] = __double2float_rn(__dsub_rn(xT[c], g.org[c]));
+    for (int c = 0; c < dim; ++c) xT[c] = cl.x[c * cl.n + t];
+    {
+      // the FP32 offset from the grid origin: lane c rounds coordinate c (one
+      // FP64 subtraction per lane instead of dim on every lane: GB300's FP64
+      // pipe is narrow), then every lane takes the dim values
+      float own = 0.0f;
+      const double xc = lane == 0 ? xT[0] : (lane == 1 ? xT[1] : xT[2]);
+      if (lane < dim) own = __double2float_rn(__dsub_rn(xc, org[lane]));
+      for (int c = 0; c < dim; ++c) xTf[c] = __shfl_sync(0xffffffffu, own, c);
     }
     bool use_hs = false;
     float nrmf[3] = {0.0f, 0.0f, 0.0f}, hs_scale = 0.0f;
@@ -714,8 +721,15 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
     if (count < kq) st |= GMLS_T_TOO_FEW_NEIGHBOURS;
     warp_sort_candidates(wb, count);
     const int kk = count < kq ? count : kq;
+    // k-nearest lists: eps = eps_factor sqrt(d2_k) waits until after the
+    // loop, where each lane takes one of the warp's targets (the k-th d2, or
+    // -1 when the list came up short, parks in out_eps); radius lists need it
+    // here
     double eps = 0.0;
-    if (kk == kq) eps = __dmul_rn(q.eps_factor, __dsqrt_rn(wb.d2[kq - 1]));
+    if (q.mode == GMLS_NBR_KNN)
+      eps = kk == kq ? wb.d2[kq - 1] : -1.0;
+    else if (kk == kq)
+      eps = __dmul_rn(q.eps_factor, __dsqrt_rn(wb.d2[kq - 1]));
     if (q.mode == GMLS_NBR_KNN && !q.k_pt) {
       for (int i = lane; i < q.k; i += 32) q.out_idx[to * q.k + i] = (i < kk) ? wb.id[i] : -1;
     } else if (q.mode == GMLS_NBR_KNN) {  // per-target k: padded rows, compacted later
@@ -742,6 +756,16 @@ __global__ void __launch_bounds__(kQueryWarps * 32) nbr_query_kernel(NbrQuery q,
       q.out_status[to] = st;
     }
     __syncwarp();
+  }
+  if (q.mode == GMLS_NBR_KNN) {
+    // eps of this warp's targets, one per lane (the warp's own writes above
+    // are ordered before these reads by the __syncwarp that ends each target)
+    const int64_t w0 = blockIdx.x * (int64_t)kQueryWarps + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kQueryWarps;
+    for (int64_t to = w0 + lane * stride; to < q.n_tgt; to += 32 * stride) {
+      const double d2 = q.out_eps[to];
+      q.out_eps[to] = d2 >= 0.0 ? __dmul_rn(q.eps_factor, __dsqrt_rn(d2)) : 0.0;
+    }
   }
 }
 
