@@ -472,7 +472,7 @@ def variant_name(v):
     if v is None:
         return None
     if v < 0:
-        return {-1: "register", -2: "register 16 lanes", -3: "factored div-free"}.get(v, str(v))
+        return {-1: "register", -2: "register 16 lanes", -3: "factored div-free", -4: "register 8 lanes"}.get(v, str(v))
     place = {0: "", 1: ", split tiles", 2: ", global tiles"}.get(v >> 3, "")
     return f"{v & 7} warp(s)/target{place}"
 

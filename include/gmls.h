@@ -378,8 +378,9 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
                                     this call waits for the stream.  0: heuristic choice      */
 #define GMLS_OPT_CLEAR_TUNING 2  /* any value: forget the cached choices and timings         */
 #define GMLS_OPT_FORCE_VARIANT 3 /* testing: the kernel variant for shapes with uniform
-                                    neighbour counts and degree: -1 / -2 register kernel
-                                    with 32 / 16 lanes per target; -3 the factored
+                                    neighbour counts and degree: -1 / -2 / -4 register
+                                    kernel with 32 / 16 / 8 lanes per target (-4: no
+                                    Neumann rows); -3 the factored
                                     divergence-free kernel (div-free basis, FP32 path);
                                     G + 8 * P for the
                                     shared-memory kernel with G = 1, 2 or 4 warps per target

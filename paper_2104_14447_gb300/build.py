@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgmls.so")
 SOURCES = ["capi.cu", "nbr.cu", "stencil.cu", "stencil_fast.cu", "noalloc.cu", "serve.cu", "stokes.cu", "krylov.cu", "fast_s2a.cu",
-           "fast_s2b.cu", "fast_s2c.cu", "fast_s3a.cu", "fast_s3b.cu", "fast_s3c.cu", "fast_d2.cu", "fast_d3.cu", "fast_g2.cu", "fast_g3.cu", "fast_n.cu", "dfx.cu"]
+           "fast_s2b.cu", "fast_s2c.cu", "fast_s3a.cu", "fast_s3b.cu", "fast_s3c.cu", "fast_d2.cu", "fast_d3.cu", "fast_g2.cu", "fast_g3.cu", "fast_n.cu", "fast_s2d.cu", "dfx.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -103,7 +103,7 @@ struct TuneKey {
 };
 struct TuneRecord {
   TuneKey key;
-  int variant;  // -1 / -2 register kernel (32 / 16 lanes per target), else warps per target
+  int variant;  // -1 / -2 / -4 register kernel (32 / 16 / 8 lanes per target), -3 factored, else warps per target
   float ms;
 };
 
@@ -303,18 +303,20 @@ static cudaError_t launch_single(gmls_ctx* ctx, const StencilJob& j, int variant
 }
 
 // Uniform neighbour counts and degree: one shape.  Candidates: the register
-// kernel with a warp (variant -1) or a half warp (variant -2) per target, when
-// this shape is instantiated, and the shared-memory kernel with 1, 2 or 4
+// kernel with a warp (variant -1), a half warp (variant -2) or 8 lanes
+// (variant -4; not for Neumann rows, which it has no instantiation for) per
+// target, when this shape is instantiated, and the shared-memory kernel with 1, 2 or 4
 // warps per target and its tile placements (generic_candidates); the
 // autotuner times each once on up to 8192 targets and the choice is cached
 // per shape.
 static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls_stencil_params* p, bool refine,
                                   int ld, int nmax, int sms, int32_t* counter) {
   const int dim = j.dim;
-  int mr32 = 0, mr16 = 0, mr_pref = 0;
+  int mr32 = 0, mr16 = 0, mr8 = 0, mr_pref = 0;
   const bool fast_allowed = refine && (p->weight_power % 2 == 0) && !ctx->force_generic;
   const bool ok32 = fast_allowed && fast_path_available(p->basis, dim, p->degree, ld, j.L, 32, &mr32);
   const bool ok16 = fast_allowed && fast_path_available(p->basis, dim, p->degree, ld, j.L, 16, &mr16);
+  const bool ok8 = fast_allowed && !p->neumann && fast_path_available(p->basis, dim, p->degree, ld, j.L, 8, &mr8);
   const int hw_pref = fast_allowed ? fast_path_preferred(p->basis, dim, p->degree, ld, j.L, &mr_pref) : 0;
   // factored divergence-free kernel (variant -3): lists of at least Q and at
   // most its capacity of neighbours
@@ -343,15 +345,16 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
       ctx->arena.release(scr);  // stream ordered: later work on this stream runs after the kernel
       return e;
     }
+    if (variant == -4) return launch_stencils_fast(ctx->launch(), jj, mr8, 8, sms);
     return variant == -2 ? launch_stencils_fast(ctx->launch(), jj, mr16, 16, sms)
                          : launch_stencils_fast(ctx->launch(), jj, mr32, 32, sms);
   };
   const TuneKey key{p->basis, dim, p->degree, p->precision, ld, j.L, p->neumann, 0};
-  int choice = 0;  // -1 / -2 register kernel (32 / 16 lanes per target), -3 factored div-free, else a vcode
+  int choice = 0;  // -1 / -2 / -4 register kernel (32 / 16 / 8 lanes per target), -3 factored div-free, else a vcode
   auto it = ctx->tune.find(key);
   if (ctx->force_variant != 0) {
     const int v = ctx->force_variant;
-    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || (v == -3 && okdfx) ||
+    const bool ok = (v == -1 && ok32) || (v == -2 && ok16) || (v == -3 && okdfx) || (v == -4 && ok8) ||
                     (v > 0 && variant_fits(v, ld, nmax, refine));
     if (!ok) return fail(ctx, GMLS_EINVAL, "gmls_stencils: the forced kernel variant is not available for this shape");
     choice = v;
@@ -389,6 +392,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     std::vector<int> cands;
     if (ok32) cands.push_back(-1);
     if (ok16) cands.push_back(-2);
+    if (ok8) cands.push_back(-4);
     if (okdfx) cands.push_back(-3);
     for (int v : generic_candidates(ld, nmax, refine)) cands.push_back(v);
     for (int c : cands) {
@@ -417,7 +421,7 @@ static gmls_status launch_uniform(gmls_ctx* ctx, const StencilJob& j, const gmls
     // Neumann targets: the register kernel's Neumann instantiation for this
     // shape when there is one (a second launch over the list the first one
     // fills), else the shared-memory kernel
-    const int mr = choice == -2 ? mr16 : mr32, hw = choice == -2 ? 16 : 32;
+    const int mr = choice == -2 ? mr16 : choice == -4 ? mr8 : mr32, hw = choice == -2 ? 16 : choice == -4 ? 8 : 32;
     const bool neu_fast = choice != -3 && j.neu_items && fast_neu_available(dim, p->degree, mr, j.L, hw);
     StencilJob jf = j;
     if (!neu_fast) jf.neu_items = jf.neu_count = nullptr;
@@ -710,10 +714,10 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
       return GMLS_OK;
     case GMLS_OPT_AUTOTUNE: ctx->autotune = value != 0; return GMLS_OK;
     case GMLS_OPT_FORCE_VARIANT:
-      if (value != 0 && value != -1 && value != -2 && value != -3 &&
+      if (value != 0 && value != -1 && value != -2 && value != -3 && value != -4 &&
           !(value > 0 && value < 24 && (v_warps((int)value) == 1 || v_warps((int)value) == 2 ||
                                         v_warps((int)value) == 4)))
-        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1, -2, -3 or G + 8 * P (G 1, 2, 4; P 0, 1, 2)");
+        return fail(ctx, GMLS_EINVAL, "gmls_set_option: variant must be 0, -1 .. -4 or G + 8 * P (G 1, 2, 4; P 0, 1, 2)");
       ctx->force_variant = (int)value;
       return GMLS_OK;
     case GMLS_OPT_POISON:

@@ -28,12 +28,14 @@ extern const FastEntry kFastG3[];
 extern const int kFastG3Count;
 extern const FastEntry kFastN[];
 extern const int kFastNCount;
+extern const FastEntry kFastS2d[];
+extern const int kFastS2dCount;
 
 struct FastTable {
   const FastEntry* e;
   const int* n;
 };
-static const FastTable kTables[] = {{kFastS2a, &kFastS2aCount}, {kFastS2b, &kFastS2bCount}, {kFastS2c, &kFastS2cCount}, {kFastS3a, &kFastS3aCount}, {kFastS3b, &kFastS3bCount}, {kFastD2, &kFastD2Count}, {kFastD3, &kFastD3Count}, {kFastS3c, &kFastS3cCount}, {kFastG2, &kFastG2Count}, {kFastG3, &kFastG3Count}, {kFastN, &kFastNCount}};
+static const FastTable kTables[] = {{kFastS2a, &kFastS2aCount}, {kFastS2b, &kFastS2bCount}, {kFastS2c, &kFastS2cCount}, {kFastS3a, &kFastS3aCount}, {kFastS3b, &kFastS3bCount}, {kFastD2, &kFastD2Count}, {kFastD3, &kFastD3Count}, {kFastS3c, &kFastS3cCount}, {kFastG2, &kFastG2Count}, {kFastG3, &kFastG3Count}, {kFastN, &kFastNCount}, {kFastS2d, &kFastS2dCount}};
 
 template <typename F>
 static void for_each_entry(F&& f) {

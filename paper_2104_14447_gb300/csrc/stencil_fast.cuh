@@ -7,13 +7,14 @@
 // Householder QR, functional rows lambda, weights w = sqrt(W) Q R^{-T}
 // lambda^T), laid out for GB300:
 //
-//  * a group of HW lanes (a whole warp, HW = 32, or half of one, HW = 16)
+//  * a group of HW lanes (a whole warp, HW = 32, half of one, HW = 16, or 8)
 //    owns one target; lane l of the group holds rows l, l+HW, ... of the FP32
 //    QR tile in registers (compile-time basis size N and rows-per-lane MR, so
 //    the factorisation is fully unrolled); padded rows are zero and exactly
 //    neutral for Householder reflections.  Half-warp groups suit systems of
 //    a few dozen rows (36 rows: 48 slots on 16 lanes instead of 64 on 32),
-//    and every cross-lane reduction then serves two targets at once;
+//    and every cross-lane reduction then serves two targets at once (four on
+//    8-lane groups: 40 slots for the 36 rows, at 5 rows a lane);
 //  * the tile B is built directly in float-float (hi + lo, ~48 bits) from the
 //    FP64 offsets x_j - x_T (one FP64 subtraction per coordinate, split into
 //    float-float with integer operations), so the result does not depend on

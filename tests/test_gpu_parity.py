@@ -161,14 +161,16 @@ NAMES = {gmls.GRAD: "grad", gmls.LAPLACIAN: "laplacian", gmls.DIV: "div", gmls.V
          gmls.CURLCURL: "curlcurl"}
 
 
-# forced variants: register kernel (-1, -2); shared-memory kernel G + 8 * placement
+# forced variants: register kernel (-1, -2, -4: 32, 16, 8 lanes a target);
+# factored div-free kernel (-3); shared-memory kernel G + 8 * placement
 # (split: float-float tile in global memory; global: both tiles there)
-VARIANT = {"reg32": -1, "reg16": -2, "dfx": -3, "split4": 4 + 8, "global1": 1 + 16, "global2": 2 + 16}
+VARIANT = {"reg32": -1, "reg16": -2, "dfx": -3, "reg8": -4, "split4": 4 + 8, "global1": 1 + 16, "global2": 2 + 16}
 
 
 @pytest.mark.parametrize("precision,kernel", [(gmls.FP64, "generic"), (gmls.FP32_REFINE, "generic"),
                                               (gmls.FP32_REFINE, "auto"), (gmls.FP32_REFINE, "reg32"),
-                                              (gmls.FP32_REFINE, "reg16"), (gmls.FP32_REFINE, "dfx"),
+                                              (gmls.FP32_REFINE, "reg16"), (gmls.FP32_REFINE, "reg8"),
+                                              (gmls.FP32_REFINE, "dfx"),
                                               (gmls.FP32_REFINE, "split4"),
                                               (gmls.FP32_REFINE, "global1"), (gmls.FP64, "global2")])
 @pytest.mark.parametrize("dim,n_axis,basis,m,k,fns", CASES)
