@@ -398,6 +398,9 @@ gmls_status gmls_launch_count(gmls_ctx* ctx, int64_t* launches);
                                     returns (weights, beta, status, iteration counts) with
                                     all-ones bytes (NaN weights), so that an entry no kernel
                                     writes cannot pass for a result left in reused memory    */
+#define GMLS_OPT_ORDER_KEY64 6   /* testing: 1 = the id order of neighbour lists (CSR column
+                                    order) is sorted on 64-bit keys even where the cloud is
+                                    small enough for 32-bit ones; the order is the same      */
 
 /* Set a context option (GMLS_OPT_*); applies to later calls. */
 gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value);

@@ -117,6 +117,7 @@ struct gmls_ctx {
   bool force_generic = false;  // testing: use the generic tile kernel for every shape
   int force_variant = 0;       // testing: this kernel variant for uniform shapes (0: off)
   bool poison = false;         // testing: fill stencil outputs with all-ones bytes first
+  bool order_key64 = false;    // testing: sort neighbour-list id orders on 64-bit keys
   bool autotune = true;
   std::map<TuneKey, int> tune;        // chosen variant per shape
   std::vector<TuneRecord> tune_log;   // every timing the autotuner took
@@ -723,6 +724,9 @@ gmls_status gmls_set_option(gmls_ctx* ctx, int32_t option, int64_t value) {
     case GMLS_OPT_POISON:
       ctx->poison = value != 0;
       return GMLS_OK;
+    case GMLS_OPT_ORDER_KEY64:
+      ctx->order_key64 = value != 0;
+      return GMLS_OK;
     case GMLS_OPT_CLEAR_TUNING:
       ctx->tune.clear();
       ctx->tune_log.clear();
@@ -1217,8 +1221,12 @@ static gmls_status ensure_order(gmls_ctx* ctx, NbrObj& nb, const char* who) {
   if (!nb.order) return fail(ctx, GMLS_ENOMEM, std::string(who) + ": arena exhausted (neighbour id order)");
   int kcap = 1;
   while (kcap < nb.cap) kcap <<= 1;
+  auto cit = ctx->objs.find(nb.cloud);
+  const int64_t n_points = (!ctx->order_key64 && cit != ctx->objs.end() && cit->second.kind == K_CLOUD)
+                               ? cit->second.c.n
+                               : INT64_MAX;  // INT64_MAX: 64-bit keys
   cudaError_t e = par ? launch_nbr_order_prefix(ctx->launch(), nb.n_tgt, par->order, par->k, nb.k, nb.order)
-                      : launch_nbr_order(ctx->launch(), nb.n_tgt, nb.off, nb.idx, kcap, nb.order);
+                      : launch_nbr_order(ctx->launch(), nb.n_tgt, nb.off, nb.idx, kcap, nb.order, n_points);
   if (e != cudaSuccess) {
     ctx->arena.release(nb.order);
     nb.order = nullptr;

@@ -247,9 +247,10 @@ cudaError_t launch_stencils_dfx(const Launch& L, const StencilJob& j, const DfxS
 
 // -------------------------------------------------------------------- CSR
 // id order of neighbour lists (see nbr_order_kernel): order[off[t] + r] =
-// position of target t's entry of rank r by particle id
+// position of target t's entry of rank r by particle id; n_points (the
+// cloud's size) selects the sort-key width
 cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off, const int32_t* idx, int kcap,
-                             int16_t* order);
+                             int16_t* order, int64_t n_points);
 // id order of the k-prefix of fixed-k lists from the order of the full lists
 // (kp entries per target): the positions below k, kept in their order
 cudaError_t launch_nbr_order_prefix(const Launch& L, int64_t n_tgt, const int16_t* parent_order, int kp, int k,

@@ -1293,8 +1293,8 @@ constexpr int kOrderWarps = 8;
 // Bitonic sort of 32 R keys held R per lane (element lane + 32 u in key[u]),
 // ascending: compare-exchanges across lanes by shuffles, within a lane for
 // strides of 32 and more.  Every size and stride is a compile-time constant.
-template <int R>
-__device__ __forceinline__ void warp_bitonic_keys(unsigned long long (&key)[R], int lane) {
+template <int R, typename K>
+__device__ __forceinline__ void warp_bitonic_keys(K (&key)[R], int lane) {
   constexpr int NE = 32 * R;
 #pragma unroll
   for (int size = 2; size <= NE; size <<= 1) {
@@ -1306,7 +1306,7 @@ __device__ __forceinline__ void warp_bitonic_keys(unsigned long long (&key)[R], 
           const int pu = u ^ (stride >> 5);
           if (pu > u) {  // element lane + 32 u is the lower one of the pair
             const bool asc = ((lane + 32 * u) & size) == 0;
-            const unsigned long long a = key[u], b = key[pu];
+            const K a = key[u], b = key[pu];
             const bool swap = asc ? (b < a) : (a < b);
             key[u] = swap ? b : a;
             key[pu] = swap ? a : b;
@@ -1315,11 +1315,11 @@ __device__ __forceinline__ void warp_bitonic_keys(unsigned long long (&key)[R], 
       } else {
 #pragma unroll
         for (int u = 0; u < R; ++u) {
-          const unsigned long long other = __shfl_xor_sync(0xffffffffu, key[u], stride);
+          const K other = __shfl_xor_sync(0xffffffffu, key[u], stride);
           const bool lower = (lane & stride) == 0;
           const bool asc = ((lane + 32 * u) & size) == 0;
-          const unsigned long long lo = other < key[u] ? other : key[u];
-          const unsigned long long hi = other < key[u] ? key[u] : other;
+          const K lo = other < key[u] ? other : key[u];
+          const K hi = other < key[u] ? key[u] : other;
           key[u] = (lower == asc) ? lo : hi;
         }
       }
@@ -1327,32 +1327,42 @@ __device__ __forceinline__ void warp_bitonic_keys(unsigned long long (&key)[R], 
   }
 }
 
-// key of a list entry: the id with its sign bit flipped (unsigned order =
-// signed order) above the position, so equal ids keep their list order
-__device__ __forceinline__ unsigned long long order_key(int32_t id, int pos) {
+// key of a list entry: the id above the position, so equal ids keep their
+// list order.  64-bit: the id with its sign bit flipped (unsigned order =
+// signed order) in the high word.  32-bit, for clouds of fewer than
+// 2^25 - 1 points and lists of at most 128 entries: id + 1 (the -1 of a short
+// list becomes 0, first as in signed order) above 7 position bits; the
+// largest key, (2^25 - 1) << 7 | 127 = ~0u, is then never a real entry, so
+// the padding (~0u) sorts after every entry as in the 64-bit form, and the
+// two forms give the same order.
+__device__ __forceinline__ unsigned long long order_key(int32_t id, int pos, unsigned long long) {
   return ((unsigned long long)((uint32_t)id ^ 0x80000000u) << 32) | (uint32_t)pos;
 }
+__device__ __forceinline__ unsigned int order_key(int32_t id, int pos, unsigned int) {
+  return ((uint32_t)(id + 1) << 7) | (uint32_t)pos;
+}
 
-template <int R>
+template <int R, typename K>
 __device__ __forceinline__ void order_in_registers(const int32_t* __restrict__ idx, int64_t o, int k, int lane,
                                                    int16_t* __restrict__ order) {
-  unsigned long long key[R];
+  constexpr uint32_t kPosMask = sizeof(K) == 4 ? 0x7fu : 0xffffffffu;
+  K key[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int e = lane + 32 * u;
-    key[u] = (e < k) ? order_key(idx[o + e], e) : ~0ull;
+    key[u] = (e < k) ? order_key(idx[o + e], e, K(0)) : ~K(0);
   }
   warp_bitonic_keys<R>(key, lane);
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int e = lane + 32 * u;
-    if (e < k) order[o + e] = (int16_t)(key[u] & 0xffffffffu);
+    if (e < k) order[o + e] = (int16_t)((uint32_t)key[u] & kPosMask);
   }
 }
 
 __global__ void __launch_bounds__(kOrderWarps * 32) nbr_order_kernel(int64_t n_tgt, const int64_t* __restrict__ off,
                                                                      const int32_t* __restrict__ idx, int kcap,
-                                                                     int16_t* __restrict__ order) {
+                                                                     int16_t* __restrict__ order, bool key32) {
   extern __shared__ __align__(16) unsigned char order_smem[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t* ids = reinterpret_cast<int32_t*>(order_smem) + (size_t)w * kcap;
@@ -1362,11 +1372,17 @@ __global__ void __launch_bounds__(kOrderWarps * 32) nbr_order_kernel(int64_t n_t
     const int64_t o = off[t];
     const int k = (int)(off[t + 1] - o);
     if (k <= 64) {  // short lists: keys in registers, no shared memory
-      order_in_registers<2>(idx, o, k, lane, order);
+      if (key32)
+        order_in_registers<2, unsigned int>(idx, o, k, lane, order);
+      else
+        order_in_registers<2, unsigned long long>(idx, o, k, lane, order);
       continue;
     }
     if (k <= 128) {
-      order_in_registers<4>(idx, o, k, lane, order);
+      if (key32)
+        order_in_registers<4, unsigned int>(idx, o, k, lane, order);
+      else
+        order_in_registers<4, unsigned long long>(idx, o, k, lane, order);
       continue;
     }
     int n2 = 1;
@@ -1400,7 +1416,7 @@ __global__ void __launch_bounds__(kOrderWarps * 32) nbr_order_kernel(int64_t n_t
 }
 
 cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off, const int32_t* idx, int kcap,
-                             int16_t* order) {
+                             int16_t* order, int64_t n_points) {
   if (n_tgt == 0) return cudaSuccess;
   if (kcap < 1 || kcap > kMaxK) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kOrderWarps * kcap * (sizeof(int32_t) + sizeof(int16_t));
@@ -1408,7 +1424,8 @@ cudaError_t launch_nbr_order(const Launch& L, int64_t n_tgt, const int64_t* off,
   if (e != cudaSuccess) return e;
   int64_t blocks = (n_tgt + kOrderWarps - 1) / kOrderWarps;
   if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
-  nbr_order_kernel<<<(unsigned)blocks, kOrderWarps * 32, smem, L.stream>>>(n_tgt, off, idx, kcap, order);
+  const bool key32 = n_points < (int64_t(1) << 25) - 1;  // 32-bit keys (lists of up to 128 entries)
+  nbr_order_kernel<<<(unsigned)blocks, kOrderWarps * 32, smem, L.stream>>>(n_tgt, off, idx, kcap, order, key32);
   *L.counter += 1;
   return cudaGetLastError();
 }

@@ -46,6 +46,7 @@ EXPORTED = [
 ]
 NOALLOC_MAX_POINTS = 262144
 OPT_FORCE_GENERIC, OPT_AUTOTUNE, OPT_CLEAR_TUNING, OPT_FORCE_VARIANT, OPT_POISON, OPT_FAIL_ALLOC = 0, 1, 2, 3, 4, 5
+OPT_ORDER_KEY64 = 6
 T_UNSUPPORTED = 64
 
 

@@ -401,6 +401,32 @@ def test_csr_of_prefix_lists_equals_direct_lists(ctx, parent_first):
     _release(ctx, cid, n48, n36p, n36, s48, sp, sd)
 
 
+@pytest.mark.parametrize("dim,n_axis,basis,m,k,fn,mode", [(2, 30, gmls.SCALAR, 4, 36, gmls.GRAD, gmls.KNN),
+                                                          (3, 10, gmls.DIVFREE, 3, 80, gmls.VEC_LAPLACIAN, gmls.KNN),
+                                                          (2, 28, gmls.SCALAR, 2, 12, gmls.GRAD, gmls.RADIUS)])
+def test_csr_column_order_same_for_both_key_widths(ctx, dim, n_axis, basis, m, k, fn, mode):
+    """The id order of the lists (the CSR column order) is sorted on 32-bit
+    keys for clouds below 2^25 - 1 points and on 64-bit keys above: forcing
+    the 64-bit keys on a small cloud gives the same operator bit for bit
+    (lists of up to 64 and of 65..128 entries, fixed-k and radius lists)."""
+    x = inputs.jittered_grid(dim, n_axis, seed=9)
+    cid = ctx.cloud(x)
+    kw = {"mode": mode, "cap": 40} if mode == gmls.RADIUS else {}
+    out = []
+    for key64 in (0, 1):
+        ctx.set_option(gmls.OPT_ORDER_KEY64, key64)
+        try:
+            nid = ctx.neighbors(cid, k, 1.6 if mode == gmls.RADIUS else 1.5, **kw)
+            sid = ctx.stencils(nid, basis, m, [fn])
+            out.append([t.cpu().numpy() for t in ctx.assemble_csr(sid, fn)])
+        finally:
+            ctx.set_option(gmls.OPT_ORDER_KEY64, 0)
+        _release(ctx, nid, sid)
+    assert all(np.array_equal(u, v) for u, v in zip(out[0], out[1]))
+    assert np.all(np.diff(out[0][1].reshape(-1)[: out[0][0][1]]) > 0)  # first row: ascending columns
+    _release(ctx, cid)
+
+
 def test_csr_assembled_in_target_ranges(ctx):
     """gmls_assemble_csr_at: an operator assembled range by range (one
     neighbour handle per contiguous target range, uneven range sizes, radius
